@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Throughput of the MG-MLQMC hot path on one GB300 (samples/s, KL + FMG).
+
+Workload (default): MLQMC with sample recycling in FP64, 6 levels of 8x8 ..
+256x256 cells, s = 100 KL modes (separable exponential covariance, sigma = 1,
+correlation length 0.3), rank-1 lattice (CBC, gamma_j = j^-2) with R = 16
+random shifts, N_l = 1024, 512, 256, 128, 64, 32 points per shift on levels
+0..5 (32,256 FMG solves per step), mean-of-u QoI. One step = normals, fields on
+every level of every sample, FMG with two V(2,2)-cycles per level, F_t and the
+reuse sums of every level, and the estimator from those sums.
+
+The same step in the mixed form (FP32 V-cycles inside FP64 refinement) is
+reported under "mixed". `--impl reference` times the CPU oracle as it stands
+on a bounded sample of the same workload.
+
+Multi-GPU (torchrun): each rank runs an independent replica (its own seed);
+no data-path collective; value = all ranks' samples / max time ("weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "samples/s (KL+FMG) and time-to-RMSE ε: mixed-precision vs FP64, one GB300"
+UNIT = "samples/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--counts-div", type=int, default=1,
+                    help="divide the per-level counts (small cases for profiler captures only)")
+    return ap.parse_args()
+
+
+def workload_config(rank: int, counts_div: int = 1):
+    cfg = dict(W.CONFIG2)
+    cfg["seed"] = cfg["seed"] + 1000 * rank
+    cfg["counts"] = [max(1, c // counts_div) for c in cfg["counts"]]
+    return cfg
+
+
+def work_list(cfg):
+    return W.fixed_count_work(cfg["counts"], cfg["R"])
+
+
+def n_samples(work):
+    return sum((ne - nb) * (re_ - rb) for (_, nb, ne, rb, re_) in work)
+
+
+# --------------------------------------------------------------------------- #
+# FP64 operation model of one sample (stated per step in the design notes)    #
+# --------------------------------------------------------------------------- #
+def fp64_ops_per_sample(level, cfg, Ka):
+    n0, s, mu0, nu1, nu2 = cfg["n0"], cfg["s"], cfg["mu0"], cfg["nu1"], cfg["nu2"]
+    N0 = n0 * n0
+    ops = 0.0
+    for t in range(level + 1):
+        n = n0 << t
+        M = n * n
+        # KL: G = sum over modes (2 s n), z = sum over Ka rows (2 Ka M), exp (M);
+        # faces (2 per cell x 4) and inverse diagonal (4)
+        ops += 2 * s * n + 2 * Ka * M + M + 12 * M
+        ops += M  # QoI
+    ops += 2 * N0 * n0 * n0 + 4 * N0 * n0  # band Cholesky of level 0 and the first solve
+
+    def vcycle(t):
+        tot = 4 * N0 * n0
+        for tau in range(1, t + 1):
+            M = (n0 << tau) ** 2
+            tot += ((nu1 + nu2) * 11 + 15 + 9) * M
+        return tot
+
+    for t in range(1, level + 1):
+        ops += 9 * (n0 << t) ** 2 + mu0 * vcycle(t)
+    return ops
+
+
+def clocks_start(path):
+    try:
+        f = open(path, "w")
+        p = subprocess.Popen(
+            ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+             "--format=csv,noheader,nounits", "-lms", "200"], stdout=f, stderr=subprocess.DEVNULL)
+        return p, f
+    except Exception:
+        return None, None
+
+
+def clocks_stop(handle, path, device_index=0):
+    p, f = handle
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    f.close()
+    rows = []
+    for line in open(path):
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9 or parts[0] != str(device_index):
+            continue
+        try:
+            rows.append((float(parts[1]), float(parts[2]), parts[5], parts[6], parts[7], parts[8]))
+        except ValueError:
+            continue
+    if not rows:
+        return None
+    mx = max(r[1] for r in rows)
+    loaded = [r for r in rows if r[0] > 0.5 * mx] or rows
+    reasons = set()
+    for r in rows:
+        for name, v in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"], r[2:]):
+            if v.lower().startswith("active"):
+                reasons.add(name)
+    return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": mx, "reasons": sorted(reasons),
+            "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# --------------------------------------------------------------------------- #
+# CPU oracle timing (baseline and reference arm)                              #
+# --------------------------------------------------------------------------- #
+def oracle_rate(cfg, counts, shift=0):
+    """Time the oracle as it stands (serial, one core) on counts[l] samples of level l, one shift."""
+    import oracle as O
+
+    z, _ = O.cbc(cfg["s"], cfg["log2_nmax"])
+    orc = O.Oracle(n_levels=cfg["n_levels"], n0=cfg["n0"], s=cfg["s"], sigma=cfg["sigma"], corr_len=cfg["corr_len"],
+                   qoi=cfg["qoi"], mu0=cfg["mu0"], nu1=cfg["nu1"], nu2=cfg["nu2"], sampler=cfg["sampler"],
+                   seed=cfg["seed"], R=cfg["R"], genvec=z, log2_nmax=cfg["log2_nmax"], reuse=cfg["reuse"])
+    work = [(lv, 0, int(c), shift, shift + 1) for lv, c in enumerate(counts) if c > 0]
+    t0 = time.perf_counter()
+    orc.sample_levels(work)
+    dt = time.perf_counter() - t0
+    return n_samples(work), dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg = workload_config(0)
+    counts = [max(1, c // 16) for c in cfg["counts"]]
+    times = []
+    for i in range(args.warmup + args.steps):
+        ns, dt = oracle_rate(cfg, counts, shift=i % cfg["R"])
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = ns * len(times) / total
+    sample = (f"per step: one shift, N_l/16 = {counts} samples of levels 0..5 "
+              f"({ns} FMG solves, same level mix as the full step)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "MLQMC with reuse, FP64, 6 levels 8x8..256x256, s=100, R=16, "
+                                   "N_l=1024..32 (bounded sample on CPU)", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- #
+# GPU arm                                                                    #
+# --------------------------------------------------------------------------- #
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1806_05619_gb300 as M
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if not os.path.exists(M.LIB_PATH):
+        raise RuntimeError("libmlqmc.so is not built; run __graft_entry__.build()")
+
+    cfg = workload_config(rank, args.counts_div)
+    work = work_list(cfg)
+    ns = n_samples(work)
+    genvec, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
+    ctx = M.Context.from_config(cfg, genvec=genvec, max_samples=ns)
+    nl, R = cfg["n_levels"], cfg["R"]
+    sums = torch.zeros(nl * R * 2, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        sums.zero_()
+        ctx.sample_levels(work, sums, stream=stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.check_device(stream)
+    barrier()
+
+    # device-timed steps (L2 flushed between steps, outside the events)
+    clk_path = os.path.join(tempfile.gettempdir(), f"clocks_{os.getpid()}.csv")
+    clk = clocks_start(clk_path)
+    launches0 = ctx.launch_count()
+    ctx.profile(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    barrier()
+    launches = ctx.launch_count() - launches0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    clocks = clocks_stop(clk, clk_path, device_index=local)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tot_ms = float(t.item())
+    ctx.check_device(stream)
+    value = ns * world * args.steps / (tot_ms * 1e-3)
+
+    # end to end through the public API from the host: work list in, estimate out
+    e2e_times = []
+    host_sums = torch.empty(nl * R * 2, dtype=torch.float64, pin_memory=True)
+    for i in range(args.steps):
+        flush.zero_()
+        barrier()
+        t0 = time.perf_counter()
+        step()
+        host_sums.copy_(sums, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        S = host_sums.numpy().reshape(nl, R, 2)
+        # estimator from the sums (eqs. Upsilon-reuse, MGMLQMC, var_of_mgmlqmc)
+        cnt = np.cumsum(np.array(cfg["counts"][::-1]))[::-1]
+        Ups = S[:, :, 0] / cnt[:, None]
+        Qr = Ups.sum(axis=0)
+        est = (Qr.mean(), Qr.var(ddof=1) / R)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_t = torch.tensor([sum(e2e_times)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = ns * world * args.steps / float(e2e_t.item())
+    h2d = len(work) * 32 + ns * (24 + 8)  # work list + the library's per-sample descriptors
+    d2h = nl * R * 2 * 8
+
+    # roofline of the dominant kernel (FMG solver) from the live event timing
+    a, b, th = ctx.modes()
+    Ka = int(a.max()) + 1
+    ops_step = sum((ne - nb) * (re_ - rb) * fp64_ops_per_sample(lv, cfg, Ka) for (lv, nb, ne, rb, re_) in work)
+    fmg_ms, fmg_n = prof["fmg"]
+    per_launch_s = fmg_ms * 1e-3 / max(1, fmg_n)
+    achieved = ops_step / per_launch_s / 1e12
+    peak_fp64 = 1.25  # TFLOP/s, GB300 FP64 (nominal; an FMA probe measured 1.20)
+    share = fmg_ms / max(1e-9, sum(v[0] for v in prof.values()))
+
+    mixed = None
+    if not args.no_mixed:
+        mixed = run_mixed_same_workload(args, cfg, work, genvec, dev, stream, flush, M)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        counts = [max(1, c // 2) for c in cfg["counts"]]
+        nsc, dt = oracle_rate(cfg, counts, shift=0)
+        cpu = {"value": nsc / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one shift, N_l/2 = {counts} samples of levels 0..5 ({nsc} FMG solves, "
+                         f"1/32 of the step, same level mix), serial oracle, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "MLQMC with reuse, FP64, 6 levels 8x8..256x256 cells, s=100 KL modes "
+                                   "(sep. exponential, sigma=1, lambda=0.3), lattice 2^10 points halving per "
+                                   "level, R=16 shifts, N_l=1024,512,256,128,64,32 per shift, FMG mu0=2 V(2,2) "
+                                   "RB-GS, mean-of-u QoI",
+                       "samples_per_step": ns * world, "counts_div": args.counts_div,
+                       "l2": "flushed between timed steps (512 MiB write)",
+                       "parallelism": f"independent replicas x{world}"},
+            "gpu_launches": launches,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
+                         "frac": achieved / peak_fp64, "traffic": None,
+                         "kernel": "k_fmg<double> (KL synthesis + FMG + QoI)",
+                         "ops_per_launch": ops_step, "ms_per_launch": per_launch_s * 1e3,
+                         "share_of_step": share, "peak_source": "nominal FP64 1.25 TFLOP/s (probe: 1.20)"},
+            "kernel_ms": {k: v[0] / max(1, v[1]) for k, v in prof.items()},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "estimate": {"Q": float(est[0]), "varQ": float(est[1])}},
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        if mixed:
+            line["mixed"] = mixed
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_mixed_same_workload(args, cfg64, work, genvec, dev, stream, flush, M):
+    """The same step with FP32 V-cycles inside FP64 refinement (mu0 refinement
+    steps per level, each one FP32 V(2,2)-cycle on the FP64 residual)."""
+    import torch
+
+    cfg = dict(cfg64)
+    cfg["precision"] = "mixed_tf32"
+    ns = n_samples(work)
+    ctx = M.Context.from_config(cfg, genvec=genvec, max_samples=ns)
+    nl, R = cfg["n_levels"], cfg["R"]
+    sums = torch.zeros(nl * R * 2, dtype=torch.float64, device=dev)
+
+    def step():
+        sums.zero_()
+        ctx.sample_levels(work, sums, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.check_device(stream)
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    ctx.check_device(stream)
+    tot = sum(a.elapsed_time(b) for a, b in ev)
+    return {"value": ns * args.steps / (tot * 1e-3), "unit": UNIT, "ms_per_step": tot / args.steps,
+            "dtype": "f32 V-cycles in f64 refinement, f32 field"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

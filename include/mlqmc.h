@@ -1,0 +1,256 @@
+/*
+ * mlqmc.h -- C ABI of the GB300 (sm_103a) library for the multigrid multilevel
+ * (quasi-)Monte Carlo method with sample recycling of Robbe, Nuyens and
+ * Vandewalle (arXiv 1806.05619).
+ *
+ * Per sample the library draws y (a randomly shifted rank-1 lattice point
+ * mapped to standard normals, Sec. 3.2, or Monte Carlo normals), synthesises
+ * the lognormal Karhunen-Loeve field a = exp(z_s) on every grid level
+ * (eq. truncatedKL, Sec. 5), solves -div(a grad u) = 1 on (0,1)^2 with zero
+ * Dirichlet data by Full Multigrid (Sec. 4, Fig. FMG), and recycles the
+ * solution of every level of that FMG into the level differences of the
+ * MG-MLQMC estimator (eqs. Upsilon-reuse, MGMLQMC, var_of_mgmlqmc).
+ *
+ * Conventions for every entry point:
+ *  - Plain C types only. "Device" pointers are CUDA global-memory addresses
+ *    on the current device; "host" pointers are ordinary CPU memory.
+ *  - The caller owns every pointer it passes; the library never frees them and
+ *    keeps no reference after the call returns (genvec is copied).
+ *  - A context owns all library scratch in device memory (tables, workspace).
+ *  - Streams are passed as void* holding a cudaStream_t (NULL = legacy stream).
+ *  - Every call returns an mlqmc_status; nothing throws across the ABI and
+ *    nothing traps on the device. Errors raised inside kernels are recorded in
+ *    a per-context device status word read by mlqmc_get_device_status.
+ *  - One context must not be used from two host threads at once.
+ */
+#ifndef MLQMC_H
+#define MLQMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MLQMC_OK = 0,
+    MLQMC_ERR_INVALID_ARG = 1,      /* a size, index or option is out of range */
+    MLQMC_ERR_CUDA = 2,             /* a CUDA runtime call failed */
+    MLQMC_ERR_OOM = 3,              /* device or host allocation failed */
+    MLQMC_ERR_POINTS_EXHAUSTED = 4, /* lattice index n >= 2^log2_nmax requested */
+    MLQMC_ERR_NOT_CONVERGED = 5,    /* a level missed refine_rtol within refine_max_iter */
+    MLQMC_ERR_TIMEOUT = 6,          /* a bounded device wait gave up */
+    MLQMC_ERR_DEVICE_STATUS = 7,    /* a kernel reported an internal check failure */
+    MLQMC_ERR_UNSUPPORTED = 8       /* option combination not built */
+} mlqmc_status;
+
+typedef enum {
+    MLQMC_FP64 = 0,         /* every step in FP64 */
+    MLQMC_MIXED_TF32 = 1,   /* KL contraction in TF32 (FP32 accumulate), FP32 V-cycles,
+                               FP64 outer residual/correction */
+    MLQMC_MIXED_BF16X3 = 2  /* as MIXED_TF32 with a three-term split-bf16 contraction */
+} mlqmc_precision;
+
+typedef enum { MLQMC_QOI_CENTER = 0, MLQMC_QOI_MEAN = 1 } mlqmc_qoi;
+typedef enum { MLQMC_SAMPLER_MC = 0, MLQMC_SAMPLER_LATTICE = 1 } mlqmc_sampler;
+
+/*
+ * Problem statement (Sec. 1 eq. PDE; Sec. 6 set-up restated on a cell-centred
+ * finite-volume grid).
+ *  n_levels      L+1 grid levels; level t has (coarse_cells * 2^t)^2 cells.
+ *  coarse_cells  cells per side on level 0 (even, >= 2).
+ *  n_modes       s, KL terms kept (eq. truncatedKL), 1..4096.
+ *  sigma, corr_len  separable exponential covariance
+ *                sigma^2 exp(-|x1-x1'|/corr_len - |x2-x2'|/corr_len).
+ *  qoi           MLQMC_QOI_CENTER: mean of the four cells around (1/2,1/2)
+ *                (the point value of Sec. 6 on a cell-centred grid);
+ *                MLQMC_QOI_MEAN: mean of u over the domain.
+ *  mu0, nu1, nu2 FMG cycles per level and pre/post red-black Gauss-Seidel sweeps
+ *                (Sec. 4: mu0, mu1, mu2).
+ *  precision     mlqmc_precision.
+ *  refine_rtol   0: FMG with exactly mu0 V-cycles per level (fixed work).
+ *                >0: after the mu0 cycles each level is iterated until
+ *                ||b - A u||_2 / ||b||_2 <= refine_rtol (FP64 residual; in the
+ *                mixed forms each correction is an FP32 V-cycle solve).
+ *  refine_max_iter cap on extra cycles / refinement steps per level.
+ *  sampler       mlqmc_sampler.
+ *  seed          Philox key: random shifts (lattice) or the normals (MC).
+ *  n_shifts      R independent shifts (or MC replicates), 1..4096.
+ *  genvec        host array of n_modes odd generating-vector entries (lattice
+ *                only; copied at create time); see mlqmc_cbc_genvec.
+ *  log2_nmax     lattice sequence length 2^log2_nmax (0..32).
+ *  reuse         1: MG-ML(Q)MC, every FMG level feeds its difference (eq.
+ *                MGMLMC); 0: plain ML(Q)MC, only the finest difference counts.
+ */
+typedef struct {
+    int32_t n_levels;
+    int32_t coarse_cells;
+    int32_t n_modes;
+    int32_t pad0;
+    double sigma;
+    double corr_len;
+    int32_t qoi;
+    int32_t mu0, nu1, nu2;
+    int32_t precision;
+    int32_t pad1;
+    double refine_rtol;
+    int32_t refine_max_iter;
+    int32_t sampler;
+    uint64_t seed;
+    int32_t n_shifts;
+    int32_t pad2;
+    const uint32_t* genvec;
+    int32_t log2_nmax;
+    int32_t reuse;
+} mlqmc_problem;
+
+/*
+ * One block of samples (Algorithm 1, SampleAndSolve): samples whose FMG ends
+ * at `level`, lattice (or MC) indices n_begin..n_end-1, shifts r_begin..r_end-1.
+ * Samples are ordered item by item, then by r, then by n.
+ */
+typedef struct {
+    int32_t level;
+    int32_t pad;
+    int64_t n_begin, n_end;
+    int32_t r_begin, r_end;
+} mlqmc_work;
+
+typedef struct mlqmc_ctx mlqmc_ctx;
+
+/* Adaptive run options (Algorithm 1). */
+typedef struct {
+    int32_t max_rounds;   /* cap on SampleAndSolve calls (0 -> 1000) */
+    int32_t cost_model;   /* 0: C_l = sum_{t<=l} n_t^2 (deterministic); 1: measured GPU time */
+    int32_t batched;      /* 0: one level per round (exact Algorithm 1);
+                             1: every level with V_l/C_l >= max/2 doubles in one launch */
+    int32_t pad;
+} mlqmc_run_opts;
+
+typedef struct {
+    double Q;             /* eq. MGMLQMC */
+    double varQ;          /* eq. var_of_mgmlqmc */
+    double bias;          /* eq. bias, |Ybar_L| / (2^alpha + 1) */
+    double alpha;         /* least-squares rate of |Ybar_l|, l = 1..L */
+    int32_t L;            /* finest level used */
+    int32_t rounds;       /* SampleAndSolve calls */
+    int32_t run_status;   /* 0 done; 7 stopped at the finest available level; 8 round cap */
+    int32_t alpha_clamped;
+    double wall_seconds;  /* host wall time of the whole run */
+    double gpu_seconds;   /* device time of all sample launches (CUDA events) */
+    int64_t N[32];        /* samples whose FMG ended at each level */
+    double Ybar[32];      /* eq. Upsilon-reuse-bar */
+    double Vell[32];      /* eq. sample_variances */
+    double C[32];         /* cost per sample used by the level choice */
+} mlqmc_result;
+
+/*
+ * Create a context: validates the problem, builds the KL eigenpairs in closed
+ * form (eq. inteq for the exponential kernel), the mode table, the per-level
+ * 1D eigenfunction tables, and allocates device workspace for
+ * max_samples_per_call samples per mlqmc_sample_levels call (0 -> 65536).
+ * The current CUDA device at this call is the context's device.
+ * Errors: INVALID_ARG (bad sizes, even genvec entry, NULL out), OOM, CUDA.
+ */
+mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples_per_call, mlqmc_ctx** out);
+
+/* Release everything the context owns. NULL is a no-op. */
+void mlqmc_destroy(mlqmc_ctx* c);
+
+/*
+ * Run SampleAndSolve (Algorithm 1) for a list of sample blocks on `stream`
+ * and ACCUMULATE the level-difference sums (eq. Upsilon-reuse numerators):
+ *   d_sums[(t*R + r)*2 + 0] += sum of dF_t,  [.. + 1] += sum of dF_t^2
+ * over the samples of shift r whose FMG level k >= t (reuse) or k == t (no
+ * reuse), dF_t = F_t - F_{t-1}, F_{-1} = 0.
+ *  d_sums  device, n_levels * R * 2 doubles, caller-owned, not cleared.
+ *  d_F     device or NULL: per sample (in work order) n_levels doubles,
+ *          F_0..F_level then zeros.
+ * Asynchronous: returns after enqueueing. Host-side validation errors
+ * (INVALID_ARG, POINTS_EXHAUSTED, more samples than max_samples_per_call)
+ * are returned at once; device-side failures (NOT_CONVERGED) are recorded
+ * for mlqmc_get_device_status. Sums are deterministic for a given input.
+ */
+mlqmc_status mlqmc_sample_levels(mlqmc_ctx* c, const mlqmc_work* work, int32_t n_work,
+                                 double* d_sums, double* d_F, void* stream);
+
+/*
+ * Algorithm 1 (MG-MLQMC(eps)): adaptive levels and sample doubling until the
+ * variance estimate is <= eps^2/2 and the bias estimate is <= eps/sqrt(2).
+ * Blocking; the result is in host memory. Uses its own stream.
+ */
+mlqmc_status mlqmc_estimate(mlqmc_ctx* c, double eps, const mlqmc_run_opts* opts, mlqmc_result* out);
+
+/* Synchronise `stream`, return and clear the deferred device status. */
+mlqmc_status mlqmc_get_device_status(mlqmc_ctx* c, void* stream);
+
+/* Static text for a status code. */
+const char* mlqmc_status_string(mlqmc_status s);
+
+/*
+ * Generating vector by component-by-component construction (Sec. 3.2 cites
+ * Nuyens-Cools): N = 2^m points, product weights gamma (host, s entries),
+ * criterion e^2 = -1 + N^-1 sum_k prod_j (1 + gamma_j B2({k z_j/N})),
+ * B2(x) = x^2 - x + 1/6; z_1 = 1; candidates odd z <= N/2, ties -> smallest.
+ * Host only, multi-threaded. z_out: s entries; e2_out (may be NULL): the
+ * criterion after each component. Errors: INVALID_ARG (s < 1, m < 1, m > 24).
+ */
+mlqmc_status mlqmc_cbc_genvec(int32_t s, int32_t m, const double* gamma, uint32_t* z_out,
+                              double* e2_out);
+
+/* ---- Introspection of intermediate steps (parity tests and tools) ------- */
+
+/* The context's modes (eq. truncatedKL ordering): host arrays of n_modes. */
+mlqmc_status mlqmc_modes(const mlqmc_ctx* c, int32_t* a, int32_t* b, double* theta);
+
+/*
+ * Lattice bits (Sec. 3.2): d_bits[i*s + j] = ((bitrev32(n_i) z_j mod 2^32) << 32)
+ * + S_{level,r,j} mod 2^64 for n_i = n_begin + i, i < count (device uint64).
+ * MC sampler: the 64 Philox bits of coordinate j instead.
+ */
+mlqmc_status mlqmc_point_bits(mlqmc_ctx* c, int32_t level, int32_t r, int64_t n_begin,
+                              int32_t count, uint64_t* d_bits, void* stream);
+
+/* Normals y = Phi^{-1}(u) for the same samples: d_y[i*s + j], FP64, device. */
+mlqmc_status mlqmc_normals(mlqmc_ctx* c, int32_t level, int32_t r, int64_t n_begin,
+                           int32_t count, double* d_y, void* stream);
+
+/*
+ * Field on grid level t for `count` normal vectors d_y[i*s + j] (device):
+ * d_k[i*n_t^2 + i2*n_t + i1] = exp(z_s) at cell centres, FP64 output, computed
+ * in the context's precision (FP64 form: FP64 synthesis; mixed forms: the
+ * tensor-core contraction, rounded to FP32, widened).
+ */
+mlqmc_status mlqmc_fields(mlqmc_ctx* c, int32_t t, const double* d_y, int32_t count, double* d_k,
+                          void* stream);
+
+/*
+ * One sample (level, r, n): the solutions of all its FMG levels, concatenated
+ * level 0..level, FP64, device (sum_t n_t^2 doubles), and F_0..F_level into
+ * d_F (device, level+1 doubles).
+ */
+mlqmc_status mlqmc_sample_solution(mlqmc_ctx* c, int32_t level, int32_t r, int64_t n, double* d_u,
+                                   double* d_F, void* stream);
+
+/* Kernel launches issued by this context since creation (all entry points). */
+int64_t mlqmc_launch_count(const mlqmc_ctx* c);
+
+/*
+ * Per-kernel device timing of mlqmc_sample_levels (off by default). With
+ * enable = 1 every later launch is bracketed by CUDA events recorded on the
+ * launch stream; enable = 0 stops recording. Either call clears the totals.
+ */
+mlqmc_status mlqmc_profile(mlqmc_ctx* c, int32_t enable);
+
+/*
+ * Totals since the last mlqmc_profile call, per kernel kind: index 0 normals,
+ * 1 FMG solver, 2 reuse sums. out_ms: device milliseconds (host, 3 doubles);
+ * out_n: launches (host, 3 int64). Waits for the recorded events.
+ */
+mlqmc_status mlqmc_profile_read(mlqmc_ctx* c, double* out_ms, int64_t* out_n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLQMC_H */

@@ -1,0 +1,270 @@
+"""GB300 (sm_103a) library for the multigrid multilevel (quasi-)Monte Carlo
+method with sample recycling (Robbe, Nuyens, Vandewalle, arXiv 1806.05619).
+
+This module only marshals arguments to the C ABI declared in
+``include/mlqmc.h`` (``libmlqmc.so``, built in-tree by :func:`build`). Every
+step of the method runs in the library's CUDA kernels; PyTorch is used for
+device memory and streams only. Importing works without a GPU; any call that
+needs the library raises if ``libmlqmc.so`` is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Iterable, Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmlqmc.so")
+_lock = threading.Lock()
+_lib = None
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "POINTS_EXHAUSTED", 5: "NOT_CONVERGED",
+          6: "TIMEOUT", 7: "DEVICE_STATUS", 8: "UNSUPPORTED"}
+PRECISION = {"fp64": 0, "mixed_tf32": 1, "mixed_bf16x3": 2}
+QOI = {"center": 0, "mean": 1}
+SAMPLER = {"mc": 0, "lattice": 1}
+
+
+class MlqmcError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({_status_text(code)})")
+
+
+class Problem(C.Structure):
+    _fields_ = [
+        ("n_levels", C.c_int32), ("coarse_cells", C.c_int32), ("n_modes", C.c_int32), ("pad0", C.c_int32),
+        ("sigma", C.c_double), ("corr_len", C.c_double),
+        ("qoi", C.c_int32), ("mu0", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32),
+        ("precision", C.c_int32), ("pad1", C.c_int32),
+        ("refine_rtol", C.c_double), ("refine_max_iter", C.c_int32), ("sampler", C.c_int32),
+        ("seed", C.c_uint64), ("n_shifts", C.c_int32), ("pad2", C.c_int32),
+        ("genvec", C.POINTER(C.c_uint32)), ("log2_nmax", C.c_int32), ("reuse", C.c_int32),
+    ]
+
+
+class Work(C.Structure):
+    _fields_ = [("level", C.c_int32), ("pad", C.c_int32), ("n_begin", C.c_int64), ("n_end", C.c_int64),
+                ("r_begin", C.c_int32), ("r_end", C.c_int32)]
+
+
+class RunOpts(C.Structure):
+    _fields_ = [("max_rounds", C.c_int32), ("cost_model", C.c_int32), ("batched", C.c_int32),
+                ("pad", C.c_int32)]
+
+
+class Result(C.Structure):
+    _fields_ = [
+        ("Q", C.c_double), ("varQ", C.c_double), ("bias", C.c_double), ("alpha", C.c_double),
+        ("L", C.c_int32), ("rounds", C.c_int32), ("run_status", C.c_int32), ("alpha_clamped", C.c_int32),
+        ("wall_seconds", C.c_double), ("gpu_seconds", C.c_double),
+        ("N", C.c_int64 * 32), ("Ybar", C.c_double * 32), ("Vell", C.c_double * 32), ("C", C.c_double * 32),
+    ]
+
+
+def build(verbose: bool = False) -> str:
+    """Compile ``libmlqmc.so`` for sm_103a in-tree (nvcc)."""
+    from . import buildlib as _b
+    return _b.build(verbose=verbose)
+
+
+def lib():
+    """The loaded C library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libmlqmc.so is not built ({LIB_PATH}); call paper_1806_05619_gb300.build()")
+            L = C.CDLL(LIB_PATH)
+            vp, i32, i64, dp = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double)
+            L.mlqmc_create.argtypes = [C.POINTER(Problem), i64, C.POINTER(vp)]
+            L.mlqmc_destroy.argtypes = [vp]
+            L.mlqmc_destroy.restype = None
+            L.mlqmc_sample_levels.argtypes = [vp, C.POINTER(Work), i32, vp, vp, vp]
+            L.mlqmc_estimate.argtypes = [vp, C.c_double, C.POINTER(RunOpts), C.POINTER(Result)]
+            L.mlqmc_get_device_status.argtypes = [vp, vp]
+            L.mlqmc_status_string.argtypes = [C.c_int]
+            L.mlqmc_status_string.restype = C.c_char_p
+            L.mlqmc_cbc_genvec.argtypes = [i32, i32, dp, C.POINTER(C.c_uint32), dp]
+            L.mlqmc_modes.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), dp]
+            L.mlqmc_point_bits.argtypes = [vp, i32, i32, i64, i32, vp, vp]
+            L.mlqmc_normals.argtypes = [vp, i32, i32, i64, i32, vp, vp]
+            L.mlqmc_fields.argtypes = [vp, i32, vp, i32, vp, vp]
+            L.mlqmc_sample_solution.argtypes = [vp, i32, i32, i64, vp, vp, vp]
+            L.mlqmc_profile.argtypes = [vp, i32]
+            L.mlqmc_profile_read.argtypes = [vp, dp, C.POINTER(C.c_int64)]
+            L.mlqmc_launch_count.argtypes = [vp]
+            L.mlqmc_launch_count.restype = i64
+            for name in ["mlqmc_create", "mlqmc_sample_levels", "mlqmc_estimate", "mlqmc_get_device_status",
+                         "mlqmc_cbc_genvec", "mlqmc_modes", "mlqmc_point_bits", "mlqmc_normals", "mlqmc_fields",
+                         "mlqmc_sample_solution", "mlqmc_profile", "mlqmc_profile_read"]:
+                getattr(L, name).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _status_text(code: int) -> str:
+    try:
+        return lib().mlqmc_status_string(int(code)).decode()
+    except Exception:
+        return ""
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise MlqmcError(code, where)
+
+
+def cbc_genvec(s: int, m: int, gamma: Optional[Sequence[float]] = None):
+    """CBC generating vector for 2^m points with product weights (default j^-2)."""
+    if gamma is None:
+        gamma = [1.0 / (j + 1) ** 2 for j in range(s)]
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    z = (C.c_uint32 * s)()
+    e2 = np.zeros(s)
+    _check(lib().mlqmc_cbc_genvec(int(s), int(m), g.ctypes.data_as(C.POINTER(C.c_double)), z,
+                                  e2.ctypes.data_as(C.POINTER(C.c_double))), "mlqmc_cbc_genvec")
+    return np.array(list(z), dtype=np.uint32), e2
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return C.c_void_p(int(t.data_ptr()))
+
+
+def _stream(stream) -> C.c_void_p:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(int(stream.cuda_stream))
+
+
+class Context:
+    """One problem on the current CUDA device (wraps ``mlqmc_ctx``)."""
+
+    def __init__(self, n_levels, coarse_cells, n_modes, sigma=1.0, corr_len=0.3, qoi="mean", mu0=2, nu1=2,
+                 nu2=2, precision="fp64", refine_rtol=0.0, refine_max_iter=60, sampler="lattice", seed=0,
+                 n_shifts=16, genvec=None, log2_nmax=20, reuse=True, max_samples=65536):
+        self.n_levels, self.n0, self.s, self.R = n_levels, coarse_cells, n_modes, n_shifts
+        self.precision = precision
+        zp = None
+        self._z = None
+        if sampler == "lattice":
+            if genvec is None:
+                raise ValueError("lattice sampler needs a generating vector")
+            self._z = (C.c_uint32 * n_modes)(*[int(v) for v in genvec[:n_modes]])
+            zp = C.cast(self._z, C.POINTER(C.c_uint32))
+        p = Problem(n_levels=n_levels, coarse_cells=coarse_cells, n_modes=n_modes, sigma=sigma, corr_len=corr_len,
+                    qoi=QOI[qoi], mu0=mu0, nu1=nu1, nu2=nu2, precision=PRECISION[precision],
+                    refine_rtol=refine_rtol, refine_max_iter=refine_max_iter, sampler=SAMPLER[sampler],
+                    seed=seed, n_shifts=n_shifts, genvec=zp, log2_nmax=log2_nmax, reuse=1 if reuse else 0)
+        h = C.c_void_p()
+        _check(lib().mlqmc_create(C.byref(p), int(max_samples), C.byref(h)), "mlqmc_create")
+        self.h = h
+
+    @classmethod
+    def from_config(cls, cfg: dict, genvec=None, **over):
+        kw = dict(n_levels=cfg["n_levels"], coarse_cells=cfg["n0"], n_modes=cfg["s"], sigma=cfg["sigma"],
+                  corr_len=cfg["corr_len"], qoi=cfg["qoi"], mu0=cfg["mu0"], nu1=cfg["nu1"], nu2=cfg["nu2"],
+                  precision=cfg["precision"], refine_rtol=cfg["rtol"], refine_max_iter=cfg["max_cycles"],
+                  sampler=cfg["sampler"], seed=cfg["seed"], n_shifts=cfg["R"], log2_nmax=cfg["log2_nmax"],
+                  reuse=cfg["reuse"], genvec=genvec)
+        kw.update(over)
+        return cls(**kw)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mlqmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def n(self, t):
+        return self.n0 << t
+
+    def modes(self):
+        a = (C.c_int32 * self.s)(); b = (C.c_int32 * self.s)(); th = np.zeros(self.s)
+        _check(lib().mlqmc_modes(self.h, a, b, th.ctypes.data_as(C.POINTER(C.c_double))), "mlqmc_modes")
+        return np.array(list(a)), np.array(list(b)), th
+
+    def sample_levels(self, work: Iterable, sums, F=None, stream=None):
+        """Accumulate the reuse sums (device tensor n_levels x R x 2, float64) for a work list."""
+        work = list(work)
+        arr = (Work * max(1, len(work)))()
+        for i, (lv, nb, ne, rb, re_) in enumerate(work):
+            arr[i] = Work(level=lv, pad=0, n_begin=nb, n_end=ne, r_begin=rb, r_end=re_)
+        _check(lib().mlqmc_sample_levels(self.h, arr, len(work), _ptr(sums), _ptr(F), _stream(stream)),
+               "mlqmc_sample_levels")
+
+    def device_status(self, stream=None):
+        return lib().mlqmc_get_device_status(self.h, _stream(stream))
+
+    def check_device(self, stream=None):
+        _check(self.device_status(stream), "device status")
+
+    def estimate(self, eps, max_rounds=0, cost_model=0, batched=False):
+        o = RunOpts(max_rounds=max_rounds, cost_model=cost_model, batched=1 if batched else 0)
+        res = Result()
+        _check(lib().mlqmc_estimate(self.h, float(eps), C.byref(o), C.byref(res)), "mlqmc_estimate")
+        L = res.L
+        return dict(Q=res.Q, varQ=res.varQ, bias=res.bias, alpha=res.alpha, L=L, rounds=res.rounds,
+                    run_status=res.run_status, alpha_clamped=res.alpha_clamped, wall_seconds=res.wall_seconds,
+                    gpu_seconds=res.gpu_seconds, N=[res.N[i] for i in range(self.n_levels)],
+                    Ybar=[res.Ybar[i] for i in range(self.n_levels)],
+                    Vell=[res.Vell[i] for i in range(self.n_levels)], C=[res.C[i] for i in range(self.n_levels)])
+
+    def point_bits(self, level, r, n_begin, count, stream=None):
+        import torch
+        out = torch.empty(count * self.s, dtype=torch.int64, device="cuda")
+        _check(lib().mlqmc_point_bits(self.h, level, r, n_begin, count, _ptr(out), _stream(stream)), "point_bits")
+        return out.view(count, self.s)
+
+    def normals(self, level, r, n_begin, count, stream=None):
+        import torch
+        out = torch.empty(count * self.s, dtype=torch.float64, device="cuda")
+        _check(lib().mlqmc_normals(self.h, level, r, n_begin, count, _ptr(out), _stream(stream)), "normals")
+        return out.view(count, self.s)
+
+    def fields(self, t, y, stream=None):
+        import torch
+        y = y.to(device="cuda", dtype=torch.float64).contiguous()
+        count = y.shape[0]
+        out = torch.empty(count * self.n(t) ** 2, dtype=torch.float64, device="cuda")
+        _check(lib().mlqmc_fields(self.h, t, _ptr(y), count, _ptr(out), _stream(stream)), "fields")
+        return out.view(count, self.n(t) ** 2)
+
+    def sample_solution(self, level, r, n, stream=None):
+        import torch
+        tot = sum(self.n(t) ** 2 for t in range(level + 1))
+        u = torch.empty(tot, dtype=torch.float64, device="cuda")
+        F = torch.empty(level + 1, dtype=torch.float64, device="cuda")
+        _check(lib().mlqmc_sample_solution(self.h, level, r, n, _ptr(u), _ptr(F), _stream(stream)),
+               "sample_solution")
+        sols, off = [], 0
+        for t in range(level + 1):
+            m = self.n(t) ** 2
+            sols.append(u[off:off + m])
+            off += m
+        return sols, F
+
+    def profile(self, enable: bool = True):
+        """Start (or stop) per-kernel CUDA-event timing of sample_levels; clears totals."""
+        _check(lib().mlqmc_profile(self.h, 1 if enable else 0), "mlqmc_profile")
+
+    def profile_read(self):
+        """{kind: (ms, launches)} for kinds 'points', 'fmg', 'sums' since profile()."""
+        ms = np.zeros(3)
+        n = (C.c_int64 * 3)()
+        _check(lib().mlqmc_profile_read(self.h, ms.ctypes.data_as(C.POINTER(C.c_double)), n), "mlqmc_profile_read")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(["points", "fmg", "sums"])}
+
+    def launch_count(self) -> int:
+        return int(lib().mlqmc_launch_count(self.h))

@@ -1,0 +1,316 @@
+"""GPU path against the FP64 oracle through the C ABI.
+
+Tolerances (FP64 form): lattice bits bit-exact; normals 1e-14 relative (CUDA's
+normcdfinv against AS 241, both within a few ulp); fields, solutions and F_t
+1e-12 relative; reuse sums within 1e-12 of the sum of |F_t| + |F_{t-1}| over
+the samples entering them (dF_t cancels, and the two sides add in different
+orders).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+M = pytest.importorskip("paper_1806_05619_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import os
+    if not os.path.exists(M.LIB_PATH):
+        M.build()
+    assert torch.cuda.is_available()
+
+
+def _genvec(cfg):
+    if cfg["sampler"] != "lattice":
+        return None
+    z, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
+    zo, _ = O.cbc(cfg["s"], cfg["log2_nmax"])
+    assert np.array_equal(z, zo)
+    return z
+
+
+def _pair(cfg, **over):
+    cfg = W.scaled(cfg, **over)
+    z = _genvec(cfg)
+    ctx = M.Context.from_config(cfg, genvec=z)
+    orc = O.Oracle(n_levels=cfg["n_levels"], n0=cfg["n0"], s=cfg["s"], sigma=cfg["sigma"],
+                   corr_len=cfg["corr_len"], qoi=cfg["qoi"], mu0=cfg["mu0"], nu1=cfg["nu1"], nu2=cfg["nu2"],
+                   rtol=cfg["rtol"] if cfg["precision"] == "fp64" else 1e-12,
+                   max_cycles=max(cfg["max_cycles"], 100), sampler=cfg["sampler"], seed=cfg["seed"], R=cfg["R"],
+                   genvec=z, log2_nmax=cfg["log2_nmax"], reuse=cfg["reuse"])
+    return cfg, ctx, orc
+
+
+def _rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+# --------------------------------------------------------------------------- #
+# a1: lattice points and normals                                              #
+# --------------------------------------------------------------------------- #
+
+
+@pytest.mark.parametrize("cid", [1, 2])
+def test_point_bits_bit_exact(cid):
+    cfg, ctx, orc = _pair(W.CONFIGS[cid])
+    for level, r, nb, cnt in [(0, 0, 0, 64), (3, 5 % cfg["R"], 17, 45), (cfg["n_levels"] - 1, cfg["R"] - 1, 0, 7)]:
+        bits = ctx.point_bits(level, r, nb, cnt).cpu().numpy().view(np.uint64)
+        for i in range(cnt):
+            n = nb + i
+            for j in range(cfg["s"]):
+                if cfg["sampler"] == "lattice":
+                    want = O.lattice_bits(int(orc._z[j]), n, O.shift_bits(cfg["seed"], level, r, j))
+                else:
+                    want = O.mc_bits(cfg["seed"], level, r, n, j)
+                assert int(bits[i, j]) == want, (level, r, n, j)
+
+
+def test_lattice_index_end_of_sequence():
+    cfg, ctx, orc = _pair(W.CONFIG2)
+    N = 2 ** cfg["log2_nmax"]
+    bits = ctx.point_bits(2, 1, N - 3, 3).cpu().numpy().view(np.uint64)
+    for i in range(3):
+        for j in range(cfg["s"]):
+            assert int(bits[i, j]) == O.lattice_bits(int(orc._z[j]), N - 3 + i, O.shift_bits(cfg["seed"], 2, 1, j))
+    with pytest.raises(M.MlqmcError) as e:
+        ctx.point_bits(2, 1, N - 2, 3)
+    assert e.value.code == 4
+
+
+@pytest.mark.parametrize("cid", [1, 2])
+def test_normals(cid):
+    cfg, ctx, orc = _pair(W.CONFIGS[cid])
+    y = ctx.normals(2, 0, 5, 40).cpu().numpy()
+    for i in range(40):
+        want = orc.normals(2, 0, 5 + i)
+        assert np.max(np.abs(y[i] - want) / np.maximum(np.abs(want), 1e-3)) < 1e-14
+
+
+# --------------------------------------------------------------------------- #
+# a2: KL field                                                                #
+# --------------------------------------------------------------------------- #
+
+
+def test_modes_match():
+    cfg, ctx, orc = _pair(W.CONFIG2)
+    a, b, th = ctx.modes()
+    ao, bo, tho, _ = orc.modes()
+    assert np.array_equal(a, ao) and np.array_equal(b, bo)
+    assert _rel(th, tho) < 1e-13
+
+
+@pytest.mark.parametrize("cid,levels", [(1, [0, 3]), (2, [0, 2, 4]), (3, [0, 3])])
+def test_fields_fp64(cid, levels):
+    cfg, ctx, orc = _pair(W.CONFIGS[cid], precision="fp64", rtol=0.0)
+    Y = W.random_normals(cfg["s"], 3, tag=20 + cid)
+    for t in levels:
+        k = ctx.fields(t, torch.from_numpy(Y)).cpu().numpy()
+        for i in range(3):
+            want = orc.field(t, Y[i])
+            assert np.max(np.abs(k[i] / want - 1.0)) < 1e-12
+
+
+# --------------------------------------------------------------------------- #
+# a3-a6: FMG solutions and F_t, FP64 form                                     #
+# --------------------------------------------------------------------------- #
+
+
+@pytest.mark.parametrize("cid,level,r,n", [(1, 3, 0, 5), (2, 0, 0, 0), (2, 3, 2, 7), (2, 5, 15, 3)])
+def test_single_sample_solutions_fp64(cid, level, r, n):
+    cfg, ctx, orc = _pair(W.CONFIGS[cid])
+    sols, F = ctx.sample_solution(level, r, n)
+    ref = orc.sample(level, r, n, want_u=True)
+    assert ref["status"] == O.OK
+    for t in range(level + 1):
+        assert _rel(sols[t].cpu().numpy(), ref["u"][t]) < 1e-12, t
+    assert _rel(F.cpu().numpy(), ref["F"]) < 1e-12
+
+
+def _check_sums(cfg, ctx, orc, work):
+    R, nl = cfg["R"], cfg["n_levels"]
+    nsamp = sum((ne - nb) * (re_ - rb) for (_, nb, ne, rb, re_) in work)
+    sums = torch.zeros(nl * R * 2, dtype=torch.float64, device="cuda")
+    F = torch.zeros(max(1, nsamp) * nl, dtype=torch.float64, device="cuda")
+    ctx.sample_levels(work, sums, F)
+    ctx.check_device()
+    torch.cuda.synchronize()
+    ref = orc.sample_levels(work, want_F=True)
+    Fg = F.cpu().numpy().reshape(-1, nl)[:nsamp]
+    assert _rel(Fg, ref["F"]) < 1e-12
+    # bound for the sums: dF_t = F_t - F_{t-1} cancels, so each term carries
+    # 1e-12 of |F_t| + |F_{t-1}|
+    absd = np.zeros((nl, R))
+    i = 0
+    for (lv, nb, ne, rb, re_) in work:
+        for r in range(rb, re_):
+            for _ in range(nb, ne):
+                for t in range(lv + 1):
+                    if cfg["reuse"] or t == lv:
+                        absd[t, r] += abs(ref["F"][i, t]) + (abs(ref["F"][i, t - 1]) if t else 0.0)
+                i += 1
+    s = sums.cpu().numpy().reshape(nl, R, 2)
+    assert np.all(np.abs(s[:, :, 0] - ref["sums"][:, :, 0]) <= 1e-12 * absd + 1e-300)
+    assert np.all(np.abs(s[:, :, 1] - ref["sums"][:, :, 1]) <= 1e-12 * np.maximum(ref["sums"][:, :, 1], 1e-300))
+    return s, Fg
+
+
+def test_config1_full_sums():
+    cfg, ctx, orc = _pair(W.CONFIG1)
+    work = W.fixed_count_work(cfg["counts"], cfg["R"])
+    _check_sums(cfg, ctx, orc, work)
+
+
+@pytest.mark.parametrize("reuse", [True, False])
+def test_config2_ragged_work(reuse):
+    cfg, ctx, orc = _pair(W.CONFIG2, R=4, reuse=reuse)
+    work = [(0, 0, 13, 0, 3), (1, 5, 9, 1, 4), (2, 0, 3, 0, 4), (3, 2, 4, 2, 3), (4, 0, 1, 0, 2), (5, 0, 1, 3, 4),
+            (2, 7, 7, 0, 4)]
+    _check_sums(cfg, ctx, orc, work)
+
+
+def test_chunked_calls_equal_single_call():
+    cfg = W.scaled(W.CONFIG2, R=2)
+    z = _genvec(cfg)
+    work = [(0, 0, 40, 0, 2), (2, 0, 9, 0, 2), (3, 0, 3, 0, 2)]
+    outs = []
+    for ms in [65536, 7]:
+        ctx = M.Context.from_config(cfg, genvec=z, max_samples=ms)
+        sums = torch.zeros(cfg["n_levels"] * 2 * 2, dtype=torch.float64, device="cuda")
+        F = torch.zeros(104 * cfg["n_levels"], dtype=torch.float64, device="cuda")
+        ctx.sample_levels(work, sums, F)
+        torch.cuda.synchronize()
+        outs.append((sums.cpu().numpy(), F.cpu().numpy()))
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert np.allclose(outs[0][0], outs[1][0], rtol=1e-13, atol=1e-18)
+
+
+def test_empty_and_invalid_work():
+    cfg, ctx, orc = _pair(W.CONFIG2, R=2)
+    sums = torch.zeros(cfg["n_levels"] * 2 * 2, dtype=torch.float64, device="cuda")
+    ctx.sample_levels([], sums)
+    ctx.sample_levels([(1, 4, 4, 0, 2)], sums)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(sums).item() == 0
+    for bad, code in [((6, 0, 1, 0, 1), 1), ((0, 3, 2, 0, 1), 1), ((0, 0, 1, 0, 3), 1), ((0, 0, 1025, 0, 1), 4)]:
+        with pytest.raises(M.MlqmcError) as e:
+            ctx.sample_levels([bad], sums)
+        assert e.value.code == code
+
+
+def test_full_config2_launch_sampled_against_oracle():
+    """The bench's workload in its launch configuration: all 32256 samples of
+    the fixed counts; sampled F rows against the oracle one by one, and the
+    sums against a host recomputation from the per-sample F (any size)."""
+    cfg, ctx, orc = _pair(W.CONFIG2)
+    work = W.fixed_count_work(cfg["counts"], cfg["R"])
+    nl, R = cfg["n_levels"], cfg["R"]
+    nsamp = sum((ne - nb) * (re_ - rb) for (_, nb, ne, rb, re_) in work)
+    sums = torch.zeros(nl * R * 2, dtype=torch.float64, device="cuda")
+    F = torch.zeros(nsamp * nl, dtype=torch.float64, device="cuda")
+    ctx.sample_levels(work, sums, F)
+    ctx.check_device()
+    torch.cuda.synchronize()
+    Fg = F.cpu().numpy().reshape(nsamp, nl)
+    index = []
+    for (lv, nb, ne, rb, re_) in work:
+        for r in range(rb, re_):
+            for n in range(nb, ne):
+                index.append((lv, r, n))
+    rg = W.rng(33)
+    picks = list(rg.choice(nsamp, 10, replace=False)) + [nsamp - 1, nsamp - 2, 0]
+    for q in picks:
+        lv, r, n = index[q]
+        ref = orc.sample(lv, r, n)
+        assert _rel(Fg[q, :lv + 1], ref["F"]) < 1e-12
+        assert np.all(Fg[q, lv + 1:] == 0.0)
+    # sums from the per-sample F (telescoped differences) in FP64 on the host
+    want = np.zeros((nl, R))
+    absd = np.zeros((nl, R))
+    for q, (lv, r, n) in enumerate(index):
+        d = np.diff(np.concatenate([[0.0], Fg[q, :lv + 1]]))
+        want[:lv + 1, r] += d
+        absd[:lv + 1, r] += np.abs(Fg[q, :lv + 1]) + np.abs(np.concatenate([[0.0], Fg[q, :lv]]))
+    s = sums.cpu().numpy().reshape(nl, R, 2)
+    assert np.all(np.abs(s[:, :, 0] - want) <= 1e-12 * absd)
+
+
+# --------------------------------------------------------------------------- #
+# a7-a8: estimator and Algorithm 1                                            #
+# --------------------------------------------------------------------------- #
+
+
+def test_algorithm1_matches_oracle():
+    cfg, ctx, orc = _pair(W.CONFIG2, n_levels=5, n0=4, s=6, R=4, seed=11, log2_nmax=10)
+    eps = 4e-4
+    g = ctx.estimate(eps)
+    o = orc.estimate(eps)
+    assert o["status"] == O.OK
+    assert g["L"] == o["L"] and g["rounds"] == o["rounds"]
+    assert g["N"] == o["N"]
+    assert abs(g["Q"] - o["Q"]) <= 1e-12 * abs(o["Q"])
+    assert abs(g["varQ"] - o["varQ"]) <= 1e-9 * o["varQ"]
+    assert g["varQ"] <= eps ** 2 / 2
+
+
+def test_device_status_not_converged():
+    cfg, ctx, orc = _pair(W.CONFIG2, R=1, rtol=1e-30, max_cycles=0)
+    sums = torch.zeros(cfg["n_levels"] * 2, dtype=torch.float64, device="cuda")
+    ctx.sample_levels([(2, 0, 2, 0, 1)], sums)
+    assert ctx.device_status() == 5
+    assert ctx.device_status() == 0  # reading clears it
+
+
+# --------------------------------------------------------------------------- #
+# Mixed precision (a2 in FP32, a4 FP32 V-cycles inside a5 FP64 refinement)     #
+# --------------------------------------------------------------------------- #
+
+
+def _field_bound(orc, cfg, y, u_in):
+    """Rounding bound on |z_mixed - z_64|: (k_terms) u_in * sum_m |sqrt(theta_m) y_m| M_a M_b with
+    M_k = sqrt((w_k^2 + c^2)/N_k) >= max |psi_k|."""
+    a, b, th, K1 = orc.modes()
+    w, _, nr = O.kl1d(cfg["corr_len"], K1)
+    c = 1.0 / cfg["corr_len"]
+    Mk = np.sqrt((w ** 2 + c ** 2) / nr)
+    return u_in * np.sum(np.sqrt(th) * np.abs(y) * Mk[a] * Mk[b])
+
+
+def test_mixed_fields_within_bound():
+    cfg, ctx, orc = _pair(W.CONFIG3, n_levels=4)
+    Y = W.random_normals(cfg["s"], 2, tag=40)
+    a, b, th, K1 = orc.modes()
+    terms = int(np.max(a)) + 1 + int(np.max(np.bincount(a))) + 4
+    for t in [0, 3]:
+        k = ctx.fields(t, torch.from_numpy(Y)).cpu().numpy()
+        for i in range(2):
+            want = orc.field(t, Y[i])
+            eta = _field_bound(orc, cfg, Y[i], terms * 2.0 ** -24)
+            assert np.max(np.abs(np.log(k[i] / want))) <= eta + 2.0 ** -22
+
+
+def test_mixed_qoi_within_bound():
+    cfg, ctx, orc = _pair(W.CONFIG3, n_levels=5, R=2)
+    for (lv, r, n) in [(4, 0, 3), (2, 1, 0)]:
+        sols, F = ctx.sample_solution(lv, r, n)
+        ref = orc.sample(lv, r, n, want_u=True)
+        assert ref["status"] == O.OK
+        y = orc.normals(lv, r, n)
+        a, b, th, K1 = orc.modes()
+        terms = int(np.max(a)) + 1 + int(np.max(np.bincount(a))) + 4
+        eta = _field_bound(orc, cfg, y, terms * 2.0 ** -24) + 2.0 ** -22
+        Fg = F.cpu().numpy()
+        for t in range(lv + 1):
+            u = ref["u"][t]
+            ratio = math.sqrt(np.mean(u ** 2)) / np.mean(u)
+            tol = math.expm1(eta) + 2 * cfg["rtol"] * ratio
+            assert abs(Fg[t] / ref["F"][t] - 1.0) <= tol, (t, Fg[t], ref["F"][t], tol)
