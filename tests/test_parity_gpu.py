@@ -149,18 +149,23 @@ def _check_sums(cfg, ctx, orc, work):
     assert _rel(Fg, ref["F"]) < 1e-12
     # bound for the sums: dF_t = F_t - F_{t-1} cancels, so each term carries
     # 1e-12 of |F_t| + |F_{t-1}|
+    # and a square dF_t^2 carries 2 |dF_t| times that
     absd = np.zeros((nl, R))
+    absd2 = np.zeros((nl, R))
     i = 0
     for (lv, nb, ne, rb, re_) in work:
         for r in range(rb, re_):
             for _ in range(nb, ne):
                 for t in range(lv + 1):
                     if cfg["reuse"] or t == lv:
-                        absd[t, r] += abs(ref["F"][i, t]) + (abs(ref["F"][i, t - 1]) if t else 0.0)
+                        mag = abs(ref["F"][i, t]) + (abs(ref["F"][i, t - 1]) if t else 0.0)
+                        d = ref["F"][i, t] - (ref["F"][i, t - 1] if t else 0.0)
+                        absd[t, r] += mag
+                        absd2[t, r] += 2 * abs(d) * mag + d * d
                 i += 1
     s = sums.cpu().numpy().reshape(nl, R, 2)
     assert np.all(np.abs(s[:, :, 0] - ref["sums"][:, :, 0]) <= 1e-12 * absd + 1e-300)
-    assert np.all(np.abs(s[:, :, 1] - ref["sums"][:, :, 1]) <= 1e-12 * np.maximum(ref["sums"][:, :, 1], 1e-300))
+    assert np.all(np.abs(s[:, :, 1] - ref["sums"][:, :, 1]) <= 1e-12 * absd2 + 1e-300)
     return s, Fg
 
 
