@@ -41,7 +41,8 @@ typedef enum {
     MLQMC_ERR_NOT_CONVERGED = 5,    /* a level missed refine_rtol within refine_max_iter */
     MLQMC_ERR_TIMEOUT = 6,          /* a bounded device wait gave up */
     MLQMC_ERR_DEVICE_STATUS = 7,    /* a kernel reported an internal check failure */
-    MLQMC_ERR_UNSUPPORTED = 8       /* option combination not built */
+    MLQMC_ERR_UNSUPPORTED = 8,      /* option combination not built */
+    MLQMC_ERR_SCRATCH_LIMIT = 9     /* larger than mlqmc_fmg_fields_noalloc's static scratch */
 } mlqmc_status;
 
 typedef enum {
@@ -231,6 +232,40 @@ mlqmc_status mlqmc_fields(mlqmc_ctx* c, int32_t t, const double* d_y, int32_t co
  */
 mlqmc_status mlqmc_sample_solution(mlqmc_ctx* c, int32_t level, int32_t r, int64_t n, double* d_u,
                                    double* d_F, void* stream);
+
+/*
+ * Allocation-free FMG solve from caller-supplied coefficient fields. The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc -- code that runs inside a CUDA stream capture or a graph
+ * being built, plug-ins whose host application owns the device memory pool,
+ * and real-time loops that must not touch the allocator. It needs no context
+ * (mlqmc_create allocates) and allocates nothing: its scratch is one static
+ * device array of MLQMC_NOALLOC_SLOTS slots of MLQMC_NOALLOC_SLOT_BYTES
+ * (16 x 1.25 MiB = 20 MiB) that every GPU loading this library holds until
+ * the process exits.
+ *
+ * It runs the same FMG as mlqmc_sample_levels (FP64 form, fixed mu0
+ * V(nu1,nu2)-cycles per level, exact level-0 solve) for `count` samples:
+ *  d_k  device, per sample the FP64 coefficient k = exp(z) of levels 0..L
+ *       concatenated, level t being (coarse_cells*2^t)^2 values row-major
+ *       [i2*n + i1]; samples follow each other.
+ *  d_F  device, count x n_levels FP64 outputs F_0..F_L (qoi as in mlqmc_qoi).
+ * Limits: coarse_cells even in 2..16, finest level at most
+ * MLQMC_NOALLOC_MAX_CELLS = 128 cells per side, n_levels <= 7; larger
+ * problems return MLQMC_ERR_SCRATCH_LIMIT without launching anything.
+ * The first call on a device looks up the static array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture. Every call shares the one array: calls whose
+ * kernels overlap on the GPU (other streams, other host threads) race and
+ * corrupt each other; order them on one stream. Nothing in the array needs
+ * to start at zero -- each solve writes every value it reads.
+ */
+#define MLQMC_NOALLOC_SLOTS 16
+#define MLQMC_NOALLOC_SLOT_BYTES (1280 * 1024)
+#define MLQMC_NOALLOC_MAX_CELLS 128
+mlqmc_status mlqmc_fmg_fields_noalloc(int32_t coarse_cells, int32_t n_levels, int32_t qoi, int32_t mu0,
+                                      int32_t nu1, int32_t nu2, int32_t count, const double* d_k, double* d_F,
+                                      void* stream);
 
 /* Kernel launches issued by this context since creation (all entry points). */
 int64_t mlqmc_launch_count(const mlqmc_ctx* c);

@@ -22,7 +22,7 @@ _lock = threading.Lock()
 _lib = None
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "POINTS_EXHAUSTED", 5: "NOT_CONVERGED",
-          6: "TIMEOUT", 7: "DEVICE_STATUS", 8: "UNSUPPORTED"}
+          6: "TIMEOUT", 7: "DEVICE_STATUS", 8: "UNSUPPORTED", 9: "SCRATCH_LIMIT"}
 PRECISION = {"fp64": 0, "mixed_tf32": 1, "mixed_bf16x3": 2}
 QOI = {"center": 0, "mean": 1}
 SAMPLER = {"mc": 0, "lattice": 1}
@@ -94,13 +94,15 @@ def lib():
             L.mlqmc_normals.argtypes = [vp, i32, i32, i64, i32, vp, vp]
             L.mlqmc_fields.argtypes = [vp, i32, vp, i32, vp, vp]
             L.mlqmc_sample_solution.argtypes = [vp, i32, i32, i64, vp, vp, vp]
+            L.mlqmc_fmg_fields_noalloc.argtypes = [i32, i32, i32, i32, i32, i32, i32, vp, vp, vp]
             L.mlqmc_profile.argtypes = [vp, i32]
             L.mlqmc_profile_read.argtypes = [vp, dp, C.POINTER(C.c_int64)]
             L.mlqmc_launch_count.argtypes = [vp]
             L.mlqmc_launch_count.restype = i64
             for name in ["mlqmc_create", "mlqmc_sample_levels", "mlqmc_estimate", "mlqmc_get_device_status",
                          "mlqmc_cbc_genvec", "mlqmc_modes", "mlqmc_point_bits", "mlqmc_normals", "mlqmc_fields",
-                         "mlqmc_sample_solution", "mlqmc_profile", "mlqmc_profile_read"]:
+                         "mlqmc_sample_solution", "mlqmc_profile", "mlqmc_profile_read",
+                         "mlqmc_fmg_fields_noalloc"]:
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib

@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -1169,6 +1170,138 @@ extern "C" mlqmc_status mlqmc_profile_read(mlqmc_ctx* c, double* out_ms, int64_t
         out_n[i] = c->prof_n[i];
     }
     return MLQMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free FMG from given fields (mlqmc_fmg_fields_noalloc).
+// Scratch lives in one static device array; host code reaches it only through
+// the address cudaGetSymbolAddress returns (the symbol itself is a host-side
+// stand-in, not a device address).
+// ---------------------------------------------------------------------------
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MLQMC_NOALLOC_SLOTS * size_t(MLQMC_NOALLOC_SLOT_BYTES)];
+
+// Faces and inverse diagonal of one level from k already in L.k.
+__device__ void noalloc_faces(const Lv<double>& L)
+{
+    const int n = L.n;
+    for (int idx = threadIdx.x; idx < n * (n + 1); idx += blockDim.x) {
+        const int i2 = idx / (n + 1);
+        const int f = idx - i2 * (n + 1);
+        const double* kr = L.k + i2 * n;
+        L.kx[idx] = (f == 0) ? 2.0 * kr[0] : (f == n) ? 2.0 * kr[n - 1] : hmean(kr[f - 1], kr[f]);
+        const int g = idx / n;
+        const int i1 = idx - g * n;
+        L.ky[idx] = (g == 0) ? 2.0 * L.k[i1]
+                  : (g == n) ? 2.0 * L.k[(n - 1) * n + i1]
+                             : hmean(L.k[(g - 1) * n + i1], L.k[g * n + i1]);
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < n * n; p += blockDim.x) {
+        const int i2 = p / n;
+        const int i1 = p - i2 * n;
+        L.idiag[p] = 1.0 / (L.kx[i2 * (n + 1) + i1] + L.kx[i2 * (n + 1) + i1 + 1] + L.ky[i2 * n + i1] +
+                            L.ky[(i2 + 1) * n + i1]);
+    }
+    __syncthreads();
+}
+
+// One CTA per scratch slot; CTA b solves samples b, b + gridDim.x, ...
+__global__ void __launch_bounds__(256) k_fmg_noalloc(FmgArgs A, const double* __restrict__ k_in, size_t k_stride,
+                                                     int count, double* __restrict__ F_out)
+{
+    extern __shared__ double smem[];
+    const int N0 = A.n0 * A.n0;
+    double* Lb = smem;
+    double* tmp = Lb + N0 * (A.n0 + 1);
+    double* red = tmp + N0;
+    double* Fv = red + 40;
+    unsigned char* slot = A.work + static_cast<size_t>(blockIdx.x) * A.slot_bytes;
+    const int Lf = A.n_levels - 1;
+    for (int q = blockIdx.x; q < count; q += gridDim.x) {
+        const double* ks = k_in + static_cast<size_t>(q) * k_stride;
+        for (int t = 0; t <= Lf; ++t) {
+            const Lv<double> L = level_view<double>(A, slot, t);
+            for (int p = threadIdx.x; p < L.n * L.n; p += blockDim.x) L.k[p] = ks[p];
+            ks += static_cast<size_t>(L.n) * L.n;
+            __syncthreads();
+            noalloc_faces(L);
+        }
+        const Lv<double> L0 = level_view<double>(A, slot, 0);
+        chol_factor(Lb, A.n0, L0.kx, L0.ky);
+        chol_solve<double, double>(Lb, A.n0, nullptr, L0.u, tmp);
+        const double F0 = qoi(L0.u, A.n0, A.qoi, red);
+        if (threadIdx.x == 0) Fv[0] = F0;
+        for (int t = 1; t <= Lf; ++t) {
+            const Lv<double> L = level_view<double>(A, slot, t);
+            const Lv<double> Lc = level_view<double>(A, slot, t - 1);
+            prolong<double, double, false>(Lc.u, Lc.n, L.u);
+            for (int m = 0; m < A.mu0; ++m) vcycle<double>(A, slot, t, nullptr, Lb, tmp);
+            const double Ft = qoi(L.u, L.n, A.qoi, red);
+            if (threadIdx.x == 0) Fv[t] = Ft;
+        }
+        __syncthreads();
+        if (threadIdx.x <= Lf) F_out[static_cast<size_t>(q) * A.n_levels + threadIdx.x] = Fv[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// Device address of the static scratch, looked up once per device.
+constexpr int kMaxDevices = 64;
+unsigned char* g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+}  // namespace
+
+extern "C" mlqmc_status mlqmc_fmg_fields_noalloc(int32_t coarse_cells, int32_t n_levels, int32_t qoi_kind,
+                                                 int32_t mu0, int32_t nu1, int32_t nu2, int32_t count,
+                                                 const double* d_k, double* d_F, void* stream)
+{
+    if (coarse_cells < 2 || (coarse_cells & 1) || n_levels < 1 || count < 0 || !d_k || !d_F || mu0 < 1 ||
+        nu1 < 0 || nu2 < 0 || mu0 > 64 || nu1 > 64 || nu2 > 64 ||
+        (qoi_kind != MLQMC_QOI_CENTER && qoi_kind != MLQMC_QOI_MEAN))
+        return MLQMC_ERR_INVALID_ARG;
+    if (coarse_cells > 16 || n_levels > 7 || (static_cast<int64_t>(coarse_cells) << (n_levels - 1)) > MLQMC_NOALLOC_MAX_CELLS)
+        return MLQMC_ERR_SCRATCH_LIMIT;
+    mlqmc_problem p{};
+    p.n_levels = n_levels;
+    p.coarse_cells = coarse_cells;
+    p.n_modes = 1;
+    p.precision = MLQMC_FP64;
+    const SlotLayout lay = make_layout(p, 0);
+    if (lay.bytes > static_cast<size_t>(MLQMC_NOALLOC_SLOT_BYTES)) return MLQMC_ERR_SCRATCH_LIMIT;
+    if (count == 0) return MLQMC_OK;
+    int dev = 0;
+    if (!ok(cudaGetDevice(&dev)) || dev < 0 || dev >= kMaxDevices) return MLQMC_ERR_CUDA;
+    unsigned char* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* ptr = nullptr;
+            if (!ok(cudaGetSymbolAddress(&ptr, g_noalloc_scratch)) || !ptr) return MLQMC_ERR_CUDA;
+            g_noalloc_ptr[dev] = static_cast<unsigned char*>(ptr);
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    FmgArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.n0 = coarse_cells;
+    A.n_levels = n_levels;
+    A.qoi = qoi_kind;
+    A.mu0 = mu0;
+    A.nu1 = nu1;
+    A.nu2 = nu2;
+    A.work = scratch;
+    A.slot_bytes = MLQMC_NOALLOC_SLOT_BYTES;
+    for (int t = 0; t < n_levels; ++t) A.lv[t] = lay.lv[t];
+    size_t k_stride = 0;
+    for (int t = 0; t < n_levels; ++t) k_stride += static_cast<size_t>(lay.lv[t].n) * lay.lv[t].n;
+    const size_t N0 = static_cast<size_t>(coarse_cells) * coarse_cells;
+    const size_t smem = sizeof(double) * (N0 * (coarse_cells + 1) + N0 + 40 + 16);
+    const int grid = std::min<int>(count, MLQMC_NOALLOC_SLOTS);
+    k_fmg_noalloc<<<grid, 256, smem, static_cast<cudaStream_t>(stream)>>>(A, d_k, k_stride, count, d_F);
+    return ok(cudaGetLastError()) ? MLQMC_OK : MLQMC_ERR_CUDA;
 }
 
 extern "C" int64_t mlqmc_launch_count(const mlqmc_ctx* c)

@@ -369,6 +369,7 @@ extern "C" const char* mlqmc_status_string(mlqmc_status s)
         case MLQMC_ERR_TIMEOUT: return "bounded device wait timed out";
         case MLQMC_ERR_DEVICE_STATUS: return "device-side check failed";
         case MLQMC_ERR_UNSUPPORTED: return "unsupported option";
+        case MLQMC_ERR_SCRATCH_LIMIT: return "problem exceeds the static scratch of the no-allocation entry point";
     }
     return "unknown status";
 }

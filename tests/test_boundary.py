@@ -65,7 +65,7 @@ int main(void) {
 
 
 def test_status_strings(lib):
-    for code in range(9):
+    for code in range(10):
         assert len(lib.mlqmc_status_string(code)) > 0
 
 
