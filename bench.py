@@ -68,31 +68,62 @@ def n_samples(work):
 
 
 # --------------------------------------------------------------------------- #
-# FP64 operation model of one sample (stated per step in the design notes)    #
+# Algorithmic work models per kernel kind (stated in the design notes)         #
 # --------------------------------------------------------------------------- #
-def fp64_ops_per_sample(level, cfg, Ka):
+HBM_GBS = 6755.5          # measured copy bandwidth of this machine's GB300 (MEASURED_PEAKS.json)
+FP64_TFLOPS = 1.25        # GB300 FP64 nominal (an FMA probe measured 1.20)
+FP32_TFLOPS = 70.0        # FP32 FMA probe on this machine's GB300
+
+
+def t_small(cfg):
+    ts = 0
+    while ts + 1 < cfg["n_levels"] and (cfg["n0"] << (ts + 1)) <= 64:
+        ts += 1
+    return ts
+
+
+def level_counts(cfg, work):
+    """B_t = samples whose FMG reaches level t."""
+    B = [0] * cfg["n_levels"]
+    for (lv, nb, ne, rb, re_) in work:
+        for t in range(lv + 1):
+            B[t] += (ne - nb) * (re_ - rb)
+    return B
+
+
+def smooth_model(cfg, work, es):
+    """Batched red-black sweeps of one step (fixed-cycle form): updated cells,
+    FLOPs (10 per update: 4 FMA + h^2 b + scaling) and algorithmic bytes (per
+    full sweep of an n x n grid 8 n^2 values move: u of the other colour,
+    the 2 n^2 faces, 1/D, b and the written u)."""
+    ts, B = t_small(cfg), level_counts(cfg, work)
+    cells = 0
+    for t in range(ts + 1, cfg["n_levels"]):
+        for tau in range(ts + 1, t + 1):
+            cells += cfg["mu0"] * (cfg["nu1"] + cfg["nu2"]) * B[t] * (cfg["n0"] << tau) ** 2
+    return dict(cells=cells, flops=10.0 * cells, bytes=8.0 * es * cells)
+
+
+def small_fp64_ops(cfg, work, Ka):
+    """FP64 operations of the per-sample kernel (levels <= 64x64) in one step:
+    KL 2 s n + 2 Ka n^2 + n^2 (exp) per level, faces and 1/D 12 n^2, GS sweep
+    11 n^2, residual+restriction 15 n^2, prolongation 9 n^2, banded Cholesky
+    2 N0 n0^2 and 4 N0 n0 per solve, QoI n^2."""
     n0, s, mu0, nu1, nu2 = cfg["n0"], cfg["s"], cfg["mu0"], cfg["nu1"], cfg["nu2"]
-    N0 = n0 * n0
-    ops = 0.0
-    for t in range(level + 1):
-        n = n0 << t
-        M = n * n
-        # KL: G = sum over modes (2 s n), z = sum over Ka rows (2 Ka M), exp (M);
-        # faces (2 per cell x 4) and inverse diagonal (4)
-        ops += 2 * s * n + 2 * Ka * M + M + 12 * M
-        ops += M  # QoI
-    ops += 2 * N0 * n0 * n0 + 4 * N0 * n0  # band Cholesky of level 0 and the first solve
-
-    def vcycle(t):
-        tot = 4 * N0 * n0
-        for tau in range(1, t + 1):
-            M = (n0 << tau) ** 2
-            tot += ((nu1 + nu2) * 11 + 15 + 9) * M
-        return tot
-
-    for t in range(1, level + 1):
-        ops += 9 * (n0 << t) ** 2 + mu0 * vcycle(t)
-    return ops
+    ts, N0 = t_small(cfg), n0 * n0
+    tot = 0.0
+    for (lv, nb, ne, rb, re_) in work:
+        cnt = (ne - nb) * (re_ - rb)
+        Ls = min(lv, ts)
+        ops = 2 * N0 * n0 * n0 + 4 * N0 * n0
+        for t in range(Ls + 1):
+            n = n0 << t
+            ops += 2 * s * n + 2 * Ka * n * n + n * n + 12 * n * n + n * n
+        for t in range(1, Ls + 1):
+            v = 4 * N0 * n0 + sum(((nu1 + nu2) * 11 + 15 + 9) * (n0 << u) ** 2 for u in range(1, t + 1))
+            ops += 9 * (n0 << t) ** 2 + mu0 * v
+        tot += cnt * ops
+    return tot
 
 
 def clocks_start(path):
@@ -284,15 +315,33 @@ def run_ours(args):
     h2d = len(work) * 32 + ns * (24 + 8)  # work list + the library's per-sample descriptors
     d2h = nl * R * 2 * 8
 
-    # roofline of the dominant kernel (FMG solver) from the live event timing
+    # roofline of the dominant kernel kind from the library's own event timing
     a, b, th = ctx.modes()
     Ka = int(a.max()) + 1
-    ops_step = sum((ne - nb) * (re_ - rb) * fp64_ops_per_sample(lv, cfg, Ka) for (lv, nb, ne, rb, re_) in work)
-    fmg_ms, fmg_n = prof["fmg"]
-    per_launch_s = fmg_ms * 1e-3 / max(1, fmg_n)
-    achieved = ops_step / per_launch_s / 1e12
-    peak_fp64 = 1.25  # TFLOP/s, GB300 FP64 (nominal; an FMA probe measured 1.20)
-    share = fmg_ms / max(1e-9, sum(v[0] for v in prof.values()))
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_n = prof[dom]
+    step_dev_ms = sum(v[0] for v in prof.values())
+    roof = {"kernel_kind": dom, "share_of_step": dom_ms / max(1e-9, step_dev_ms), "launches": dom_n,
+            "ms_per_step": dom_ms / args.steps, "traffic": None}
+    if dom == "smooth":
+        m = smooth_model(cfg, work, 8)
+        t_s = dom_ms * 1e-3 / args.steps
+        t_hbm, t_alu = m["bytes"] / (HBM_GBS * 1e9), m["flops"] / (FP64_TFLOPS * 1e12)
+        if t_hbm >= t_alu:
+            roof.update(bound="hbm", achieved=m["bytes"] / t_s / 1e9, peak=HBM_GBS, unit="GB/s",
+                        peak_source="measured copy bandwidth (MEASURED_PEAKS.json)")
+        else:
+            roof.update(bound="alu", achieved=m["flops"] / t_s / 1e12, peak=FP64_TFLOPS, unit="TFLOP/s",
+                        peak_source="nominal FP64 1.25 TFLOP/s (probe 1.20)")
+        roof.update(kernel="kb_gs<double> (batched red-black sweeps)", algorithmic_bytes_per_step=m["bytes"],
+                    flops_per_step=m["flops"])
+    else:
+        ops = small_fp64_ops(cfg, work, Ka)
+        t_s = dom_ms * 1e-3 / args.steps
+        roof.update(bound="alu", achieved=ops / t_s / 1e12, peak=FP64_TFLOPS, unit="TFLOP/s",
+                    peak_source="nominal FP64 1.25 TFLOP/s (probe 1.20)", kernel=f"{dom} kernels",
+                    flops_per_step=ops)
+    roof["frac"] = roof["achieved"] / roof["peak"]
 
     mixed = None
     if not args.no_mixed:
@@ -319,12 +368,8 @@ def run_ours(args):
                        "l2": "flushed between timed steps (512 MiB write)",
                        "parallelism": f"independent replicas x{world}"},
             "gpu_launches": launches,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
-                         "frac": achieved / peak_fp64, "traffic": None,
-                         "kernel": "k_fmg<double> (KL synthesis + FMG + QoI)",
-                         "ops_per_launch": ops_step, "ms_per_launch": per_launch_s * 1e3,
-                         "share_of_step": share, "peak_source": "nominal FP64 1.25 TFLOP/s (probe: 1.20)"},
-            "kernel_ms": {k: v[0] / max(1, v[1]) for k, v in prof.items()},
+            "roofline": roof,
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "estimate": {"Q": float(est[0]), "varQ": float(est[1])}},
             "clocks": clocks,

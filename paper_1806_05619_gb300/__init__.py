@@ -261,12 +261,14 @@ class Context:
         """Start (or stop) per-kernel CUDA-event timing of sample_levels; clears totals."""
         _check(lib().mlqmc_profile(self.h, 1 if enable else 0), "mlqmc_profile")
 
+    PROFILE_KINDS = ["points", "small", "synth", "smooth", "transfer", "small_vcycle", "reduce", "unused"]
+
     def profile_read(self):
-        """{kind: (ms, launches)} for kinds 'points', 'fmg', 'sums' since profile()."""
-        ms = np.zeros(3)
-        n = (C.c_int64 * 3)()
+        """{kind: (ms, launches)} per kernel kind since profile(); kinds as in mlqmc_profile_read."""
+        ms = np.zeros(8)
+        n = (C.c_int64 * 8)()
         _check(lib().mlqmc_profile_read(self.h, ms.ctypes.data_as(C.POINTER(C.c_double)), n), "mlqmc_profile_read")
-        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(["points", "fmg", "sums"])}
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.PROFILE_KINDS)}
 
     def launch_count(self) -> int:
         return int(lib().mlqmc_launch_count(self.h))

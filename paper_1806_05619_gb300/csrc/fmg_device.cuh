@@ -1,0 +1,476 @@
+// Device-side building blocks of the FMG solver: per-sample level views over
+// the level pools, the KL field, red-black Gauss-Seidel, residual/restriction,
+// prolongation, the banded exact solve on level 0 and the V-cycle (Sec. 4).
+// Every function here is called by all threads of a team (a CTA or one warp)
+// working on one sample.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mlqmc_internal.h"
+
+namespace mlqmc_dev {
+
+constexpr int kStatusNotConverged = 1;
+constexpr int kStatusCheck = 2;
+
+// Array of per-sample blocks: block i starts at base + i * stride (bytes).
+struct ArrDesc {
+    unsigned char* base;
+    size_t stride;
+};
+
+struct LevelDesc {
+    int n;
+    ArrDesc u, bc, kx, ky, idiag, k, G, u64;
+};
+
+template <typename T>
+struct Lv {
+    int n;
+    T* u;      // iterate (FMG solution on the current top level, correction below it)
+    T* bc;     // right-hand side of the coarse correction equation
+    T* kx;     // x faces: row i2, face f between cells f-1 and f, [i2*(n+1) + f]; f = 0, n hold 2k (boundary)
+    T* ky;     // y faces: face g between rows g-1 and g, [g*n + i1]; g = 0, n hold 2k (boundary)
+    T* idiag;  // 1 / (sum of the four face coefficients)
+    T* k;      // coefficient exp(z) at the cell centres
+    T* G;      // KL partial sums, Ka x n
+    double* u64;  // mixed forms: FP64 solution
+};
+
+struct FmgArgs {
+    const SampleDesc* samples;  // rank order: finest level descending
+    int n_samples;
+    const double* Y;  // normals, s per sample, indexed by canon
+    int s;
+    int n0;
+    int n_levels;
+    int t_small;  // levels <= t_small are solved by one CTA per sample
+    int qoi;
+    int mu0, nu1, nu2;
+    double rtol;
+    int max_iter;
+    int Ka;
+    const void* psi;
+    size_t psi_off[MLQMC_MAX_LEVELS];
+    const int* grp_start;
+    const int* grp_b;
+    const int* grp_m;
+    const double* grp_sqrt;
+    LevelDesc lv[MLQMC_MAX_LEVELS];
+    ArrDesc chol;      // banded factor of level 0, per sample
+    double* F;         // F_t per rank, n_levels each
+    double* usol;      // single-sample solutions (concatenated levels) or null
+    double* k_out;     // field-only mode: k of field_level per sample (by canon) or null
+    int field_level;
+    int* queue;
+    int* status;
+    const int* active;  // per rank; null: all samples active
+    double* norms;      // per rank residual norms
+};
+
+template <typename T>
+__device__ __forceinline__ T* at(const ArrDesc& a, int i)
+{
+    return reinterpret_cast<T*>(a.base + static_cast<size_t>(i) * a.stride);
+}
+
+template <typename T>
+__device__ __forceinline__ Lv<T> view(const FmgArgs& A, int t, int i)
+{
+    const LevelDesc& d = A.lv[t];
+    Lv<T> L;
+    L.n = d.n;
+    L.u = at<T>(d.u, i);
+    L.bc = at<T>(d.bc, i);
+    L.kx = at<T>(d.kx, i);
+    L.ky = at<T>(d.ky, i);
+    L.idiag = at<T>(d.idiag, i);
+    L.k = at<T>(d.k, i);
+    L.G = at<T>(d.G, i);
+    L.u64 = at<double>(d.u64, i);
+    return L;
+}
+
+// A team of threads that works on one sample: a whole CTA or one warp.
+struct BlockTeam {
+    __device__ __forceinline__ int rank() const { return threadIdx.x; }
+    __device__ __forceinline__ int size() const { return blockDim.x; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ bool leader() const { return threadIdx.x == 0; }
+    __device__ __forceinline__ bool first_warp() const { return threadIdx.x < 32; }
+};
+
+struct WarpTeam {
+    __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
+    __device__ __forceinline__ int size() const { return 32; }
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+    __device__ __forceinline__ bool leader() const { return (threadIdx.x & 31) == 0; }
+    __device__ __forceinline__ bool first_warp() const { return true; }
+};
+
+__device__ __forceinline__ double block_sum(double v, double* red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) red[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int w = 0; w < nw; ++w) t += red[w];  // fixed order: deterministic
+        red[32] = t;
+    }
+    __syncthreads();
+    const double t = red[32];
+    __syncthreads();
+    return t;
+}
+
+// Sum over the team, the same value in every thread, in a fixed order.
+__device__ __forceinline__ double team_sum(const BlockTeam&, double v, double* red) { return block_sum(v, red); }
+
+__device__ __forceinline__ double team_sum(const WarpTeam&, double v, double*)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float expT(float x) { return expf(x); }
+__device__ __forceinline__ double expT(double x) { return exp(x); }
+
+template <typename T>
+__device__ __forceinline__ T hmean(T a, T b)
+{
+    return T(2) * a * b / (a + b);
+}
+
+// x face f of row i2 (f = 0..n) from the cell coefficients of that row.
+template <typename T>
+__device__ __forceinline__ T face_x(const T* k, int n, int i2, int f)
+{
+    const T* kr = k + i2 * n;
+    if (f == 0) return T(2) * kr[0];
+    if (f == n) return T(2) * kr[n - 1];
+    return hmean(kr[f - 1], kr[f]);
+}
+
+// y face g of column i1 (g = 0..n).
+template <typename T>
+__device__ __forceinline__ T face_y(const T* k, int n, int g, int i1)
+{
+    if (g == 0) return T(2) * k[i1];
+    if (g == n) return T(2) * k[(n - 1) * n + i1];
+    return hmean(k[(g - 1) * n + i1], k[g * n + i1]);
+}
+
+template <typename T>
+__device__ __forceinline__ T inv_diag(const T* kx, const T* ky, int n, int i1, int i2)
+{
+    return T(1) / (kx[i2 * (n + 1) + i1] + kx[i2 * (n + 1) + i1 + 1] + ky[i2 * n + i1] + ky[(i2 + 1) * n + i1]);
+}
+
+// KL field on one level (eq. truncatedKL at the level's own cell centres):
+// z(x1,x2) = sum_a psi_a(x1) G_a(x2), G_a(x2) = sum_{m: a_m = a} sqrt(theta_m) y_m psi_{b_m}(x2);
+// then k = exp(z), harmonic-mean faces and the inverse diagonal.
+template <typename T, typename TM>
+__device__ void synth_level(const TM& tm, const FmgArgs& A, const Lv<T>& L, int t, const double* cy)
+{
+    const int n = L.n;
+    const T* psi = static_cast<const T*>(A.psi) + A.psi_off[t];
+    const int Ka = A.Ka;
+    for (int idx = tm.rank(); idx < Ka * n; idx += tm.size()) {
+        const int a = idx / n;
+        const int i2 = idx - a * n;
+        T acc = T(0);
+        const int g1 = A.grp_start[a + 1];
+        for (int g = A.grp_start[a]; g < g1; ++g) acc += static_cast<T>(cy[g]) * psi[A.grp_b[g] * n + i2];
+        L.G[idx] = acc;
+    }
+    tm.sync();
+    for (int p = tm.rank(); p < n * n; p += tm.size()) {
+        const int i2 = p / n;
+        const int i1 = p - i2 * n;
+        T z = T(0);
+        for (int a = 0; a < Ka; ++a) z += psi[a * n + i1] * L.G[a * n + i2];
+        L.k[p] = expT(z);
+    }
+    tm.sync();
+    for (int idx = tm.rank(); idx < n * (n + 1); idx += tm.size()) {
+        const int i2 = idx / (n + 1);
+        L.kx[idx] = face_x(L.k, n, i2, idx - i2 * (n + 1));
+        const int g = idx / n;
+        L.ky[idx] = face_y(L.k, n, g, idx - g * n);
+    }
+    tm.sync();
+    for (int p = tm.rank(); p < n * n; p += tm.size()) {
+        const int i2 = p / n;
+        L.idiag[p] = inv_diag(L.kx, L.ky, n, p - i2 * n, i2);
+    }
+    tm.sync();
+}
+
+// Gauss-Seidel update of one cell: u_P = (h^2 b_P + sum_Q k_PQ u_Q) / D_P.
+template <typename T>
+__device__ __forceinline__ void gs_cell(const Lv<T>& L, const T* b, T h2, int i1, int i2)
+{
+    const int n = L.n;
+    const int p = i2 * n + i1;
+    const T* kx = L.kx + i2 * (n + 1);
+    T acc = h2 * (b ? b[p] : T(1));
+    if (i1 > 0) acc += kx[i1] * L.u[p - 1];
+    if (i1 < n - 1) acc += kx[i1 + 1] * L.u[p + 1];
+    if (i2 > 0) acc += L.ky[i2 * n + i1] * L.u[p - n];
+    if (i2 < n - 1) acc += L.ky[(i2 + 1) * n + i1] * L.u[p + n];
+    L.u[p] = acc * L.idiag[p];
+}
+
+// One red-black half sweep (colour 0: i1+i2 even). b == null: b = 1.
+template <typename T, typename TM>
+__device__ __forceinline__ void gs_colour(const TM& tm, const Lv<T>& L, const T* b, int colour)
+{
+    const int n = L.n;
+    const int half = n >> 1;
+    const T h2 = T(1) / (T(n) * T(n));
+    for (int idx = tm.rank(); idx < n * half; idx += tm.size()) {
+        const int i2 = idx / half;
+        gs_cell(L, b, h2, 2 * (idx - i2 * half) + ((i2 + colour) & 1), i2);
+    }
+    tm.sync();
+}
+
+// (A u)_P scaled by h^2 in flux form: sum over faces k_f (u_P - u_Q), with
+// u_Q = 0 across the boundary (where k_f holds 2 k_P). Differences of
+// neighbouring values keep the FP64 residual floor near eps * |flux|.
+template <typename T, typename U>
+__device__ __forceinline__ U apply_h2(const T* kx, const T* ky, const U* u, int n, int i1, int i2)
+{
+    const int p = i2 * n + i1;
+    const U up = u[p];
+    U acc = U(kx[i2 * (n + 1) + i1]) * (up - (i1 > 0 ? u[p - 1] : U(0)));
+    acc += U(kx[i2 * (n + 1) + i1 + 1]) * (up - (i1 < n - 1 ? u[p + 1] : U(0)));
+    acc += U(ky[i2 * n + i1]) * (up - (i2 > 0 ? u[p - n] : U(0)));
+    acc += U(ky[(i2 + 1) * n + i1]) * (up - (i2 < n - 1 ? u[p + n] : U(0)));
+    return acc;
+}
+
+// Coarse value (I1, I2) of the restricted residual: mean over the 4 children of b - A u.
+template <typename T>
+__device__ __forceinline__ T resid_restrict_cell(const Lv<T>& F, const T* b, int I1, int I2)
+{
+    const int n = F.n;
+    const T ih2 = T(n) * T(n);
+    T s = T(0);
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        const int i1 = 2 * I1 + (d & 1), i2 = 2 * I2 + (d >> 1);
+        s += (b ? b[i2 * n + i1] : T(1)) - ih2 * apply_h2<T, T>(F.kx, F.ky, F.u, n, i1, i2);
+    }
+    return T(0.25) * s;
+}
+
+template <typename T, typename TM>
+__device__ void resid_restrict(const TM& tm, const Lv<T>& F, const T* b, T* bc)
+{
+    const int nc = F.n >> 1;
+    for (int idx = tm.rank(); idx < nc * nc; idx += tm.size()) {
+        const int I2 = idx / nc;
+        bc[idx] = resid_restrict_cell(F, b, idx - I2 * nc, I2);
+    }
+    tm.sync();
+}
+
+template <typename T>
+__device__ __forceinline__ T ghost(const T* e, int nc, int I1, int I2)
+{
+    T sg = T(1);
+    if (I1 < 0) { I1 = 0; sg = -sg; }
+    if (I1 >= nc) { I1 = nc - 1; sg = -sg; }
+    if (I2 < 0) { I2 = 0; sg = -sg; }
+    if (I2 >= nc) { I2 = nc - 1; sg = -sg; }
+    return sg * e[I2 * nc + I1];
+}
+
+// Bilinear cell-centred prolongation (9,3,3,1)/16 of fine cell (i1, i2), odd
+// reflection at the Dirichlet boundary.
+template <typename S, typename D>
+__device__ __forceinline__ D prolong_cell(const S* e, int nc, int i1, int i2)
+{
+    const int I1 = i1 >> 1, I2 = i2 >> 1;
+    const int s1 = (i1 & 1) ? 1 : -1, s2 = (i2 & 1) ? 1 : -1;
+    const D v = D(9) * D(ghost(e, nc, I1, I2)) + D(3) * D(ghost(e, nc, I1 + s1, I2)) +
+                D(3) * D(ghost(e, nc, I1, I2 + s2)) + D(ghost(e, nc, I1 + s1, I2 + s2));
+    return v * D(0.0625);
+}
+
+template <typename S, typename D, bool ADD, typename TM>
+__device__ void prolong(const TM& tm, const S* e, int nc, D* fine)
+{
+    const int nf = 2 * nc;
+    for (int p = tm.rank(); p < nf * nf; p += tm.size()) {
+        const int i2 = p / nf;
+        const D v = prolong_cell<S, D>(e, nc, p - i2 * nf, i2);
+        if (ADD) fine[p] += v;
+        else fine[p] = v;
+    }
+    tm.sync();
+}
+
+// Banded Cholesky of h0^2 A_0 (bandwidth n0) by the team's first warp:
+// Lb[i*(n0+1) + d] = L(i, i-d).
+template <typename F, typename TM>
+__device__ void chol_factor(const TM& tm, double* Lb, int n0, const F* kx, const F* ky)
+{
+    if (tm.first_warp()) {
+        const int N = n0 * n0, W = n0 + 1, lane = threadIdx.x & 31;
+        for (int j = 0; j < N; ++j) {
+            const int j1 = j % n0, j2 = j / n0;
+            double d = static_cast<double>(kx[j2 * (n0 + 1) + j1]) + static_cast<double>(kx[j2 * (n0 + 1) + j1 + 1]) +
+                       static_cast<double>(ky[j2 * n0 + j1]) + static_cast<double>(ky[(j2 + 1) * n0 + j1]);
+            for (int q = 1; q <= n0 && q <= j; ++q) {
+                const double l = Lb[j * W + q];
+                d -= l * l;
+            }
+            const double Ljj = sqrt(d);
+            if (lane == 0) Lb[j * W] = Ljj;
+            if (lane >= 1 && lane <= n0 && j + lane < N) {
+                const int i = j + lane;
+                const int i1 = i % n0, i2 = i / n0;
+                double a = 0.0;
+                if (lane == 1 && i1 > 0) a = -static_cast<double>(kx[i2 * (n0 + 1) + i1]);
+                if (lane == n0) a = -static_cast<double>(ky[i2 * n0 + i1]);
+                for (int tt = (i - n0 > 0 ? i - n0 : 0); tt < j; ++tt) a -= Lb[i * W + (i - tt)] * Lb[j * W + (j - tt)];
+                Lb[i * W + lane] = a / Ljj;
+            }
+            __syncwarp();
+        }
+    }
+    tm.sync();
+}
+
+// Solve (h0^2 A_0) x = h0^2 b with the band factor; b == null: b = 1. Team leader.
+template <typename B, typename X, typename TM>
+__device__ void chol_solve(const TM& tm, const double* Lb, int n0, const B* b, X* x, double* tmp)
+{
+    if (tm.leader()) {
+        const int N = n0 * n0, W = n0 + 1;
+        const double h2 = 1.0 / (static_cast<double>(n0) * n0);
+        for (int i = 0; i < N; ++i) {
+            double v = h2 * (b ? static_cast<double>(b[i]) : 1.0);
+            for (int q = 1; q <= n0 && q <= i; ++q) v -= Lb[i * W + q] * tmp[i - q];
+            tmp[i] = v / Lb[i * W];
+        }
+        for (int i = N - 1; i >= 0; --i) {
+            double v = tmp[i];
+            for (int q = 1; q <= n0 && i + q < N; ++q) v -= Lb[(i + q) * W + q] * tmp[i + q];
+            tmp[i] = v / Lb[i * W];
+        }
+        for (int i = 0; i < N; ++i) x[i] = static_cast<X>(tmp[i]);
+    }
+    tm.sync();
+}
+
+template <typename T, typename TM>
+__device__ void zero(const TM& tm, T* a, int cnt)
+{
+    for (int p = tm.rank(); p < cnt; p += tm.size()) a[p] = T(0);
+    tm.sync();
+}
+
+// V-cycle (Sec. 4 correction scheme, recursively) of sample i on levels
+// t_top..0. top_b == null: right-hand side 1 on the top level; the top
+// iterate is used as given, lower levels start from zero.
+template <typename T, typename TM>
+__device__ void vcycle(const TM& tm, const FmgArgs& A, int i, int t_top, const T* top_b, const double* Lb,
+                       double* tmp)
+{
+    for (int t = t_top; t >= 1; --t) {
+        const Lv<T> F = view<T>(A, t, i);
+        const T* b = (t == t_top) ? top_b : F.bc;
+        if (t < t_top) zero(tm, F.u, F.n * F.n);
+        for (int s = 0; s < A.nu1; ++s) {
+            gs_colour(tm, F, b, 0);
+            gs_colour(tm, F, b, 1);
+        }
+        resid_restrict(tm, F, b, view<T>(A, t - 1, i).bc);
+    }
+    {
+        const Lv<T> C0 = view<T>(A, 0, i);
+        chol_solve(tm, Lb, A.n0, t_top == 0 ? top_b : C0.bc, C0.u, tmp);
+    }
+    for (int t = 1; t <= t_top; ++t) {
+        const Lv<T> F = view<T>(A, t, i);
+        const Lv<T> Cl = view<T>(A, t - 1, i);
+        prolong<T, T, true>(tm, Cl.u, Cl.n, F.u);
+        const T* b = (t == t_top) ? top_b : F.bc;
+        for (int s = 0; s < A.nu2; ++s) {
+            gs_colour(tm, F, b, 1);
+            gs_colour(tm, F, b, 0);
+        }
+    }
+}
+
+// ||1 - A u||_2 on one level (b = 1), FP64 accumulation.
+template <typename T, typename TM>
+__device__ double resid_norm_ones(const TM& tm, const Lv<T>& L, double* red)
+{
+    const int n = L.n;
+    const double ih2 = static_cast<double>(n) * n;
+    double acc = 0.0;
+    for (int p = tm.rank(); p < n * n; p += tm.size()) {
+        const int i2 = p / n, i1 = p - i2 * n;
+        const double r = 1.0 - ih2 * static_cast<double>(apply_h2<T, T>(L.kx, L.ky, L.u, n, i1, i2));
+        acc += r * r;
+    }
+    return sqrt(team_sum(tm, acc, red));
+}
+
+// Mixed forms: r = 1 - A u64 in FP64 with the FP32 faces widened; r stored to
+// the FP32 right-hand side. Returns ||r||_2 when red != null.
+__device__ __forceinline__ double resid64_cell(const Lv<float>& L, int i1, int i2)
+{
+    const double ih2 = static_cast<double>(L.n) * L.n;
+    return 1.0 - ih2 * apply_h2<float, double>(L.kx, L.ky, L.u64, L.n, i1, i2);
+}
+
+template <typename TM>
+__device__ double resid64_to_rhs(const TM& tm, const Lv<float>& L, double* red)
+{
+    const int n = L.n;
+    double acc = 0.0;
+    for (int p = tm.rank(); p < n * n; p += tm.size()) {
+        const int i2 = p / n;
+        const double r = resid64_cell(L, p - i2 * n, i2);
+        L.bc[p] = static_cast<float>(r);
+        acc += r * r;
+    }
+    return sqrt(team_sum(tm, acc, red));
+}
+
+template <typename T, typename TM>
+__device__ double qoi(const TM& tm, const T* u, int n, int kind, double* red)
+{
+    if (kind == MLQMC_QOI_MEAN) {
+        double acc = 0.0;
+        for (int p = tm.rank(); p < n * n; p += tm.size()) acc += static_cast<double>(u[p]);
+        return team_sum(tm, acc, red) / (static_cast<double>(n) * n);
+    }
+    const int m = n / 2;
+    const double v = 0.25 * (static_cast<double>(u[(m - 1) * n + (m - 1)]) + static_cast<double>(u[(m - 1) * n + m]) +
+                             static_cast<double>(u[m * n + (m - 1)]) + static_cast<double>(u[m * n + m]));
+    tm.sync();
+    return v;
+}
+
+template <typename T, typename TM>
+__device__ void copy_out(const TM& tm, const T* src, double* dst, int cnt)
+{
+    for (int p = tm.rank(); p < cnt; p += tm.size()) dst[p] = static_cast<double>(src[p]);
+    tm.sync();
+}
+
+}  // namespace mlqmc_dev

@@ -1,15 +1,18 @@
 // CUDA path of the MG-MLQMC library (sm_103a).
 //
-// Kernels:
-//  k_points     shifted rank-1 lattice sequence / Philox MC bits -> normals (Sec. 3.2)
-//  k_fmg<T,MX>  persistent per-sample solver: one CTA takes one sample from a
-//               queue (largest level first), synthesises the KL field on every
-//               level of its hierarchy (eq. truncatedKL), runs Full Multigrid
-//               with red-black Gauss-Seidel V-cycles (Sec. 4, Fig. FMG) and
-//               writes F_t and dF_t for every level t of that FMG (the recycled
-//               solutions of eq. Upsilon-reuse). MX: FP32 V-cycles inside FP64
-//               residual refinement.
-//  k_sums       deterministic per (level, shift) reuse sums (eq. Upsilon-reuse).
+// One call of mlqmc_sample_levels runs SampleAndSolve (Algorithm 1) for a list
+// of samples. Samples are ranked by finest level, descending; every level t
+// keeps a pool with one block of arrays per sample whose FMG reaches t
+// (B_t samples, B_t non-increasing in t), so sample i uses block i at every
+// level. Two kinds of kernels share these pools:
+//  - k_small: one CTA per sample for the small levels (n_t <= 64): KL field,
+//    faces, banded Cholesky of level 0 and the FMG stages up to 64x64 (Sec. 4,
+//    Fig. FMG). Working sets are L2 resident.
+//  - kb_*: level-synchronous kernels over all B_t samples of a large level
+//    (KL field, faces, red-black sweeps, residual/restriction, prolongation,
+//    FP64 refinement steps, QoI). A V-cycle on a large level runs kb_* down to
+//    the first small level, k_small_vcycle for the levels below, and kb_* up.
+// Then k_sums forms the reuse sums (eq. Upsilon-reuse) in a fixed order.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,12 +23,12 @@
 #include <new>
 #include <vector>
 
+#include "fmg_device.cuh"
 #include "mlqmc_internal.h"
 
-namespace {
+using namespace mlqmc_dev;
 
-constexpr int kStatusNotConverged = 1;
-constexpr int kStatusCheck = 2;
+namespace {
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
@@ -86,522 +89,390 @@ __global__ void k_points(const SampleDesc* __restrict__ smp, int count, int s, i
 }
 
 // ---------------------------------------------------------------------------
-// Block-wide helpers
+// Per-sample solver of the small levels: one warp per sample, 8 per CTA.
+// Shared memory per warp: cy[s] | Lb[n0^2 (n0+1)] | tmp[n0^2] | F[16].
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double block_sum(double v, double* red)
+__host__ __device__ __forceinline__ int small_warp_doubles(int s, int n0)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int warp = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) red[warp] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        const int nw = (blockDim.x + 31) >> 5;
-        for (int w = 0; w < nw; ++w) t += red[w];  // fixed order: deterministic
-        red[32] = t;
-    }
-    __syncthreads();
-    const double t = red[32];
-    __syncthreads();
-    return t;
+    const int N0 = n0 * n0;
+    return ((s + 1) & ~1) + N0 * (n0 + 1) + N0 + 16;
 }
 
-template <typename T>
-struct Lv {
-    int n;
-    T* u;      // iterate (FMG solution on the current top level, correction below it)
-    T* bc;     // right-hand side of the coarse correction equation
-    T* kx;     // faces x: row i2, face f between cells f-1 and f, [i2*(n+1) + f]; f=0,n: 2k (boundary)
-    T* ky;     // faces y: face g between rows g-1 and g, [g*n + i1]; g=0,n: 2k (boundary)
-    T* idiag;  // 1 / (sum of the four face coefficients)
-    T* k;      // coefficient exp(z) at cell centres
-    T* G;      // KL partial sums, Ka x n
-    double* u64;   // mixed forms: FP64 solution
-    double* kx64;  // mixed forms: faces from the FP32 field, widened, in FP64
-    double* ky64;
-};
-
-struct FmgArgs {
-    const SampleDesc* samples;
-    int n_samples;
-    const double* Y;
-    int s;
-    int n0;
-    int n_levels;
-    int qoi;
-    int mu0, nu1, nu2;
-    double rtol;
-    int max_iter;
-    int Ka;
-    const void* psi;
-    size_t psi_off[MLQMC_MAX_LEVELS];
-    const int* grp_start;
-    const int* grp_b;
-    const int* grp_m;
-    const double* grp_sqrt;
-    unsigned char* work;
-    size_t slot_bytes;
-    LevelOffsets lv[MLQMC_MAX_LEVELS];
-    double* dF;
-    double* F_out;
-    double* usol;        // single-sample solution output (concatenated levels) or null
-    double* k_out;       // field-only mode: k of level `field_level` per sample, or null
-    int field_level;
-    int* queue;
-    int* status;
-};
-
-template <typename T>
-__device__ __forceinline__ Lv<T> level_view(const FmgArgs& A, unsigned char* slot, int t)
-{
-    const LevelOffsets& o = A.lv[t];
-    Lv<T> L;
-    L.n = o.n;
-    L.u = reinterpret_cast<T*>(slot + o.u);
-    L.bc = reinterpret_cast<T*>(slot + o.bc);
-    L.kx = reinterpret_cast<T*>(slot + o.kx);
-    L.ky = reinterpret_cast<T*>(slot + o.ky);
-    L.idiag = reinterpret_cast<T*>(slot + o.idiag);
-    L.k = reinterpret_cast<T*>(slot + o.k);
-    L.G = reinterpret_cast<T*>(slot + o.G);
-    L.u64 = reinterpret_cast<double*>(slot + o.u64);
-    L.kx64 = reinterpret_cast<double*>(slot + o.kx64);
-    L.ky64 = reinterpret_cast<double*>(slot + o.ky64);
-    return L;
-}
-
-__device__ __forceinline__ float expT(float x) { return expf(x); }
-__device__ __forceinline__ double expT(double x) { return exp(x); }
-
-template <typename T>
-__device__ __forceinline__ T hmean(T a, T b)
-{
-    return T(2) * a * b / (a + b);
-}
-
-// KL field on one level (eq. truncatedKL at the level's own cell centres):
-// z(x1,x2) = sum_a psi_a(x1) G_a(x2), G_a(x2) = sum_{m: a_m = a} sqrt(theta_m) y_m psi_{b_m}(x2);
-// then k = exp(z), harmonic-mean faces and the inverse diagonal.
 template <typename T, bool MX>
-__device__ void synth_level(const FmgArgs& A, const Lv<T>& L, int t, const double* cy)
-{
-    const int n = L.n;
-    const T* psi = static_cast<const T*>(A.psi) + A.psi_off[t];
-    const int Ka = A.Ka;
-    for (int idx = threadIdx.x; idx < Ka * n; idx += blockDim.x) {
-        const int a = idx / n;
-        const int i2 = idx - a * n;
-        T acc = T(0);
-        const int g1 = A.grp_start[a + 1];
-        for (int g = A.grp_start[a]; g < g1; ++g) acc += static_cast<T>(cy[g]) * psi[A.grp_b[g] * n + i2];
-        L.G[idx] = acc;
-    }
-    __syncthreads();
-    for (int p = threadIdx.x; p < n * n; p += blockDim.x) {
-        const int i2 = p / n;
-        const int i1 = p - i2 * n;
-        T z = T(0);
-        for (int a = 0; a < Ka; ++a) z += psi[a * n + i1] * L.G[a * n + i2];
-        L.k[p] = expT(z);
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < n * (n + 1); idx += blockDim.x) {
-        const int i2 = idx / (n + 1);
-        const int f = idx - i2 * (n + 1);
-        const T* kr = L.k + i2 * n;
-        T v;
-        if (f == 0) v = T(2) * kr[0];
-        else if (f == n) v = T(2) * kr[n - 1];
-        else v = hmean(kr[f - 1], kr[f]);
-        L.kx[idx] = v;
-        // y faces: face g = idx / n between rows g-1 and g
-        const int g = idx / n;
-        const int i1 = idx - g * n;
-        T w;
-        if (g == 0) w = T(2) * L.k[i1];
-        else if (g == n) w = T(2) * L.k[(n - 1) * n + i1];
-        else w = hmean(L.k[(g - 1) * n + i1], L.k[g * n + i1]);
-        L.ky[idx] = w;
-        if constexpr (MX) {
-            double v64, w64;
-            if (f == 0) v64 = 2.0 * static_cast<double>(kr[0]);
-            else if (f == n) v64 = 2.0 * static_cast<double>(kr[n - 1]);
-            else v64 = hmean(static_cast<double>(kr[f - 1]), static_cast<double>(kr[f]));
-            if (g == 0) w64 = 2.0 * static_cast<double>(L.k[i1]);
-            else if (g == n) w64 = 2.0 * static_cast<double>(L.k[(n - 1) * n + i1]);
-            else w64 = hmean(static_cast<double>(L.k[(g - 1) * n + i1]), static_cast<double>(L.k[g * n + i1]));
-            L.kx64[idx] = v64;
-            L.ky64[idx] = w64;
-        }
-    }
-    __syncthreads();
-    for (int p = threadIdx.x; p < n * n; p += blockDim.x) {
-        const int i2 = p / n;
-        const int i1 = p - i2 * n;
-        const T d = L.kx[i2 * (n + 1) + i1] + L.kx[i2 * (n + 1) + i1 + 1] + L.ky[i2 * n + i1] + L.ky[(i2 + 1) * n + i1];
-        L.idiag[p] = T(1) / d;
-    }
-    __syncthreads();
-}
-
-// One red-black Gauss-Seidel half sweep (colour 0: i1+i2 even). b == null: b = 1.
-template <typename T>
-__device__ __forceinline__ void gs_colour(const Lv<T>& L, const T* b, int colour)
-{
-    const int n = L.n;
-    const int half = n >> 1;
-    const T h2 = T(1) / (T(n) * T(n));
-    for (int idx = threadIdx.x; idx < n * half; idx += blockDim.x) {
-        const int i2 = idx / half;
-        const int i1 = 2 * (idx - i2 * half) + ((i2 + colour) & 1);
-        const int p = i2 * n + i1;
-        const T* kx = L.kx + i2 * (n + 1);
-        T acc = h2 * (b ? b[p] : T(1));
-        if (i1 > 0) acc += kx[i1] * L.u[p - 1];
-        if (i1 < n - 1) acc += kx[i1 + 1] * L.u[p + 1];
-        if (i2 > 0) acc += L.ky[i2 * n + i1] * L.u[p - n];
-        if (i2 < n - 1) acc += L.ky[(i2 + 1) * n + i1] * L.u[p + n];
-        L.u[p] = acc * L.idiag[p];
-    }
-    __syncthreads();
-}
-
-// (A u)_P scaled by h^2 in flux form: sum over faces k_f (u_P - u_Q), with
-// u_Q = 0 across the boundary (where k_f holds 2 k_P). Differences of
-// neighbouring values keep the FP64 residual floor near eps * |flux|.
-template <typename T, typename U>
-__device__ __forceinline__ U apply_h2(const T* kx, const T* ky, const U* u, int n, int i1, int i2)
-{
-    const int p = i2 * n + i1;
-    const U up = u[p];
-    U acc = U(kx[i2 * (n + 1) + i1]) * (up - (i1 > 0 ? u[p - 1] : U(0)));
-    acc += U(kx[i2 * (n + 1) + i1 + 1]) * (up - (i1 < n - 1 ? u[p + 1] : U(0)));
-    acc += U(ky[i2 * n + i1]) * (up - (i2 > 0 ? u[p - n] : U(0)));
-    acc += U(ky[(i2 + 1) * n + i1]) * (up - (i2 < n - 1 ? u[p + n] : U(0)));
-    return acc;
-}
-
-// r = b - A u on the fine level, restricted by the mean of the four children.
-template <typename T>
-__device__ void resid_restrict(const Lv<T>& F, const T* b, T* bc)
-{
-    const int n = F.n;
-    const int nc = n >> 1;
-    const T ih2 = T(n) * T(n);
-    for (int idx = threadIdx.x; idx < nc * nc; idx += blockDim.x) {
-        const int I2 = idx / nc;
-        const int I1 = idx - I2 * nc;
-        T s = T(0);
-#pragma unroll
-        for (int d = 0; d < 4; ++d) {
-            const int i1 = 2 * I1 + (d & 1), i2 = 2 * I2 + (d >> 1);
-            const int p = i2 * n + i1;
-            s += (b ? b[p] : T(1)) - ih2 * apply_h2<T, T>(F.kx, F.ky, F.u, n, i1, i2);
-        }
-        bc[idx] = T(0.25) * s;
-    }
-    __syncthreads();
-}
-
-template <typename T>
-__device__ __forceinline__ T ghost(const T* e, int nc, int I1, int I2)
-{
-    T sg = T(1);
-    if (I1 < 0) { I1 = 0; sg = -sg; }
-    if (I1 >= nc) { I1 = nc - 1; sg = -sg; }
-    if (I2 < 0) { I2 = 0; sg = -sg; }
-    if (I2 >= nc) { I2 = nc - 1; sg = -sg; }
-    return sg * e[I2 * nc + I1];
-}
-
-// Bilinear cell-centred prolongation (9,3,3,1)/16 with odd reflection at the
-// Dirichlet boundary; ADD: fine += P e, else fine = P e.
-template <typename S, typename D, bool ADD>
-__device__ void prolong(const S* e, int nc, D* fine)
-{
-    const int nf = 2 * nc;
-    for (int p = threadIdx.x; p < nf * nf; p += blockDim.x) {
-        const int i2 = p / nf;
-        const int i1 = p - i2 * nf;
-        const int I1 = i1 >> 1, I2 = i2 >> 1;
-        const int s1 = (i1 & 1) ? 1 : -1, s2 = (i2 & 1) ? 1 : -1;
-        const D v = D(9) * D(ghost(e, nc, I1, I2)) + D(3) * D(ghost(e, nc, I1 + s1, I2)) +
-                    D(3) * D(ghost(e, nc, I1, I2 + s2)) + D(ghost(e, nc, I1 + s1, I2 + s2));
-        if (ADD) fine[p] += v * D(0.0625);
-        else fine[p] = v * D(0.0625);
-    }
-    __syncthreads();
-}
-
-// Banded Cholesky of h0^2 A_0 (bandwidth n0), warp 0. Lb[i*(n0+1) + d] = L(i, i-d).
-template <typename F>
-__device__ void chol_factor(double* Lb, int n0, const F* kx, const F* ky)
-{
-    if (threadIdx.x < 32) {
-        const int N = n0 * n0, W = n0 + 1, lane = threadIdx.x;
-        for (int j = 0; j < N; ++j) {
-            const int j1 = j % n0, j2 = j / n0;
-            double d = static_cast<double>(kx[j2 * (n0 + 1) + j1]) + static_cast<double>(kx[j2 * (n0 + 1) + j1 + 1]) +
-                       static_cast<double>(ky[j2 * n0 + j1]) + static_cast<double>(ky[(j2 + 1) * n0 + j1]);
-            for (int q = 1; q <= n0 && q <= j; ++q) {
-                const double l = Lb[j * W + q];
-                d -= l * l;
-            }
-            const double Ljj = sqrt(d);
-            if (lane == 0) Lb[j * W] = Ljj;
-            if (lane >= 1 && lane <= n0 && j + lane < N) {
-                const int i = j + lane;
-                const int i1 = i % n0, i2 = i / n0;
-                double a = 0.0;
-                if (lane == 1 && i1 > 0) a = -static_cast<double>(kx[i2 * (n0 + 1) + i1]);
-                if (lane == n0) a = -static_cast<double>(ky[i2 * n0 + i1]);
-                for (int tt = (i - n0 > 0 ? i - n0 : 0); tt < j; ++tt) a -= Lb[i * W + (i - tt)] * Lb[j * W + (j - tt)];
-                Lb[i * W + lane] = a / Ljj;
-            }
-            __syncwarp();
-        }
-    }
-    __syncthreads();
-}
-
-// Solve (h0^2 A_0) x = h0^2 b with the band factor; b == null: b = 1. Thread 0.
-template <typename B, typename X>
-__device__ void chol_solve(const double* Lb, int n0, const B* b, X* x, double* tmp)
-{
-    if (threadIdx.x == 0) {
-        const int N = n0 * n0, W = n0 + 1;
-        const double h2 = 1.0 / (static_cast<double>(n0) * n0);
-        for (int i = 0; i < N; ++i) {
-            double v = h2 * (b ? static_cast<double>(b[i]) : 1.0);
-            for (int q = 1; q <= n0 && q <= i; ++q) v -= Lb[i * W + q] * tmp[i - q];
-            tmp[i] = v / Lb[i * W];
-        }
-        for (int i = N - 1; i >= 0; --i) {
-            double v = tmp[i];
-            for (int q = 1; q <= n0 && i + q < N; ++q) v -= Lb[(i + q) * W + q] * tmp[i + q];
-            tmp[i] = v / Lb[i * W];
-        }
-        for (int i = 0; i < N; ++i) x[i] = static_cast<X>(tmp[i]);
-    }
-    __syncthreads();
-}
-
-template <typename T>
-__device__ void zero(T* a, int cnt)
-{
-    for (int p = threadIdx.x; p < cnt; p += blockDim.x) a[p] = T(0);
-    __syncthreads();
-}
-
-// V-cycle (Sec. 4 correction scheme, recursively) on levels t_top..0.
-// top_b == null: right-hand side 1 on the top level.
-template <typename T>
-__device__ void vcycle(const FmgArgs& A, unsigned char* slot, int t_top, const T* top_b, const double* Lb, double* tmp)
-{
-    for (int t = t_top; t >= 1; --t) {
-        const Lv<T> F = level_view<T>(A, slot, t);
-        const T* b = (t == t_top) ? top_b : F.bc;
-        if (t < t_top) zero(F.u, F.n * F.n);
-        for (int s = 0; s < A.nu1; ++s) {
-            gs_colour(F, b, 0);
-            gs_colour(F, b, 1);
-        }
-        const Lv<T> Cl = level_view<T>(A, slot, t - 1);
-        resid_restrict(F, b, Cl.bc);
-    }
-    {
-        const Lv<T> C0 = level_view<T>(A, slot, 0);
-        chol_solve(Lb, A.n0, t_top == 0 ? top_b : C0.bc, C0.u, tmp);
-    }
-    for (int t = 1; t <= t_top; ++t) {
-        const Lv<T> F = level_view<T>(A, slot, t);
-        const Lv<T> Cl = level_view<T>(A, slot, t - 1);
-        prolong<T, T, true>(Cl.u, Cl.n, F.u);
-        const T* b = (t == t_top) ? top_b : F.bc;
-        for (int s = 0; s < A.nu2; ++s) {
-            gs_colour(F, b, 1);
-            gs_colour(F, b, 0);
-        }
-    }
-}
-
-// ||1 - A u||_2 on one level (b = 1), FP64 accumulation.
-template <typename T>
-__device__ double resid_norm_ones(const Lv<T>& L, double* red)
-{
-    const int n = L.n;
-    const double ih2 = static_cast<double>(n) * n;
-    double acc = 0.0;
-    for (int p = threadIdx.x; p < n * n; p += blockDim.x) {
-        const int i2 = p / n, i1 = p - i2 * n;
-        const double r = 1.0 - ih2 * static_cast<double>(apply_h2<T, T>(L.kx, L.ky, L.u, n, i1, i2));
-        acc += r * r;
-    }
-    return sqrt(block_sum(acc, red));
-}
-
-// Mixed forms: r = 1 - A64 u64 in FP64, stored to the FP32 rhs; returns ||r||_2.
-__device__ double resid64_to_rhs(const Lv<float>& L, double* red)
-{
-    const int n = L.n;
-    const double ih2 = static_cast<double>(n) * n;
-    double acc = 0.0;
-    for (int p = threadIdx.x; p < n * n; p += blockDim.x) {
-        const int i2 = p / n, i1 = p - i2 * n;
-        const double r = 1.0 - ih2 * apply_h2<double, double>(L.kx64, L.ky64, L.u64, n, i1, i2);
-        L.bc[p] = static_cast<float>(r);
-        acc += r * r;
-    }
-    return sqrt(block_sum(acc, red));
-}
-
-template <typename T>
-__device__ double qoi(const T* u, int n, int kind, double* red)
-{
-    if (kind == MLQMC_QOI_MEAN) {
-        double acc = 0.0;
-        for (int p = threadIdx.x; p < n * n; p += blockDim.x) acc += static_cast<double>(u[p]);
-        return block_sum(acc, red) / (static_cast<double>(n) * n);
-    }
-    const int m = n / 2;
-    const double v = 0.25 * (static_cast<double>(u[(m - 1) * n + (m - 1)]) + static_cast<double>(u[(m - 1) * n + m]) +
-                             static_cast<double>(u[m * n + (m - 1)]) + static_cast<double>(u[m * n + m]));
-    __syncthreads();
-    return v;
-}
-
-template <typename T>
-__device__ void copy_out(const T* src, double* dst, int cnt)
-{
-    for (int p = threadIdx.x; p < cnt; p += blockDim.x) dst[p] = static_cast<double>(src[p]);
-    __syncthreads();
-}
-
-// Persistent FMG kernel. Shared memory: cy[s] | Lb[n0^2 (n0+1)] | tmp[n0^2] | red[40] | F[16].
-template <typename T, bool MX>
-__global__ void __launch_bounds__(256) k_fmg(FmgArgs A)
+__global__ void __launch_bounds__(256, 3) k_small(FmgArgs A)
 {
     extern __shared__ double smem[];
-    double* cy = smem;
+    const WarpTeam tm;
     const int N0 = A.n0 * A.n0;
+    double* cy = smem + (threadIdx.x >> 5) * small_warp_doubles(A.s, A.n0);
     double* Lb = cy + ((A.s + 1) & ~1);
     double* tmp = Lb + N0 * (A.n0 + 1);
-    double* red = tmp + N0;
-    double* Fv = red + 40;
-    __shared__ int s_q;
-    unsigned char* slot = A.work + static_cast<size_t>(blockIdx.x) * A.slot_bytes;
+    double* Fv = tmp + N0;
+    double* red = nullptr;  // warp sums need no scratch
+    const int lane = tm.rank();
 
     for (;;) {
-        if (threadIdx.x == 0) s_q = atomicAdd(A.queue, 1);
-        __syncthreads();
-        const int q = s_q;
-        __syncthreads();
-        if (q >= A.n_samples) break;
-        const SampleDesc d = A.samples[q];
-        const int Lf = d.level;
+        int i = 0;
+        if (tm.leader()) i = atomicAdd(A.queue, 1);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= A.n_samples) break;
+        const SampleDesc d = A.samples[i];
         // sqrt(theta_m) y_m in grouped-by-a order
-        for (int g = threadIdx.x; g < A.s; g += blockDim.x)
+        for (int g = lane; g < A.s; g += 32)
             cy[g] = A.grp_sqrt[g] * A.Y[static_cast<size_t>(d.canon) * A.s + A.grp_m[g]];
-        __syncthreads();
+        tm.sync();
 
         if (A.k_out) {  // field-only mode (introspection)
-            const Lv<T> L = level_view<T>(A, slot, A.field_level);
-            synth_level<T, MX>(A, L, A.field_level, cy);
-            copy_out(L.k, A.k_out + static_cast<size_t>(d.canon) * L.n * L.n, L.n * L.n);
+            const Lv<T> L = view<T>(A, A.field_level, i);
+            synth_level<T>(tm, A, L, A.field_level, cy);
+            copy_out(tm, L.k, A.k_out + static_cast<size_t>(d.canon) * L.n * L.n, L.n * L.n);
             continue;
         }
 
-        for (int t = 0; t <= Lf; ++t) synth_level<T, MX>(A, level_view<T>(A, slot, t), t, cy);
+        const int Ls = d.level < A.t_small ? d.level : A.t_small;
+        for (int t = 0; t <= Ls; ++t) synth_level<T>(tm, A, view<T>(A, t, i), t, cy);
 
-        size_t uoff = 0;
-        {
-            const Lv<T> L0 = level_view<T>(A, slot, 0);
-            if constexpr (MX) {
-                chol_factor(Lb, A.n0, L0.kx64, L0.ky64);
-                chol_solve<T, double>(Lb, A.n0, nullptr, L0.u64, tmp);
-                const double F0 = qoi(L0.u64, A.n0, A.qoi, red);
-                if (threadIdx.x == 0) Fv[0] = F0;
-                if (A.usol) copy_out(L0.u64, A.usol, N0);
-            } else {
-                chol_factor(Lb, A.n0, L0.kx, L0.ky);
-                chol_solve<T, T>(Lb, A.n0, nullptr, L0.u, tmp);
-                const double F0 = qoi(L0.u, A.n0, A.qoi, red);
-                if (threadIdx.x == 0) Fv[0] = F0;
-                if (A.usol) copy_out(L0.u, A.usol, N0);
-            }
-            uoff = N0;
+        const Lv<T> L0 = view<T>(A, 0, i);
+        chol_factor(tm, Lb, A.n0, L0.kx, L0.ky);
+        if (d.level > A.t_small) {  // kept for the V-cycles of the large levels
+            double* g = at<double>(A.chol, i);
+            for (int q = lane; q < N0 * (A.n0 + 1); q += 32) g[q] = Lb[q];
         }
-        for (int t = 1; t <= Lf; ++t) {
-            const Lv<T> L = level_view<T>(A, slot, t);
-            const Lv<T> Lc = level_view<T>(A, slot, t - 1);
+        size_t uoff = N0;
+        if constexpr (MX) {
+            chol_solve<T, double>(tm, Lb, A.n0, nullptr, L0.u64, tmp);
+            const double F0 = qoi(tm, L0.u64, A.n0, A.qoi, red);
+            if (tm.leader()) Fv[0] = F0;
+            if (A.usol) copy_out(tm, L0.u64, A.usol, N0);
+        } else {
+            chol_solve<T, T>(tm, Lb, A.n0, nullptr, L0.u, tmp);
+            const double F0 = qoi(tm, L0.u, A.n0, A.qoi, red);
+            if (tm.leader()) Fv[0] = F0;
+            if (A.usol) copy_out(tm, L0.u, A.usol, N0);
+        }
+        for (int t = 1; t <= Ls; ++t) {
+            const Lv<T> L = view<T>(A, t, i);
+            const Lv<T> Lc = view<T>(A, t - 1, i);
             const int n = L.n;
             double Ft;
             if constexpr (MX) {
-                prolong<double, double, false>(Lc.u64, Lc.n, L.u64);
+                prolong<double, double, false>(tm, Lc.u64, Lc.n, L.u64);
                 for (int m = 0; m < A.mu0; ++m) {
-                    // one refinement step per FMG cycle: r = 1 - A64 u64, FP32 V-cycle on A e = r
-                    resid64_to_rhs(L, red);
-                    zero(L.u, n * n);
-                    vcycle<T>(A, slot, t, L.bc, Lb, tmp);
-                    for (int p = threadIdx.x; p < n * n; p += blockDim.x) L.u64[p] += static_cast<double>(L.u[p]);
-                    __syncthreads();
+                    // one refinement step per FMG cycle: r = 1 - A u64 in FP64, FP32 V-cycle on A e = r
+                    resid64_to_rhs(tm, L, red);
+                    zero(tm, L.u, n * n);
+                    vcycle<T>(tm, A, i, t, L.bc, Lb, tmp);
+                    for (int p = lane; p < n * n; p += 32) L.u64[p] += static_cast<double>(L.u[p]);
+                    tm.sync();
                 }
                 if (A.rtol > 0.0) {
-                    int it = 0;
-                    for (;;) {
-                        const double rn = resid64_to_rhs(L, red);
+                    for (int it = 0;; ++it) {
+                        const double rn = resid64_to_rhs(tm, L, red);
                         if (rn <= A.rtol * n) break;
                         if (it >= A.max_iter) {
-                            if (threadIdx.x == 0) atomicOr(A.status, kStatusNotConverged);
+                            if (tm.leader()) atomicOr(A.status, kStatusNotConverged);
                             break;
                         }
-                        zero(L.u, n * n);
-                        vcycle<T>(A, slot, t, L.bc, Lb, tmp);
-                        for (int p = threadIdx.x; p < n * n; p += blockDim.x) L.u64[p] += static_cast<double>(L.u[p]);
-                        __syncthreads();
-                        ++it;
+                        zero(tm, L.u, n * n);
+                        vcycle<T>(tm, A, i, t, L.bc, Lb, tmp);
+                        for (int p = lane; p < n * n; p += 32) L.u64[p] += static_cast<double>(L.u[p]);
+                        tm.sync();
                     }
                 }
-                Ft = qoi(L.u64, n, A.qoi, red);
-                if (A.usol) copy_out(L.u64, A.usol + uoff, n * n);
+                Ft = qoi(tm, L.u64, n, A.qoi, red);
+                if (A.usol) copy_out(tm, L.u64, A.usol + uoff, n * n);
             } else {
-                prolong<T, T, false>(Lc.u, Lc.n, L.u);
-                for (int m = 0; m < A.mu0; ++m) vcycle<T>(A, slot, t, nullptr, Lb, tmp);
+                prolong<T, T, false>(tm, Lc.u, Lc.n, L.u);
+                for (int m = 0; m < A.mu0; ++m) vcycle<T>(tm, A, i, t, nullptr, Lb, tmp);
                 if (A.rtol > 0.0) {
-                    int it = 0;
-                    for (;;) {
-                        const double rn = resid_norm_ones(L, red);
+                    for (int it = 0;; ++it) {
+                        const double rn = resid_norm_ones(tm, L, red);
                         if (rn <= A.rtol * n) break;
                         if (it >= A.max_iter) {
-                            if (threadIdx.x == 0) atomicOr(A.status, kStatusNotConverged);
+                            if (tm.leader()) atomicOr(A.status, kStatusNotConverged);
                             break;
                         }
-                        vcycle<T>(A, slot, t, nullptr, Lb, tmp);
-                        ++it;
+                        vcycle<T>(tm, A, i, t, nullptr, Lb, tmp);
                     }
                 }
-                Ft = qoi(L.u, n, A.qoi, red);
-                if (A.usol) copy_out(L.u, A.usol + uoff, n * n);
+                Ft = qoi(tm, L.u, n, A.qoi, red);
+                if (A.usol) copy_out(tm, L.u, A.usol + uoff, n * n);
             }
-            if (threadIdx.x == 0) Fv[t] = Ft;
+            if (tm.leader()) Fv[t] = Ft;
             uoff += static_cast<size_t>(n) * n;
         }
-        __syncthreads();
-        if (threadIdx.x < A.n_levels) {
-            const int t = threadIdx.x;
-            const size_t o = static_cast<size_t>(d.canon) * A.n_levels + t;
-            const double Ft = t <= Lf ? Fv[t] : 0.0;
-            const double dF = t <= Lf ? Ft - (t > 0 ? Fv[t - 1] : 0.0) : 0.0;
-            if (A.dF) A.dF[o] = dF;
-            if (A.F_out) A.F_out[o] = Ft;
-        }
-        __syncthreads();
+        tm.sync();
+        if (lane <= Ls) A.F[static_cast<size_t>(i) * A.n_levels + lane] = Fv[lane];
+        tm.sync();
     }
 }
 
-// Deterministic reuse sums per (level t, shift r): one block each, fixed order.
-__global__ void k_sums(const int2* __restrict__ canon, int n, const double* __restrict__ dF, int n_levels, int R,
+// V-cycle on the small levels t_small..0 of samples i < B (zero start, right-hand
+// side in bc of level t_small), below a V-cycle on the large levels; one warp
+// per sample.
+template <typename T>
+__global__ void __launch_bounds__(256) k_small_vcycle(FmgArgs A, int B)
+{
+    __shared__ double tmp_all[8][256];
+    const WarpTeam tm;
+    const int warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    for (int i = blockIdx.x * nw + warp; i < B; i += gridDim.x * nw) {
+        if (A.active && !A.active[i]) continue;
+        const Lv<T> Ts = view<T>(A, A.t_small, i);
+        zero(tm, Ts.u, Ts.n * Ts.n);
+        vcycle<T>(tm, A, i, A.t_small, Ts.bc, at<double>(A.chol, i), tmp_all[warp]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Level-synchronous kernels over samples 0..B-1 of level t.
+// ---------------------------------------------------------------------------
+#define GRID_STRIDE(idx, total)                                                                         \
+    for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < (total); \
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x)
+
+__device__ __forceinline__ bool inactive(const FmgArgs& A, int i)
+{
+    return A.active && !A.active[i];
+}
+
+// G[i][a][i2] = sum_{m: a_m = a} sqrt(theta_m) y_m psi_{b_m}(x2)
+template <typename T>
+__global__ void kb_synth_G(FmgArgs A, int t, int B)
+{
+    const int n = A.lv[t].n;
+    const T* psi = static_cast<const T*>(A.psi) + A.psi_off[t];
+    const int64_t per = static_cast<int64_t>(A.Ka) * n;
+    GRID_STRIDE(idx, B * per)
+    {
+        const int i = static_cast<int>(idx / per);
+        const int rem = static_cast<int>(idx - i * per);
+        const int a = rem / n;
+        const int i2 = rem - a * n;
+        const double* y = A.Y + static_cast<size_t>(A.samples[i].canon) * A.s;
+        T acc = T(0);
+        const int g1 = A.grp_start[a + 1];
+        for (int g = A.grp_start[a]; g < g1; ++g)
+            acc += static_cast<T>(A.grp_sqrt[g] * y[A.grp_m[g]]) * psi[A.grp_b[g] * n + i2];
+        at<T>(A.lv[t].G, i)[rem] = acc;
+    }
+}
+
+// k = exp(sum_a psi_a(x1) G_a(x2))
+template <typename T>
+__global__ void kb_synth_z(FmgArgs A, int t, int B)
+{
+    const int n = A.lv[t].n;
+    const T* psi = static_cast<const T*>(A.psi) + A.psi_off[t];
+    const int64_t per = static_cast<int64_t>(n) * n;
+    GRID_STRIDE(idx, B * per)
+    {
+        const int i = static_cast<int>(idx / per);
+        const int p = static_cast<int>(idx - i * per);
+        const int i2 = p / n;
+        const int i1 = p - i2 * n;
+        const T* G = at<T>(A.lv[t].G, i);
+        T z = T(0);
+        for (int a = 0; a < A.Ka; ++a) z += psi[a * n + i1] * G[a * n + i2];
+        at<T>(A.lv[t].k, i)[p] = expT(z);
+    }
+}
+
+template <typename T>
+__global__ void kb_faces(FmgArgs A, int t, int B)
+{
+    const int n = A.lv[t].n;
+    const int64_t per = static_cast<int64_t>(n) * (n + 1);
+    GRID_STRIDE(idx, B * per)
+    {
+        const int i = static_cast<int>(idx / per);
+        const int q = static_cast<int>(idx - i * per);
+        const T* k = at<T>(A.lv[t].k, i);
+        const int i2 = q / (n + 1);
+        at<T>(A.lv[t].kx, i)[q] = face_x(k, n, i2, q - i2 * (n + 1));
+        const int g = q / n;
+        at<T>(A.lv[t].ky, i)[q] = face_y(k, n, g, q - g * n);
+    }
+}
+
+template <typename T>
+__global__ void kb_idiag(FmgArgs A, int t, int B)
+{
+    const int n = A.lv[t].n;
+    const int64_t per = static_cast<int64_t>(n) * n;
+    GRID_STRIDE(idx, B * per)
+    {
+        const int i = static_cast<int>(idx / per);
+        const int p = static_cast<int>(idx - i * per);
+        const int i2 = p / n;
+        at<T>(A.lv[t].idiag, i)[p] = inv_diag(at<T>(A.lv[t].kx, i), at<T>(A.lv[t].ky, i), n, p - i2 * n, i2);
+    }
+}
+
+// One colour of a red-black sweep; ones: right-hand side 1, else bc of level t.
+template <typename T>
+__global__ void kb_gs(FmgArgs A, int t, int B, int colour, int ones)
+{
+    const int n = A.lv[t].n;
+    const int half = n >> 1;
+    const int64_t per = static_cast<int64_t>(n) * half;
+    const T h2 = T(1) / (T(n) * T(n));
+    GRID_STRIDE(idx, B * per)
+    {
+        const int i = static_cast<int>(idx / per);
+        if (inactive(A, i)) continue;
+        const int q = static_cast<int>(idx - i * per);
+        const int i2 = q / half;
+        const Lv<T> L = view<T>(A, t, i);
+        gs_cell(L, ones ? nullptr : L.bc, h2, 2 * (q - i2 * half) + ((i2 + colour) & 1), i2);
+    }
+}
+
+// bc of level t-1 = mean over children of (b - A u) on level t.
+template <typename T>
+__global__ void kb_resid_restrict(FmgArgs A, int t, int B, int ones)
+{
+    const int nc = A.lv[t].n >> 1;
+    const int64_t per = static_cast<int64_t>(nc) * nc;
+    GRID_STRIDE(idx, B * per)
+    {
+        const int i = static_cast<int>(idx / per);
+        if (inactive(A, i)) continue;
+        const int q = static_cast<int>(idx - i * per);
+        const int I2 = q / nc;
+        const Lv<T> F = view<T>(A, t, i);
+        at<T>(A.lv[t - 1].bc, i)[q] = resid_restrict_cell(F, ones ? nullptr : F.bc, q - I2 * nc, I2);
+    }
+}
+
+// u of level t (+)= P u of level t-1 (FP64 solution arrays when U64).
+template <typename T, bool ADD, bool U64>
+__global__ void kb_prolong(FmgArgs A, int t, int B)
+{
+    const int n = A.lv[t].n;
+    const int nc = n >> 1;
+    const int64_t per = static_cast<int64_t>(n) * n;
+    GRID_STRIDE(idx, B * per)
+    {
+        const int i = static_cast<int>(idx / per);
+        if (inactive(A, i)) continue;
+        const int p = static_cast<int>(idx - i * per);
+        const int i2 = p / n;
+        const int i1 = p - i2 * n;
+        if constexpr (U64) {
+            const double v = prolong_cell<double, double>(at<double>(A.lv[t - 1].u64, i), nc, i1, i2);
+            double* u = at<double>(A.lv[t].u64, i);
+            if (ADD) u[p] += v;
+            else u[p] = v;
+        } else {
+            const T v = prolong_cell<T, T>(at<T>(A.lv[t - 1].u, i), nc, i1, i2);
+            T* u = at<T>(A.lv[t].u, i);
+            if (ADD) u[p] += v;
+            else u[p] = v;
+        }
+    }
+}
+
+// Mixed forms: bc = 1 - A u64 (FP64 residual, FP32 faces widened).
+__global__ void kb_resid64(FmgArgs A, int t, int B)
+{
+    const int n = A.lv[t].n;
+    const int64_t per = static_cast<int64_t>(n) * n;
+    GRID_STRIDE(idx, B * per)
+    {
+        const int i = static_cast<int>(idx / per);
+        if (inactive(A, i)) continue;
+        const int p = static_cast<int>(idx - i * per);
+        const int i2 = p / n;
+        const Lv<float> L = view<float>(A, t, i);
+        L.bc[p] = static_cast<float>(resid64_cell(L, p - i2 * n, i2));
+    }
+}
+
+// Mixed forms: u64 += e.
+__global__ void kb_update64(FmgArgs A, int t, int B)
+{
+    const int n = A.lv[t].n;
+    const int64_t per = static_cast<int64_t>(n) * n;
+    GRID_STRIDE(idx, B * per)
+    {
+        const int i = static_cast<int>(idx / per);
+        if (inactive(A, i)) continue;
+        const int p = static_cast<int>(idx - i * per);
+        at<double>(A.lv[t].u64, i)[p] += static_cast<double>(at<float>(A.lv[t].u, i)[p]);
+    }
+}
+
+// Per-sample residual norm (one CTA per sample, deterministic); the mixed forms
+// also leave r in bc for the next correction.
+template <typename T, bool MX>
+__global__ void __launch_bounds__(256) kb_resnorm(FmgArgs A, int t, int B)
+{
+    __shared__ double red[48];
+    const BlockTeam tm;
+    for (int i = blockIdx.x; i < B; i += gridDim.x) {
+        const Lv<T> L = view<T>(A, t, i);
+        double nr;
+        if constexpr (MX) nr = resid64_to_rhs(tm, L, red);
+        else nr = resid_norm_ones(tm, L, red);
+        if (threadIdx.x == 0) A.norms[i] = nr;
+    }
+}
+
+// active[i] = (norm_i > thresh); *count = number of active samples.
+__global__ void kb_flags(const double* norms, int* active, int B, double thresh, int* count)
+{
+    GRID_STRIDE(i, B)
+    {
+        const int a = norms[i] > thresh ? 1 : 0;
+        active[i] = a;
+        if (a) atomicAdd(count, 1);
+    }
+}
+
+// F_t of samples 0..B-1 (one CTA per sample).
+template <typename T, bool U64>
+__global__ void __launch_bounds__(256) kb_qoi(FmgArgs A, int t, int B)
+{
+    __shared__ double red[48];
+    const BlockTeam tm;
+    for (int i = blockIdx.x; i < B; i += gridDim.x) {
+        double v;
+        if constexpr (U64) v = qoi(tm, at<double>(A.lv[t].u64, i), A.lv[t].n, A.qoi, red);
+        else v = qoi(tm, at<T>(A.lv[t].u, i), A.lv[t].n, A.qoi, red);
+        if (threadIdx.x == 0) A.F[static_cast<size_t>(i) * A.n_levels + t] = v;
+    }
+}
+
+// k of level t (samples 0..B-1) widened to FP64, by canon (introspection).
+template <typename T>
+__global__ void kb_k_out(FmgArgs A, int t, int B, double* out)
+{
+    const int n = A.lv[t].n;
+    const int64_t per = static_cast<int64_t>(n) * n;
+    GRID_STRIDE(idx, B * per)
+    {
+        const int i = static_cast<int>(idx / per);
+        const int p = static_cast<int>(idx - i * per);
+        out[static_cast<size_t>(A.samples[i].canon) * per + p] = static_cast<double>(at<T>(A.lv[t].k, i)[p]);
+    }
+}
+
+// Solution of level t of sample 0 widened to FP64 (introspection).
+template <typename T, bool U64>
+__global__ void kb_u_out(FmgArgs A, int t, double* out)
+{
+    const int n = A.lv[t].n;
+    GRID_STRIDE(p, static_cast<int64_t>(n) * n)
+    {
+        if constexpr (U64) out[p] = at<double>(A.lv[t].u64, 0)[p];
+        else out[p] = static_cast<double>(at<T>(A.lv[t].u, 0)[p]);
+    }
+}
+
+// Deterministic reuse sums per (level t, shift r): one block each, rank order.
+__global__ void k_sums(const SampleDesc* __restrict__ smp, int n, const double* __restrict__ F, int n_levels, int R,
                        int reuse, double* __restrict__ sums)
 {
     __shared__ double red[48];
@@ -609,9 +480,10 @@ __global__ void k_sums(const int2* __restrict__ canon, int n, const double* __re
     const int r = blockIdx.x - t * R;
     double a = 0.0, a2 = 0.0;
     for (int q = threadIdx.x; q < n; q += blockDim.x) {
-        const int2 lr = canon[q];
-        if (lr.y == r && (reuse ? lr.x >= t : lr.x == t)) {
-            const double v = dF[static_cast<size_t>(q) * n_levels + t];
+        const SampleDesc d = smp[q];
+        if (d.r == r && (reuse ? d.level >= t : d.level == t)) {
+            const double* Fq = F + static_cast<size_t>(q) * n_levels;
+            const double v = Fq[t] - (t > 0 ? Fq[t - 1] : 0.0);
             a += v;
             a2 += v * v;
         }
@@ -624,8 +496,21 @@ __global__ void k_sums(const int2* __restrict__ canon, int n, const double* __re
     }
 }
 
+// Per-sample F_0..F_level (zeros above) in work order.
+__global__ void k_fout(const SampleDesc* __restrict__ smp, int n, const double* __restrict__ F, int n_levels,
+                       double* __restrict__ out)
+{
+    GRID_STRIDE(idx, static_cast<int64_t>(n) * n_levels)
+    {
+        const int q = static_cast<int>(idx / n_levels);
+        const int t = static_cast<int>(idx - static_cast<int64_t>(q) * n_levels);
+        const SampleDesc d = smp[q];
+        out[static_cast<size_t>(d.gidx) * n_levels + t] = t <= d.level ? F[static_cast<size_t>(q) * n_levels + t] : 0.0;
+    }
+}
+
 // ---------------------------------------------------------------------------
-// Host helpers
+// Host side
 // ---------------------------------------------------------------------------
 inline bool ok(cudaError_t e) { return e == cudaSuccess; }
 
@@ -633,60 +518,74 @@ size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
 bool is_mixed(const mlqmc_problem& p) { return p.precision != MLQMC_FP64; }
 
-SlotLayout make_layout(const mlqmc_problem& p, int Ka)
+size_t elem_size(const mlqmc_problem& p) { return is_mixed(p) ? sizeof(float) : sizeof(double); }
+
+// Bytes per sample of each pooled array of level t.
+void level_strides(const mlqmc_problem& p, int Ka, int t, size_t st[kPoolArrs])
 {
-    SlotLayout L;
-    L.n_levels = p.n_levels;
-    const size_t es = is_mixed(p) ? sizeof(float) : sizeof(double);
-    size_t off = 0;
-    for (int t = 0; t < p.n_levels; ++t) {
-        const size_t n = static_cast<size_t>(p.coarse_cells) << t;
-        LevelOffsets& o = L.lv[t];
-        o.n = static_cast<int>(n);
-        o.u = off; off = align256(off + es * n * n);
-        o.bc = off; off = align256(off + es * n * n);
-        o.kx = off; off = align256(off + es * n * (n + 1));
-        o.ky = off; off = align256(off + es * n * (n + 1));
-        o.idiag = off; off = align256(off + es * n * n);
-        o.k = off; off = align256(off + es * n * n);
-        o.G = off; off = align256(off + es * Ka * n);
-        if (is_mixed(p)) {
-            o.u64 = off; off = align256(off + 8 * n * n);
-            o.kx64 = off; off = align256(off + 8 * n * (n + 1));
-            o.ky64 = off; off = align256(off + 8 * n * (n + 1));
-        } else {
-            o.u64 = o.kx64 = o.ky64 = 0;
-        }
+    const size_t n = static_cast<size_t>(p.coarse_cells) << t;
+    const size_t es = elem_size(p);
+    st[kU] = align256(es * n * n);
+    st[kBc] = align256(es * n * n);
+    st[kKx] = align256(es * n * (n + 1));
+    st[kKy] = align256(es * n * (n + 1));
+    st[kIdiag] = align256(es * n * n);
+    st[kK] = align256(es * n * n);
+    st[kG] = align256(es * static_cast<size_t>(std::max(Ka, 1)) * n);
+    st[kU64] = is_mixed(p) ? align256(8 * n * n) : 0;
+}
+
+size_t level_bytes_per_sample(const mlqmc_problem& p, int Ka, int t)
+{
+    size_t st[kPoolArrs];
+    level_strides(p, Ka, t, st);
+    size_t b = 0;
+    for (int a = 0; a < kPoolArrs; ++a) b += st[a];
+    return b;
+}
+
+// Grow the pool of level t to hold at least `need` samples.
+mlqmc_status ensure_pool(mlqmc_ctx* c, int t, int64_t need)
+{
+    LevelPool& P = c->pools[t];
+    if (need <= P.cap) return MLQMC_OK;
+    const int64_t cap = std::max<int64_t>(need, P.cap + P.cap / 2);
+    size_t st[kPoolArrs];
+    level_strides(c->p, c->Ka, t, st);
+    size_t off = 0, offs[kPoolArrs];
+    for (int a = 0; a < kPoolArrs; ++a) {
+        offs[a] = off;
+        off += st[a] * static_cast<size_t>(cap);
     }
-    L.bytes = off;
-    return L;
-}
-
-size_t fmg_smem_bytes(const mlqmc_problem& p)
-{
-    const size_t N0 = static_cast<size_t>(p.coarse_cells) * p.coarse_cells;
-    return sizeof(double) * (((p.n_modes + 1) & ~1) + N0 * (p.coarse_cells + 1) + N0 + 40 + 16);
-}
-
-template <typename T, bool MX>
-void* fmg_kernel_ptr()
-{
-    return reinterpret_cast<void*>(&k_fmg<T, MX>);
-}
-
-void* fmg_kernel(const mlqmc_problem& p)
-{
-    return is_mixed(p) ? fmg_kernel_ptr<float, true>() : fmg_kernel_ptr<double, false>();
+    if (P.mem) {
+        cudaDeviceSynchronize();
+        cudaFree(P.mem);
+        P.mem = nullptr;
+        P.cap = 0;
+    }
+    if (!ok(cudaMalloc(&P.mem, std::max<size_t>(off, 256)))) {
+        cudaGetLastError();
+        P.mem = nullptr;
+        return MLQMC_ERR_OOM;
+    }
+    P.cap = cap;
+    for (int a = 0; a < kPoolArrs; ++a) {
+        P.off[a] = offs[a];
+        P.stride[a] = st[a];
+    }
+    return MLQMC_OK;
 }
 
 FmgArgs base_args(mlqmc_ctx* c)
 {
     FmgArgs A;
     std::memset(&A, 0, sizeof(A));
+    A.samples = c->d_samples;
     A.Y = c->d_Y;
     A.s = c->p.n_modes;
     A.n0 = c->p.coarse_cells;
     A.n_levels = c->p.n_levels;
+    A.t_small = c->t_small;
     A.qoi = c->p.qoi;
     A.mu0 = c->p.mu0;
     A.nu1 = c->p.nu1;
@@ -700,11 +599,22 @@ FmgArgs base_args(mlqmc_ctx* c)
     A.grp_b = c->d_grp_b;
     A.grp_m = c->d_grp_m;
     A.grp_sqrt = c->d_grp_sqrt;
-    A.work = c->d_work;
-    A.slot_bytes = c->layout.bytes;
-    for (int t = 0; t < c->p.n_levels; ++t) A.lv[t] = c->layout.lv[t];
+    for (int t = 0; t < c->p.n_levels; ++t) {
+        const LevelPool& P = c->pools[t];
+        LevelDesc& d = A.lv[t];
+        d.n = c->p.coarse_cells << t;
+        ArrDesc* arr[kPoolArrs] = {&d.u, &d.bc, &d.kx, &d.ky, &d.idiag, &d.k, &d.G, &d.u64};
+        for (int a = 0; a < kPoolArrs; ++a) {
+            arr[a]->base = P.mem ? P.mem + P.off[a] : nullptr;
+            arr[a]->stride = P.stride[a];
+        }
+    }
+    A.chol.base = reinterpret_cast<unsigned char*>(c->d_chol);
+    A.chol.stride = c->chol_stride;
+    A.F = c->d_F;
     A.queue = c->d_queue;
     A.status = c->d_status;
+    A.norms = c->d_norms;
     return A;
 }
 
@@ -720,48 +630,280 @@ cudaEvent_t take_event(mlqmc_ctx* c)
     return e;
 }
 
-// Record the opening event of a timed launch (no-op unless profiling).
-cudaEvent_t mark_begin(mlqmc_ctx* c, cudaStream_t st)
+// Brackets one launch with events when profiling is on.
+struct Timed {
+    mlqmc_ctx* c;
+    int kind;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    Timed(mlqmc_ctx* c_, int kind_, cudaStream_t st_) : c(c_), kind(kind_), st(st_)
+    {
+        if (c->profiling) {
+            a = take_event(c);
+            cudaEventRecord(a, st);
+        }
+    }
+    ~Timed()
+    {
+        c->launches += 1;
+        if (!a) return;
+        cudaEvent_t b = take_event(c);
+        cudaEventRecord(b, st);
+        c->marks.push_back({kind, a, b});
+    }
+};
+
+int grid_for(mlqmc_ctx* c, int64_t work, int threads = 256)
 {
-    if (!c->profiling) return nullptr;
-    cudaEvent_t e = take_event(c);
-    cudaEventRecord(e, st);
-    return e;
+    const int64_t want = (work + threads - 1) / threads;
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, static_cast<int64_t>(c->sm_count) * 32)));
 }
 
-void mark_end(mlqmc_ctx* c, int kind, cudaEvent_t a, cudaStream_t st)
+int grid_samples(mlqmc_ctx* c, int B)
 {
-    if (!a) return;
-    cudaEvent_t b = take_event(c);
-    cudaEventRecord(b, st);
-    c->marks.push_back({kind, a, b});
+    return std::max(1, std::min(B, c->sm_count * 8));
 }
 
-mlqmc_status launch_fmg(mlqmc_ctx* c, FmgArgs& A, int n_samples, cudaStream_t st)
+mlqmc_status last_error()
 {
-    A.n_samples = n_samples;
+    return ok(cudaGetLastError()) ? MLQMC_OK : MLQMC_ERR_CUDA;
+}
+
+template <typename T, bool MX>
+void* small_kernel_ptr()
+{
+    return reinterpret_cast<void*>(&k_small<T, MX>);
+}
+
+void* small_kernel(const mlqmc_problem& p)
+{
+    return is_mixed(p) ? small_kernel_ptr<float, true>() : small_kernel_ptr<double, false>();
+}
+
+mlqmc_status launch_small(mlqmc_ctx* c, FmgArgs& A, int count, cudaStream_t st)
+{
+    A.n_samples = count;
     if (!ok(cudaMemsetAsync(c->d_queue, 0, sizeof(int), st))) return MLQMC_ERR_CUDA;
-    const int grid = std::max(1, std::min(n_samples, c->slots));
+    const int grid = std::max(1, std::min((count + 7) / 8, c->small_grid));
     void* args[] = {&A};
-    cudaEvent_t m = mark_begin(c, st);
-    if (!ok(cudaLaunchKernel(fmg_kernel(c->p), dim3(grid), dim3(c->fmg_threads), args, c->fmg_smem, st)))
+    Timed tm(c, kProfSmall, st);
+    if (!ok(cudaLaunchKernel(small_kernel(c->p), dim3(grid), dim3(c->fmg_threads), args, c->small_smem, st)))
         return MLQMC_ERR_CUDA;
-    mark_end(c, 1, m, st);
-    c->launches += 1;
     return MLQMC_OK;
 }
 
 mlqmc_status launch_points(mlqmc_ctx* c, const SampleDesc* d_s, int count, double* Y, uint64_t* bits, cudaStream_t st)
 {
     const int64_t total = static_cast<int64_t>(count) * c->p.n_modes;
-    const int threads = 256;
-    const int64_t want = (total + threads - 1) / threads;
-    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, static_cast<int64_t>(c->sm_count) * 16)));
-    cudaEvent_t m = mark_begin(c, st);
-    k_points<<<grid, threads, 0, st>>>(d_s, count, c->p.n_modes, c->p.sampler, c->p.seed, c->d_z, Y, bits);
-    if (!ok(cudaGetLastError())) return MLQMC_ERR_CUDA;
-    mark_end(c, 0, m, st);
-    c->launches += 1;
+    Timed tm(c, kProfPoints, st);
+    k_points<<<grid_for(c, total), 256, 0, st>>>(d_s, count, c->p.n_modes, c->p.sampler, c->p.seed, c->d_z, Y, bits);
+    return last_error();
+}
+
+// Batched KL field and faces of level t for samples 0..B-1.
+template <typename T>
+mlqmc_status synth_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cudaStream_t st)
+{
+    const int64_t n = c->p.coarse_cells << t;
+    {
+        Timed tm(c, kProfSynth, st);
+        kb_synth_G<T><<<grid_for(c, B * c->Ka * n), 256, 0, st>>>(A, t, B);
+    }
+    {
+        Timed tm(c, kProfSynth, st);
+        kb_synth_z<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
+    }
+    {
+        Timed tm(c, kProfSynth, st);
+        kb_faces<T><<<grid_for(c, B * n * (n + 1)), 256, 0, st>>>(A, t, B);
+    }
+    {
+        Timed tm(c, kProfSynth, st);
+        kb_idiag<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
+    }
+    return last_error();
+}
+
+mlqmc_status zero_u(mlqmc_ctx* c, int t, int B, cudaStream_t st)
+{
+    const LevelPool& P = c->pools[t];
+    return ok(cudaMemsetAsync(P.mem + P.off[kU], 0, P.stride[kU] * static_cast<size_t>(B), st)) ? MLQMC_OK
+                                                                                                : MLQMC_ERR_CUDA;
+}
+
+// V-cycle on level t_top (> t_small) for samples 0..B-1: batched sweeps and
+// transfers on the large levels, k_small_vcycle below them. ones: the top
+// right-hand side is 1 (FP64 form), else bc of t_top (mixed correction).
+template <typename T>
+mlqmc_status vcycle_batched(mlqmc_ctx* c, const FmgArgs& A, int t_top, int B, bool ones, cudaStream_t st)
+{
+    const int ts = c->t_small;
+    for (int t = t_top; t > ts; --t) {
+        const int64_t n = c->p.coarse_cells << t;
+        const int top_ones = (t == t_top && ones) ? 1 : 0;
+        if (t < t_top && zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
+        for (int s = 0; s < c->p.nu1; ++s) {
+            for (int colour = 0; colour < 2; ++colour) {
+                Timed tm(c, kProfSmooth, st);
+                kb_gs<T><<<grid_for(c, B * n * n / 2), 256, 0, st>>>(A, t, B, colour, top_ones);
+            }
+        }
+        Timed tm(c, kProfTransfer, st);
+        kb_resid_restrict<T><<<grid_for(c, B * n * n / 4), 256, 0, st>>>(A, t, B, top_ones);
+    }
+    {
+        Timed tm(c, kProfSmallV, st);
+        k_small_vcycle<T><<<std::max(1, std::min((B + 7) / 8, c->sm_count * 8)), 256, 0, st>>>(A, B);
+    }
+    for (int t = ts + 1; t <= t_top; ++t) {
+        const int64_t n = c->p.coarse_cells << t;
+        const int top_ones = (t == t_top && ones) ? 1 : 0;
+        {
+            Timed tm(c, kProfTransfer, st);
+            kb_prolong<T, true, false><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
+        }
+        for (int s = 0; s < c->p.nu2; ++s) {
+            for (int colour = 1; colour >= 0; --colour) {
+                Timed tm(c, kProfSmooth, st);
+                kb_gs<T><<<grid_for(c, B * n * n / 2), 256, 0, st>>>(A, t, B, colour, top_ones);
+            }
+        }
+    }
+    return last_error();
+}
+
+// Host loop of the converged form on a large level: per-sample norms, active
+// flags, one more cycle for the active samples, until none is active.
+template <typename T, bool MX>
+mlqmc_status converge_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cudaStream_t st)
+{
+    const int64_t n = c->p.coarse_cells << t;
+    for (int it = 0;; ++it) {
+        {
+            Timed tm(c, kProfReduce, st);
+            kb_resnorm<T, MX><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
+        }
+        if (!ok(cudaMemsetAsync(c->d_count, 0, sizeof(int), st))) return MLQMC_ERR_CUDA;
+        {
+            Timed tm(c, kProfReduce, st);
+            kb_flags<<<grid_for(c, B), 256, 0, st>>>(c->d_norms, c->d_active, B, c->p.refine_rtol * n, c->d_count);
+        }
+        if (!ok(cudaMemcpyAsync(c->h_count, c->d_count, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
+            !ok(cudaStreamSynchronize(st)))
+            return MLQMC_ERR_CUDA;
+        if (*c->h_count == 0) break;
+        if (it >= c->p.refine_max_iter) {
+            c->host_status |= kStatusNotConverged;
+            break;
+        }
+        FmgArgs M = A;
+        M.active = c->d_active;
+        if constexpr (MX) {
+            if (zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
+            mlqmc_status s = vcycle_batched<T>(c, M, t, B, false, st);
+            if (s != MLQMC_OK) return s;
+            Timed tm(c, kProfTransfer, st);
+            kb_update64<<<grid_for(c, B * n * n), 256, 0, st>>>(M, t, B);
+        } else {
+            mlqmc_status s = vcycle_batched<T>(c, M, t, B, true, st);
+            if (s != MLQMC_OK) return s;
+        }
+    }
+    return last_error();
+}
+
+// FMG stages above t_small for the B_t samples that reach them.
+template <typename T, bool MX>
+mlqmc_status large_stages(mlqmc_ctx* c, const FmgArgs& A, const int* Bt, int Lmax, double* d_usol, cudaStream_t st)
+{
+    size_t uoff = 0;
+    for (int t = 0; t <= c->t_small && t <= Lmax; ++t) uoff += static_cast<size_t>(A.lv[t].n) * A.lv[t].n;
+    for (int t = c->t_small + 1; t <= Lmax; ++t) {
+        const int B = Bt[t];
+        if (B == 0) break;
+        const int64_t n = c->p.coarse_cells << t;
+        {
+            Timed tm(c, kProfTransfer, st);
+            kb_prolong<T, false, MX><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
+        }
+        for (int m = 0; m < c->p.mu0; ++m) {
+            if constexpr (MX) {
+                {
+                    Timed tm(c, kProfTransfer, st);
+                    kb_resid64<<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
+                }
+                if (zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
+                mlqmc_status s = vcycle_batched<T>(c, A, t, B, false, st);
+                if (s != MLQMC_OK) return s;
+                Timed tm(c, kProfTransfer, st);
+                kb_update64<<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
+            } else {
+                mlqmc_status s = vcycle_batched<T>(c, A, t, B, true, st);
+                if (s != MLQMC_OK) return s;
+            }
+        }
+        if (c->p.refine_rtol > 0.0) {
+            mlqmc_status s = converge_batched<T, MX>(c, A, t, B, st);
+            if (s != MLQMC_OK) return s;
+        }
+        {
+            Timed tm(c, kProfReduce, st);
+            kb_qoi<T, MX><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
+        }
+        if (d_usol) {
+            Timed tm(c, kProfReduce, st);
+            kb_u_out<T, MX><<<grid_for(c, n * n), 256, 0, st>>>(A, t, d_usol + uoff);
+            uoff += static_cast<size_t>(n) * n;
+        }
+    }
+    return last_error();
+}
+
+// Everything for one chunk of samples already staged in d_samples (rank order).
+mlqmc_status run_chunk(mlqmc_ctx* c, int count, const int* Bt, int Lmax, double* d_sums, double* d_Fout,
+                       double* d_usol, cudaStream_t st)
+{
+    const mlqmc_problem& p = c->p;
+    for (int t = 0; t <= Lmax; ++t) {
+        mlqmc_status s = ensure_pool(c, t, Bt[t]);
+        if (s != MLQMC_OK) return s;
+    }
+    FmgArgs A = base_args(c);
+    mlqmc_status s = launch_points(c, c->d_samples, count, c->d_Y, nullptr, st);
+    if (s != MLQMC_OK) return s;
+    A.usol = d_usol;
+    s = launch_small(c, A, count, st);
+    if (s != MLQMC_OK) return s;
+    A.usol = nullptr;
+    for (int t = c->t_small + 1; t <= Lmax && Bt[t] > 0; ++t) {
+        s = is_mixed(p) ? synth_batched<float>(c, A, t, Bt[t], st) : synth_batched<double>(c, A, t, Bt[t], st);
+        if (s != MLQMC_OK) return s;
+    }
+    s = is_mixed(p) ? large_stages<float, true>(c, A, Bt, Lmax, d_usol, st)
+                    : large_stages<double, false>(c, A, Bt, Lmax, d_usol, st);
+    if (s != MLQMC_OK) return s;
+    if (d_sums) {
+        Timed tm(c, kProfReduce, st);
+        k_sums<<<p.n_levels * p.n_shifts, 256, 0, st>>>(c->d_samples, count, c->d_F, p.n_levels, p.n_shifts, p.reuse,
+                                                        d_sums);
+    }
+    if (d_Fout) {
+        Timed tm(c, kProfReduce, st);
+        k_fout<<<grid_for(c, static_cast<int64_t>(count) * p.n_levels), 256, 0, st>>>(c->d_samples, count, c->d_F,
+                                                                                      p.n_levels, d_Fout);
+    }
+    return last_error();
+}
+
+// Upload `count` descriptors (rank order) from host memory.
+mlqmc_status stage_samples(mlqmc_ctx* c, const SampleDesc* src, int count, cudaStream_t st)
+{
+    if (!ok(cudaEventSynchronize(c->staged))) return MLQMC_ERR_CUDA;
+    std::memcpy(c->h_samples, src, static_cast<size_t>(count) * sizeof(SampleDesc));
+    if (count > 0 &&
+        (!ok(cudaMemcpyAsync(c->d_samples, c->h_samples, count * sizeof(SampleDesc), cudaMemcpyHostToDevice, st)) ||
+         !ok(cudaEventRecord(c->staged, st))))
+        return MLQMC_ERR_CUDA;
     return MLQMC_OK;
 }
 
@@ -776,12 +918,15 @@ void free_ctx(mlqmc_ctx* c)
     cudaFree(c->d_grp_sqrt);
     cudaFree(c->d_z);
     cudaFree(c->d_samples);
-    cudaFree(c->d_canon);
     cudaFree(c->d_Y);
-    cudaFree(c->d_dF);
-    cudaFree(c->d_work);
+    cudaFree(c->d_F);
+    cudaFree(c->d_chol);
+    cudaFree(c->d_norms);
+    cudaFree(c->d_active);
+    cudaFree(c->d_count);
     cudaFree(c->d_status);
     cudaFree(c->d_queue);
+    for (auto& P : c->pools) cudaFree(P.mem);
     if (c->staged) cudaEventDestroy(c->staged);
     for (auto& m : c->marks) {
         cudaEventDestroy(m.a);
@@ -789,7 +934,7 @@ void free_ctx(mlqmc_ctx* c)
     }
     for (auto e : c->pool) cudaEventDestroy(e);
     if (c->h_samples) cudaFreeHost(c->h_samples);
-    if (c->h_canon) cudaFreeHost(c->h_canon);
+    if (c->h_count) cudaFreeHost(c->h_count);
     delete c;
 }
 
@@ -823,6 +968,17 @@ mlqmc_status check_problem(const mlqmc_problem* p)
     return MLQMC_OK;
 }
 
+// Samples per level count of a rank-ordered range: B[t] = #{level >= t}.
+void count_levels(const SampleDesc* s, int count, int n_levels, int* Bt, int* Lmax)
+{
+    for (int t = 0; t < n_levels; ++t) Bt[t] = 0;
+    *Lmax = -1;
+    for (int q = 0; q < count; ++q) {
+        for (int t = 0; t <= s[q].level; ++t) Bt[t]++;
+        *Lmax = std::max(*Lmax, s[q].level);
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -846,6 +1002,9 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
     if (p->sampler == MLQMC_SAMPLER_LATTICE) c->z.assign(p->genvec, p->genvec + p->n_modes);
     else c->z.assign(p->n_modes, 1u);
     c->p.genvec = nullptr;
+    // levels up to 64 x 64 cells are solved per sample by one CTA
+    c->t_small = 0;
+    while (c->t_small + 1 < p->n_levels && (p->coarse_cells << (c->t_small + 1)) <= 64) ++c->t_small;
 
     // KL tables (Sec. 5): modes, 1D eigenpairs, per-level psi tables
     c->modes = mlqmc::select_modes(p->corr_len, p->sigma, p->n_modes);
@@ -867,7 +1026,6 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
     }
     gstart[Ka] = static_cast<int>(gb.size());
     std::vector<double> psi_all, tab;
-    std::vector<float> psi32;
     size_t off = 0;
     for (int t = 0; t < p->n_levels; ++t) {
         const int n = p->coarse_cells << t;
@@ -876,7 +1034,7 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
         psi_all.insert(psi_all.end(), tab.begin(), tab.end());
         off += tab.size();
     }
-    psi32.assign(psi_all.begin(), psi_all.end());
+    std::vector<float> psi32(psi_all.begin(), psi_all.end());
     bool good = dev_upload(&c->d_psi, psi_all.data(), psi_all.size()) &&
                 dev_upload(&c->d_psi32, psi32.data(), psi32.size()) &&
                 dev_upload(&c->d_grp_start, gstart.data(), gstart.size()) &&
@@ -888,14 +1046,18 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
         return MLQMC_ERR_OOM;
     }
 
-    // per-call buffers
+    // per-chunk buffers
     c->max_samples = max_samples_per_call > 0 ? max_samples_per_call : 65536;
     const size_t ms = static_cast<size_t>(c->max_samples);
-    good = ok(cudaMalloc(&c->d_samples, ms * sizeof(SampleDesc))) && ok(cudaMalloc(&c->d_canon, ms * sizeof(int2))) &&
+    const size_t N0 = static_cast<size_t>(p->coarse_cells) * p->coarse_cells;
+    c->chol_stride = align256(sizeof(double) * N0 * (p->coarse_cells + 1));
+    good = ok(cudaMalloc(&c->d_samples, ms * sizeof(SampleDesc))) &&
            ok(cudaMalloc(&c->d_Y, ms * p->n_modes * sizeof(double))) &&
-           ok(cudaMalloc(&c->d_dF, (ms + 1) * p->n_levels * sizeof(double))) &&
+           ok(cudaMalloc(&c->d_F, ms * p->n_levels * sizeof(double))) &&
+           ok(cudaMalloc(&c->d_chol, ms * c->chol_stride)) && ok(cudaMalloc(&c->d_norms, ms * sizeof(double))) &&
+           ok(cudaMalloc(&c->d_active, ms * sizeof(int))) && ok(cudaMalloc(&c->d_count, sizeof(int))) &&
            ok(cudaMallocHost(&c->h_samples, ms * sizeof(SampleDesc))) &&
-           ok(cudaMallocHost(&c->h_canon, ms * sizeof(int2))) && ok(cudaMalloc(&c->d_status, sizeof(int))) &&
+           ok(cudaMallocHost(&c->h_count, sizeof(int))) && ok(cudaMalloc(&c->d_status, sizeof(int))) &&
            ok(cudaMalloc(&c->d_queue, sizeof(int))) && ok(cudaMemset(c->d_status, 0, sizeof(int))) &&
            ok(cudaEventCreateWithFlags(&c->staged, cudaEventDisableTiming));
     if (!good) {
@@ -903,35 +1065,24 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
         return MLQMC_ERR_OOM;
     }
 
-    // FMG workspace: one slot per resident CTA, capped by a memory budget
-    c->layout = make_layout(c->p, Ka);
-    c->fmg_smem = fmg_smem_bytes(c->p);
-    void* kern = fmg_kernel(c->p);
-    if (c->fmg_smem > 48 * 1024 &&
-        !ok(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(c->fmg_smem)))) {
+    // per-sample kernel launch shape and the pool budget
+    const size_t smem = sizeof(double) * 8 * static_cast<size_t>(small_warp_doubles(p->n_modes, p->coarse_cells));
+    c->small_smem = smem;
+    void* kern = small_kernel(c->p);
+    if (smem > 48 * 1024 &&
+        !ok(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)))) {
         free_ctx(c);
         return MLQMC_ERR_CUDA;
     }
     int per_sm = 0;
-    if (!ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, c->fmg_threads, c->fmg_smem)) || per_sm < 1) {
+    if (!ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, c->fmg_threads, smem)) || per_sm < 1) {
         free_ctx(c);
         return MLQMC_ERR_CUDA;
     }
+    c->small_grid = c->sm_count * per_sm;
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
-    const size_t budget = std::min<size_t>(free_b / 2, static_cast<size_t>(48) << 30);
-    int64_t slots = static_cast<int64_t>(c->sm_count) * per_sm;
-    slots = std::min<int64_t>(slots, static_cast<int64_t>(budget / std::max<size_t>(1, c->layout.bytes)));
-    slots = std::min<int64_t>(slots, c->max_samples);
-    if (slots < 1) {
-        free_ctx(c);
-        return MLQMC_ERR_OOM;
-    }
-    c->slots = static_cast<int>(slots);
-    if (!ok(cudaMalloc(&c->d_work, static_cast<size_t>(c->slots) * c->layout.bytes))) {
-        free_ctx(c);
-        return MLQMC_ERR_OOM;
-    }
+    c->pool_budget = std::min<size_t>(free_b / 2, static_cast<size_t>(96) << 30);
     *out = c;
     return MLQMC_OK;
 }
@@ -949,7 +1100,6 @@ extern "C" mlqmc_status mlqmc_sample_levels(mlqmc_ctx* c, const mlqmc_work* work
     if (!c || n_work < 0 || (n_work > 0 && !work) || !d_sums) return MLQMC_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const mlqmc_problem& p = c->p;
-    // validate and count
     int64_t total = 0;
     for (int i = 0; i < n_work; ++i) {
         const mlqmc_work& w = work[i];
@@ -962,60 +1112,46 @@ extern "C" mlqmc_status mlqmc_sample_levels(mlqmc_ctx* c, const mlqmc_work* work
         total += (w.n_end - w.n_begin) * (w.r_end - w.r_begin);
     }
     if (total == 0) return MLQMC_OK;
-    // expand in work order, process in chunks of max_samples
-    int item = 0, rr = n_work > 0 ? work[0].r_begin : 0;
-    int64_t nn = n_work > 0 ? work[0].n_begin : 0;
-    int64_t done = 0;
-    while (done < total) {
-        const int64_t chunk = std::min<int64_t>(total - done, c->max_samples);
-        // the pinned staging buffers may still feed an earlier call's copies
-        if (!ok(cudaEventSynchronize(c->staged))) return MLQMC_ERR_CUDA;
-        std::vector<SampleDesc> buf;
-        buf.reserve(chunk);
-        for (int64_t q = 0; q < chunk; ++q) {
-            while (item < n_work && (work[item].n_end == work[item].n_begin || work[item].r_end == work[item].r_begin ||
-                                     rr >= work[item].r_end)) {
-                ++item;
-                if (item < n_work) {
-                    rr = work[item].r_begin;
-                    nn = work[item].n_begin;
-                }
+    // expand in work order, then rank by finest level (stable, descending)
+    std::vector<SampleDesc> all;
+    all.reserve(static_cast<size_t>(total));
+    for (int i = 0; i < n_work; ++i) {
+        const mlqmc_work& w = work[i];
+        for (int r = w.r_begin; r < w.r_end; ++r)
+            for (int64_t n = w.n_begin; n < w.n_end; ++n) {
+                SampleDesc d;
+                d.n = n;
+                d.gidx = static_cast<int64_t>(all.size());
+                d.r = r;
+                d.level = w.level;
+                d.canon = 0;
+                d.pad = 0;
+                all.push_back(d);
             }
-            SampleDesc d;
-            d.n = nn;
-            d.r = rr;
-            d.level = work[item].level;
-            d.canon = static_cast<int32_t>(q);
-            d.pad = 0;
-            buf.push_back(d);
-            c->h_canon[q] = make_int2(d.level, d.r);
-            if (++nn >= work[item].n_end) {
-                nn = work[item].n_begin;
-                ++rr;
-            }
+    }
+    std::stable_sort(all.begin(), all.end(), [](const SampleDesc& x, const SampleDesc& y) { return x.level > y.level; });
+    // chunks: consecutive ranks that fit max_samples and the pool budget
+    std::vector<size_t> lvl_bytes(p.n_levels);
+    for (int t = 0; t < p.n_levels; ++t) lvl_bytes[t] = level_bytes_per_sample(p, c->Ka, t);
+    size_t a = 0;
+    while (a < all.size()) {
+        size_t b = a, bytes = 0;
+        while (b < all.size() && static_cast<int64_t>(b - a) < c->max_samples) {
+            size_t add = 0;
+            for (int t = 0; t <= all[b].level; ++t) add += lvl_bytes[t];
+            if (b > a && bytes + add > c->pool_budget) break;
+            bytes += add;
+            ++b;
         }
-        // queue order: largest level first (stable), so long solves start early
-        std::stable_sort(buf.begin(), buf.end(), [](const SampleDesc& x, const SampleDesc& y) { return x.level > y.level; });
-        std::memcpy(c->h_samples, buf.data(), chunk * sizeof(SampleDesc));
-        if (!ok(cudaMemcpyAsync(c->d_samples, c->h_samples, chunk * sizeof(SampleDesc), cudaMemcpyHostToDevice, st)) ||
-            !ok(cudaMemcpyAsync(c->d_canon, c->h_canon, chunk * sizeof(int2), cudaMemcpyHostToDevice, st)) ||
-            !ok(cudaEventRecord(c->staged, st)))
-            return MLQMC_ERR_CUDA;
-        mlqmc_status s1 = launch_points(c, c->d_samples, static_cast<int>(chunk), c->d_Y, nullptr, st);
-        if (s1 != MLQMC_OK) return s1;
-        FmgArgs A = base_args(c);
-        A.samples = c->d_samples;
-        A.dF = c->d_dF;
-        A.F_out = d_F ? d_F + done * p.n_levels : nullptr;
-        s1 = launch_fmg(c, A, static_cast<int>(chunk), st);
-        if (s1 != MLQMC_OK) return s1;
-        cudaEvent_t m = mark_begin(c, st);
-        k_sums<<<p.n_levels * p.n_shifts, 256, 0, st>>>(c->d_canon, static_cast<int>(chunk), c->d_dF, p.n_levels,
-                                                        p.n_shifts, p.reuse, d_sums);
-        if (!ok(cudaGetLastError())) return MLQMC_ERR_CUDA;
-        mark_end(c, 2, m, st);
-        c->launches += 1;
-        done += chunk;
+        const int count = static_cast<int>(b - a);
+        for (int q = 0; q < count; ++q) all[a + q].canon = q;
+        int Bt[MLQMC_MAX_LEVELS], Lmax = -1;
+        count_levels(all.data() + a, count, p.n_levels, Bt, &Lmax);
+        mlqmc_status s = stage_samples(c, all.data() + a, count, st);
+        if (s != MLQMC_OK) return s;
+        s = run_chunk(c, count, Bt, Lmax, d_sums, d_F, nullptr, st);
+        if (s != MLQMC_OK) return s;
+        a = b;
     }
     return MLQMC_OK;
 }
@@ -1029,6 +1165,8 @@ extern "C" mlqmc_status mlqmc_get_device_status(mlqmc_ctx* c, void* stream)
         !ok(cudaStreamSynchronize(st)) || !ok(cudaMemsetAsync(c->d_status, 0, sizeof(int), st)) ||
         !ok(cudaStreamSynchronize(st)))
         return MLQMC_ERR_CUDA;
+    h |= c->host_status;
+    c->host_status = 0;
     if (h & kStatusNotConverged) return MLQMC_ERR_NOT_CONVERGED;
     if (h & kStatusCheck) return MLQMC_ERR_DEVICE_STATUS;
     return MLQMC_OK;
@@ -1046,6 +1184,7 @@ extern "C" mlqmc_status mlqmc_modes(const mlqmc_ctx* c, int32_t* a, int32_t* b, 
 }
 
 namespace {
+// A block of `count` samples (level, r, n_begin + i) staged in rank order.
 mlqmc_status stage_block(mlqmc_ctx* c, int32_t level, int32_t r, int64_t n_begin, int32_t count, cudaStream_t st,
                          bool check_points = true)
 {
@@ -1056,21 +1195,16 @@ mlqmc_status stage_block(mlqmc_ctx* c, int32_t level, int32_t r, int64_t n_begin
     if (check_points && p.sampler == MLQMC_SAMPLER_LATTICE && p.log2_nmax < 32 &&
         n_begin + count > (int64_t(1) << p.log2_nmax))
         return MLQMC_ERR_POINTS_EXHAUSTED;
-    if (!ok(cudaEventSynchronize(c->staged))) return MLQMC_ERR_CUDA;
+    std::vector<SampleDesc> v(count);
     for (int i = 0; i < count; ++i) {
-        SampleDesc d;
-        d.n = n_begin + i;
-        d.r = r;
-        d.level = level;
-        d.canon = i;
-        d.pad = 0;
-        c->h_samples[i] = d;
+        v[i].n = n_begin + i;
+        v[i].gidx = i;
+        v[i].r = r;
+        v[i].level = level;
+        v[i].canon = i;
+        v[i].pad = 0;
     }
-    if (count > 0 &&
-        (!ok(cudaMemcpyAsync(c->d_samples, c->h_samples, count * sizeof(SampleDesc), cudaMemcpyHostToDevice, st)) ||
-         !ok(cudaEventRecord(c->staged, st))))
-        return MLQMC_ERR_CUDA;
-    return MLQMC_OK;
+    return stage_samples(c, v.data(), count, st);
 }
 }  // namespace
 
@@ -1106,11 +1240,21 @@ extern "C" mlqmc_status mlqmc_fields(mlqmc_ctx* c, int32_t t, const double* d_y,
     if (!ok(cudaMemcpyAsync(c->d_Y, d_y, static_cast<size_t>(count) * c->p.n_modes * sizeof(double),
                             cudaMemcpyDeviceToDevice, st)))
         return MLQMC_ERR_CUDA;
+    s = ensure_pool(c, t, count);
+    if (s != MLQMC_OK) return s;
     FmgArgs A = base_args(c);
-    A.samples = c->d_samples;
-    A.k_out = d_k;
-    A.field_level = t;
-    return launch_fmg(c, A, count, st);
+    if (t <= c->t_small) {
+        A.k_out = d_k;
+        A.field_level = t;
+        return launch_small(c, A, count, st);
+    }
+    s = is_mixed(c->p) ? synth_batched<float>(c, A, t, count, st) : synth_batched<double>(c, A, t, count, st);
+    if (s != MLQMC_OK) return s;
+    const int64_t n = c->p.coarse_cells << t;
+    Timed tm(c, kProfReduce, st);
+    if (is_mixed(c->p)) kb_k_out<float><<<grid_for(c, count * n * n), 256, 0, st>>>(A, t, count, d_k);
+    else kb_k_out<double><<<grid_for(c, count * n * n), 256, 0, st>>>(A, t, count, d_k);
+    return last_error();
 }
 
 extern "C" mlqmc_status mlqmc_sample_solution(mlqmc_ctx* c, int32_t level, int32_t r, int64_t n, double* d_u,
@@ -1120,17 +1264,11 @@ extern "C" mlqmc_status mlqmc_sample_solution(mlqmc_ctx* c, int32_t level, int32
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     mlqmc_status s = stage_block(c, level, r, n, 1, st);
     if (s != MLQMC_OK) return s;
-    s = launch_points(c, c->d_samples, 1, c->d_Y, nullptr, st);
+    int Bt[MLQMC_MAX_LEVELS];
+    for (int t = 0; t < c->p.n_levels; ++t) Bt[t] = t <= level ? 1 : 0;
+    s = run_chunk(c, 1, Bt, level, nullptr, nullptr, d_u, st);
     if (s != MLQMC_OK) return s;
-    FmgArgs A = base_args(c);
-    A.samples = c->d_samples;
-    A.dF = c->d_dF;
-    A.usol = d_u;
-    // F_0..F_level land in the first row of a scratch block, then copied out
-    A.F_out = c->d_dF + c->p.n_levels;
-    s = launch_fmg(c, A, 1, st);
-    if (s != MLQMC_OK) return s;
-    if (!ok(cudaMemcpyAsync(d_F, c->d_dF + c->p.n_levels, (level + 1) * sizeof(double), cudaMemcpyDeviceToDevice, st)))
+    if (!ok(cudaMemcpyAsync(d_F, c->d_F, (level + 1) * sizeof(double), cudaMemcpyDeviceToDevice, st)))
         return MLQMC_ERR_CUDA;
     return MLQMC_OK;
 }
@@ -1145,7 +1283,7 @@ extern "C" mlqmc_status mlqmc_profile(mlqmc_ctx* c, int32_t enable)
     }
     c->marks.clear();
     c->profiling = enable != 0;
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < kProfKinds; ++i) {
         c->prof_ms[i] = 0.0;
         c->prof_n[i] = 0;
     }
@@ -1165,7 +1303,7 @@ extern "C" mlqmc_status mlqmc_profile_read(mlqmc_ctx* c, double* out_ms, int64_t
         c->pool.push_back(m.b);
     }
     c->marks.clear();
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < kProfKinds; ++i) {
         out_ms[i] = c->prof_ms[i];
         out_n[i] = c->prof_n[i];
     }
@@ -1188,21 +1326,14 @@ __device__ void noalloc_faces(const Lv<double>& L)
     const int n = L.n;
     for (int idx = threadIdx.x; idx < n * (n + 1); idx += blockDim.x) {
         const int i2 = idx / (n + 1);
-        const int f = idx - i2 * (n + 1);
-        const double* kr = L.k + i2 * n;
-        L.kx[idx] = (f == 0) ? 2.0 * kr[0] : (f == n) ? 2.0 * kr[n - 1] : hmean(kr[f - 1], kr[f]);
+        L.kx[idx] = face_x(L.k, n, i2, idx - i2 * (n + 1));
         const int g = idx / n;
-        const int i1 = idx - g * n;
-        L.ky[idx] = (g == 0) ? 2.0 * L.k[i1]
-                  : (g == n) ? 2.0 * L.k[(n - 1) * n + i1]
-                             : hmean(L.k[(g - 1) * n + i1], L.k[g * n + i1]);
+        L.ky[idx] = face_y(L.k, n, g, idx - g * n);
     }
     __syncthreads();
     for (int p = threadIdx.x; p < n * n; p += blockDim.x) {
         const int i2 = p / n;
-        const int i1 = p - i2 * n;
-        L.idiag[p] = 1.0 / (L.kx[i2 * (n + 1) + i1] + L.kx[i2 * (n + 1) + i1 + 1] + L.ky[i2 * n + i1] +
-                            L.ky[(i2 + 1) * n + i1]);
+        L.idiag[p] = inv_diag(L.kx, L.ky, n, p - i2 * n, i2);
     }
     __syncthreads();
 }
@@ -1217,28 +1348,29 @@ __global__ void __launch_bounds__(256) k_fmg_noalloc(FmgArgs A, const double* __
     double* tmp = Lb + N0 * (A.n0 + 1);
     double* red = tmp + N0;
     double* Fv = red + 40;
-    unsigned char* slot = A.work + static_cast<size_t>(blockIdx.x) * A.slot_bytes;
+    const int slot = blockIdx.x;
     const int Lf = A.n_levels - 1;
     for (int q = blockIdx.x; q < count; q += gridDim.x) {
         const double* ks = k_in + static_cast<size_t>(q) * k_stride;
         for (int t = 0; t <= Lf; ++t) {
-            const Lv<double> L = level_view<double>(A, slot, t);
+            const Lv<double> L = view<double>(A, t, slot);
             for (int p = threadIdx.x; p < L.n * L.n; p += blockDim.x) L.k[p] = ks[p];
             ks += static_cast<size_t>(L.n) * L.n;
             __syncthreads();
             noalloc_faces(L);
         }
-        const Lv<double> L0 = level_view<double>(A, slot, 0);
-        chol_factor(Lb, A.n0, L0.kx, L0.ky);
-        chol_solve<double, double>(Lb, A.n0, nullptr, L0.u, tmp);
-        const double F0 = qoi(L0.u, A.n0, A.qoi, red);
+        const BlockTeam tm;
+        const Lv<double> L0 = view<double>(A, 0, slot);
+        chol_factor(tm, Lb, A.n0, L0.kx, L0.ky);
+        chol_solve<double, double>(tm, Lb, A.n0, nullptr, L0.u, tmp);
+        const double F0 = qoi(tm, L0.u, A.n0, A.qoi, red);
         if (threadIdx.x == 0) Fv[0] = F0;
         for (int t = 1; t <= Lf; ++t) {
-            const Lv<double> L = level_view<double>(A, slot, t);
-            const Lv<double> Lc = level_view<double>(A, slot, t - 1);
-            prolong<double, double, false>(Lc.u, Lc.n, L.u);
-            for (int m = 0; m < A.mu0; ++m) vcycle<double>(A, slot, t, nullptr, Lb, tmp);
-            const double Ft = qoi(L.u, L.n, A.qoi, red);
+            const Lv<double> L = view<double>(A, t, slot);
+            const Lv<double> Lc = view<double>(A, t - 1, slot);
+            prolong<double, double, false>(tm, Lc.u, Lc.n, L.u);
+            for (int m = 0; m < A.mu0; ++m) vcycle<double>(tm, A, slot, t, nullptr, Lb, tmp);
+            const double Ft = qoi(tm, L.u, L.n, A.qoi, red);
             if (threadIdx.x == 0) Fv[t] = Ft;
         }
         __syncthreads();
@@ -1262,15 +1394,25 @@ extern "C" mlqmc_status mlqmc_fmg_fields_noalloc(int32_t coarse_cells, int32_t n
         nu1 < 0 || nu2 < 0 || mu0 > 64 || nu1 > 64 || nu2 > 64 ||
         (qoi_kind != MLQMC_QOI_CENTER && qoi_kind != MLQMC_QOI_MEAN))
         return MLQMC_ERR_INVALID_ARG;
-    if (coarse_cells > 16 || n_levels > 7 || (static_cast<int64_t>(coarse_cells) << (n_levels - 1)) > MLQMC_NOALLOC_MAX_CELLS)
+    if (coarse_cells > 16 || n_levels > 7 ||
+        (static_cast<int64_t>(coarse_cells) << (n_levels - 1)) > MLQMC_NOALLOC_MAX_CELLS)
         return MLQMC_ERR_SCRATCH_LIMIT;
+    // slot layout: the levels' arrays one after another
     mlqmc_problem p{};
-    p.n_levels = n_levels;
     p.coarse_cells = coarse_cells;
-    p.n_modes = 1;
     p.precision = MLQMC_FP64;
-    const SlotLayout lay = make_layout(p, 0);
-    if (lay.bytes > static_cast<size_t>(MLQMC_NOALLOC_SLOT_BYTES)) return MLQMC_ERR_SCRATCH_LIMIT;
+    size_t offs[MLQMC_MAX_LEVELS][kPoolArrs];
+    size_t off = 0;
+    for (int t = 0; t < n_levels; ++t) {
+        size_t st[kPoolArrs];
+        level_strides(p, 0, t, st);
+        st[kG] = 0;
+        for (int a = 0; a < kPoolArrs; ++a) {
+            offs[t][a] = off;
+            off += st[a];
+        }
+    }
+    if (off > static_cast<size_t>(MLQMC_NOALLOC_SLOT_BYTES)) return MLQMC_ERR_SCRATCH_LIMIT;
     if (count == 0) return MLQMC_OK;
     int dev = 0;
     if (!ok(cudaGetDevice(&dev)) || dev < 0 || dev >= kMaxDevices) return MLQMC_ERR_CUDA;
@@ -1288,15 +1430,22 @@ extern "C" mlqmc_status mlqmc_fmg_fields_noalloc(int32_t coarse_cells, int32_t n
     std::memset(&A, 0, sizeof(A));
     A.n0 = coarse_cells;
     A.n_levels = n_levels;
+    A.t_small = n_levels - 1;
     A.qoi = qoi_kind;
     A.mu0 = mu0;
     A.nu1 = nu1;
     A.nu2 = nu2;
-    A.work = scratch;
-    A.slot_bytes = MLQMC_NOALLOC_SLOT_BYTES;
-    for (int t = 0; t < n_levels; ++t) A.lv[t] = lay.lv[t];
+    for (int t = 0; t < n_levels; ++t) {
+        LevelDesc& d = A.lv[t];
+        d.n = coarse_cells << t;
+        ArrDesc* arr[kPoolArrs] = {&d.u, &d.bc, &d.kx, &d.ky, &d.idiag, &d.k, &d.G, &d.u64};
+        for (int a = 0; a < kPoolArrs; ++a) {
+            arr[a]->base = scratch + offs[t][a];
+            arr[a]->stride = MLQMC_NOALLOC_SLOT_BYTES;
+        }
+    }
     size_t k_stride = 0;
-    for (int t = 0; t < n_levels; ++t) k_stride += static_cast<size_t>(lay.lv[t].n) * lay.lv[t].n;
+    for (int t = 0; t < n_levels; ++t) k_stride += static_cast<size_t>(A.lv[t].n) * A.lv[t].n;
     const size_t N0 = static_cast<size_t>(coarse_cells) * coarse_cells;
     const size_t smem = sizeof(double) * (N0 * (coarse_cells + 1) + N0 + 40 + 16);
     const int grid = std::min<int>(count, MLQMC_NOALLOC_SLOTS);

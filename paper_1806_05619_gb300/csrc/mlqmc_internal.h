@@ -41,23 +41,34 @@ mlqmc_status run_estimate(mlqmc_ctx* c, double eps, const mlqmc_run_opts* o, mlq
 // ---- device-side sample descriptor ---------------------------------------
 struct SampleDesc {
     int64_t n;      // lattice / MC index
+    int64_t gidx;   // position in work order across the whole call (output index)
     int32_t r;      // shift
     int32_t level;  // finest FMG level of this sample
-    int32_t canon;  // position in work order (output index)
+    int32_t canon;  // position inside its chunk (index of its normals)
     int32_t pad;
 };
 
-// Per-level offsets inside one workspace slot (bytes from the slot base).
-struct LevelOffsets {
-    int n;
-    size_t u, bc, kx, ky, idiag, k, G;  // working precision arrays
-    size_t u64, kx64, ky64;             // FP64 arrays of the mixed forms
+// Kinds of kernels for the optional per-kind event timing.
+enum ProfKind {
+    kProfPoints = 0,   // normals
+    kProfSmall = 1,    // per-sample solver of the small levels
+    kProfSynth = 2,    // batched KL field, faces, inverse diagonal
+    kProfSmooth = 3,   // batched red-black sweeps
+    kProfTransfer = 4, // batched residual/restriction, prolongation, FP64 refinement updates
+    kProfSmallV = 5,   // per-sample V-cycle below the large levels
+    kProfReduce = 6,   // QoI, norms, reuse sums, outputs
+    kProfKinds = 8
 };
 
-struct SlotLayout {
-    int n_levels = 0;
-    LevelOffsets lv[MLQMC_MAX_LEVELS];
-    size_t bytes = 0;
+// Pool of per-sample arrays of one level: array a of sample i lives at
+// mem + off[a] + i * stride[a].
+enum PoolArr { kU = 0, kBc, kKx, kKy, kIdiag, kK, kG, kU64, kPoolArrs };
+
+struct LevelPool {
+    unsigned char* mem = nullptr;
+    int64_t cap = 0;
+    size_t off[kPoolArrs] = {};
+    size_t stride[kPoolArrs] = {};
 };
 
 struct mlqmc_ctx {
@@ -67,7 +78,8 @@ struct mlqmc_ctx {
     std::vector<uint32_t> z;
     mlqmc::Modes modes;
     mlqmc::Eig1D eig;
-    int Ka = 0;  // 1 + max a over the kept modes
+    int Ka = 0;       // 1 + max a over the kept modes
+    int t_small = 0;  // levels <= t_small are solved per sample by one CTA
 
     // device tables
     double* d_psi = nullptr;  // per level: K1 x n_t doubles
@@ -79,22 +91,26 @@ struct mlqmc_ctx {
     double* d_grp_sqrt = nullptr;
     uint32_t* d_z = nullptr;
 
-    // per-call buffers
+    // per-chunk buffers (max_samples entries)
     int64_t max_samples = 0;
-    SampleDesc* d_samples = nullptr;  // queue order (largest level first)
-    int2* d_canon = nullptr;          // (level, r) in work order
-    double* d_Y = nullptr;            // max_samples x s normals
-    double* d_dF = nullptr;           // max_samples x n_levels
+    SampleDesc* d_samples = nullptr;  // rank order (finest level descending)
+    double* d_Y = nullptr;            // normals, s per sample
+    double* d_F = nullptr;            // F_t per sample, n_levels each
+    double* d_chol = nullptr;         // banded level-0 factor per sample
+    double* d_norms = nullptr;
+    int* d_active = nullptr;
+    int* d_count = nullptr;
     SampleDesc* h_samples = nullptr;  // pinned staging
-    int2* h_canon = nullptr;
-    cudaEvent_t staged = nullptr;     // recorded after the last copy out of the staging buffers
+    int* h_count = nullptr;           // pinned
+    cudaEvent_t staged = nullptr;     // recorded after the last copy out of the staging buffer
+    size_t chol_stride = 0;
 
-    // FMG workspace: `slots` slots of `layout.bytes`
-    unsigned char* d_work = nullptr;
-    int slots = 0;
+    // level pools, grown on demand; chunks are cut to fit pool_budget bytes
+    LevelPool pools[MLQMC_MAX_LEVELS];
+    size_t pool_budget = 0;
+    int small_grid = 0;   // CTAs of the per-sample kernels
     int fmg_threads = 256;
-    size_t fmg_smem = 0;
-    SlotLayout layout;
+    size_t small_smem = 0;
 
     // optional per-kernel event timing
     bool profiling = false;
@@ -102,12 +118,13 @@ struct mlqmc_ctx {
         int kind;
         cudaEvent_t a, b;
     };
-    std::vector<Mark> marks;       // recorded, not yet read
-    std::vector<cudaEvent_t> pool; // free events
-    double prof_ms[3] = {0, 0, 0};
-    int64_t prof_n[3] = {0, 0, 0};
+    std::vector<Mark> marks;        // recorded, not yet read
+    std::vector<cudaEvent_t> pool;  // free events
+    double prof_ms[kProfKinds] = {};
+    int64_t prof_n[kProfKinds] = {};
 
     int* d_status = nullptr;  // deferred device status bits
+    int host_status = 0;      // deferred status found on the host (converged-form loops)
     int* d_queue = nullptr;   // work-queue counter
     int64_t launches = 0;
 };
