@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed_tf32"],
+                    help="form of the main measurement (the other form is reported under 'mixed')")
     ap.add_argument("--counts-div", type=int, default=1,
                     help="divide the per-level counts (small cases for profiler captures only)")
     return ap.parse_args()
@@ -242,6 +244,7 @@ def run_ours(args):
         raise RuntimeError("libmlqmc.so is not built; run __graft_entry__.build()")
 
     cfg = workload_config(rank, args.counts_div)
+    cfg["precision"] = args.precision
     work = work_list(cfg)
     ns = n_samples(work)
     genvec, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
@@ -324,7 +327,7 @@ def run_ours(args):
     roof = {"kernel_kind": dom, "share_of_step": dom_ms / max(1e-9, step_dev_ms), "launches": dom_n,
             "ms_per_step": dom_ms / args.steps, "traffic": None}
     if dom == "smooth":
-        m = smooth_model(cfg, work, 8)
+        m = smooth_model(cfg, work, 8 if cfg["precision"] == "fp64" else 4)
         t_s = dom_ms * 1e-3 / args.steps
         t_hbm, t_alu = m["bytes"] / (HBM_GBS * 1e9), m["flops"] / (FP64_TFLOPS * 1e12)
         if t_hbm >= t_alu:
@@ -344,7 +347,7 @@ def run_ours(args):
     roof["frac"] = roof["achieved"] / roof["peak"]
 
     mixed = None
-    if not args.no_mixed:
+    if not args.no_mixed and cfg["precision"] == "fp64":
         mixed = run_mixed_same_workload(args, cfg, work, genvec, dev, stream, flush, M)
 
     cpu = None
@@ -359,7 +362,9 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if cfg["precision"] == "fp64" else "f32 V-cycles in f64 refinement",
+            "data": "synthetic",
             "config": {"workload": "MLQMC with reuse, FP64, 6 levels 8x8..256x256 cells, s=100 KL modes "
                                    "(sep. exponential, sigma=1, lambda=0.3), lattice 2^10 points halving per "
                                    "level, R=16 shifts, N_l=1024,512,256,128,64,32 per shift, FMG mu0=2 V(2,2) "
@@ -402,6 +407,7 @@ def run_mixed_same_workload(args, cfg64, work, genvec, dev, stream, flush, M):
         step()
     ctx.check_device(stream)
     torch.cuda.synchronize(dev)
+    ctx.profile(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     for i in range(args.steps):
         flush.zero_()
@@ -409,10 +415,13 @@ def run_mixed_same_workload(args, cfg64, work, genvec, dev, stream, flush, M):
         step()
         ev[i][1].record(stream)
     torch.cuda.synchronize(dev)
+    prof = ctx.profile_read()
+    ctx.profile(False)
     ctx.check_device(stream)
     tot = sum(a.elapsed_time(b) for a, b in ev)
     return {"value": ns * args.steps / (tot * 1e-3), "unit": UNIT, "ms_per_step": tot / args.steps,
-            "dtype": "f32 V-cycles in f64 refinement, f32 field"}
+            "dtype": "f32 V-cycles in f64 refinement, f32 field",
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]}}
 
 
 def main():

@@ -279,10 +279,10 @@ mlqmc_status mlqmc_profile(mlqmc_ctx* c, int32_t enable);
 
 /*
  * Totals since the last mlqmc_profile call, per kernel kind (8 entries):
- * 0 normals, 1 per-sample solver of the small levels (<= 64x64), 2 batched KL
- * field and faces, 3 batched red-black sweeps, 4 batched residual/restriction,
- * prolongation and FP64 refinement updates, 5 per-sample V-cycle below the
- * batched levels, 6 QoI, norms, reuse sums and outputs, 7 unused.
+ * 0 normals, 1 level-0 banded factor and exact solve (per sample), 2 KL field
+ * and faces, 3 red-black sweeps, 4 residual/restriction, prolongation and
+ * FP64 refinement updates, 5 coarse solves of the V-cycles, 6 QoI, norms,
+ * reuse sums and outputs, 7 unused.
  * out_ms: device milliseconds (host, 8 doubles); out_n: launches (host, 8
  * int64). Waits for the recorded events.
  */

@@ -47,7 +47,6 @@ struct FmgArgs {
     int s;
     int n0;
     int n_levels;
-    int t_small;  // levels <= t_small are solved by one CTA per sample
     int qoi;
     int mu0, nu1, nu2;
     double rtol;
@@ -60,11 +59,10 @@ struct FmgArgs {
     const int* grp_m;
     const double* grp_sqrt;
     LevelDesc lv[MLQMC_MAX_LEVELS];
-    ArrDesc chol;      // banded factor of level 0, per sample
+    ArrDesc chol;      // banded level-0 factor (FP64): entry q of sample i at base[q * stride + i] (elements)
+    void* chol32;      // FP32 copy of the factor, same layout (mixed forms)
     double* F;         // F_t per rank, n_levels each
     double* usol;      // single-sample solutions (concatenated levels) or null
-    double* k_out;     // field-only mode: k of field_level per sample (by canon) or null
-    int field_level;
     int* queue;
     int* status;
     const int* active;  // per rank; null: all samples active
@@ -352,20 +350,21 @@ __device__ void chol_factor(const TM& tm, double* Lb, int n0, const F* kx, const
     tm.sync();
 }
 
-// Solve (h0^2 A_0) x = h0^2 b with the band factor; b == null: b = 1. Team leader.
-template <typename B, typename X, typename TM>
-__device__ void chol_solve(const TM& tm, const double* Lb, int n0, const B* b, X* x, double* tmp)
+// Solve (h0^2 A_0) x = h0^2 b with the band factor, in the factor's precision
+// F; b == null: b = 1. Team leader.
+template <typename B, typename X, typename F, typename TM>
+__device__ void chol_solve(const TM& tm, const F* Lb, int n0, const B* b, X* x, F* tmp)
 {
     if (tm.leader()) {
         const int N = n0 * n0, W = n0 + 1;
-        const double h2 = 1.0 / (static_cast<double>(n0) * n0);
+        const F h2 = F(1) / (F(n0) * F(n0));
         for (int i = 0; i < N; ++i) {
-            double v = h2 * (b ? static_cast<double>(b[i]) : 1.0);
+            F v = h2 * (b ? static_cast<F>(b[i]) : F(1));
             for (int q = 1; q <= n0 && q <= i; ++q) v -= Lb[i * W + q] * tmp[i - q];
             tmp[i] = v / Lb[i * W];
         }
         for (int i = N - 1; i >= 0; --i) {
-            double v = tmp[i];
+            F v = tmp[i];
             for (int q = 1; q <= n0 && i + q < N; ++q) v -= Lb[(i + q) * W + q] * tmp[i + q];
             tmp[i] = v / Lb[i * W];
         }
@@ -383,10 +382,10 @@ __device__ void zero(const TM& tm, T* a, int cnt)
 
 // V-cycle (Sec. 4 correction scheme, recursively) of sample i on levels
 // t_top..0. top_b == null: right-hand side 1 on the top level; the top
-// iterate is used as given, lower levels start from zero.
+// iterate is used as given, lower levels start from zero. The exact level-0
+// solve uses the band factor Lb in the working precision T.
 template <typename T, typename TM>
-__device__ void vcycle(const TM& tm, const FmgArgs& A, int i, int t_top, const T* top_b, const double* Lb,
-                       double* tmp)
+__device__ void vcycle(const TM& tm, const FmgArgs& A, int i, int t_top, const T* top_b, const T* Lb, T* tmp)
 {
     for (int t = t_top; t >= 1; --t) {
         const Lv<T> F = view<T>(A, t, i);

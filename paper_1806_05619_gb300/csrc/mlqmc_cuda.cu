@@ -4,15 +4,14 @@
 // of samples. Samples are ranked by finest level, descending; every level t
 // keeps a pool with one block of arrays per sample whose FMG reaches t
 // (B_t samples, B_t non-increasing in t), so sample i uses block i at every
-// level. Two kinds of kernels share these pools:
-//  - k_small: one CTA per sample for the small levels (n_t <= 64): KL field,
-//    faces, banded Cholesky of level 0 and the FMG stages up to 64x64 (Sec. 4,
-//    Fig. FMG). Working sets are L2 resident.
-//  - kb_*: level-synchronous kernels over all B_t samples of a large level
-//    (KL field, faces, red-black sweeps, residual/restriction, prolongation,
-//    FP64 refinement steps, QoI). A V-cycle on a large level runs kb_* down to
-//    the first small level, k_small_vcycle for the levels below, and kb_* up.
-// Then k_sums forms the reuse sums (eq. Upsilon-reuse) in a fixed order.
+// level. All grid work is level-synchronous: each kb_* kernel is one flat grid
+// over the B_t samples of one level (KL field, faces, red-black sweeps,
+// residual/restriction, prolongation, FP64 refinement steps, QoI), so samples
+// of uneven finest levels share every launch of the levels they have in
+// common (Sec. 4 FMG, Fig. FMG). Only level 0 is per sample: kb_level0 factors
+// the banded level-0 matrix (one warp per sample) and kb_coarse does the
+// coarse solves of the V-cycles (one thread per sample). k_sums then forms the
+// reuse sums (eq. Upsilon-reuse) in a fixed order.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -21,6 +20,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "fmg_device.cuh"
@@ -88,149 +88,125 @@ __global__ void k_points(const SampleDesc* __restrict__ smp, int count, int s, i
     }
 }
 
+#define GRID_STRIDE(idx, total)                                                                         \
+    for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < (total); \
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x)
+
 // ---------------------------------------------------------------------------
-// Per-sample solver of the small levels: one warp per sample, 8 per CTA.
-// Shared memory per warp: cy[s] | Lb[n0^2 (n0+1)] | tmp[n0^2] | F[16].
+// Level 0, one thread per sample. GB300 issues FP64 at a few operations per
+// clock per SM, charged per warp instruction whatever the active lanes, so
+// the per-sample band work runs with every lane busy on its own sample.
+// Band factor of h0^2 A_0 (bandwidth n0): entry (r, d) = L(r, r-d) of sample i
+// at fac[(r*(n0+1) + d) * stride + i] (coalesced across samples); the
+// diagonal d = 0 holds 1/L(r, r).
 // ---------------------------------------------------------------------------
-__host__ __device__ __forceinline__ int small_warp_doubles(int s, int n0)
+template <typename T>
+__device__ __forceinline__ T band_a(const T* kx, const T* ky, int n0, int r, int l)
 {
-    const int N0 = n0 * n0;
-    return ((s + 1) & ~1) + N0 * (n0 + 1) + N0 + 16;
+    const int r1 = r % n0, r2 = r / n0;
+    if (l == 1 && r1 > 0) return -kx[r2 * (n0 + 1) + r1];
+    if (l == n0) return -ky[r2 * n0 + r1];
+    return T(0);
 }
 
+// Factor, exact FP64 solve with f = 1, F_0; the mixed forms also keep an FP32
+// copy of the factor for the coarse solves of their FP32 V-cycles.
 template <typename T, bool MX>
-__global__ void __launch_bounds__(256, 3) k_small(FmgArgs A)
+__global__ void kb_level0(FmgArgs A, int B)
 {
-    extern __shared__ double smem[];
-    const WarpTeam tm;
-    const int N0 = A.n0 * A.n0;
-    double* cy = smem + (threadIdx.x >> 5) * small_warp_doubles(A.s, A.n0);
-    double* Lb = cy + ((A.s + 1) & ~1);
-    double* tmp = Lb + N0 * (A.n0 + 1);
-    double* Fv = tmp + N0;
-    double* red = nullptr;  // warp sums need no scratch
-    const int lane = tm.rank();
-
-    for (;;) {
-        int i = 0;
-        if (tm.leader()) i = atomicAdd(A.queue, 1);
-        i = __shfl_sync(0xffffffffu, i, 0);
-        if (i >= A.n_samples) break;
-        const SampleDesc d = A.samples[i];
-        // sqrt(theta_m) y_m in grouped-by-a order
-        for (int g = lane; g < A.s; g += 32)
-            cy[g] = A.grp_sqrt[g] * A.Y[static_cast<size_t>(d.canon) * A.s + A.grp_m[g]];
-        tm.sync();
-
-        if (A.k_out) {  // field-only mode (introspection)
-            const Lv<T> L = view<T>(A, A.field_level, i);
-            synth_level<T>(tm, A, L, A.field_level, cy);
-            copy_out(tm, L.k, A.k_out + static_cast<size_t>(d.canon) * L.n * L.n, L.n * L.n);
-            continue;
-        }
-
-        const int Ls = d.level < A.t_small ? d.level : A.t_small;
-        for (int t = 0; t <= Ls; ++t) synth_level<T>(tm, A, view<T>(A, t, i), t, cy);
-
+    const int n0 = A.n0, N = n0 * n0, W = n0 + 1;
+    const size_t cs = A.chol.stride;
+    double* fac = reinterpret_cast<double*>(A.chol.base);
+    GRID_STRIDE(ii, B)
+    {
+        const int i = static_cast<int>(ii);
         const Lv<T> L0 = view<T>(A, 0, i);
-        chol_factor(tm, Lb, A.n0, L0.kx, L0.ky);
-        if (d.level > A.t_small) {  // kept for the V-cycles of the large levels
-            double* g = at<double>(A.chol, i);
-            for (int q = lane; q < N0 * (A.n0 + 1); q += 32) g[q] = Lb[q];
-        }
-        size_t uoff = N0;
-        if constexpr (MX) {
-            chol_solve<T, double>(tm, Lb, A.n0, nullptr, L0.u64, tmp);
-            const double F0 = qoi(tm, L0.u64, A.n0, A.qoi, red);
-            if (tm.leader()) Fv[0] = F0;
-            if (A.usol) copy_out(tm, L0.u64, A.usol, N0);
-        } else {
-            chol_solve<T, T>(tm, Lb, A.n0, nullptr, L0.u, tmp);
-            const double F0 = qoi(tm, L0.u, A.n0, A.qoi, red);
-            if (tm.leader()) Fv[0] = F0;
-            if (A.usol) copy_out(tm, L0.u, A.usol, N0);
-        }
-        for (int t = 1; t <= Ls; ++t) {
-            const Lv<T> L = view<T>(A, t, i);
-            const Lv<T> Lc = view<T>(A, t - 1, i);
-            const int n = L.n;
-            double Ft;
-            if constexpr (MX) {
-                prolong<double, double, false>(tm, Lc.u64, Lc.n, L.u64);
-                for (int m = 0; m < A.mu0; ++m) {
-                    // one refinement step per FMG cycle: r = 1 - A u64 in FP64, FP32 V-cycle on A e = r
-                    resid64_to_rhs(tm, L, red);
-                    zero(tm, L.u, n * n);
-                    vcycle<T>(tm, A, i, t, L.bc, Lb, tmp);
-                    for (int p = lane; p < n * n; p += 32) L.u64[p] += static_cast<double>(L.u[p]);
-                    tm.sync();
-                }
-                if (A.rtol > 0.0) {
-                    for (int it = 0;; ++it) {
-                        const double rn = resid64_to_rhs(tm, L, red);
-                        if (rn <= A.rtol * n) break;
-                        if (it >= A.max_iter) {
-                            if (tm.leader()) atomicOr(A.status, kStatusNotConverged);
-                            break;
-                        }
-                        zero(tm, L.u, n * n);
-                        vcycle<T>(tm, A, i, t, L.bc, Lb, tmp);
-                        for (int p = lane; p < n * n; p += 32) L.u64[p] += static_cast<double>(L.u[p]);
-                        tm.sync();
-                    }
-                }
-                Ft = qoi(tm, L.u64, n, A.qoi, red);
-                if (A.usol) copy_out(tm, L.u64, A.usol + uoff, n * n);
-            } else {
-                prolong<T, T, false>(tm, Lc.u, Lc.n, L.u);
-                for (int m = 0; m < A.mu0; ++m) vcycle<T>(tm, A, i, t, nullptr, Lb, tmp);
-                if (A.rtol > 0.0) {
-                    for (int it = 0;; ++it) {
-                        const double rn = resid_norm_ones(tm, L, red);
-                        if (rn <= A.rtol * n) break;
-                        if (it >= A.max_iter) {
-                            if (tm.leader()) atomicOr(A.status, kStatusNotConverged);
-                            break;
-                        }
-                        vcycle<T>(tm, A, i, t, nullptr, Lb, tmp);
-                    }
-                }
-                Ft = qoi(tm, L.u, n, A.qoi, red);
-                if (A.usol) copy_out(tm, L.u, A.usol + uoff, n * n);
+        for (int j = 0; j < N; ++j) {
+            const int j1 = j % n0, j2 = j / n0;
+            double d = static_cast<double>(L0.kx[j2 * (n0 + 1) + j1]) + static_cast<double>(L0.kx[j2 * (n0 + 1) + j1 + 1]) +
+                       static_cast<double>(L0.ky[j2 * n0 + j1]) + static_cast<double>(L0.ky[(j2 + 1) * n0 + j1]);
+            for (int q = 1; q <= n0 && q <= j; ++q) {
+                const double l = fac[static_cast<size_t>(j * W + q) * cs + i];
+                d -= l * l;
             }
-            if (tm.leader()) Fv[t] = Ft;
-            uoff += static_cast<size_t>(n) * n;
+            const double rl = 1.0 / sqrt(d);
+            fac[static_cast<size_t>(j * W) * cs + i] = rl;
+            for (int l = 1; l <= n0 && j + l < N; ++l) {
+                const int r = j + l;
+                double a = static_cast<double>(band_a(L0.kx, L0.ky, n0, r, l));
+                for (int tt = (r - n0 > 0 ? r - n0 : 0); tt < j; ++tt)
+                    a -= fac[static_cast<size_t>(r * W + (r - tt)) * cs + i] * fac[static_cast<size_t>(j * W + (j - tt)) * cs + i];
+                fac[static_cast<size_t>(r * W + l) * cs + i] = a * rl;
+            }
         }
-        tm.sync();
-        if (lane <= Ls) A.F[static_cast<size_t>(i) * A.n_levels + lane] = Fv[lane];
-        tm.sync();
+        // exact solution of level 0 with f = 1 (the first node of Fig. FMG)
+        double* x = MX ? L0.u64 : reinterpret_cast<double*>(L0.u);
+        const double h2 = 1.0 / (static_cast<double>(n0) * n0);
+        for (int r = 0; r < N; ++r) {
+            double v = h2;
+            for (int q = 1; q <= n0 && q <= r; ++q) v -= fac[static_cast<size_t>(r * W + q) * cs + i] * x[r - q];
+            x[r] = v * fac[static_cast<size_t>(r * W) * cs + i];
+        }
+        for (int r = N - 1; r >= 0; --r) {
+            double v = x[r];
+            for (int q = 1; q <= n0 && r + q < N; ++q) v -= fac[static_cast<size_t>((r + q) * W + q) * cs + i] * x[r + q];
+            x[r] = v * fac[static_cast<size_t>(r * W) * cs + i];
+        }
+        double F0;
+        if (A.qoi == MLQMC_QOI_MEAN) {
+            double acc = 0.0;
+            for (int r = 0; r < N; ++r) acc += x[r];
+            F0 = acc / static_cast<double>(N);
+        } else {
+            const int m = n0 / 2;
+            F0 = 0.25 * (x[(m - 1) * n0 + (m - 1)] + x[(m - 1) * n0 + m] + x[m * n0 + (m - 1)] + x[m * n0 + m]);
+        }
+        A.F[static_cast<size_t>(i) * A.n_levels] = F0;
+        if constexpr (MX) {
+            float* f32 = reinterpret_cast<float*>(A.chol32);
+            for (int q = 0; q < N * W; ++q) f32[static_cast<size_t>(q) * cs + i] = static_cast<float>(fac[static_cast<size_t>(q) * cs + i]);
+        }
     }
 }
 
-// V-cycle on the small levels t_small..0 of samples i < B (zero start, right-hand
-// side in bc of level t_small), below a V-cycle on the large levels; one warp
-// per sample.
-template <typename T>
-__global__ void __launch_bounds__(256) k_small_vcycle(FmgArgs A, int B)
+// Coarse solve of the V-cycles, u_0 = A_0^{-1} bc_0, one thread per sample, in
+// the working precision. SM: the thread's vector lives in shared memory
+// (element r at xs[r * blockDim + tid]), else in its pool block.
+template <typename T, bool SM>
+__global__ void kb_coarse(FmgArgs A, int B)
 {
-    __shared__ double tmp_all[8][256];
-    const WarpTeam tm;
-    const int warp = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
-    for (int i = blockIdx.x * nw + warp; i < B; i += gridDim.x * nw) {
+    extern __shared__ unsigned char sraw[];
+    const int n0 = A.n0, N = n0 * n0, W = n0 + 1;
+    const T h2 = T(1) / (T(n0) * T(n0));
+    const T* fac = reinterpret_cast<const T*>(sizeof(T) == 4 ? A.chol32 : A.chol.base);
+    const size_t cs = A.chol.stride;
+    const int bd = blockDim.x;
+    for (int64_t ii = blockIdx.x * static_cast<int64_t>(bd) + threadIdx.x;; ii += static_cast<int64_t>(gridDim.x) * bd) {
+        if (ii >= B) break;
+        const int i = static_cast<int>(ii);
         if (A.active && !A.active[i]) continue;
-        const Lv<T> Ts = view<T>(A, A.t_small, i);
-        zero(tm, Ts.u, Ts.n * Ts.n);
-        vcycle<T>(tm, A, i, A.t_small, Ts.bc, at<double>(A.chol, i), tmp_all[warp]);
+        const T* b = at<T>(A.lv[0].bc, i);
+        T* xo = at<T>(A.lv[0].u, i);
+        T* xs = SM ? reinterpret_cast<T*>(sraw) + threadIdx.x : xo;
+        const int xst = SM ? bd : 1;
+        for (int r = 0; r < N; ++r) {
+            T v = h2 * b[r];
+            for (int q = 1; q <= n0 && q <= r; ++q) v -= fac[static_cast<size_t>(r * W + q) * cs + i] * xs[(r - q) * xst];
+            xs[r * xst] = v * fac[static_cast<size_t>(r * W) * cs + i];
+        }
+        for (int r = N - 1; r >= 0; --r) {
+            T v = xs[r * xst];
+            for (int q = 1; q <= n0 && r + q < N; ++q) v -= fac[static_cast<size_t>((r + q) * W + q) * cs + i] * xs[(r + q) * xst];
+            xs[r * xst] = v * fac[static_cast<size_t>(r * W) * cs + i];
+        }
+        if (SM)
+            for (int r = 0; r < N; ++r) xo[r] = xs[r * xst];
     }
 }
 
 // ---------------------------------------------------------------------------
 // Level-synchronous kernels over samples 0..B-1 of level t.
 // ---------------------------------------------------------------------------
-#define GRID_STRIDE(idx, total)                                                                         \
-    for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < (total); \
-         idx += static_cast<int64_t>(gridDim.x) * blockDim.x)
 
 __device__ __forceinline__ bool inactive(const FmgArgs& A, int i)
 {
@@ -585,7 +561,6 @@ FmgArgs base_args(mlqmc_ctx* c)
     A.s = c->p.n_modes;
     A.n0 = c->p.coarse_cells;
     A.n_levels = c->p.n_levels;
-    A.t_small = c->t_small;
     A.qoi = c->p.qoi;
     A.mu0 = c->p.mu0;
     A.nu1 = c->p.nu1;
@@ -610,7 +585,8 @@ FmgArgs base_args(mlqmc_ctx* c)
         }
     }
     A.chol.base = reinterpret_cast<unsigned char*>(c->d_chol);
-    A.chol.stride = c->chol_stride;
+    A.chol.stride = static_cast<size_t>(c->max_samples);  // interleaved: entry q of sample i at q * max_samples + i
+    A.chol32 = c->d_chol32;
     A.F = c->d_F;
     A.queue = c->d_queue;
     A.status = c->d_status;
@@ -669,27 +645,22 @@ mlqmc_status last_error()
     return ok(cudaGetLastError()) ? MLQMC_OK : MLQMC_ERR_CUDA;
 }
 
-template <typename T, bool MX>
-void* small_kernel_ptr()
+// Level-0 factor, exact solve and F_0 of samples 0..B-1 (one thread each).
+mlqmc_status launch_level0(mlqmc_ctx* c, const FmgArgs& A, int B, cudaStream_t st)
 {
-    return reinterpret_cast<void*>(&k_small<T, MX>);
-}
-
-void* small_kernel(const mlqmc_problem& p)
-{
-    return is_mixed(p) ? small_kernel_ptr<float, true>() : small_kernel_ptr<double, false>();
-}
-
-mlqmc_status launch_small(mlqmc_ctx* c, FmgArgs& A, int count, cudaStream_t st)
-{
-    A.n_samples = count;
-    if (!ok(cudaMemsetAsync(c->d_queue, 0, sizeof(int), st))) return MLQMC_ERR_CUDA;
-    const int grid = std::max(1, std::min((count + 7) / 8, c->small_grid));
-    void* args[] = {&A};
     Timed tm(c, kProfSmall, st);
-    if (!ok(cudaLaunchKernel(small_kernel(c->p), dim3(grid), dim3(c->fmg_threads), args, c->small_smem, st)))
-        return MLQMC_ERR_CUDA;
-    return MLQMC_OK;
+    if (is_mixed(c->p)) kb_level0<float, true><<<grid_for(c, B, 128), 128, 0, st>>>(A, B);
+    else kb_level0<double, false><<<grid_for(c, B, 128), 128, 0, st>>>(A, B);
+    return last_error();
+}
+
+template <typename T>
+void launch_coarse(mlqmc_ctx* c, const FmgArgs& A, int B, cudaStream_t st)
+{
+    const size_t N0 = static_cast<size_t>(c->p.coarse_cells) * c->p.coarse_cells;
+    const size_t smem = N0 * 64 * sizeof(T);
+    if (smem <= 48 * 1024) kb_coarse<T, true><<<grid_for(c, B, 64), 64, smem, st>>>(A, B);
+    else kb_coarse<T, false><<<grid_for(c, B, 64), 64, 0, st>>>(A, B);
 }
 
 mlqmc_status launch_points(mlqmc_ctx* c, const SampleDesc* d_s, int count, double* Y, uint64_t* bits, cudaStream_t st)
@@ -731,14 +702,13 @@ mlqmc_status zero_u(mlqmc_ctx* c, int t, int B, cudaStream_t st)
                                                                                                 : MLQMC_ERR_CUDA;
 }
 
-// V-cycle on level t_top (> t_small) for samples 0..B-1: batched sweeps and
-// transfers on the large levels, k_small_vcycle below them. ones: the top
-// right-hand side is 1 (FP64 form), else bc of t_top (mixed correction).
+// V-cycle on level t_top (>= 1) for samples 0..B-1: batched sweeps and
+// transfers down to level 1, the coarse solve on level 0, and back up. ones:
+// the top right-hand side is 1 (FP64 form), else bc of t_top (mixed correction).
 template <typename T>
 mlqmc_status vcycle_batched(mlqmc_ctx* c, const FmgArgs& A, int t_top, int B, bool ones, cudaStream_t st)
 {
-    const int ts = c->t_small;
-    for (int t = t_top; t > ts; --t) {
+    for (int t = t_top; t >= 1; --t) {
         const int64_t n = c->p.coarse_cells << t;
         const int top_ones = (t == t_top && ones) ? 1 : 0;
         if (t < t_top && zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
@@ -753,9 +723,9 @@ mlqmc_status vcycle_batched(mlqmc_ctx* c, const FmgArgs& A, int t_top, int B, bo
     }
     {
         Timed tm(c, kProfSmallV, st);
-        k_small_vcycle<T><<<std::max(1, std::min((B + 7) / 8, c->sm_count * 8)), 256, 0, st>>>(A, B);
+        launch_coarse<T>(c, A, B, st);
     }
-    for (int t = ts + 1; t <= t_top; ++t) {
+    for (int t = 1; t <= t_top; ++t) {
         const int64_t n = c->p.coarse_cells << t;
         const int top_ones = (t == t_top && ones) ? 1 : 0;
         {
@@ -800,8 +770,10 @@ mlqmc_status converge_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cuda
         M.active = c->d_active;
         if constexpr (MX) {
             if (zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
-            mlqmc_status s = vcycle_batched<T>(c, M, t, B, false, st);
-            if (s != MLQMC_OK) return s;
+            for (int m = 0; m < c->p.mu0; ++m) {
+                mlqmc_status s = vcycle_batched<T>(c, M, t, B, false, st);
+                if (s != MLQMC_OK) return s;
+            }
             Timed tm(c, kProfTransfer, st);
             kb_update64<<<grid_for(c, B * n * n), 256, 0, st>>>(M, t, B);
         } else {
@@ -812,13 +784,12 @@ mlqmc_status converge_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cuda
     return last_error();
 }
 
-// FMG stages above t_small for the B_t samples that reach them.
+// FMG stages 1..Lmax for the B_t samples that reach each level.
 template <typename T, bool MX>
-mlqmc_status large_stages(mlqmc_ctx* c, const FmgArgs& A, const int* Bt, int Lmax, double* d_usol, cudaStream_t st)
+mlqmc_status fmg_stages(mlqmc_ctx* c, const FmgArgs& A, const int* Bt, int Lmax, double* d_usol, cudaStream_t st)
 {
-    size_t uoff = 0;
-    for (int t = 0; t <= c->t_small && t <= Lmax; ++t) uoff += static_cast<size_t>(A.lv[t].n) * A.lv[t].n;
-    for (int t = c->t_small + 1; t <= Lmax; ++t) {
+    size_t uoff = static_cast<size_t>(A.lv[0].n) * A.lv[0].n;
+    for (int t = 1; t <= Lmax; ++t) {
         const int B = Bt[t];
         if (B == 0) break;
         const int64_t n = c->p.coarse_cells << t;
@@ -826,18 +797,21 @@ mlqmc_status large_stages(mlqmc_ctx* c, const FmgArgs& A, const int* Bt, int Lma
             Timed tm(c, kProfTransfer, st);
             kb_prolong<T, false, MX><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
         }
-        for (int m = 0; m < c->p.mu0; ++m) {
-            if constexpr (MX) {
-                {
-                    Timed tm(c, kProfTransfer, st);
-                    kb_resid64<<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
-                }
-                if (zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
+        if constexpr (MX) {
+            // refinement step: r = 1 - A u64 (FP64), mu0 FP32 V-cycles on A e = r, u64 += e
+            {
+                Timed tm(c, kProfTransfer, st);
+                kb_resid64<<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
+            }
+            if (zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
+            for (int m = 0; m < c->p.mu0; ++m) {
                 mlqmc_status s = vcycle_batched<T>(c, A, t, B, false, st);
                 if (s != MLQMC_OK) return s;
-                Timed tm(c, kProfTransfer, st);
-                kb_update64<<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
-            } else {
+            }
+            Timed tm(c, kProfTransfer, st);
+            kb_update64<<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
+        } else {
+            for (int m = 0; m < c->p.mu0; ++m) {
                 mlqmc_status s = vcycle_batched<T>(c, A, t, B, true, st);
                 if (s != MLQMC_OK) return s;
             }
@@ -871,16 +845,20 @@ mlqmc_status run_chunk(mlqmc_ctx* c, int count, const int* Bt, int Lmax, double*
     FmgArgs A = base_args(c);
     mlqmc_status s = launch_points(c, c->d_samples, count, c->d_Y, nullptr, st);
     if (s != MLQMC_OK) return s;
-    A.usol = d_usol;
-    s = launch_small(c, A, count, st);
-    if (s != MLQMC_OK) return s;
-    A.usol = nullptr;
-    for (int t = c->t_small + 1; t <= Lmax && Bt[t] > 0; ++t) {
+    for (int t = 0; t <= Lmax && Bt[t] > 0; ++t) {
         s = is_mixed(p) ? synth_batched<float>(c, A, t, Bt[t], st) : synth_batched<double>(c, A, t, Bt[t], st);
         if (s != MLQMC_OK) return s;
     }
-    s = is_mixed(p) ? large_stages<float, true>(c, A, Bt, Lmax, d_usol, st)
-                    : large_stages<double, false>(c, A, Bt, Lmax, d_usol, st);
+    s = launch_level0(c, A, Bt[0], st);
+    if (s != MLQMC_OK) return s;
+    if (d_usol) {
+        const int64_t n0 = p.coarse_cells;
+        Timed tm(c, kProfReduce, st);
+        if (is_mixed(p)) kb_u_out<float, true><<<grid_for(c, n0 * n0), 256, 0, st>>>(A, 0, d_usol);
+        else kb_u_out<double, false><<<grid_for(c, n0 * n0), 256, 0, st>>>(A, 0, d_usol);
+    }
+    s = is_mixed(p) ? fmg_stages<float, true>(c, A, Bt, Lmax, d_usol, st)
+                    : fmg_stages<double, false>(c, A, Bt, Lmax, d_usol, st);
     if (s != MLQMC_OK) return s;
     if (d_sums) {
         Timed tm(c, kProfReduce, st);
@@ -921,6 +899,7 @@ void free_ctx(mlqmc_ctx* c)
     cudaFree(c->d_Y);
     cudaFree(c->d_F);
     cudaFree(c->d_chol);
+    cudaFree(c->d_chol32);
     cudaFree(c->d_norms);
     cudaFree(c->d_active);
     cudaFree(c->d_count);
@@ -1002,9 +981,6 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
     if (p->sampler == MLQMC_SAMPLER_LATTICE) c->z.assign(p->genvec, p->genvec + p->n_modes);
     else c->z.assign(p->n_modes, 1u);
     c->p.genvec = nullptr;
-    // levels up to 64 x 64 cells are solved per sample by one CTA
-    c->t_small = 0;
-    while (c->t_small + 1 < p->n_levels && (p->coarse_cells << (c->t_small + 1)) <= 64) ++c->t_small;
 
     // KL tables (Sec. 5): modes, 1D eigenpairs, per-level psi tables
     c->modes = mlqmc::select_modes(p->corr_len, p->sigma, p->n_modes);
@@ -1054,7 +1030,8 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
     good = ok(cudaMalloc(&c->d_samples, ms * sizeof(SampleDesc))) &&
            ok(cudaMalloc(&c->d_Y, ms * p->n_modes * sizeof(double))) &&
            ok(cudaMalloc(&c->d_F, ms * p->n_levels * sizeof(double))) &&
-           ok(cudaMalloc(&c->d_chol, ms * c->chol_stride)) && ok(cudaMalloc(&c->d_norms, ms * sizeof(double))) &&
+           ok(cudaMalloc(&c->d_chol, ms * c->chol_stride)) && ok(cudaMalloc(&c->d_chol32, ms * c->chol_stride / 2)) &&
+           ok(cudaMalloc(&c->d_norms, ms * sizeof(double))) &&
            ok(cudaMalloc(&c->d_active, ms * sizeof(int))) && ok(cudaMalloc(&c->d_count, sizeof(int))) &&
            ok(cudaMallocHost(&c->h_samples, ms * sizeof(SampleDesc))) &&
            ok(cudaMallocHost(&c->h_count, sizeof(int))) && ok(cudaMalloc(&c->d_status, sizeof(int))) &&
@@ -1065,21 +1042,6 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
         return MLQMC_ERR_OOM;
     }
 
-    // per-sample kernel launch shape and the pool budget
-    const size_t smem = sizeof(double) * 8 * static_cast<size_t>(small_warp_doubles(p->n_modes, p->coarse_cells));
-    c->small_smem = smem;
-    void* kern = small_kernel(c->p);
-    if (smem > 48 * 1024 &&
-        !ok(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)))) {
-        free_ctx(c);
-        return MLQMC_ERR_CUDA;
-    }
-    int per_sm = 0;
-    if (!ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, c->fmg_threads, smem)) || per_sm < 1) {
-        free_ctx(c);
-        return MLQMC_ERR_CUDA;
-    }
-    c->small_grid = c->sm_count * per_sm;
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     c->pool_budget = std::min<size_t>(free_b / 2, static_cast<size_t>(96) << 30);
@@ -1243,11 +1205,6 @@ extern "C" mlqmc_status mlqmc_fields(mlqmc_ctx* c, int32_t t, const double* d_y,
     s = ensure_pool(c, t, count);
     if (s != MLQMC_OK) return s;
     FmgArgs A = base_args(c);
-    if (t <= c->t_small) {
-        A.k_out = d_k;
-        A.field_level = t;
-        return launch_small(c, A, count, st);
-    }
     s = is_mixed(c->p) ? synth_batched<float>(c, A, t, count, st) : synth_batched<double>(c, A, t, count, st);
     if (s != MLQMC_OK) return s;
     const int64_t n = c->p.coarse_cells << t;
@@ -1430,7 +1387,6 @@ extern "C" mlqmc_status mlqmc_fmg_fields_noalloc(int32_t coarse_cells, int32_t n
     std::memset(&A, 0, sizeof(A));
     A.n0 = coarse_cells;
     A.n_levels = n_levels;
-    A.t_small = n_levels - 1;
     A.qoi = qoi_kind;
     A.mu0 = mu0;
     A.nu1 = nu1;

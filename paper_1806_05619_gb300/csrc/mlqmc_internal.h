@@ -51,11 +51,11 @@ struct SampleDesc {
 // Kinds of kernels for the optional per-kind event timing.
 enum ProfKind {
     kProfPoints = 0,   // normals
-    kProfSmall = 1,    // per-sample solver of the small levels
+    kProfSmall = 1,    // per-sample level-0 factor and exact solve
     kProfSynth = 2,    // batched KL field, faces, inverse diagonal
     kProfSmooth = 3,   // batched red-black sweeps
     kProfTransfer = 4, // batched residual/restriction, prolongation, FP64 refinement updates
-    kProfSmallV = 5,   // per-sample V-cycle below the large levels
+    kProfSmallV = 5,   // coarse solves of the V-cycles (one thread per sample)
     kProfReduce = 6,   // QoI, norms, reuse sums, outputs
     kProfKinds = 8
 };
@@ -78,8 +78,7 @@ struct mlqmc_ctx {
     std::vector<uint32_t> z;
     mlqmc::Modes modes;
     mlqmc::Eig1D eig;
-    int Ka = 0;       // 1 + max a over the kept modes
-    int t_small = 0;  // levels <= t_small are solved per sample by one CTA
+    int Ka = 0;  // 1 + max a over the kept modes
 
     // device tables
     double* d_psi = nullptr;  // per level: K1 x n_t doubles
@@ -96,7 +95,8 @@ struct mlqmc_ctx {
     SampleDesc* d_samples = nullptr;  // rank order (finest level descending)
     double* d_Y = nullptr;            // normals, s per sample
     double* d_F = nullptr;            // F_t per sample, n_levels each
-    double* d_chol = nullptr;         // banded level-0 factor per sample
+    double* d_chol = nullptr;         // banded level-0 factor per sample (interleaved by sample)
+    float* d_chol32 = nullptr;        // its FP32 copy (mixed forms)
     double* d_norms = nullptr;
     int* d_active = nullptr;
     int* d_count = nullptr;
@@ -108,9 +108,6 @@ struct mlqmc_ctx {
     // level pools, grown on demand; chunks are cut to fit pool_budget bytes
     LevelPool pools[MLQMC_MAX_LEVELS];
     size_t pool_budget = 0;
-    int small_grid = 0;   // CTAs of the per-sample kernels
-    int fmg_threads = 256;
-    size_t small_smem = 0;
 
     // optional per-kernel event timing
     bool profiling = false;
