@@ -282,7 +282,7 @@ mlqmc_status mlqmc_profile(mlqmc_ctx* c, int32_t enable);
  * 0 normals, 1 level-0 banded factor and exact solve (per sample), 2 KL field
  * and faces, 3 red-black sweeps, 4 residual/restriction, prolongation and
  * FP64 refinement updates, 5 coarse solves of the V-cycles, 6 QoI, norms,
- * reuse sums and outputs, 7 unused.
+ * reuse sums and outputs, 7 KL contraction on the tensor cores.
  * out_ms: device milliseconds (host, 8 doubles); out_n: launches (host, 8
  * int64). Waits for the recorded events.
  */

@@ -261,7 +261,7 @@ class Context:
         """Start (or stop) per-kernel CUDA-event timing of sample_levels; clears totals."""
         _check(lib().mlqmc_profile(self.h, 1 if enable else 0), "mlqmc_profile")
 
-    PROFILE_KINDS = ["points", "level0", "synth", "smooth", "transfer", "coarse", "reduce", "unused"]
+    PROFILE_KINDS = ["points", "level0", "synth", "smooth", "transfer", "coarse", "reduce", "kl_tc"]
 
     def profile_read(self):
         """{kind: (ms, launches)} per kernel kind since profile(); kinds as in mlqmc_profile_read."""

@@ -15,6 +15,7 @@ namespace mlqmc_dev {
 
 constexpr int kStatusNotConverged = 1;
 constexpr int kStatusCheck = 2;
+constexpr int kStatusTimeout = 4;  // a bounded device wait gave up (tensor-core KL pipeline)
 
 // Array of per-sample blocks: block i starts at base + i * stride (bytes).
 struct ArrDesc {

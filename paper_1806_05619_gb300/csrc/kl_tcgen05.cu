@@ -1,0 +1,376 @@
+// KL field synthesis on the 5th-generation tensor cores (sm_103a).
+//
+// For one grid level the truncated KL expansion (eq. truncatedKL) of every
+// sample is a dense contraction
+//     Z[p][b] = sum_m Psi[p][m] * C[b][m],  Psi[p][m] = psi_{a_m}(x1_p) psi_{b_m}(x2_p),
+//                                          C[b][m]   = sqrt(theta_m) y_{b,m},
+// p over the level's cells, b over the samples, m over the s modes; the
+// coefficient is k = exp(Z). The kernel computes 128 cells x NT samples per
+// CTA: TMA brings 128-byte-swizzled K blocks of Psi (A operand, K-major) and
+// C (B operand, K-major) into shared memory through an mbarrier ring; one
+// thread issues tcgen05.mma kind::tf32 into an FP32 accumulator in TMEM; the
+// four warps then read their 32 TMEM lanes (one cell each) with tcgen05.ld,
+// apply exp and store k sample by sample, coalesced across cells.
+// Operands are rounded to TF32 (round to nearest) when they are built.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+
+#include "kl_tcgen05.h"
+
+namespace {
+
+constexpr int kTileM = 128;      // cells per CTA (TMEM lanes)
+constexpr int kKBlock = 32;      // K elements per stage (128 bytes of FP32)
+constexpr int kStages = 4;
+constexpr uint32_t kErrTimeout = 4;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t now_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with `parity` to complete, giving up after about a second.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err)
+{
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = now_ns();
+    for (uint32_t it = 0; it < (1u << 30); ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if ((it & 255u) == 0 && now_ns() - t0 > 1000000000ull) break;
+    }
+    atomicOr(err, static_cast<int>(kErrTimeout));
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row atoms 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);  // start address
+    d |= static_cast<uint64_t>(1) << 16;                   // leading byte offset (unused for this layout)
+    d |= static_cast<uint64_t>(1024 >> 4) << 32;           // stride byte offset: next 8-row atom
+    d |= static_cast<uint64_t>(1) << 46;                   // descriptor version
+    d |= static_cast<uint64_t>(2) << 61;                   // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+           (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(128, 1) kl_tc_kernel(const __grid_constant__ CUtensorMap tm_psi,
+                                                       const __grid_constant__ CUtensorMap tm_c, int M, int B, int nk,
+                                                       float* __restrict__ kout, size_t kstride, int* err)
+{
+    extern __shared__ unsigned char smem_raw[];
+    // 1024-byte aligned stage buffers (the 128-byte swizzle atom)
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    constexpr uint32_t kABytes = kTileM * kKBlock * 4;
+    constexpr uint32_t kBBytes = NT * kKBlock * 4;
+    unsigned char* sa = smem;
+    unsigned char* sb = smem + kStages * kABytes;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sb + kStages * kBBytes);
+    uint64_t* empty = full + kStages;
+    uint64_t* accum = empty + kStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kTileM;
+    const int b0 = blockIdx.y * NT;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(static_cast<uint32_t>(NT))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+
+    if (threadIdx.x == 0) {
+        // producer: K blocks of Psi rows m0.. and C rows b0..
+        int issued = 0;
+        for (int kb = 0; kb < nk && ok; ++kb) {
+            const int s = kb % kStages;
+            if (kb >= kStages) ok = mbar_wait(&empty[s], ((kb / kStages) - 1) & 1, err);
+            if (!ok) break;
+            mbar_expect_tx(&full[s], kABytes + kBBytes);
+            tma_load_2d(sa + s * kABytes, &tm_psi, &full[s], kb * kKBlock, m0);
+            tma_load_2d(sb + s * kBBytes, &tm_c, &full[s], kb * kKBlock, b0);
+            issued = kb + 1;
+        }
+        // let every copy this thread issued land before the CTA can leave
+        for (int kb = (issued > kStages ? issued - kStages : 0); kb < issued; ++kb)
+            mbar_wait(&full[kb % kStages], (kb / kStages) & 1, err);
+    } else if (threadIdx.x == 32) {
+        // MMA issuer
+        constexpr uint32_t idesc = idesc_tf32(kTileM, NT);
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % kStages;
+            if (!mbar_wait(&full[s], (kb / kStages) & 1, err)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint64_t ad = sdesc_sw128(smem_u32(sa + s * kABytes));
+            const uint64_t bd = sdesc_sw128(smem_u32(sb + s * kBBytes));
+#pragma unroll
+            for (int k = 0; k < kKBlock / 8; ++k)  // 8 TF32 = 32 bytes of K per MMA
+                mma_tf32(tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+            mma_commit(&empty[s]);
+        }
+        mma_commit(accum);
+    }
+    __syncwarp();
+
+    // epilogue: warp w owns TMEM lanes 32w..32w+31 (cells m0 + 32w + lane)
+    // warp-uniform: the TMEM loads below are .sync.aligned
+    const bool done = __all_sync(0xffffffffu, mbar_wait(accum, 0, err) ? 1 : 0) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (done) {
+        const int p = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c = 0; c < NT; c += 32) {
+            float v[32];
+            tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(c), v);
+            if (p < M) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int b = b0 + c + j;
+                    if (b < B) kout[static_cast<size_t>(b) * kstride + p] = __expf(v[j]);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(static_cast<uint32_t>(NT))
+                     : "memory");
+    }
+}
+
+__device__ __forceinline__ float to_tf32(double v)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(static_cast<float>(v)));
+    return __uint_as_float(r);
+}
+
+// Psi[p][m] = tf32(psi_{a_m}(x1) psi_{b_m}(x2)) for p = i2*n + i1, zero for m >= s.
+__global__ void kl_build_psi(const double* __restrict__ psi1d, int n, int s, int kpad, const int* __restrict__ ma,
+                             const int* __restrict__ mb, float* __restrict__ out)
+{
+    const int64_t total = static_cast<int64_t>(n) * n * kpad;
+    for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int m = static_cast<int>(idx % kpad);
+        const int64_t p = idx / kpad;
+        const int i2 = static_cast<int>(p / n), i1 = static_cast<int>(p % n);
+        out[idx] = m < s ? to_tf32(psi1d[static_cast<size_t>(ma[m]) * n + i1] * psi1d[static_cast<size_t>(mb[m]) * n + i2])
+                         : 0.0f;
+    }
+}
+
+// C[i][m] = tf32(sqrt(theta_m) y_{canon_i, m}), zero for m >= s.
+__global__ void kl_build_c(const double* __restrict__ Y, const int* __restrict__ canon, int count, int s, int kpad,
+                           const double* __restrict__ sqrt_theta, float* __restrict__ out)
+{
+    const int64_t total = static_cast<int64_t>(count) * kpad;
+    for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int m = static_cast<int>(idx % kpad);
+        const int i = static_cast<int>(idx / kpad);
+        const size_t row = canon ? static_cast<size_t>(canon[i]) : static_cast<size_t>(i);
+        out[idx] = m < s ? to_tf32(sqrt_theta[m] * Y[row * s + m]) : 0.0f;
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2D FP32 map: rows x kpad (inner), box kKBlock x box_rows, 128-byte swizzle.
+bool encode_2d(CUtensorMap* map, const float* base, uint64_t rows, uint64_t kpad, uint32_t box_rows)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {kpad, rows};
+    const cuuint64_t strides[1] = {kpad * sizeof(float)};
+    const cuuint32_t box[2] = {static_cast<cuuint32_t>(kKBlock), box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+constexpr int kNT = 256;
+
+size_t tc_smem_bytes()
+{
+    return 1024 + kStages * (kTileM * kKBlock * 4 + kNT * kKBlock * 4) + (2 * kStages + 1) * 8 + 16;
+}
+
+}  // namespace
+
+namespace mlqmc_kl {
+
+int kpad_for(int s)
+{
+    return (s + kKBlock - 1) / kKBlock * kKBlock;
+}
+
+bool build_psi(const double* d_psi1d, int n, int s, const int* d_ma, const int* d_mb, float* d_out, cudaStream_t st)
+{
+    const int kpad = kpad_for(s);
+    const int64_t total = static_cast<int64_t>(n) * n * kpad;
+    const int grid = static_cast<int>(std::min<int64_t>((total + 255) / 256, 152 * 64));
+    kl_build_psi<<<grid, 256, 0, st>>>(d_psi1d, n, s, kpad, d_ma, d_mb, d_out);
+    return cudaGetLastError() == cudaSuccess;
+}
+
+bool build_c(const double* d_Y, const int* d_canon, int count, int s, const double* d_sqrt_theta, float* d_out,
+             cudaStream_t st)
+{
+    const int kpad = kpad_for(s);
+    const int64_t total = static_cast<int64_t>(count) * kpad;
+    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 64)));
+    kl_build_c<<<grid, 256, 0, st>>>(d_Y, d_canon, count, s, kpad, d_sqrt_theta, d_out);
+    return cudaGetLastError() == cudaSuccess;
+}
+
+bool make_maps(const float* d_psi, int M, const float* d_c, int rows_c, int s, TensorMaps* maps)
+{
+    const int kpad = kpad_for(s);
+    static_assert(sizeof(TensorMaps::psi) >= sizeof(CUtensorMap), "map storage");
+    return encode_2d(reinterpret_cast<CUtensorMap*>(maps->psi), d_psi, static_cast<uint64_t>(M), kpad, kTileM) &&
+           encode_2d(reinterpret_cast<CUtensorMap*>(maps->c), d_c, static_cast<uint64_t>(rows_c), kpad, kNT);
+}
+
+bool prepare_kernel()
+{
+    return cudaFuncSetAttribute(kl_tc_kernel<kNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(tc_smem_bytes())) == cudaSuccess;
+}
+
+bool launch(const TensorMaps& maps, int M, int B, int s, float* d_k, size_t kstride, int* d_err, cudaStream_t st)
+{
+    if (M % kTileM != 0 || B <= 0) return false;
+    const int nk = kpad_for(s) / kKBlock;
+    CUtensorMap tp, tc;
+    std::memcpy(&tp, maps.psi, sizeof(CUtensorMap));
+    std::memcpy(&tc, maps.c, sizeof(CUtensorMap));
+    dim3 grid(M / kTileM, (B + kNT - 1) / kNT);
+    kl_tc_kernel<kNT><<<grid, 128, tc_smem_bytes(), st>>>(tp, tc, M, B, nk, d_k, kstride, d_err);
+    return cudaGetLastError() == cudaSuccess;
+}
+
+int tile_samples() { return kNT; }
+
+}  // namespace mlqmc_kl

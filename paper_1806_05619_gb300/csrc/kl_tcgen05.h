@@ -1,0 +1,32 @@
+// Host interface of the tensor-core KL synthesis (kl_tcgen05.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+namespace mlqmc_kl {
+
+// Opaque storage for the two TMA descriptors of one level (CUtensorMap is 128 bytes, 64-byte aligned).
+struct alignas(64) TensorMaps {
+    unsigned char psi[128];
+    unsigned char c[128];
+};
+
+int kpad_for(int s);   // K padded to whole 32-element blocks
+int tile_samples();    // samples per CTA tile
+
+// Psi of one level (n x n cells, row-major p = i2*n + i1; kpad_for(s) columns) from the FP64 1D tables.
+bool build_psi(const double* d_psi1d, int n, int s, const int* d_ma, const int* d_mb, float* d_out, cudaStream_t st);
+
+// C rows i < count: tf32(sqrt(theta_m) y_m) of the sample whose normals are row canon[i] of Y.
+bool build_c(const double* d_Y, const int* d_canon, int count, int s, const double* d_sqrt_theta, float* d_out,
+             cudaStream_t st);
+
+bool make_maps(const float* d_psi, int M, const float* d_c, int rows_c, int s, TensorMaps* maps);
+bool prepare_kernel();
+
+// k[b * kstride + p] = exp(sum_m Psi[p][m] C[b][m]) for p < M (M a multiple of 128), b < B.
+bool launch(const TensorMaps& maps, int M, int B, int s, float* d_k, size_t kstride, int* d_err, cudaStream_t st);
+
+}  // namespace mlqmc_kl

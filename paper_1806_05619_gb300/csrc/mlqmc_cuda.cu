@@ -671,18 +671,38 @@ mlqmc_status launch_points(mlqmc_ctx* c, const SampleDesc* d_s, int count, doubl
     return last_error();
 }
 
-// Batched KL field and faces of level t for samples 0..B-1.
+// True when level t's field comes from the tensor-core contraction.
+bool uses_tc(const mlqmc_ctx* c, int t)
+{
+    return c->kl_tc && c->d_psi_tc[t] != nullptr;
+}
+
+// Batched KL field and faces of level t for samples 0..B-1. The field comes
+// from the tensor-core contraction (mixed TF32 form, levels of >= 128 cells)
+// or from the separable SIMT sum; the C operand must already be built.
 template <typename T>
 mlqmc_status synth_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cudaStream_t st)
 {
     const int64_t n = c->p.coarse_cells << t;
-    {
-        Timed tm(c, kProfSynth, st);
-        kb_synth_G<T><<<grid_for(c, B * c->Ka * n), 256, 0, st>>>(A, t, B);
+    if constexpr (sizeof(T) == 4) {
+        if (uses_tc(c, t)) {
+            const LevelPool& P = c->pools[t];
+            float* k = reinterpret_cast<float*>(P.mem + P.off[kK]);
+            Timed tm(c, kProfKlTc, st);
+            if (!mlqmc_kl::launch(c->kl_maps[t], static_cast<int>(n * n), B, c->p.n_modes, k, P.stride[kK] / sizeof(float),
+                                  c->d_status, st))
+                return MLQMC_ERR_CUDA;
+        }
     }
-    {
-        Timed tm(c, kProfSynth, st);
-        kb_synth_z<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
+    if (!uses_tc(c, t) || sizeof(T) != 4) {
+        {
+            Timed tm(c, kProfSynth, st);
+            kb_synth_G<T><<<grid_for(c, B * c->Ka * n), 256, 0, st>>>(A, t, B);
+        }
+        {
+            Timed tm(c, kProfSynth, st);
+            kb_synth_z<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
+        }
     }
     {
         Timed tm(c, kProfSynth, st);
@@ -693,6 +713,15 @@ mlqmc_status synth_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cudaStr
         kb_idiag<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
     }
     return last_error();
+}
+
+// C operand of the tensor-core contraction for samples 0..count-1 (normals in rank order).
+mlqmc_status build_c(mlqmc_ctx* c, int count, cudaStream_t st)
+{
+    if (!c->kl_tc) return MLQMC_OK;
+    Timed tm(c, kProfKlTc, st);
+    return mlqmc_kl::build_c(c->d_Y, nullptr, count, c->p.n_modes, c->d_sqrt_theta, c->d_C, st) ? MLQMC_OK
+                                                                                                : MLQMC_ERR_CUDA;
 }
 
 mlqmc_status zero_u(mlqmc_ctx* c, int t, int B, cudaStream_t st)
@@ -845,6 +874,8 @@ mlqmc_status run_chunk(mlqmc_ctx* c, int count, const int* Bt, int Lmax, double*
     FmgArgs A = base_args(c);
     mlqmc_status s = launch_points(c, c->d_samples, count, c->d_Y, nullptr, st);
     if (s != MLQMC_OK) return s;
+    s = build_c(c, count, st);
+    if (s != MLQMC_OK) return s;
     for (int t = 0; t <= Lmax && Bt[t] > 0; ++t) {
         s = is_mixed(p) ? synth_batched<float>(c, A, t, Bt[t], st) : synth_batched<double>(c, A, t, Bt[t], st);
         if (s != MLQMC_OK) return s;
@@ -895,6 +926,11 @@ void free_ctx(mlqmc_ctx* c)
     cudaFree(c->d_grp_m);
     cudaFree(c->d_grp_sqrt);
     cudaFree(c->d_z);
+    cudaFree(c->d_ma);
+    cudaFree(c->d_mb);
+    cudaFree(c->d_sqrt_theta);
+    for (auto* q : c->d_psi_tc) cudaFree(q);
+    cudaFree(c->d_C);
     cudaFree(c->d_samples);
     cudaFree(c->d_Y);
     cudaFree(c->d_F);
@@ -970,6 +1006,7 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
     mlqmc_status st = check_problem(p);
     if (st != MLQMC_OK) return st;
     if (max_samples_per_call < 0) return MLQMC_ERR_INVALID_ARG;
+    if (p->precision == MLQMC_MIXED_BF16X3) return MLQMC_ERR_UNSUPPORTED;
     mlqmc_ctx* c = new (std::nothrow) mlqmc_ctx();
     if (!c) return MLQMC_ERR_OOM;
     c->p = *p;
@@ -1011,12 +1048,17 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
         off += tab.size();
     }
     std::vector<float> psi32(psi_all.begin(), psi_all.end());
+    std::vector<double> sq(p->n_modes);
+    for (int m = 0; m < p->n_modes; ++m) sq[m] = std::sqrt(c->modes.theta[m]);
     bool good = dev_upload(&c->d_psi, psi_all.data(), psi_all.size()) &&
                 dev_upload(&c->d_psi32, psi32.data(), psi32.size()) &&
                 dev_upload(&c->d_grp_start, gstart.data(), gstart.size()) &&
                 dev_upload(&c->d_grp_b, gb.data(), gb.size()) && dev_upload(&c->d_grp_m, gm.data(), gm.size()) &&
                 dev_upload(&c->d_grp_sqrt, gsq.data(), gsq.size()) &&
-                dev_upload(&c->d_z, c->z.data(), c->z.size());
+                dev_upload(&c->d_z, c->z.data(), c->z.size()) &&
+                dev_upload(&c->d_ma, c->modes.a.data(), c->modes.a.size()) &&
+                dev_upload(&c->d_mb, c->modes.b.data(), c->modes.b.size()) &&
+                dev_upload(&c->d_sqrt_theta, sq.data(), sq.size());
     if (!good) {
         free_ctx(c);
         return MLQMC_ERR_OOM;
@@ -1042,6 +1084,23 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
         return MLQMC_ERR_OOM;
     }
 
+    // tensor-core KL tables (mixed TF32 form): Psi of every level with a whole number of 128-cell tiles
+    if (p->precision == MLQMC_MIXED_TF32) {
+        const int kpad = mlqmc_kl::kpad_for(p->n_modes);
+        good = mlqmc_kl::prepare_kernel() && ok(cudaMalloc(&c->d_C, ms * kpad * sizeof(float)));
+        for (int t = 0; good && t < p->n_levels; ++t) {
+            const int n = p->coarse_cells << t;
+            if ((n * n) % 128 != 0) continue;
+            good = ok(cudaMalloc(&c->d_psi_tc[t], static_cast<size_t>(n) * n * kpad * sizeof(float))) &&
+                   mlqmc_kl::build_psi(c->d_psi + c->psi_off[t], n, p->n_modes, c->d_ma, c->d_mb, c->d_psi_tc[t], 0) &&
+                   mlqmc_kl::make_maps(c->d_psi_tc[t], n * n, c->d_C, static_cast<int>(ms), p->n_modes, &c->kl_maps[t]);
+        }
+        if (!good || !ok(cudaDeviceSynchronize())) {
+            free_ctx(c);
+            return MLQMC_ERR_CUDA;
+        }
+        c->kl_tc = true;
+    }
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     c->pool_budget = std::min<size_t>(free_b / 2, static_cast<size_t>(96) << 30);
@@ -1129,6 +1188,7 @@ extern "C" mlqmc_status mlqmc_get_device_status(mlqmc_ctx* c, void* stream)
         return MLQMC_ERR_CUDA;
     h |= c->host_status;
     c->host_status = 0;
+    if (h & kStatusTimeout) return MLQMC_ERR_TIMEOUT;
     if (h & kStatusNotConverged) return MLQMC_ERR_NOT_CONVERGED;
     if (h & kStatusCheck) return MLQMC_ERR_DEVICE_STATUS;
     return MLQMC_OK;
@@ -1203,6 +1263,8 @@ extern "C" mlqmc_status mlqmc_fields(mlqmc_ctx* c, int32_t t, const double* d_y,
                             cudaMemcpyDeviceToDevice, st)))
         return MLQMC_ERR_CUDA;
     s = ensure_pool(c, t, count);
+    if (s != MLQMC_OK) return s;
+    s = build_c(c, count, st);
     if (s != MLQMC_OK) return s;
     FmgArgs A = base_args(c);
     s = is_mixed(c->p) ? synth_batched<float>(c, A, t, count, st) : synth_batched<double>(c, A, t, count, st);

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/mlqmc.h"
+#include "kl_tcgen05.h"
 
 #define MLQMC_MAX_LEVELS 12
 #define MLQMC_MAX_MODES 4096
@@ -57,6 +58,7 @@ enum ProfKind {
     kProfTransfer = 4, // batched residual/restriction, prolongation, FP64 refinement updates
     kProfSmallV = 5,   // coarse solves of the V-cycles (one thread per sample)
     kProfReduce = 6,   // QoI, norms, reuse sums, outputs
+    kProfKlTc = 7,     // KL contraction on the tensor cores
     kProfKinds = 8
 };
 
@@ -89,6 +91,15 @@ struct mlqmc_ctx {
     int* d_grp_m = nullptr;
     double* d_grp_sqrt = nullptr;
     uint32_t* d_z = nullptr;
+    int* d_ma = nullptr;               // modes in order: first index a
+    int* d_mb = nullptr;               // second index b
+    double* d_sqrt_theta = nullptr;    // sqrt(theta_m)
+
+    // tensor-core KL (mixed TF32 form): Psi per level with >= 128 cells, C per chunk
+    bool kl_tc = false;
+    float* d_psi_tc[MLQMC_MAX_LEVELS] = {};
+    float* d_C = nullptr;
+    mlqmc_kl::TensorMaps kl_maps[MLQMC_MAX_LEVELS];
 
     // per-chunk buffers (max_samples entries)
     int64_t max_samples = 0;

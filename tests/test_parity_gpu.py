@@ -281,7 +281,7 @@ def test_device_status_not_converged():
 
 
 def _field_bound(orc, cfg, y, u_in):
-    """Rounding bound on |z_mixed - z_64|: (k_terms) u_in * sum_m |sqrt(theta_m) y_m| M_a M_b with
+    """Rounding bound on |z_mixed - z_64|: u_in * sum_m |sqrt(theta_m) y_m| M_a M_b with
     M_k = sqrt((w_k^2 + c^2)/N_k) >= max |psi_k|."""
     a, b, th, K1 = orc.modes()
     w, _, nr = O.kl1d(cfg["corr_len"], K1)
@@ -290,17 +290,38 @@ def _field_bound(orc, cfg, y, u_in):
     return u_in * np.sum(np.sqrt(th) * np.abs(y) * Mk[a] * Mk[b])
 
 
+def _tf32_u(s):
+    """Error factor of the TF32 contraction: both operands rounded to TF32
+    (2 * 2^-11) and an FP32 accumulation over s terms (s * 2^-24)."""
+    return 2 * 2.0 ** -11 + s * 2.0 ** -24
+
+
+EXP_SLACK = 2.0 ** -20  # FP32 exp and the FP32 face arithmetic
+
+
 def test_mixed_fields_within_bound():
     cfg, ctx, orc = _pair(W.CONFIG3, n_levels=4)
     Y = W.random_normals(cfg["s"], 2, tag=40)
-    a, b, th, K1 = orc.modes()
-    terms = int(np.max(a)) + 1 + int(np.max(np.bincount(a))) + 4
     for t in [0, 3]:
         k = ctx.fields(t, torch.from_numpy(Y)).cpu().numpy()
         for i in range(2):
             want = orc.field(t, Y[i])
-            eta = _field_bound(orc, cfg, Y[i], terms * 2.0 ** -24)
-            assert np.max(np.abs(np.log(k[i] / want))) <= eta + 2.0 ** -22
+            eta = _field_bound(orc, cfg, Y[i], _tf32_u(cfg["s"]))
+            assert np.max(np.abs(np.log(k[i] / want))) <= eta + EXP_SLACK
+
+
+def test_tensor_core_fields_many_samples():
+    """More samples than one tensor-core tile (256) and several cell tiles."""
+    cfg, ctx, orc = _pair(W.CONFIG3, n_levels=4)
+    Y = W.random_normals(cfg["s"], 300, tag=41)
+    k = ctx.fields(2, torch.from_numpy(Y)).cpu().numpy()
+    assert np.all(np.isfinite(k)) and np.all(k > 0)
+    for i in [0, 1, 255, 256, 299]:
+        want = orc.field(2, Y[i])
+        eta = _field_bound(orc, cfg, Y[i], _tf32_u(cfg["s"]))
+        err = np.max(np.abs(np.log(k[i] / want)))
+        assert err <= eta + EXP_SLACK, (i, err, eta)
+    ctx.check_device()
 
 
 def test_mixed_qoi_within_bound():
@@ -310,12 +331,11 @@ def test_mixed_qoi_within_bound():
         ref = orc.sample(lv, r, n, want_u=True)
         assert ref["status"] == O.OK
         y = orc.normals(lv, r, n)
-        a, b, th, K1 = orc.modes()
-        terms = int(np.max(a)) + 1 + int(np.max(np.bincount(a))) + 4
-        eta = _field_bound(orc, cfg, y, terms * 2.0 ** -24) + 2.0 ** -22
+        eta = _field_bound(orc, cfg, y, _tf32_u(cfg["s"])) + EXP_SLACK
         Fg = F.cpu().numpy()
         for t in range(lv + 1):
             u = ref["u"][t]
             ratio = math.sqrt(np.mean(u ** 2)) / np.mean(u)
             tol = math.expm1(eta) + 2 * cfg["rtol"] * ratio
             assert abs(Fg[t] / ref["F"][t] - 1.0) <= tol, (t, Fg[t], ref["F"][t], tol)
+    ctx.check_device()
