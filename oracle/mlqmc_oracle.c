@@ -281,7 +281,7 @@ typedef struct {
     int qoi;         /* 0: mean of the four centre cells, 1: mean of u over D */
     int mu0, nu1, nu2;
     double rtol;     /* 0: fixed cycle count; >0: each level to ||b-Au||/||b|| <= rtol */
-    int max_cycles;  /* cap on V-cycles per level in the converged form */
+    int max_cycles;  /* cap on correction steps beyond the first in the converged form */
     int sampler;     /* 0: Monte Carlo (Philox), 1: shifted lattice sequence */
     uint64_t seed;
     int R;           /* shifts (or MC replicates) */
@@ -596,18 +596,6 @@ static void vcycle(or_mg* g, int t, double* u, const double* b)
     mg_log(g, t);
 }
 
-static double resid_ratio(int n, const double* k, const double* u, const double* b, double* tmp)
-{
-    or_apply_A(n, k, u, tmp);
-    double rr = 0.0, bb = 0.0;
-    for (int p = 0; p < n * n; ++p) {
-        const double r = b[p] - tmp[p];
-        rr += r * r;
-        bb += b[p] * b[p];
-    }
-    return sqrt(rr) / sqrt(bb);
-}
-
 static double qoi_value(int qoi, int n, const double* u)
 {
     if (qoi == 1) {
@@ -665,13 +653,34 @@ static int fmg_solve(const or_ctx* c, or_mg* g, const double* rhs, double* F, do
         const int n = nlev(g, t);
         prolong_add(n / 2, ul[t - 1], ul[t]); /* FMG interpolation: u_t = P u_{t-1} */
         int cyc = 0;
-        for (int q = 0; q < p->mu0; ++q) {
-            vcycle(g, t, ul[t], bl[t]);
-            ++cyc;
-        }
         if (p->rtol > 0.0) {
-            while (resid_ratio(n, g->k[t], ul[t], bl[t], g->tmp[t]) > p->rtol) {
-                if (cyc >= p->max_cycles) { status = OR_ERR_NOT_CONVERGED; break; }
+            /* converged form (reading A21): defect correction. r = b - A u, mu0
+             * V-cycles on A e = r from e = 0, u += e, until ||r|| <= rtol ||b||;
+             * the first step equals mu0 V-cycles on u. */
+            const size_t nn = (size_t)n * n;
+            double* r = malloc(sizeof(double) * nn);
+            double* e = malloc(sizeof(double) * nn);
+            for (int it = 0;; ++it) {
+                or_apply_A(n, g->k[t], ul[t], r);
+                double rr = 0.0, bb = 0.0;
+                for (size_t q = 0; q < nn; ++q) {
+                    r[q] = bl[t][q] - r[q];
+                    rr += r[q] * r[q];
+                    bb += bl[t][q] * bl[t][q];
+                }
+                if (it > 0 && sqrt(rr) <= p->rtol * sqrt(bb)) break;
+                if (it > p->max_cycles) { status = OR_ERR_NOT_CONVERGED; break; }
+                for (size_t q = 0; q < nn; ++q) e[q] = 0.0;
+                for (int q = 0; q < p->mu0; ++q) {
+                    vcycle(g, t, e, r);
+                    ++cyc;
+                }
+                for (size_t q = 0; q < nn; ++q) ul[t][q] += e[q];
+            }
+            free(r);
+            free(e);
+        } else {
+            for (int q = 0; q < p->mu0; ++q) {
                 vcycle(g, t, ul[t], bl[t]);
                 ++cyc;
             }
