@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed_tf32"],
                     help="form of the main measurement (the other form is reported under 'mixed')")
+    ap.add_argument("--no-precision", action="store_true", help="skip the 1024x1024 precision-form comparison")
+    ap.add_argument("--no-tte", action="store_true", help="skip the time-to-epsilon runs of Algorithm 1")
     ap.add_argument("--counts-div", type=int, default=1,
                     help="divide the per-level counts (small cases for profiler captures only)")
     return ap.parse_args()
@@ -78,10 +80,8 @@ FP32_TFLOPS = 70.0        # FP32 FMA probe on this machine's GB300
 
 
 def t_small(cfg):
-    ts = 0
-    while ts + 1 < cfg["n_levels"] and (cfg["n0"] << (ts + 1)) <= 64:
-        ts += 1
-    return ts
+    """Every level above 0 runs level-synchronous kernels."""
+    return 0
 
 
 def level_counts(cfg, work):
@@ -349,6 +349,12 @@ def run_ours(args):
     mixed = None
     if not args.no_mixed and cfg["precision"] == "fp64":
         mixed = run_mixed_same_workload(args, cfg, work, genvec, dev, stream, flush, M)
+    precision_form = None
+    if not args.no_precision and rank == 0 and args.counts_div == 1:
+        precision_form = run_precision_form(dev, stream, flush, M)
+    tte = None
+    if not args.no_tte and rank == 0 and args.counts_div == 1:
+        tte = run_time_to_eps(M)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -382,6 +388,10 @@ def run_ours(args):
         }
         if mixed:
             line["mixed"] = mixed
+        if precision_form:
+            line["precision_form"] = precision_form
+        if tte:
+            line["time_to_eps"] = tte
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -422,6 +432,87 @@ def run_mixed_same_workload(args, cfg64, work, genvec, dev, stream, flush, M):
     return {"value": ns * args.steps / (tot * 1e-3), "unit": UNIT, "ms_per_step": tot / args.steps,
             "dtype": "f32 V-cycles in f64 refinement, f32 field",
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]}}
+
+
+def run_precision_form(dev, stream, flush, M):
+    """Precision form: one batch of 256 samples whose FMG ends on the 1024x1024
+    level (8 levels from 8x8), s = 400 KL modes (lambda = 0.1), 16 shifts x 16
+    lattice points, every level refined to ||r||_2/||b||_2 <= 1e-10: the mixed
+    form (TF32 tensor-core KL, FP32 V-cycles, FP64 residual and correction)
+    against the all-FP64 GPU form, timing per batch and the mixed results'
+    deviation from the FP64 ones (field, solution, F on every level)."""
+    import torch
+
+    cfg = dict(W.CONFIG3)
+    cfg["log2_nmax"] = 10
+    genvec, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
+    top = cfg["n_levels"] - 1
+    work = [(top, 0, 16, 0, 16)]
+    ns = n_samples(work)
+    nl, R = cfg["n_levels"], cfg["R"]
+    out = {"workload": "256 samples (16 shifts x 16 points) on 8 levels 8x8..1024x1024, s=400, lambda=0.1, "
+                       "refined to relative residual 1e-10 on every level"}
+    res = {}
+    for prec in ["mixed_tf32", "fp64"]:
+        c = dict(cfg)
+        c["precision"] = prec
+        ctx = M.Context.from_config(c, genvec=genvec, max_samples=ns)
+        sums = torch.zeros(nl * R * 2, dtype=torch.float64, device=dev)
+        F = torch.zeros(ns * nl, dtype=torch.float64, device=dev)
+        ctx.sample_levels(work, sums, F, stream=stream)  # warm-up (pools)
+        ctx.check_device(stream)
+        times = []
+        for _ in range(2):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            sums.zero_()
+            e0.record(stream)
+            ctx.sample_levels(work, sums, F, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            times.append(e0.elapsed_time(e1))
+        ctx.check_device(stream)
+        y = ctx.normals(top, 3, 5, 4)
+        kf = ctx.fields(top, y)
+        u, Fs = ctx.sample_solution(top, 3, 5)
+        res[prec] = dict(ms=min(times), F=F.cpu().numpy().reshape(ns, nl), k=kf.cpu().numpy(),
+                         u=u[top].cpu().numpy())
+        out[prec] = {"ms_per_batch": min(times), "samples_per_s": ns / (min(times) * 1e-3)}
+        del ctx
+        torch.cuda.empty_cache()
+    a, b = res["mixed_tf32"], res["fp64"]
+    out["speedup_mixed_over_fp64"] = b["ms"] / a["ms"]
+    out["err_mixed_vs_fp64"] = {
+        "field_max_abs_log_ratio": float(np.max(np.abs(np.log(a["k"] / b["k"])))),
+        "solution_max_rel": float(np.max(np.abs(a["u"] - b["u"])) / np.max(np.abs(b["u"]))),
+        "F_max_rel_per_level": [float(np.max(np.abs(a["F"][:, t] / b["F"][:, t] - 1))) for t in range(nl)],
+    }
+    return out
+
+
+def run_time_to_eps(M):
+    """Time to RMSE eps of Algorithm 1 (exact one-level-per-round form,
+    deterministic cost model) on the 7-level adaptive problem (8x8..512x512,
+    s = 200, lambda = 0.3, 16 shifts, mean-of-u QoI, every level refined to
+    1e-10), mixed form against the FP64 form, for eps in {1e-2, 3e-3, 1e-3}
+    and two smaller tolerances (3e-4, 1e-4) where the runs take longer."""
+    cfg = dict(W.CONFIG4)
+    cfg["log2_nmax"] = 12
+    genvec, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
+    out = {"workload": "Algorithm 1 on 7 levels 8x8..512x512, s=200, lambda=0.3, R=16, rtol 1e-10"}
+    for prec in ["mixed_tf32", "fp64"]:
+        c = dict(cfg)
+        c["precision"] = prec
+        ctx = M.Context.from_config(c, genvec=genvec, max_samples=1 << 17)
+        rows = []
+        for eps in cfg["eps"] + [3e-4, 1e-4]:
+            r = ctx.estimate(eps)
+            rows.append({"eps": eps, "seconds": r["wall_seconds"], "gpu_seconds": r["gpu_seconds"], "Q": r["Q"],
+                         "rmse_bound": float(np.sqrt(r["varQ"] + r["bias"] ** 2)), "L": r["L"],
+                         "rounds": r["rounds"], "N": r["N"][:r["L"] + 1], "run_status": r["run_status"]})
+        out[prec] = rows
+        del ctx
+    return out
 
 
 def main():

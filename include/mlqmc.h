@@ -267,6 +267,14 @@ mlqmc_status mlqmc_fmg_fields_noalloc(int32_t coarse_cells, int32_t n_levels, in
                                       int32_t nu1, int32_t nu2, int32_t count, const double* d_k, double* d_F,
                                       void* stream);
 
+/*
+ * Converged form: for each level (host array of n_levels), the largest
+ * number of cycles (FP64 form) or refinement steps (mixed forms) beyond the
+ * first mu0 that any sample of the calls since the previous query needed on
+ * the batched path. Reading clears the counters.
+ */
+mlqmc_status mlqmc_last_iterations(mlqmc_ctx* c, int32_t* out);
+
 /* Kernel launches issued by this context since creation (all entry points). */
 int64_t mlqmc_launch_count(const mlqmc_ctx* c);
 

@@ -95,6 +95,7 @@ def lib():
             L.mlqmc_fields.argtypes = [vp, i32, vp, i32, vp, vp]
             L.mlqmc_sample_solution.argtypes = [vp, i32, i32, i64, vp, vp, vp]
             L.mlqmc_fmg_fields_noalloc.argtypes = [i32, i32, i32, i32, i32, i32, i32, vp, vp, vp]
+            L.mlqmc_last_iterations.argtypes = [vp, C.POINTER(C.c_int32)]
             L.mlqmc_profile.argtypes = [vp, i32]
             L.mlqmc_profile_read.argtypes = [vp, dp, C.POINTER(C.c_int64)]
             L.mlqmc_launch_count.argtypes = [vp]
@@ -102,7 +103,7 @@ def lib():
             for name in ["mlqmc_create", "mlqmc_sample_levels", "mlqmc_estimate", "mlqmc_get_device_status",
                          "mlqmc_cbc_genvec", "mlqmc_modes", "mlqmc_point_bits", "mlqmc_normals", "mlqmc_fields",
                          "mlqmc_sample_solution", "mlqmc_profile", "mlqmc_profile_read",
-                         "mlqmc_fmg_fields_noalloc"]:
+                         "mlqmc_fmg_fields_noalloc", "mlqmc_last_iterations"]:
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -269,6 +270,12 @@ class Context:
         n = (C.c_int64 * 8)()
         _check(lib().mlqmc_profile_read(self.h, ms.ctypes.data_as(C.POINTER(C.c_double)), n), "mlqmc_profile_read")
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.PROFILE_KINDS)}
+
+    def last_iterations(self):
+        """Per level, the most extra cycles / refinement steps any sample needed since the last query."""
+        out = (C.c_int32 * self.n_levels)()
+        _check(lib().mlqmc_last_iterations(self.h, out), "mlqmc_last_iterations")
+        return list(out)
 
     def launch_count(self) -> int:
         return int(lib().mlqmc_launch_count(self.h))

@@ -68,6 +68,7 @@ struct FmgArgs {
     int* status;
     const int* active;  // per rank; null: all samples active
     double* norms;      // per rank residual norms
+    int refine;         // solutions kept in u64 and corrected (mixed forms; converged FP64 form)
 };
 
 template <typename T>
@@ -429,23 +430,25 @@ __device__ double resid_norm_ones(const TM& tm, const Lv<T>& L, double* red)
     return sqrt(team_sum(tm, acc, red));
 }
 
-// Mixed forms: r = 1 - A u64 in FP64 with the FP32 faces widened; r stored to
-// the FP32 right-hand side. Returns ||r||_2 when red != null.
-__device__ __forceinline__ double resid64_cell(const Lv<float>& L, int i1, int i2)
+// Refinement path (mixed forms, and the converged FP64 form): r = 1 - A u64 in
+// FP64 with the working-precision faces widened; r stored to the working
+// precision right-hand side. Returns ||r||_2.
+template <typename T>
+__device__ __forceinline__ double resid64_cell(const Lv<T>& L, int i1, int i2)
 {
     const double ih2 = static_cast<double>(L.n) * L.n;
-    return 1.0 - ih2 * apply_h2<float, double>(L.kx, L.ky, L.u64, L.n, i1, i2);
+    return 1.0 - ih2 * apply_h2<T, double>(L.kx, L.ky, L.u64, L.n, i1, i2);
 }
 
-template <typename TM>
-__device__ double resid64_to_rhs(const TM& tm, const Lv<float>& L, double* red)
+template <typename TM, typename T>
+__device__ double resid64_to_rhs(const TM& tm, const Lv<T>& L, double* red)
 {
     const int n = L.n;
     double acc = 0.0;
     for (int p = tm.rank(); p < n * n; p += tm.size()) {
         const int i2 = p / n;
         const double r = resid64_cell(L, p - i2 * n, i2);
-        L.bc[p] = static_cast<float>(r);
+        L.bc[p] = static_cast<T>(r);
         acc += r * r;
     }
     return sqrt(team_sum(tm, acc, red));

@@ -140,7 +140,7 @@ __global__ void kb_level0(FmgArgs A, int B)
             }
         }
         // exact solution of level 0 with f = 1 (the first node of Fig. FMG)
-        double* x = MX ? L0.u64 : reinterpret_cast<double*>(L0.u);
+        double* x = (MX || A.refine) ? L0.u64 : reinterpret_cast<double*>(L0.u);
         const double h2 = 1.0 / (static_cast<double>(n0) * n0);
         for (int r = 0; r < N; ++r) {
             double v = h2;
@@ -350,7 +350,8 @@ __global__ void kb_prolong(FmgArgs A, int t, int B)
     }
 }
 
-// Mixed forms: bc = 1 - A u64 (FP64 residual, FP32 faces widened).
+// Refinement path: bc = 1 - A u64 (FP64 residual, working-precision faces widened).
+template <typename T>
 __global__ void kb_resid64(FmgArgs A, int t, int B)
 {
     const int n = A.lv[t].n;
@@ -361,12 +362,13 @@ __global__ void kb_resid64(FmgArgs A, int t, int B)
         if (inactive(A, i)) continue;
         const int p = static_cast<int>(idx - i * per);
         const int i2 = p / n;
-        const Lv<float> L = view<float>(A, t, i);
-        L.bc[p] = static_cast<float>(resid64_cell(L, p - i2 * n, i2));
+        const Lv<T> L = view<T>(A, t, i);
+        L.bc[p] = static_cast<T>(resid64_cell(L, p - i2 * n, i2));
     }
 }
 
-// Mixed forms: u64 += e.
+// Refinement path: u64 += e.
+template <typename T>
 __global__ void kb_update64(FmgArgs A, int t, int B)
 {
     const int n = A.lv[t].n;
@@ -376,13 +378,13 @@ __global__ void kb_update64(FmgArgs A, int t, int B)
         const int i = static_cast<int>(idx / per);
         if (inactive(A, i)) continue;
         const int p = static_cast<int>(idx - i * per);
-        at<double>(A.lv[t].u64, i)[p] += static_cast<double>(at<float>(A.lv[t].u, i)[p]);
+        at<double>(A.lv[t].u64, i)[p] += static_cast<double>(at<T>(A.lv[t].u, i)[p]);
     }
 }
 
-// Per-sample residual norm (one CTA per sample, deterministic); the mixed forms
-// also leave r in bc for the next correction.
-template <typename T, bool MX>
+// Per-sample residual norm (one CTA per sample, deterministic); the refinement
+// path also leaves r in bc for the next correction.
+template <typename T, bool REF>
 __global__ void __launch_bounds__(256) kb_resnorm(FmgArgs A, int t, int B)
 {
     __shared__ double red[48];
@@ -390,7 +392,7 @@ __global__ void __launch_bounds__(256) kb_resnorm(FmgArgs A, int t, int B)
     for (int i = blockIdx.x; i < B; i += gridDim.x) {
         const Lv<T> L = view<T>(A, t, i);
         double nr;
-        if constexpr (MX) nr = resid64_to_rhs(tm, L, red);
+        if constexpr (REF) nr = resid64_to_rhs(tm, L, red);
         else nr = resid_norm_ones(tm, L, red);
         if (threadIdx.x == 0) A.norms[i] = nr;
     }
@@ -508,7 +510,7 @@ void level_strides(const mlqmc_problem& p, int Ka, int t, size_t st[kPoolArrs])
     st[kIdiag] = align256(es * n * n);
     st[kK] = align256(es * n * n);
     st[kG] = align256(es * static_cast<size_t>(std::max(Ka, 1)) * n);
-    st[kU64] = is_mixed(p) ? align256(8 * n * n) : 0;
+    st[kU64] = (is_mixed(p) || p.refine_rtol > 0.0) ? align256(8 * n * n) : 0;
 }
 
 size_t level_bytes_per_sample(const mlqmc_problem& p, int Ka, int t)
@@ -591,6 +593,7 @@ FmgArgs base_args(mlqmc_ctx* c)
     A.queue = c->d_queue;
     A.status = c->d_status;
     A.norms = c->d_norms;
+    A.refine = (is_mixed(c->p) || c->p.refine_rtol > 0.0) ? 1 : 0;
     return A;
 }
 
@@ -771,16 +774,17 @@ mlqmc_status vcycle_batched(mlqmc_ctx* c, const FmgArgs& A, int t_top, int B, bo
     return last_error();
 }
 
-// Host loop of the converged form on a large level: per-sample norms, active
-// flags, one more cycle for the active samples, until none is active.
-template <typename T, bool MX>
+// Host loop of the converged form on level t (refinement path): per-sample
+// FP64 residual norms (r left in bc), active flags, then mu0 V-cycles on the
+// correction of the active samples and u64 += e, until none is active.
+template <typename T>
 mlqmc_status converge_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cudaStream_t st)
 {
     const int64_t n = c->p.coarse_cells << t;
     for (int it = 0;; ++it) {
         {
             Timed tm(c, kProfReduce, st);
-            kb_resnorm<T, MX><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
+            kb_resnorm<T, true><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
         }
         if (!ok(cudaMemsetAsync(c->d_count, 0, sizeof(int), st))) return MLQMC_ERR_CUDA;
         {
@@ -790,6 +794,7 @@ mlqmc_status converge_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cuda
         if (!ok(cudaMemcpyAsync(c->h_count, c->d_count, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
             !ok(cudaStreamSynchronize(st)))
             return MLQMC_ERR_CUDA;
+        c->last_iters[t] = std::max(c->last_iters[t], it);
         if (*c->h_count == 0) break;
         if (it >= c->p.refine_max_iter) {
             c->host_status |= kStatusNotConverged;
@@ -797,65 +802,71 @@ mlqmc_status converge_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cuda
         }
         FmgArgs M = A;
         M.active = c->d_active;
-        if constexpr (MX) {
-            if (zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
-            for (int m = 0; m < c->p.mu0; ++m) {
-                mlqmc_status s = vcycle_batched<T>(c, M, t, B, false, st);
-                if (s != MLQMC_OK) return s;
-            }
-            Timed tm(c, kProfTransfer, st);
-            kb_update64<<<grid_for(c, B * n * n), 256, 0, st>>>(M, t, B);
-        } else {
-            mlqmc_status s = vcycle_batched<T>(c, M, t, B, true, st);
+        if (zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
+        for (int m = 0; m < c->p.mu0; ++m) {
+            mlqmc_status s = vcycle_batched<T>(c, M, t, B, false, st);
             if (s != MLQMC_OK) return s;
         }
+        Timed tm(c, kProfTransfer, st);
+        kb_update64<T><<<grid_for(c, B * n * n), 256, 0, st>>>(M, t, B);
     }
     return last_error();
 }
 
-// FMG stages 1..Lmax for the B_t samples that reach each level.
+// FMG stages 1..Lmax for the B_t samples that reach each level. Refinement
+// path (mixed forms, converged FP64 form): solutions in u64, each stage starts
+// with one correction step of mu0 V-cycles, then (rtol > 0) repeats it until
+// converged. Otherwise (fixed-cycle FP64 form) mu0 V-cycles act on u itself.
 template <typename T, bool MX>
 mlqmc_status fmg_stages(mlqmc_ctx* c, const FmgArgs& A, const int* Bt, int Lmax, double* d_usol, cudaStream_t st)
 {
+    const bool refine = A.refine != 0;
     size_t uoff = static_cast<size_t>(A.lv[0].n) * A.lv[0].n;
     for (int t = 1; t <= Lmax; ++t) {
         const int B = Bt[t];
         if (B == 0) break;
         const int64_t n = c->p.coarse_cells << t;
-        {
-            Timed tm(c, kProfTransfer, st);
-            kb_prolong<T, false, MX><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
-        }
-        if constexpr (MX) {
-            // refinement step: r = 1 - A u64 (FP64), mu0 FP32 V-cycles on A e = r, u64 += e
+        if (refine) {
             {
                 Timed tm(c, kProfTransfer, st);
-                kb_resid64<<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
+                kb_prolong<T, false, true><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
+            }
+            {
+                Timed tm(c, kProfTransfer, st);
+                kb_resid64<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
             }
             if (zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
             for (int m = 0; m < c->p.mu0; ++m) {
                 mlqmc_status s = vcycle_batched<T>(c, A, t, B, false, st);
                 if (s != MLQMC_OK) return s;
             }
-            Timed tm(c, kProfTransfer, st);
-            kb_update64<<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
+            {
+                Timed tm(c, kProfTransfer, st);
+                kb_update64<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
+            }
+            if (c->p.refine_rtol > 0.0) {
+                mlqmc_status s = converge_batched<T>(c, A, t, B, st);
+                if (s != MLQMC_OK) return s;
+            }
         } else {
+            {
+                Timed tm(c, kProfTransfer, st);
+                kb_prolong<T, false, false><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
+            }
             for (int m = 0; m < c->p.mu0; ++m) {
                 mlqmc_status s = vcycle_batched<T>(c, A, t, B, true, st);
                 if (s != MLQMC_OK) return s;
             }
         }
-        if (c->p.refine_rtol > 0.0) {
-            mlqmc_status s = converge_batched<T, MX>(c, A, t, B, st);
-            if (s != MLQMC_OK) return s;
-        }
         {
             Timed tm(c, kProfReduce, st);
-            kb_qoi<T, MX><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
+            if (refine) kb_qoi<T, true><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
+            else kb_qoi<T, false><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
         }
         if (d_usol) {
             Timed tm(c, kProfReduce, st);
-            kb_u_out<T, MX><<<grid_for(c, n * n), 256, 0, st>>>(A, t, d_usol + uoff);
+            if (refine) kb_u_out<T, true><<<grid_for(c, n * n), 256, 0, st>>>(A, t, d_usol + uoff);
+            else kb_u_out<T, false><<<grid_for(c, n * n), 256, 0, st>>>(A, t, d_usol + uoff);
             uoff += static_cast<size_t>(n) * n;
         }
     }
@@ -886,6 +897,7 @@ mlqmc_status run_chunk(mlqmc_ctx* c, int count, const int* Bt, int Lmax, double*
         const int64_t n0 = p.coarse_cells;
         Timed tm(c, kProfReduce, st);
         if (is_mixed(p)) kb_u_out<float, true><<<grid_for(c, n0 * n0), 256, 0, st>>>(A, 0, d_usol);
+        else if (A.refine) kb_u_out<double, true><<<grid_for(c, n0 * n0), 256, 0, st>>>(A, 0, d_usol);
         else kb_u_out<double, false><<<grid_for(c, n0 * n0), 256, 0, st>>>(A, 0, d_usol);
     }
     s = is_mixed(p) ? fmg_stages<float, true>(c, A, Bt, Lmax, d_usol, st)
@@ -1469,6 +1481,16 @@ extern "C" mlqmc_status mlqmc_fmg_fields_noalloc(int32_t coarse_cells, int32_t n
     const int grid = std::min<int>(count, MLQMC_NOALLOC_SLOTS);
     k_fmg_noalloc<<<grid, 256, smem, static_cast<cudaStream_t>(stream)>>>(A, d_k, k_stride, count, d_F);
     return ok(cudaGetLastError()) ? MLQMC_OK : MLQMC_ERR_CUDA;
+}
+
+extern "C" mlqmc_status mlqmc_last_iterations(mlqmc_ctx* c, int32_t* out)
+{
+    if (!c || !out) return MLQMC_ERR_INVALID_ARG;
+    for (int t = 0; t < c->p.n_levels; ++t) {
+        out[t] = c->last_iters[t];
+        c->last_iters[t] = 0;
+    }
+    return MLQMC_OK;
 }
 
 extern "C" int64_t mlqmc_launch_count(const mlqmc_ctx* c)

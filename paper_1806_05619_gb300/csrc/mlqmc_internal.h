@@ -133,6 +133,7 @@ struct mlqmc_ctx {
 
     int* d_status = nullptr;  // deferred device status bits
     int host_status = 0;      // deferred status found on the host (converged-form loops)
+    int last_iters[MLQMC_MAX_LEVELS] = {};  // extra cycles / refinement steps per level, last converged-form call
     int* d_queue = nullptr;   // work-queue counter
     int64_t launches = 0;
 };
