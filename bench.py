@@ -336,7 +336,7 @@ def run_ours(args):
         else:
             roof.update(bound="alu", achieved=m["flops"] / t_s / 1e12, peak=FP64_TFLOPS, unit="TFLOP/s",
                         peak_source="nominal FP64 1.25 TFLOP/s (probe 1.20)")
-        roof.update(kernel="kb_gs<double> (batched red-black sweeps)", algorithmic_bytes_per_step=m["bytes"],
+        roof.update(kernel="batched red-black sweeps (kb_gs / kb_rbgs_tile)", algorithmic_bytes_per_step=m["bytes"],
                     flops_per_step=m["flops"])
     else:
         ops = small_fp64_ops(cfg, work, Ka)

@@ -25,7 +25,7 @@ struct ArrDesc {
 
 struct LevelDesc {
     int n;
-    ArrDesc u, bc, kx, ky, idiag, k, G, u64;
+    ArrDesc u, bc, kx, ky, idiag, k, G, u64, u2;  // u2: ping-pong partner of u for the tiled smoother
 };
 
 template <typename T>

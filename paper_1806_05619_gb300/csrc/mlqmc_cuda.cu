@@ -305,6 +305,105 @@ __global__ void kb_gs(FmgArgs A, int t, int B, int colour, int ones)
     }
 }
 
+// NS full red-black sweeps of one TILE x TILE tile per CTA iteration (temporal
+// blocking, FP32): u, 1/D and b are staged in shared memory with a halo of 4
+// cells on each side (128-bit loads from 16-byte aligned rows, zeros outside
+// the domain, which is the Dirichlet ghost value), the x and y faces of the
+// same region too; the NS sweeps consume 2*NS of that halo.
+// u is read from u and written to u2 (ping-pong, so no tile reads a
+// neighbour's half-updated cells). Phase p updates its colour on the tile
+// grown by H-1-p; the result equals NS passes of kb_gs over both colours.
+// first: colour of the first half sweep (0 red for pre-smoothing, 1 black).
+template <int TILE, int NS>
+__global__ void __launch_bounds__(256) kb_rbgs_tile(FmgArgs A, int t, int B, int ones, int first)
+{
+    static_assert(NS == 1 || NS == 2, "one or two sweeps per launch");
+    constexpr int H = 4;              // staged halo: keeps x0 - H a multiple of 4 (16-byte loads)
+    constexpr int HN = 2 * NS;        // halo the NS sweeps consume
+    constexpr int SU = TILE + 2 * H;  // staged side (multiple of 4)
+    constexpr int V = SU / 4;         // float4 per staged row
+    static_assert(SU % 4 == 0, "staged rows are whole float4");
+    extern __shared__ float4 smraw4[];
+    float* su = reinterpret_cast<float*>(smraw4);  // SU x SU
+    float* sid = su + SU * SU;                       // SU x SU
+    float* sb = sid + SU * SU;                       // SU x SU
+    float* sky = sb + SU * SU;                       // (SU + 1) face rows x SU
+    float* skx = sky + (SU + 1) * SU;                // SU rows x (SU + 1) faces
+    const int n = A.lv[t].n;
+    const int tx_n = n / TILE;
+    const int64_t per = static_cast<int64_t>(tx_n) * tx_n;
+    const float h2 = 1.0f / (static_cast<float>(n) * static_cast<float>(n));
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t tile = blockIdx.x; tile < B * per; tile += gridDim.x) {
+        const int i = static_cast<int>(tile / per);
+        if (inactive(A, i)) continue;
+        const int tr = static_cast<int>(tile - i * per);
+        const int y0 = (tr / tx_n) * TILE, x0 = (tr % tx_n) * TILE;
+        const Lv<float> L = view<float>(A, t, i);
+        float* uo = at<float>(A.lv[t].u2, i);
+        // cell arrays: rows y0-H.., columns x0-H.. in float4 (x0-H is a multiple of 4)
+#pragma unroll 4
+        for (int q = threadIdx.x; q < SU * V; q += blockDim.x) {
+            const int r = q / V, v = q - (q / V) * V;
+            const int gy = y0 - H + r, gx = x0 - H + 4 * v;
+            const bool in = gy >= 0 && gy < n && gx >= 0 && gx < n;
+            const size_t o = static_cast<size_t>(gy) * n + gx;
+            reinterpret_cast<float4*>(su)[q] = in ? *reinterpret_cast<const float4*>(L.u + o) : z4;
+            reinterpret_cast<float4*>(sid)[q] = in ? *reinterpret_cast<const float4*>(L.idiag + o) : z4;
+            reinterpret_cast<float4*>(sb)[q] =
+                in ? (ones ? make_float4(1.f, 1.f, 1.f, 1.f) : *reinterpret_cast<const float4*>(L.bc + o)) : z4;
+        }
+        // y faces: face rows y0-H .. y0-H+SU, columns as above
+#pragma unroll 4
+        for (int q = threadIdx.x; q < (SU + 1) * V; q += blockDim.x) {
+            const int r = q / V, v = q - (q / V) * V;
+            const int gy = y0 - H + r, gx = x0 - H + 4 * v;
+            const bool in = gy >= 0 && gy <= n && gx >= 0 && gx < n;
+            reinterpret_cast<float4*>(sky)[q] = in ? *reinterpret_cast<const float4*>(L.ky + static_cast<size_t>(gy) * n + gx) : z4;
+        }
+        // x faces: rows y0-H.., faces x0-H .. x0-H+SU (row pitch n+1: scalar loads)
+#pragma unroll 4
+        for (int q = threadIdx.x; q < SU * (SU + 1); q += blockDim.x) {
+            const int r = q / (SU + 1), f = q - (q / (SU + 1)) * (SU + 1);
+            const int gy = y0 - H + r, gx = x0 - H + f;
+            skx[q] = (gy >= 0 && gy < n && gx >= 0 && gx <= n) ? L.kx[static_cast<size_t>(gy) * (n + 1) + gx] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ph = 0; ph < 2 * NS; ++ph) {
+            const int colour = (first + ph) & 1;
+            const int g = HN - 1 - ph;  // growth of the updated region beyond the tile
+            const int side = TILE + 2 * g;
+            const int half = side / 2;
+            for (int q = threadIdx.x; q < side * half; q += blockDim.x) {
+                const int ry = q / half;
+                const int gy = y0 - g + ry;
+                const int rx = 2 * (q - ry * half) + ((gy + x0 - g + colour) & 1);
+                const int gx = x0 - g + rx;
+                if (gy < 0 || gy >= n || gx < 0 || gx >= n) continue;
+                const int sy = gy - y0 + H, sx = gx - x0 + H;
+                const int c0 = sy * SU + sx;
+                const float* kr = skx + sy * (SU + 1);
+                float acc = h2 * sb[c0];
+                acc += kr[sx] * su[c0 - 1];
+                acc += kr[sx + 1] * su[c0 + 1];
+                acc += sky[sy * SU + sx] * su[c0 - SU];
+                acc += sky[(sy + 1) * SU + sx] * su[c0 + SU];
+                su[c0] = acc * sid[c0];
+            }
+            __syncthreads();
+        }
+        constexpr int TV = TILE / 4;
+        for (int q = threadIdx.x; q < TILE * TV; q += blockDim.x) {
+            const int ry = q / TV, v = q - (q / TV) * TV;
+            const float* src = su + (ry + H) * SU + H + 4 * v;
+            *reinterpret_cast<float4*>(uo + static_cast<size_t>(y0 + ry) * n + x0 + 4 * v) =
+                make_float4(src[0], src[1], src[2], src[3]);
+        }
+        __syncthreads();
+    }
+}
+
 // bc of level t-1 = mean over children of (b - A u) on level t.
 template <typename T>
 __global__ void kb_resid_restrict(FmgArgs A, int t, int B, int ones)
@@ -511,6 +610,7 @@ void level_strides(const mlqmc_problem& p, int Ka, int t, size_t st[kPoolArrs])
     st[kK] = align256(es * n * n);
     st[kG] = align256(es * static_cast<size_t>(std::max(Ka, 1)) * n);
     st[kU64] = (is_mixed(p) || p.refine_rtol > 0.0) ? align256(8 * n * n) : 0;
+    st[kU2] = t > 0 ? align256(es * n * n) : 0;
 }
 
 size_t level_bytes_per_sample(const mlqmc_problem& p, int Ka, int t)
@@ -580,7 +680,7 @@ FmgArgs base_args(mlqmc_ctx* c)
         const LevelPool& P = c->pools[t];
         LevelDesc& d = A.lv[t];
         d.n = c->p.coarse_cells << t;
-        ArrDesc* arr[kPoolArrs] = {&d.u, &d.bc, &d.kx, &d.ky, &d.idiag, &d.k, &d.G, &d.u64};
+        ArrDesc* arr[kPoolArrs] = {&d.u, &d.bc, &d.kx, &d.ky, &d.idiag, &d.k, &d.G, &d.u64, &d.u2};
         for (int a = 0; a < kPoolArrs; ++a) {
             arr[a]->base = P.mem ? P.mem + P.off[a] : nullptr;
             arr[a]->stride = P.stride[a];
@@ -737,19 +837,73 @@ mlqmc_status zero_u(mlqmc_ctx* c, int t, int B, cudaStream_t st)
 // V-cycle on level t_top (>= 1) for samples 0..B-1: batched sweeps and
 // transfers down to level 1, the coarse solve on level 0, and back up. ones:
 // the top right-hand side is 1 (FP64 form), else bc of t_top (mixed correction).
+// Swap the roles of u and u2 on level t (after a ping-pong smoothing launch).
+void swap_u(mlqmc_ctx* c, FmgArgs& A, int t)
+{
+    std::swap(c->pools[t].off[kU], c->pools[t].off[kU2]);
+    std::swap(A.lv[t].u, A.lv[t].u2);
+}
+
+template <int TILE, int NS>
+constexpr size_t tile_smem()
+{
+    constexpr int SU = TILE + 8;
+    return sizeof(float) * (3 * SU * SU + 2 * (SU + 1) * SU);
+}
+
+template <int TILE, int NS>
+void launch_tile(mlqmc_ctx* c, const FmgArgs& A, int t, int B, int ones, int first, cudaStream_t st)
+{
+    const int64_t n = c->p.coarse_cells << t;
+    const int64_t tiles = B * (n / TILE) * (n / TILE);
+    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(tiles, c->sm_count * 16)));
+    kb_rbgs_tile<TILE, NS><<<grid, 256, tile_smem<TILE, NS>(), st>>>(A, t, B, ones, first);
+}
+
+template <int TILE>
+bool tile_attrs()
+{
+    return cudaFuncSetAttribute(kb_rbgs_tile<TILE, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(tile_smem<TILE, 2>())) == cudaSuccess &&
+           cudaFuncSetAttribute(kb_rbgs_tile<TILE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(tile_smem<TILE, 1>())) == cudaSuccess;
+}
+
+// nsweeps full red-black sweeps of level t (first: colour of the first half
+// sweep). FP32: two sweeps per tiled launch (memory-bound, the halo work is
+// cheap). FP64 and sides other than 8, 16 or a multiple of 32: two kb_gs
+// launches per sweep (FP64 is arithmetic-bound on GB300 and the tiles' halo
+// updates would add work).
 template <typename T>
-mlqmc_status vcycle_batched(mlqmc_ctx* c, const FmgArgs& A, int t_top, int B, bool ones, cudaStream_t st)
+void smooth(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int first, int ones, cudaStream_t st)
+{
+    const int64_t n = c->p.coarse_cells << t;
+    const int tile = sizeof(T) == 8 ? 0 : (n >= 32 && n % 32 == 0 ? 32 : (n == 16 ? 16 : (n == 8 ? 8 : 0)));
+    while (nsweeps > 0) {
+        const int ns = nsweeps >= 2 ? 2 : 1;
+        Timed tm(c, kProfSmooth, st);
+        if (tile == 0) {
+            for (int h = 0; h < 2 * ns; ++h)
+                kb_gs<T><<<grid_for(c, B * n * n / 2), 256, 0, st>>>(A, t, B, (first + h) & 1, ones);
+            nsweeps -= ns;
+            continue;
+        }
+        if (tile == 32) (ns == 2 ? launch_tile<32, 2> : launch_tile<32, 1>)(c, A, t, B, ones, first, st);
+        else if (tile == 16) (ns == 2 ? launch_tile<16, 2> : launch_tile<16, 1>)(c, A, t, B, ones, first, st);
+        else (ns == 2 ? launch_tile<8, 2> : launch_tile<8, 1>)(c, A, t, B, ones, first, st);
+        swap_u(c, A, t);
+        nsweeps -= ns;
+    }
+}
+
+template <typename T>
+mlqmc_status vcycle_batched(mlqmc_ctx* c, FmgArgs& A, int t_top, int B, bool ones, cudaStream_t st)
 {
     for (int t = t_top; t >= 1; --t) {
         const int64_t n = c->p.coarse_cells << t;
         const int top_ones = (t == t_top && ones) ? 1 : 0;
         if (t < t_top && zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
-        for (int s = 0; s < c->p.nu1; ++s) {
-            for (int colour = 0; colour < 2; ++colour) {
-                Timed tm(c, kProfSmooth, st);
-                kb_gs<T><<<grid_for(c, B * n * n / 2), 256, 0, st>>>(A, t, B, colour, top_ones);
-            }
-        }
+        smooth<T>(c, A, t, B, c->p.nu1, 0, top_ones, st);
         Timed tm(c, kProfTransfer, st);
         kb_resid_restrict<T><<<grid_for(c, B * n * n / 4), 256, 0, st>>>(A, t, B, top_ones);
     }
@@ -764,12 +918,7 @@ mlqmc_status vcycle_batched(mlqmc_ctx* c, const FmgArgs& A, int t_top, int B, bo
             Timed tm(c, kProfTransfer, st);
             kb_prolong<T, true, false><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
         }
-        for (int s = 0; s < c->p.nu2; ++s) {
-            for (int colour = 1; colour >= 0; --colour) {
-                Timed tm(c, kProfSmooth, st);
-                kb_gs<T><<<grid_for(c, B * n * n / 2), 256, 0, st>>>(A, t, B, colour, top_ones);
-            }
-        }
+        smooth<T>(c, A, t, B, c->p.nu2, 1, top_ones, st);
     }
     return last_error();
 }
@@ -778,7 +927,7 @@ mlqmc_status vcycle_batched(mlqmc_ctx* c, const FmgArgs& A, int t_top, int B, bo
 // FP64 residual norms (r left in bc), active flags, then mu0 V-cycles on the
 // correction of the active samples and u64 += e, until none is active.
 template <typename T>
-mlqmc_status converge_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cudaStream_t st)
+mlqmc_status converge_batched(mlqmc_ctx* c, FmgArgs& A, int t, int B, cudaStream_t st)
 {
     const int64_t n = c->p.coarse_cells << t;
     for (int it = 0;; ++it) {
@@ -800,15 +949,15 @@ mlqmc_status converge_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cuda
             c->host_status |= kStatusNotConverged;
             break;
         }
-        FmgArgs M = A;
-        M.active = c->d_active;
-        if (zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
-        for (int m = 0; m < c->p.mu0; ++m) {
-            mlqmc_status s = vcycle_batched<T>(c, M, t, B, false, st);
-            if (s != MLQMC_OK) return s;
+        A.active = c->d_active;
+        mlqmc_status s = zero_u(c, t, B, st);
+        for (int m = 0; m < c->p.mu0 && s == MLQMC_OK; ++m) s = vcycle_batched<T>(c, A, t, B, false, st);
+        if (s == MLQMC_OK) {
+            Timed tm(c, kProfTransfer, st);
+            kb_update64<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
         }
-        Timed tm(c, kProfTransfer, st);
-        kb_update64<T><<<grid_for(c, B * n * n), 256, 0, st>>>(M, t, B);
+        A.active = nullptr;
+        if (s != MLQMC_OK) return s;
     }
     return last_error();
 }
@@ -818,7 +967,7 @@ mlqmc_status converge_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cuda
 // with one correction step of mu0 V-cycles, then (rtol > 0) repeats it until
 // converged. Otherwise (fixed-cycle FP64 form) mu0 V-cycles act on u itself.
 template <typename T, bool MX>
-mlqmc_status fmg_stages(mlqmc_ctx* c, const FmgArgs& A, const int* Bt, int Lmax, double* d_usol, cudaStream_t st)
+mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, double* d_usol, cudaStream_t st)
 {
     const bool refine = A.refine != 0;
     size_t uoff = static_cast<size_t>(A.lv[0].n) * A.lv[0].n;
@@ -1096,6 +1245,11 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
         return MLQMC_ERR_OOM;
     }
 
+    // shared memory of the tiled smoother
+    if (!(tile_attrs<32>() && tile_attrs<16>() && tile_attrs<8>())) {
+        free_ctx(c);
+        return MLQMC_ERR_CUDA;
+    }
     // tensor-core KL tables (mixed TF32 form): Psi of every level with a whole number of 128-cell tiles
     if (p->precision == MLQMC_MIXED_TF32) {
         const int kpad = mlqmc_kl::kpad_for(p->n_modes);
@@ -1438,6 +1592,7 @@ extern "C" mlqmc_status mlqmc_fmg_fields_noalloc(int32_t coarse_cells, int32_t n
         size_t st[kPoolArrs];
         level_strides(p, 0, t, st);
         st[kG] = 0;
+        st[kU2] = 0;
         for (int a = 0; a < kPoolArrs; ++a) {
             offs[t][a] = off;
             off += st[a];
@@ -1468,7 +1623,7 @@ extern "C" mlqmc_status mlqmc_fmg_fields_noalloc(int32_t coarse_cells, int32_t n
     for (int t = 0; t < n_levels; ++t) {
         LevelDesc& d = A.lv[t];
         d.n = coarse_cells << t;
-        ArrDesc* arr[kPoolArrs] = {&d.u, &d.bc, &d.kx, &d.ky, &d.idiag, &d.k, &d.G, &d.u64};
+        ArrDesc* arr[kPoolArrs] = {&d.u, &d.bc, &d.kx, &d.ky, &d.idiag, &d.k, &d.G, &d.u64, &d.u2};
         for (int a = 0; a < kPoolArrs; ++a) {
             arr[a]->base = scratch + offs[t][a];
             arr[a]->stride = MLQMC_NOALLOC_SLOT_BYTES;

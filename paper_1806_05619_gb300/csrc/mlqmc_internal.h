@@ -64,7 +64,7 @@ enum ProfKind {
 
 // Pool of per-sample arrays of one level: array a of sample i lives at
 // mem + off[a] + i * stride[a].
-enum PoolArr { kU = 0, kBc, kKx, kKy, kIdiag, kK, kG, kU64, kPoolArrs };
+enum PoolArr { kU = 0, kBc, kKx, kKy, kIdiag, kK, kG, kU64, kU2, kPoolArrs };
 
 struct LevelPool {
     unsigned char* mem = nullptr;
