@@ -284,27 +284,26 @@ __device__ void resid_restrict(const TM& tm, const Lv<T>& F, const T* b, T* bc)
     tm.sync();
 }
 
-template <typename T>
-__device__ __forceinline__ T ghost(const T* e, int nc, int I1, int I2)
-{
-    T sg = T(1);
-    if (I1 < 0) { I1 = 0; sg = -sg; }
-    if (I1 >= nc) { I1 = nc - 1; sg = -sg; }
-    if (I2 < 0) { I2 = 0; sg = -sg; }
-    if (I2 >= nc) { I2 = nc - 1; sg = -sg; }
-    return sg * e[I2 * nc + I1];
-}
-
-// Bilinear cell-centred prolongation (9,3,3,1)/16 of fine cell (i1, i2), odd
-// reflection at the Dirichlet boundary.
+// Bilinear cell-centred prolongation (9,3,3,1)/16 of fine cell (i1, i2):
+// 9/16 of the parent a, 3/16 of the coarse neighbours b (along x1) and c
+// (along x2), 1/16 of the diagonal one d, with odd reflection across the
+// Dirichlet boundary (a neighbour outside the grid is minus its mirror).
 template <typename S, typename D>
 __device__ __forceinline__ D prolong_cell(const S* e, int nc, int i1, int i2)
 {
     const int I1 = i1 >> 1, I2 = i2 >> 1;
-    const int s1 = (i1 & 1) ? 1 : -1, s2 = (i2 & 1) ? 1 : -1;
-    const D v = D(9) * D(ghost(e, nc, I1, I2)) + D(3) * D(ghost(e, nc, I1 + s1, I2)) +
-                D(3) * D(ghost(e, nc, I1, I2 + s2)) + D(ghost(e, nc, I1 + s1, I2 + s2));
-    return v * D(0.0625);
+    const int J1 = (i1 & 1) ? I1 + 1 : I1 - 1;
+    const int J2 = (i2 & 1) ? I2 + 1 : I2 - 1;
+    const bool o1 = J1 < 0 || J1 >= nc, o2 = J2 < 0 || J2 >= nc;
+    const int K1 = o1 ? I1 : J1, K2 = o2 ? I2 : J2;
+    const D a = D(e[I2 * nc + I1]);
+    const D b0 = D(e[I2 * nc + K1]);
+    const D c0 = D(e[K2 * nc + I1]);
+    const D d0 = D(e[K2 * nc + K1]);
+    const D b = o1 ? -b0 : b0;
+    const D c = o2 ? -c0 : c0;
+    const D d = (o1 != o2) ? -d0 : d0;
+    return fma(D(0.5625), a, fma(D(0.1875), b + c, D(0.0625) * d));
 }
 
 template <typename S, typename D, bool ADD, typename TM>
@@ -430,6 +429,29 @@ __device__ double resid_norm_ones(const TM& tm, const Lv<T>& L, double* red)
     return sqrt(team_sum(tm, acc, red));
 }
 
+// Exact widening of a positive normal float (a face coefficient) to double by
+// re-biasing its exponent on the integer pipe: the 8-bit exponent e becomes
+// e - 127 + 1023 and the 23-bit mantissa moves to the top of the 52-bit one.
+__device__ __forceinline__ double widen_pos(float f)
+{
+    const unsigned long long b = static_cast<unsigned long long>(__float_as_uint(f) & 0x7FFFFFFFu);
+    return __longlong_as_double(static_cast<long long>((b << 29) + (896ull << 52)));
+}
+__device__ __forceinline__ double widen_pos(double f) { return f; }
+
+// (A u)_P h^2 in flux form, FP64, from working-precision faces.
+template <typename T>
+__device__ __forceinline__ double apply_h2_64(const T* kx, const T* ky, const double* u, int n, int i1, int i2)
+{
+    const int p = i2 * n + i1;
+    const double up = u[p];
+    double acc = widen_pos(kx[i2 * (n + 1) + i1]) * (up - (i1 > 0 ? u[p - 1] : 0.0));
+    acc = fma(widen_pos(kx[i2 * (n + 1) + i1 + 1]), up - (i1 < n - 1 ? u[p + 1] : 0.0), acc);
+    acc = fma(widen_pos(ky[i2 * n + i1]), up - (i2 > 0 ? u[p - n] : 0.0), acc);
+    acc = fma(widen_pos(ky[(i2 + 1) * n + i1]), up - (i2 < n - 1 ? u[p + n] : 0.0), acc);
+    return acc;
+}
+
 // Refinement path (mixed forms, and the converged FP64 form): r = 1 - A u64 in
 // FP64 with the working-precision faces widened; r stored to the working
 // precision right-hand side. Returns ||r||_2.
@@ -437,7 +459,7 @@ template <typename T>
 __device__ __forceinline__ double resid64_cell(const Lv<T>& L, int i1, int i2)
 {
     const double ih2 = static_cast<double>(L.n) * L.n;
-    return 1.0 - ih2 * apply_h2<T, double>(L.kx, L.ky, L.u64, L.n, i1, i2);
+    return fma(-ih2, apply_h2_64<T>(L.kx, L.ky, L.u64, L.n, i1, i2), 1.0);
 }
 
 template <typename TM, typename T>

@@ -314,7 +314,9 @@ __global__ void kb_gs(FmgArgs A, int t, int B, int colour, int ones)
 // neighbour's half-updated cells). Phase p updates its colour on the tile
 // grown by H-1-p; the result equals NS passes of kb_gs over both colours.
 // first: colour of the first half sweep (0 red for pre-smoothing, 1 black).
-template <int TILE, int NS>
+// PROLONG: the staged u first receives the coarse-grid correction P e from
+// level t-1 (post-smoothing of the V-cycle), as kb_prolong would add it.
+template <int TILE, int NS, bool PROLONG>
 __global__ void __launch_bounds__(256) kb_rbgs_tile(FmgArgs A, int t, int B, int ones, int first)
 {
     static_assert(NS == 1 || NS == 2, "one or two sweeps per launch");
@@ -352,6 +354,16 @@ __global__ void __launch_bounds__(256) kb_rbgs_tile(FmgArgs A, int t, int B, int
             reinterpret_cast<float4*>(sid)[q] = in ? *reinterpret_cast<const float4*>(L.idiag + o) : z4;
             reinterpret_cast<float4*>(sb)[q] =
                 in ? (ones ? make_float4(1.f, 1.f, 1.f, 1.f) : *reinterpret_cast<const float4*>(L.bc + o)) : z4;
+        }
+        if constexpr (PROLONG) {
+            // coarse-grid correction first: u += P e on every staged cell of the domain
+            __syncthreads();
+            const float* e = at<float>(A.lv[t - 1].u, i);
+            const int nc = n >> 1;
+            for (int q = threadIdx.x; q < SU * SU; q += blockDim.x) {
+                const int gy = y0 - H + q / SU, gx = x0 - H + q % SU;
+                if (gy >= 0 && gy < n && gx >= 0 && gx < n) su[q] += prolong_cell<float, float>(e, nc, gx, gy);
+            }
         }
         // y faces: face rows y0-H .. y0-H+SU, columns as above
 #pragma unroll 4
@@ -852,21 +864,29 @@ constexpr size_t tile_smem()
 }
 
 template <int TILE, int NS>
-void launch_tile(mlqmc_ctx* c, const FmgArgs& A, int t, int B, int ones, int first, cudaStream_t st)
+void launch_tile(mlqmc_ctx* c, const FmgArgs& A, int t, int B, int ones, int first, bool pro, cudaStream_t st)
 {
     const int64_t n = c->p.coarse_cells << t;
     const int64_t tiles = B * (n / TILE) * (n / TILE);
     const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(tiles, c->sm_count * 16)));
-    kb_rbgs_tile<TILE, NS><<<grid, 256, tile_smem<TILE, NS>(), st>>>(A, t, B, ones, first);
+    if (pro) kb_rbgs_tile<TILE, NS, true><<<grid, 256, tile_smem<TILE, NS>(), st>>>(A, t, B, ones, first);
+    else kb_rbgs_tile<TILE, NS, false><<<grid, 256, tile_smem<TILE, NS>(), st>>>(A, t, B, ones, first);
+}
+
+template <int TILE, int NS>
+bool tile_attr()
+{
+    const int b = static_cast<int>(tile_smem<TILE, NS>());
+    return cudaFuncSetAttribute(kb_rbgs_tile<TILE, NS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(kb_rbgs_tile<TILE, NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) ==
+               cudaSuccess;
 }
 
 template <int TILE>
 bool tile_attrs()
 {
-    return cudaFuncSetAttribute(kb_rbgs_tile<TILE, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(tile_smem<TILE, 2>())) == cudaSuccess &&
-           cudaFuncSetAttribute(kb_rbgs_tile<TILE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(tile_smem<TILE, 1>())) == cudaSuccess;
+    return tile_attr<TILE, 2>() && tile_attr<TILE, 1>();
 }
 
 // nsweeps full red-black sweeps of level t (first: colour of the first half
@@ -875,10 +895,24 @@ bool tile_attrs()
 // launches per sweep (FP64 is arithmetic-bound on GB300 and the tiles' halo
 // updates would add work).
 template <typename T>
-void smooth(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int first, int ones, cudaStream_t st)
+int tile_side(const mlqmc_ctx* c, int t)
 {
     const int64_t n = c->p.coarse_cells << t;
-    const int tile = sizeof(T) == 8 ? 0 : (n >= 32 && n % 32 == 0 ? 32 : (n == 16 ? 16 : (n == 8 ? 8 : 0)));
+    if (sizeof(T) == 8) return 0;
+    return n >= 32 && n % 32 == 0 ? 32 : (n == 16 ? 16 : (n == 8 ? 8 : 0));
+}
+
+// pro: add the coarse-grid correction P e first (post-smoothing).
+template <typename T>
+void smooth(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int first, int ones, bool pro, cudaStream_t st)
+{
+    const int64_t n = c->p.coarse_cells << t;
+    const int tile = tile_side<T>(c, t);
+    if (pro && tile == 0) {
+        Timed tm(c, kProfTransfer, st);
+        kb_prolong<T, true, false><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
+        pro = false;
+    }
     while (nsweeps > 0) {
         const int ns = nsweeps >= 2 ? 2 : 1;
         Timed tm(c, kProfSmooth, st);
@@ -888,11 +922,16 @@ void smooth(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int first, int 
             nsweeps -= ns;
             continue;
         }
-        if (tile == 32) (ns == 2 ? launch_tile<32, 2> : launch_tile<32, 1>)(c, A, t, B, ones, first, st);
-        else if (tile == 16) (ns == 2 ? launch_tile<16, 2> : launch_tile<16, 1>)(c, A, t, B, ones, first, st);
-        else (ns == 2 ? launch_tile<8, 2> : launch_tile<8, 1>)(c, A, t, B, ones, first, st);
+        if (tile == 32) (ns == 2 ? launch_tile<32, 2> : launch_tile<32, 1>)(c, A, t, B, ones, first, pro, st);
+        else if (tile == 16) (ns == 2 ? launch_tile<16, 2> : launch_tile<16, 1>)(c, A, t, B, ones, first, pro, st);
+        else (ns == 2 ? launch_tile<8, 2> : launch_tile<8, 1>)(c, A, t, B, ones, first, pro, st);
         swap_u(c, A, t);
+        pro = false;
         nsweeps -= ns;
+    }
+    if (pro) {  // no sweeps at all: the correction alone
+        Timed tm(c, kProfTransfer, st);
+        kb_prolong<T, true, false><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
     }
 }
 
@@ -903,7 +942,7 @@ mlqmc_status vcycle_batched(mlqmc_ctx* c, FmgArgs& A, int t_top, int B, bool one
         const int64_t n = c->p.coarse_cells << t;
         const int top_ones = (t == t_top && ones) ? 1 : 0;
         if (t < t_top && zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
-        smooth<T>(c, A, t, B, c->p.nu1, 0, top_ones, st);
+        smooth<T>(c, A, t, B, c->p.nu1, 0, top_ones, false, st);
         Timed tm(c, kProfTransfer, st);
         kb_resid_restrict<T><<<grid_for(c, B * n * n / 4), 256, 0, st>>>(A, t, B, top_ones);
     }
@@ -912,13 +951,8 @@ mlqmc_status vcycle_batched(mlqmc_ctx* c, FmgArgs& A, int t_top, int B, bool one
         launch_coarse<T>(c, A, B, st);
     }
     for (int t = 1; t <= t_top; ++t) {
-        const int64_t n = c->p.coarse_cells << t;
         const int top_ones = (t == t_top && ones) ? 1 : 0;
-        {
-            Timed tm(c, kProfTransfer, st);
-            kb_prolong<T, true, false><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
-        }
-        smooth<T>(c, A, t, B, c->p.nu2, 1, top_ones, st);
+        smooth<T>(c, A, t, B, c->p.nu2, 1, top_ones, true, st);
     }
     return last_error();
 }
