@@ -204,6 +204,73 @@ __global__ void kb_coarse(FmgArgs A, int B)
     }
 }
 
+// Coarse solve for n0 = NC fixed at compile time: a CTA of 64 threads takes 64
+// consecutive samples, stages their right-hand sides transposed in shared
+// memory (coalesced loads; row pitch 65 avoids bank conflicts), solves one
+// sample per thread with the factor rows prefetched PF rows ahead, and writes
+// the solutions back coalesced.
+template <typename T, int NC>
+__global__ void __launch_bounds__(64) kb_coarse_fixed(FmgArgs A, int B)
+{
+    constexpr int N = NC * NC, W = NC + 1, P = 65, PF = 4;
+    __shared__ T xs[N * P];
+    const T h2 = T(1) / (T(NC) * T(NC));
+    const T* fac = reinterpret_cast<const T*>(sizeof(T) == 4 ? A.chol32 : A.chol.base);
+    const size_t cs = A.chol.stride;
+    for (int base = blockIdx.x * 64; base < B; base += gridDim.x * 64) {
+        const int cnt = B - base < 64 ? B - base : 64;
+        for (int q = threadIdx.x; q < cnt * N; q += 64) {
+            const int j = q / N, r = q - j * N;
+            xs[r * P + j] = h2 * at<T>(A.lv[0].bc, base + j)[r];
+        }
+        __syncthreads();
+        const int j = threadIdx.x;
+        const int i = base + j;
+        if (j < cnt && !(A.active && !A.active[i])) {
+            T* x = xs + j;
+            T ring[PF][W];
+#pragma unroll
+            for (int a = 0; a < PF; ++a)
+#pragma unroll
+                for (int q = 0; q < W; ++q) ring[a][q] = fac[static_cast<size_t>(a * W + q) * cs + i];
+            for (int r0 = 0; r0 < N; r0 += PF) {
+#pragma unroll
+                for (int a = 0; a < PF; ++a) {
+                    const int r = r0 + a;
+                    T v = x[r * P];
+#pragma unroll
+                    for (int q = NC; q >= 1; --q)
+                        if (q <= r) v -= ring[a][q] * x[(r - q) * P];
+                    x[r * P] = v * ring[a][0];
+                    if (r + PF < N) {
+#pragma unroll
+                        for (int q = 0; q < W; ++q) ring[a][q] = fac[static_cast<size_t>((r + PF) * W + q) * cs + i];
+                    }
+                }
+            }
+            // backward: x_r -= sum_q L(r+q, r) x_{r+q}, entry (r+q, q)
+            for (int r0 = N - 1; r0 >= 0; r0 -= PF) {
+#pragma unroll
+                for (int a = 0; a < PF; ++a) {
+                    const int r = r0 - a;
+                    if (r < 0) break;
+                    T v = x[r * P];
+#pragma unroll
+                    for (int q = NC; q >= 1; --q)
+                        if (r + q < N) v -= fac[static_cast<size_t>((r + q) * W + q) * cs + i] * x[(r + q) * P];
+                    x[r * P] = v * fac[static_cast<size_t>(r * W) * cs + i];
+                }
+            }
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < cnt * N; q += 64) {
+            const int jj = q / N, r = q - jj * N;
+            if (!(A.active && !A.active[base + jj])) at<T>(A.lv[0].u, base + jj)[r] = xs[r * P + jj];
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Level-synchronous kernels over samples 0..B-1 of level t.
 // ---------------------------------------------------------------------------
@@ -772,6 +839,14 @@ mlqmc_status launch_level0(mlqmc_ctx* c, const FmgArgs& A, int B, cudaStream_t s
 template <typename T>
 void launch_coarse(mlqmc_ctx* c, const FmgArgs& A, int B, cudaStream_t st)
 {
+    if (c->p.coarse_cells == 8) {
+        kb_coarse_fixed<T, 8><<<std::max(1, std::min((B + 63) / 64, c->sm_count * 32)), 64, 0, st>>>(A, B);
+        return;
+    }
+    if (c->p.coarse_cells == 4) {
+        kb_coarse_fixed<T, 4><<<std::max(1, std::min((B + 63) / 64, c->sm_count * 32)), 64, 0, st>>>(A, B);
+        return;
+    }
     const size_t N0 = static_cast<size_t>(c->p.coarse_cells) * c->p.coarse_cells;
     const size_t smem = N0 * 64 * sizeof(T);
     if (smem <= 48 * 1024) kb_coarse<T, true><<<grid_for(c, B, 64), 64, smem, st>>>(A, B);
