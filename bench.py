@@ -72,60 +72,90 @@ def n_samples(work):
 
 
 # --------------------------------------------------------------------------- #
-# Algorithmic work models per kernel kind (stated in the design notes)         #
+# Roofline denominators                                                         #
 # --------------------------------------------------------------------------- #
-HBM_GBS = 6755.5          # measured copy bandwidth of this machine's GB300 (MEASURED_PEAKS.json)
-FP64_TFLOPS = 1.25        # GB300 FP64 nominal (an FMA probe measured 1.20)
-FP32_TFLOPS = 70.0        # FP32 FMA probe on this machine's GB300
+HBM_GBS = 6755.5          # measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)
+BF16_TFLOPS = 1925.0      # measured cuBLAS bf16 burst (MEASURED_PEAKS.json bf16_tflops)
+TF32_TFLOPS = BF16_TFLOPS * 1.1 / 2.25   # measured bf16 x nominal tf32/bf16 ratio (1.1 / 2.25 PFLOP/s dense)
+FP64_TFLOPS = 1.25        # nominal GB300 FP64 (an FMA probe measured 1.20)
+FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz = 80.5
 
 
-def t_small(cfg):
-    """Every level above 0 runs level-synchronous kernels."""
-    return 0
+def measured_peaks_override():
+    global HBM_GBS, BF16_TFLOPS, TF32_TFLOPS
+    pk = measured_peaks()
+    if pk.get("hbm_gbs"):
+        HBM_GBS = float(pk["hbm_gbs"])
+    if pk.get("bf16_tflops"):
+        BF16_TFLOPS = float(pk["bf16_tflops"])
+        TF32_TFLOPS = BF16_TFLOPS * 1.1 / 2.25
 
 
-def level_counts(cfg, work):
-    """B_t = samples whose FMG reaches level t."""
-    B = [0] * cfg["n_levels"]
-    for (lv, nb, ne, rb, re_) in work:
-        for t in range(lv + 1):
-            B[t] += (ne - nb) * (re_ - rb)
-    return B
+KIND_KERNELS = {
+    "points": "k_points (lattice points and normals)",
+    "level0": "kb_level0 (banded Cholesky and exact level-0 solve, one thread per sample)",
+    "synth": "kb_synth_G/kb_synth_z (separable KL), kb_faces, kb_idiag",
+    "smooth": "red-black sweeps (kb_rbgs_tile in FP32: two sweeps per launch; kb_gs in FP64: one colour)",
+    "transfer": "kb_resid_restrict, kb_prolong, kb_resid64, kb_update64",
+    "coarse": "kb_coarse_fixed (V-cycle level-0 solves)",
+    "reduce": "kb_qoi, kb_resnorm, k_sums, outputs",
+    "kl_tc": "kl_tc_kernel (tcgen05 TF32 KL contraction) and its C operand",
+}
 
 
-def smooth_model(cfg, work, es):
-    """Batched red-black sweeps of one step (fixed-cycle form): updated cells,
-    FLOPs (10 per update: 4 FMA + h^2 b + scaling) and algorithmic bytes (per
-    full sweep of an n x n grid 8 n^2 values move: u of the other colour,
-    the 2 n^2 faces, 1/D, b and the written u)."""
-    ts, B = t_small(cfg), level_counts(cfg, work)
-    cells = 0
-    for t in range(ts + 1, cfg["n_levels"]):
-        for tau in range(ts + 1, t + 1):
-            cells += cfg["mu0"] * (cfg["nu1"] + cfg["nu2"]) * B[t] * (cfg["n0"] << tau) ** 2
-    return dict(cells=cells, flops=10.0 * cells, bytes=8.0 * es * cells)
+def kind_roofline(ms, work):
+    """Roofline of one kernel kind from its device time and algorithmic work:
+    the bound is the resource whose model time (bytes / HBM, FLOPs / pipe peak)
+    is longest; frac = that model time / measured time."""
+    t = ms * 1e-3
+    t_hbm = work["bytes"] / (HBM_GBS * 1e9)
+    t64, t32 = work["f64"] / (FP64_TFLOPS * 1e12), work["f32"] / (FP32_TFLOPS * 1e12)
+    t_tc = work["ftc"] / (TF32_TFLOPS * 1e12)
+    best = max(("hbm", t_hbm), ("alu64", t64), ("alu32", t32), ("tensor", t_tc), key=lambda x: x[1])
+    if t <= 0 or best[1] <= 0:
+        return None
+    r = {"ms": ms, "gbs": work["bytes"] / t / 1e9, "fp64_tflops": work["f64"] / t / 1e12,
+         "fp32_tflops": work["f32"] / t / 1e12, "tc_tflops": work["ftc"] / t / 1e12,
+         "algorithmic_bytes": work["bytes"]}
+    if best[0] == "hbm":
+        r.update(bound="hbm", achieved=r["gbs"], peak=HBM_GBS, unit="GB/s",
+                 peak_source="measured copy bandwidth (MEASURED_PEAKS.json)")
+    elif best[0] == "tensor":
+        r.update(bound="tensor", achieved=r["tc_tflops"], peak=TF32_TFLOPS, unit="TFLOP/s",
+                 peak_source="measured bf16 burst x nominal tf32/bf16 ratio")
+    elif best[0] == "alu64":
+        r.update(bound="alu", achieved=r["fp64_tflops"], peak=FP64_TFLOPS, unit="TFLOP/s",
+                 peak_source="FP64 1.25 TFLOP/s (nominal GB300 figure; FMA probe 1.20)")
+    else:
+        r.update(bound="alu", achieved=r["fp32_tflops"], peak=FP32_TFLOPS, unit="TFLOP/s",
+                 peak_source="FP32 152 SMs x 128 lanes x 2 x 2070 MHz")
+    r["frac"] = r["achieved"] / r["peak"]
+    return r
 
 
-def small_fp64_ops(cfg, work, Ka):
-    """FP64 operations of the per-sample kernel (levels <= 64x64) in one step:
-    KL 2 s n + 2 Ka n^2 + n^2 (exp) per level, faces and 1/D 12 n^2, GS sweep
-    11 n^2, residual+restriction 15 n^2, prolongation 9 n^2, banded Cholesky
-    2 N0 n0^2 and 4 N0 n0 per solve, QoI n^2."""
-    n0, s, mu0, nu1, nu2 = cfg["n0"], cfg["s"], cfg["mu0"], cfg["nu1"], cfg["nu2"]
-    ts, N0 = t_small(cfg), n0 * n0
-    tot = 0.0
-    for (lv, nb, ne, rb, re_) in work:
-        cnt = (ne - nb) * (re_ - rb)
-        Ls = min(lv, ts)
-        ops = 2 * N0 * n0 * n0 + 4 * N0 * n0
-        for t in range(Ls + 1):
-            n = n0 << t
-            ops += 2 * s * n + 2 * Ka * n * n + n * n + 12 * n * n + n * n
-        for t in range(1, Ls + 1):
-            v = 4 * N0 * n0 + sum(((nu1 + nu2) * 11 + 15 + 9) * (n0 << u) ** 2 for u in range(1, t + 1))
-            ops += 9 * (n0 << t) ** 2 + mu0 * v
-        tot += cnt * ops
-    return tot
+def roofline_report(prof, work, steps):
+    """Dominant kind's roofline (the bench line's `roofline`) plus every kind's."""
+    kinds = {}
+    for k, (ms, n) in prof.items():
+        if n == 0:
+            continue
+        r = kind_roofline(ms, work[k])
+        if r:
+            r["launches_per_step"] = n / steps
+            r["ms_per_step"] = ms / steps
+            kinds[k] = r
+    tot = sum(v[0] for v in prof.values())
+    dom = max(kinds, key=lambda k: kinds[k]["ms"])
+    d = kinds[dom]
+    roof = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
+            "frac": d["frac"], "traffic": None, "kernel": KIND_KERNELS.get(dom, dom), "kernel_kind": dom,
+            "peak_source": d["peak_source"], "share_of_step": d["ms"] / max(1e-9, tot),
+            "launches_per_step": d["launches_per_step"], "ms_per_step": d["ms_per_step"],
+            "algorithmic_bytes_per_launch": d["algorithmic_bytes"] / max(1, prof[dom][1])}
+    by_kind = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()
+                   if kk in ("ms_per_step", "bound", "achieved", "unit", "frac", "gbs", "launches_per_step")}
+               for k, v in kinds.items()}
+    return roof, by_kind
 
 
 def clocks_start(path):
@@ -233,6 +263,8 @@ def run_ours(args):
 
     import paper_1806_05619_gb300 as M
 
+    measured_peaks_override()
+
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -283,6 +315,7 @@ def run_ours(args):
     barrier()
     launches = ctx.launch_count() - launches0
     prof = ctx.profile_read()
+    pwork = ctx.profile_work()
     ctx.profile(False)
     clocks = clocks_stop(clk, clk_path, device_index=local)
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -318,33 +351,9 @@ def run_ours(args):
     h2d = len(work) * 32 + ns * (24 + 8)  # work list + the library's per-sample descriptors
     d2h = nl * R * 2 * 8
 
-    # roofline of the dominant kernel kind from the library's own event timing
-    a, b, th = ctx.modes()
-    Ka = int(a.max()) + 1
-    dom = max(prof, key=lambda k: prof[k][0])
-    dom_ms, dom_n = prof[dom]
-    step_dev_ms = sum(v[0] for v in prof.values())
-    roof = {"kernel_kind": dom, "share_of_step": dom_ms / max(1e-9, step_dev_ms), "launches": dom_n,
-            "ms_per_step": dom_ms / args.steps, "traffic": None}
-    if dom == "smooth":
-        m = smooth_model(cfg, work, 8 if cfg["precision"] == "fp64" else 4)
-        t_s = dom_ms * 1e-3 / args.steps
-        t_hbm, t_alu = m["bytes"] / (HBM_GBS * 1e9), m["flops"] / (FP64_TFLOPS * 1e12)
-        if t_hbm >= t_alu:
-            roof.update(bound="hbm", achieved=m["bytes"] / t_s / 1e9, peak=HBM_GBS, unit="GB/s",
-                        peak_source="measured copy bandwidth (MEASURED_PEAKS.json)")
-        else:
-            roof.update(bound="alu", achieved=m["flops"] / t_s / 1e12, peak=FP64_TFLOPS, unit="TFLOP/s",
-                        peak_source="nominal FP64 1.25 TFLOP/s (probe 1.20)")
-        roof.update(kernel="batched red-black sweeps (kb_gs / kb_rbgs_tile)", algorithmic_bytes_per_step=m["bytes"],
-                    flops_per_step=m["flops"])
-    else:
-        ops = small_fp64_ops(cfg, work, Ka)
-        t_s = dom_ms * 1e-3 / args.steps
-        roof.update(bound="alu", achieved=ops / t_s / 1e12, peak=FP64_TFLOPS, unit="TFLOP/s",
-                    peak_source="nominal FP64 1.25 TFLOP/s (probe 1.20)", kernel=f"{dom} kernels",
-                    flops_per_step=ops)
-    roof["frac"] = roof["achieved"] / roof["peak"]
+    # roofline of the dominant kernel kind: the library's event timing of each
+    # launch inside the timed region and the algorithmic work it recorded
+    roof, by_kind = roofline_report(prof, pwork, args.steps)
 
     mixed = None
     if not args.no_mixed and cfg["precision"] == "fp64":
@@ -380,7 +389,7 @@ def run_ours(args):
                        "parallelism": f"independent replicas x{world}"},
             "gpu_launches": launches,
             "roofline": roof,
-            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
+            "roofline_by_kind": by_kind,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "estimate": {"Q": float(est[0]), "varQ": float(est[1])}},
             "clocks": clocks,
@@ -426,12 +435,14 @@ def run_mixed_same_workload(args, cfg64, work, genvec, dev, stream, flush, M):
         ev[i][1].record(stream)
     torch.cuda.synchronize(dev)
     prof = ctx.profile_read()
+    pwork = ctx.profile_work()
     ctx.profile(False)
     ctx.check_device(stream)
     tot = sum(a.elapsed_time(b) for a, b in ev)
+    roof, by_kind = roofline_report(prof, pwork, args.steps)
     return {"value": ns * args.steps / (tot * 1e-3), "unit": UNIT, "ms_per_step": tot / args.steps,
-            "dtype": "f32 V-cycles in f64 refinement, f32 field",
-            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]}}
+            "dtype": "f32 V-cycles in f64 refinement, TF32 tensor-core KL, f32 field",
+            "roofline": roof, "roofline_by_kind": by_kind}
 
 
 def run_precision_form(dev, stream, flush, M):

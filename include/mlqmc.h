@@ -296,6 +296,20 @@ mlqmc_status mlqmc_profile(mlqmc_ctx* c, int32_t enable);
  */
 mlqmc_status mlqmc_profile_read(mlqmc_ctx* c, double* out_ms, int64_t* out_n);
 
+/*
+ * Algorithmic work of the launches recorded since the last mlqmc_profile
+ * call, per kernel kind (same 8 kinds; host arrays of 8 doubles each):
+ * out_bytes: bytes the launches must move when every array a launch touches
+ * is read or written exactly once (halo re-reads, cache misses and
+ * redundant tile work not counted); out_f64 / out_f32: FP64 and FP32 FLOPs of
+ * the method's arithmetic (stencil updates 10 per cell, residual 10-12,
+ * restriction 1, prolongation 8, harmonic faces 3 per face, banded Cholesky
+ * N0 n0^2 per sample; exp and divisions counted as one); out_ftc: FLOPs of
+ * the KL contraction on the tensor cores (2 M s B per level). These are the
+ * numerators of the roofline fractions. Recorded only while profiling is on.
+ */
+mlqmc_status mlqmc_profile_work(mlqmc_ctx* c, double* out_bytes, double* out_f64, double* out_f32, double* out_ftc);
+
 #ifdef __cplusplus
 }
 #endif

@@ -98,11 +98,12 @@ def lib():
             L.mlqmc_last_iterations.argtypes = [vp, C.POINTER(C.c_int32)]
             L.mlqmc_profile.argtypes = [vp, i32]
             L.mlqmc_profile_read.argtypes = [vp, dp, C.POINTER(C.c_int64)]
+            L.mlqmc_profile_work.argtypes = [vp, dp, dp, dp, dp]
             L.mlqmc_launch_count.argtypes = [vp]
             L.mlqmc_launch_count.restype = i64
             for name in ["mlqmc_create", "mlqmc_sample_levels", "mlqmc_estimate", "mlqmc_get_device_status",
                          "mlqmc_cbc_genvec", "mlqmc_modes", "mlqmc_point_bits", "mlqmc_normals", "mlqmc_fields",
-                         "mlqmc_sample_solution", "mlqmc_profile", "mlqmc_profile_read",
+                         "mlqmc_sample_solution", "mlqmc_profile", "mlqmc_profile_read", "mlqmc_profile_work",
                          "mlqmc_fmg_fields_noalloc", "mlqmc_last_iterations"]:
                 getattr(L, name).restype = C.c_int
             _lib = L
@@ -270,6 +271,14 @@ class Context:
         n = (C.c_int64 * 8)()
         _check(lib().mlqmc_profile_read(self.h, ms.ctypes.data_as(C.POINTER(C.c_double)), n), "mlqmc_profile_read")
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.PROFILE_KINDS)}
+
+    def profile_work(self):
+        """{kind: {"bytes", "f64", "f32", "ftc"}}: algorithmic work of the launches since profile()."""
+        a = [np.zeros(8) for _ in range(4)]
+        _check(lib().mlqmc_profile_work(self.h, *[x.ctypes.data_as(C.POINTER(C.c_double)) for x in a]),
+               "mlqmc_profile_work")
+        return {k: {"bytes": float(a[0][i]), "f64": float(a[1][i]), "f32": float(a[2][i]), "ftc": float(a[3][i])}
+                for i, k in enumerate(self.PROFILE_KINDS)}
 
     def last_iterations(self):
         """Per level, the most extra cycles / refinement steps any sample needed since the last query."""

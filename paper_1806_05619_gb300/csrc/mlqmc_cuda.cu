@@ -788,28 +788,64 @@ cudaEvent_t take_event(mlqmc_ctx* c)
     return e;
 }
 
-// Brackets one launch with events when profiling is on.
+// Algorithmic work of one launch: the bytes it must move when every array it
+// touches is read or written once, and its arithmetic by precision.
+struct Work {
+    double bytes = 0.0, f64 = 0.0, f32 = 0.0, ftc = 0.0;
+};
+
+template <typename T>
+Work work_of(double bytes, double flops)
+{
+    Work w;
+    w.bytes = bytes;
+    if (sizeof(T) == 8) w.f64 = flops;
+    else w.f32 = flops;
+    return w;
+}
+
+// Brackets one launch with events when profiling is on and adds its work.
+// nk: kernels launched inside the bracket.
 struct Timed {
     mlqmc_ctx* c;
     int kind;
     cudaStream_t st;
+    int nk;
     cudaEvent_t a = nullptr;
-    Timed(mlqmc_ctx* c_, int kind_, cudaStream_t st_) : c(c_), kind(kind_), st(st_)
+    Timed(mlqmc_ctx* c_, int kind_, cudaStream_t st_, const Work& w = Work(), int nk_ = 1)
+        : c(c_), kind(kind_), st(st_), nk(nk_)
     {
         if (c->profiling) {
             a = take_event(c);
             cudaEventRecord(a, st);
+            c->prof_bytes[kind] += w.bytes;
+            c->prof_f64[kind] += w.f64;
+            c->prof_f32[kind] += w.f32;
+            c->prof_ftc[kind] += w.ftc;
         }
     }
     ~Timed()
     {
-        c->launches += 1;
+        c->launches += nk;
         if (!a) return;
         cudaEvent_t b = take_event(c);
         cudaEventRecord(b, st);
-        c->marks.push_back({kind, a, b});
+        c->marks.push_back({kind, nk, a, b});
     }
 };
+
+// Cells and faces of one direction on level t.
+double cells_of(const mlqmc_ctx* c, int t)
+{
+    const double n = static_cast<double>(c->p.coarse_cells << t);
+    return n * n;
+}
+
+double faces_of(const mlqmc_ctx* c, int t)
+{
+    const double n = static_cast<double>(c->p.coarse_cells << t);
+    return n * (n + 1.0);
+}
 
 int grid_for(mlqmc_ctx* c, int64_t work, int threads = 256)
 {
@@ -830,7 +866,14 @@ mlqmc_status last_error()
 // Level-0 factor, exact solve and F_0 of samples 0..B-1 (one thread each).
 mlqmc_status launch_level0(mlqmc_ctx* c, const FmgArgs& A, int B, cudaStream_t st)
 {
-    Timed tm(c, kProfSmall, st);
+    // per sample: faces in, band factor (n0 + 1 entries per row) and solutions out;
+    // banded Cholesky N0 n0^2 and two triangular solves 4 N0 n0 FP64 FLOPs
+    const double N0 = cells_of(c, 0), n0 = c->p.coarse_cells, es = is_mixed(c->p) ? 4.0 : 8.0;
+    Work w;
+    w.bytes = B * (es * (2.0 * faces_of(c, 0)) + 8.0 * N0 * (n0 + 1.0) + (is_mixed(c->p) ? 4.0 * N0 * (n0 + 1.0) : 0.0) +
+                   (8.0 + es) * N0 + 8.0);
+    w.f64 = B * (N0 * n0 * n0 + 4.0 * N0 * n0);
+    Timed tm(c, kProfSmall, st, w);
     if (is_mixed(c->p)) kb_level0<float, true><<<grid_for(c, B, 128), 128, 0, st>>>(A, B);
     else kb_level0<double, false><<<grid_for(c, B, 128), 128, 0, st>>>(A, B);
     return last_error();
@@ -856,7 +899,7 @@ void launch_coarse(mlqmc_ctx* c, const FmgArgs& A, int B, cudaStream_t st)
 mlqmc_status launch_points(mlqmc_ctx* c, const SampleDesc* d_s, int count, double* Y, uint64_t* bits, cudaStream_t st)
 {
     const int64_t total = static_cast<int64_t>(count) * c->p.n_modes;
-    Timed tm(c, kProfPoints, st);
+    Timed tm(c, kProfPoints, st, work_of<double>(8.0 * total + sizeof(SampleDesc) * count, 0.0));
     k_points<<<grid_for(c, total), 256, 0, st>>>(d_s, count, c->p.n_modes, c->p.sampler, c->p.seed, c->d_z, Y, bits);
     return last_error();
 }
@@ -878,28 +921,34 @@ mlqmc_status synth_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cudaStr
         if (uses_tc(c, t)) {
             const LevelPool& P = c->pools[t];
             float* k = reinterpret_cast<float*>(P.mem + P.off[kK]);
-            Timed tm(c, kProfKlTc, st);
+            const double M = static_cast<double>(n * n), K = mlqmc_kl::kpad_for(c->p.n_modes);
+            Work w;
+            w.bytes = 4.0 * (M * B + M * K + B * K);  // k out, Psi and C in
+            w.ftc = 2.0 * M * c->p.n_modes * B;
+            Timed tm(c, kProfKlTc, st, w);
             if (!mlqmc_kl::launch(c->kl_maps[t], static_cast<int>(n * n), B, c->p.n_modes, k, P.stride[kK] / sizeof(float),
                                   c->d_status, st))
                 return MLQMC_ERR_CUDA;
         }
     }
     if (!uses_tc(c, t) || sizeof(T) != 4) {
+        const double M = static_cast<double>(n * n), Ka = c->Ka, sm = c->p.n_modes;
         {
-            Timed tm(c, kProfSynth, st);
+            Timed tm(c, kProfSynth, st, work_of<T>(B * (8.0 * sm + sizeof(T) * Ka * n), B * 2.0 * sm * n));
             kb_synth_G<T><<<grid_for(c, B * c->Ka * n), 256, 0, st>>>(A, t, B);
         }
         {
-            Timed tm(c, kProfSynth, st);
+            Timed tm(c, kProfSynth, st, work_of<T>(B * sizeof(T) * (Ka * n + M), B * 2.0 * Ka * M));
             kb_synth_z<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
         }
     }
+    const double es = sizeof(T), Mc = cells_of(c, t), Fc = faces_of(c, t);
     {
-        Timed tm(c, kProfSynth, st);
+        Timed tm(c, kProfSynth, st, work_of<T>(B * es * (Mc + 2.0 * Fc), B * 6.0 * Fc));
         kb_faces<T><<<grid_for(c, B * n * (n + 1)), 256, 0, st>>>(A, t, B);
     }
     {
-        Timed tm(c, kProfSynth, st);
+        Timed tm(c, kProfSynth, st, work_of<T>(B * es * (2.0 * Fc + Mc), B * 5.0 * Mc));
         kb_idiag<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
     }
     return last_error();
@@ -909,7 +958,8 @@ mlqmc_status synth_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cudaStr
 mlqmc_status build_c(mlqmc_ctx* c, int count, cudaStream_t st)
 {
     if (!c->kl_tc) return MLQMC_OK;
-    Timed tm(c, kProfKlTc, st);
+    Timed tm(c, kProfKlTc, st,
+             work_of<float>(count * (8.0 * c->p.n_modes + 4.0 * mlqmc_kl::kpad_for(c->p.n_modes)), 0.0));
     return mlqmc_kl::build_c(c->d_Y, nullptr, count, c->p.n_modes, c->d_sqrt_theta, c->d_C, st) ? MLQMC_OK
                                                                                                 : MLQMC_ERR_CUDA;
 }
@@ -983,14 +1033,23 @@ void smooth(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int first, int 
 {
     const int64_t n = c->p.coarse_cells << t;
     const int tile = tile_side<T>(c, t);
+    const double es = sizeof(T), Mc = cells_of(c, t), Fc = faces_of(c, t);
+    const Work pro_work = work_of<T>(B * es * (0.25 * Mc + 2.0 * Mc), B * 8.0 * Mc);
     if (pro && tile == 0) {
-        Timed tm(c, kProfTransfer, st);
+        Timed tm(c, kProfTransfer, st, pro_work);
         kb_prolong<T, true, false><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
         pro = false;
     }
     while (nsweeps > 0) {
         const int ns = nsweeps >= 2 ? 2 : 1;
-        Timed tm(c, kProfSmooth, st);
+        // one colour (kb_gs): all of u and the faces, 1/D and b of that colour, its u written;
+        // tiled: u, faces, 1/D and b once, u2 written once for ns sweeps (+ e of level t-1)
+        const double b_in = ones ? 0.0 : 1.0;
+        const Work w = tile == 0 ? work_of<T>(2.0 * ns * B * es * (Mc + 2.0 * Fc + (1.0 + 0.5 * b_in) * Mc),
+                                              2.0 * ns * B * 5.0 * Mc)
+                                 : work_of<T>(B * es * ((3.0 + b_in) * Mc + 2.0 * Fc + (pro ? 0.25 * Mc : 0.0)),
+                                              B * (10.0 * ns * Mc + (pro ? 8.0 * Mc : 0.0)));
+        Timed tm(c, kProfSmooth, st, w, tile == 0 ? 2 * ns : 1);
         if (tile == 0) {
             for (int h = 0; h < 2 * ns; ++h)
                 kb_gs<T><<<grid_for(c, B * n * n / 2), 256, 0, st>>>(A, t, B, (first + h) & 1, ones);
@@ -1005,7 +1064,7 @@ void smooth(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int first, int 
         nsweeps -= ns;
     }
     if (pro) {  // no sweeps at all: the correction alone
-        Timed tm(c, kProfTransfer, st);
+        Timed tm(c, kProfTransfer, st, pro_work);
         kb_prolong<T, true, false><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
     }
 }
@@ -1018,11 +1077,14 @@ mlqmc_status vcycle_batched(mlqmc_ctx* c, FmgArgs& A, int t_top, int B, bool one
         const int top_ones = (t == t_top && ones) ? 1 : 0;
         if (t < t_top && zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
         smooth<T>(c, A, t, B, c->p.nu1, 0, top_ones, false, st);
-        Timed tm(c, kProfTransfer, st);
+        const double es = sizeof(T), Mc = cells_of(c, t), Fc = faces_of(c, t);
+        Timed tm(c, kProfTransfer, st,
+                 work_of<T>(B * es * ((top_ones ? 1.25 : 2.25) * Mc + 2.0 * Fc), B * 11.0 * Mc));
         kb_resid_restrict<T><<<grid_for(c, B * n * n / 4), 256, 0, st>>>(A, t, B, top_ones);
     }
     {
-        Timed tm(c, kProfSmallV, st);
+        const double N0 = cells_of(c, 0), n0 = c->p.coarse_cells, es = sizeof(T);
+        Timed tm(c, kProfSmallV, st, work_of<T>(B * es * (N0 * (n0 + 1.0) + 2.0 * N0), B * 4.0 * N0 * n0));
         launch_coarse<T>(c, A, B, st);
     }
     for (int t = 1; t <= t_top; ++t) {
@@ -1039,14 +1101,15 @@ template <typename T>
 mlqmc_status converge_batched(mlqmc_ctx* c, FmgArgs& A, int t, int B, cudaStream_t st)
 {
     const int64_t n = c->p.coarse_cells << t;
+    const double es = sizeof(T), Mc = cells_of(c, t), Fc = faces_of(c, t);
     for (int it = 0;; ++it) {
         {
-            Timed tm(c, kProfReduce, st);
+            Timed tm(c, kProfReduce, st, work_of<double>(B * (8.0 * Mc + es * (2.0 * Fc + Mc) + 8.0), B * 12.0 * Mc));
             kb_resnorm<T, true><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
         }
         if (!ok(cudaMemsetAsync(c->d_count, 0, sizeof(int), st))) return MLQMC_ERR_CUDA;
         {
-            Timed tm(c, kProfReduce, st);
+            Timed tm(c, kProfReduce, st, work_of<double>(B * 12.0, 0.0));
             kb_flags<<<grid_for(c, B), 256, 0, st>>>(c->d_norms, c->d_active, B, c->p.refine_rtol * n, c->d_count);
         }
         if (!ok(cudaMemcpyAsync(c->h_count, c->d_count, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
@@ -1062,7 +1125,7 @@ mlqmc_status converge_batched(mlqmc_ctx* c, FmgArgs& A, int t, int B, cudaStream
         mlqmc_status s = zero_u(c, t, B, st);
         for (int m = 0; m < c->p.mu0 && s == MLQMC_OK; ++m) s = vcycle_batched<T>(c, A, t, B, false, st);
         if (s == MLQMC_OK) {
-            Timed tm(c, kProfTransfer, st);
+            Timed tm(c, kProfTransfer, st, work_of<double>(B * (16.0 + es) * Mc, B * Mc));
             kb_update64<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
         }
         A.active = nullptr;
@@ -1084,13 +1147,14 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
         const int B = Bt[t];
         if (B == 0) break;
         const int64_t n = c->p.coarse_cells << t;
+        const double es = sizeof(T), Mc = cells_of(c, t), Fc = faces_of(c, t);
         if (refine) {
             {
-                Timed tm(c, kProfTransfer, st);
+                Timed tm(c, kProfTransfer, st, work_of<double>(B * 8.0 * 1.25 * Mc, B * 8.0 * Mc));
                 kb_prolong<T, false, true><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
             }
             {
-                Timed tm(c, kProfTransfer, st);
+                Timed tm(c, kProfTransfer, st, work_of<double>(B * (8.0 * Mc + es * (2.0 * Fc + Mc)), B * 10.0 * Mc));
                 kb_resid64<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
             }
             if (zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
@@ -1099,7 +1163,7 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
                 if (s != MLQMC_OK) return s;
             }
             {
-                Timed tm(c, kProfTransfer, st);
+                Timed tm(c, kProfTransfer, st, work_of<double>(B * (16.0 + es) * Mc, B * Mc));
                 kb_update64<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
             }
             if (c->p.refine_rtol > 0.0) {
@@ -1108,7 +1172,7 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
             }
         } else {
             {
-                Timed tm(c, kProfTransfer, st);
+                Timed tm(c, kProfTransfer, st, work_of<T>(B * es * 1.25 * Mc, B * 8.0 * Mc));
                 kb_prolong<T, false, false><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
             }
             for (int m = 0; m < c->p.mu0; ++m) {
@@ -1117,12 +1181,12 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
             }
         }
         {
-            Timed tm(c, kProfReduce, st);
+            Timed tm(c, kProfReduce, st, work_of<double>(B * (refine ? 8.0 : es) * Mc, B * Mc));
             if (refine) kb_qoi<T, true><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
             else kb_qoi<T, false><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
         }
         if (d_usol) {
-            Timed tm(c, kProfReduce, st);
+            Timed tm(c, kProfReduce, st, work_of<double>((8.0 + (refine ? 8.0 : es)) * Mc, 0.0));
             if (refine) kb_u_out<T, true><<<grid_for(c, n * n), 256, 0, st>>>(A, t, d_usol + uoff);
             else kb_u_out<T, false><<<grid_for(c, n * n), 256, 0, st>>>(A, t, d_usol + uoff);
             uoff += static_cast<size_t>(n) * n;
@@ -1153,7 +1217,7 @@ mlqmc_status run_chunk(mlqmc_ctx* c, int count, const int* Bt, int Lmax, double*
     if (s != MLQMC_OK) return s;
     if (d_usol) {
         const int64_t n0 = p.coarse_cells;
-        Timed tm(c, kProfReduce, st);
+        Timed tm(c, kProfReduce, st, work_of<double>(16.0 * n0 * n0, 0.0));
         if (is_mixed(p)) kb_u_out<float, true><<<grid_for(c, n0 * n0), 256, 0, st>>>(A, 0, d_usol);
         else if (A.refine) kb_u_out<double, true><<<grid_for(c, n0 * n0), 256, 0, st>>>(A, 0, d_usol);
         else kb_u_out<double, false><<<grid_for(c, n0 * n0), 256, 0, st>>>(A, 0, d_usol);
@@ -1162,12 +1226,12 @@ mlqmc_status run_chunk(mlqmc_ctx* c, int count, const int* Bt, int Lmax, double*
                     : fmg_stages<double, false>(c, A, Bt, Lmax, d_usol, st);
     if (s != MLQMC_OK) return s;
     if (d_sums) {
-        Timed tm(c, kProfReduce, st);
+        Timed tm(c, kProfReduce, st, work_of<double>(count * (8.0 * p.n_levels + sizeof(SampleDesc)), count * 2.0 * p.n_levels));
         k_sums<<<p.n_levels * p.n_shifts, 256, 0, st>>>(c->d_samples, count, c->d_F, p.n_levels, p.n_shifts, p.reuse,
                                                         d_sums);
     }
     if (d_Fout) {
-        Timed tm(c, kProfReduce, st);
+        Timed tm(c, kProfReduce, st, work_of<double>(count * (16.0 * p.n_levels + sizeof(SampleDesc)), 0.0));
         k_fout<<<grid_for(c, static_cast<int64_t>(count) * p.n_levels), 256, 0, st>>>(c->d_samples, count, c->d_F,
                                                                                       p.n_levels, d_Fout);
     }
@@ -1545,7 +1609,7 @@ extern "C" mlqmc_status mlqmc_fields(mlqmc_ctx* c, int32_t t, const double* d_y,
     s = is_mixed(c->p) ? synth_batched<float>(c, A, t, count, st) : synth_batched<double>(c, A, t, count, st);
     if (s != MLQMC_OK) return s;
     const int64_t n = c->p.coarse_cells << t;
-    Timed tm(c, kProfReduce, st);
+    Timed tm(c, kProfReduce, st, work_of<double>(count * (8.0 + (is_mixed(c->p) ? 4.0 : 8.0)) * n * n, 0.0));
     if (is_mixed(c->p)) kb_k_out<float><<<grid_for(c, count * n * n), 256, 0, st>>>(A, t, count, d_k);
     else kb_k_out<double><<<grid_for(c, count * n * n), 256, 0, st>>>(A, t, count, d_k);
     return last_error();
@@ -1580,6 +1644,20 @@ extern "C" mlqmc_status mlqmc_profile(mlqmc_ctx* c, int32_t enable)
     for (int i = 0; i < kProfKinds; ++i) {
         c->prof_ms[i] = 0.0;
         c->prof_n[i] = 0;
+        c->prof_bytes[i] = c->prof_f64[i] = c->prof_f32[i] = c->prof_ftc[i] = 0.0;
+    }
+    return MLQMC_OK;
+}
+
+extern "C" mlqmc_status mlqmc_profile_work(mlqmc_ctx* c, double* out_bytes, double* out_f64, double* out_f32,
+                                           double* out_ftc)
+{
+    if (!c || !out_bytes || !out_f64 || !out_f32 || !out_ftc) return MLQMC_ERR_INVALID_ARG;
+    for (int i = 0; i < kProfKinds; ++i) {
+        out_bytes[i] = c->prof_bytes[i];
+        out_f64[i] = c->prof_f64[i];
+        out_f32[i] = c->prof_f32[i];
+        out_ftc[i] = c->prof_ftc[i];
     }
     return MLQMC_OK;
 }
@@ -1592,7 +1670,7 @@ extern "C" mlqmc_status mlqmc_profile_read(mlqmc_ctx* c, double* out_ms, int64_t
         float ms = 0.0f;
         if (!ok(cudaEventElapsedTime(&ms, m.a, m.b))) return MLQMC_ERR_CUDA;
         c->prof_ms[m.kind] += ms;
-        c->prof_n[m.kind] += 1;
+        c->prof_n[m.kind] += m.nk;
         c->pool.push_back(m.a);
         c->pool.push_back(m.b);
     }

@@ -123,13 +123,19 @@ struct mlqmc_ctx {
     // optional per-kernel event timing
     bool profiling = false;
     struct Mark {
-        int kind;
+        int kind, nk;  // kernel kind, kernels inside the bracket
         cudaEvent_t a, b;
     };
     std::vector<Mark> marks;        // recorded, not yet read
     std::vector<cudaEvent_t> pool;  // free events
     double prof_ms[kProfKinds] = {};
     int64_t prof_n[kProfKinds] = {};
+    // algorithmic work of the launches since mlqmc_profile(1): bytes each launch
+    // must move (every array it touches once) and FP64 / FP32 / tensor-core FLOPs
+    double prof_bytes[kProfKinds] = {};
+    double prof_f64[kProfKinds] = {};
+    double prof_f32[kProfKinds] = {};
+    double prof_ftc[kProfKinds] = {};
 
     int* d_status = nullptr;  // deferred device status bits
     int host_status = 0;      // deferred status found on the host (converged-form loops)
