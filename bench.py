@@ -51,6 +51,8 @@ def parse():
                     help="form of the main measurement (the other form is reported under 'mixed')")
     ap.add_argument("--no-precision", action="store_true", help="skip the 1024x1024 precision-form comparison")
     ap.add_argument("--no-tte", action="store_true", help="skip the time-to-epsilon runs of Algorithm 1")
+    ap.add_argument("--smoother", default="auto", choices=["auto", "stream", "tma", "tile"],
+                    help="mixed form: force this smoother on every level it handles (default: the autotuner's pick)")
     ap.add_argument("--counts-div", type=int, default=1,
                     help="divide the per-level counts (small cases for profiler captures only)")
     return ap.parse_args()
@@ -257,6 +259,17 @@ def run_reference(args):
 # --------------------------------------------------------------------------- #
 # GPU arm                                                                    #
 # --------------------------------------------------------------------------- #
+def force_smoother(ctx, name):
+    if name == "auto" or ctx.precision == "fp64":
+        return
+    import paper_1806_05619_gb300 as M
+    for t in range(1, ctx.n_levels):
+        try:
+            ctx.set_smoother(t, name)
+        except M.MlqmcError:
+            pass
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -281,6 +294,7 @@ def run_ours(args):
     ns = n_samples(work)
     genvec, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
     ctx = M.Context.from_config(cfg, genvec=genvec, max_samples=ns)
+    force_smoother(ctx, args.smoother)
     nl, R = cfg["n_levels"], cfg["R"]
     sums = torch.zeros(nl * R * 2, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -415,6 +429,7 @@ def run_mixed_same_workload(args, cfg64, work, genvec, dev, stream, flush, M):
     cfg["precision"] = "mixed_tf32"
     ns = n_samples(work)
     ctx = M.Context.from_config(cfg, genvec=genvec, max_samples=ns)
+    force_smoother(ctx, args.smoother)
     nl, R = cfg["n_levels"], cfg["R"]
     sums = torch.zeros(nl * R * 2, dtype=torch.float64, device=dev)
 
@@ -442,7 +457,8 @@ def run_mixed_same_workload(args, cfg64, work, genvec, dev, stream, flush, M):
     roof, by_kind = roofline_report(prof, pwork, args.steps)
     return {"value": ns * args.steps / (tot * 1e-3), "unit": UNIT, "ms_per_step": tot / args.steps,
             "dtype": "f32 V-cycles in f64 refinement, TF32 tensor-core KL, f32 field",
-            "roofline": roof, "roofline_by_kind": by_kind}
+            "roofline": roof, "roofline_by_kind": by_kind,
+            "smoothers": [{"level": t, "kind": k, "tuned_ms": ms} for t, (k, ms) in enumerate(ctx.smoother_info())]}
 
 
 def run_precision_form(dev, stream, flush, M):

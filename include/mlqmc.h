@@ -53,6 +53,14 @@ typedef enum {
 } mlqmc_precision;
 
 typedef enum { MLQMC_QOI_CENTER = 0, MLQMC_QOI_MEAN = 1 } mlqmc_qoi;
+
+/* Smoother of a level's red-black sweeps (all compute the same sweeps). */
+typedef enum {
+    MLQMC_SMOOTHER_GS = 0,     /* one launch per colour (FP64 form) */
+    MLQMC_SMOOTHER_TILE = 1,   /* shared-memory tiles staged by plain loads, two sweeps per launch */
+    MLQMC_SMOOTHER_STREAM = 2, /* row wavefront with bulk-copy rings, residual/correction fused (n <= 256) */
+    MLQMC_SMOOTHER_TMA = 3     /* 32 x 32 tiles staged by TMA tensor copies, double-buffered (n >= 64) */
+} mlqmc_smoother;
 typedef enum { MLQMC_SAMPLER_MC = 0, MLQMC_SAMPLER_LATTICE = 1 } mlqmc_sampler;
 
 /*
@@ -220,7 +228,8 @@ mlqmc_status mlqmc_normals(mlqmc_ctx* c, int32_t level, int32_t r, int64_t n_beg
  * Field on grid level t for `count` normal vectors d_y[i*s + j] (device):
  * d_k[i*n_t^2 + i2*n_t + i1] = exp(z_s) at cell centres, FP64 output, computed
  * in the context's precision (FP64 form: FP64 synthesis; mixed forms: the
- * tensor-core contraction, rounded to FP32, widened).
+ * tensor-core contraction, rounded to FP32, widened). MLQMC_ERR_INVALID_ARG
+ * when count exceeds max_samples or count x n_t (n_t + 1) reaches 2^31.
  */
 mlqmc_status mlqmc_fields(mlqmc_ctx* c, int32_t t, const double* d_y, int32_t count, double* d_k,
                           void* stream);
@@ -277,6 +286,23 @@ mlqmc_status mlqmc_last_iterations(mlqmc_ctx* c, int32_t* out);
 
 /* Kernel launches issued by this context since creation (all entry points). */
 int64_t mlqmc_launch_count(const mlqmc_ctx* c);
+
+/*
+ * Smoother per level of the FP32 V-cycles (mixed forms). mlqmc_create picks
+ * one per level: where more than one smoother can run a level, an autotuner
+ * times one V-cycle visit of that level (pre-smoothing with the restricted
+ * residual, correction and post-smoothing) of each on min(max_samples, 1024)
+ * samples of scratch data and keeps the fastest.
+ * mlqmc_smoother_info: kind (host, n_levels int32, MLQMC_SMOOTHER_*; level 0
+ * has no sweeps and reports 0) and tuned_ms (host, n_levels x 4 doubles,
+ * [level][kind] milliseconds of the tuning visit, 0 where not timed); either
+ * may be NULL. FP64 form: every level MLQMC_SMOOTHER_GS.
+ * mlqmc_set_smoother: force `kind` on `level` (1 <= level < n_levels) for
+ * later calls; MLQMC_ERR_INVALID_ARG if that smoother cannot run the level
+ * (kind GS, or a side it does not handle) or the form is FP64.
+ */
+mlqmc_status mlqmc_smoother_info(const mlqmc_ctx* c, int32_t* kind, double* tuned_ms);
+mlqmc_status mlqmc_set_smoother(mlqmc_ctx* c, int32_t level, int32_t kind);
 
 /*
  * Per-kernel device timing of mlqmc_sample_levels (off by default). With

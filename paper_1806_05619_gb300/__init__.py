@@ -99,11 +99,13 @@ def lib():
             L.mlqmc_profile.argtypes = [vp, i32]
             L.mlqmc_profile_read.argtypes = [vp, dp, C.POINTER(C.c_int64)]
             L.mlqmc_profile_work.argtypes = [vp, dp, dp, dp, dp]
+            L.mlqmc_smoother_info.argtypes = [vp, C.POINTER(C.c_int32), dp]
+            L.mlqmc_set_smoother.argtypes = [vp, i32, i32]
             L.mlqmc_launch_count.argtypes = [vp]
             L.mlqmc_launch_count.restype = i64
             for name in ["mlqmc_create", "mlqmc_sample_levels", "mlqmc_estimate", "mlqmc_get_device_status",
                          "mlqmc_cbc_genvec", "mlqmc_modes", "mlqmc_point_bits", "mlqmc_normals", "mlqmc_fields",
-                         "mlqmc_sample_solution", "mlqmc_profile", "mlqmc_profile_read", "mlqmc_profile_work",
+                         "mlqmc_sample_solution", "mlqmc_profile", "mlqmc_profile_read", "mlqmc_profile_work", "mlqmc_smoother_info", "mlqmc_set_smoother",
                          "mlqmc_fmg_fields_noalloc", "mlqmc_last_iterations"]:
                 getattr(L, name).restype = C.c_int
             _lib = L
@@ -285,6 +287,21 @@ class Context:
         out = (C.c_int32 * self.n_levels)()
         _check(lib().mlqmc_last_iterations(self.h, out), "mlqmc_last_iterations")
         return list(out)
+
+    SMOOTHERS = ["gs", "tile", "stream", "tma"]
+
+    def smoother_info(self):
+        """Per level (smoother name, {name: tuned ms}); level 0 has no sweeps."""
+        kind = (C.c_int32 * self.n_levels)()
+        ms = np.zeros(self.n_levels * 4)
+        _check(lib().mlqmc_smoother_info(self.h, kind, ms.ctypes.data_as(C.POINTER(C.c_double))), "mlqmc_smoother_info")
+        ms = ms.reshape(self.n_levels, 4)
+        return [(self.SMOOTHERS[kind[t]], {self.SMOOTHERS[k]: float(ms[t, k]) for k in range(4) if ms[t, k] > 0})
+                for t in range(self.n_levels)]
+
+    def set_smoother(self, level: int, name: str):
+        """Force smoother `name` ("tile", "stream" or "tma") on `level` for later calls."""
+        _check(lib().mlqmc_set_smoother(self.h, int(level), self.SMOOTHERS.index(name)), "mlqmc_set_smoother")
 
     def launch_count(self) -> int:
         return int(lib().mlqmc_launch_count(self.h))

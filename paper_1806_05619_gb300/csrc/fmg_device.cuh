@@ -17,6 +17,10 @@ constexpr int kStatusNotConverged = 1;
 constexpr int kStatusCheck = 2;
 constexpr int kStatusTimeout = 4;  // a bounded device wait gave up (tensor-core KL pipeline)
 
+// Row pitch (elements) of the x-face array of an n x n level: n + 1 faces per
+// row padded to n + 4, so that every row starts on a 16-byte boundary.
+__host__ __device__ constexpr int kx_pitch(int n) { return n + 4; }
+
 // Array of per-sample blocks: block i starts at base + i * stride (bytes).
 struct ArrDesc {
     unsigned char* base;
@@ -33,7 +37,7 @@ struct Lv {
     int n;
     T* u;      // iterate (FMG solution on the current top level, correction below it)
     T* bc;     // right-hand side of the coarse correction equation
-    T* kx;     // x faces: row i2, face f between cells f-1 and f, [i2*(n+1) + f]; f = 0, n hold 2k (boundary)
+    T* kx;     // x faces: row i2, face f between cells f-1 and f, [i2*kx_pitch(n) + f]; f = 0, n hold 2k (boundary)
     T* ky;     // y faces: face g between rows g-1 and g, [g*n + i1]; g = 0, n hold 2k (boundary)
     T* idiag;  // 1 / (sum of the four face coefficients)
     T* k;      // coefficient exp(z) at the cell centres
@@ -171,7 +175,8 @@ __device__ __forceinline__ T face_y(const T* k, int n, int g, int i1)
 template <typename T>
 __device__ __forceinline__ T inv_diag(const T* kx, const T* ky, int n, int i1, int i2)
 {
-    return T(1) / (kx[i2 * (n + 1) + i1] + kx[i2 * (n + 1) + i1 + 1] + ky[i2 * n + i1] + ky[(i2 + 1) * n + i1]);
+    const T* kr = kx + i2 * kx_pitch(n);
+    return T(1) / (kr[i1] + kr[i1 + 1] + ky[i2 * n + i1] + ky[(i2 + 1) * n + i1]);
 }
 
 // KL field on one level (eq. truncatedKL at the level's own cell centres):
@@ -202,7 +207,7 @@ __device__ void synth_level(const TM& tm, const FmgArgs& A, const Lv<T>& L, int 
     tm.sync();
     for (int idx = tm.rank(); idx < n * (n + 1); idx += tm.size()) {
         const int i2 = idx / (n + 1);
-        L.kx[idx] = face_x(L.k, n, i2, idx - i2 * (n + 1));
+        L.kx[i2 * kx_pitch(n) + idx - i2 * (n + 1)] = face_x(L.k, n, i2, idx - i2 * (n + 1));
         const int g = idx / n;
         L.ky[idx] = face_y(L.k, n, g, idx - g * n);
     }
@@ -220,7 +225,7 @@ __device__ __forceinline__ void gs_cell(const Lv<T>& L, const T* b, T h2, int i1
 {
     const int n = L.n;
     const int p = i2 * n + i1;
-    const T* kx = L.kx + i2 * (n + 1);
+    const T* kx = L.kx + i2 * kx_pitch(n);
     T acc = h2 * (b ? b[p] : T(1));
     if (i1 > 0) acc += kx[i1] * L.u[p - 1];
     if (i1 < n - 1) acc += kx[i1 + 1] * L.u[p + 1];
@@ -251,8 +256,8 @@ __device__ __forceinline__ U apply_h2(const T* kx, const T* ky, const U* u, int 
 {
     const int p = i2 * n + i1;
     const U up = u[p];
-    U acc = U(kx[i2 * (n + 1) + i1]) * (up - (i1 > 0 ? u[p - 1] : U(0)));
-    acc += U(kx[i2 * (n + 1) + i1 + 1]) * (up - (i1 < n - 1 ? u[p + 1] : U(0)));
+    U acc = U(kx[i2 * kx_pitch(n) + i1]) * (up - (i1 > 0 ? u[p - 1] : U(0)));
+    acc += U(kx[i2 * kx_pitch(n) + i1 + 1]) * (up - (i1 < n - 1 ? u[p + 1] : U(0)));
     acc += U(ky[i2 * n + i1]) * (up - (i2 > 0 ? u[p - n] : U(0)));
     acc += U(ky[(i2 + 1) * n + i1]) * (up - (i2 < n - 1 ? u[p + n] : U(0)));
     return acc;
@@ -328,7 +333,7 @@ __device__ void chol_factor(const TM& tm, double* Lb, int n0, const F* kx, const
         const int N = n0 * n0, W = n0 + 1, lane = threadIdx.x & 31;
         for (int j = 0; j < N; ++j) {
             const int j1 = j % n0, j2 = j / n0;
-            double d = static_cast<double>(kx[j2 * (n0 + 1) + j1]) + static_cast<double>(kx[j2 * (n0 + 1) + j1 + 1]) +
+            double d = static_cast<double>(kx[j2 * kx_pitch(n0) + j1]) + static_cast<double>(kx[j2 * kx_pitch(n0) + j1 + 1]) +
                        static_cast<double>(ky[j2 * n0 + j1]) + static_cast<double>(ky[(j2 + 1) * n0 + j1]);
             for (int q = 1; q <= n0 && q <= j; ++q) {
                 const double l = Lb[j * W + q];
@@ -340,7 +345,7 @@ __device__ void chol_factor(const TM& tm, double* Lb, int n0, const F* kx, const
                 const int i = j + lane;
                 const int i1 = i % n0, i2 = i / n0;
                 double a = 0.0;
-                if (lane == 1 && i1 > 0) a = -static_cast<double>(kx[i2 * (n0 + 1) + i1]);
+                if (lane == 1 && i1 > 0) a = -static_cast<double>(kx[i2 * kx_pitch(n0) + i1]);
                 if (lane == n0) a = -static_cast<double>(ky[i2 * n0 + i1]);
                 for (int tt = (i - n0 > 0 ? i - n0 : 0); tt < j; ++tt) a -= Lb[i * W + (i - tt)] * Lb[j * W + (j - tt)];
                 Lb[i * W + lane] = a / Ljj;
@@ -445,8 +450,8 @@ __device__ __forceinline__ double apply_h2_64(const T* kx, const T* ky, const do
 {
     const int p = i2 * n + i1;
     const double up = u[p];
-    double acc = widen_pos(kx[i2 * (n + 1) + i1]) * (up - (i1 > 0 ? u[p - 1] : 0.0));
-    acc = fma(widen_pos(kx[i2 * (n + 1) + i1 + 1]), up - (i1 < n - 1 ? u[p + 1] : 0.0), acc);
+    double acc = widen_pos(kx[i2 * kx_pitch(n) + i1]) * (up - (i1 > 0 ? u[p - 1] : 0.0));
+    acc = fma(widen_pos(kx[i2 * kx_pitch(n) + i1 + 1]), up - (i1 < n - 1 ? u[p + 1] : 0.0), acc);
     acc = fma(widen_pos(ky[i2 * n + i1]), up - (i2 > 0 ? u[p - n] : 0.0), acc);
     acc = fma(widen_pos(ky[(i2 + 1) * n + i1]), up - (i2 < n - 1 ? u[p + n] : 0.0), acc);
     return acc;

@@ -25,6 +25,8 @@
 
 #include "fmg_device.cuh"
 #include "mlqmc_internal.h"
+#include "rbgs_stream.h"
+#include "rbgs_tma.h"
 
 using namespace mlqmc_dev;
 
@@ -88,9 +90,11 @@ __global__ void k_points(const SampleDesc* __restrict__ smp, int count, int s, i
     }
 }
 
-#define GRID_STRIDE(idx, total)                                                                         \
-    for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < (total); \
-         idx += static_cast<int64_t>(gridDim.x) * blockDim.x)
+// Flat loops in 32-bit indices: chunks are cut so that every level's
+// samples x elements stays below 2^31 (see mlqmc_sample_levels).
+#define GRID_STRIDE(idx, total)                                                                       \
+    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < static_cast<uint32_t>(total); \
+         idx += gridDim.x * blockDim.x)
 
 // ---------------------------------------------------------------------------
 // Level 0, one thread per sample. GB300 issues FP64 at a few operations per
@@ -104,7 +108,7 @@ template <typename T>
 __device__ __forceinline__ T band_a(const T* kx, const T* ky, int n0, int r, int l)
 {
     const int r1 = r % n0, r2 = r / n0;
-    if (l == 1 && r1 > 0) return -kx[r2 * (n0 + 1) + r1];
+    if (l == 1 && r1 > 0) return -kx[r2 * kx_pitch(n0) + r1];
     if (l == n0) return -ky[r2 * n0 + r1];
     return T(0);
 }
@@ -123,7 +127,7 @@ __global__ void kb_level0(FmgArgs A, int B)
         const Lv<T> L0 = view<T>(A, 0, i);
         for (int j = 0; j < N; ++j) {
             const int j1 = j % n0, j2 = j / n0;
-            double d = static_cast<double>(L0.kx[j2 * (n0 + 1) + j1]) + static_cast<double>(L0.kx[j2 * (n0 + 1) + j1 + 1]) +
+            double d = static_cast<double>(L0.kx[j2 * kx_pitch(n0) + j1]) + static_cast<double>(L0.kx[j2 * kx_pitch(n0) + j1 + 1]) +
                        static_cast<double>(L0.ky[j2 * n0 + j1]) + static_cast<double>(L0.ky[(j2 + 1) * n0 + j1]);
             for (int q = 1; q <= n0 && q <= j; ++q) {
                 const double l = fac[static_cast<size_t>(j * W + q) * cs + i];
@@ -163,6 +167,8 @@ __global__ void kb_level0(FmgArgs A, int B)
         }
         A.F[static_cast<size_t>(i) * A.n_levels] = F0;
         if constexpr (MX) {
+            float* u32 = reinterpret_cast<float*>(L0.u);  // FP32 copy for the first FMG interpolation
+            for (int r = 0; r < N; ++r) u32[r] = static_cast<float>(x[r]);
             float* f32 = reinterpret_cast<float*>(A.chol32);
             for (int q = 0; q < N * W; ++q) f32[static_cast<size_t>(q) * cs + i] = static_cast<float>(fac[static_cast<size_t>(q) * cs + i]);
         }
@@ -286,7 +292,7 @@ __global__ void kb_synth_G(FmgArgs A, int t, int B)
 {
     const int n = A.lv[t].n;
     const T* psi = static_cast<const T*>(A.psi) + A.psi_off[t];
-    const int64_t per = static_cast<int64_t>(A.Ka) * n;
+    const uint32_t per = static_cast<uint32_t>(A.Ka) * static_cast<uint32_t>(n);
     GRID_STRIDE(idx, B * per)
     {
         const int i = static_cast<int>(idx / per);
@@ -308,7 +314,7 @@ __global__ void kb_synth_z(FmgArgs A, int t, int B)
 {
     const int n = A.lv[t].n;
     const T* psi = static_cast<const T*>(A.psi) + A.psi_off[t];
-    const int64_t per = static_cast<int64_t>(n) * n;
+    const uint32_t per = static_cast<uint32_t>(n) * static_cast<uint32_t>(n);
     GRID_STRIDE(idx, B * per)
     {
         const int i = static_cast<int>(idx / per);
@@ -326,14 +332,14 @@ template <typename T>
 __global__ void kb_faces(FmgArgs A, int t, int B)
 {
     const int n = A.lv[t].n;
-    const int64_t per = static_cast<int64_t>(n) * (n + 1);
+    const uint32_t per = static_cast<uint32_t>(n) * static_cast<uint32_t>((n + 1));
     GRID_STRIDE(idx, B * per)
     {
         const int i = static_cast<int>(idx / per);
         const int q = static_cast<int>(idx - i * per);
         const T* k = at<T>(A.lv[t].k, i);
         const int i2 = q / (n + 1);
-        at<T>(A.lv[t].kx, i)[q] = face_x(k, n, i2, q - i2 * (n + 1));
+        at<T>(A.lv[t].kx, i)[i2 * kx_pitch(n) + q - i2 * (n + 1)] = face_x(k, n, i2, q - i2 * (n + 1));
         const int g = q / n;
         at<T>(A.lv[t].ky, i)[q] = face_y(k, n, g, q - g * n);
     }
@@ -343,7 +349,7 @@ template <typename T>
 __global__ void kb_idiag(FmgArgs A, int t, int B)
 {
     const int n = A.lv[t].n;
-    const int64_t per = static_cast<int64_t>(n) * n;
+    const uint32_t per = static_cast<uint32_t>(n) * static_cast<uint32_t>(n);
     GRID_STRIDE(idx, B * per)
     {
         const int i = static_cast<int>(idx / per);
@@ -359,7 +365,7 @@ __global__ void kb_gs(FmgArgs A, int t, int B, int colour, int ones)
 {
     const int n = A.lv[t].n;
     const int half = n >> 1;
-    const int64_t per = static_cast<int64_t>(n) * half;
+    const uint32_t per = static_cast<uint32_t>(n) * static_cast<uint32_t>(half);
     const T h2 = T(1) / (T(n) * T(n));
     GRID_STRIDE(idx, B * per)
     {
@@ -400,7 +406,7 @@ __global__ void __launch_bounds__(256) kb_rbgs_tile(FmgArgs A, int t, int B, int
     float* skx = sky + (SU + 1) * SU;                // SU rows x (SU + 1) faces
     const int n = A.lv[t].n;
     const int tx_n = n / TILE;
-    const int64_t per = static_cast<int64_t>(tx_n) * tx_n;
+    const uint32_t per = static_cast<uint32_t>(tx_n) * static_cast<uint32_t>(tx_n);
     const float h2 = 1.0f / (static_cast<float>(n) * static_cast<float>(n));
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int64_t tile = blockIdx.x; tile < B * per; tile += gridDim.x) {
@@ -440,12 +446,12 @@ __global__ void __launch_bounds__(256) kb_rbgs_tile(FmgArgs A, int t, int B, int
             const bool in = gy >= 0 && gy <= n && gx >= 0 && gx < n;
             reinterpret_cast<float4*>(sky)[q] = in ? *reinterpret_cast<const float4*>(L.ky + static_cast<size_t>(gy) * n + gx) : z4;
         }
-        // x faces: rows y0-H.., faces x0-H .. x0-H+SU (row pitch n+1: scalar loads)
+        // x faces: rows y0-H.., faces x0-H .. x0-H+SU (row pitch kx_pitch(n): scalar loads)
 #pragma unroll 4
         for (int q = threadIdx.x; q < SU * (SU + 1); q += blockDim.x) {
             const int r = q / (SU + 1), f = q - (q / (SU + 1)) * (SU + 1);
             const int gy = y0 - H + r, gx = x0 - H + f;
-            skx[q] = (gy >= 0 && gy < n && gx >= 0 && gx <= n) ? L.kx[static_cast<size_t>(gy) * (n + 1) + gx] : 0.f;
+            skx[q] = (gy >= 0 && gy < n && gx >= 0 && gx <= n) ? L.kx[static_cast<size_t>(gy) * kx_pitch(n) + gx] : 0.f;
         }
         __syncthreads();
 #pragma unroll
@@ -488,7 +494,7 @@ template <typename T>
 __global__ void kb_resid_restrict(FmgArgs A, int t, int B, int ones)
 {
     const int nc = A.lv[t].n >> 1;
-    const int64_t per = static_cast<int64_t>(nc) * nc;
+    const uint32_t per = static_cast<uint32_t>(nc) * static_cast<uint32_t>(nc);
     GRID_STRIDE(idx, B * per)
     {
         const int i = static_cast<int>(idx / per);
@@ -506,7 +512,7 @@ __global__ void kb_prolong(FmgArgs A, int t, int B)
 {
     const int n = A.lv[t].n;
     const int nc = n >> 1;
-    const int64_t per = static_cast<int64_t>(n) * n;
+    const uint32_t per = static_cast<uint32_t>(n) * static_cast<uint32_t>(n);
     GRID_STRIDE(idx, B * per)
     {
         const int i = static_cast<int>(idx / per);
@@ -515,7 +521,12 @@ __global__ void kb_prolong(FmgArgs A, int t, int B)
         const int i2 = p / n;
         const int i1 = p - i2 * n;
         if constexpr (U64) {
-            const double v = prolong_cell<double, double>(at<double>(A.lv[t - 1].u64, i), nc, i1, i2);
+            // FMG interpolation of the refinement path into u64: mixed forms
+            // interpolate the FP32 copy of the coarse solution in FP32 (the
+            // first FP64 residual then sees it exactly), FP64 form in FP64
+            double v;
+            if constexpr (sizeof(T) == 4) v = static_cast<double>(prolong_cell<float, float>(at<float>(A.lv[t - 1].u, i), nc, i1, i2));
+            else v = prolong_cell<double, double>(at<double>(A.lv[t - 1].u64, i), nc, i1, i2);
             double* u = at<double>(A.lv[t].u64, i);
             if (ADD) u[p] += v;
             else u[p] = v;
@@ -533,7 +544,7 @@ template <typename T>
 __global__ void kb_resid64(FmgArgs A, int t, int B)
 {
     const int n = A.lv[t].n;
-    const int64_t per = static_cast<int64_t>(n) * n;
+    const uint32_t per = static_cast<uint32_t>(n) * static_cast<uint32_t>(n);
     GRID_STRIDE(idx, B * per)
     {
         const int i = static_cast<int>(idx / per);
@@ -550,7 +561,7 @@ template <typename T>
 __global__ void kb_update64(FmgArgs A, int t, int B)
 {
     const int n = A.lv[t].n;
-    const int64_t per = static_cast<int64_t>(n) * n;
+    const uint32_t per = static_cast<uint32_t>(n) * static_cast<uint32_t>(n);
     GRID_STRIDE(idx, B * per)
     {
         const int i = static_cast<int>(idx / per);
@@ -598,6 +609,13 @@ __global__ void __launch_bounds__(256) kb_qoi(FmgArgs A, int t, int B)
         if constexpr (U64) v = qoi(tm, at<double>(A.lv[t].u64, i), A.lv[t].n, A.qoi, red);
         else v = qoi(tm, at<T>(A.lv[t].u, i), A.lv[t].n, A.qoi, red);
         if (threadIdx.x == 0) A.F[static_cast<size_t>(i) * A.n_levels + t] = v;
+        if constexpr (U64 && sizeof(T) == 4) {
+            // mixed forms: FP32 copy of the level's solution for the next FMG interpolation
+            const double* u64 = at<double>(A.lv[t].u64, i);
+            float* u = at<float>(A.lv[t].u, i);
+            const int nn = A.lv[t].n * A.lv[t].n;
+            for (int p = threadIdx.x; p < nn; p += blockDim.x) u[p] = static_cast<float>(u64[p]);
+        }
     }
 }
 
@@ -606,7 +624,7 @@ template <typename T>
 __global__ void kb_k_out(FmgArgs A, int t, int B, double* out)
 {
     const int n = A.lv[t].n;
-    const int64_t per = static_cast<int64_t>(n) * n;
+    const uint32_t per = static_cast<uint32_t>(n) * static_cast<uint32_t>(n);
     GRID_STRIDE(idx, B * per)
     {
         const int i = static_cast<int>(idx / per);
@@ -620,7 +638,7 @@ template <typename T, bool U64>
 __global__ void kb_u_out(FmgArgs A, int t, double* out)
 {
     const int n = A.lv[t].n;
-    GRID_STRIDE(p, static_cast<int64_t>(n) * n)
+    GRID_STRIDE(p, static_cast<uint32_t>(n) * static_cast<uint32_t>(n))
     {
         if constexpr (U64) out[p] = at<double>(A.lv[t].u64, 0)[p];
         else out[p] = static_cast<double>(at<T>(A.lv[t].u, 0)[p]);
@@ -656,7 +674,7 @@ __global__ void k_sums(const SampleDesc* __restrict__ smp, int n, const double* 
 __global__ void k_fout(const SampleDesc* __restrict__ smp, int n, const double* __restrict__ F, int n_levels,
                        double* __restrict__ out)
 {
-    GRID_STRIDE(idx, static_cast<int64_t>(n) * n_levels)
+    GRID_STRIDE(idx, static_cast<uint32_t>(n) * static_cast<uint32_t>(n_levels))
     {
         const int q = static_cast<int>(idx / n_levels);
         const int t = static_cast<int>(idx - static_cast<int64_t>(q) * n_levels);
@@ -683,13 +701,20 @@ void level_strides(const mlqmc_problem& p, int Ka, int t, size_t st[kPoolArrs])
     const size_t es = elem_size(p);
     st[kU] = align256(es * n * n);
     st[kBc] = align256(es * n * n);
-    st[kKx] = align256(es * n * (n + 1));
+    st[kKx] = align256(es * n * kx_pitch(static_cast<int>(n)));
     st[kKy] = align256(es * n * (n + 1));
     st[kIdiag] = align256(es * n * n);
     st[kK] = align256(es * n * n);
     st[kG] = align256(es * static_cast<size_t>(std::max(Ka, 1)) * n);
     st[kU64] = (is_mixed(p) || p.refine_rtol > 0.0) ? align256(8 * n * n) : 0;
     st[kU2] = t > 0 ? align256(es * n * n) : 0;
+}
+
+// Most elements one sample of level t has in a flat kernel loop (faces, cells, KL partial sums).
+uint64_t level_elems_per_sample(const mlqmc_problem& p, int Ka, int t)
+{
+    const uint64_t n = static_cast<uint64_t>(p.coarse_cells) << t;
+    return std::max<uint64_t>(n * (n + 1), static_cast<uint64_t>(std::max(Ka, 1)) * n);
 }
 
 size_t level_bytes_per_sample(const mlqmc_problem& p, int Ka, int t)
@@ -904,6 +929,32 @@ mlqmc_status launch_points(mlqmc_ctx* c, const SampleDesc* d_s, int count, doubl
     return last_error();
 }
 
+// Smoother of level t's sweeps in working precision T (FP64: kb_gs).
+template <typename T>
+int smoother_of(const mlqmc_ctx* c, int t)
+{
+    return sizeof(T) == 8 ? MLQMC_SMOOTHER_GS : c->smoother[t];
+}
+
+// True when level t's FP32 sweeps run on the wavefront smoother (rbgs_stream.cu).
+template <typename T>
+bool streams(const mlqmc_ctx* c, int t)
+{
+    return smoother_of<T>(c, t) == MLQMC_SMOOTHER_STREAM;
+}
+
+// Whether smoother kind k can run level t (FP32 arrays).
+bool smoother_fits(const mlqmc_ctx* c, int k, int t)
+{
+    const int n = c->p.coarse_cells << t;
+    switch (k) {
+    case MLQMC_SMOOTHER_STREAM: return mlqmc_stream::supported(n);
+    case MLQMC_SMOOTHER_TMA: return mlqmc_tma::supported(n);
+    case MLQMC_SMOOTHER_TILE: return n == 8 || n == 16 || (n >= 32 && n % 32 == 0);
+    default: return true;
+    }
+}
+
 // True when level t's field comes from the tensor-core contraction.
 bool uses_tc(const mlqmc_ctx* c, int t)
 {
@@ -947,7 +998,7 @@ mlqmc_status synth_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cudaStr
         Timed tm(c, kProfSynth, st, work_of<T>(B * es * (Mc + 2.0 * Fc), B * 6.0 * Fc));
         kb_faces<T><<<grid_for(c, B * n * (n + 1)), 256, 0, st>>>(A, t, B);
     }
-    {
+    if (t > 0 && smoother_of<T>(c, t) <= MLQMC_SMOOTHER_TILE) {  // 1/D: only kb_gs and kb_rbgs_tile read it
         Timed tm(c, kProfSynth, st, work_of<T>(B * es * (2.0 * Fc + Mc), B * 5.0 * Mc));
         kb_idiag<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
     }
@@ -1023,7 +1074,7 @@ template <typename T>
 int tile_side(const mlqmc_ctx* c, int t)
 {
     const int64_t n = c->p.coarse_cells << t;
-    if (sizeof(T) == 8) return 0;
+    if (sizeof(T) == 8 || c->smoother[t] != MLQMC_SMOOTHER_TILE) return 0;
     return n >= 32 && n % 32 == 0 ? 32 : (n == 16 ? 16 : (n == 8 ? 8 : 0));
 }
 
@@ -1069,18 +1120,87 @@ void smooth(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int first, int 
     }
 }
 
+// nsweeps sweeps of level t by the wavefront smoother, two per launch, u in
+// place; post: the first launch adds P e first; pre: the last launch also
+// writes the restricted residual into bc of level t-1.
+mlqmc_status smooth_stream(mlqmc_ctx* c, const FmgArgs& A, int t, int B, int nsweeps, int first, int ones, bool pre,
+                           bool post, cudaStream_t st)
+{
+    const int n = c->p.coarse_cells << t;
+    const double Mc = cells_of(c, t), Fc = faces_of(c, t);
+    while (nsweeps > 0) {
+        const int ns = nsweeps >= 2 ? 2 : 1;
+        const bool last = nsweeps == ns;
+        const bool p = pre && last;
+        Work w;
+        w.bytes = 4.0 * B * ((ones ? 2.0 : 3.0) * Mc + 2.0 * Fc + (post ? 0.25 * Mc : 0.0) + (p ? 0.25 * Mc : 0.0));
+        w.f32 = B * (10.0 * ns * Mc + (post ? 8.0 * Mc : 0.0) + (p ? 11.0 * Mc : 0.0));
+        Timed tm(c, kProfSmooth, st, w);
+        if (!mlqmc_stream::launch(A, t, n, B, ns, ones, first, p, post, st)) return MLQMC_ERR_CUDA;
+        post = false;
+        nsweeps -= ns;
+    }
+    return MLQMC_OK;
+}
+
+// nsweeps sweeps of level t by the TMA-fed tiled smoother, two per launch, u
+// -> u2 swapped after each launch; pro: the first launch adds P e first.
+mlqmc_status smooth_tma(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int first, int ones, bool pro,
+                        cudaStream_t st)
+{
+    const int n = c->p.coarse_cells << t;
+    const double Mc = cells_of(c, t), Fc = faces_of(c, t);
+    while (nsweeps > 0) {
+        const int ns = nsweeps >= 2 ? 2 : 1;
+        const Work w = work_of<float>(4.0 * B * ((ones ? 3.0 : 4.0) * Mc + 2.0 * Fc + (pro ? 0.25 * Mc : 0.0)),
+                                      B * (10.0 * ns * Mc + (pro ? 8.0 * Mc : 0.0)));
+        Timed tm(c, kProfSmooth, st, w);
+        if (!mlqmc_tma::launch(A, t, n, B, ns, ones, first, pro, c->sm_count, st)) return MLQMC_ERR_CUDA;
+        swap_u(c, A, t);
+        pro = false;
+        nsweeps -= ns;
+    }
+    return MLQMC_OK;
+}
+
+// Pre-smoothing of level t and the restricted residual into bc of level t-1.
+template <typename T>
+mlqmc_status presmooth_restrict(mlqmc_ctx* c, FmgArgs& A, int t, int B, int top_ones, cudaStream_t st)
+{
+    const int sk = smoother_of<T>(c, t);
+    if (sk == MLQMC_SMOOTHER_STREAM && c->p.nu1 > 0)  // residual and restriction fused into the last pass
+        return smooth_stream(c, A, t, B, c->p.nu1, 0, top_ones, true, false, st);
+    if (sk == MLQMC_SMOOTHER_TMA && c->p.nu1 > 0) {
+        if (smooth_tma(c, A, t, B, c->p.nu1, 0, top_ones, false, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
+    } else {
+        smooth<T>(c, A, t, B, c->p.nu1, 0, top_ones, false, st);
+    }
+    const int64_t n = c->p.coarse_cells << t;
+    const double es = sizeof(T), Mc = cells_of(c, t), Fc = faces_of(c, t);
+    Timed tm(c, kProfTransfer, st, work_of<T>(B * es * ((top_ones ? 1.25 : 2.25) * Mc + 2.0 * Fc), B * 11.0 * Mc));
+    kb_resid_restrict<T><<<grid_for(c, B * n * n / 4), 256, 0, st>>>(A, t, B, top_ones);
+    return last_error();
+}
+
+// Coarse-grid correction of level t and its post-smoothing.
+template <typename T>
+mlqmc_status correct_postsmooth(mlqmc_ctx* c, FmgArgs& A, int t, int B, int top_ones, cudaStream_t st)
+{
+    const int sk = smoother_of<T>(c, t);
+    if (sk == MLQMC_SMOOTHER_STREAM && c->p.nu2 > 0)  // the correction fused into the first pass
+        return smooth_stream(c, A, t, B, c->p.nu2, 1, top_ones, false, true, st);
+    if (sk == MLQMC_SMOOTHER_TMA && c->p.nu2 > 0) return smooth_tma(c, A, t, B, c->p.nu2, 1, top_ones, true, st);
+    smooth<T>(c, A, t, B, c->p.nu2, 1, top_ones, true, st);
+    return last_error();
+}
+
 template <typename T>
 mlqmc_status vcycle_batched(mlqmc_ctx* c, FmgArgs& A, int t_top, int B, bool ones, cudaStream_t st)
 {
     for (int t = t_top; t >= 1; --t) {
-        const int64_t n = c->p.coarse_cells << t;
         const int top_ones = (t == t_top && ones) ? 1 : 0;
         if (t < t_top && zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
-        smooth<T>(c, A, t, B, c->p.nu1, 0, top_ones, false, st);
-        const double es = sizeof(T), Mc = cells_of(c, t), Fc = faces_of(c, t);
-        Timed tm(c, kProfTransfer, st,
-                 work_of<T>(B * es * ((top_ones ? 1.25 : 2.25) * Mc + 2.0 * Fc), B * 11.0 * Mc));
-        kb_resid_restrict<T><<<grid_for(c, B * n * n / 4), 256, 0, st>>>(A, t, B, top_ones);
+        if (presmooth_restrict<T>(c, A, t, B, top_ones, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
     }
     {
         const double N0 = cells_of(c, 0), n0 = c->p.coarse_cells, es = sizeof(T);
@@ -1089,7 +1209,7 @@ mlqmc_status vcycle_batched(mlqmc_ctx* c, FmgArgs& A, int t_top, int B, bool one
     }
     for (int t = 1; t <= t_top; ++t) {
         const int top_ones = (t == t_top && ones) ? 1 : 0;
-        smooth<T>(c, A, t, B, c->p.nu2, 1, top_ones, true, st);
+        if (correct_postsmooth<T>(c, A, t, B, top_ones, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
     }
     return last_error();
 }
@@ -1150,7 +1270,7 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
         const double es = sizeof(T), Mc = cells_of(c, t), Fc = faces_of(c, t);
         if (refine) {
             {
-                Timed tm(c, kProfTransfer, st, work_of<double>(B * 8.0 * 1.25 * Mc, B * 8.0 * Mc));
+                Timed tm(c, kProfTransfer, st, work_of<T>(B * (es * 0.25 + 8.0) * Mc, B * 8.0 * Mc));
                 kb_prolong<T, false, true><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
             }
             {
@@ -1181,7 +1301,8 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
             }
         }
         {
-            Timed tm(c, kProfReduce, st, work_of<double>(B * (refine ? 8.0 : es) * Mc, B * Mc));
+            Timed tm(c, kProfReduce, st,
+                     work_of<double>(B * ((refine ? 8.0 : es) + (refine && sizeof(T) == 4 ? 4.0 : 0.0)) * Mc, B * Mc));
             if (refine) kb_qoi<T, true><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
             else kb_qoi<T, false><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
         }
@@ -1193,6 +1314,82 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
         }
     }
     return last_error();
+}
+
+// Default smoother per level: the FP32 wavefront where it fits, else the TMA
+// tiles, else the plain tiles; FP64 form: kb_gs.
+void default_smoothers(mlqmc_ctx* c)
+{
+    for (int t = 0; t < c->p.n_levels; ++t) {
+        if (t == 0 || !is_mixed(c->p)) c->smoother[t] = MLQMC_SMOOTHER_GS;
+        else if (smoother_fits(c, MLQMC_SMOOTHER_STREAM, t)) c->smoother[t] = MLQMC_SMOOTHER_STREAM;
+        else if (smoother_fits(c, MLQMC_SMOOTHER_TMA, t)) c->smoother[t] = MLQMC_SMOOTHER_TMA;
+        else c->smoother[t] = MLQMC_SMOOTHER_TILE;
+    }
+}
+
+// Autotuner (mixed forms): for every level that more than one smoother can
+// run, time one V-cycle visit of the level (pre-smoothing and the restricted
+// residual, correction and post-smoothing) of each candidate on B samples of
+// zeroed scratch pools (the timing does not depend on the values) and keep
+// the fastest. Runs once, at creation, on its own stream.
+mlqmc_status tune_smoothers(mlqmc_ctx* c, int64_t max_samples)
+{
+    default_smoothers(c);
+    if (!is_mixed(c->p)) return MLQMC_OK;
+    const int64_t launches0 = c->launches;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!ok(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) || !ok(cudaEventCreate(&e0)) ||
+        !ok(cudaEventCreate(&e1)))
+        return MLQMC_ERR_CUDA;
+    mlqmc_status res = MLQMC_OK;
+    const int cands[2] = {MLQMC_SMOOTHER_STREAM, MLQMC_SMOOTHER_TMA};
+    for (int t = 1; t < c->p.n_levels && res == MLQMC_OK; ++t) {
+        if (!smoother_fits(c, cands[0], t) || !smoother_fits(c, cands[1], t)) continue;
+        int64_t B = std::max<int64_t>(1, std::min<int64_t>(max_samples, 1024));
+        const size_t per = level_bytes_per_sample(c->p, c->Ka, t) + level_bytes_per_sample(c->p, c->Ka, t - 1);
+        while (B > 64 && per * static_cast<size_t>(B) > c->pool_budget / 4) B /= 2;
+        if (ensure_pool(c, t - 1, B) != MLQMC_OK || ensure_pool(c, t, B) != MLQMC_OK) {
+            res = MLQMC_ERR_OOM;
+            break;
+        }
+        for (int u = t - 1; u <= t; ++u) {
+            const LevelPool& P = c->pools[u];
+            const size_t bytes = level_bytes_per_sample(c->p, c->Ka, u) * static_cast<size_t>(P.cap);
+            if (!ok(cudaMemsetAsync(P.mem, 0, bytes, st))) res = MLQMC_ERR_CUDA;
+        }
+        double best = 0.0;
+        for (int k = 0; k < 2 && res == MLQMC_OK; ++k) {
+            c->smoother[t] = cands[k];
+            FmgArgs A = base_args(c);
+            float ms = 0.0f, tot = 0.0f;
+            for (int rep = 0; rep < 4 && res == MLQMC_OK; ++rep) {  // one untimed visit, then three timed
+                if (!ok(cudaEventRecord(e0, st))) res = MLQMC_ERR_CUDA;
+                if (res == MLQMC_OK) res = presmooth_restrict<float>(c, A, t, static_cast<int>(B), 0, st);
+                if (res == MLQMC_OK) res = correct_postsmooth<float>(c, A, t, static_cast<int>(B), 0, st);
+                if (res == MLQMC_OK && (!ok(cudaEventRecord(e1, st)) || !ok(cudaEventSynchronize(e1)) ||
+                                        !ok(cudaEventElapsedTime(&ms, e0, e1))))
+                    res = MLQMC_ERR_CUDA;
+                if (rep > 0) tot += ms;
+            }
+            c->tune_ms[t][cands[k]] = tot / 3.0;
+            if (k == 0 || tot / 3.0 < best) best = tot / 3.0;
+        }
+        c->smoother[t] = c->tune_ms[t][cands[1]] < c->tune_ms[t][cands[0]] ? cands[1] : cands[0];
+    }
+    if (res == MLQMC_OK && !ok(cudaStreamSynchronize(st))) res = MLQMC_ERR_CUDA;
+    if (res == MLQMC_OK && c->host_status == 0) {
+        int dev = 0;
+        if (!ok(cudaMemcpy(&dev, c->d_status, sizeof(int), cudaMemcpyDeviceToHost))) res = MLQMC_ERR_CUDA;
+        else if (dev != 0) res = MLQMC_ERR_DEVICE_STATUS;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    c->launches = launches0;
+    if (res != MLQMC_OK) default_smoothers(c);
+    return res;
 }
 
 // Everything for one chunk of samples already staged in d_samples (rank order).
@@ -1419,7 +1616,7 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
     }
 
     // shared memory of the tiled smoother
-    if (!(tile_attrs<32>() && tile_attrs<16>() && tile_attrs<8>())) {
+    if (!(tile_attrs<32>() && tile_attrs<16>() && tile_attrs<8>() && mlqmc_stream::prepare())) {
         free_ctx(c);
         return MLQMC_ERR_CUDA;
     }
@@ -1443,6 +1640,15 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     c->pool_budget = std::min<size_t>(free_b / 2, static_cast<size_t>(96) << 30);
+    if (!mlqmc_tma::prepare()) {
+        free_ctx(c);
+        return MLQMC_ERR_CUDA;
+    }
+    st = tune_smoothers(c, max_samples_per_call > 0 ? max_samples_per_call : 1024);
+    if (st != MLQMC_OK) {
+        free_ctx(c);
+        return st;
+    }
     *out = c;
     return MLQMC_OK;
 }
@@ -1490,17 +1696,28 @@ extern "C" mlqmc_status mlqmc_sample_levels(mlqmc_ctx* c, const mlqmc_work* work
             }
     }
     std::stable_sort(all.begin(), all.end(), [](const SampleDesc& x, const SampleDesc& y) { return x.level > y.level; });
-    // chunks: consecutive ranks that fit max_samples and the pool budget
+    // chunks: consecutive ranks that fit max_samples, the pool budget and the
+    // 32-bit flat loops (samples x elements of every level below 2^31)
     std::vector<size_t> lvl_bytes(p.n_levels);
-    for (int t = 0; t < p.n_levels; ++t) lvl_bytes[t] = level_bytes_per_sample(p, c->Ka, t);
+    std::vector<uint64_t> lvl_elems(p.n_levels);
+    for (int t = 0; t < p.n_levels; ++t) {
+        lvl_bytes[t] = level_bytes_per_sample(p, c->Ka, t);
+        lvl_elems[t] = level_elems_per_sample(p, c->Ka, t);
+    }
     size_t a = 0;
     while (a < all.size()) {
         size_t b = a, bytes = 0;
+        uint64_t cnt[MLQMC_MAX_LEVELS] = {};
         while (b < all.size() && static_cast<int64_t>(b - a) < c->max_samples) {
             size_t add = 0;
-            for (int t = 0; t <= all[b].level; ++t) add += lvl_bytes[t];
-            if (b > a && bytes + add > c->pool_budget) break;
+            bool fits = true;
+            for (int t = 0; t <= all[b].level; ++t) {
+                add += lvl_bytes[t];
+                fits = fits && (cnt[t] + 1) * lvl_elems[t] < (uint64_t(1) << 31);
+            }
+            if (b > a && (bytes + add > c->pool_budget || !fits)) break;
             bytes += add;
+            for (int t = 0; t <= all[b].level; ++t) ++cnt[t];
             ++b;
         }
         const int count = static_cast<int>(b - a);
@@ -1592,7 +1809,8 @@ extern "C" mlqmc_status mlqmc_normals(mlqmc_ctx* c, int32_t level, int32_t r, in
 extern "C" mlqmc_status mlqmc_fields(mlqmc_ctx* c, int32_t t, const double* d_y, int32_t count, double* d_k,
                                      void* stream)
 {
-    if (!c || !d_y || !d_k || t < 0 || t >= c->p.n_levels || count < 0 || count > c->max_samples)
+    if (!c || !d_y || !d_k || t < 0 || t >= c->p.n_levels || count < 0 || count > c->max_samples ||
+        static_cast<uint64_t>(count) * level_elems_per_sample(c->p, c->Ka, t) >= (uint64_t(1) << 31))
         return MLQMC_ERR_INVALID_ARG;
     if (count == 0) return MLQMC_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1698,7 +1916,7 @@ __device__ void noalloc_faces(const Lv<double>& L)
     const int n = L.n;
     for (int idx = threadIdx.x; idx < n * (n + 1); idx += blockDim.x) {
         const int i2 = idx / (n + 1);
-        L.kx[idx] = face_x(L.k, n, i2, idx - i2 * (n + 1));
+        L.kx[i2 * kx_pitch(n) + idx - i2 * (n + 1)] = face_x(L.k, n, i2, idx - i2 * (n + 1));
         const int g = idx / n;
         L.ky[idx] = face_y(L.k, n, g, idx - g * n);
     }
@@ -1838,4 +2056,23 @@ extern "C" mlqmc_status mlqmc_last_iterations(mlqmc_ctx* c, int32_t* out)
 extern "C" int64_t mlqmc_launch_count(const mlqmc_ctx* c)
 {
     return c ? c->launches : 0;
+}
+
+extern "C" mlqmc_status mlqmc_smoother_info(const mlqmc_ctx* c, int32_t* kind, double* tuned_ms)
+{
+    if (!c) return MLQMC_ERR_INVALID_ARG;
+    for (int t = 0; t < c->p.n_levels; ++t) {
+        if (kind) kind[t] = t == 0 ? 0 : c->smoother[t];
+        for (int k = 0; k < 4 && tuned_ms; ++k) tuned_ms[t * 4 + k] = c->tune_ms[t][k];
+    }
+    return MLQMC_OK;
+}
+
+extern "C" mlqmc_status mlqmc_set_smoother(mlqmc_ctx* c, int32_t level, int32_t kind)
+{
+    if (!c || !is_mixed(c->p) || level < 1 || level >= c->p.n_levels || kind < MLQMC_SMOOTHER_TILE ||
+        kind > MLQMC_SMOOTHER_TMA || !smoother_fits(c, kind, level))
+        return MLQMC_ERR_INVALID_ARG;
+    c->smoother[level] = kind;
+    return MLQMC_OK;
 }

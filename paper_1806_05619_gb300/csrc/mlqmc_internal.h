@@ -137,6 +137,12 @@ struct mlqmc_ctx {
     double prof_f32[kProfKinds] = {};
     double prof_ftc[kProfKinds] = {};
 
+    // smoother of each level's V-cycle sweeps (MLQMC_SMOOTHER_*), picked by
+    // the autotuner at creation (mixed forms) or fixed by mlqmc_set_smoother;
+    // tune_ms: the tuner's time per candidate (ms, 0 when not timed)
+    int smoother[MLQMC_MAX_LEVELS] = {};
+    double tune_ms[MLQMC_MAX_LEVELS][4] = {};
+
     int* d_status = nullptr;  // deferred device status bits
     int host_status = 0;      // deferred status found on the host (converged-form loops)
     int last_iters[MLQMC_MAX_LEVELS] = {};  // extra cycles / refinement steps per level, last converged-form call

@@ -339,3 +339,79 @@ def test_mixed_qoi_within_bound():
             tol = math.expm1(eta) + 2 * cfg["rtol"] * ratio
             assert abs(Fg[t] / ref["F"][t] - 1.0) <= tol, (t, Fg[t], ref["F"][t], tol)
     ctx.check_device()
+
+
+# --------------------------------------------------------------------------- #
+# Smoothers of the FP32 V-cycles: same sweeps whichever kernel runs them      #
+# --------------------------------------------------------------------------- #
+
+
+def _force(ctx, name):
+    for t in range(1, ctx.n_levels):
+        try:
+            ctx.set_smoother(t, name)
+        except M.MlqmcError:
+            pass  # this smoother does not handle the level; the tuned one stays
+
+
+def _mixed_F(ctx, cfg, work, names):
+    out = {}
+    ns = sum((ne - nb) * (re_ - rb) for (_, nb, ne, rb, re_) in work)
+    for name in names:
+        _force(ctx, name)
+        sums = torch.zeros(cfg["n_levels"] * cfg["R"] * 2, dtype=torch.float64, device="cuda")
+        F = torch.zeros(ns * cfg["n_levels"], dtype=torch.float64, device="cuda")
+        ctx.sample_levels(work, sums, F)
+        torch.cuda.synchronize()
+        ctx.check_device()
+        out[name] = F.cpu().numpy().reshape(ns, cfg["n_levels"])
+    return out
+
+
+def test_smoothers_agree_fixed_cycles():
+    """Mixed form, fixed cycles (6 levels up to 256x256): the wavefront
+    (residual and correction fused), TMA-tile and plain-tile smoothers run the
+    same red-black sweeps; per-sample F agree to FP32 rounding of the
+    residual's summation order (1e-5 relative)."""
+    cfg = W.scaled(W.CONFIG2, R=2, precision="mixed_tf32")
+    z = _genvec(cfg)
+    ctx = M.Context.from_config(cfg, genvec=z)
+    work = [(5, 0, 3, 0, 2), (4, 1, 4, 0, 2), (3, 0, 5, 1, 2), (1, 2, 6, 0, 1)]
+    F = _mixed_F(ctx, cfg, work, ["stream", "tma", "tile"])
+    mask = F["tile"] != 0
+    for name in ["stream", "tma"]:
+        assert np.array_equal(F[name] != 0, mask)
+        assert _rel(F[name][mask], F["tile"][mask]) <= 1e-5, name
+
+
+def test_smoothers_agree_converged():
+    """Converged mixed form (rtol 1e-10, levels up to 128x128, samples leave
+    the refinement loop at different steps): per-sample F of the wavefront and
+    TMA-tile smoothers agree within 1e-8 relative."""
+    cfg = W.scaled(W.CONFIG3, n_levels=5, R=2)
+    z = _genvec(cfg)
+    ctx = M.Context.from_config(cfg, genvec=z)
+    work = [(4, 0, 6, 0, 2), (3, 0, 3, 0, 1)]
+    F = _mixed_F(ctx, cfg, work, ["stream", "tma"])
+    mask = F["stream"] != 0
+    assert _rel(F["tma"][mask], F["stream"][mask]) <= 1e-8
+
+
+def test_autotuner_report():
+    cfg = W.scaled(W.CONFIG2, R=2, precision="mixed_tf32")
+    ctx = M.Context.from_config(cfg, genvec=_genvec(cfg), max_samples=2048)
+    info = ctx.smoother_info()
+    assert info[0][0] == "gs"
+    for t, (name, ms) in enumerate(info[1:], start=1):
+        n = cfg["n0"] << t
+        assert name in ("stream", "tma", "tile")
+        if len(ms) >= 2:
+            assert name == min(ms, key=ms.get), (t, name, ms)
+        if n > 256:
+            assert name == "tma"
+    with pytest.raises(M.MlqmcError):
+        ctx.set_smoother(1, "tma")  # 16 x 16: no whole TMA tile with its halo inside the grid
+    c64 = M.Context.from_config(W.scaled(W.CONFIG2, R=2), genvec=_genvec(cfg))
+    assert all(k == "gs" for k, _ in c64.smoother_info())
+    with pytest.raises(M.MlqmcError):
+        c64.set_smoother(3, "stream")  # FP64 form: kb_gs only
