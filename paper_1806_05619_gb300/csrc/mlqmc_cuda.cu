@@ -506,35 +506,77 @@ __global__ void kb_resid_restrict(FmgArgs A, int t, int B, int ones)
     }
 }
 
-// u of level t (+)= P u of level t-1 (FP64 solution arrays when U64).
+// The 2 x 2 fine cells of coarse parent (I1, I2) receive P e (the arithmetic
+// of prolong_cell): the parent's 3 x 3 coarse neighbourhood, a neighbour
+// outside the coarse grid replaced by minus the parent's row or column (odd
+// reflection; the corner by the product of the two signs). dst(fx, fy) of
+// the block at rows 2 I2 + fy, columns 2 I1 + fx.
+template <typename S, typename D, typename Store>
+__device__ __forceinline__ void prolong_block(const S* e, int nc, int I1, int I2, Store store)
+{
+    const bool lo1 = I1 == 0, hi1 = I1 == nc - 1, lo2 = I2 == 0, hi2 = I2 == nc - 1;
+    D E[3][3];
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            const bool ry = (dy < 0 && lo2) || (dy > 0 && hi2);
+            const bool rx = (dx < 0 && lo1) || (dx > 0 && hi1);
+            const D v = D(e[(I2 + (ry ? 0 : dy)) * nc + I1 + (rx ? 0 : dx)]);
+            E[dy + 1][dx + 1] = (ry != rx) ? -v : v;
+        }
+    }
+    D out[2][2];
+#pragma unroll
+    for (int fy = 0; fy < 2; ++fy)
+#pragma unroll
+        for (int fx = 0; fx < 2; ++fx)
+            out[fy][fx] = fma(D(0.5625), E[1][1], fma(D(0.1875), E[1][2 * fx] + E[2 * fy][1], D(0.0625) * E[2 * fy][2 * fx]));
+    store(out);
+}
+
+// u of level t (+)= P u of level t-1 (FP64 solution arrays when U64), one
+// coarse parent (2 x 2 fine cells) per thread.
 template <typename T, bool ADD, bool U64>
 __global__ void kb_prolong(FmgArgs A, int t, int B)
 {
     const int n = A.lv[t].n;
     const int nc = n >> 1;
-    const uint32_t per = static_cast<uint32_t>(n) * static_cast<uint32_t>(n);
+    const uint32_t per = static_cast<uint32_t>(nc) * static_cast<uint32_t>(nc);
     GRID_STRIDE(idx, B * per)
     {
         const int i = static_cast<int>(idx / per);
         if (inactive(A, i)) continue;
-        const int p = static_cast<int>(idx - i * per);
-        const int i2 = p / n;
-        const int i1 = p - i2 * n;
+        const int q = static_cast<int>(idx - i * per);
+        const int I2 = q / nc;
+        const int I1 = q - I2 * nc;
+        const size_t o = static_cast<size_t>(2 * I2) * n + 2 * I1;
         if constexpr (U64) {
             // FMG interpolation of the refinement path into u64: mixed forms
             // interpolate the FP32 copy of the coarse solution in FP32 (the
             // first FP64 residual then sees it exactly), FP64 form in FP64
-            double v;
-            if constexpr (sizeof(T) == 4) v = static_cast<double>(prolong_cell<float, float>(at<float>(A.lv[t - 1].u, i), nc, i1, i2));
-            else v = prolong_cell<double, double>(at<double>(A.lv[t - 1].u64, i), nc, i1, i2);
-            double* u = at<double>(A.lv[t].u64, i);
-            if (ADD) u[p] += v;
-            else u[p] = v;
+            double* u = at<double>(A.lv[t].u64, i) + o;
+            auto store = [&](const auto& v) {
+#pragma unroll
+                for (int fy = 0; fy < 2; ++fy) {
+                    double2* d = reinterpret_cast<double2*>(u + fy * n);
+                    const double2 w = make_double2(static_cast<double>(v[fy][0]), static_cast<double>(v[fy][1]));
+                    if (ADD) *d = make_double2(d->x + w.x, d->y + w.y);
+                    else *d = w;
+                }
+            };
+            if constexpr (sizeof(T) == 4) prolong_block<float, float>(at<float>(A.lv[t - 1].u, i), nc, I1, I2, store);
+            else prolong_block<double, double>(at<double>(A.lv[t - 1].u64, i), nc, I1, I2, store);
         } else {
-            const T v = prolong_cell<T, T>(at<T>(A.lv[t - 1].u, i), nc, i1, i2);
-            T* u = at<T>(A.lv[t].u, i);
-            if (ADD) u[p] += v;
-            else u[p] = v;
+            T* u = at<T>(A.lv[t].u, i) + o;
+            prolong_block<T, T>(at<T>(A.lv[t - 1].u, i), nc, I1, I2, [&](const T (&v)[2][2]) {
+#pragma unroll
+                for (int fy = 0; fy < 2; ++fy) {
+                    T* d = u + fy * n;
+                    d[0] = ADD ? d[0] + v[fy][0] : v[fy][0];
+                    d[1] = ADD ? d[1] + v[fy][1] : v[fy][1];
+                }
+            });
         }
     }
 }
@@ -1088,7 +1130,7 @@ void smooth(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int first, int 
     const Work pro_work = work_of<T>(B * es * (0.25 * Mc + 2.0 * Mc), B * 8.0 * Mc);
     if (pro && tile == 0) {
         Timed tm(c, kProfTransfer, st, pro_work);
-        kb_prolong<T, true, false><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
+        kb_prolong<T, true, false><<<grid_for(c, B * n * n / 4), 256, 0, st>>>(A, t, B);
         pro = false;
     }
     while (nsweeps > 0) {
@@ -1116,7 +1158,7 @@ void smooth(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int first, int 
     }
     if (pro) {  // no sweeps at all: the correction alone
         Timed tm(c, kProfTransfer, st, pro_work);
-        kb_prolong<T, true, false><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
+        kb_prolong<T, true, false><<<grid_for(c, B * n * n / 4), 256, 0, st>>>(A, t, B);
     }
 }
 
@@ -1271,7 +1313,7 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
         if (refine) {
             {
                 Timed tm(c, kProfTransfer, st, work_of<T>(B * (es * 0.25 + 8.0) * Mc, B * 8.0 * Mc));
-                kb_prolong<T, false, true><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
+                kb_prolong<T, false, true><<<grid_for(c, B * n * n / 4), 256, 0, st>>>(A, t, B);
             }
             {
                 Timed tm(c, kProfTransfer, st, work_of<double>(B * (8.0 * Mc + es * (2.0 * Fc + Mc)), B * 10.0 * Mc));
@@ -1293,7 +1335,7 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
         } else {
             {
                 Timed tm(c, kProfTransfer, st, work_of<T>(B * es * 1.25 * Mc, B * 8.0 * Mc));
-                kb_prolong<T, false, false><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
+                kb_prolong<T, false, false><<<grid_for(c, B * n * n / 4), 256, 0, st>>>(A, t, B);
             }
             for (int m = 0; m < c->p.mu0; ++m) {
                 mlqmc_status s = vcycle_batched<T>(c, A, t, B, true, st);

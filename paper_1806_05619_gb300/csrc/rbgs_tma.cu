@@ -36,7 +36,7 @@ struct Maps {
 
 constexpr int round32(int v) { return (v + 31) / 32 * 32; }  // 128-byte aligned sub-buffers
 
-template <int TILE>
+template <int TILE, bool POST>
 struct TGeom {
     static constexpr int SU = TILE + 2 * kH;       // staged cells per side
     static constexpr int XW = SU + 4;              // staged x faces per row (box width, 16-byte multiple)
@@ -46,16 +46,17 @@ struct TGeom {
     static constexpr int oKX = oB + round32(SU * SU);
     static constexpr int oKY = oKX + round32(SU * XW);
     static constexpr int oE = oKY + round32((SU + 1) * SU);
-    static constexpr int buf = oE + round32(EC * EC);  // floats per buffer
+    static constexpr int buf = oE + (POST ? round32(EC * EC) : 0);  // floats per buffer
     static constexpr size_t bytes = 128 + 2 * sizeof(float) * static_cast<size_t>(buf);
+    static constexpr int ctas_per_sm = POST ? 3 : 4;  // as many as fit the 227 KB of shared memory
     static_assert((SU * 4) % 16 == 0 && (XW * 4) % 16 == 0 && (EC * 4) % 16 == 0, "TMA boxes: 16-byte rows");
 };
 
 template <int TILE, int NS, bool POST>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, TGeom<TILE, POST>::ctas_per_sm)
     kb_rbgs_tma(const __grid_constant__ Maps maps, FmgArgs A, int t, int B, int ones, int first)
 {
-    using Gm = TGeom<TILE>;
+    using Gm = TGeom<TILE, POST>;
     constexpr int SU = Gm::SU, XW = Gm::XW, EC = Gm::EC;
     constexpr int HN = 2 * NS;  // halo the NS sweeps consume
     static_assert(HN <= kH, "halo");
@@ -91,6 +92,35 @@ __global__ void __launch_bounds__(kThreads, 3)
         if (POST) tensor_load_3d(S + Gm::oE, &maps.e, bar, x0 / 2 - kH, y0 / 2 - kH, i);
     };
 
+    // Work of half sweep ph (growth g = HN - 1 - ph) on the staged tile:
+    // - the tile's own 32 rows x 16 cells of the colour, two per thread: warp
+    //   w takes row pairs w and w + 8, lanes 0-15 the upper row and 16-31 the
+    //   lower one, so every shared access of a warp hits 32 distinct banks;
+    // - the ring of the grown region around the tile (64 g + 2 g^2 cells, at
+    //   most one per thread): the 2g full rows above and below ((16 + g) cells
+    //   each, by cell index m) and g cells at the ends of each tile row (by
+    //   index k: the left strip's cells first). Packed per thread: bit 15 =
+    //   end-of-row cell, bits 8-14 staged row, bits 0-7 m or k; -1: none.
+    static_assert(TILE == 32 && kThreads == 256, "two tile cells per thread and half sweep");
+    int ring[HN];
+#pragma unroll
+    for (int ph = 0; ph < HN; ++ph) {
+        const int g = HN - 1 - ph;
+        const int r = threadIdx.x;
+        const int full = 2 * g * (TILE / 2 + g);
+        int pk = -1;
+        if (r < full) {
+            const int rr = r / (TILE / 2 + g), m = r - rr * (TILE / 2 + g);
+            const int sy = rr < g ? kH - g + rr : kH + TILE + rr - g;
+            pk = (sy << 8) | m;
+        } else if (r < full + TILE * g) {
+            const int rr = (r - full) / g, k = r - full - rr * g;
+            pk = 0x8000 | ((kH + rr) << 8) | k;
+        }
+        ring[ph] = g > 0 ? pk : -1;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
     bool live = true;
     int issued = 0;  // tiles issued by this CTA (thread 0's count)
     if (threadIdx.x == 0 && static_cast<int>(blockIdx.x) < total) {
@@ -117,64 +147,89 @@ __global__ void __launch_bounds__(kThreads, 3)
             const float* skx = S + Gm::oKX;
             const float* sky = S + Gm::oKY;
             if constexpr (POST) {
-                // coarse-grid correction on every staged cell of the domain (as prolong_cell)
+                // coarse-grid correction on every staged cell of the domain, one
+                // 2 x 2 block of fine cells (one coarse parent) per thread: the
+                // parent's 3 x 3 coarse neighbourhood, a neighbour outside the
+                // coarse grid replaced by minus the parent's row or column
+                // (odd reflection; the corner then by the product of the two
+                // signs), gives each fine cell the arithmetic of prolong_cell
                 const float* se = S + Gm::oE;
                 const int nc = n >> 1;
-                const int ex0 = x0 / 2 - kH, ey0 = y0 / 2 - kH;
-                for (int q = threadIdx.x; q < SU * SU; q += kThreads) {
-                    const int gy = y0 - kH + q / SU, gx = x0 - kH + q % SU;
-                    if (gy < 0 || gy >= n || gx < 0 || gx >= n) continue;
-                    const int I1 = gx >> 1, I2 = gy >> 1;
-                    const int J1 = (gx & 1) ? I1 + 1 : I1 - 1;
-                    const int J2 = (gy & 1) ? I2 + 1 : I2 - 1;
-                    const bool o1 = J1 < 0 || J1 >= nc, o2 = J2 < 0 || J2 >= nc;
-                    const int K1 = o1 ? I1 : J1, K2 = o2 ? I2 : J2;
-                    const float a = se[(I2 - ey0) * EC + I1 - ex0];
-                    const float b0 = se[(I2 - ey0) * EC + K1 - ex0];
-                    const float c0 = se[(K2 - ey0) * EC + I1 - ex0];
-                    const float d0 = se[(K2 - ey0) * EC + K1 - ex0];
-                    const float bb = o1 ? -b0 : b0;
-                    const float cc = o2 ? -c0 : c0;
-                    const float dd = (o1 != o2) ? -d0 : d0;
-                    su[q] += fmaf(0.5625f, a, fmaf(0.1875f, bb + cc, 0.0625f * dd));
+                constexpr int SB = SU / 2;  // staged blocks per side (x0 - kH, y0 - kH even)
+                for (int q = threadIdx.x; q < SB * SB; q += kThreads) {
+                    const int by = q / SB, bx = q - (q / SB) * SB;
+                    const int I2 = (y0 - kH) / 2 + by, I1 = (x0 - kH) / 2 + bx;
+                    if (I2 < 0 || I2 >= nc || I1 < 0 || I1 >= nc) continue;
+                    const int ey = I2 - (y0 / 2 - kH), ex = I1 - (x0 / 2 - kH);  // in the staged coarse box
+                    const bool lo1 = I1 == 0, hi1 = I1 == nc - 1, lo2 = I2 == 0, hi2 = I2 == nc - 1;
+                    float E[3][3];
+#pragma unroll
+                    for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            const bool ry = (dy < 0 && lo2) || (dy > 0 && hi2);
+                            const bool rx = (dx < 0 && lo1) || (dx > 0 && hi1);
+                            const float v = se[(ey + (ry ? 0 : dy)) * EC + ex + (rx ? 0 : dx)];
+                            E[dy + 1][dx + 1] = (ry != rx) ? -v : v;
+                        }
+                    }
+                    float* f = su + (2 * by) * SU + 2 * bx;
+#pragma unroll
+                    for (int fy = 0; fy < 2; ++fy) {
+#pragma unroll
+                        for (int fx = 0; fx < 2; ++fx) {
+                            const int dy = 2 * fy, dx = 2 * fx;  // -1 -> 0, +1 -> 2 in E
+                            f[fy * SU + fx] +=
+                                fmaf(0.5625f, E[1][1], fmaf(0.1875f, E[1][dx] + E[dy][1], 0.0625f * E[dy][dx]));
+                        }
+                    }
                 }
                 __syncthreads();
             }
             // tiles whose grown regions stay inside the domain skip the per-cell test
             const bool interior = x0 >= HN && y0 >= HN && x0 + TILE + HN <= n && y0 + TILE + HN <= n;
+            // one red-black update of staged cell (sy, sx)
+            auto update = [&](int sy, int sx) {
+                const int c0 = sy * SU + sx;
+                const float* kr = skx + sy * XW;
+                const float w = kr[sx], e = kr[sx + 1];
+                const float nn = sky[c0], so = sky[c0 + SU];
+                float acc = h2 * (ones ? 1.0f : sb[c0]);
+                acc += w * su[c0 - 1];
+                acc += e * su[c0 + 1];
+                acc += nn * su[c0 - SU];
+                acc += so * su[c0 + SU];
+                su[c0] = __fdividef(acc, w + e + nn + so);  // hardware reciprocal: within 2 ulp
+            };
 #pragma unroll
             for (int ph = 0; ph < HN; ++ph) {
                 const int colour = (first + ph) & 1;
                 const int g = HN - 1 - ph;  // growth of the updated region beyond the tile
-                const int side = TILE + 2 * g;
-                const int half = side / 2;
-                for (int q = threadIdx.x; q < side * half; q += kThreads) {
-                    const int ry = q / half;
-                    const int gy = y0 - g + ry;
-                    const int rx = 2 * (q - ry * half) + ((gy + x0 - g + colour) & 1);
-                    const int gx = x0 - g + rx;
-                    if (!interior && (gy < 0 || gy >= n || gx < 0 || gx >= n)) continue;
-                    const int sy = gy - y0 + kH, sx = gx - x0 + kH;
-                    const int c0 = sy * SU + sx;
-                    const float* kr = skx + sy * XW;
-                    const float w = kr[sx], e = kr[sx + 1];
-                    const float nn = sky[sy * SU + sx], so = sky[(sy + 1) * SU + sx];
-                    float acc = h2 * (ones ? 1.0f : sb[c0]);
-                    acc += w * su[c0 - 1];
-                    acc += e * su[c0 + 1];
-                    acc += nn * su[c0 - SU];
-                    acc += so * su[c0 + SU];
-                    su[c0] = __fdividef(acc, w + e + nn + so);  // hardware reciprocal: within 2 ulp
+                // colour cells: (gx + gy) & 1 == colour, with x0 - kH and y0 - kH even
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int sy = kH + 2 * (warp + 8 * j) + (lane >> 4);
+                    update(sy, kH + 2 * (lane & 15) + ((colour + sy) & 1));
+                }
+                const int pk = ring[ph];
+                if (pk >= 0) {
+                    const int sy = (pk >> 8) & 127;
+                    const int p = (colour + g + sy) & 1;
+                    int m = pk & 255;
+                    if (pk & 0x8000) m = m < ((g - p + 1) >> 1) ? m : m + TILE / 2;  // left strip, then right
+                    const int sx = kH - g + 2 * m + p;
+                    const int gy = y0 - kH + sy, gx = x0 - kH + sx;
+                    if (interior || (gy >= 0 && gy < n && gx >= 0 && gx < n)) update(sy, sx);
                 }
                 __syncthreads();
             }
             float* uo = at<float>(A.lv[t].u2, i);
             constexpr int TV = TILE / 4;
+            static_assert((SU * 4) % 16 == 0 && (kH * 4) % 16 == 0, "16-byte aligned staged rows");
             for (int q = threadIdx.x; q < TILE * TV; q += kThreads) {
                 const int ry = q / TV, v = q - (q / TV) * TV;
-                const float* src = su + (ry + kH) * SU + kH + 4 * v;
                 *reinterpret_cast<float4*>(uo + static_cast<size_t>(y0 + ry) * n + x0 + 4 * v) =
-                    make_float4(src[0], src[1], src[2], src[3]);
+                    *reinterpret_cast<const float4*>(su + (ry + kH) * SU + kH + 4 * v);
             }
         }
         // this buffer is refilled by the TMA next iteration: order the generic accesses first
@@ -223,7 +278,7 @@ template <int TILE, int NS, bool POST>
 bool attr()
 {
     return cudaFuncSetAttribute(kb_rbgs_tma<TILE, NS, POST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(TGeom<TILE>::bytes)) == cudaSuccess;
+                                static_cast<int>(TGeom<TILE, POST>::bytes)) == cudaSuccess;
 }
 
 template <int TILE>
@@ -232,10 +287,18 @@ bool attrs()
     return attr<TILE, 1, false>() && attr<TILE, 1, true>() && attr<TILE, 2, false>() && attr<TILE, 2, true>();
 }
 
-template <int TILE>
-bool go(const FmgArgs& A, int t, int n, int B, int ns, int ones, int first, bool post, int max_ctas, cudaStream_t st)
+template <int TILE, int NS, bool POST>
+void run(const Maps& m, const FmgArgs& A, int t, int B, int tiles, int ones, int first, int sm_count, cudaStream_t st)
 {
-    using Gm = TGeom<TILE>;
+    using Gm = TGeom<TILE, POST>;
+    const int cap = Gm::ctas_per_sm * sm_count;
+    kb_rbgs_tma<TILE, NS, POST><<<tiles < cap ? tiles : cap, kThreads, Gm::bytes, st>>>(m, A, t, B, ones, first);
+}
+
+template <int TILE>
+bool go(const FmgArgs& A, int t, int n, int B, int ns, int ones, int first, bool post, int sm_count, cudaStream_t st)
+{
+    using Gm = TGeom<TILE, true>;
     const LevelDesc& L = A.lv[t];
     Maps m;
     std::memset(&m, 0, sizeof(m));
@@ -247,13 +310,12 @@ bool go(const FmgArgs& A, int t, int n, int B, int ns, int ones, int first, bool
               (!post || encode_3d(&m.e, A.lv[t - 1].u, un / 2, un / 2, un / 2, ub, Gm::EC, Gm::EC));
     if (!ok) return false;
     const int tiles = B * (n / TILE) * (n / TILE);
-    const int grid = tiles < max_ctas ? tiles : max_ctas;
     if (ns == 2) {
-        if (post) kb_rbgs_tma<TILE, 2, true><<<grid, kThreads, Gm::bytes, st>>>(m, A, t, B, ones, first);
-        else kb_rbgs_tma<TILE, 2, false><<<grid, kThreads, Gm::bytes, st>>>(m, A, t, B, ones, first);
+        if (post) run<TILE, 2, true>(m, A, t, B, tiles, ones, first, sm_count, st);
+        else run<TILE, 2, false>(m, A, t, B, tiles, ones, first, sm_count, st);
     } else {
-        if (post) kb_rbgs_tma<TILE, 1, true><<<grid, kThreads, Gm::bytes, st>>>(m, A, t, B, ones, first);
-        else kb_rbgs_tma<TILE, 1, false><<<grid, kThreads, Gm::bytes, st>>>(m, A, t, B, ones, first);
+        if (post) run<TILE, 1, true>(m, A, t, B, tiles, ones, first, sm_count, st);
+        else run<TILE, 1, false>(m, A, t, B, tiles, ones, first, sm_count, st);
     }
     return cudaGetLastError() == cudaSuccess;
 }
@@ -277,7 +339,7 @@ bool launch(const FmgArgs& A, int t, int n, int B, int ns, int ones, int first, 
 {
     if (B <= 0) return true;
     if (!supported(n) || t < 1 || A.lv[t].n != n || (ns != 1 && ns != 2)) return false;
-    return go<32>(A, t, n, B, ns, ones, first, post, 3 * sm_count, st);
+    return go<32>(A, t, n, B, ns, ones, first, post, sm_count, st);
 }
 
 }  // namespace mlqmc_tma
