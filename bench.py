@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-tte", action="store_true", help="skip the time-to-epsilon runs of Algorithm 1")
     ap.add_argument("--smoother", default="auto", choices=["auto", "stream", "tma", "tile"],
                     help="mixed form: force this smoother on every level it handles (default: the autotuner's pick)")
+    ap.add_argument("--no-graphs", action="store_true", help="launch kernel by kernel instead of replaying a CUDA graph")
     ap.add_argument("--counts-div", type=int, default=1,
                     help="divide the per-level counts (small cases for profiler captures only)")
     return ap.parse_args()
@@ -259,6 +260,40 @@ def run_reference(args):
 # --------------------------------------------------------------------------- #
 # GPU arm                                                                    #
 # --------------------------------------------------------------------------- #
+def timed_steps(step, K, stream, flush):
+    """K steps, each bracketed by CUDA events on the launch stream, L2 flushed
+    (512 MiB write) before each outside the events; per-step milliseconds."""
+    import torch
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for i in range(K):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def profiled_pass(ctx, step, args, stream, flush):
+    """K more steps with the library's per-kernel event brackets on (two
+    untimed calls first: the graph is captured again with its brackets):
+    per-kind (ms, launches), algorithmic work, and the mean step time of
+    the pass. Profiling is off again afterwards (two more untimed calls
+    restore the plain graph)."""
+    ctx.profile(True)
+    for _ in range(2):
+        step()
+    ctx.profile(True)  # clear the totals of those two calls
+    ms = timed_steps(step, args.steps, stream, flush)
+    prof = ctx.profile_read()
+    work = ctx.profile_work()
+    ctx.profile(False)
+    for _ in range(2):
+        step()
+    return prof, work, sum(ms) / len(ms)
+
+
 def force_smoother(ctx, name):
     if name == "auto" or ctx.precision == "fp64":
         return
@@ -295,6 +330,7 @@ def run_ours(args):
     genvec, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
     ctx = M.Context.from_config(cfg, genvec=genvec, max_samples=ns)
     force_smoother(ctx, args.smoother)
+    ctx.set_graphs(not args.no_graphs)
     nl, R = cfg["n_levels"], cfg["R"]
     sums = torch.zeros(nl * R * 2, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -309,6 +345,7 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    # warm-up: the repeated step is captured as one CUDA graph on its second call
     for _ in range(args.warmup):
         step()
     ctx.check_device(stream)
@@ -318,21 +355,13 @@ def run_ours(args):
     clk_path = os.path.join(tempfile.gettempdir(), f"clocks_{os.getpid()}.csv")
     clk = clocks_start(clk_path)
     launches0 = ctx.launch_count()
-    ctx.profile(True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    replays0 = ctx.graph_replays()
     barrier()
-    for i in range(args.steps):
-        flush.zero_()
-        ev[i][0].record(stream)
-        step()
-        ev[i][1].record(stream)
+    step_ms = timed_steps(step, args.steps, stream, flush)
     barrier()
     launches = ctx.launch_count() - launches0
-    prof = ctx.profile_read()
-    pwork = ctx.profile_work()
-    ctx.profile(False)
+    replays = ctx.graph_replays() - replays0
     clocks = clocks_stop(clk, clk_path, device_index=local)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
     tot_ms = sum(step_ms)
     t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
     if world > 1:
@@ -340,6 +369,10 @@ def run_ours(args):
     tot_ms = float(t.item())
     ctx.check_device(stream)
     value = ns * world * args.steps / (tot_ms * 1e-3)
+
+    # the same K steps again with every kernel bracketed by events (the
+    # library's per-kind timing and algorithmic work): roofline per kind
+    prof, pwork, prof_ms = profiled_pass(ctx, step, args, stream, flush)
 
     # end to end through the public API from the host: work list in, estimate out
     e2e_times = []
@@ -402,6 +435,8 @@ def run_ours(args):
                        "l2": "flushed between timed steps (512 MiB write)",
                        "parallelism": f"independent replicas x{world}"},
             "gpu_launches": launches,
+            "graph_replays": replays,
+            "profiled_pass_ms_per_step": prof_ms,
             "roofline": roof,
             "roofline_by_kind": by_kind,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -430,6 +465,7 @@ def run_mixed_same_workload(args, cfg64, work, genvec, dev, stream, flush, M):
     ns = n_samples(work)
     ctx = M.Context.from_config(cfg, genvec=genvec, max_samples=ns)
     force_smoother(ctx, args.smoother)
+    ctx.set_graphs(not args.no_graphs)
     nl, R = cfg["n_levels"], cfg["R"]
     sums = torch.zeros(nl * R * 2, dtype=torch.float64, device=dev)
 
@@ -441,23 +477,15 @@ def run_mixed_same_workload(args, cfg64, work, genvec, dev, stream, flush, M):
         step()
     ctx.check_device(stream)
     torch.cuda.synchronize(dev)
-    ctx.profile(True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.zero_()
-        ev[i][0].record(stream)
-        step()
-        ev[i][1].record(stream)
-    torch.cuda.synchronize(dev)
-    prof = ctx.profile_read()
-    pwork = ctx.profile_work()
-    ctx.profile(False)
+    ms = timed_steps(step, args.steps, stream, flush)
+    tot = sum(ms)
+    prof, pwork, prof_ms = profiled_pass(ctx, step, args, stream, flush)
     ctx.check_device(stream)
-    tot = sum(a.elapsed_time(b) for a, b in ev)
     roof, by_kind = roofline_report(prof, pwork, args.steps)
     return {"value": ns * args.steps / (tot * 1e-3), "unit": UNIT, "ms_per_step": tot / args.steps,
             "dtype": "f32 V-cycles in f64 refinement, TF32 tensor-core KL, f32 field",
-            "roofline": roof, "roofline_by_kind": by_kind,
+            "roofline": roof, "roofline_by_kind": by_kind, "profiled_pass_ms_per_step": prof_ms,
+            "graph_replays": ctx.graph_replays(),
             "smoothers": [{"level": t, "kind": k, "tuned_ms": ms} for t, (k, ms) in enumerate(ctx.smoother_info())]}
 
 

@@ -305,6 +305,23 @@ mlqmc_status mlqmc_smoother_info(const mlqmc_ctx* c, int32_t* kind, double* tune
 mlqmc_status mlqmc_set_smoother(mlqmc_ctx* c, int32_t level, int32_t kind);
 
 /*
+ * Graph replay (on by default). In the fixed-cycle forms (refine_rtol = 0) a
+ * call of mlqmc_sample_levels that fits one chunk and repeats the previous
+ * call exactly (same ranked samples, same d_sums and d_F, no pool
+ * reallocated or smoother changed since) is captured as one CUDA graph:
+ * the upload of the sample descriptors and every launch of the call. Later
+ * identical calls replay that graph on a stream of the library's own,
+ * ordered after the caller's earlier work on `stream` and before its later
+ * work by events. Results equal those of the launch-by-launch path (same
+ * kernels, same order). With profiling on, the graph records its brackets
+ * and each replay adds them to the totals (the call then waits for the
+ * replay). mlqmc_set_graphs(c, 0) drops the graph and turns replay off;
+ * mlqmc_graph_replays counts replays since creation.
+ */
+mlqmc_status mlqmc_set_graphs(mlqmc_ctx* c, int32_t enable);
+int64_t mlqmc_graph_replays(const mlqmc_ctx* c);
+
+/*
  * Per-kernel device timing of mlqmc_sample_levels (off by default). With
  * enable = 1 every later launch is bracketed by CUDA events recorded on the
  * launch stream; enable = 0 stops recording. Either call clears the totals.

@@ -101,11 +101,14 @@ def lib():
             L.mlqmc_profile_work.argtypes = [vp, dp, dp, dp, dp]
             L.mlqmc_smoother_info.argtypes = [vp, C.POINTER(C.c_int32), dp]
             L.mlqmc_set_smoother.argtypes = [vp, i32, i32]
+            L.mlqmc_set_graphs.argtypes = [vp, i32]
+            L.mlqmc_graph_replays.argtypes = [vp]
+            L.mlqmc_graph_replays.restype = i64
             L.mlqmc_launch_count.argtypes = [vp]
             L.mlqmc_launch_count.restype = i64
             for name in ["mlqmc_create", "mlqmc_sample_levels", "mlqmc_estimate", "mlqmc_get_device_status",
                          "mlqmc_cbc_genvec", "mlqmc_modes", "mlqmc_point_bits", "mlqmc_normals", "mlqmc_fields",
-                         "mlqmc_sample_solution", "mlqmc_profile", "mlqmc_profile_read", "mlqmc_profile_work", "mlqmc_smoother_info", "mlqmc_set_smoother",
+                         "mlqmc_sample_solution", "mlqmc_profile", "mlqmc_profile_read", "mlqmc_profile_work", "mlqmc_smoother_info", "mlqmc_set_smoother", "mlqmc_set_graphs",
                          "mlqmc_fmg_fields_noalloc", "mlqmc_last_iterations"]:
                 getattr(L, name).restype = C.c_int
             _lib = L
@@ -302,6 +305,13 @@ class Context:
     def set_smoother(self, level: int, name: str):
         """Force smoother `name` ("tile", "stream" or "tma") on `level` for later calls."""
         _check(lib().mlqmc_set_smoother(self.h, int(level), self.SMOOTHERS.index(name)), "mlqmc_set_smoother")
+
+    def set_graphs(self, enable: bool):
+        """Graph replay of repeated identical fixed-cycle calls (on by default)."""
+        _check(lib().mlqmc_set_graphs(self.h, 1 if enable else 0), "mlqmc_set_graphs")
+
+    def graph_replays(self) -> int:
+        return int(lib().mlqmc_graph_replays(self.h))
 
     def launch_count(self) -> int:
         return int(lib().mlqmc_launch_count(self.h))

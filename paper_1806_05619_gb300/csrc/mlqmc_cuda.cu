@@ -787,6 +787,7 @@ mlqmc_status ensure_pool(mlqmc_ctx* c, int t, int64_t need)
         P.mem = nullptr;
         P.cap = 0;
     }
+    ++c->pool_epoch;
     if (!ok(cudaMalloc(&P.mem, std::max<size_t>(off, 256)))) {
         cudaGetLastError();
         P.mem = nullptr;
@@ -884,7 +885,7 @@ struct Timed {
     {
         if (c->profiling) {
             a = take_event(c);
-            cudaEventRecord(a, st);
+            record(a);
             c->prof_bytes[kind] += w.bytes;
             c->prof_f64[kind] += w.f64;
             c->prof_f32[kind] += w.f32;
@@ -896,8 +897,15 @@ struct Timed {
         c->launches += nk;
         if (!a) return;
         cudaEvent_t b = take_event(c);
-        cudaEventRecord(b, st);
+        record(b);
         c->marks.push_back({kind, nk, a, b});
+    }
+    // inside a stream capture the record must become an event-record node of
+    // the graph (external), so that the host can time every replay
+    void record(cudaEvent_t e) const
+    {
+        if (c->graph.capturing) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+        else cudaEventRecord(e, st);
     }
 };
 
@@ -1695,11 +1703,139 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
     return MLQMC_OK;
 }
 
+void graph_free(mlqmc_ctx* c);
+
 extern "C" void mlqmc_destroy(mlqmc_ctx* c)
 {
     if (!c) return;
     cudaDeviceSynchronize();
+    graph_free(c);
     free_ctx(c);
+}
+
+// ---------------------------------------------------------------------------
+// Graph replay of repeated identical calls (fixed-cycle forms, one chunk).
+// ---------------------------------------------------------------------------
+void graph_reset(mlqmc_ctx* c)
+{
+    mlqmc_ctx::GraphCache& G = c->graph;
+    if (G.exec) {
+        cudaStreamSynchronize(G.stream);
+        cudaGraphExecDestroy(G.exec);
+        G.exec = nullptr;
+    }
+    for (auto& m : G.marks) {
+        c->pool.push_back(m.a);
+        c->pool.push_back(m.b);
+    }
+    G.marks.clear();
+    G.seen = 0;
+    G.key.clear();
+}
+
+void graph_free(mlqmc_ctx* c)
+{
+    graph_reset(c);
+    mlqmc_ctx::GraphCache& G = c->graph;
+    if (G.stream) cudaStreamDestroy(G.stream);
+    if (G.in) cudaEventDestroy(G.in);
+    if (G.out) cudaEventDestroy(G.out);
+    if (G.h_samples) cudaFreeHost(G.h_samples);
+    G.stream = nullptr;
+    G.in = G.out = nullptr;
+    G.h_samples = nullptr;
+}
+
+mlqmc_status graph_replay(mlqmc_ctx* c, cudaStream_t st)
+{
+    mlqmc_ctx::GraphCache& G = c->graph;
+    if (!ok(cudaEventRecord(G.in, st)) || !ok(cudaStreamWaitEvent(G.stream, G.in, 0)) ||
+        !ok(cudaGraphLaunch(G.exec, G.stream)) || !ok(cudaEventRecord(G.out, G.stream)) ||
+        !ok(cudaStreamWaitEvent(st, G.out, 0)))
+        return MLQMC_ERR_CUDA;
+    c->launches += G.launches;
+    ++G.replays;
+    if (c->profiling && G.profiled && !G.marks.empty()) {
+        // the graph re-records its events on every replay: read them now
+        if (!ok(cudaEventSynchronize(G.marks.back().b))) return MLQMC_ERR_CUDA;
+        for (const auto& m : G.marks) {
+            float ms = 0.0f;
+            if (!ok(cudaEventElapsedTime(&ms, m.a, m.b))) return MLQMC_ERR_CUDA;
+            c->prof_ms[m.kind] += ms;
+            c->prof_n[m.kind] += m.nk;
+        }
+        for (int k = 0; k < kProfKinds; ++k) {
+            c->prof_bytes[k] += G.work[0][k];
+            c->prof_f64[k] += G.work[1][k];
+            c->prof_f32[k] += G.work[2][k];
+            c->prof_ftc[k] += G.work[3][k];
+        }
+    }
+    return MLQMC_OK;
+}
+
+// Capture the chunk (upload of the ranked samples + run_chunk) on the graph
+// stream, instantiate it and replay it once for this call.
+mlqmc_status graph_capture(mlqmc_ctx* c, int count, const int* Bt, int Lmax, double* d_sums, double* d_F,
+                           cudaStream_t st)
+{
+    mlqmc_ctx::GraphCache& G = c->graph;
+    if (!G.stream && !ok(cudaStreamCreateWithFlags(&G.stream, cudaStreamNonBlocking))) return MLQMC_ERR_CUDA;
+    if (!G.in && !ok(cudaEventCreateWithFlags(&G.in, cudaEventDisableTiming))) return MLQMC_ERR_CUDA;
+    if (!G.out && !ok(cudaEventCreateWithFlags(&G.out, cudaEventDisableTiming))) return MLQMC_ERR_CUDA;
+    if (!G.h_samples && !ok(cudaMallocHost(&G.h_samples, c->max_samples * sizeof(SampleDesc)))) {
+        G.h_samples = nullptr;
+        return MLQMC_ERR_OOM;
+    }
+    // the graph's upload reads G.h_samples: no replay of an older graph may be in flight
+    if (!ok(cudaStreamSynchronize(G.stream))) return MLQMC_ERR_CUDA;
+    std::memcpy(G.h_samples, G.key.data(), static_cast<size_t>(count) * sizeof(SampleDesc));
+    const size_t marks0 = c->marks.size();
+    const int64_t launches0 = c->launches;
+    double w0[4][kProfKinds];
+    for (int k = 0; k < kProfKinds; ++k) {
+        w0[0][k] = c->prof_bytes[k];
+        w0[1][k] = c->prof_f64[k];
+        w0[2][k] = c->prof_f32[k];
+        w0[3][k] = c->prof_ftc[k];
+    }
+    if (!ok(cudaStreamBeginCapture(G.stream, cudaStreamCaptureModeThreadLocal))) return MLQMC_ERR_CUDA;
+    G.capturing = true;
+    mlqmc_status s = ok(cudaMemcpyAsync(c->d_samples, G.h_samples, count * sizeof(SampleDesc), cudaMemcpyHostToDevice,
+                                        G.stream))
+                         ? run_chunk(c, count, Bt, Lmax, d_sums, d_F, nullptr, G.stream)
+                         : MLQMC_ERR_CUDA;
+    G.capturing = false;
+    cudaGraph_t graph = nullptr;
+    const bool ended = ok(cudaStreamEndCapture(G.stream, &graph));
+    // whatever happened, the brackets and work recorded while capturing belong to the graph
+    G.marks.assign(c->marks.begin() + static_cast<std::ptrdiff_t>(marks0), c->marks.end());
+    c->marks.resize(marks0);
+    G.launches = c->launches - launches0;
+    c->launches = launches0;
+    for (int k = 0; k < kProfKinds; ++k) {
+        G.work[0][k] = c->prof_bytes[k] - w0[0][k];
+        G.work[1][k] = c->prof_f64[k] - w0[1][k];
+        G.work[2][k] = c->prof_f32[k] - w0[2][k];
+        G.work[3][k] = c->prof_ftc[k] - w0[3][k];
+        c->prof_bytes[k] = w0[0][k];
+        c->prof_f64[k] = w0[1][k];
+        c->prof_f32[k] = w0[2][k];
+        c->prof_ftc[k] = w0[3][k];
+    }
+    if (s == MLQMC_OK && (!ended || !graph)) s = MLQMC_ERR_CUDA;
+    if (s == MLQMC_OK && !ok(cudaGraphInstantiate(&G.exec, graph, 0))) {
+        G.exec = nullptr;
+        s = MLQMC_ERR_CUDA;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (s != MLQMC_OK) {
+        graph_reset(c);
+        return s;
+    }
+    G.seen = 2;
+    return graph_replay(c, st);
 }
 
 extern "C" mlqmc_status mlqmc_sample_levels(mlqmc_ctx* c, const mlqmc_work* work, int32_t n_work, double* d_sums,
@@ -1746,6 +1882,8 @@ extern "C" mlqmc_status mlqmc_sample_levels(mlqmc_ctx* c, const mlqmc_work* work
         lvl_bytes[t] = level_bytes_per_sample(p, c->Ka, t);
         lvl_elems[t] = level_elems_per_sample(p, c->Ka, t);
     }
+    // graph replay: one chunk, fixed cycles (no host-side convergence loop)
+    const bool graphable = c->graph.enabled && p.refine_rtol == 0.0;
     size_t a = 0;
     while (a < all.size()) {
         size_t b = a, bytes = 0;
@@ -1766,10 +1904,30 @@ extern "C" mlqmc_status mlqmc_sample_levels(mlqmc_ctx* c, const mlqmc_work* work
         for (int q = 0; q < count; ++q) all[a + q].canon = q;
         int Bt[MLQMC_MAX_LEVELS], Lmax = -1;
         count_levels(all.data() + a, count, p.n_levels, Bt, &Lmax);
+        const bool single = a == 0 && b == all.size();
+        mlqmc_ctx::GraphCache& G = c->graph;
+        if (graphable && single) {
+            const bool same = G.seen > 0 && G.epoch == c->pool_epoch && G.sums == d_sums && G.F == d_F &&
+                              G.profiled == c->profiling && G.key.size() == all.size() &&
+                              std::memcmp(G.key.data(), all.data(), all.size() * sizeof(SampleDesc)) == 0;
+            bool fits = true;
+            for (int t = 0; t <= Lmax; ++t) fits = fits && Bt[t] <= c->pools[t].cap;
+            if (same && G.seen == 2) return graph_replay(c, st);
+            if (same && G.seen == 1 && fits) return graph_capture(c, count, Bt, Lmax, d_sums, d_F, st);
+        }
+        if (graphable && single) graph_reset(c);
         mlqmc_status s = stage_samples(c, all.data() + a, count, st);
         if (s != MLQMC_OK) return s;
         s = run_chunk(c, count, Bt, Lmax, d_sums, d_F, nullptr, st);
         if (s != MLQMC_OK) return s;
+        if (graphable && single) {  // remember the call: the next identical one is captured
+            G.key = all;
+            G.sums = d_sums;
+            G.F = d_F;
+            G.profiled = c->profiling;
+            G.epoch = c->pool_epoch;
+            G.seen = 1;
+        }
         a = b;
     }
     return MLQMC_OK;
@@ -2116,5 +2274,19 @@ extern "C" mlqmc_status mlqmc_set_smoother(mlqmc_ctx* c, int32_t level, int32_t 
         kind > MLQMC_SMOOTHER_TMA || !smoother_fits(c, kind, level))
         return MLQMC_ERR_INVALID_ARG;
     c->smoother[level] = kind;
+    ++c->pool_epoch;  // a captured graph runs the old smoother
     return MLQMC_OK;
+}
+
+extern "C" mlqmc_status mlqmc_set_graphs(mlqmc_ctx* c, int32_t enable)
+{
+    if (!c) return MLQMC_ERR_INVALID_ARG;
+    if (!enable) graph_reset(c);
+    c->graph.enabled = enable != 0;
+    return MLQMC_OK;
+}
+
+extern "C" int64_t mlqmc_graph_replays(const mlqmc_ctx* c)
+{
+    return c ? c->graph.replays : 0;
 }

@@ -143,6 +143,30 @@ struct mlqmc_ctx {
     int smoother[MLQMC_MAX_LEVELS] = {};
     double tune_ms[MLQMC_MAX_LEVELS][4] = {};
 
+    // Replay of repeated identical calls of the fixed-cycle forms as one CUDA
+    // graph: the second call with the same ranked samples, outputs and pools
+    // is captured (on a stream of the library's own, since the caller's may
+    // be the legacy stream), later ones replay it.
+    struct GraphCache {
+        bool enabled = true;
+        cudaStream_t stream = nullptr;
+        cudaEvent_t in = nullptr, out = nullptr;  // caller stream -> graph stream -> caller stream
+        SampleDesc* h_samples = nullptr;          // pinned descriptors the graph's upload reads
+        std::vector<SampleDesc> key;              // ranked samples of the pending / captured call
+        double* sums = nullptr;
+        double* F = nullptr;
+        uint64_t epoch = 0;
+        bool profiled = false;
+        int seen = 0;  // 1: key seen once, 2: captured
+        cudaGraphExec_t exec = nullptr;
+        std::vector<Mark> marks;  // events recorded inside the graph (profiling)
+        double work[4][kProfKinds] = {};
+        int64_t launches = 0;
+        int64_t replays = 0;
+        bool capturing = false;  // event brackets become graph event-record nodes
+    } graph;
+    uint64_t pool_epoch = 0;  // bumped whenever a pool or device buffer is reallocated
+
     int* d_status = nullptr;  // deferred device status bits
     int host_status = 0;      // deferred status found on the host (converged-form loops)
     int last_iters[MLQMC_MAX_LEVELS] = {};  // extra cycles / refinement steps per level, last converged-form call

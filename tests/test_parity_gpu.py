@@ -415,3 +415,75 @@ def test_autotuner_report():
     assert all(k == "gs" for k, _ in c64.smoother_info())
     with pytest.raises(M.MlqmcError):
         c64.set_smoother(3, "stream")  # FP64 form: kb_gs only
+
+
+# --------------------------------------------------------------------------- #
+# Graph replay of repeated identical calls                                    #
+# --------------------------------------------------------------------------- #
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_tf32"])
+def test_graph_replay_equals_direct_path(precision):
+    """The second identical call is captured as a CUDA graph and replayed,
+    later ones replay it: sums and per-sample F are bit-identical to the
+    launch-by-launch call; a different call runs directly; turning graphs
+    off gives the same results again."""
+    cfg = W.scaled(W.CONFIG2, R=2, precision=precision)
+    ctx = M.Context.from_config(cfg, genvec=_genvec(cfg))
+    nl = cfg["n_levels"]
+    work = [(5, 0, 2, 0, 2), (3, 1, 5, 0, 1), (1, 0, 7, 1, 2)]
+    ns = sum((ne - nb) * (re_ - rb) for (_, nb, ne, rb, re_) in work)
+    sums = torch.zeros(nl * 2 * 2, dtype=torch.float64, device="cuda")
+    F = torch.zeros(ns * nl, dtype=torch.float64, device="cuda")
+
+    def call(w=work):
+        sums.zero_()
+        F.zero_()
+        ctx.sample_levels(w, sums, F)
+        torch.cuda.synchronize()
+        return sums.cpu().numpy().copy(), F.cpu().numpy().copy()
+
+    ref = call()
+    assert ctx.graph_replays() == 0
+    for k in range(3):
+        got = call()
+        assert ctx.graph_replays() == k + 1
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    other = [(2, 0, 3, 0, 2)]
+    call(other)
+    assert ctx.graph_replays() == 3
+    got = call()  # remembered again, runs directly
+    assert np.array_equal(got[1], ref[1]) and ctx.graph_replays() == 3
+    ctx.set_graphs(False)
+    for _ in range(2):
+        got = call()
+        assert np.array_equal(got[1], ref[1])
+    assert ctx.graph_replays() == 3
+    ctx.check_device()
+
+
+def test_graph_replay_with_profiling():
+    """Profiling through a replayed graph: each replay's kernel brackets are
+    read back; per-kind launch counts grow by the same amount per call and
+    the results stay those of the direct path."""
+    cfg = W.scaled(W.CONFIG2, R=2, precision="mixed_tf32")
+    ctx = M.Context.from_config(cfg, genvec=_genvec(cfg))
+    nl = cfg["n_levels"]
+    work = [(4, 0, 3, 0, 2), (2, 0, 4, 0, 2)]
+    sums = torch.zeros(nl * 2 * 2, dtype=torch.float64, device="cuda")
+    ctx.profile(True)
+    outs, counts = [], []
+    for _ in range(4):
+        sums.zero_()
+        ctx.sample_levels(work, sums)
+        torch.cuda.synchronize()
+        outs.append(sums.cpu().numpy().copy())
+        prof = ctx.profile_read()
+        counts.append({k: v[1] for k, v in prof.items()})
+        ctx.profile(True)
+        assert all(v[0] > 0 for v in prof.values() if v[1] > 0)
+    ctx.profile(False)
+    assert ctx.graph_replays() == 3
+    assert all(np.array_equal(o, outs[0]) for o in outs)
+    assert all(c == counts[0] for c in counts)
+    ctx.check_device()
