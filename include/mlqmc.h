@@ -190,6 +190,21 @@ mlqmc_status mlqmc_sample_levels(mlqmc_ctx* c, const mlqmc_work* work, int32_t n
  */
 mlqmc_status mlqmc_estimate(mlqmc_ctx* c, double eps, const mlqmc_run_opts* opts, mlqmc_result* out);
 
+/*
+ * The estimator from reuse sums (host only, no context or device needed): for
+ * levels t = 0..L and shifts r < R, sums[(t*R + r)*2 + 0] = sum of dF_t over
+ * the samples that enter level t's difference ([.. + 1] the sum of squares,
+ * not used here), N[t] = samples whose FMG ended at level t. Writes Q (eq.
+ * MGMLQMC), varQ (eq. var_of_mgmlqmc) and, when non-NULL, Ybar[t] (eq.
+ * Upsilon-reuse-bar) and Vell[t] (eq. sample_variances), L+1 entries each.
+ * With reuse = 0 the difference of level t averages over N[t] samples (plain
+ * ML(Q)MC), else over N[t] + ... + N[L] (eq. Upsilon-reuse). This is how
+ * sums all-reduced over ranks that ran disjoint shift ranges become one
+ * estimate. Errors: INVALID_ARG (L outside 0..31, R < 1, negative N, NULL).
+ */
+mlqmc_status mlqmc_estimator_from_sums(int32_t L, int32_t R, int32_t reuse, const int64_t* N, const double* sums,
+                                       double* Q, double* varQ, double* Ybar, double* Vell);
+
 /* Synchronise `stream`, return and clear the deferred device status. */
 mlqmc_status mlqmc_get_device_status(mlqmc_ctx* c, void* stream);
 

@@ -102,6 +102,7 @@ def lib():
             L.mlqmc_smoother_info.argtypes = [vp, C.POINTER(C.c_int32), dp]
             L.mlqmc_set_smoother.argtypes = [vp, i32, i32]
             L.mlqmc_set_graphs.argtypes = [vp, i32]
+            L.mlqmc_estimator_from_sums.argtypes = [i32, i32, i32, C.POINTER(C.c_int64), dp, dp, dp, dp, dp]
             L.mlqmc_graph_replays.argtypes = [vp]
             L.mlqmc_graph_replays.restype = i64
             L.mlqmc_launch_count.argtypes = [vp]
@@ -109,6 +110,7 @@ def lib():
             for name in ["mlqmc_create", "mlqmc_sample_levels", "mlqmc_estimate", "mlqmc_get_device_status",
                          "mlqmc_cbc_genvec", "mlqmc_modes", "mlqmc_point_bits", "mlqmc_normals", "mlqmc_fields",
                          "mlqmc_sample_solution", "mlqmc_profile", "mlqmc_profile_read", "mlqmc_profile_work", "mlqmc_smoother_info", "mlqmc_set_smoother", "mlqmc_set_graphs",
+                         "mlqmc_estimator_from_sums",
                          "mlqmc_fmg_fields_noalloc", "mlqmc_last_iterations"]:
                 getattr(L, name).restype = C.c_int
             _lib = L
@@ -137,6 +139,23 @@ def cbc_genvec(s: int, m: int, gamma: Optional[Sequence[float]] = None):
     _check(lib().mlqmc_cbc_genvec(int(s), int(m), g.ctypes.data_as(C.POINTER(C.c_double)), z,
                                   e2.ctypes.data_as(C.POINTER(C.c_double))), "mlqmc_cbc_genvec")
     return np.array(list(z), dtype=np.uint32), e2
+
+
+def estimator_from_sums(N, sums, R: int, reuse: bool = True):
+    """Q, varQ, Ybar, Vell from reuse sums [L+1][R][2] (host; eqs. MGMLQMC,
+    var_of_mgmlqmc, Upsilon-reuse-bar, sample_variances)."""
+    Nn = np.ascontiguousarray(N, dtype=np.int64)
+    S = np.ascontiguousarray(sums, dtype=np.float64).reshape(-1)
+    L = len(Nn) - 1
+    if S.size != (L + 1) * R * 2:
+        raise ValueError("sums must hold (L+1) x R x 2 values")
+    Q, V = C.c_double(), C.c_double()
+    Yb, Vl = np.zeros(L + 1), np.zeros(L + 1)
+    dp = C.POINTER(C.c_double)
+    _check(lib().mlqmc_estimator_from_sums(int(L), int(R), 1 if reuse else 0, Nn.ctypes.data_as(C.POINTER(C.c_int64)),
+                                           S.ctypes.data_as(dp), C.byref(Q), C.byref(V), Yb.ctypes.data_as(dp),
+                                           Vl.ctypes.data_as(dp)), "mlqmc_estimator_from_sums")
+    return dict(Q=Q.value, varQ=V.value, Ybar=Yb, Vell=Vl)
 
 
 def _ptr(t) -> Optional[int]:

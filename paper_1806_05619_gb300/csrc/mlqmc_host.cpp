@@ -429,3 +429,21 @@ extern "C" mlqmc_status mlqmc_estimate(mlqmc_ctx* c, double eps, const mlqmc_run
 {
     return mlqmc::run_estimate(c, eps, opts, out);
 }
+
+extern "C" mlqmc_status mlqmc_estimator_from_sums(int32_t L, int32_t R, int32_t reuse, const int64_t* N,
+                                                  const double* sums, double* Q, double* varQ, double* Ybar,
+                                                  double* Vell)
+{
+    if (L < 0 || L >= 32 || R < 1 || !N || !sums || !Q || !varQ) return MLQMC_ERR_INVALID_ARG;
+    for (int t = 0; t <= L; ++t)
+        if (N[t] < 0) return MLQMC_ERR_INVALID_ARG;
+    const std::vector<double> s(sums, sums + static_cast<size_t>(L + 1) * R * 2);
+    const mlqmc::Est e = mlqmc::finalize(L, R, reuse != 0, N, s);
+    *Q = e.Q;
+    *varQ = e.varQ;
+    for (int t = 0; t <= L; ++t) {
+        if (Ybar) Ybar[t] = e.Ybar[t];
+        if (Vell) Vell[t] = e.V[t];
+    }
+    return MLQMC_OK;
+}
