@@ -493,9 +493,9 @@ def run_precision_form(dev, stream, flush, M):
     """Precision form: one batch of 256 samples whose FMG ends on the 1024x1024
     level (8 levels from 8x8), s = 400 KL modes (lambda = 0.1), 16 shifts x 16
     lattice points, every level refined to ||r||_2/||b||_2 <= 1e-10: the mixed
-    form (TF32 tensor-core KL, FP32 V-cycles, FP64 residual and correction)
-    against the all-FP64 GPU form, timing per batch and the mixed results'
-    deviation from the FP64 ones (field, solution, F on every level)."""
+    forms (TF32 or split-BF16 tensor-core KL, FP32 V-cycles, FP64 residual and
+    correction) against the all-FP64 GPU form, timing per batch and the mixed
+    results' deviation from the FP64 ones (field, solution, F on every level)."""
     import torch
 
     cfg = dict(W.CONFIG3)
@@ -508,7 +508,7 @@ def run_precision_form(dev, stream, flush, M):
     out = {"workload": "256 samples (16 shifts x 16 points) on 8 levels 8x8..1024x1024, s=400, lambda=0.1, "
                        "refined to relative residual 1e-10 on every level"}
     res = {}
-    for prec in ["mixed_tf32", "fp64"]:
+    for prec in ["mixed_tf32", "mixed_bf16x3", "fp64"]:
         c = dict(cfg)
         c["precision"] = prec
         ctx = M.Context.from_config(c, genvec=genvec, max_samples=ns)
@@ -535,13 +535,15 @@ def run_precision_form(dev, stream, flush, M):
         out[prec] = {"ms_per_batch": min(times), "samples_per_s": ns / (min(times) * 1e-3)}
         del ctx
         torch.cuda.empty_cache()
-    a, b = res["mixed_tf32"], res["fp64"]
-    out["speedup_mixed_over_fp64"] = b["ms"] / a["ms"]
-    out["err_mixed_vs_fp64"] = {
-        "field_max_abs_log_ratio": float(np.max(np.abs(np.log(a["k"] / b["k"])))),
-        "solution_max_rel": float(np.max(np.abs(a["u"] - b["u"])) / np.max(np.abs(b["u"]))),
-        "F_max_rel_per_level": [float(np.max(np.abs(a["F"][:, t] / b["F"][:, t] - 1))) for t in range(nl)],
-    }
+    b = res["fp64"]
+    for prec in ["mixed_tf32", "mixed_bf16x3"]:
+        a = res[prec]
+        out[prec]["speedup_over_fp64"] = b["ms"] / a["ms"]
+        out[prec]["err_vs_fp64"] = {
+            "field_max_abs_log_ratio": float(np.max(np.abs(np.log(a["k"] / b["k"])))),
+            "solution_max_rel": float(np.max(np.abs(a["u"] - b["u"])) / np.max(np.abs(b["u"]))),
+            "F_max_rel_per_level": [float(np.max(np.abs(a["F"][:, t] / b["F"][:, t] - 1))) for t in range(nl)],
+        }
     return out
 
 

@@ -12,6 +12,13 @@
 // four warps then read their 32 TMEM lanes (one cell each) with tcgen05.ld,
 // apply exp and store k sample by sample, coalesced across cells.
 // Operands are rounded to TF32 (round to nearest) when they are built.
+//
+// Split-BF16 variant: every operand x is split into hi = bf16(x) and
+// lo = bf16(x - hi), and the contraction sums the three products hi*hi,
+// hi*lo and lo*hi (the lo*lo term is below FP32 resolution of the sum). The
+// three products are one GEMM over a tripled K: Psi rows hold [hi | hi | lo],
+// C rows [hi | lo | hi], so the kernel is the TF32 one with kind::f16 MMAs on
+// BF16 operands; a 128-byte K block holds 64 BF16 instead of 32 TF32.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -19,6 +26,8 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+
+#include <cuda_bf16.h>
 
 #include "kl_tcgen05.h"
 
@@ -116,6 +125,23 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_
         : "memory");
 }
 
+// Instruction descriptor: kind::f16 with A = B = BF16, D = F32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+           (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -139,7 +165,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-template <int NT>
+template <int NT, bool BF>
 __global__ void __launch_bounds__(128, 1) kl_tc_kernel(const __grid_constant__ CUtensorMap tm_psi,
                                                        const __grid_constant__ CUtensorMap tm_c, int M, int B, int nk,
                                                        float* __restrict__ kout, size_t kstride, int* err)
@@ -190,8 +216,9 @@ __global__ void __launch_bounds__(128, 1) kl_tc_kernel(const __grid_constant__ C
             if (kb >= kStages) ok = mbar_wait(&empty[s], ((kb / kStages) - 1) & 1, err);
             if (!ok) break;
             mbar_expect_tx(&full[s], kABytes + kBBytes);
-            tma_load_2d(sa + s * kABytes, &tm_psi, &full[s], kb * kKBlock, m0);
-            tma_load_2d(sb + s * kBBytes, &tm_c, &full[s], kb * kKBlock, b0);
+            constexpr int kElems = BF ? 64 : kKBlock;  // elements per 128-byte K block
+            tma_load_2d(sa + s * kABytes, &tm_psi, &full[s], kb * kElems, m0);
+            tma_load_2d(sb + s * kBBytes, &tm_c, &full[s], kb * kElems, b0);
             issued = kb + 1;
         }
         // let every copy this thread issued land before the CTA can leave
@@ -199,7 +226,7 @@ __global__ void __launch_bounds__(128, 1) kl_tc_kernel(const __grid_constant__ C
             mbar_wait(&full[kb % kStages], (kb / kStages) & 1, err);
     } else if (threadIdx.x == 32) {
         // MMA issuer
-        constexpr uint32_t idesc = idesc_tf32(kTileM, NT);
+        constexpr uint32_t idesc = BF ? idesc_bf16(kTileM, NT) : idesc_tf32(kTileM, NT);
         for (int kb = 0; kb < nk; ++kb) {
             const int s = kb % kStages;
             if (!mbar_wait(&full[s], (kb / kStages) & 1, err)) {
@@ -210,8 +237,10 @@ __global__ void __launch_bounds__(128, 1) kl_tc_kernel(const __grid_constant__ C
             const uint64_t ad = sdesc_sw128(smem_u32(sa + s * kABytes));
             const uint64_t bd = sdesc_sw128(smem_u32(sb + s * kBBytes));
 #pragma unroll
-            for (int k = 0; k < kKBlock / 8; ++k)  // 8 TF32 = 32 bytes of K per MMA
-                mma_tf32(tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+            for (int k = 0; k < kKBlock / 8; ++k) {  // 32 bytes of K per MMA: 8 TF32 or 16 BF16
+                if constexpr (BF) mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+                else mma_tf32(tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+            }
             mma_commit(&empty[s]);
         }
         mma_commit(accum);
@@ -282,6 +311,52 @@ __global__ void kl_build_c(const double* __restrict__ Y, const int* __restrict__
     }
 }
 
+// hi + lo split of x (round to nearest both times)
+__device__ __forceinline__ void split_bf16(double v, __nv_bfloat16& hi, __nv_bfloat16& lo)
+{
+    const float x = static_cast<float>(v);
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// Psi3[p][j], j < 3 kp: [hi | hi | lo] of psi_{a_m}(x1) psi_{b_m}(x2), zero for m >= s.
+__global__ void kl_build_psi_bf16x3(const double* __restrict__ psi1d, int n, int s, int kp, const int* __restrict__ ma,
+                                    const int* __restrict__ mb, __nv_bfloat16* __restrict__ out)
+{
+    const int64_t total = static_cast<int64_t>(n) * n * kp;
+    for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int m = static_cast<int>(idx % kp);
+        const int64_t p = idx / kp;
+        const int i2 = static_cast<int>(p / n), i1 = static_cast<int>(p % n);
+        __nv_bfloat16 hi = __float2bfloat16_rn(0.0f), lo = hi;
+        if (m < s) split_bf16(psi1d[static_cast<size_t>(ma[m]) * n + i1] * psi1d[static_cast<size_t>(mb[m]) * n + i2], hi, lo);
+        __nv_bfloat16* row = out + p * 3 * kp;
+        row[m] = hi;
+        row[kp + m] = hi;
+        row[2 * kp + m] = lo;
+    }
+}
+
+// C3[i][j]: [hi | lo | hi] of sqrt(theta_m) y_{canon_i, m}, zero for m >= s.
+__global__ void kl_build_c_bf16x3(const double* __restrict__ Y, const int* __restrict__ canon, int count, int s, int kp,
+                                  const double* __restrict__ sqrt_theta, __nv_bfloat16* __restrict__ out)
+{
+    const int64_t total = static_cast<int64_t>(count) * kp;
+    for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int m = static_cast<int>(idx % kp);
+        const int i = static_cast<int>(idx / kp);
+        const size_t src = canon ? static_cast<size_t>(canon[i]) : static_cast<size_t>(i);
+        __nv_bfloat16 hi = __float2bfloat16_rn(0.0f), lo = hi;
+        if (m < s) split_bf16(sqrt_theta[m] * Y[src * s + m], hi, lo);
+        __nv_bfloat16* row = out + static_cast<size_t>(i) * 3 * kp;
+        row[m] = hi;
+        row[kp + m] = lo;
+        row[2 * kp + m] = hi;
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -296,18 +371,20 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-// 2D FP32 map: rows x kpad (inner), box kKBlock x box_rows, 128-byte swizzle.
-bool encode_2d(CUtensorMap* map, const float* base, uint64_t rows, uint64_t kpad, uint32_t box_rows)
+// 2D map over rows x kdim (inner) elements of 4 (FP32) or 2 (BF16) bytes:
+// box of one 128-byte K block x box_rows, 128-byte swizzle.
+bool encode_2d(CUtensorMap* map, const void* base, uint64_t rows, uint64_t kdim, uint32_t box_rows, bool bf16)
 {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
     if (!fn) return false;
-    const cuuint64_t dims[2] = {kpad, rows};
-    const cuuint64_t strides[1] = {kpad * sizeof(float)};
-    const cuuint32_t box[2] = {static_cast<cuuint32_t>(kKBlock), box_rows};
+    const uint64_t es = bf16 ? 2 : 4;
+    const cuuint64_t dims[2] = {kdim, rows};
+    const cuuint64_t strides[1] = {kdim * es};
+    const cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / es), box_rows};
     const cuuint32_t estr[2] = {1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base),
+              dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 constexpr int kNT = 256;
@@ -326,48 +403,70 @@ int kpad_for(int s)
     return (s + kKBlock - 1) / kKBlock * kKBlock;
 }
 
-bool build_psi(const double* d_psi1d, int n, int s, const int* d_ma, const int* d_mb, float* d_out, cudaStream_t st)
+int kdim_for(Variant v, int s)
 {
-    const int kpad = kpad_for(s);
-    const int64_t total = static_cast<int64_t>(n) * n * kpad;
+    if (v == Variant::TF32) return kpad_for(s);
+    return 3 * ((s + 63) / 64 * 64);  // three BF16 parts, each whole 64-element (128-byte) blocks
+}
+
+size_t row_bytes(Variant v, int s)
+{
+    return static_cast<size_t>(kdim_for(v, s)) * (v == Variant::TF32 ? 4 : 2);
+}
+
+bool build_psi(Variant v, const double* d_psi1d, int n, int s, const int* d_ma, const int* d_mb, void* d_out,
+               cudaStream_t st)
+{
+    const int kp = v == Variant::TF32 ? kpad_for(s) : kdim_for(v, s) / 3;
+    const int64_t total = static_cast<int64_t>(n) * n * kp;
     const int grid = static_cast<int>(std::min<int64_t>((total + 255) / 256, 152 * 64));
-    kl_build_psi<<<grid, 256, 0, st>>>(d_psi1d, n, s, kpad, d_ma, d_mb, d_out);
+    if (v == Variant::TF32) kl_build_psi<<<grid, 256, 0, st>>>(d_psi1d, n, s, kp, d_ma, d_mb, static_cast<float*>(d_out));
+    else kl_build_psi_bf16x3<<<grid, 256, 0, st>>>(d_psi1d, n, s, kp, d_ma, d_mb, static_cast<__nv_bfloat16*>(d_out));
     return cudaGetLastError() == cudaSuccess;
 }
 
-bool build_c(const double* d_Y, const int* d_canon, int count, int s, const double* d_sqrt_theta, float* d_out,
-             cudaStream_t st)
+bool build_c(Variant v, const double* d_Y, const int* d_canon, int count, int s, const double* d_sqrt_theta,
+             void* d_out, cudaStream_t st)
 {
-    const int kpad = kpad_for(s);
-    const int64_t total = static_cast<int64_t>(count) * kpad;
+    const int kp = v == Variant::TF32 ? kpad_for(s) : kdim_for(v, s) / 3;
+    const int64_t total = static_cast<int64_t>(count) * kp;
     const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 64)));
-    kl_build_c<<<grid, 256, 0, st>>>(d_Y, d_canon, count, s, kpad, d_sqrt_theta, d_out);
+    if (v == Variant::TF32)
+        kl_build_c<<<grid, 256, 0, st>>>(d_Y, d_canon, count, s, kp, d_sqrt_theta, static_cast<float*>(d_out));
+    else
+        kl_build_c_bf16x3<<<grid, 256, 0, st>>>(d_Y, d_canon, count, s, kp, d_sqrt_theta,
+                                                static_cast<__nv_bfloat16*>(d_out));
     return cudaGetLastError() == cudaSuccess;
 }
 
-bool make_maps(const float* d_psi, int M, const float* d_c, int rows_c, int s, TensorMaps* maps)
+bool make_maps(Variant v, const void* d_psi, int M, const void* d_c, int rows_c, int s, TensorMaps* maps)
 {
-    const int kpad = kpad_for(s);
+    const int kd = kdim_for(v, s);
+    const bool bf = v == Variant::BF16X3;
     static_assert(sizeof(TensorMaps::psi) >= sizeof(CUtensorMap), "map storage");
-    return encode_2d(reinterpret_cast<CUtensorMap*>(maps->psi), d_psi, static_cast<uint64_t>(M), kpad, kTileM) &&
-           encode_2d(reinterpret_cast<CUtensorMap*>(maps->c), d_c, static_cast<uint64_t>(rows_c), kpad, kNT);
+    return encode_2d(reinterpret_cast<CUtensorMap*>(maps->psi), d_psi, static_cast<uint64_t>(M), kd, kTileM, bf) &&
+           encode_2d(reinterpret_cast<CUtensorMap*>(maps->c), d_c, static_cast<uint64_t>(rows_c), kd, kNT, bf);
 }
 
 bool prepare_kernel()
 {
-    return cudaFuncSetAttribute(kl_tc_kernel<kNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(tc_smem_bytes())) == cudaSuccess;
+    const int b = static_cast<int>(tc_smem_bytes());
+    return cudaFuncSetAttribute(kl_tc_kernel<kNT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(kl_tc_kernel<kNT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) == cudaSuccess;
 }
 
-bool launch(const TensorMaps& maps, int M, int B, int s, float* d_k, size_t kstride, int* d_err, cudaStream_t st)
+bool launch(Variant v, const TensorMaps& maps, int M, int B, int s, float* d_k, size_t kstride, int* d_err,
+            cudaStream_t st)
 {
     if (M % kTileM != 0 || B <= 0) return false;
-    const int nk = kpad_for(s) / kKBlock;
+    const int nk = static_cast<int>(row_bytes(v, s) / 128);  // 128-byte K blocks
     CUtensorMap tp, tc;
     std::memcpy(&tp, maps.psi, sizeof(CUtensorMap));
     std::memcpy(&tc, maps.c, sizeof(CUtensorMap));
     dim3 grid(M / kTileM, (B + kNT - 1) / kNT);
-    kl_tc_kernel<kNT><<<grid, 128, tc_smem_bytes(), st>>>(tp, tc, M, B, nk, d_k, kstride, d_err);
+    if (v == Variant::TF32) kl_tc_kernel<kNT, false><<<grid, 128, tc_smem_bytes(), st>>>(tp, tc, M, B, nk, d_k, kstride, d_err);
+    else kl_tc_kernel<kNT, true><<<grid, 128, tc_smem_bytes(), st>>>(tp, tc, M, B, nk, d_k, kstride, d_err);
     return cudaGetLastError() == cudaSuccess;
 }
 

@@ -13,20 +13,27 @@ struct alignas(64) TensorMaps {
     unsigned char c[128];
 };
 
-int kpad_for(int s);   // K padded to whole 32-element blocks
-int tile_samples();    // samples per CTA tile
+// Operand form: TF32 (one rounding per operand) or split BF16 (three products).
+enum class Variant { TF32, BF16X3 };
 
-// Psi of one level (n x n cells, row-major p = i2*n + i1; kpad_for(s) columns) from the FP64 1D tables.
-bool build_psi(const double* d_psi1d, int n, int s, const int* d_ma, const int* d_mb, float* d_out, cudaStream_t st);
+int kpad_for(int s);                    // s padded to whole 32-element blocks (TF32)
+int kdim_for(Variant v, int s);         // K of the GEMM: kpad_for(s), or 3 x (s padded to 64) for BF16X3
+size_t row_bytes(Variant v, int s);     // bytes of one operand row (a whole number of 128-byte K blocks)
+int tile_samples();                     // samples per CTA tile
 
-// C rows i < count: tf32(sqrt(theta_m) y_m) of the sample whose normals are row canon[i] of Y.
-bool build_c(const double* d_Y, const int* d_canon, int count, int s, const double* d_sqrt_theta, float* d_out,
-             cudaStream_t st);
+// Psi of one level (n x n cells, row-major p = i2*n + i1; kdim_for(v, s) columns) from the FP64 1D tables.
+bool build_psi(Variant v, const double* d_psi1d, int n, int s, const int* d_ma, const int* d_mb, void* d_out,
+               cudaStream_t st);
 
-bool make_maps(const float* d_psi, int M, const float* d_c, int rows_c, int s, TensorMaps* maps);
+// C rows i < count: sqrt(theta_m) y_m of the sample whose normals are row canon[i] of Y (canon NULL: row i).
+bool build_c(Variant v, const double* d_Y, const int* d_canon, int count, int s, const double* d_sqrt_theta,
+             void* d_out, cudaStream_t st);
+
+bool make_maps(Variant v, const void* d_psi, int M, const void* d_c, int rows_c, int s, TensorMaps* maps);
 bool prepare_kernel();
 
 // k[b * kstride + p] = exp(sum_m Psi[p][m] C[b][m]) for p < M (M a multiple of 128), b < B.
-bool launch(const TensorMaps& maps, int M, int B, int s, float* d_k, size_t kstride, int* d_err, cudaStream_t st);
+bool launch(Variant v, const TensorMaps& maps, int M, int B, int s, float* d_k, size_t kstride, int* d_err,
+            cudaStream_t st);
 
 }  // namespace mlqmc_kl

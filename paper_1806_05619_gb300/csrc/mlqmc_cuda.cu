@@ -1022,12 +1022,14 @@ mlqmc_status synth_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cudaStr
         if (uses_tc(c, t)) {
             const LevelPool& P = c->pools[t];
             float* k = reinterpret_cast<float*>(P.mem + P.off[kK]);
-            const double M = static_cast<double>(n * n), K = mlqmc_kl::kpad_for(c->p.n_modes);
+            const double M = static_cast<double>(n * n);
+            const double K = static_cast<double>(mlqmc_kl::row_bytes(c->kl_variant, c->p.n_modes)) / 4.0;
             Work w;
             w.bytes = 4.0 * (M * B + M * K + B * K);  // k out, Psi and C in
             w.ftc = 2.0 * M * c->p.n_modes * B;
             Timed tm(c, kProfKlTc, st, w);
-            if (!mlqmc_kl::launch(c->kl_maps[t], static_cast<int>(n * n), B, c->p.n_modes, k, P.stride[kK] / sizeof(float),
+            if (!mlqmc_kl::launch(c->kl_variant, c->kl_maps[t], static_cast<int>(n * n), B, c->p.n_modes, k,
+                                  P.stride[kK] / sizeof(float),
                                   c->d_status, st))
                 return MLQMC_ERR_CUDA;
         }
@@ -1060,8 +1062,9 @@ mlqmc_status build_c(mlqmc_ctx* c, int count, cudaStream_t st)
 {
     if (!c->kl_tc) return MLQMC_OK;
     Timed tm(c, kProfKlTc, st,
-             work_of<float>(count * (8.0 * c->p.n_modes + 4.0 * mlqmc_kl::kpad_for(c->p.n_modes)), 0.0));
-    return mlqmc_kl::build_c(c->d_Y, nullptr, count, c->p.n_modes, c->d_sqrt_theta, c->d_C, st) ? MLQMC_OK
+             work_of<float>(count * (8.0 * c->p.n_modes + mlqmc_kl::row_bytes(c->kl_variant, c->p.n_modes)), 0.0));
+    return mlqmc_kl::build_c(c->kl_variant, c->d_Y, nullptr, count, c->p.n_modes, c->d_sqrt_theta, c->d_C, st)
+               ? MLQMC_OK
                                                                                                 : MLQMC_ERR_CUDA;
 }
 
@@ -1587,7 +1590,6 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
     mlqmc_status st = check_problem(p);
     if (st != MLQMC_OK) return st;
     if (max_samples_per_call < 0) return MLQMC_ERR_INVALID_ARG;
-    if (p->precision == MLQMC_MIXED_BF16X3) return MLQMC_ERR_UNSUPPORTED;
     mlqmc_ctx* c = new (std::nothrow) mlqmc_ctx();
     if (!c) return MLQMC_ERR_OOM;
     c->p = *p;
@@ -1671,15 +1673,18 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
         return MLQMC_ERR_CUDA;
     }
     // tensor-core KL tables (mixed TF32 form): Psi of every level with a whole number of 128-cell tiles
-    if (p->precision == MLQMC_MIXED_TF32) {
-        const int kpad = mlqmc_kl::kpad_for(p->n_modes);
-        good = mlqmc_kl::prepare_kernel() && ok(cudaMalloc(&c->d_C, ms * kpad * sizeof(float)));
+    if (p->precision == MLQMC_MIXED_TF32 || p->precision == MLQMC_MIXED_BF16X3) {
+        c->kl_variant = p->precision == MLQMC_MIXED_TF32 ? mlqmc_kl::Variant::TF32 : mlqmc_kl::Variant::BF16X3;
+        const size_t rb = mlqmc_kl::row_bytes(c->kl_variant, p->n_modes);
+        good = mlqmc_kl::prepare_kernel() && ok(cudaMalloc(&c->d_C, ms * rb));
         for (int t = 0; good && t < p->n_levels; ++t) {
             const int n = p->coarse_cells << t;
             if ((n * n) % 128 != 0) continue;
-            good = ok(cudaMalloc(&c->d_psi_tc[t], static_cast<size_t>(n) * n * kpad * sizeof(float))) &&
-                   mlqmc_kl::build_psi(c->d_psi + c->psi_off[t], n, p->n_modes, c->d_ma, c->d_mb, c->d_psi_tc[t], 0) &&
-                   mlqmc_kl::make_maps(c->d_psi_tc[t], n * n, c->d_C, static_cast<int>(ms), p->n_modes, &c->kl_maps[t]);
+            good = ok(cudaMalloc(&c->d_psi_tc[t], static_cast<size_t>(n) * n * rb)) &&
+                   mlqmc_kl::build_psi(c->kl_variant, c->d_psi + c->psi_off[t], n, p->n_modes, c->d_ma, c->d_mb,
+                                       c->d_psi_tc[t], 0) &&
+                   mlqmc_kl::make_maps(c->kl_variant, c->d_psi_tc[t], n * n, c->d_C, static_cast<int>(ms), p->n_modes,
+                                       &c->kl_maps[t]);
         }
         if (!good || !ok(cudaDeviceSynchronize())) {
             free_ctx(c);

@@ -97,8 +97,9 @@ struct mlqmc_ctx {
 
     // tensor-core KL (mixed TF32 form): Psi per level with >= 128 cells, C per chunk
     bool kl_tc = false;
-    float* d_psi_tc[MLQMC_MAX_LEVELS] = {};
-    float* d_C = nullptr;
+    void* d_psi_tc[MLQMC_MAX_LEVELS] = {};  // Psi operand per level (FP32 or split BF16 rows)
+    void* d_C = nullptr;   // C operand of the contraction (FP32 or split BF16 rows)
+    mlqmc_kl::Variant kl_variant = mlqmc_kl::Variant::TF32;
     mlqmc_kl::TensorMaps kl_maps[MLQMC_MAX_LEVELS];
 
     // per-chunk buffers (max_samples entries)

@@ -296,42 +296,66 @@ def _tf32_u(s):
     return 2 * 2.0 ** -11 + s * 2.0 ** -24
 
 
+def _bf16x3_u(s):
+    """Error factor of the split-BF16 contraction: each operand x = hi + lo + d
+    with |d| <= 2^-16 |x| (8-bit significands, unit roundoff 2^-8 twice), the
+    dropped lo*lo product <= 2^-16 |ab|, the FP32 rounding of both operands
+    (2 * 2^-24) and an FP32 accumulation over the 3s products (3s * 2^-24)."""
+    return 3 * 2.0 ** -16 + 2 * 2.0 ** -24 + 3 * s * 2.0 ** -24
+
+
 EXP_SLACK = 2.0 ** -20  # FP32 exp and the FP32 face arithmetic
+MIXED = [("mixed_tf32", _tf32_u), ("mixed_bf16x3", _bf16x3_u)]
 
 
-def test_mixed_fields_within_bound():
-    cfg, ctx, orc = _pair(W.CONFIG3, n_levels=4)
+@pytest.mark.parametrize("precision,ufun", MIXED)
+def test_mixed_fields_within_bound(precision, ufun):
+    cfg, ctx, orc = _pair(W.CONFIG3, n_levels=4, precision=precision)
     Y = W.random_normals(cfg["s"], 2, tag=40)
     for t in [0, 3]:
         k = ctx.fields(t, torch.from_numpy(Y)).cpu().numpy()
         for i in range(2):
             want = orc.field(t, Y[i])
-            eta = _field_bound(orc, cfg, Y[i], _tf32_u(cfg["s"]))
+            eta = _field_bound(orc, cfg, Y[i], ufun(cfg["s"]))
             assert np.max(np.abs(np.log(k[i] / want))) <= eta + EXP_SLACK
 
 
-def test_tensor_core_fields_many_samples():
+def test_split_bf16_more_accurate_than_tf32():
+    """Same normals, level of 256 x 256 cells (tensor-core path): the split-BF16
+    field's largest log-error is at least 8x below the TF32 one."""
+    errs = {}
+    for precision in ["mixed_tf32", "mixed_bf16x3"]:
+        cfg, ctx, orc = _pair(W.CONFIG3, n_levels=6, precision=precision)
+        Y = W.random_normals(cfg["s"], 3, tag=42)
+        k = ctx.fields(5, torch.from_numpy(Y)).cpu().numpy()
+        errs[precision] = max(np.max(np.abs(np.log(k[i] / orc.field(5, Y[i])))) for i in range(3))
+    assert errs["mixed_bf16x3"] * 8 <= errs["mixed_tf32"], errs
+
+
+@pytest.mark.parametrize("precision,ufun", MIXED)
+def test_tensor_core_fields_many_samples(precision, ufun):
     """More samples than one tensor-core tile (256) and several cell tiles."""
-    cfg, ctx, orc = _pair(W.CONFIG3, n_levels=4)
+    cfg, ctx, orc = _pair(W.CONFIG3, n_levels=4, precision=precision)
     Y = W.random_normals(cfg["s"], 300, tag=41)
     k = ctx.fields(2, torch.from_numpy(Y)).cpu().numpy()
     assert np.all(np.isfinite(k)) and np.all(k > 0)
     for i in [0, 1, 255, 256, 299]:
         want = orc.field(2, Y[i])
-        eta = _field_bound(orc, cfg, Y[i], _tf32_u(cfg["s"]))
+        eta = _field_bound(orc, cfg, Y[i], ufun(cfg["s"]))
         err = np.max(np.abs(np.log(k[i] / want)))
         assert err <= eta + EXP_SLACK, (i, err, eta)
     ctx.check_device()
 
 
-def test_mixed_qoi_within_bound():
-    cfg, ctx, orc = _pair(W.CONFIG3, n_levels=5, R=2)
+@pytest.mark.parametrize("precision,ufun", MIXED)
+def test_mixed_qoi_within_bound(precision, ufun):
+    cfg, ctx, orc = _pair(W.CONFIG3, n_levels=5, R=2, precision=precision)
     for (lv, r, n) in [(4, 0, 3), (2, 1, 0)]:
         sols, F = ctx.sample_solution(lv, r, n)
         ref = orc.sample(lv, r, n, want_u=True)
         assert ref["status"] == O.OK
         y = orc.normals(lv, r, n)
-        eta = _field_bound(orc, cfg, y, _tf32_u(cfg["s"])) + EXP_SLACK
+        eta = _field_bound(orc, cfg, y, ufun(cfg["s"])) + EXP_SLACK
         Fg = F.cpu().numpy()
         for t in range(lv + 1):
             u = ref["u"][t]
