@@ -210,6 +210,112 @@ __global__ void kb_coarse(FmgArgs A, int B)
     }
 }
 
+// Level 0 for n0 = NC fixed at compile time, one thread per sample, with the
+// working rows of the factorisation in shared memory: column j of L needs
+// rows j..j+NC only, so a ring of NC+1 rows per thread (transposed by thread:
+// conflict-free) holds them; a finished row goes to the global factor once.
+// The forward substitution runs along with the factorisation, the backward
+// one on the thread's y in shared memory. Same arithmetic, in the same order,
+// as kb_level0.
+template <typename T, bool MX, int NC>
+__global__ void __launch_bounds__(64) kb_level0_fixed(FmgArgs A, int B)
+{
+    constexpr int N = NC * NC, W = NC + 1, TPB = 64;
+    extern __shared__ double l0sh[];
+    double* ring = l0sh;             // [(slot * W + e) * TPB + tid]
+    double* ys = l0sh + W * W * TPB;  // [r * TPB + tid]
+    const int tid = threadIdx.x;
+    const size_t cs = A.chol.stride;
+    double* fac = reinterpret_cast<double*>(A.chol.base);
+    float* f32 = reinterpret_cast<float*>(A.chol32);
+    const double h2 = 1.0 / (static_cast<double>(NC) * NC);
+    for (int base = blockIdx.x * TPB; base < B; base += gridDim.x * TPB) {
+        const int i = base + tid;
+        if (i >= B) continue;  // no barriers in this kernel: shared rows are private to the thread
+        auto Rs = [&](int slot, int e) -> double& { return ring[(slot * W + e) * TPB + tid]; };
+        auto Y = [&](int r) -> double& { return ys[r * TPB + tid]; };
+        const Lv<T> L0 = view<T>(A, 0, i);
+        // step j: row j's diagonal, its forward-substitution value, the row to
+        // global memory, then column j of L for rows j+1..j+NC (ring slot of
+        // row r: r mod W; FULL: j >= NC, every loop has its whole, compile-time range)
+        auto step = [&](int j, auto full) {
+            constexpr bool FULL = decltype(full)::value;
+            const int s0 = j % W;
+            auto slot = [&](int l) { return s0 + l >= W ? s0 + l - W : s0 + l; };  // slot of row j + l
+            const int j1 = j % NC, j2 = j / NC;
+            double d = static_cast<double>(L0.kx[j2 * kx_pitch(NC) + j1]) +
+                       static_cast<double>(L0.kx[j2 * kx_pitch(NC) + j1 + 1]) +
+                       static_cast<double>(L0.ky[j2 * NC + j1]) + static_cast<double>(L0.ky[(j2 + 1) * NC + j1]);
+#pragma unroll
+            for (int q = 1; q <= NC; ++q) {
+                if (!FULL && q > j) break;
+                const double l = Rs(s0, q);
+                d -= l * l;
+            }
+            const double rl = 1.0 / sqrt(d);
+            Rs(s0, 0) = rl;
+            double v = h2;  // forward substitution, f = 1
+#pragma unroll
+            for (int q = 1; q <= NC; ++q) {
+                if (!FULL && q > j) break;
+                v -= Rs(s0, q) * Y(j - q);
+            }
+            Y(j) = v * rl;
+#pragma unroll
+            for (int e = 0; e <= NC; ++e) {
+                if (!FULL && e > j) break;
+                fac[static_cast<size_t>(j * W + e) * cs + i] = Rs(s0, e);
+                if constexpr (MX) f32[static_cast<size_t>(j * W + e) * cs + i] = static_cast<float>(Rs(s0, e));
+            }
+#pragma unroll
+            for (int l = 1; l <= NC; ++l) {
+                const int r = j + l;
+                if (r >= N) break;
+                double a = static_cast<double>(band_a(L0.kx, L0.ky, NC, r, l));
+                const int sr = slot(l);
+                if constexpr (FULL) {
+#pragma unroll
+                    for (int u = 0; u < NC - l; ++u) {  // tt = r - NC + u = j - (NC - l) + u
+                        a -= Rs(sr, NC - u) * Rs(s0, NC - l - u);
+                    }
+                } else {
+                    for (int tt = (r - NC > 0 ? r - NC : 0); tt < j; ++tt) a -= Rs(sr, r - tt) * Rs(s0, j - tt);
+                }
+                Rs(sr, l) = a * rl;
+            }
+        };
+        for (int j = 0; j < NC; ++j) step(j, std::false_type());
+        for (int j = NC; j < N; ++j) step(j, std::true_type());
+        for (int r = N - 1; r >= 0; --r) {
+            double v = Y(r);
+            for (int q = 1; q <= NC && r + q < N; ++q) v -= fac[static_cast<size_t>((r + q) * W + q) * cs + i] * Y(r + q);
+            Y(r) = v * fac[static_cast<size_t>(r * W) * cs + i];
+        }
+        double* x = (MX || A.refine) ? L0.u64 : reinterpret_cast<double*>(L0.u);
+        for (int r = 0; r < N; ++r) x[r] = Y(r);
+        if constexpr (MX) {
+            float* u32 = reinterpret_cast<float*>(L0.u);  // FP32 copy for the first FMG interpolation
+            for (int r = 0; r < N; ++r) u32[r] = static_cast<float>(Y(r));
+        }
+        double F0;
+        if (A.qoi == MLQMC_QOI_MEAN) {
+            double acc = 0.0;
+            for (int r = 0; r < N; ++r) acc += Y(r);
+            F0 = acc / static_cast<double>(N);
+        } else {
+            constexpr int m = NC / 2;
+            F0 = 0.25 * (Y((m - 1) * NC + (m - 1)) + Y((m - 1) * NC + m) + Y(m * NC + (m - 1)) + Y(m * NC + m));
+        }
+        A.F[static_cast<size_t>(i) * A.n_levels] = F0;
+    }
+}
+
+template <int NC>
+constexpr size_t level0_smem()
+{
+    return sizeof(double) * static_cast<size_t>((NC + 1) * (NC + 1) + NC * NC) * 64;
+}
+
 // Coarse solve for n0 = NC fixed at compile time: a CTA of 64 threads takes 64
 // consecutive samples, stages their right-hand sides transposed in shared
 // memory (coalesced loads; row pitch 65 avoids bank conflicts), solves one
@@ -331,17 +437,25 @@ __global__ void kb_synth_z(FmgArgs A, int t, int B)
 template <typename T>
 __global__ void kb_faces(FmgArgs A, int t, int B)
 {
+    // one cell per thread: its west x face and north y face, plus the east
+    // boundary face in the last column and the south one in the last row
     const int n = A.lv[t].n;
-    const uint32_t per = static_cast<uint32_t>(n) * static_cast<uint32_t>((n + 1));
+    const bool pow2 = (n & (n - 1)) == 0;
+    const int lg = __ffs(n) - 1;
+    const uint32_t per = static_cast<uint32_t>(n) * static_cast<uint32_t>(n);
     GRID_STRIDE(idx, B * per)
     {
-        const int i = static_cast<int>(idx / per);
-        const int q = static_cast<int>(idx - i * per);
+        const int i = pow2 ? static_cast<int>(idx >> (2 * lg)) : static_cast<int>(idx / per);
+        const int p = static_cast<int>(idx - i * per);
+        const int i2 = pow2 ? p >> lg : p / n;
+        const int i1 = p - i2 * n;
         const T* k = at<T>(A.lv[t].k, i);
-        const int i2 = q / (n + 1);
-        at<T>(A.lv[t].kx, i)[i2 * kx_pitch(n) + q - i2 * (n + 1)] = face_x(k, n, i2, q - i2 * (n + 1));
-        const int g = q / n;
-        at<T>(A.lv[t].ky, i)[q] = face_y(k, n, g, q - g * n);
+        T* kx = at<T>(A.lv[t].kx, i) + i2 * kx_pitch(n);
+        T* ky = at<T>(A.lv[t].ky, i);
+        kx[i1] = face_x(k, n, i2, i1);
+        if (i1 == n - 1) kx[n] = face_x(k, n, i2, n);
+        ky[i2 * n + i1] = face_y(k, n, i2, i1);
+        if (i2 == n - 1) ky[n * n + i1] = face_y(k, n, n, i1);
     }
 }
 
@@ -640,23 +754,42 @@ __global__ void kb_flags(const double* norms, int* active, int B, double thresh,
     }
 }
 
-// F_t of samples 0..B-1 (one CTA per sample).
-template <typename T, bool U64>
+// Team index and count of a flat grid: one CTA or one warp per sample.
+template <typename TM>
+__device__ __forceinline__ int team_index()
+{
+    if constexpr (std::is_same<TM, WarpTeam>::value) return blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    else return blockIdx.x;
+}
+
+template <typename TM>
+__device__ __forceinline__ int team_count()
+{
+    if constexpr (std::is_same<TM, WarpTeam>::value) return gridDim.x * (blockDim.x >> 5);
+    else return gridDim.x;
+}
+
+// F_t of samples 0..B-1: one CTA per sample on large levels, one warp per
+// sample on small ones (TM), the sum in a fixed order either way.
+template <typename T, bool U64, typename TM>
 __global__ void __launch_bounds__(256) kb_qoi(FmgArgs A, int t, int B)
 {
     __shared__ double red[48];
-    const BlockTeam tm;
-    for (int i = blockIdx.x; i < B; i += gridDim.x) {
+    const TM tm;
+    for (int i = team_index<TM>(); i < B; i += team_count<TM>()) {
         double v;
         if constexpr (U64) v = qoi(tm, at<double>(A.lv[t].u64, i), A.lv[t].n, A.qoi, red);
         else v = qoi(tm, at<T>(A.lv[t].u, i), A.lv[t].n, A.qoi, red);
-        if (threadIdx.x == 0) A.F[static_cast<size_t>(i) * A.n_levels + t] = v;
+        if (tm.leader()) A.F[static_cast<size_t>(i) * A.n_levels + t] = v;
         if constexpr (U64 && sizeof(T) == 4) {
             // mixed forms: FP32 copy of the level's solution for the next FMG interpolation
-            const double* u64 = at<double>(A.lv[t].u64, i);
-            float* u = at<float>(A.lv[t].u, i);
-            const int nn = A.lv[t].n * A.lv[t].n;
-            for (int p = threadIdx.x; p < nn; p += blockDim.x) u[p] = static_cast<float>(u64[p]);
+            const double2* u64 = reinterpret_cast<const double2*>(at<double>(A.lv[t].u64, i));
+            float2* u = reinterpret_cast<float2*>(at<float>(A.lv[t].u, i));
+            const int nn2 = A.lv[t].n * A.lv[t].n / 2;
+            for (int p = tm.rank(); p < nn2; p += tm.size()) {
+                const double2 w = u64[p];
+                u[p] = make_float2(static_cast<float>(w.x), static_cast<float>(w.y));
+            }
         }
     }
 }
@@ -949,8 +1082,18 @@ mlqmc_status launch_level0(mlqmc_ctx* c, const FmgArgs& A, int B, cudaStream_t s
                    (8.0 + es) * N0 + 8.0);
     w.f64 = B * (N0 * n0 * n0 + 4.0 * N0 * n0);
     Timed tm(c, kProfSmall, st, w);
-    if (is_mixed(c->p)) kb_level0<float, true><<<grid_for(c, B, 128), 128, 0, st>>>(A, B);
-    else kb_level0<double, false><<<grid_for(c, B, 128), 128, 0, st>>>(A, B);
+    const int g64 = std::max(1, std::min((B + 63) / 64, c->sm_count * 8));
+    if (c->p.coarse_cells == 8) {
+        if (is_mixed(c->p)) kb_level0_fixed<float, true, 8><<<g64, 64, level0_smem<8>(), st>>>(A, B);
+        else kb_level0_fixed<double, false, 8><<<g64, 64, level0_smem<8>(), st>>>(A, B);
+    } else if (c->p.coarse_cells == 4) {
+        if (is_mixed(c->p)) kb_level0_fixed<float, true, 4><<<g64, 64, level0_smem<4>(), st>>>(A, B);
+        else kb_level0_fixed<double, false, 4><<<g64, 64, level0_smem<4>(), st>>>(A, B);
+    } else if (is_mixed(c->p)) {
+        kb_level0<float, true><<<grid_for(c, B, 128), 128, 0, st>>>(A, B);
+    } else {
+        kb_level0<double, false><<<grid_for(c, B, 128), 128, 0, st>>>(A, B);
+    }
     return last_error();
 }
 
@@ -1048,7 +1191,7 @@ mlqmc_status synth_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cudaStr
     const double es = sizeof(T), Mc = cells_of(c, t), Fc = faces_of(c, t);
     {
         Timed tm(c, kProfSynth, st, work_of<T>(B * es * (Mc + 2.0 * Fc), B * 6.0 * Fc));
-        kb_faces<T><<<grid_for(c, B * n * (n + 1)), 256, 0, st>>>(A, t, B);
+        kb_faces<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
     }
     if (t > 0 && smoother_of<T>(c, t) <= MLQMC_SMOOTHER_TILE) {  // 1/D: only kb_gs and kb_rbgs_tile read it
         Timed tm(c, kProfSynth, st, work_of<T>(B * es * (2.0 * Fc + Mc), B * 5.0 * Mc));
@@ -1356,8 +1499,14 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
         {
             Timed tm(c, kProfReduce, st,
                      work_of<double>(B * ((refine ? 8.0 : es) + (refine && sizeof(T) == 4 ? 4.0 : 0.0)) * Mc, B * Mc));
-            if (refine) kb_qoi<T, true><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
-            else kb_qoi<T, false><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
+            if (n * n <= 4096) {  // one warp per sample
+                const int grid = std::max(1, std::min((B + 7) / 8, c->sm_count * 16));
+                if (refine) kb_qoi<T, true, WarpTeam><<<grid, 256, 0, st>>>(A, t, B);
+                else kb_qoi<T, false, WarpTeam><<<grid, 256, 0, st>>>(A, t, B);
+            } else {
+                if (refine) kb_qoi<T, true, BlockTeam><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
+                else kb_qoi<T, false, BlockTeam><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
+            }
         }
         if (d_usol) {
             Timed tm(c, kProfReduce, st, work_of<double>((8.0 + (refine ? 8.0 : es)) * Mc, 0.0));
@@ -1668,7 +1817,11 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
     }
 
     // shared memory of the tiled smoother
-    if (!(tile_attrs<32>() && tile_attrs<16>() && tile_attrs<8>() && mlqmc_stream::prepare())) {
+    if (!(tile_attrs<32>() && tile_attrs<16>() && tile_attrs<8>() && mlqmc_stream::prepare() &&
+          ok(cudaFuncSetAttribute(kb_level0_fixed<float, true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(level0_smem<8>()))) &&
+          ok(cudaFuncSetAttribute(kb_level0_fixed<double, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(level0_smem<8>()))))) {
         free_ctx(c);
         return MLQMC_ERR_CUDA;
     }
