@@ -59,7 +59,8 @@ typedef enum {
     MLQMC_SMOOTHER_GS = 0,     /* one launch per colour (FP64 form) */
     MLQMC_SMOOTHER_TILE = 1,   /* shared-memory tiles staged by plain loads, two sweeps per launch */
     MLQMC_SMOOTHER_STREAM = 2, /* row wavefront with bulk-copy rings, residual/correction fused (n <= 256) */
-    MLQMC_SMOOTHER_TMA = 3     /* 32 x 32 tiles staged by TMA tensor copies, double-buffered (n >= 64) */
+    MLQMC_SMOOTHER_TMA = 3,    /* 32 x 32 tiles staged by TMA tensor copies, double-buffered (n >= 64) */
+    MLQMC_SMOOTHER_WHOLE = 4   /* the whole grid of a sample in shared memory, residual/correction fused (n <= 64) */
 } mlqmc_smoother;
 typedef enum { MLQMC_SAMPLER_MC = 0, MLQMC_SAMPLER_LATTICE = 1 } mlqmc_sampler;
 
@@ -309,7 +310,7 @@ int64_t mlqmc_launch_count(const mlqmc_ctx* c);
  * residual, correction and post-smoothing) of each on min(max_samples, 1024)
  * samples of scratch data and keeps the fastest.
  * mlqmc_smoother_info: kind (host, n_levels int32, MLQMC_SMOOTHER_*; level 0
- * has no sweeps and reports 0) and tuned_ms (host, n_levels x 4 doubles,
+ * has no sweeps and reports 0) and tuned_ms (host, n_levels x 5 doubles,
  * [level][kind] milliseconds of the tuning visit, 0 where not timed); either
  * may be NULL. FP64 form: every level MLQMC_SMOOTHER_GS.
  * mlqmc_set_smoother: force `kind` on `level` (1 <= level < n_levels) for

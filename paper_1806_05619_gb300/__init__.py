@@ -310,19 +310,20 @@ class Context:
         _check(lib().mlqmc_last_iterations(self.h, out), "mlqmc_last_iterations")
         return list(out)
 
-    SMOOTHERS = ["gs", "tile", "stream", "tma"]
+    SMOOTHERS = ["gs", "tile", "stream", "tma", "whole"]
 
     def smoother_info(self):
         """Per level (smoother name, {name: tuned ms}); level 0 has no sweeps."""
         kind = (C.c_int32 * self.n_levels)()
-        ms = np.zeros(self.n_levels * 4)
+        nk = len(self.SMOOTHERS)
+        ms = np.zeros(self.n_levels * nk)
         _check(lib().mlqmc_smoother_info(self.h, kind, ms.ctypes.data_as(C.POINTER(C.c_double))), "mlqmc_smoother_info")
-        ms = ms.reshape(self.n_levels, 4)
-        return [(self.SMOOTHERS[kind[t]], {self.SMOOTHERS[k]: float(ms[t, k]) for k in range(4) if ms[t, k] > 0})
+        ms = ms.reshape(self.n_levels, nk)
+        return [(self.SMOOTHERS[kind[t]], {self.SMOOTHERS[k]: float(ms[t, k]) for k in range(nk) if ms[t, k] > 0})
                 for t in range(self.n_levels)]
 
     def set_smoother(self, level: int, name: str):
-        """Force smoother `name` ("tile", "stream" or "tma") on `level` for later calls."""
+        """Force smoother `name` ("tile", "stream", "tma" or "whole") on `level` for later calls."""
         _check(lib().mlqmc_set_smoother(self.h, int(level), self.SMOOTHERS.index(name)), "mlqmc_set_smoother")
 
     def set_graphs(self, enable: bool):

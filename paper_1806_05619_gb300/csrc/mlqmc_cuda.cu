@@ -27,6 +27,7 @@
 #include "mlqmc_internal.h"
 #include "rbgs_stream.h"
 #include "rbgs_tma.h"
+#include "rbgs_whole.h"
 
 using namespace mlqmc_dev;
 
@@ -1143,6 +1144,7 @@ bool smoother_fits(const mlqmc_ctx* c, int k, int t)
     switch (k) {
     case MLQMC_SMOOTHER_STREAM: return mlqmc_stream::supported(n);
     case MLQMC_SMOOTHER_TMA: return mlqmc_tma::supported(n);
+    case MLQMC_SMOOTHER_WHOLE: return mlqmc_whole::supported(n);
     case MLQMC_SMOOTHER_TILE: return n == 8 || n == 16 || (n >= 32 && n % 32 == 0);
     default: return true;
     }
@@ -1359,11 +1361,27 @@ mlqmc_status smooth_tma(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int
     return MLQMC_OK;
 }
 
+// nsweeps sweeps of level t by the whole-sample smoother in one launch, u in
+// place; pre: also the restricted residual; post: P e added first.
+mlqmc_status smooth_whole(mlqmc_ctx* c, const FmgArgs& A, int t, int B, int nsweeps, int first, int ones, bool pre,
+                          bool post, cudaStream_t st)
+{
+    const int n = c->p.coarse_cells << t;
+    const double Mc = cells_of(c, t), Fc = faces_of(c, t);
+    Work w;
+    w.bytes = 4.0 * B * ((ones ? 2.0 : 3.0) * Mc + 2.0 * Fc + (post ? 0.25 * Mc : 0.0) + (pre ? 0.25 * Mc : 0.0));
+    w.f32 = B * (10.0 * nsweeps * Mc + (post ? 8.0 * Mc : 0.0) + (pre ? 11.0 * Mc : 0.0));
+    Timed tm(c, kProfSmooth, st, w);
+    return mlqmc_whole::launch(A, t, n, B, nsweeps, ones, first, pre, post, st) ? MLQMC_OK : MLQMC_ERR_CUDA;
+}
+
 // Pre-smoothing of level t and the restricted residual into bc of level t-1.
 template <typename T>
 mlqmc_status presmooth_restrict(mlqmc_ctx* c, FmgArgs& A, int t, int B, int top_ones, cudaStream_t st)
 {
     const int sk = smoother_of<T>(c, t);
+    if (sk == MLQMC_SMOOTHER_WHOLE && c->p.nu1 > 0)  // residual and restriction in the same pass
+        return smooth_whole(c, A, t, B, c->p.nu1, 0, top_ones, true, false, st);
     if (sk == MLQMC_SMOOTHER_STREAM && c->p.nu1 > 0)  // residual and restriction fused into the last pass
         return smooth_stream(c, A, t, B, c->p.nu1, 0, top_ones, true, false, st);
     if (sk == MLQMC_SMOOTHER_TMA && c->p.nu1 > 0) {
@@ -1383,6 +1401,8 @@ template <typename T>
 mlqmc_status correct_postsmooth(mlqmc_ctx* c, FmgArgs& A, int t, int B, int top_ones, cudaStream_t st)
 {
     const int sk = smoother_of<T>(c, t);
+    if (sk == MLQMC_SMOOTHER_WHOLE && c->p.nu2 > 0)  // the correction in the same pass
+        return smooth_whole(c, A, t, B, c->p.nu2, 1, top_ones, false, true, st);
     if (sk == MLQMC_SMOOTHER_STREAM && c->p.nu2 > 0)  // the correction fused into the first pass
         return smooth_stream(c, A, t, B, c->p.nu2, 1, top_ones, false, true, st);
     if (sk == MLQMC_SMOOTHER_TMA && c->p.nu2 > 0) return smooth_tma(c, A, t, B, c->p.nu2, 1, top_ones, true, st);
@@ -1524,6 +1544,7 @@ void default_smoothers(mlqmc_ctx* c)
 {
     for (int t = 0; t < c->p.n_levels; ++t) {
         if (t == 0 || !is_mixed(c->p)) c->smoother[t] = MLQMC_SMOOTHER_GS;
+        else if (smoother_fits(c, MLQMC_SMOOTHER_WHOLE, t)) c->smoother[t] = MLQMC_SMOOTHER_WHOLE;
         else if (smoother_fits(c, MLQMC_SMOOTHER_STREAM, t)) c->smoother[t] = MLQMC_SMOOTHER_STREAM;
         else if (smoother_fits(c, MLQMC_SMOOTHER_TMA, t)) c->smoother[t] = MLQMC_SMOOTHER_TMA;
         else c->smoother[t] = MLQMC_SMOOTHER_TILE;
@@ -1546,9 +1567,12 @@ mlqmc_status tune_smoothers(mlqmc_ctx* c, int64_t max_samples)
         !ok(cudaEventCreate(&e1)))
         return MLQMC_ERR_CUDA;
     mlqmc_status res = MLQMC_OK;
-    const int cands[2] = {MLQMC_SMOOTHER_STREAM, MLQMC_SMOOTHER_TMA};
+    const int all[3] = {MLQMC_SMOOTHER_WHOLE, MLQMC_SMOOTHER_STREAM, MLQMC_SMOOTHER_TMA};
     for (int t = 1; t < c->p.n_levels && res == MLQMC_OK; ++t) {
-        if (!smoother_fits(c, cands[0], t) || !smoother_fits(c, cands[1], t)) continue;
+        int cands[3], nc = 0;
+        for (int k : all)
+            if (smoother_fits(c, k, t)) cands[nc++] = k;
+        if (nc < 2) continue;
         int64_t B = std::max<int64_t>(1, std::min<int64_t>(max_samples, 1024));
         const size_t per = level_bytes_per_sample(c->p, c->Ka, t) + level_bytes_per_sample(c->p, c->Ka, t - 1);
         while (B > 64 && per * static_cast<size_t>(B) > c->pool_budget / 4) B /= 2;
@@ -1561,8 +1585,8 @@ mlqmc_status tune_smoothers(mlqmc_ctx* c, int64_t max_samples)
             const size_t bytes = level_bytes_per_sample(c->p, c->Ka, u) * static_cast<size_t>(P.cap);
             if (!ok(cudaMemsetAsync(P.mem, 0, bytes, st))) res = MLQMC_ERR_CUDA;
         }
-        double best = 0.0;
-        for (int k = 0; k < 2 && res == MLQMC_OK; ++k) {
+        int best = cands[0];
+        for (int k = 0; k < nc && res == MLQMC_OK; ++k) {
             c->smoother[t] = cands[k];
             FmgArgs A = base_args(c);
             float ms = 0.0f, tot = 0.0f;
@@ -1576,9 +1600,9 @@ mlqmc_status tune_smoothers(mlqmc_ctx* c, int64_t max_samples)
                 if (rep > 0) tot += ms;
             }
             c->tune_ms[t][cands[k]] = tot / 3.0;
-            if (k == 0 || tot / 3.0 < best) best = tot / 3.0;
+            if (c->tune_ms[t][cands[k]] < c->tune_ms[t][best]) best = cands[k];
         }
-        c->smoother[t] = c->tune_ms[t][cands[1]] < c->tune_ms[t][cands[0]] ? cands[1] : cands[0];
+        c->smoother[t] = best;
     }
     if (res == MLQMC_OK && !ok(cudaStreamSynchronize(st))) res = MLQMC_ERR_CUDA;
     if (res == MLQMC_OK && c->host_status == 0) {
@@ -1848,7 +1872,7 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     c->pool_budget = std::min<size_t>(free_b / 2, static_cast<size_t>(96) << 30);
-    if (!mlqmc_tma::prepare()) {
+    if (!mlqmc_tma::prepare() || !mlqmc_whole::prepare()) {
         free_ctx(c);
         return MLQMC_ERR_CUDA;
     }
@@ -2421,7 +2445,7 @@ extern "C" mlqmc_status mlqmc_smoother_info(const mlqmc_ctx* c, int32_t* kind, d
     if (!c) return MLQMC_ERR_INVALID_ARG;
     for (int t = 0; t < c->p.n_levels; ++t) {
         if (kind) kind[t] = t == 0 ? 0 : c->smoother[t];
-        for (int k = 0; k < 4 && tuned_ms; ++k) tuned_ms[t * 4 + k] = c->tune_ms[t][k];
+        for (int k = 0; k < 5 && tuned_ms; ++k) tuned_ms[t * 5 + k] = c->tune_ms[t][k];
     }
     return MLQMC_OK;
 }
@@ -2429,7 +2453,7 @@ extern "C" mlqmc_status mlqmc_smoother_info(const mlqmc_ctx* c, int32_t* kind, d
 extern "C" mlqmc_status mlqmc_set_smoother(mlqmc_ctx* c, int32_t level, int32_t kind)
 {
     if (!c || !is_mixed(c->p) || level < 1 || level >= c->p.n_levels || kind < MLQMC_SMOOTHER_TILE ||
-        kind > MLQMC_SMOOTHER_TMA || !smoother_fits(c, kind, level))
+        kind > MLQMC_SMOOTHER_WHOLE || !smoother_fits(c, kind, level))
         return MLQMC_ERR_INVALID_ARG;
     c->smoother[level] = kind;
     ++c->pool_epoch;  // a captured graph runs the old smoother

@@ -142,7 +142,7 @@ struct mlqmc_ctx {
     // the autotuner at creation (mixed forms) or fixed by mlqmc_set_smoother;
     // tune_ms: the tuner's time per candidate (ms, 0 when not timed)
     int smoother[MLQMC_MAX_LEVELS] = {};
-    double tune_ms[MLQMC_MAX_LEVELS][4] = {};
+    double tune_ms[MLQMC_MAX_LEVELS][5] = {};
 
     // Replay of repeated identical calls of the fixed-cycle forms as one CUDA
     // graph: the second call with the same ranked samples, outputs and pools

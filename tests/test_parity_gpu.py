@@ -393,17 +393,17 @@ def _mixed_F(ctx, cfg, work, names):
 
 
 def test_smoothers_agree_fixed_cycles():
-    """Mixed form, fixed cycles (6 levels up to 256x256): the wavefront
-    (residual and correction fused), TMA-tile and plain-tile smoothers run the
-    same red-black sweeps; per-sample F agree to FP32 rounding of the
-    residual's summation order (1e-5 relative)."""
+    """Mixed form, fixed cycles (6 levels up to 256x256): the wavefront and
+    whole-sample smoothers (residual and correction fused), TMA-tile and
+    plain-tile smoothers run the same red-black sweeps; per-sample F agree to
+    FP32 rounding of the residual's summation order (1e-5 relative)."""
     cfg = W.scaled(W.CONFIG2, R=2, precision="mixed_tf32")
     z = _genvec(cfg)
     ctx = M.Context.from_config(cfg, genvec=z)
     work = [(5, 0, 3, 0, 2), (4, 1, 4, 0, 2), (3, 0, 5, 1, 2), (1, 2, 6, 0, 1)]
-    F = _mixed_F(ctx, cfg, work, ["stream", "tma", "tile"])
+    F = _mixed_F(ctx, cfg, work, ["stream", "tma", "tile", "whole"])
     mask = F["tile"] != 0
-    for name in ["stream", "tma"]:
+    for name in ["stream", "tma", "whole"]:
         assert np.array_equal(F[name] != 0, mask)
         assert _rel(F[name][mask], F["tile"][mask]) <= 1e-5, name
 
@@ -416,9 +416,10 @@ def test_smoothers_agree_converged():
     z = _genvec(cfg)
     ctx = M.Context.from_config(cfg, genvec=z)
     work = [(4, 0, 6, 0, 2), (3, 0, 3, 0, 1)]
-    F = _mixed_F(ctx, cfg, work, ["stream", "tma"])
+    F = _mixed_F(ctx, cfg, work, ["stream", "tma", "whole"])
     mask = F["stream"] != 0
     assert _rel(F["tma"][mask], F["stream"][mask]) <= 1e-8
+    assert _rel(F["whole"][mask], F["stream"][mask]) <= 1e-8
 
 
 def test_autotuner_report():
@@ -428,7 +429,7 @@ def test_autotuner_report():
     assert info[0][0] == "gs"
     for t, (name, ms) in enumerate(info[1:], start=1):
         n = cfg["n0"] << t
-        assert name in ("stream", "tma", "tile")
+        assert name in ("stream", "tma", "tile", "whole")
         if len(ms) >= 2:
             assert name == min(ms, key=ms.get), (t, name, ms)
         if n > 256:
