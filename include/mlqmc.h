@@ -304,18 +304,23 @@ mlqmc_status mlqmc_last_iterations(mlqmc_ctx* c, int32_t* out);
 int64_t mlqmc_launch_count(const mlqmc_ctx* c);
 
 /*
- * Smoother per level of the FP32 V-cycles (mixed forms). mlqmc_create picks
+ * Smoother per level of the V-cycles. mlqmc_create picks
  * one per level: where more than one smoother can run a level, an autotuner
  * times one V-cycle visit of that level (pre-smoothing with the restricted
- * residual, correction and post-smoothing) of each on min(max_samples, 1024)
- * samples of scratch data and keeps the fastest.
+ * residual, correction and post-smoothing) of each on 1024 samples of
+ * scratch data and keeps the fastest (mixed forms; the choice changes results
+ * by FP32 rounding only).
  * mlqmc_smoother_info: kind (host, n_levels int32, MLQMC_SMOOTHER_*; level 0
  * has no sweeps and reports 0) and tuned_ms (host, n_levels x 5 doubles,
  * [level][kind] milliseconds of the tuning visit, 0 where not timed); either
- * may be NULL. FP64 form: every level MLQMC_SMOOTHER_GS.
+ * may be NULL. The FP64 form takes a fixed rule, so that every context gives
+ * the same bits: MLQMC_SMOOTHER_WHOLE for n <= 32, MLQMC_SMOOTHER_GS above
+ * (both multiply by the stored FP64 1/D and agree to rounding); the others
+ * are FP32 only.
  * mlqmc_set_smoother: force `kind` on `level` (1 <= level < n_levels) for
  * later calls; MLQMC_ERR_INVALID_ARG if that smoother cannot run the level
- * (kind GS, or a side it does not handle) or the form is FP64.
+ * in the context's form (GS in a mixed form, an FP32-only smoother in the
+ * FP64 form, or a side it does not handle).
  */
 mlqmc_status mlqmc_smoother_info(const mlqmc_ctx* c, int32_t* kind, double* tuned_ms);
 mlqmc_status mlqmc_set_smoother(mlqmc_ctx* c, int32_t level, int32_t kind);

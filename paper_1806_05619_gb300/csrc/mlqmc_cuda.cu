@@ -1127,7 +1127,7 @@ mlqmc_status launch_points(mlqmc_ctx* c, const SampleDesc* d_s, int count, doubl
 template <typename T>
 int smoother_of(const mlqmc_ctx* c, int t)
 {
-    return sizeof(T) == 8 ? MLQMC_SMOOTHER_GS : c->smoother[t];
+    return c->smoother[t];
 }
 
 // True when level t's FP32 sweeps run on the wavefront smoother (rbgs_stream.cu).
@@ -1137,14 +1137,16 @@ bool streams(const mlqmc_ctx* c, int t)
     return smoother_of<T>(c, t) == MLQMC_SMOOTHER_STREAM;
 }
 
-// Whether smoother kind k can run level t (FP32 arrays).
+// Whether smoother kind k can run level t in the context's form (FP64: kb_gs
+// and the whole-sample smoother; the tiled and wavefront ones are FP32 only).
 bool smoother_fits(const mlqmc_ctx* c, int k, int t)
 {
     const int n = c->p.coarse_cells << t;
+    if (!is_mixed(c->p) && k != MLQMC_SMOOTHER_GS && k != MLQMC_SMOOTHER_WHOLE) return false;
     switch (k) {
     case MLQMC_SMOOTHER_STREAM: return mlqmc_stream::supported(n);
     case MLQMC_SMOOTHER_TMA: return mlqmc_tma::supported(n);
-    case MLQMC_SMOOTHER_WHOLE: return mlqmc_whole::supported(n);
+    case MLQMC_SMOOTHER_WHOLE: return mlqmc_whole::supported(n, !is_mixed(c->p));
     case MLQMC_SMOOTHER_TILE: return n == 8 || n == 16 || (n >= 32 && n % 32 == 0);
     default: return true;
     }
@@ -1195,7 +1197,7 @@ mlqmc_status synth_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cudaStr
         Timed tm(c, kProfSynth, st, work_of<T>(B * es * (Mc + 2.0 * Fc), B * 6.0 * Fc));
         kb_faces<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
     }
-    if (t > 0 && smoother_of<T>(c, t) <= MLQMC_SMOOTHER_TILE) {  // 1/D: only kb_gs and kb_rbgs_tile read it
+    if (t > 0 && (sizeof(T) == 8 || smoother_of<T>(c, t) <= MLQMC_SMOOTHER_TILE)) {  // 1/D: FP64 sweeps, tiles
         Timed tm(c, kProfSynth, st, work_of<T>(B * es * (2.0 * Fc + Mc), B * 5.0 * Mc));
         kb_idiag<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
     }
@@ -1367,12 +1369,16 @@ mlqmc_status smooth_whole(mlqmc_ctx* c, const FmgArgs& A, int t, int B, int nswe
                           bool post, cudaStream_t st)
 {
     const int n = c->p.coarse_cells << t;
-    const double Mc = cells_of(c, t), Fc = faces_of(c, t);
+    const bool f64 = !is_mixed(c->p);
+    const double Mc = cells_of(c, t), Fc = faces_of(c, t), es = f64 ? 8.0 : 4.0;
     Work w;
-    w.bytes = 4.0 * B * ((ones ? 2.0 : 3.0) * Mc + 2.0 * Fc + (post ? 0.25 * Mc : 0.0) + (pre ? 0.25 * Mc : 0.0));
-    w.f32 = B * (10.0 * nsweeps * Mc + (post ? 8.0 * Mc : 0.0) + (pre ? 11.0 * Mc : 0.0));
+    w.bytes = es * B * ((ones ? 2.0 : 3.0) * Mc + (f64 ? Mc : 0.0) + 2.0 * Fc + (post ? 0.25 * Mc : 0.0) +
+                        (pre ? 0.25 * Mc : 0.0));
+    const double fl = B * (10.0 * nsweeps * Mc + (post ? 8.0 * Mc : 0.0) + (pre ? 11.0 * Mc : 0.0));
+    if (f64) w.f64 = fl;
+    else w.f32 = fl;
     Timed tm(c, kProfSmooth, st, w);
-    return mlqmc_whole::launch(A, t, n, B, nsweeps, ones, first, pre, post, st) ? MLQMC_OK : MLQMC_ERR_CUDA;
+    return mlqmc_whole::launch(A, t, n, B, nsweeps, ones, first, pre, post, f64, st) ? MLQMC_OK : MLQMC_ERR_CUDA;
 }
 
 // Pre-smoothing of level t and the restricted residual into bc of level t-1.
@@ -1543,7 +1549,9 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
 void default_smoothers(mlqmc_ctx* c)
 {
     for (int t = 0; t < c->p.n_levels; ++t) {
-        if (t == 0 || !is_mixed(c->p)) c->smoother[t] = MLQMC_SMOOTHER_GS;
+        if (t == 0) c->smoother[t] = MLQMC_SMOOTHER_GS;
+        else if (!is_mixed(c->p))  // FP64 form: a fixed rule, so every context gives the same bits
+            c->smoother[t] = smoother_fits(c, MLQMC_SMOOTHER_WHOLE, t) ? MLQMC_SMOOTHER_WHOLE : MLQMC_SMOOTHER_GS;
         else if (smoother_fits(c, MLQMC_SMOOTHER_WHOLE, t)) c->smoother[t] = MLQMC_SMOOTHER_WHOLE;
         else if (smoother_fits(c, MLQMC_SMOOTHER_STREAM, t)) c->smoother[t] = MLQMC_SMOOTHER_STREAM;
         else if (smoother_fits(c, MLQMC_SMOOTHER_TMA, t)) c->smoother[t] = MLQMC_SMOOTHER_TMA;
@@ -1553,13 +1561,15 @@ void default_smoothers(mlqmc_ctx* c)
 
 // Autotuner (mixed forms): for every level that more than one smoother can
 // run, time one V-cycle visit of the level (pre-smoothing and the restricted
-// residual, correction and post-smoothing) of each candidate on B samples of
-// zeroed scratch pools (the timing does not depend on the values) and keep
-// the fastest. Runs once, at creation, on its own stream.
-mlqmc_status tune_smoothers(mlqmc_ctx* c, int64_t max_samples)
+// residual, correction and post-smoothing) of each candidate on 1024 samples
+// of zeroed scratch pools (the timing does not depend on the values) and keep
+// the fastest. Runs once, at creation, on its own stream. The FP64 form takes
+// a fixed rule instead (default_smoothers).
+mlqmc_status tune_smoothers(mlqmc_ctx* c)
 {
     default_smoothers(c);
-    if (!is_mixed(c->p)) return MLQMC_OK;
+    const bool f64 = !is_mixed(c->p);
+    if (f64) return MLQMC_OK;
     const int64_t launches0 = c->launches;
     cudaStream_t st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1567,13 +1577,13 @@ mlqmc_status tune_smoothers(mlqmc_ctx* c, int64_t max_samples)
         !ok(cudaEventCreate(&e1)))
         return MLQMC_ERR_CUDA;
     mlqmc_status res = MLQMC_OK;
-    const int all[3] = {MLQMC_SMOOTHER_WHOLE, MLQMC_SMOOTHER_STREAM, MLQMC_SMOOTHER_TMA};
+    const int all[4] = {MLQMC_SMOOTHER_GS, MLQMC_SMOOTHER_WHOLE, MLQMC_SMOOTHER_STREAM, MLQMC_SMOOTHER_TMA};
     for (int t = 1; t < c->p.n_levels && res == MLQMC_OK; ++t) {
-        int cands[3], nc = 0;
+        int cands[4], nc = 0;
         for (int k : all)
-            if (smoother_fits(c, k, t)) cands[nc++] = k;
+            if ((f64 || k != MLQMC_SMOOTHER_GS) && smoother_fits(c, k, t)) cands[nc++] = k;
         if (nc < 2) continue;
-        int64_t B = std::max<int64_t>(1, std::min<int64_t>(max_samples, 1024));
+        int64_t B = 1024;  // the same for every context, whatever its max_samples
         const size_t per = level_bytes_per_sample(c->p, c->Ka, t) + level_bytes_per_sample(c->p, c->Ka, t - 1);
         while (B > 64 && per * static_cast<size_t>(B) > c->pool_budget / 4) B /= 2;
         if (ensure_pool(c, t - 1, B) != MLQMC_OK || ensure_pool(c, t, B) != MLQMC_OK) {
@@ -1592,8 +1602,12 @@ mlqmc_status tune_smoothers(mlqmc_ctx* c, int64_t max_samples)
             float ms = 0.0f, tot = 0.0f;
             for (int rep = 0; rep < 4 && res == MLQMC_OK; ++rep) {  // one untimed visit, then three timed
                 if (!ok(cudaEventRecord(e0, st))) res = MLQMC_ERR_CUDA;
-                if (res == MLQMC_OK) res = presmooth_restrict<float>(c, A, t, static_cast<int>(B), 0, st);
-                if (res == MLQMC_OK) res = correct_postsmooth<float>(c, A, t, static_cast<int>(B), 0, st);
+                if (res == MLQMC_OK)
+                    res = f64 ? presmooth_restrict<double>(c, A, t, static_cast<int>(B), 0, st)
+                              : presmooth_restrict<float>(c, A, t, static_cast<int>(B), 0, st);
+                if (res == MLQMC_OK)
+                    res = f64 ? correct_postsmooth<double>(c, A, t, static_cast<int>(B), 0, st)
+                              : correct_postsmooth<float>(c, A, t, static_cast<int>(B), 0, st);
                 if (res == MLQMC_OK && (!ok(cudaEventRecord(e1, st)) || !ok(cudaEventSynchronize(e1)) ||
                                         !ok(cudaEventElapsedTime(&ms, e0, e1))))
                     res = MLQMC_ERR_CUDA;
@@ -1876,7 +1890,7 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
         free_ctx(c);
         return MLQMC_ERR_CUDA;
     }
-    st = tune_smoothers(c, max_samples_per_call > 0 ? max_samples_per_call : 1024);
+    st = tune_smoothers(c);
     if (st != MLQMC_OK) {
         free_ctx(c);
         return st;
@@ -2452,8 +2466,8 @@ extern "C" mlqmc_status mlqmc_smoother_info(const mlqmc_ctx* c, int32_t* kind, d
 
 extern "C" mlqmc_status mlqmc_set_smoother(mlqmc_ctx* c, int32_t level, int32_t kind)
 {
-    if (!c || !is_mixed(c->p) || level < 1 || level >= c->p.n_levels || kind < MLQMC_SMOOTHER_TILE ||
-        kind > MLQMC_SMOOTHER_WHOLE || !smoother_fits(c, kind, level))
+    if (!c || level < 1 || level >= c->p.n_levels || kind < MLQMC_SMOOTHER_GS || kind > MLQMC_SMOOTHER_WHOLE ||
+        (kind == MLQMC_SMOOTHER_GS && is_mixed(c->p)) || !smoother_fits(c, kind, level))
         return MLQMC_ERR_INVALID_ARG;
     c->smoother[level] = kind;
     ++c->pool_epoch;  // a captured graph runs the old smoother

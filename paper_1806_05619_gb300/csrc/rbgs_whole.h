@@ -7,18 +7,18 @@
 
 namespace mlqmc_whole {
 
-// Level sides whose whole grid one team stages in shared memory (FP32 arrays).
-bool supported(int n);
+// Level sides whose whole grid one team stages in shared memory (FP32: n <= 64; FP64: n <= 32).
+bool supported(int n, bool fp64);
 
 // Raise the dynamic shared-memory limit of every instance; once per process.
 bool prepare();
 
 // ns red-black sweeps of level t (n cells per side) for samples 0..B-1 of A,
-// u updated in place. first: colour of the first half sweep (0 red:
+// u updated in place; fp64: the FP64 form's arrays (the stored 1/D is used). first: colour of the first half sweep (0 red:
 // (i1 + i2) even). ones: right-hand side 1, else bc of level t. post: add
 // the coarse-grid correction P u_{t-1} to u before the sweeps. pre:
 // afterwards write bc of level t-1 = mean over the 4 children of b - A u.
 bool launch(const mlqmc_dev::FmgArgs& A, int t, int n, int B, int ns, int ones, int first, bool pre, bool post,
-            cudaStream_t st);
+            bool fp64, cudaStream_t st);
 
 }  // namespace mlqmc_whole
