@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-tte", action="store_true", help="skip the time-to-epsilon runs of Algorithm 1")
     ap.add_argument("--smoother", default="auto", choices=["auto", "stream", "tma", "tile"],
                     help="mixed form: force this smoother on every level it handles (default: the autotuner's pick)")
+    ap.add_argument("--smoother-plan", default="",
+                    help="mixed form: pin smoothers per level, e.g. 1:whole,2:whole,4:tma (profiler runs, where "
+                         "the autotuner's timings are not representative)")
     ap.add_argument("--no-graphs", action="store_true", help="launch kernel by kernel instead of replaying a CUDA graph")
     ap.add_argument("--counts-div", type=int, default=1,
                     help="divide the per-level counts (small cases for profiler captures only)")
@@ -98,7 +101,8 @@ KIND_KERNELS = {
     "points": "k_points (lattice points and normals)",
     "level0": "kb_level0 (banded Cholesky and exact level-0 solve, one thread per sample)",
     "synth": "kb_synth_G/kb_synth_z (separable KL), kb_faces, kb_idiag",
-    "smooth": "red-black sweeps (kb_rbgs_tile in FP32: two sweeps per launch; kb_gs in FP64: one colour)",
+    "smooth": "red-black sweeps (kb_rbgs_whole up to 64x64 with residual/correction fused, kb_rbgs_tma tiles "
+              "above; FP64 form: kb_rbgs_whole up to 32x32, kb_gs above)",
     "transfer": "kb_resid_restrict, kb_prolong, kb_resid64, kb_update64",
     "coarse": "kb_coarse_fixed (V-cycle level-0 solves)",
     "reduce": "kb_qoi, kb_resnorm, k_sums, outputs",
@@ -294,15 +298,19 @@ def profiled_pass(ctx, step, args, stream, flush):
     return prof, work, sum(ms) / len(ms)
 
 
-def force_smoother(ctx, name):
-    if name == "auto" or ctx.precision == "fp64":
+def force_smoother(ctx, name, plan=""):
+    if ctx.precision == "fp64":
         return
     import paper_1806_05619_gb300 as M
-    for t in range(1, ctx.n_levels):
-        try:
-            ctx.set_smoother(t, name)
-        except M.MlqmcError:
-            pass
+    if name != "auto":
+        for t in range(1, ctx.n_levels):
+            try:
+                ctx.set_smoother(t, name)
+            except M.MlqmcError:
+                pass
+    for item in filter(None, plan.split(",")):
+        lv, kind = item.split(":")
+        ctx.set_smoother(int(lv), kind)
 
 
 def run_ours(args):
@@ -329,7 +337,7 @@ def run_ours(args):
     ns = n_samples(work)
     genvec, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
     ctx = M.Context.from_config(cfg, genvec=genvec, max_samples=ns)
-    force_smoother(ctx, args.smoother)
+    force_smoother(ctx, args.smoother, args.smoother_plan)
     ctx.set_graphs(not args.no_graphs)
     nl, R = cfg["n_levels"], cfg["R"]
     sums = torch.zeros(nl * R * 2, dtype=torch.float64, device=dev)
@@ -464,7 +472,7 @@ def run_mixed_same_workload(args, cfg64, work, genvec, dev, stream, flush, M):
     cfg["precision"] = "mixed_tf32"
     ns = n_samples(work)
     ctx = M.Context.from_config(cfg, genvec=genvec, max_samples=ns)
-    force_smoother(ctx, args.smoother)
+    force_smoother(ctx, args.smoother, args.smoother_plan)
     ctx.set_graphs(not args.no_graphs)
     nl, R = cfg["n_levels"], cfg["R"]
     sums = torch.zeros(nl * R * 2, dtype=torch.float64, device=dev)
@@ -556,18 +564,25 @@ def run_time_to_eps(M):
     cfg = dict(W.CONFIG4)
     cfg["log2_nmax"] = 12
     genvec, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
-    out = {"workload": "Algorithm 1 on 7 levels 8x8..512x512, s=200, lambda=0.3, R=16, rtol 1e-10"}
-    for prec in ["mixed_tf32", "fp64"]:
+    out = {"workload": "Algorithm 1 on 7 levels 8x8..512x512, s=200, lambda=0.3, R=16, rtol 1e-10",
+           "variants": "mixed_tf32 / fp64: reuse (MG-MLQMC), one level per round; mixed_tf32_no_reuse: plain "
+                       "MLQMC (each difference from its own samples); mixed_tf32_batched: every level with "
+                       "V_l/C_l >= max/2 doubles in one round"}
+    variants = [("mixed_tf32", "mixed_tf32", True, False), ("fp64", "fp64", True, False),
+                ("mixed_tf32_no_reuse", "mixed_tf32", False, False), ("mixed_tf32_batched", "mixed_tf32", True, True)]
+    for name, prec, reuse, batched in variants:
         c = dict(cfg)
         c["precision"] = prec
+        c["reuse"] = reuse
         ctx = M.Context.from_config(c, genvec=genvec, max_samples=1 << 17)
         rows = []
         for eps in cfg["eps"] + [3e-4, 1e-4]:
-            r = ctx.estimate(eps)
+            r = ctx.estimate(eps, batched=batched)
             rows.append({"eps": eps, "seconds": r["wall_seconds"], "gpu_seconds": r["gpu_seconds"], "Q": r["Q"],
                          "rmse_bound": float(np.sqrt(r["varQ"] + r["bias"] ** 2)), "L": r["L"],
-                         "rounds": r["rounds"], "N": r["N"][:r["L"] + 1], "run_status": r["run_status"]})
-        out[prec] = rows
+                         "rounds": r["rounds"], "N": r["N"][:r["L"] + 1], "run_status": r["run_status"],
+                         "alpha": r["alpha"], "Ybar": r["Ybar"][:r["L"] + 1], "Vell": r["Vell"][:r["L"] + 1]})
+        out[name] = rows
         del ctx
     return out
 

@@ -130,8 +130,20 @@ __global__ void __launch_bounds__(WGeom<T, N>::TS * WGeom<T, N>::SPC)
     for (int ph = 0; ph < 2 * ns; ++ph) {
         const int colour = (first + ph) & 1;
         for (int q = ts; q < N * NC; q += TS) {
-            const int y = q / NC;
-            const int x = 2 * (q - y * NC) + ((y + colour) & 1);
+            // n <= 32: cells row-major; n = 64: each warp slot covers 16 cells
+            // of two neighbouring rows (lanes 0-15 and 16-31), whose opposite
+            // colour parities put the 32 accesses in 32 distinct banks
+            int y, m;
+            if constexpr (NC >= 32) {
+                constexpr int SEG = NC / 16;  // 16-cell segments per row
+                const int unit = q >> 5, lane = q & 31;
+                y = 2 * (unit / SEG) + (lane >> 4);
+                m = 16 * (unit - (unit / SEG) * SEG) + (lane & 15);
+            } else {
+                y = q / NC;
+                m = q - y * NC;
+            }
+            const int x = 2 * m + ((y + colour) & 1);
             const int c0 = y * N + x;
             const T* kr = skx + y * XP;
             const T w = kr[x], e = kr[x + 1];
