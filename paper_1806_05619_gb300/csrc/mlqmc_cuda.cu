@@ -1646,11 +1646,17 @@ mlqmc_status run_chunk(mlqmc_ctx* c, int count, const int* Bt, int Lmax, double*
     if (s != MLQMC_OK) return s;
     s = build_c(c, count, st);
     if (s != MLQMC_OK) return s;
-    for (int t = 0; t <= Lmax && Bt[t] > 0; ++t) {
+    // level 0 (field, faces, factorisation and exact solve: latency-bound,
+    // one thread per sample) on the side stream while the main stream
+    // synthesises levels 1..Lmax; joined before the FMG stages
+    if (!ok(cudaEventRecord(c->ev_fork, st)) || !ok(cudaStreamWaitEvent(c->side, c->ev_fork, 0)))
+        return MLQMC_ERR_CUDA;
+    s = is_mixed(p) ? synth_batched<float>(c, A, 0, Bt[0], c->side) : synth_batched<double>(c, A, 0, Bt[0], c->side);
+    if (s == MLQMC_OK) s = launch_level0(c, A, Bt[0], c->side);
+    if (!ok(cudaEventRecord(c->ev_join, c->side))) s = MLQMC_ERR_CUDA;
+    for (int t = 1; s == MLQMC_OK && t <= Lmax && Bt[t] > 0; ++t)
         s = is_mixed(p) ? synth_batched<float>(c, A, t, Bt[t], st) : synth_batched<double>(c, A, t, Bt[t], st);
-        if (s != MLQMC_OK) return s;
-    }
-    s = launch_level0(c, A, Bt[0], st);
+    if (!ok(cudaStreamWaitEvent(st, c->ev_join, 0)) && s == MLQMC_OK) s = MLQMC_ERR_CUDA;
     if (s != MLQMC_OK) return s;
     if (d_usol) {
         const int64_t n0 = p.coarse_cells;
@@ -1714,6 +1720,9 @@ void free_ctx(mlqmc_ctx* c)
     cudaFree(c->d_queue);
     for (auto& P : c->pools) cudaFree(P.mem);
     if (c->staged) cudaEventDestroy(c->staged);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) cudaStreamDestroy(c->side);
     for (auto& m : c->marks) {
         cudaEventDestroy(m.a);
         cudaEventDestroy(m.b);
@@ -1848,7 +1857,10 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
            ok(cudaMallocHost(&c->h_samples, ms * sizeof(SampleDesc))) &&
            ok(cudaMallocHost(&c->h_count, sizeof(int))) && ok(cudaMalloc(&c->d_status, sizeof(int))) &&
            ok(cudaMalloc(&c->d_queue, sizeof(int))) && ok(cudaMemset(c->d_status, 0, sizeof(int))) &&
-           ok(cudaEventCreateWithFlags(&c->staged, cudaEventDisableTiming));
+           ok(cudaEventCreateWithFlags(&c->staged, cudaEventDisableTiming)) &&
+           ok(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) &&
+           ok(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) &&
+           ok(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     if (!good) {
         free_ctx(c);
         return MLQMC_ERR_OOM;

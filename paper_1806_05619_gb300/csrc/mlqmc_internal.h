@@ -115,6 +115,10 @@ struct mlqmc_ctx {
     SampleDesc* h_samples = nullptr;  // pinned staging
     int* h_count = nullptr;           // pinned
     cudaEvent_t staged = nullptr;     // recorded after the last copy out of the staging buffer
+    // level 0 (its field, faces and banded factorisation) runs on a second
+    // stream beside the other levels' fields: fork and join by events
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     size_t chol_stride = 0;
 
     // level pools, grown on demand; chunks are cut to fit pool_budget bytes
