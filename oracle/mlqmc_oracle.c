@@ -378,42 +378,44 @@ int or_normals(const or_ctx* c, int level, int r, uint64_t n, double* y)
 /* ((i1+1/2)h, (i2+1/2)h) of that level's own grid (reading A3).             */
 /* Layout: k[i2*n + i1], i1 along x1.                                        */
 /* ------------------------------------------------------------------------- */
-void or_field(const or_ctx* c, int n, const double* y, double* k)
+/* Z(x) = sum_m sqrt(theta_m) y_m psi_{a_m}(x1) psi_{b_m}(x2) at the cell      */
+/* centres of an n x n grid (eq. truncatedKL with the separable modes). Each  */
+/* 1D factor psi_a((i + 1/2)/n) is evaluated once per coordinate and looked   */
+/* up; the terms are the same products, added in mode order.                  */
+static int field_sum(const or_ctx* c, int n, const double* y, double* zout)
 {
     const double cc = 1.0 / c->p.corr_len;
+    double* P = malloc(sizeof(double) * (size_t)c->K1 * n);  /* P[a*n + i] = psi_a((i+1/2)/n) */
+    if (!P) return OR_ERR_OOM;
+    for (int a = 0; a < c->K1; ++a)
+        for (int i = 0; i < n; ++i) P[(size_t)a * n + i] = or_psi1d(c->w1[a], cc, c->nrm1[a], (i + 0.5) / n);
     for (int i2 = 0; i2 < n; ++i2) {
-        const double x2 = (i2 + 0.5) / n;
         for (int i1 = 0; i1 < n; ++i1) {
-            const double x1 = (i1 + 0.5) / n;
             double z = 0.0;
-            for (int m = 0; m < c->p.s; ++m) {
-                const int a = c->ma[m], b = c->mb[m];
-                const double pa = or_psi1d(c->w1[a], cc, c->nrm1[a], x1);
-                const double pb = or_psi1d(c->w1[b], cc, c->nrm1[b], x2);
-                z += y[m] * sqrt(c->mtheta[m]) * pa * pb;
-            }
-            k[i2 * n + i1] = exp(z);
+            for (int m = 0; m < c->p.s; ++m)
+                z += y[m] * sqrt(c->mtheta[m]) * P[(size_t)c->ma[m] * n + i1] * P[(size_t)c->mb[m] * n + i2];
+            zout[i2 * n + i1] = z;
         }
     }
+    free(P);
+    return OR_OK;
+}
+
+/* Lognormal field k = exp(Z) (Sec. 5); NaN everywhere when out of memory. */
+void or_field(const or_ctx* c, int n, const double* y, double* k)
+{
+    if (field_sum(c, n, y, k) != OR_OK) {
+        for (size_t p = 0; p < (size_t)n * n; ++p) k[p] = NAN;
+        return;
+    }
+    for (size_t p = 0; p < (size_t)n * n; ++p) k[p] = exp(k[p]);
 }
 
 /* Gaussian part only (same sum without the exponential). */
 void or_field_z(const or_ctx* c, int n, const double* y, double* zout)
 {
-    const double cc = 1.0 / c->p.corr_len;
-    for (int i2 = 0; i2 < n; ++i2) {
-        const double x2 = (i2 + 0.5) / n;
-        for (int i1 = 0; i1 < n; ++i1) {
-            const double x1 = (i1 + 0.5) / n;
-            double z = 0.0;
-            for (int m = 0; m < c->p.s; ++m) {
-                const int a = c->ma[m], b = c->mb[m];
-                z += y[m] * sqrt(c->mtheta[m]) * or_psi1d(c->w1[a], cc, c->nrm1[a], x1) *
-                     or_psi1d(c->w1[b], cc, c->nrm1[b], x2);
-            }
-            zout[i2 * n + i1] = z;
-        }
-    }
+    if (field_sum(c, n, y, zout) != OR_OK)
+        for (size_t p = 0; p < (size_t)n * n; ++p) zout[p] = NAN;
 }
 
 /* ------------------------------------------------------------------------- */
