@@ -1,0 +1,123 @@
+"""GPU path against the FP64 oracle at the full sizes of the larger problems.
+
+* Problem 3 (precision form): the batch of 256 samples whose FMG ends on the
+  1024 x 1024 level (8 levels, s = 400, lambda = 0.1, every level refined to a
+  relative residual of 1e-10), in one call as the benchmark runs it. Sampled
+  samples' F on every level, one whole finest field, and the reuse sums
+  against a host recomputation from the per-sample F.
+* Problem 5: samples whose FMG ends on the 2048 x 2048 level (9 levels,
+  s = 1000, lambda = 0.05, refined to 1e-10). The generating vector is built
+  for 2^10 points (the oracle's plain CBC search at 2^16 points and 1000
+  coordinates takes hours); grids, modes and refinement are the problem's own.
+
+Tolerances: both sides refine every level to the problem's relative
+residual 1e-10 (the FP64 residual of a 1024 x 1024 grid bottoms out near
+1e-11, so the oracle cannot be driven much tighter); a converged solve on
+either side is within that tolerance of the exact discrete solution, so F_t
+agree to 2 rtol times the ratio rms(u)/mean(u) of the level, plus (mixed forms) the rounding bound of
+the field, exp(eta) - 1 with eta the bound on |z_mixed - z_64| (same bound as
+the smaller parity tests), plus 1e-12 for the FP64 arithmetic.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from test_parity_gpu import EXP_SLACK, _bf16x3_u, _field_bound, _rel, _tf32_u
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+M = pytest.importorskip("paper_1806_05619_gb300")
+
+UFUN = {"mixed_tf32": _tf32_u, "mixed_bf16x3": _bf16x3_u, "fp64": lambda s: 0.0}
+
+
+def _setup(cfg, max_samples):
+    z, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
+    zo, _ = O.cbc(cfg["s"], cfg["log2_nmax"])
+    assert np.array_equal(z, zo)
+    ctx = M.Context.from_config(cfg, genvec=z, max_samples=max_samples)
+    orc = O.Oracle(n_levels=cfg["n_levels"], n0=cfg["n0"], s=cfg["s"], sigma=cfg["sigma"],
+                   corr_len=cfg["corr_len"], qoi=cfg["qoi"], mu0=cfg["mu0"], nu1=cfg["nu1"], nu2=cfg["nu2"],
+                   rtol=cfg["rtol"], max_cycles=100, sampler=cfg["sampler"], seed=cfg["seed"], R=cfg["R"],
+                   genvec=zo, log2_nmax=cfg["log2_nmax"], reuse=cfg["reuse"])
+    return ctx, orc
+
+
+def _run(ctx, cfg, work):
+    nl, R = cfg["n_levels"], cfg["R"]
+    ns = sum((ne - nb) * (re_ - rb) for (_, nb, ne, rb, re_) in work)
+    sums = torch.zeros(nl * R * 2, dtype=torch.float64, device="cuda")
+    F = torch.zeros(ns * nl, dtype=torch.float64, device="cuda")
+    ctx.sample_levels(work, sums, F)
+    torch.cuda.synchronize()
+    ctx.check_device()
+    index = [(lv, r, n) for (lv, nb, ne, rb, re_) in work for r in range(rb, re_) for n in range(nb, ne)]
+    return F.cpu().numpy().reshape(ns, nl), sums.cpu().numpy().reshape(nl, R, 2), index
+
+
+def _check_F(cfg, orc, Frow, lv, r, n, precision):
+    ref = orc.sample(lv, r, n, want_u=True)
+    assert ref["status"] == O.OK
+    eta = _field_bound(orc, cfg, orc.normals(lv, r, n), UFUN[precision](cfg["s"]))
+    slack = EXP_SLACK if precision != "fp64" else 0.0
+    for t in range(lv + 1):
+        u = ref["u"][t]
+        ratio = math.sqrt(np.mean(u ** 2)) / np.mean(u)
+        tol = math.expm1(eta + slack) + 2 * cfg["rtol"] * ratio + 1e-12
+        assert abs(Frow[t] / ref["F"][t] - 1.0) <= tol, (lv, r, n, t, Frow[t], ref["F"][t], tol)
+    assert np.all(Frow[lv + 1:] == 0.0)
+
+
+def _check_field(cfg, ctx, orc, t, y, precision):
+    k = ctx.fields(t, torch.from_numpy(y[None, :])).cpu().numpy()[0]
+    want = orc.field(t, y)
+    if precision == "fp64":
+        assert _rel(k, want) < 1e-12
+    else:
+        eta = _field_bound(orc, cfg, y, UFUN[precision](cfg["s"]))
+        assert np.max(np.abs(np.log(k / want))) <= eta + EXP_SLACK
+
+
+def _check_sums_from_F(cfg, Fg, sums, index):
+    nl, R = cfg["n_levels"], cfg["R"]
+    want = np.zeros((nl, R))
+    absd = np.zeros((nl, R))
+    for q, (lv, r, n) in enumerate(index):
+        d = np.diff(np.concatenate([[0.0], Fg[q, :lv + 1]]))
+        want[:lv + 1, r] += d
+        absd[:lv + 1, r] += np.abs(Fg[q, :lv + 1]) + np.abs(np.concatenate([[0.0], Fg[q, :lv]]))
+    assert np.all(np.abs(sums[:, :, 0] - want) <= 1e-12 * absd)
+
+
+@pytest.mark.parametrize("precision", ["mixed_tf32", "mixed_bf16x3", "fp64"])
+def test_problem3_batch_of_256_on_1024x1024(precision):
+    cfg = W.scaled(W.CONFIG3, precision=precision, log2_nmax=10)
+    top = cfg["n_levels"] - 1
+    work = [(top, 0, 16, 0, 16)]
+    ctx, orc = _setup(cfg, max_samples=256)
+    Fg, sums, index = _run(ctx, cfg, work)
+    assert np.all(np.isfinite(Fg)) and np.all(Fg > 0)
+    for q in [0, 3 * 16 + 5, 255]:
+        lv, r, n = index[q]
+        _check_F(cfg, orc, Fg[q], lv, r, n, precision)
+    _check_sums_from_F(cfg, Fg, sums, index)
+    _check_field(cfg, ctx, orc, top, orc.normals(top, 7, 9), precision)
+
+
+@pytest.mark.parametrize("precision", ["mixed_tf32", "fp64"])
+def test_problem5_samples_on_2048x2048(precision):
+    cfg = W.scaled(W.CONFIG5, precision=precision, log2_nmax=10)
+    top = cfg["n_levels"] - 1
+    work = [(top, 0, 2, 0, 2), (0, 0, 40, 0, 3), (5, 3, 5, 1, 2)]
+    ctx, orc = _setup(cfg, max_samples=256)
+    Fg, sums, index = _run(ctx, cfg, work)
+    assert np.all(np.isfinite(Fg))
+    for q in [3, len(index) - 1]:  # (top, r=1, n=1) and the last level-5 sample
+        lv, r, n = index[q]
+        _check_F(cfg, orc, Fg[q], lv, r, n, precision)
+    _check_sums_from_F(cfg, Fg, sums, index)
+    _check_field(cfg, ctx, orc, 6, orc.normals(top, 0, 1), precision)
