@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -57,6 +58,9 @@ def parse():
                     help="mixed form: pin smoothers per level, e.g. 1:whole,2:whole,4:tma (profiler runs, where "
                          "the autotuner's timings are not representative)")
     ap.add_argument("--no-graphs", action="store_true", help="launch kernel by kernel instead of replaying a CUDA graph")
+    ap.add_argument("--traffic-from", default="",
+                    help="ncu CSV of one timed step (DRAM bytes, durations): summarise into profiles/")
+    ap.add_argument("--traffic-line", default="", help="the bench JSON line of the same command without ncu")
     ap.add_argument("--counts-div", type=int, default=1,
                     help="divide the per-level counts (small cases for profiler captures only)")
     return ap.parse_args()
@@ -110,6 +114,93 @@ KIND_KERNELS = {
 }
 
 
+# kernel name -> the library's timing kind (the same grouping as its event brackets)
+KIND_PATTERNS = [
+    ("points", r"k_points"), ("level0", r"kb_level0"), ("synth", r"kb_synth_|kb_faces|kb_idiag"),
+    ("smooth", r"kb_gs|kb_rbgs_"), ("transfer", r"kb_resid_restrict|kb_prolong|kb_resid64|kb_update64"),
+    ("coarse", r"kb_coarse"), ("reduce", r"kb_qoi|kb_resnorm|kb_flags|k_sums|k_fout|kb_u_out|kb_k_out"),
+    ("kl_tc", r"kl_tc_kernel|kl_build_c|kl_build_psi"),
+]
+TRAFFIC_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "dram_traffic_mlqmc6.json")
+
+
+def kernel_kind(name):
+    for kind, pat in KIND_PATTERNS:
+        if re.search(pat, name):
+            return kind
+    return None
+
+
+def sources_digest():
+    """SHA-256 over the library's CUDA/C++ sources and header: DRAM counters
+    taken on other sources no longer describe these kernels."""
+    import glob
+    import hashlib
+
+    root = os.path.dirname(os.path.abspath(__file__))
+    files = sorted(glob.glob(os.path.join(root, "paper_1806_05619_gb300", "csrc", "*")))
+    files = [f for f in files if f.endswith((".cu", ".cuh", ".h", ".cpp"))]
+    files.append(os.path.join(root, "include", "mlqmc.h"))
+    h = hashlib.sha256()
+    for f in files:
+        h.update(os.path.relpath(f, root).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def summarize_traffic(csv_path, form, smoothers):
+    """Per-kind DRAM bytes and launches of one captured timed step (ncu CSV of
+    dram__bytes_read.sum, dram__bytes_write.sum and gpu__time_duration.sum in
+    base units), merged into the traffic file under `form`."""
+    import collections
+    import csv
+
+    with open(csv_path) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    per_launch = collections.defaultdict(dict)
+    names = {}
+    for row in csv.DictReader(lines):
+        v = float(row["Metric Value"].replace(",", ""))
+        per_launch[row["ID"]][row["Metric Name"]] = v
+        names[row["ID"]] = row["Kernel Name"]
+    kinds = collections.defaultdict(lambda: {"launches": 0, "dram_bytes": 0.0, "ns": 0.0})
+    for i, m in per_launch.items():
+        k = kernel_kind(names[i])
+        if k is None:
+            continue
+        d = kinds[k]
+        d["launches"] += 1
+        d["dram_bytes"] += m.get("dram__bytes_read.sum", 0.0) + m.get("dram__bytes_write.sum", 0.0)
+        d["ns"] += m.get("gpu__time_duration.sum", 0.0)
+    for d in kinds.values():
+        d["dram_bytes_per_launch"] = d["dram_bytes"] / d["launches"]
+    data = {}
+    if os.path.exists(TRAFFIC_FILE):
+        with open(TRAFFIC_FILE) as f:
+            data = json.load(f)
+    data.setdefault("forms", {})[form] = {"sources_sha256": sources_digest(), "smoothers": smoothers,
+                                         "kinds": dict(kinds)}
+    with open(TRAFFIC_FILE, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    return data["forms"][form]
+
+
+def measured_traffic(form, kind, smoothers):
+    """DRAM bytes per launch of `kind` from the committed ncu capture of this
+    form's timed step, or None when there is none, the sources changed since,
+    or the smoothers differ from the captured ones."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)["forms"][form]
+    except (OSError, KeyError, ValueError):
+        return None
+    if rec.get("sources_sha256") != sources_digest() or rec.get("smoothers") != smoothers:
+        return None
+    d = rec["kinds"].get(kind)
+    return d["dram_bytes_per_launch"] if d else None
+
+
 def kind_roofline(ms, work):
     """Roofline of one kernel kind from its device time and algorithmic work:
     the bound is the resource whose model time (bytes / HBM, FLOPs / pipe peak)
@@ -140,8 +231,10 @@ def kind_roofline(ms, work):
     return r
 
 
-def roofline_report(prof, work, steps):
-    """Dominant kind's roofline (the bench line's `roofline`) plus every kind's."""
+def roofline_report(prof, work, steps, form=None, smoothers=None):
+    """Dominant kind's roofline (the bench line's `roofline`) plus every kind's.
+    traffic: DRAM bytes per launch of that kind from the committed ncu capture
+    of the same form's timed step (None when stale or absent)."""
     kinds = {}
     for k, (ms, n) in prof.items():
         if n == 0:
@@ -155,7 +248,8 @@ def roofline_report(prof, work, steps):
     dom = max(kinds, key=lambda k: kinds[k]["ms"])
     d = kinds[dom]
     roof = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
-            "frac": d["frac"], "traffic": None, "kernel": KIND_KERNELS.get(dom, dom), "kernel_kind": dom,
+            "frac": d["frac"], "traffic": measured_traffic(form, dom, smoothers) if form else None,
+            "kernel": KIND_KERNELS.get(dom, dom), "kernel_kind": dom,
             "peak_source": d["peak_source"], "share_of_step": d["ms"] / max(1e-9, tot),
             "launches_per_step": d["launches_per_step"], "ms_per_step": d["ms_per_step"],
             "algorithmic_bytes_per_launch": d["algorithmic_bytes"] / max(1, prof[dom][1])}
@@ -365,7 +459,9 @@ def run_ours(args):
     launches0 = ctx.launch_count()
     replays0 = ctx.graph_replays()
     barrier()
+    torch.cuda.profiler.start()  # a profiler started with --profile-from-start off sees these steps only
     step_ms = timed_steps(step, args.steps, stream, flush)
+    torch.cuda.profiler.stop()
     barrier()
     launches = ctx.launch_count() - launches0
     replays = ctx.graph_replays() - replays0
@@ -408,7 +504,8 @@ def run_ours(args):
 
     # roofline of the dominant kernel kind: the library's event timing of each
     # launch inside the timed region and the algorithmic work it recorded
-    roof, by_kind = roofline_report(prof, pwork, args.steps)
+    smoothers = [k for k, _ in ctx.smoother_info()]
+    roof, by_kind = roofline_report(prof, pwork, args.steps, form=cfg["precision"], smoothers=smoothers)
 
     mixed = None
     if not args.no_mixed and cfg["precision"] == "fp64":
@@ -439,6 +536,7 @@ def run_ours(args):
                                    "(sep. exponential, sigma=1, lambda=0.3), lattice 2^10 points halving per "
                                    "level, R=16 shifts, N_l=1024,512,256,128,64,32 per shift, FMG mu0=2 V(2,2) "
                                    "RB-GS, mean-of-u QoI",
+                       "precision": cfg["precision"], "smoothers": smoothers,
                        "samples_per_step": ns * world, "counts_div": args.counts_div,
                        "l2": "flushed between timed steps (512 MiB write)",
                        "parallelism": f"independent replicas x{world}"},
@@ -489,7 +587,8 @@ def run_mixed_same_workload(args, cfg64, work, genvec, dev, stream, flush, M):
     tot = sum(ms)
     prof, pwork, prof_ms = profiled_pass(ctx, step, args, stream, flush)
     ctx.check_device(stream)
-    roof, by_kind = roofline_report(prof, pwork, args.steps)
+    roof, by_kind = roofline_report(prof, pwork, args.steps, form="mixed_tf32",
+                                    smoothers=[k for k, _ in ctx.smoother_info()])
     return {"value": ns * args.steps / (tot * 1e-3), "unit": UNIT, "ms_per_step": tot / args.steps,
             "dtype": "f32 V-cycles in f64 refinement, TF32 tensor-core KL, f32 field",
             "roofline": roof, "roofline_by_kind": by_kind, "profiled_pass_ms_per_step": prof_ms,
@@ -589,6 +688,14 @@ def run_time_to_eps(M):
 
 def main():
     args = parse()
+    if args.traffic_from:
+        # fold an ncu capture of one timed step (see profiles/) into the traffic file
+        with open(args.traffic_line) as f:
+            line = json.loads([ln for ln in f if ln.startswith("{")][-1])
+        form = line["config"]["precision"]
+        rec = summarize_traffic(args.traffic_from, form, line["config"]["smoothers"])
+        print(json.dumps({form: rec}, indent=1))
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
