@@ -506,6 +506,45 @@ __device__ __forceinline__ double widen_pos(float f)
 }
 __device__ __forceinline__ double widen_pos(double f) { return f; }
 
+// float -> double (exact) by moving the bits: sign, exponent rebiased by
+// 1023 - 127, mantissa shifted up by 29. Zero, subnormal, infinite and NaN
+// inputs take the conversion instruction, which on GB300 issues at the FP64 rate.
+__device__ __forceinline__ double widen(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = b & 0x7F800000u;
+    if (e == 0u || e == 0x7F800000u) return static_cast<double>(f);
+    const unsigned long long sgn = static_cast<unsigned long long>(b & 0x80000000u) << 32;
+    const unsigned long long mag = static_cast<unsigned long long>(b & 0x7FFFFFFFu);
+    return __longlong_as_double(static_cast<long long>(sgn | ((mag << 29) + (896ull << 52))));
+}
+__device__ __forceinline__ double widen(double f) { return f; }
+
+// double -> float rounded to nearest even, in integer arithmetic on the bits
+// when the result is a normal float or overflows (biased exponent of |x| in
+// 897..1150): add 2^28 - 1 plus the lowest kept bit, drop 29 mantissa bits,
+// rebias the exponent (a carry out of the mantissa moves into the exponent,
+// up to infinity). Smaller magnitudes, infinities and NaN take the
+// conversion instruction.
+__device__ __forceinline__ float narrow(double x)
+{
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned long long a = b & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned e = static_cast<unsigned>(a >> 52);
+    if (e < 897u || e > 1150u) return __double2float_rn(x);
+    const unsigned long long r = a + 0x0FFFFFFFull + ((a >> 29) & 1ull);
+    const uint32_t mag = static_cast<uint32_t>((r >> 29) - (896ull << 23));
+    return __uint_as_float(mag | (static_cast<uint32_t>(b >> 32) & 0x80000000u));
+}
+
+// A double result stored in working precision T.
+template <typename T>
+__device__ __forceinline__ T to_work(double x)
+{
+    if constexpr (sizeof(T) == 4) return narrow(x);
+    else return x;
+}
+
 // (A u)_P h^2 in flux form, FP64, from working-precision faces.
 template <typename T>
 __device__ __forceinline__ double apply_h2_64(const T* kx, const T* ky, const double* u, int n, int i1, int i2)
@@ -522,10 +561,10 @@ __device__ __forceinline__ double apply_h2_64(const T* kx, const T* ky, const do
 // Refinement path (mixed forms, and the converged FP64 form): r = 1 - A u64 in
 // FP64 with the working-precision faces widened; r stored to the working
 // precision right-hand side. Returns ||r||_2.
+// ih2 = n^2, hoisted by the caller.
 template <typename T>
-__device__ __forceinline__ double resid64_cell(const Lv<T>& L, int i1, int i2)
+__device__ __forceinline__ double resid64_cell(const Lv<T>& L, double ih2, int i1, int i2)
 {
-    const double ih2 = static_cast<double>(L.n) * L.n;
     return fma(-ih2, apply_h2_64<T>(L.kx, L.ky, L.u64, L.n, i1, i2), 1.0);
 }
 
@@ -533,11 +572,12 @@ template <typename TM, typename T>
 __device__ double resid64_to_rhs(const TM& tm, const Lv<T>& L, double* red)
 {
     const int n = L.n;
+    const double ih2 = static_cast<double>(n) * n;
     double acc = 0.0;
     for (int p = tm.rank(); p < n * n; p += tm.size()) {
         const int i2 = p / n;
-        const double r = resid64_cell(L, p - i2 * n, i2);
-        L.bc[p] = static_cast<T>(r);
+        const double r = resid64_cell(L, ih2, p - i2 * n, i2);
+        L.bc[p] = to_work<T>(r);
         acc += r * r;
     }
     return sqrt(team_sum(tm, acc, red));

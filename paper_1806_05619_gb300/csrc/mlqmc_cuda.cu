@@ -675,7 +675,7 @@ __global__ void kb_prolong(FmgArgs A, int t, int B)
 #pragma unroll
                 for (int fy = 0; fy < 2; ++fy) {
                     double2* d = reinterpret_cast<double2*>(u + fy * n);
-                    const double2 w = make_double2(static_cast<double>(v[fy][0]), static_cast<double>(v[fy][1]));
+                    const double2 w = make_double2(widen(v[fy][0]), widen(v[fy][1]));
                     if (ADD) *d = make_double2(d->x + w.x, d->y + w.y);
                     else *d = w;
                 }
@@ -702,6 +702,7 @@ __global__ void kb_resid64(FmgArgs A, int t, int B)
 {
     const int n = A.lv[t].n;
     const uint32_t per = static_cast<uint32_t>(n) * static_cast<uint32_t>(n);
+    const double ih2 = static_cast<double>(n) * n;
     GRID_STRIDE(idx, B * per)
     {
         const int i = static_cast<int>(idx / per);
@@ -709,7 +710,7 @@ __global__ void kb_resid64(FmgArgs A, int t, int B)
         const int p = static_cast<int>(idx - i * per);
         const int i2 = p / n;
         const Lv<T> L = view<T>(A, t, i);
-        L.bc[p] = static_cast<T>(resid64_cell(L, p - i2 * n, i2));
+        L.bc[p] = to_work<T>(resid64_cell(L, ih2, p - i2 * n, i2));
     }
 }
 
@@ -724,7 +725,7 @@ __global__ void kb_update64(FmgArgs A, int t, int B)
         const int i = static_cast<int>(idx / per);
         if (inactive(A, i)) continue;
         const int p = static_cast<int>(idx - i * per);
-        at<double>(A.lv[t].u64, i)[p] += static_cast<double>(at<T>(A.lv[t].u, i)[p]);
+        at<double>(A.lv[t].u64, i)[p] += widen(at<T>(A.lv[t].u, i)[p]);
     }
 }
 
@@ -772,24 +773,72 @@ __device__ __forceinline__ int team_count()
 
 // F_t of samples 0..B-1: one CTA per sample on large levels, one warp per
 // sample on small ones (TM), the sum in a fixed order either way.
-template <typename T, bool U64, typename TM>
+// UPD (mixed forms, one refinement step per level): the step's last update
+// u64 += e (e the FP32 correction in u), the FP32 copy of u64 and the sum run
+// in one pass over each thread's cell pairs, so u64 is read once.
+template <typename T, bool U64, typename TM, bool UPD = false>
 __global__ void __launch_bounds__(256) kb_qoi(FmgArgs A, int t, int B)
 {
+    static_assert(!UPD || (U64 && sizeof(T) == 4), "the fused update is the mixed forms' refinement step");
     __shared__ double red[48];
     const TM tm;
     for (int i = team_index<TM>(); i < B; i += team_count<TM>()) {
         double v;
-        if constexpr (U64) v = qoi(tm, at<double>(A.lv[t].u64, i), A.lv[t].n, A.qoi, red);
-        else v = qoi(tm, at<T>(A.lv[t].u, i), A.lv[t].n, A.qoi, red);
+        if constexpr (UPD) {
+            double2* u64 = reinterpret_cast<double2*>(at<double>(A.lv[t].u64, i));
+            float2* u = reinterpret_cast<float2*>(at<float>(A.lv[t].u, i));
+            const int n = A.lv[t].n;
+            const int np = n * n / 2, sz = tm.size();
+            double acc = 0.0;
+            // four pairs per round, all loads first (the stores could alias the
+            // next loads as far as the compiler knows); cells summed in p order
+            constexpr int U = 4;
+            int p = tm.rank();
+            for (; p + (U - 1) * sz < np; p += U * sz) {
+                double2 w[U];
+                float2 d[U];
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+                    w[k] = u64[p + k * sz];
+                    d[k] = u[p + k * sz];  // the correction e, replaced by the FP32 copy of u64
+                }
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+                    const double2 r = make_double2(w[k].x + widen(d[k].x), w[k].y + widen(d[k].y));
+                    u64[p + k * sz] = r;
+                    u[p + k * sz] = make_float2(narrow(r.x), narrow(r.y));
+                    acc += r.x;
+                    acc += r.y;
+                }
+            }
+            for (; p < np; p += sz) {
+                const double2 w = u64[p];
+                const float2 d = u[p];
+                const double2 r = make_double2(w.x + widen(d.x), w.y + widen(d.y));
+                u64[p] = r;
+                u[p] = make_float2(narrow(r.x), narrow(r.y));
+                acc += r.x;
+                acc += r.y;
+            }
+            if (A.qoi == MLQMC_QOI_MEAN) {
+                v = team_sum(tm, acc, red) / (static_cast<double>(n) * n);
+            } else {
+                tm.sync();
+                v = qoi(tm, at<double>(A.lv[t].u64, i), n, A.qoi, red);
+            }
+        } else {
+            if constexpr (U64) v = qoi(tm, at<double>(A.lv[t].u64, i), A.lv[t].n, A.qoi, red);
+            else v = qoi(tm, at<T>(A.lv[t].u, i), A.lv[t].n, A.qoi, red);
+        }
         if (tm.leader()) A.F[static_cast<size_t>(i) * A.n_levels + t] = v;
-        if constexpr (U64 && sizeof(T) == 4) {
+        if constexpr (U64 && sizeof(T) == 4 && !UPD) {
             // mixed forms: FP32 copy of the level's solution for the next FMG interpolation
             const double2* u64 = reinterpret_cast<const double2*>(at<double>(A.lv[t].u64, i));
             float2* u = reinterpret_cast<float2*>(at<float>(A.lv[t].u, i));
             const int nn2 = A.lv[t].n * A.lv[t].n / 2;
             for (int p = tm.rank(); p < nn2; p += tm.size()) {
                 const double2 w = u64[p];
-                u[p] = make_float2(static_cast<float>(w.x), static_cast<float>(w.y));
+                u[p] = make_float2(narrow(w.x), narrow(w.y));
             }
         }
     }
@@ -1484,6 +1533,9 @@ template <typename T, bool MX>
 mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, double* d_usol, cudaStream_t st)
 {
     const bool refine = A.refine != 0;
+    // mixed forms with one refinement step per level: the step's u64 += e runs
+    // inside the QoI kernel, which reads u64 anyway
+    const bool fuse_update = MX && refine && !(c->p.refine_rtol > 0.0);
     size_t uoff = static_cast<size_t>(A.lv[0].n) * A.lv[0].n;
     for (int t = 1; t <= Lmax; ++t) {
         const int B = Bt[t];
@@ -1504,7 +1556,7 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
                 mlqmc_status s = vcycle_batched<T>(c, A, t, B, false, st);
                 if (s != MLQMC_OK) return s;
             }
-            {
+            if (!fuse_update) {
                 Timed tm(c, kProfTransfer, st, work_of<double>(B * (16.0 + es) * Mc, B * Mc));
                 kb_update64<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
             }
@@ -1523,14 +1575,18 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
             }
         }
         {
-            Timed tm(c, kProfReduce, st,
-                     work_of<double>(B * ((refine ? 8.0 : es) + (refine && sizeof(T) == 4 ? 4.0 : 0.0)) * Mc, B * Mc));
+            // bytes: u (or u64) read, the FP32 copy written; fused update: u64 also
+            // written and the correction read (FP64: update and sum)
+            const double qb = fuse_update ? 24.0 : (refine ? 8.0 : es) + (refine && sizeof(T) == 4 ? 4.0 : 0.0);
+            Timed tm(c, kProfReduce, st, work_of<double>(B * qb * Mc, B * (fuse_update ? 2.0 : 1.0) * Mc));
             if (n * n <= 4096) {  // one warp per sample
                 const int grid = std::max(1, std::min((B + 7) / 8, c->sm_count * 16));
-                if (refine) kb_qoi<T, true, WarpTeam><<<grid, 256, 0, st>>>(A, t, B);
+                if (fuse_update) kb_qoi<T, true, WarpTeam, MX><<<grid, 256, 0, st>>>(A, t, B);
+                else if (refine) kb_qoi<T, true, WarpTeam><<<grid, 256, 0, st>>>(A, t, B);
                 else kb_qoi<T, false, WarpTeam><<<grid, 256, 0, st>>>(A, t, B);
             } else {
-                if (refine) kb_qoi<T, true, BlockTeam><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
+                if (fuse_update) kb_qoi<T, true, BlockTeam, MX><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
+                else if (refine) kb_qoi<T, true, BlockTeam><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
                 else kb_qoi<T, false, BlockTeam><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
             }
         }
