@@ -660,6 +660,8 @@ def run_time_to_eps(M):
     s = 200, lambda = 0.3, 16 shifts, mean-of-u QoI, every level refined to
     1e-10), mixed form against the FP64 form, for eps in {1e-2, 3e-3, 1e-3}
     and two smaller tolerances (3e-4, 1e-4) where the runs take longer."""
+    from paper_1806_05619_gb300 import rates
+
     cfg = dict(W.CONFIG4)
     cfg["log2_nmax"] = 12
     genvec, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
@@ -682,7 +684,22 @@ def run_time_to_eps(M):
                          "rounds": r["rounds"], "N": r["N"][:r["L"] + 1], "run_status": r["run_status"],
                          "alpha": r["alpha"], "Ybar": r["Ybar"][:r["L"] + 1], "Vell": r["Vell"][:r["L"] + 1]})
         out[name] = rows
+        if name == "mixed_tf32":
+            # rates of (A1)-(A4) on the same problem, and Proposition 1 against
+            # the recycling runs: the predicted factor, the factor the run's own
+            # counts give with the measured per-sample costs, and the measured
+            # device-time ratio to the run without recycling
+            out["rates"] = rates.measure(ctx, n_points=256, lambda_level=2, gamma_levels=3)
         del ctx
+    rt = out["rates"]
+    prop = {"predicted": rt["prop1_ratio"], "from_counts": [], "measured_gpu_time": []}
+    for a, b in zip(out["mixed_tf32"], out["mixed_tf32_no_reuse"]):
+        L = a["L"]
+        used = np.cumsum(np.array(a["N"][:L + 1], dtype=np.float64)[::-1])[::-1]  # samples on level l
+        prop["from_counts"].append({"eps": a["eps"],
+                                    "ratio": rates.reuse_cost_ratio(used, rt["ms_per_sample"][:L + 1])})
+        prop["measured_gpu_time"].append({"eps": a["eps"], "ratio": a["gpu_seconds"] / b["gpu_seconds"]})
+    out["prop1"] = prop
     return out
 
 
