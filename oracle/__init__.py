@@ -69,6 +69,15 @@ class Result(C.Structure):
     ]
 
 
+def mlmc_nopt(V, Cost, eps):
+    """eq. nopt (Sec. 2): N_l = ceil(2/eps^2 sqrt(V_l/C_l) sum_t sqrt(V_t C_t))."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    Cost = np.ascontiguousarray(Cost, dtype=np.float64)
+    out = np.zeros(len(V))
+    lib().or_mlmc_nopt(len(V) - 1, _dp(V), _dp(Cost), float(eps), _dp(out))
+    return out
+
+
 def lib():
     global _lib
     with _lock:
@@ -107,6 +116,9 @@ def lib():
             L.or_sample_levels.argtypes = [C.c_void_p, C.POINTER(Work), C.c_int, dp, dp]
             L.or_finalize.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int64), dp, dp, dp, dp, dp, dp]
             L.or_estimate.argtypes = [C.c_void_p, C.c_double, C.c_int, C.POINTER(Result)]
+            L.or_estimate_mlmc.argtypes = [C.c_void_p, C.c_double, C.c_int, C.POINTER(Result)]
+            L.or_mlmc_nopt.argtypes = [C.c_int, dp, dp, C.c_double, dp]
+            L.or_mlmc_nopt.restype = None
             L.or_cbc.argtypes = [C.c_int, C.c_int, dp, C.POINTER(C.c_uint32), dp]
             L.or_cbc_criterion.argtypes = [C.c_int, C.c_int, dp, C.POINTER(C.c_uint32)]
             L.or_cbc_criterion.restype = C.c_double
@@ -350,6 +362,19 @@ class Oracle:
         if want_F:
             out["F"] = F.reshape(nsamp, self.n_levels)
         return out
+
+    def estimate_mlmc(self, eps, max_rounds=200):
+        """Plain MLMC (Sec. 2: eqs. MSE, vardecomp, nopt; reading A28); Monte Carlo
+        sampler and no recycling only."""
+        res = Result()
+        st = lib().or_estimate_mlmc(self.ctx, float(eps), int(max_rounds), C.byref(res))
+        L = res.L
+        return dict(status=st, run_status=res.status, Q=res.Q, varQ=res.varQ, bias=res.bias,
+                    alpha=res.alpha, alpha_clamped=res.alpha_clamped, L=L, rounds=res.rounds,
+                    N=[res.N[i] for i in range(self.n_levels)],
+                    Ybar=[res.Ybar[i] for i in range(self.n_levels)],
+                    Vell=[res.Vell[i] for i in range(self.n_levels)],
+                    C=[res.C[i] for i in range(self.n_levels)])
 
     def estimate(self, eps, max_rounds=200):
         """Algorithm 1 with the deterministic cost model C_l = sum_{t<=l} n_t^2."""

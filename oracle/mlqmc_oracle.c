@@ -982,6 +982,101 @@ out:
 }
 
 /* ------------------------------------------------------------------------- */
+/* Plain MLMC, the comparison baseline (Sec. 2): independent MC samples per  */
+/* level, no recycling, one replicate (r = 0). MSE split (eq. MSE): variance */
+/* sum V_l/N_l <= eps^2/2 (eq. vardecomp) through the counts of eq. nopt,    */
+/* bias <= eps/sqrt(2) by the test of Algorithm 1 (readings A14, A15).       */
+/* Reading A28: levels are added one at a time from L = 0, a new level first */
+/* takes 32 samples; after each round every level below its eq. nopt count  */
+/* is topped up (one round); when none is short the bias test (L >= 2)      */
+/* stops the run or adds a level. V_l: sample variance (ddof 1) of          */
+/* F_l - F_{l-1}; C_l: the cell count of the FMG hierarchy (reading A17).    */
+/* ------------------------------------------------------------------------- */
+
+/* eq. nopt: N_l = ceil(2/eps^2 sqrt(V_l/C_l) sum_{t<=L} sqrt(V_t C_t)). */
+void or_mlmc_nopt(int L, const double* V, const double* C, double eps, double* N_out)
+{
+    double acc = 0.0;
+    for (int t = 0; t <= L; ++t) acc += sqrt(V[t] * C[t]);
+    for (int l = 0; l <= L; ++l) N_out[l] = ceil(2.0 / (eps * eps) * sqrt(V[l] / C[l]) * acc);
+}
+
+int or_estimate_mlmc(const or_ctx* c, double eps, int max_rounds, or_result* res)
+{
+    const or_problem* p = &c->p;
+    if (p->sampler != 0 || p->reuse != 0 || !(eps > 0.0)) return OR_ERR_ARG;
+    const int Lmax = p->n_levels - 1;
+    const int R = p->R;
+    int64_t N[32] = {0}, want[32] = {0};
+    double V[32], C[32], Ybar[32], Nopt[32];
+    double* sums = calloc((size_t)(Lmax + 1) * R * 2, sizeof(double));
+    for (int l = 0; l <= Lmax; ++l) {
+        V[l] = INFINITY;
+        Ybar[l] = 0.0;
+        C[l] = 0.0;
+        for (int t = 0; t <= l; ++t) C[l] += (double)(p->n0 << t) * (double)(p->n0 << t);
+    }
+    int L = 0, rounds = 0, st = OR_OK, clamped = 0;
+    double bias = INFINITY, alpha = NAN;
+    want[0] = 32;
+    for (;;) {
+        int short_any = 0;
+        for (int l = 0; l <= L; ++l) if (want[l] > N[l]) short_any = 1;
+        if (short_any) {
+            if (rounds >= max_rounds) { st = 8; break; }
+            for (int l = 0; l <= L; ++l) {
+                if (want[l] <= N[l]) continue;
+                or_work w;
+                w.level = l; w.pad = 0; w.n_begin = N[l]; w.n_end = want[l]; w.r_begin = 0; w.r_end = 1;
+                st = or_sample_levels(c, &w, 1, sums, NULL);
+                if (st != OR_OK) goto out;
+                N[l] = want[l];
+            }
+            ++rounds;
+            for (int l = 0; l <= L; ++l) {
+                const double n = (double)N[l];
+                const double s1 = sums[(size_t)l * R * 2], s2 = sums[(size_t)l * R * 2 + 1];
+                Ybar[l] = s1 / n;
+                V[l] = N[l] > 1 ? (s2 - s1 * s1 / n) / (n - 1.0) : INFINITY;
+            }
+            or_mlmc_nopt(L, V, C, eps, Nopt);
+            for (int l = 0; l <= L; ++l) {
+                const int64_t n = (int64_t)(Nopt[l] < 9.0e18 ? Nopt[l] : 9.0e18);
+                want[l] = n > N[l] ? n : N[l];
+            }
+            continue;
+        }
+        if (L >= 2) {
+            alpha = fit_alpha(L, Ybar, &clamped);
+            bias = fabs(Ybar[L]) / (pow(2.0, alpha) + 1.0);
+            if (!(bias > eps / sqrt(2.0))) break;
+        }
+        if (L + 1 > Lmax) { st = 7; break; }
+        L = L + 1;
+        want[L] = 32;
+    }
+out:
+    {
+        double Q = 0.0, varQ = 0.0;
+        for (int l = 0; l <= L; ++l) {
+            Q += Ybar[l];
+            varQ += N[l] > 0 ? V[l] / (double)N[l] : INFINITY;
+        }
+        res->Q = Q; res->varQ = varQ;
+    }
+    res->bias = bias; res->alpha = alpha;
+    res->L = L; res->rounds = rounds; res->status = st; res->alpha_clamped = clamped;
+    for (int l = 0; l < 32; ++l) {
+        res->Ybar[l] = l <= Lmax ? Ybar[l] : 0.0;
+        res->Vell[l] = l <= Lmax ? V[l] : 0.0;
+        res->C[l] = l <= Lmax ? C[l] : 0.0;
+        res->N[l] = l <= Lmax ? N[l] : 0;
+    }
+    free(sums);
+    return (st == 7 || st == 8) ? OR_OK : st;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Component-by-component construction of the generating vector (Sec. 3.2   */
 /* cites Nuyens-Cools; reading A13). Criterion: shift-averaged worst-case    */
 /* error in the unanchored weighted Sobolev space with product weights:      */
