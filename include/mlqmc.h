@@ -192,6 +192,29 @@ mlqmc_status mlqmc_sample_levels(mlqmc_ctx* c, const mlqmc_work* work, int32_t n
 mlqmc_status mlqmc_estimate(mlqmc_ctx* c, double eps, const mlqmc_run_opts* opts, mlqmc_result* out);
 
 /*
+ * Plain MLMC, the baseline of the paper's comparison (Sec. 2; Tab. speedup,
+ * S1 and S2): independent Monte Carlo samples per level, no recycling, one
+ * replicate (shift index 0 only), the mean-square error split into variance
+ * and squared bias, each at most eps^2/2 (eq. MSE). Levels are added one at
+ * a time from L = 0; a new level first takes 32 samples; after each round
+ * the sample counts are raised to eq. nopt,
+ *   N_l = ceil(2/eps^2 sqrt(V_l/C_l) sum_{t<=L} sqrt(V_t C_t)),
+ * with V_l the sample variance of F_l - F_{l-1} (ddof 1) and C_l as in
+ * mlqmc_estimate (opts->cost_model), all levels short of their count sampled
+ * in one mlqmc_sample_levels call; when no level is short, the bias test of
+ * mlqmc_estimate (least-squares alpha over levels 1..L, |Ybar_L|/(2^alpha+1))
+ * decides between stopping and adding a level (L >= 2 first).
+ * The context must use the Monte Carlo sampler and no recycling
+ * (MLQMC_ERR_INVALID_ARG otherwise); opts->batched is ignored.
+ * Result: Q = sum of the level means, varQ = sum V_l/N_l (eq. vardecomp),
+ * N[l] samples of level l, Ybar[l] their mean difference, Vell[l] = V_l,
+ * C[l]; rounds = mlqmc_sample_levels calls; run_status 7 when the finest
+ * level is reached with the bias test failing, 8 at max_rounds.
+ * Blocking; uses its own stream.
+ */
+mlqmc_status mlqmc_estimate_mlmc(mlqmc_ctx* c, double eps, const mlqmc_run_opts* opts, mlqmc_result* out);
+
+/*
  * The estimator from reuse sums (host only, no context or device needed): for
  * levels t = 0..L and shifts r < R, sums[(t*R + r)*2 + 0] = sum of dF_t over
  * the samples that enter level t's difference ([.. + 1] the sum of squares,

@@ -85,6 +85,7 @@ def lib():
             L.mlqmc_destroy.restype = None
             L.mlqmc_sample_levels.argtypes = [vp, C.POINTER(Work), i32, vp, vp, vp]
             L.mlqmc_estimate.argtypes = [vp, C.c_double, C.POINTER(RunOpts), C.POINTER(Result)]
+            L.mlqmc_estimate_mlmc.argtypes = [vp, C.c_double, C.POINTER(RunOpts), C.POINTER(Result)]
             L.mlqmc_get_device_status.argtypes = [vp, vp]
             L.mlqmc_status_string.argtypes = [C.c_int]
             L.mlqmc_status_string.restype = C.c_char_p
@@ -107,7 +108,8 @@ def lib():
             L.mlqmc_graph_replays.restype = i64
             L.mlqmc_launch_count.argtypes = [vp]
             L.mlqmc_launch_count.restype = i64
-            for name in ["mlqmc_create", "mlqmc_sample_levels", "mlqmc_estimate", "mlqmc_get_device_status",
+            for name in ["mlqmc_create", "mlqmc_sample_levels", "mlqmc_estimate", "mlqmc_estimate_mlmc",
+                         "mlqmc_get_device_status",
                          "mlqmc_cbc_genvec", "mlqmc_modes", "mlqmc_point_bits", "mlqmc_normals", "mlqmc_fields",
                          "mlqmc_sample_solution", "mlqmc_profile", "mlqmc_profile_read", "mlqmc_profile_work", "mlqmc_smoother_info", "mlqmc_set_smoother", "mlqmc_set_graphs",
                          "mlqmc_estimator_from_sums",
@@ -242,6 +244,19 @@ class Context:
         o = RunOpts(max_rounds=max_rounds, cost_model=cost_model, batched=1 if batched else 0)
         res = Result()
         _check(lib().mlqmc_estimate(self.h, float(eps), C.byref(o), C.byref(res)), "mlqmc_estimate")
+        L = res.L
+        return dict(Q=res.Q, varQ=res.varQ, bias=res.bias, alpha=res.alpha, L=L, rounds=res.rounds,
+                    run_status=res.run_status, alpha_clamped=res.alpha_clamped, wall_seconds=res.wall_seconds,
+                    gpu_seconds=res.gpu_seconds, N=[res.N[i] for i in range(self.n_levels)],
+                    Ybar=[res.Ybar[i] for i in range(self.n_levels)],
+                    Vell=[res.Vell[i] for i in range(self.n_levels)], C=[res.C[i] for i in range(self.n_levels)])
+
+    def estimate_mlmc(self, eps, max_rounds=0, cost_model=0):
+        """Plain MLMC (Monte Carlo sampler, no recycling): the comparison baseline
+        of the paper's speed-ups, sample counts from eq. nopt."""
+        o = RunOpts(max_rounds=max_rounds, cost_model=cost_model, batched=0)
+        res = Result()
+        _check(lib().mlqmc_estimate_mlmc(self.h, float(eps), C.byref(o), C.byref(res)), "mlqmc_estimate_mlmc")
         L = res.L
         return dict(Q=res.Q, varQ=res.varQ, bias=res.bias, alpha=res.alpha, L=L, rounds=res.rounds,
                     run_status=res.run_status, alpha_clamped=res.alpha_clamped, wall_seconds=res.wall_seconds,

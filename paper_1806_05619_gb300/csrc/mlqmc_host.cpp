@@ -353,6 +353,157 @@ done:
     return st;
 }
 
+// ---- plain MLMC (the comparison baseline: eqs. MSE, vardecomp, nopt) -------
+
+mlqmc_status run_estimate_mlmc(mlqmc_ctx* c, double eps, const mlqmc_run_opts* o, mlqmc_result* out)
+{
+    if (!c || !out || !(eps > 0.0)) return MLQMC_ERR_INVALID_ARG;
+    if (c->p.sampler != MLQMC_SAMPLER_MC || c->p.reuse != 0) return MLQMC_ERR_INVALID_ARG;
+    mlqmc_run_opts opts{};
+    if (o) opts = *o;
+    if (opts.max_rounds <= 0) opts.max_rounds = 1000;
+    constexpr int64_t kWarm = 32;  // first samples of a new level
+    const auto t_start = std::chrono::steady_clock::now();
+    const int Lmax = c->p.n_levels - 1;
+    const int R = c->p.n_shifts;
+    const double inf = std::numeric_limits<double>::infinity();
+    std::vector<int64_t> N(32, 0), want(32, 0);
+    std::vector<double> V(32, inf), C(32, 0.0), Ybar(32, 0.0), model(32, 0.0);
+    std::vector<double> sums(static_cast<size_t>(Lmax + 1) * R * 2, 0.0);
+    for (int l = 0; l <= Lmax; ++l)
+        for (int t = 0; t <= l; ++t) {
+            const double n = static_cast<double>(c->p.coarse_cells << t);
+            model[l] += n * n;
+        }
+    cudaStream_t stream = nullptr;
+    double* d_sums = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    mlqmc_status st = MLQMC_OK;
+    if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMalloc(&d_sums, sums.size() * sizeof(double)) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+        cudaMemsetAsync(d_sums, 0, sums.size() * sizeof(double), stream) != cudaSuccess)
+        st = MLQMC_ERR_CUDA;
+
+    int L = 0, rounds = 0, run_status = 0, clamped = 0;
+    double bias = inf, alpha = std::nan(""), gpu_s = 0.0;
+    want[0] = kWarm;
+    // eq. nopt over levels 0..L from the current V_l, C_l
+    auto optimal = [&]() {
+        double acc = 0.0;
+        for (int l = 0; l <= L; ++l) acc += std::sqrt(V[l] * C[l]);
+        for (int l = 0; l <= L; ++l) {
+            const double n = std::ceil(2.0 / (eps * eps) * std::sqrt(V[l] / C[l]) * acc);
+            want[l] = std::max(N[l], static_cast<int64_t>(std::min(n, 9.0e18)));
+        }
+    };
+    while (st == MLQMC_OK) {
+        std::vector<mlqmc_work> work;
+        double model_work = 0.0;
+        for (int l = 0; l <= L; ++l)
+            if (want[l] > N[l]) {
+                mlqmc_work w{};
+                w.level = l;
+                w.n_begin = N[l];
+                w.n_end = want[l];
+                w.r_begin = 0;
+                w.r_end = 1;
+                work.push_back(w);
+                model_work += model[l] * static_cast<double>(want[l] - N[l]);
+            }
+        if (!work.empty()) {
+            if (rounds >= opts.max_rounds) {
+                run_status = 8;
+                break;
+            }
+            cudaEventRecord(e0, stream);
+            st = mlqmc_sample_levels(c, work.data(), static_cast<int32_t>(work.size()), d_sums, nullptr, stream);
+            cudaEventRecord(e1, stream);
+            if (st != MLQMC_OK) break;
+            if (cudaMemcpyAsync(sums.data(), d_sums, sums.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                stream) != cudaSuccess ||
+                cudaStreamSynchronize(stream) != cudaSuccess) {
+                st = MLQMC_ERR_CUDA;
+                break;
+            }
+            st = mlqmc_get_device_status(c, stream);
+            if (st != MLQMC_OK) break;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            gpu_s += ms * 1e-3;
+            ++rounds;
+            for (const mlqmc_work& w : work) {
+                const int l = w.level;
+                N[l] = w.n_end;
+                C[l] = (opts.cost_model == 1 && model_work > 0.0) ? (ms * 1e-3) * model[l] / model_work : model[l];
+            }
+            for (int l = 0; l <= L; ++l) {
+                const double n = static_cast<double>(N[l]);
+                const double s1 = sums[static_cast<size_t>(l) * R * 2], s2 = sums[static_cast<size_t>(l) * R * 2 + 1];
+                Ybar[l] = s1 / n;
+                V[l] = N[l] > 1 ? (s2 - s1 * s1 / n) / (n - 1.0) : inf;
+            }
+            optimal();
+            continue;
+        }
+        // every level has its count: the bias test, else one more level
+        if (L >= 2) {
+            double sx = 0, sy = 0, sxx = 0, sxy = 0;
+            int m = 0;
+            for (int l = 1; l <= L; ++l) {
+                const double y = std::log2(std::fabs(Ybar[l]));
+                if (!std::isfinite(y)) continue;
+                sx += l;
+                sy += y;
+                sxx += static_cast<double>(l) * l;
+                sxy += l * y;
+                ++m;
+            }
+            alpha = m >= 2 ? -(m * sxy - sx * sy) / (m * sxx - sx * sx) : std::nan("");
+            clamped = 0;
+            if (!(alpha > 0.0)) {
+                alpha = 0.5;
+                clamped = 1;
+            }
+            bias = std::fabs(Ybar[L]) / (std::pow(2.0, alpha) + 1.0);
+            if (!(bias > eps / std::sqrt(2.0))) break;
+        }
+        if (L + 1 > Lmax) {
+            run_status = 7;
+            break;
+        }
+        ++L;
+        want[L] = kWarm;
+    }
+    std::memset(out, 0, sizeof(*out));
+    double Q = 0.0, varQ = 0.0;
+    for (int l = 0; l <= L; ++l) {
+        Q += Ybar[l];
+        varQ += N[l] > 0 ? V[l] / static_cast<double>(N[l]) : inf;
+    }
+    out->Q = Q;
+    out->varQ = varQ;
+    out->bias = bias;
+    out->alpha = alpha;
+    out->L = L;
+    out->rounds = rounds;
+    out->run_status = run_status;
+    out->alpha_clamped = clamped;
+    out->gpu_seconds = gpu_s;
+    for (int l = 0; l <= Lmax && l < 32; ++l) {
+        out->N[l] = N[l];
+        out->Ybar[l] = Ybar[l];
+        out->Vell[l] = V[l];
+        out->C[l] = C[l];
+    }
+    out->wall_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (d_sums) cudaFree(d_sums);
+    if (stream) cudaStreamDestroy(stream);
+    return st;
+}
+
 }  // namespace mlqmc
 
 // ---- C ABI: host-only entry points ---------------------------------------
@@ -428,6 +579,11 @@ extern "C" mlqmc_status mlqmc_cbc_genvec(int32_t s, int32_t m, const double* gam
 extern "C" mlqmc_status mlqmc_estimate(mlqmc_ctx* c, double eps, const mlqmc_run_opts* opts, mlqmc_result* out)
 {
     return mlqmc::run_estimate(c, eps, opts, out);
+}
+
+extern "C" mlqmc_status mlqmc_estimate_mlmc(mlqmc_ctx* c, double eps, const mlqmc_run_opts* opts, mlqmc_result* out)
+{
+    return mlqmc::run_estimate_mlmc(c, eps, opts, out);
 }
 
 extern "C" mlqmc_status mlqmc_estimator_from_sums(int32_t L, int32_t R, int32_t reuse, const int64_t* N,

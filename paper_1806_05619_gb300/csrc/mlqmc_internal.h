@@ -36,6 +36,7 @@ void psi_table(const Eig1D& e, double corr_len, int K1, int n, std::vector<doubl
 
 // Algorithm 1 driver (host control around mlqmc_sample_levels).
 mlqmc_status run_estimate(mlqmc_ctx* c, double eps, const mlqmc_run_opts* o, mlqmc_result* out);
+mlqmc_status run_estimate_mlmc(mlqmc_ctx* c, double eps, const mlqmc_run_opts* o, mlqmc_result* out);
 
 }  // namespace mlqmc
 
