@@ -668,7 +668,8 @@ def run_time_to_eps(M):
     out = {"workload": "Algorithm 1 on 7 levels 8x8..512x512, s=200, lambda=0.3, R=16, rtol 1e-10",
            "variants": "mixed_tf32 / fp64: reuse (MG-MLQMC), one level per round; mixed_tf32_no_reuse: plain "
                        "MLQMC (each difference from its own samples); mixed_tf32_batched: every level with "
-                       "V_l/C_l >= max/2 doubles in one round"}
+                       "V_l/C_l >= max/2 doubles in one round; mlmc_mixed_tf32: plain MLMC (Monte Carlo "
+                       "normals, one replicate, eq. nopt counts)"}
     variants = [("mixed_tf32", "mixed_tf32", True, False), ("fp64", "fp64", True, False),
                 ("mixed_tf32_no_reuse", "mixed_tf32", False, False), ("mixed_tf32_batched", "mixed_tf32", True, True)]
     for name, prec, reuse, batched in variants:
@@ -700,6 +701,36 @@ def run_time_to_eps(M):
                                     "ratio": rates.reuse_cost_ratio(used, rt["ms_per_sample"][:L + 1])})
         prop["measured_gpu_time"].append({"eps": a["eps"], "ratio": a["gpu_seconds"] / b["gpu_seconds"]})
     out["prop1"] = prop
+    # plain MLMC (Monte Carlo normals, no recycling, eq. nopt counts) on the same
+    # problem, and the paper's speed-ups (Tab. speedup) in device time:
+    # S1 = MLMC / MLQMC, S2 = MLMC / MG-MLQMC, S3 = MLQMC / MG-MLQMC
+    c = dict(cfg)
+    c.update(precision="mixed_tf32", sampler="mc", R=1, reuse=False)
+    ctx = M.Context.from_config(c, max_samples=1 << 17)
+    rows = []
+    for eps in cfg["eps"] + [3e-4, 1e-4]:
+        r = ctx.estimate_mlmc(eps)
+        rows.append({"eps": eps, "seconds": r["wall_seconds"], "gpu_seconds": r["gpu_seconds"], "Q": r["Q"],
+                     "rmse_bound": float(np.sqrt(r["varQ"] + r["bias"] ** 2)), "L": r["L"],
+                     "rounds": r["rounds"], "N": r["N"][:r["L"] + 1], "run_status": r["run_status"]})
+    del ctx
+    out["mlmc_mixed_tf32"] = rows
+    # also in work (cells of the FMG hierarchy per sample, sum_{t<=l} n_t^2, times samples
+    # and replicates): the paper's one-sample-per-core cost, which device time on a
+    # latency-bound GPU does not follow
+    model = np.cumsum([(cfg["n0"] << t) ** 2 for t in range(cfg["n_levels"])])
+
+    def work(row, R):
+        return R * float(np.dot(row["N"], model[:len(row["N"])]))
+
+    sp = []
+    for m, q, g in zip(rows, out["mixed_tf32_no_reuse"], out["mixed_tf32"]):
+        wm, wq, wg = work(m, 1), work(q, cfg["R"]), work(g, cfg["R"])
+        sp.append({"eps": m["eps"], "S1": m["gpu_seconds"] / q["gpu_seconds"],
+                   "S2": m["gpu_seconds"] / g["gpu_seconds"], "S3": q["gpu_seconds"] / g["gpu_seconds"],
+                   "S1_work": wm / wq, "S2_work": wm / wg, "S3_work": wq / wg})
+    keys = ("S1", "S2", "S3", "S1_work", "S2_work", "S3_work")
+    out["speedups"] = {"per_eps": sp, "mean": {k: float(np.mean([x[k] for x in sp])) for k in keys}}
     return out
 
 
