@@ -63,6 +63,10 @@ typedef enum {
     MLQMC_SMOOTHER_WHOLE = 4   /* the whole grid of a sample in shared memory, residual/correction fused (n <= 64) */
 } mlqmc_smoother;
 typedef enum { MLQMC_SAMPLER_MC = 0, MLQMC_SAMPLER_LATTICE = 1 } mlqmc_sampler;
+typedef enum {
+    MLQMC_COV_SEPARABLE_EXP = 0, /* sigma^2 exp(-|x1-x1'|/l - |x2-x2'|/l), closed-form eigenpairs */
+    MLQMC_COV_MATERN = 1         /* Matern (eq. matern) with Nystrom eigenpairs (Sec. 5) */
+} mlqmc_covariance;
 
 /*
  * Problem statement (Sec. 1 eq. PDE; Sec. 6 set-up restated on a cell-centred
@@ -91,6 +95,17 @@ typedef enum { MLQMC_SAMPLER_MC = 0, MLQMC_SAMPLER_LATTICE = 1 } mlqmc_sampler;
  *  log2_nmax     lattice sequence length 2^log2_nmax (0..32).
  *  reuse         1: MG-ML(Q)MC, every FMG level feeds its difference (eq.
  *                MGMLMC); 0: plain ML(Q)MC, only the finest difference counts.
+ *  covariance    mlqmc_covariance (0 when the fields below are left zero).
+ *  MLQMC_COV_MATERN (eq. matern, variance sigma^2, correlation length
+ *  corr_len, smoothness matern_nu in {0.5, 1.5, 2.5}, where K_nu has a closed
+ *  form): the KL modes are the Nystrom eigenpairs (eqs. discrinteq,
+ *  matrixequation) on the cell centres of an nystrom_m x nystrom_m grid with
+ *  midpoint weights 1/nystrom_m^2 (2..128), as mlqmc_nystrom_modes returns
+ *  them: nystrom_theta (n_modes eigenvalues, positive) and nystrom_psi
+ *  (nystrom_m^2 x n_modes, node-major, the eigenfunctions at the nodes,
+ *  normalised to sum_q w_q psi_j(x_q)^2 = 1), host arrays copied at create
+ *  time. Every level's cell-centre values come from the Nystrom
+ *  interpolation formula (Sec. 5), evaluated once at create time in FP64.
  */
 typedef struct {
     int32_t n_levels;
@@ -112,6 +127,11 @@ typedef struct {
     const uint32_t* genvec;
     int32_t log2_nmax;
     int32_t reuse;
+    int32_t covariance;
+    int32_t nystrom_m;
+    double matern_nu;
+    const double* nystrom_theta;
+    const double* nystrom_psi;
 } mlqmc_problem;
 
 /*
@@ -163,6 +183,23 @@ typedef struct {
  * Errors: INVALID_ARG (bad sizes, even genvec entry, NULL out), OOM, CUDA.
  */
 mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples_per_call, mlqmc_ctx** out);
+
+/*
+ * Nystrom eigenpairs of the Matern covariance (Sec. 5, eqs. discrinteq and
+ * matrixequation): nodes x_q at the cell centres of an m x m grid on the unit
+ * square (q = k2*m + k1), weights w_q = 1/m^2, B = sqrt(W) Sigma sqrt(W) with
+ * Sigma_kq = C(x_k, x_q) (eq. matern, variance sigma^2), all eigenpairs of B
+ * by the dense symmetric eigensolver of cuSOLVER in FP64 on the current
+ * device, the s largest returned in descending order:
+ *  theta_out  host, s eigenvalues;
+ *  psi_out    host, m*m x s (node-major): psi_j(x_q) = v_qj / sqrt(w_q), so
+ *             that sum_q w_q psi_j(x_q) psi_i(x_q) = delta_ij.
+ * Within an eigenvalue of multiplicity > 1 the basis is the solver's; an
+ * eigenvector's sign is the solver's. nu in {0.5, 1.5, 2.5}; 2 <= m <= 128;
+ * 1 <= s <= m*m. Blocking. Errors: INVALID_ARG, OOM, CUDA (solver failure).
+ */
+mlqmc_status mlqmc_nystrom_modes(double nu, double corr_len, double sigma, int32_t m, int32_t s,
+                                 double* theta_out, double* psi_out);
 
 /* Release everything the context owns. NULL is a no-op. */
 void mlqmc_destroy(mlqmc_ctx* c);

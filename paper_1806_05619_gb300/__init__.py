@@ -43,6 +43,8 @@ class Problem(C.Structure):
         ("refine_rtol", C.c_double), ("refine_max_iter", C.c_int32), ("sampler", C.c_int32),
         ("seed", C.c_uint64), ("n_shifts", C.c_int32), ("pad2", C.c_int32),
         ("genvec", C.POINTER(C.c_uint32)), ("log2_nmax", C.c_int32), ("reuse", C.c_int32),
+        ("covariance", C.c_int32), ("nystrom_m", C.c_int32), ("matern_nu", C.c_double),
+        ("nystrom_theta", C.POINTER(C.c_double)), ("nystrom_psi", C.POINTER(C.c_double)),
     ]
 
 
@@ -86,6 +88,7 @@ def lib():
             L.mlqmc_sample_levels.argtypes = [vp, C.POINTER(Work), i32, vp, vp, vp]
             L.mlqmc_estimate.argtypes = [vp, C.c_double, C.POINTER(RunOpts), C.POINTER(Result)]
             L.mlqmc_estimate_mlmc.argtypes = [vp, C.c_double, C.POINTER(RunOpts), C.POINTER(Result)]
+            L.mlqmc_nystrom_modes.argtypes = [C.c_double, C.c_double, C.c_double, i32, i32, dp, dp]
             L.mlqmc_get_device_status.argtypes = [vp, vp]
             L.mlqmc_status_string.argtypes = [C.c_int]
             L.mlqmc_status_string.restype = C.c_char_p
@@ -109,6 +112,7 @@ def lib():
             L.mlqmc_launch_count.argtypes = [vp]
             L.mlqmc_launch_count.restype = i64
             for name in ["mlqmc_create", "mlqmc_sample_levels", "mlqmc_estimate", "mlqmc_estimate_mlmc",
+                         "mlqmc_nystrom_modes",
                          "mlqmc_get_device_status",
                          "mlqmc_cbc_genvec", "mlqmc_modes", "mlqmc_point_bits", "mlqmc_normals", "mlqmc_fields",
                          "mlqmc_sample_solution", "mlqmc_profile", "mlqmc_profile_read", "mlqmc_profile_work", "mlqmc_smoother_info", "mlqmc_set_smoother", "mlqmc_set_graphs",
@@ -160,6 +164,20 @@ def estimator_from_sums(N, sums, R: int, reuse: bool = True):
     return dict(Q=Q.value, varQ=V.value, Ybar=Yb, Vell=Vl)
 
 
+COVARIANCE = {"sep_exp": 0, "matern": 1}
+
+
+def nystrom_modes(nu, corr_len, sigma, m, s):
+    """Nystrom eigenpairs of the Matern covariance on the m x m midpoint nodes
+    (``mlqmc_nystrom_modes``): (theta (s,), psi (m*m, s)), descending."""
+    th = np.zeros(s)
+    ps = np.zeros(m * m * s)
+    dp = C.POINTER(C.c_double)
+    _check(lib().mlqmc_nystrom_modes(float(nu), float(corr_len), float(sigma), int(m), int(s), th.ctypes.data_as(dp),
+                                     ps.ctypes.data_as(dp)), "mlqmc_nystrom_modes")
+    return th, ps.reshape(m * m, s)
+
+
 def _ptr(t) -> Optional[int]:
     if t is None:
         return None
@@ -178,7 +196,11 @@ class Context:
 
     def __init__(self, n_levels, coarse_cells, n_modes, sigma=1.0, corr_len=0.3, qoi="mean", mu0=2, nu1=2,
                  nu2=2, precision="fp64", refine_rtol=0.0, refine_max_iter=60, sampler="lattice", seed=0,
-                 n_shifts=16, genvec=None, log2_nmax=20, reuse=True, max_samples=65536):
+                 n_shifts=16, genvec=None, log2_nmax=20, reuse=True, max_samples=65536, covariance="sep_exp",
+                 matern_nu=0.5, nystrom_m=0, nystrom_theta=None, nystrom_psi=None):
+        """covariance "matern": Matern covariance (eq. matern) with the Nystrom
+        eigenpairs nystrom_theta (n_modes) and nystrom_psi (nystrom_m^2 x n_modes,
+        node-major) as `nystrom_modes` returns them."""
         self.n_levels, self.n0, self.s, self.R = n_levels, coarse_cells, n_modes, n_shifts
         self.precision = precision
         zp = None
@@ -192,6 +214,16 @@ class Context:
                     qoi=QOI[qoi], mu0=mu0, nu1=nu1, nu2=nu2, precision=PRECISION[precision],
                     refine_rtol=refine_rtol, refine_max_iter=refine_max_iter, sampler=SAMPLER[sampler],
                     seed=seed, n_shifts=n_shifts, genvec=zp, log2_nmax=log2_nmax, reuse=1 if reuse else 0)
+        if covariance == "matern":
+            th = np.ascontiguousarray(nystrom_theta, dtype=np.float64)
+            ps = np.ascontiguousarray(nystrom_psi, dtype=np.float64)
+            if th.size != n_modes or ps.size != nystrom_m * nystrom_m * n_modes:
+                raise ValueError("Nystrom modes: n_modes eigenvalues and nystrom_m^2 x n_modes nodal values")
+            p.covariance, p.nystrom_m, p.matern_nu = COVARIANCE["matern"], int(nystrom_m), float(matern_nu)
+            p.nystrom_theta = th.ctypes.data_as(C.POINTER(C.c_double))
+            p.nystrom_psi = ps.ctypes.data_as(C.POINTER(C.c_double))
+        elif covariance != "sep_exp":
+            raise ValueError(f"unknown covariance {covariance!r}")
         h = C.c_void_p()
         _check(lib().mlqmc_create(C.byref(p), int(max_samples), C.byref(h)), "mlqmc_create")
         self.h = h

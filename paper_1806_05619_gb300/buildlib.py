@@ -11,7 +11,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmlqmc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["mlqmc_cuda.cu", "kl_tcgen05.cu", "rbgs_stream.cu", "rbgs_tma.cu", "rbgs_whole.cu", "mlqmc_host.cpp"]
+SOURCES = ["mlqmc_cuda.cu", "kl_tcgen05.cu", "rbgs_stream.cu", "rbgs_tma.cu", "rbgs_whole.cu", "matern_nystrom.cu",
+           "mlqmc_host.cpp"]
 
 
 def _nvcc():
@@ -39,7 +40,7 @@ def build(verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call([_nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-lgomp", "-lcudart"])
+    subprocess.check_call([_nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-lgomp", "-lcudart", "-lcusolver"])
     os.replace(tmp, LIB)
     return LIB
 

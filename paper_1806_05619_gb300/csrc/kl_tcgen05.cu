@@ -338,6 +338,30 @@ __global__ void kl_build_psi_bf16x3(const double* __restrict__ psi1d, int n, int
     }
 }
 
+// Psi operand from dense FP64 modes (Matern, Nystrom): src[p * s + m] -> TF32
+// row p, or the [hi | hi | lo] split rows; zero for m >= s.
+__global__ void kl_build_psi_dense(const double* __restrict__ src, int64_t M, int s, int kp, int split,
+                                   void* __restrict__ out)
+{
+    const int64_t total = M * kp;
+    for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int m = static_cast<int>(idx % kp);
+        const int64_t p = idx / kp;
+        const double v = m < s ? src[p * s + m] : 0.0;
+        if (!split) {
+            static_cast<float*>(out)[idx] = m < s ? to_tf32(v) : 0.0f;
+        } else {
+            __nv_bfloat16 hi = __float2bfloat16_rn(0.0f), lo = hi;
+            if (m < s) split_bf16(v, hi, lo);
+            __nv_bfloat16* row = static_cast<__nv_bfloat16*>(out) + p * 3 * kp;
+            row[m] = hi;
+            row[kp + m] = hi;
+            row[2 * kp + m] = lo;
+        }
+    }
+}
+
 // C3[i][j]: [hi | lo | hi] of sqrt(theta_m) y_{canon_i, m}, zero for m >= s.
 __global__ void kl_build_c_bf16x3(const double* __restrict__ Y, const int* __restrict__ canon, int count, int s, int kp,
                                   const double* __restrict__ sqrt_theta, __nv_bfloat16* __restrict__ out)
@@ -412,6 +436,15 @@ int kdim_for(Variant v, int s)
 size_t row_bytes(Variant v, int s)
 {
     return static_cast<size_t>(kdim_for(v, s)) * (v == Variant::TF32 ? 4 : 2);
+}
+
+bool build_psi_dense(Variant v, const double* d_modes, int64_t M, int s, void* d_out, cudaStream_t st)
+{
+    const int kp = v == Variant::TF32 ? kpad_for(s) : kdim_for(v, s) / 3;
+    const int64_t total = M * kp;
+    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 64)));
+    kl_build_psi_dense<<<grid, 256, 0, st>>>(d_modes, M, s, kp, v == Variant::TF32 ? 0 : 1, d_out);
+    return cudaGetLastError() == cudaSuccess;
 }
 
 bool build_psi(Variant v, const double* d_psi1d, int n, int s, const int* d_ma, const int* d_mb, void* d_out,

@@ -25,6 +25,9 @@ int tile_samples();                     // samples per CTA tile
 bool build_psi(Variant v, const double* d_psi1d, int n, int s, const int* d_ma, const int* d_mb, void* d_out,
                cudaStream_t st);
 
+// Psi of one level from dense FP64 modes (M cells x s, cell-major), same operand layout.
+bool build_psi_dense(Variant v, const double* d_modes, int64_t M, int s, void* d_out, cudaStream_t st);
+
 // C rows i < count: sqrt(theta_m) y_m of the sample whose normals are row canon[i] of Y (canon NULL: row i).
 bool build_c(Variant v, const double* d_Y, const int* d_canon, int count, int s, const double* d_sqrt_theta,
              void* d_out, cudaStream_t st);

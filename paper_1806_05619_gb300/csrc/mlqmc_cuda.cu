@@ -28,6 +28,7 @@
 #include "rbgs_stream.h"
 #include "rbgs_tma.h"
 #include "rbgs_whole.h"
+#include "matern_nystrom.h"
 
 using namespace mlqmc_dev;
 
@@ -432,6 +433,50 @@ __global__ void kb_synth_z(FmgArgs A, int t, int B)
         T z = T(0);
         for (int a = 0; a < A.Ka; ++a) z += psi[a * n + i1] * G[a * n + i2];
         at<T>(A.lv[t].k, i)[p] = expT(z);
+    }
+}
+
+// Matern modes: z(x_p) = sum_j Psi_t(x_p, j) sqrt(theta_j) y_j (eq.
+// truncatedKL with the level's interpolated Nystrom modes), k = exp(z), the
+// sum in FP64. A thread takes one cell and kG samples, so each row of Psi_t
+// is read once per kG samples; the kG samples' coefficients sqrt(theta_j) y_j
+// are staged in shared memory, kJ modes at a time.
+constexpr int kDenseG = 8, kDenseJ = 512;
+template <typename T>
+__global__ void __launch_bounds__(256) kb_synth_dense(FmgArgs A, int t, int B, const double* __restrict__ psi, int s,
+                                                      const double* __restrict__ sq)
+{
+    __shared__ double cs[kDenseG][kDenseJ];
+    const int n = A.lv[t].n;
+    const int ncell = n * n;
+    const int i0 = blockIdx.y * kDenseG;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[kDenseG];
+#pragma unroll
+    for (int g = 0; g < kDenseG; ++g) acc[g] = 0.0;
+    for (int j0 = 0; j0 < s; j0 += kDenseJ) {
+        const int jn = min(kDenseJ, s - j0);
+        for (int e = threadIdx.x; e < kDenseG * kDenseJ; e += blockDim.x) {
+            const int g = e / kDenseJ, jj = e - g * kDenseJ;
+            const int i = i0 + g;
+            cs[g][jj] = (i < B && jj < jn) ? sq[j0 + jj] * A.Y[static_cast<size_t>(A.samples[i].canon) * A.s + j0 + jj]
+                                           : 0.0;
+        }
+        __syncthreads();
+        if (p < ncell) {
+            const double* row = psi + static_cast<size_t>(p) * s + j0;
+            for (int jj = 0; jj < jn; ++jj) {
+                const double v = row[jj];
+#pragma unroll
+                for (int g = 0; g < kDenseG; ++g) acc[g] = fma(v, cs[g][jj], acc[g]);
+            }
+        }
+        __syncthreads();
+    }
+    if (p < ncell) {
+#pragma unroll
+        for (int g = 0; g < kDenseG; ++g)
+            if (i0 + g < B) at<T>(A.lv[t].k, i0 + g)[p] = expT(static_cast<T>(acc[g]));
     }
 }
 
@@ -1230,7 +1275,15 @@ mlqmc_status synth_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cudaStr
                 return MLQMC_ERR_CUDA;
         }
     }
-    if (!uses_tc(c, t) || sizeof(T) != 4) {
+    if (c->matern && (!uses_tc(c, t) || sizeof(T) != 4)) {
+        const double M = static_cast<double>(n * n), sm = c->p.n_modes;
+        Timed tm(c, kProfSynth, st,
+                 work_of<T>(8.0 * M * sm * std::ceil(B / static_cast<double>(kDenseG)) + sizeof(T) * M * B,
+                            2.0 * M * sm * B));
+        const dim3 grid(static_cast<unsigned>((n * n + 255) / 256), static_cast<unsigned>((B + kDenseG - 1) / kDenseG));
+        kb_synth_dense<T><<<grid, 256, 0, st>>>(A, t, B, c->d_psi_dense + c->dense_off[t], c->p.n_modes,
+                                               c->d_sqrt_theta);
+    } else if (!uses_tc(c, t) || sizeof(T) != 4) {
         const double M = static_cast<double>(n * n), Ka = c->Ka, sm = c->p.n_modes;
         {
             Timed tm(c, kProfSynth, st, work_of<T>(B * (8.0 * sm + sizeof(T) * Ka * n), B * 2.0 * sm * n));
@@ -1776,6 +1829,7 @@ void free_ctx(mlqmc_ctx* c)
     cudaFree(c->d_queue);
     for (auto& P : c->pools) cudaFree(P.mem);
     if (c->staged) cudaEventDestroy(c->staged);
+    cudaFree(c->d_psi_dense);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->side) cudaStreamDestroy(c->side);
@@ -1811,6 +1865,14 @@ mlqmc_status check_problem(const mlqmc_problem* p)
     if (p->sampler != MLQMC_SAMPLER_MC && p->sampler != MLQMC_SAMPLER_LATTICE) return MLQMC_ERR_INVALID_ARG;
     if (p->n_shifts < 1 || p->n_shifts > 4096) return MLQMC_ERR_INVALID_ARG;
     if (p->reuse != 0 && p->reuse != 1) return MLQMC_ERR_INVALID_ARG;
+    if (p->covariance != MLQMC_COV_SEPARABLE_EXP && p->covariance != MLQMC_COV_MATERN) return MLQMC_ERR_INVALID_ARG;
+    if (p->covariance == MLQMC_COV_MATERN) {
+        if (!mlqmc_matern::supported_nu(p->matern_nu) || p->nystrom_m < 2 || p->nystrom_m > 128 ||
+            !p->nystrom_theta || !p->nystrom_psi || p->n_modes > p->nystrom_m * p->nystrom_m)
+            return MLQMC_ERR_INVALID_ARG;
+        for (int j = 0; j < p->n_modes; ++j)
+            if (!(p->nystrom_theta[j] > 0.0)) return MLQMC_ERR_INVALID_ARG;
+    }
     if (p->sampler == MLQMC_SAMPLER_LATTICE) {
         if (!p->genvec || p->log2_nmax < 0 || p->log2_nmax > 32) return MLQMC_ERR_INVALID_ARG;
         for (int j = 0; j < p->n_modes; ++j)
@@ -1819,42 +1881,11 @@ mlqmc_status check_problem(const mlqmc_problem* p)
     return MLQMC_OK;
 }
 
-// Samples per level count of a rank-ordered range: B[t] = #{level >= t}.
-void count_levels(const SampleDesc* s, int count, int n_levels, int* Bt, int* Lmax)
+// Separable exponential covariance: the s largest products of the closed-form
+// 1D eigenpairs (Sec. 5), each level's 1D tables and the modes grouped by
+// their first index for the separable synthesis.
+mlqmc_status setup_separable(mlqmc_ctx* c, const mlqmc_problem* p)
 {
-    for (int t = 0; t < n_levels; ++t) Bt[t] = 0;
-    *Lmax = -1;
-    for (int q = 0; q < count; ++q) {
-        for (int t = 0; t <= s[q].level; ++t) Bt[t]++;
-        *Lmax = std::max(*Lmax, s[q].level);
-    }
-}
-
-}  // namespace
-
-// ---------------------------------------------------------------------------
-// C ABI
-// ---------------------------------------------------------------------------
-extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples_per_call, mlqmc_ctx** out)
-{
-    if (!out) return MLQMC_ERR_INVALID_ARG;
-    *out = nullptr;
-    mlqmc_status st = check_problem(p);
-    if (st != MLQMC_OK) return st;
-    if (max_samples_per_call < 0) return MLQMC_ERR_INVALID_ARG;
-    mlqmc_ctx* c = new (std::nothrow) mlqmc_ctx();
-    if (!c) return MLQMC_ERR_OOM;
-    c->p = *p;
-    if (!ok(cudaGetDevice(&c->device)) ||
-        !ok(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device))) {
-        free_ctx(c);
-        return MLQMC_ERR_CUDA;
-    }
-    if (p->sampler == MLQMC_SAMPLER_LATTICE) c->z.assign(p->genvec, p->genvec + p->n_modes);
-    else c->z.assign(p->n_modes, 1u);
-    c->p.genvec = nullptr;
-
-    // KL tables (Sec. 5): modes, 1D eigenpairs, per-level psi tables
     c->modes = mlqmc::select_modes(p->corr_len, p->sigma, p->n_modes);
     const int K1 = c->modes.K1;
     c->eig = mlqmc::kl_eigen_1d(p->corr_len, K1);
@@ -1894,9 +1925,95 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
                 dev_upload(&c->d_ma, c->modes.a.data(), c->modes.a.size()) &&
                 dev_upload(&c->d_mb, c->modes.b.data(), c->modes.b.size()) &&
                 dev_upload(&c->d_sqrt_theta, sq.data(), sq.size());
+    return good ? MLQMC_OK : MLQMC_ERR_OOM;
+}
+
+// Matern covariance: the caller's Nystrom eigenpairs at the nodes, every
+// level's modes at its cell centres by the Nystrom interpolation formula
+// (Sec. 5), FP64 on the device, once.
+mlqmc_status setup_matern(mlqmc_ctx* c, const mlqmc_problem* p)
+{
+    const int s = p->n_modes, m = p->nystrom_m, M = m * m;
+    c->modes.theta.assign(p->nystrom_theta, p->nystrom_theta + s);
+    c->modes.a.assign(s, -1);
+    c->modes.b.assign(s, -1);
+    c->modes.K1 = 0;
+    c->Ka = 1;
+    std::vector<double> wpsi(static_cast<size_t>(M) * s), sq(s);
+    for (int q = 0; q < M; ++q)
+        for (int j = 0; j < s; ++j)
+            wpsi[static_cast<size_t>(q) * s + j] = p->nystrom_psi[static_cast<size_t>(q) * s + j] / M / p->nystrom_theta[j];
+    for (int j = 0; j < s; ++j) sq[j] = std::sqrt(p->nystrom_theta[j]);
+    size_t total = 0;
+    for (int t = 0; t < p->n_levels; ++t) {
+        const size_t n = static_cast<size_t>(p->coarse_cells) << t;
+        c->dense_off[t] = total;
+        total += n * n * s;
+    }
+    const std::vector<int> zeros(s, 0), gstart(2, 0);
+    const double one = 0.0;
+    const float one32 = 0.0f;
+    double* d_wpsi = nullptr;
+    bool good = dev_upload(&d_wpsi, wpsi.data(), wpsi.size()) && ok(cudaMalloc(&c->d_psi_dense, total * sizeof(double))) &&
+                dev_upload(&c->d_psi, &one, 1) && dev_upload(&c->d_psi32, &one32, 1) &&
+                dev_upload(&c->d_grp_start, gstart.data(), gstart.size()) &&
+                dev_upload(&c->d_z, c->z.data(), c->z.size()) && dev_upload(&c->d_ma, zeros.data(), zeros.size()) &&
+                dev_upload(&c->d_mb, zeros.data(), zeros.size()) && dev_upload(&c->d_sqrt_theta, sq.data(), sq.size());
     if (!good) {
-        free_ctx(c);
+        cudaFree(d_wpsi);
         return MLQMC_ERR_OOM;
+    }
+    for (int t = 0; good && t < p->n_levels; ++t)
+        good = mlqmc_matern::interpolate(p->matern_nu, p->corr_len, p->sigma, m, s, d_wpsi,
+                                         p->coarse_cells << t, c->d_psi_dense + c->dense_off[t], 0);
+    good = good && ok(cudaDeviceSynchronize());
+    cudaFree(d_wpsi);
+    return good ? MLQMC_OK : MLQMC_ERR_CUDA;
+}
+
+// Samples per level count of a rank-ordered range: B[t] = #{level >= t}.
+void count_levels(const SampleDesc* s, int count, int n_levels, int* Bt, int* Lmax)
+{
+    for (int t = 0; t < n_levels; ++t) Bt[t] = 0;
+    *Lmax = -1;
+    for (int q = 0; q < count; ++q) {
+        for (int t = 0; t <= s[q].level; ++t) Bt[t]++;
+        *Lmax = std::max(*Lmax, s[q].level);
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples_per_call, mlqmc_ctx** out)
+{
+    if (!out) return MLQMC_ERR_INVALID_ARG;
+    *out = nullptr;
+    mlqmc_status st = check_problem(p);
+    if (st != MLQMC_OK) return st;
+    if (max_samples_per_call < 0) return MLQMC_ERR_INVALID_ARG;
+    mlqmc_ctx* c = new (std::nothrow) mlqmc_ctx();
+    if (!c) return MLQMC_ERR_OOM;
+    c->p = *p;
+    if (!ok(cudaGetDevice(&c->device)) ||
+        !ok(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device))) {
+        free_ctx(c);
+        return MLQMC_ERR_CUDA;
+    }
+    if (p->sampler == MLQMC_SAMPLER_LATTICE) c->z.assign(p->genvec, p->genvec + p->n_modes);
+    else c->z.assign(p->n_modes, 1u);
+    c->p.genvec = nullptr;
+
+    // KL tables (Sec. 5)
+    c->matern = p->covariance == MLQMC_COV_MATERN;
+    c->p.nystrom_theta = nullptr;
+    c->p.nystrom_psi = nullptr;
+    mlqmc_status kst = c->matern ? setup_matern(c, p) : setup_separable(c, p);
+    if (kst != MLQMC_OK) {
+        free_ctx(c);
+        return kst;
     }
 
     // per-chunk buffers
@@ -1904,7 +2021,7 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
     const size_t ms = static_cast<size_t>(c->max_samples);
     const size_t N0 = static_cast<size_t>(p->coarse_cells) * p->coarse_cells;
     c->chol_stride = align256(sizeof(double) * N0 * (p->coarse_cells + 1));
-    good = ok(cudaMalloc(&c->d_samples, ms * sizeof(SampleDesc))) &&
+    bool good = ok(cudaMalloc(&c->d_samples, ms * sizeof(SampleDesc))) &&
            ok(cudaMalloc(&c->d_Y, ms * p->n_modes * sizeof(double))) &&
            ok(cudaMalloc(&c->d_F, ms * p->n_levels * sizeof(double))) &&
            ok(cudaMalloc(&c->d_chol, ms * c->chol_stride)) && ok(cudaMalloc(&c->d_chol32, ms * c->chol_stride / 2)) &&
@@ -1940,8 +2057,10 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
             const int n = p->coarse_cells << t;
             if ((n * n) % 128 != 0) continue;
             good = ok(cudaMalloc(&c->d_psi_tc[t], static_cast<size_t>(n) * n * rb)) &&
-                   mlqmc_kl::build_psi(c->kl_variant, c->d_psi + c->psi_off[t], n, p->n_modes, c->d_ma, c->d_mb,
-                                       c->d_psi_tc[t], 0) &&
+                   (c->matern ? mlqmc_kl::build_psi_dense(c->kl_variant, c->d_psi_dense + c->dense_off[t],
+                                                          static_cast<int64_t>(n) * n, p->n_modes, c->d_psi_tc[t], 0)
+                              : mlqmc_kl::build_psi(c->kl_variant, c->d_psi + c->psi_off[t], n, p->n_modes, c->d_ma,
+                                                    c->d_mb, c->d_psi_tc[t], 0)) &&
                    mlqmc_kl::make_maps(c->kl_variant, c->d_psi_tc[t], n * n, c->d_C, static_cast<int>(ms), p->n_modes,
                                        &c->kl_maps[t]);
         }

@@ -95,6 +95,11 @@ struct mlqmc_ctx {
     int* d_ma = nullptr;               // modes in order: first index a
     int* d_mb = nullptr;               // second index b
     double* d_sqrt_theta = nullptr;    // sqrt(theta_m)
+    // Matern covariance: every level's modes at its cell centres, FP64,
+    // cell-major (n_t^2 x s), level t at d_psi_dense + dense_off[t]
+    bool matern = false;
+    double* d_psi_dense = nullptr;
+    size_t dense_off[MLQMC_MAX_LEVELS] = {};
 
     // tensor-core KL (mixed TF32 form): Psi per level with >= 128 cells, C per chunk
     bool kl_tc = false;
