@@ -296,7 +296,11 @@ mlqmc_status mlqmc_modes(const mlqmc_ctx* c, int32_t* a, int32_t* b, double* the
 mlqmc_status mlqmc_point_bits(mlqmc_ctx* c, int32_t level, int32_t r, int64_t n_begin,
                               int32_t count, uint64_t* d_bits, void* stream);
 
-/* Normals y = Phi^{-1}(u) for the same samples: d_y[i*s + j], FP64, device. */
+/* Normals y = Phi^{-1}(u) for the same samples: d_y[i*s + j], device doubles;
+ * u = ((bits >> 11) + 1/2) 2^-53. FP64 form: Phi^{-1} in FP64. Mixed forms
+ * (whose normals only enter FP32 and tensor-core arithmetic): Phi^{-1} in
+ * FP32 of u (u < 1/2) or of 1 - u (negated), so both tails keep float
+ * resolution; these are the normals the mixed forms' samples use. */
 mlqmc_status mlqmc_normals(mlqmc_ctx* c, int32_t level, int32_t r, int64_t n_begin,
                            int32_t count, double* d_y, void* stream);
 

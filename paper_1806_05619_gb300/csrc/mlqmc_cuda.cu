@@ -73,8 +73,12 @@ __device__ __forceinline__ uint64_t point_bits(int sampler, uint64_t seed, const
                         0x4D43524Eu, seed, j);
 }
 
+// Points and normals y = Phi^-1(u) (Sec. 3.2). fp32 (mixed forms, whose
+// normals only enter FP32 and tensor-core arithmetic): Phi^-1 in FP32, each
+// half of (0, 1) taken from its own end (1 - u formed exactly in integers),
+// so both tails keep float resolution; the FP64 form uses FP64.
 __global__ void k_points(const SampleDesc* __restrict__ smp, int count, int s, int sampler, uint64_t seed,
-                         const uint32_t* __restrict__ z, double* __restrict__ Y, uint64_t* __restrict__ bits)
+                         const uint32_t* __restrict__ z, double* __restrict__ Y, uint64_t* __restrict__ bits, int fp32)
 {
     const int64_t total = static_cast<int64_t>(count) * s;
     for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
@@ -85,7 +89,13 @@ __global__ void k_points(const SampleDesc* __restrict__ smp, int count, int s, i
         const uint64_t x = point_bits(sampler, seed, z, d.level, d.r, d.n, j);
         const size_t o = static_cast<size_t>(d.canon) * s + j;
         if (bits) bits[o] = x;
-        if (Y) {
+        if (Y && fp32) {
+            const uint64_t k = x >> 11;  // u = (k + 1/2) 2^-53
+            const bool lo = k < (1ull << 52);
+            const uint64_t kk = lo ? k : ((1ull << 53) - 1ull) - k;  // 1 - u = (kk + 1/2) 2^-53 in the upper half
+            const float y = normcdfinvf(fmaf(__ull2float_rn(kk), 0x1p-53f, 0x1p-54f));
+            Y[o] = widen(lo ? y : -y);
+        } else if (Y) {
             const double u = (static_cast<double>(x >> 11) + 0.5) * 0x1.0p-53;  // open (0,1)
             Y[o] = normcdfinv(u);
         }
@@ -1213,7 +1223,8 @@ mlqmc_status launch_points(mlqmc_ctx* c, const SampleDesc* d_s, int count, doubl
 {
     const int64_t total = static_cast<int64_t>(count) * c->p.n_modes;
     Timed tm(c, kProfPoints, st, work_of<double>(8.0 * total + sizeof(SampleDesc) * count, 0.0));
-    k_points<<<grid_for(c, total), 256, 0, st>>>(d_s, count, c->p.n_modes, c->p.sampler, c->p.seed, c->d_z, Y, bits);
+    k_points<<<grid_for(c, total), 256, 0, st>>>(d_s, count, c->p.n_modes, c->p.sampler, c->p.seed, c->d_z, Y, bits,
+                                                 is_mixed(c->p) ? 1 : 0);
     return last_error();
 }
 
