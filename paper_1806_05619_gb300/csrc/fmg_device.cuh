@@ -49,6 +49,7 @@ struct FmgArgs {
     const SampleDesc* samples;  // rank order: finest level descending
     int n_samples;
     const double* Y;  // normals, s per sample, indexed by canon
+    const float* c32;  // mixed forms: sqrt(theta_m) y_m rounded to FP32, s per sample in rank order
     int s;
     int n0;
     int n_levels;
@@ -204,6 +205,20 @@ __device__ __forceinline__ double rcp64(double d)
     r = fma(r, e, r);
     e = fma(-d, r, 1.0);
     return fma(r, e, r);
+}
+
+// 1/sqrt(d) for a positive normal d in FP64: the hardware's estimate refined
+// by two Newton-Raphson steps y <- y + (y/2)(1 - d y^2), each squaring the
+// relative error, within about one ulp; eight FP64 operations in place of a
+// square root and a division.
+__device__ __forceinline__ double rsqrt64(double d)
+{
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+    double e = fma(-d * y, y, 1.0);
+    y = fma(0.5 * y, e, y);
+    e = fma(-d * y, y, 1.0);
+    return fma(0.5 * y, e, y);
 }
 
 __device__ __forceinline__ float expT(float x) { return expf(x); }

@@ -139,17 +139,17 @@ __global__ void kb_level0(FmgArgs A, int B)
         const Lv<T> L0 = view<T>(A, 0, i);
         for (int j = 0; j < N; ++j) {
             const int j1 = j % n0, j2 = j / n0;
-            double d = static_cast<double>(L0.kx[j2 * kx_pitch(n0) + j1]) + static_cast<double>(L0.kx[j2 * kx_pitch(n0) + j1 + 1]) +
-                       static_cast<double>(L0.ky[j2 * n0 + j1]) + static_cast<double>(L0.ky[(j2 + 1) * n0 + j1]);
+            double d = widen(L0.kx[j2 * kx_pitch(n0) + j1]) + widen(L0.kx[j2 * kx_pitch(n0) + j1 + 1]) +
+                       widen(L0.ky[j2 * n0 + j1]) + widen(L0.ky[(j2 + 1) * n0 + j1]);
             for (int q = 1; q <= n0 && q <= j; ++q) {
                 const double l = fac[static_cast<size_t>(j * W + q) * cs + i];
                 d -= l * l;
             }
-            const double rl = 1.0 / sqrt(d);
+            const double rl = rsqrt64(d);
             fac[static_cast<size_t>(j * W) * cs + i] = rl;
             for (int l = 1; l <= n0 && j + l < N; ++l) {
                 const int r = j + l;
-                double a = static_cast<double>(band_a(L0.kx, L0.ky, n0, r, l));
+                double a = widen(band_a(L0.kx, L0.ky, n0, r, l));
                 for (int tt = (r - n0 > 0 ? r - n0 : 0); tt < j; ++tt)
                     a -= fac[static_cast<size_t>(r * W + (r - tt)) * cs + i] * fac[static_cast<size_t>(j * W + (j - tt)) * cs + i];
                 fac[static_cast<size_t>(r * W + l) * cs + i] = a * rl;
@@ -255,16 +255,15 @@ __global__ void __launch_bounds__(64) kb_level0_fixed(FmgArgs A, int B)
             const int s0 = j % W;
             auto slot = [&](int l) { return s0 + l >= W ? s0 + l - W : s0 + l; };  // slot of row j + l
             const int j1 = j % NC, j2 = j / NC;
-            double d = static_cast<double>(L0.kx[j2 * kx_pitch(NC) + j1]) +
-                       static_cast<double>(L0.kx[j2 * kx_pitch(NC) + j1 + 1]) +
-                       static_cast<double>(L0.ky[j2 * NC + j1]) + static_cast<double>(L0.ky[(j2 + 1) * NC + j1]);
+            double d = widen(L0.kx[j2 * kx_pitch(NC) + j1]) + widen(L0.kx[j2 * kx_pitch(NC) + j1 + 1]) +
+                       widen(L0.ky[j2 * NC + j1]) + widen(L0.ky[(j2 + 1) * NC + j1]);
 #pragma unroll
             for (int q = 1; q <= NC; ++q) {
                 if (!FULL && q > j) break;
                 const double l = Rs(s0, q);
                 d -= l * l;
             }
-            const double rl = 1.0 / sqrt(d);
+            const double rl = rsqrt64(d);
             Rs(s0, 0) = rl;
             double v = h2;  // forward substitution, f = 1
 #pragma unroll
@@ -277,13 +276,13 @@ __global__ void __launch_bounds__(64) kb_level0_fixed(FmgArgs A, int B)
             for (int e = 0; e <= NC; ++e) {
                 if (!FULL && e > j) break;
                 fac[static_cast<size_t>(j * W + e) * cs + i] = Rs(s0, e);
-                if constexpr (MX) f32[static_cast<size_t>(j * W + e) * cs + i] = static_cast<float>(Rs(s0, e));
+                if constexpr (MX) f32[static_cast<size_t>(j * W + e) * cs + i] = narrow(Rs(s0, e));
             }
 #pragma unroll
             for (int l = 1; l <= NC; ++l) {
                 const int r = j + l;
                 if (r >= N) break;
-                double a = static_cast<double>(band_a(L0.kx, L0.ky, NC, r, l));
+                double a = widen(band_a(L0.kx, L0.ky, NC, r, l));
                 const int sr = slot(l);
                 if constexpr (FULL) {
 #pragma unroll
@@ -307,7 +306,7 @@ __global__ void __launch_bounds__(64) kb_level0_fixed(FmgArgs A, int B)
         for (int r = 0; r < N; ++r) x[r] = Y(r);
         if constexpr (MX) {
             float* u32 = reinterpret_cast<float*>(L0.u);  // FP32 copy for the first FMG interpolation
-            for (int r = 0; r < N; ++r) u32[r] = static_cast<float>(Y(r));
+            for (int r = 0; r < N; ++r) u32[r] = narrow(Y(r));
         }
         double F0;
         if (A.qoi == MLQMC_QOI_MEAN) {
@@ -417,12 +416,31 @@ __global__ void kb_synth_G(FmgArgs A, int t, int B)
         const int rem = static_cast<int>(idx - i * per);
         const int a = rem / n;
         const int i2 = rem - a * n;
-        const double* y = A.Y + static_cast<size_t>(A.samples[i].canon) * A.s;
         T acc = T(0);
         const int g1 = A.grp_start[a + 1];
-        for (int g = A.grp_start[a]; g < g1; ++g)
-            acc += static_cast<T>(A.grp_sqrt[g] * y[A.grp_m[g]]) * psi[A.grp_b[g] * n + i2];
+        if constexpr (sizeof(T) == 4) {
+            // FP32 coefficients sqrt(theta_m) y_m from k_coef32 (the same rounded products)
+            const float* cf = A.c32 + static_cast<size_t>(i) * A.s;
+            for (int g = A.grp_start[a]; g < g1; ++g) acc += cf[A.grp_m[g]] * psi[A.grp_b[g] * n + i2];
+        } else {
+            const double* y = A.Y + static_cast<size_t>(A.samples[i].canon) * A.s;
+            for (int g = A.grp_start[a]; g < g1; ++g) acc += (A.grp_sqrt[g] * y[A.grp_m[g]]) * psi[A.grp_b[g] * n + i2];
+        }
         at<T>(A.lv[t].G, i)[rem] = acc;
+    }
+}
+
+// Mixed forms: c32[i][m] = sqrt(theta_m) y_m of sample i (rank order) rounded
+// to FP32, once per launch of the FP32 separable synthesis, so that its inner
+// loop issues no FP64 operation.
+__global__ void k_coef32(FmgArgs A, int B, const double* __restrict__ sq, float* __restrict__ out)
+{
+    const int64_t total = static_cast<int64_t>(B) * A.s;
+    for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int i = static_cast<int>(idx / A.s);
+        const int m = static_cast<int>(idx - static_cast<int64_t>(i) * A.s);
+        out[idx] = narrow(sq[m] * A.Y[static_cast<size_t>(A.samples[i].canon) * A.s + m]);
     }
 }
 
@@ -1045,6 +1063,7 @@ FmgArgs base_args(mlqmc_ctx* c)
     std::memset(&A, 0, sizeof(A));
     A.samples = c->d_samples;
     A.Y = c->d_Y;
+    A.c32 = c->d_c32;
     A.s = c->p.n_modes;
     A.n0 = c->p.coarse_cells;
     A.n_levels = c->p.n_levels;
@@ -1296,8 +1315,15 @@ mlqmc_status synth_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cudaStr
                                                c->d_sqrt_theta);
     } else if (!uses_tc(c, t) || sizeof(T) != 4) {
         const double M = static_cast<double>(n * n), Ka = c->Ka, sm = c->p.n_modes;
+        if constexpr (sizeof(T) == 4) {
+            if (!c->c32_ready) {
+                Timed tm(c, kProfSynth, st, work_of<double>(B * 12.0 * sm, B * sm));
+                k_coef32<<<grid_for(c, static_cast<int64_t>(B) * c->p.n_modes), 256, 0, st>>>(A, B, c->d_sqrt_theta,
+                                                                                           c->d_c32);
+            }
+        }
         {
-            Timed tm(c, kProfSynth, st, work_of<T>(B * (8.0 * sm + sizeof(T) * Ka * n), B * 2.0 * sm * n));
+            Timed tm(c, kProfSynth, st, work_of<T>(B * (sizeof(T) * sm + sizeof(T) * Ka * n), B * 2.0 * sm * n));
             kb_synth_G<T><<<grid_for(c, B * c->Ka * n), 256, 0, st>>>(A, t, B);
         }
         {
@@ -1766,17 +1792,28 @@ mlqmc_status run_chunk(mlqmc_ctx* c, int count, const int* Bt, int Lmax, double*
     if (s != MLQMC_OK) return s;
     s = build_c(c, count, st);
     if (s != MLQMC_OK) return s;
+    // mixed forms, separable modes: FP32 coefficients of all the chunk's
+    // samples once, before both streams' SIMT syntheses read them
+    if (is_mixed(p) && !c->matern) {
+        Timed tm(c, kProfSynth, st, work_of<double>(count * 12.0 * p.n_modes, count * 1.0 * p.n_modes));
+        k_coef32<<<grid_for(c, static_cast<int64_t>(count) * p.n_modes), 256, 0, st>>>(A, count, c->d_sqrt_theta,
+                                                                                        c->d_c32);
+        c->c32_ready = true;
+    }
     // level 0 (field, faces, factorisation and exact solve: latency-bound,
     // one thread per sample) on the side stream while the main stream
     // synthesises levels 1..Lmax; joined before the FMG stages
-    if (!ok(cudaEventRecord(c->ev_fork, st)) || !ok(cudaStreamWaitEvent(c->side, c->ev_fork, 0)))
+    if (!ok(cudaEventRecord(c->ev_fork, st)) || !ok(cudaStreamWaitEvent(c->side, c->ev_fork, 0))) {
+        c->c32_ready = false;
         return MLQMC_ERR_CUDA;
+    }
     s = is_mixed(p) ? synth_batched<float>(c, A, 0, Bt[0], c->side) : synth_batched<double>(c, A, 0, Bt[0], c->side);
     if (s == MLQMC_OK) s = launch_level0(c, A, Bt[0], c->side);
     if (!ok(cudaEventRecord(c->ev_join, c->side))) s = MLQMC_ERR_CUDA;
     for (int t = 1; s == MLQMC_OK && t <= Lmax && Bt[t] > 0; ++t)
         s = is_mixed(p) ? synth_batched<float>(c, A, t, Bt[t], st) : synth_batched<double>(c, A, t, Bt[t], st);
     if (!ok(cudaStreamWaitEvent(st, c->ev_join, 0)) && s == MLQMC_OK) s = MLQMC_ERR_CUDA;
+    c->c32_ready = false;
     if (s != MLQMC_OK) return s;
     if (d_usol) {
         const int64_t n0 = p.coarse_cells;
@@ -1841,6 +1878,7 @@ void free_ctx(mlqmc_ctx* c)
     for (auto& P : c->pools) cudaFree(P.mem);
     if (c->staged) cudaEventDestroy(c->staged);
     cudaFree(c->d_psi_dense);
+    cudaFree(c->d_c32);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->side) cudaStreamDestroy(c->side);
@@ -2034,6 +2072,7 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
     c->chol_stride = align256(sizeof(double) * N0 * (p->coarse_cells + 1));
     bool good = ok(cudaMalloc(&c->d_samples, ms * sizeof(SampleDesc))) &&
            ok(cudaMalloc(&c->d_Y, ms * p->n_modes * sizeof(double))) &&
+           (p->precision == MLQMC_FP64 || ok(cudaMalloc(&c->d_c32, ms * p->n_modes * sizeof(float)))) &&
            ok(cudaMalloc(&c->d_F, ms * p->n_levels * sizeof(double))) &&
            ok(cudaMalloc(&c->d_chol, ms * c->chol_stride)) && ok(cudaMalloc(&c->d_chol32, ms * c->chol_stride / 2)) &&
            ok(cudaMalloc(&c->d_norms, ms * sizeof(double))) &&

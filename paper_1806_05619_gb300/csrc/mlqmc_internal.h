@@ -97,6 +97,8 @@ struct mlqmc_ctx {
     double* d_sqrt_theta = nullptr;    // sqrt(theta_m)
     // Matern covariance: every level's modes at its cell centres, FP64,
     // cell-major (n_t^2 x s), level t at d_psi_dense + dense_off[t]
+    float* d_c32 = nullptr;  // mixed forms: FP32 KL coefficients of the chunk's samples (max_samples x s)
+    bool c32_ready = false;  // d_c32 holds the current chunk's coefficients (set inside run_chunk)
     bool matern = false;
     double* d_psi_dense = nullptr;
     size_t dense_off[MLQMC_MAX_LEVELS] = {};
