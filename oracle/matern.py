@@ -26,8 +26,11 @@ def matern_bessel(r, nu, corr_len, sigma=1.0):
 
 
 def matern(r, nu, corr_len, sigma=1.0):
-    """eq. matern for nu = 1/2, 3/2, 5/2 in closed form (K_nu of half-integer
-    order): exp(-z) times 1, 1 + z, 1 + z + z^2/3, z = sqrt(2 nu) r / corr_len."""
+    """eq. matern: for nu = 1/2, 3/2, 5/2 in closed form (K_nu of half-integer
+    order): exp(-z) times 1, 1 + z, 1 + z + z^2/3, z = sqrt(2 nu) r / corr_len;
+    for nu = 1, 2 the Bessel form."""
+    if nu in (1.0, 2.0):
+        return matern_bessel(r, nu, corr_len, sigma)
     r = np.asarray(r, dtype=np.float64)
     z = np.sqrt(2.0 * nu) * r / corr_len
     if nu == 0.5:

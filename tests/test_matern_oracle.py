@@ -17,6 +17,24 @@ def test_closed_forms_equal_the_bessel_form(nu):
     assert np.allclose(a, b, rtol=1e-12, atol=0)
 
 
+@pytest.mark.parametrize("nu", [1.0, 2.0])
+def test_integer_order_against_the_integral_representation(nu):
+    """K_nu(z) = int_0^inf exp(-z cosh t) cosh(nu t) dt (an independent route to
+    the Bessel function) in eq. matern, at several distances."""
+    pytest.importorskip("scipy")
+    from math import gamma
+    from scipy.integrate import quad
+
+    lam, sigma = 0.3, 1.1
+    for r in [1e-3, 0.02, 0.3, 1.2]:
+        z = np.sqrt(2 * nu) * r / lam
+        t_max = np.log(400.0 / z) + 4.0  # exp(-z cosh t) below 1e-80 beyond it
+        K = quad(lambda t: np.exp(-z * np.cosh(t)) * np.cosh(nu * t), 0, t_max, epsabs=0, epsrel=1e-13, limit=400)[0]
+        want = sigma ** 2 * 2 ** (1 - nu) / gamma(nu) * z ** nu * K
+        assert MT.matern(r, nu, lam, sigma) == pytest.approx(want, rel=1e-11)
+    assert MT.matern(0.0, nu, lam, sigma) == sigma ** 2
+
+
 def _kern(nu=1.5, lam=0.3, sigma=1.0):
     return MT.isotropic(lambda r: MT.matern(r, nu, lam, sigma))
 
