@@ -97,8 +97,9 @@ typedef enum {
  *                MGMLMC); 0: plain ML(Q)MC, only the finest difference counts.
  *  covariance    mlqmc_covariance (0 when the fields below are left zero).
  *  MLQMC_COV_MATERN (eq. matern, variance sigma^2, correlation length
- *  corr_len, smoothness matern_nu in {0.5, 1.5, 2.5}, where K_nu has a closed
- *  form): the KL modes are the Nystrom eigenpairs (eqs. discrinteq,
+ *  corr_len, smoothness matern_nu in {0.5, 1, 1.5, 2, 2.5}; half-integer nu in
+ *  closed form, nu = 1, 2 through K_nu by the trapezoidal rule on its integral
+ *  representation, tabulated with cubic Hermite interpolation): the KL modes are the Nystrom eigenpairs (eqs. discrinteq,
  *  matrixequation) on the cell centres of an nystrom_m x nystrom_m grid with
  *  midpoint weights 1/nystrom_m^2 (2..128), as mlqmc_nystrom_modes returns
  *  them: nystrom_theta (n_modes eigenvalues, positive) and nystrom_psi
@@ -195,7 +196,7 @@ mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples_per_call, 
  *  psi_out    host, m*m x s (node-major): psi_j(x_q) = v_qj / sqrt(w_q), so
  *             that sum_q w_q psi_j(x_q) psi_i(x_q) = delta_ij.
  * Within an eigenvalue of multiplicity > 1 the basis is the solver's; an
- * eigenvector's sign is the solver's. nu in {0.5, 1.5, 2.5}; 2 <= m <= 128;
+ * eigenvector's sign is the solver's. nu in {0.5, 1, 1.5, 2, 2.5}; 2 <= m <= 128;
  * 1 <= s <= m*m. Blocking. Errors: INVALID_ARG, OOM, CUDA (solver failure).
  */
 mlqmc_status mlqmc_nystrom_modes(double nu, double corr_len, double sigma, int32_t m, int32_t s,

@@ -7,7 +7,7 @@
 
 namespace mlqmc_matern {
 
-// nu in {0.5, 1.5, 2.5}: the smoothness values whose K_nu has a closed form.
+// nu in {0.5, 1, 1.5, 2, 2.5}: half-integer orders in closed form, 1 and 2 by quadrature.
 bool supported_nu(double nu);
 
 // The s largest Nystrom eigenpairs on the m x m midpoint nodes (see

@@ -33,7 +33,7 @@ def _groups(ev, s, tol=1e-8):
     return out
 
 
-@pytest.mark.parametrize("nu", [0.5, 1.5, 2.5])
+@pytest.mark.parametrize("nu", [0.5, 1.0, 1.5, 2.0, 2.5])
 def test_nystrom_modes_match_oracle(nu):
     m, s, lam, sigma = 16, 40, 0.3, 1.2
     th, ps = M.nystrom_modes(nu, lam, sigma, m, s)
@@ -61,7 +61,7 @@ def _ctx(precision, nu, m, s, theta, psi, **over):
     return cfg, z, ctx
 
 
-@pytest.mark.parametrize("nu", [0.5, 2.5])
+@pytest.mark.parametrize("nu", [0.5, 1.0, 2.0, 2.5])
 def test_fields_fp64_match_oracle(nu):
     m, s = 16, 30
     k = _kern(nu, 0.3, 1.0)
@@ -133,8 +133,8 @@ def test_mixed_forms_run_and_reject_bad_input():
         Fh = F.cpu().numpy()
         assert np.all(np.isfinite(Fh)) and np.all(Fh > 0)
     with pytest.raises(M.MlqmcError):
-        _ctx("fp64", 1.0, m, s, theta, psi)  # nu without a closed-form K_nu
+        _ctx("fp64", 0.75, m, s, theta, psi)  # nu outside {1/2, 1, 3/2, 2, 5/2}
     with pytest.raises(M.MlqmcError):
         _ctx("fp64", nu, m, s, -theta, psi)
     with pytest.raises(M.MlqmcError):
-        M.nystrom_modes(1.0, 0.3, 1.0, m, s)
+        M.nystrom_modes(3.0, 0.3, 1.0, m, s)
