@@ -226,16 +226,18 @@ __global__ void kb_coarse(FmgArgs A, int B)
 // working rows of the factorisation in shared memory: column j of L needs
 // rows j..j+NC only, so a ring of NC+1 rows per thread (transposed by thread:
 // conflict-free) holds them; a finished row goes to the global factor once.
-// The forward substitution runs along with the factorisation, the backward
-// one on the thread's y in shared memory. Same arithmetic, in the same order,
-// as kb_level0.
+// The forward substitution runs along with the factorisation, its last NC
+// values in registers and every value stored into the sample's solution
+// array, which the backward substitution then overwrites in place (again
+// with the last NC values in registers); shared memory holds the ring only,
+// so that all samples of a call fit on the GPU at once. Same arithmetic, in
+// the same order, as kb_level0.
 template <typename T, bool MX, int NC>
 __global__ void __launch_bounds__(64) kb_level0_fixed(FmgArgs A, int B)
 {
     constexpr int N = NC * NC, W = NC + 1, TPB = 64;
     extern __shared__ double l0sh[];
-    double* ring = l0sh;             // [(slot * W + e) * TPB + tid]
-    double* ys = l0sh + W * W * TPB;  // [r * TPB + tid]
+    double* ring = l0sh;  // [(slot * W + e) * TPB + tid]
     const int tid = threadIdx.x;
     const size_t cs = A.chol.stride;
     double* fac = reinterpret_cast<double*>(A.chol.base);
@@ -245,8 +247,11 @@ __global__ void __launch_bounds__(64) kb_level0_fixed(FmgArgs A, int B)
         const int i = base + tid;
         if (i >= B) continue;  // no barriers in this kernel: shared rows are private to the thread
         auto Rs = [&](int slot, int e) -> double& { return ring[(slot * W + e) * TPB + tid]; };
-        auto Y = [&](int r) -> double& { return ys[r * TPB + tid]; };
         const Lv<T> L0 = view<T>(A, 0, i);
+        double* x = (MX || A.refine) ? L0.u64 : reinterpret_cast<double*>(L0.u);
+        double win[NC];  // win[q - 1] = y_(j - q), the forward values of the last NC rows
+#pragma unroll
+        for (int q = 0; q < NC; ++q) win[q] = 0.0;
         // step j: row j's diagonal, its forward-substitution value, the row to
         // global memory, then column j of L for rows j+1..j+NC (ring slot of
         // row r: r mod W; FULL: j >= NC, every loop has its whole, compile-time range)
@@ -269,9 +274,13 @@ __global__ void __launch_bounds__(64) kb_level0_fixed(FmgArgs A, int B)
 #pragma unroll
             for (int q = 1; q <= NC; ++q) {
                 if (!FULL && q > j) break;
-                v -= Rs(s0, q) * Y(j - q);
+                v -= Rs(s0, q) * win[q - 1];
             }
-            Y(j) = v * rl;
+            const double yj = v * rl;
+            x[j] = yj;
+#pragma unroll
+            for (int q = NC - 1; q > 0; --q) win[q] = win[q - 1];
+            win[0] = yj;
 #pragma unroll
             for (int e = 0; e <= NC; ++e) {
                 if (!FULL && e > j) break;
@@ -297,25 +306,29 @@ __global__ void __launch_bounds__(64) kb_level0_fixed(FmgArgs A, int B)
         };
         for (int j = 0; j < NC; ++j) step(j, std::false_type());
         for (int j = NC; j < N; ++j) step(j, std::true_type());
+        // backward: x_r = (y_r - sum_q L(r+q, r) x_(r+q)) / L(r, r), win[q - 1] = x_(r+q)
+#pragma unroll
+        for (int q = 0; q < NC; ++q) win[q] = 0.0;
         for (int r = N - 1; r >= 0; --r) {
-            double v = Y(r);
-            for (int q = 1; q <= NC && r + q < N; ++q) v -= fac[static_cast<size_t>((r + q) * W + q) * cs + i] * Y(r + q);
-            Y(r) = v * fac[static_cast<size_t>(r * W) * cs + i];
-        }
-        double* x = (MX || A.refine) ? L0.u64 : reinterpret_cast<double*>(L0.u);
-        for (int r = 0; r < N; ++r) x[r] = Y(r);
-        if constexpr (MX) {
-            float* u32 = reinterpret_cast<float*>(L0.u);  // FP32 copy for the first FMG interpolation
-            for (int r = 0; r < N; ++r) u32[r] = narrow(Y(r));
+            double v = x[r];
+#pragma unroll
+            for (int q = 1; q <= NC; ++q)
+                if (r + q < N) v -= fac[static_cast<size_t>((r + q) * W + q) * cs + i] * win[q - 1];
+            const double xr = v * fac[static_cast<size_t>(r * W) * cs + i];
+            x[r] = xr;
+#pragma unroll
+            for (int q = NC - 1; q > 0; --q) win[q] = win[q - 1];
+            win[0] = xr;
+            if constexpr (MX) reinterpret_cast<float*>(L0.u)[r] = narrow(xr);  // FP32 copy for the first FMG interpolation
         }
         double F0;
         if (A.qoi == MLQMC_QOI_MEAN) {
             double acc = 0.0;
-            for (int r = 0; r < N; ++r) acc += Y(r);
+            for (int r = 0; r < N; ++r) acc += x[r];
             F0 = acc / static_cast<double>(N);
         } else {
             constexpr int m = NC / 2;
-            F0 = 0.25 * (Y((m - 1) * NC + (m - 1)) + Y((m - 1) * NC + m) + Y(m * NC + (m - 1)) + Y(m * NC + m));
+            F0 = 0.25 * (x[(m - 1) * NC + (m - 1)] + x[(m - 1) * NC + m] + x[m * NC + (m - 1)] + x[m * NC + m]);
         }
         A.F[static_cast<size_t>(i) * A.n_levels] = F0;
     }
@@ -324,7 +337,7 @@ __global__ void __launch_bounds__(64) kb_level0_fixed(FmgArgs A, int B)
 template <int NC>
 constexpr size_t level0_smem()
 {
-    return sizeof(double) * static_cast<size_t>((NC + 1) * (NC + 1) + NC * NC) * 64;
+    return sizeof(double) * static_cast<size_t>((NC + 1) * (NC + 1)) * 64;
 }
 
 // Coarse solve for n0 = NC fixed at compile time: a CTA of 64 threads takes 64
