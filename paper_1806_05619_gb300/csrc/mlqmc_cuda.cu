@@ -348,8 +348,8 @@ constexpr size_t level0_smem()
 template <typename T, int NC>
 __global__ void __launch_bounds__(64) kb_coarse_fixed(FmgArgs A, int B)
 {
-    // rows prefetched ahead: each group of PF rows costs one memory latency
-    constexpr int N = NC * NC, W = NC + 1, P = 65, PF = sizeof(T) == 4 ? 8 : 4;
+    // rows prefetched ahead: each group of PF rows costs one memory latency (FP64: 190 registers, no spills)
+    constexpr int N = NC * NC, W = NC + 1, P = 65, PF = 8;
     __shared__ T xs[N * P];
     const T h2 = T(1) / (T(NC) * T(NC));
     const T* fac = reinterpret_cast<const T*>(sizeof(T) == 4 ? A.chol32 : A.chol.base);
