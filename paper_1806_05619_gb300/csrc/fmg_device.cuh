@@ -172,9 +172,11 @@ __device__ const double kExp2Tab[64] = {
 // (truncation below 4e-17 relative). Ten FP64 operations where the library
 // exp takes about twice that on a part with GB300's FP64 rate. The lognormal
 // fields keep |x| far below 700; beyond it the library exp answers.
+static __device__ __noinline__ double exp_rare(double x) { return exp(x); }  // out of line: never if-converted
+
 __device__ __forceinline__ double exp64(double x)
 {
-    if (!(fabs(x) < 700.0)) return exp(x);
+    if (!(fabs(x) < 700.0)) return exp_rare(x);
     constexpr double kMagic = 0x1.8p52;                  // 1.5 * 2^52: rounds to an integer in the low bits
     constexpr double kInvL = 0x1.71547652b82fep+6;       // 64 / ln2
     constexpr double kL1 = 0x1.62e42fee00000p-7;         // ln2/64, leading 32 bits
@@ -521,17 +523,23 @@ __device__ __forceinline__ double widen_pos(float f)
 }
 __device__ __forceinline__ double widen_pos(double f) { return f; }
 
+// The conversion instructions, kept out of line: when the compiler turns a
+// short two-way branch into a select it issues both sides, and these belong
+// to the FP64 pipe on GB300; a call runs only for the lanes that take it.
+static __device__ __noinline__ double widen_rare(float f) { return static_cast<double>(f); }
+static __device__ __noinline__ float narrow_rare(double x) { return __double2float_rn(x); }
+
 // float -> double (exact) by moving the bits: sign, exponent rebiased by
-// 1023 - 127, mantissa shifted up by 29. Zero, subnormal, infinite and NaN
-// inputs take the conversion instruction, which on GB300 issues at the FP64 rate.
+// 1023 - 127, mantissa shifted up by 29; zero by a select. Subnormal,
+// infinite and NaN inputs take the conversion instruction (out of line).
 __device__ __forceinline__ double widen(float f)
 {
     const uint32_t b = __float_as_uint(f);
-    const uint32_t e = b & 0x7F800000u;
-    if (e == 0u || e == 0x7F800000u) return static_cast<double>(f);
+    const uint32_t mag = b & 0x7FFFFFFFu;
     const unsigned long long sgn = static_cast<unsigned long long>(b & 0x80000000u) << 32;
-    const unsigned long long mag = static_cast<unsigned long long>(b & 0x7FFFFFFFu);
-    return __longlong_as_double(static_cast<long long>(sgn | ((mag << 29) + (896ull << 52))));
+    if (mag == 0u) return __longlong_as_double(static_cast<long long>(sgn));
+    if (mag - 0x00800000u >= 0x7F000000u) return widen_rare(f);
+    return __longlong_as_double(static_cast<long long>(sgn | ((static_cast<unsigned long long>(mag) << 29) + (896ull << 52))));
 }
 __device__ __forceinline__ double widen(double f) { return f; }
 
@@ -539,17 +547,19 @@ __device__ __forceinline__ double widen(double f) { return f; }
 // when the result is a normal float or overflows (biased exponent of |x| in
 // 897..1150): add 2^28 - 1 plus the lowest kept bit, drop 29 mantissa bits,
 // rebias the exponent (a carry out of the mantissa moves into the exponent,
-// up to infinity). Smaller magnitudes, infinities and NaN take the
-// conversion instruction.
+// up to infinity); zero by a select. Smaller magnitudes, infinities and NaN
+// take the conversion instruction (out of line).
 __device__ __forceinline__ float narrow(double x)
 {
     const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
     const unsigned long long a = b & 0x7FFFFFFFFFFFFFFFull;
+    const uint32_t sgn = static_cast<uint32_t>(b >> 32) & 0x80000000u;
+    if (a == 0ull) return __uint_as_float(sgn);
     const unsigned e = static_cast<unsigned>(a >> 52);
-    if (e < 897u || e > 1150u) return __double2float_rn(x);
+    if (e < 897u || e > 1150u) return narrow_rare(x);
     const unsigned long long r = a + 0x0FFFFFFFull + ((a >> 29) & 1ull);
     const uint32_t mag = static_cast<uint32_t>((r >> 29) - (896ull << 23));
-    return __uint_as_float(mag | (static_cast<uint32_t>(b >> 32) & 0x80000000u));
+    return __uint_as_float(mag | sgn);
 }
 
 // A double result stored in working precision T.
