@@ -201,6 +201,27 @@ __global__ void __launch_bounds__(kThreads, TGeom<TILE, POST>::ctas_per_sm)
                 acc += so * su[c0 + SU];
                 su[c0] = __fdividef(acc, w + e + nn + so);  // hardware reciprocal: within 2 ulp
             };
+            // the thread's own tile cells (two rows, both colours): their faces,
+            // h^2 b and diagonal stay in registers across the half sweeps, so an
+            // update reads only the four neighbouring u from shared memory (same
+            // operands, same order as `update`)
+            float cw[2][2], ce[2][2], cn[2][2], cso[2][2], cb[2][2], cd[2][2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int sy = kH + 2 * (warp + 8 * j) + (lane >> 4);
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    const int sx = kH + 2 * (lane & 15) + p;
+                    const int c0 = sy * SU + sx;
+                    const float* kr = skx + sy * XW;
+                    cw[j][p] = kr[sx];
+                    ce[j][p] = kr[sx + 1];
+                    cn[j][p] = sky[c0];
+                    cso[j][p] = sky[c0 + SU];
+                    cb[j][p] = h2 * (ones ? 1.0f : sb[c0]);
+                    cd[j][p] = cw[j][p] + ce[j][p] + cn[j][p] + cso[j][p];
+                }
+            }
 #pragma unroll
             for (int ph = 0; ph < HN; ++ph) {
                 const int colour = (first + ph) & 1;
@@ -209,7 +230,14 @@ __global__ void __launch_bounds__(kThreads, TGeom<TILE, POST>::ctas_per_sm)
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     const int sy = kH + 2 * (warp + 8 * j) + (lane >> 4);
-                    update(sy, kH + 2 * (lane & 15) + ((colour + sy) & 1));
+                    const int p = (colour + sy) & 1;
+                    const int c0 = sy * SU + kH + 2 * (lane & 15) + p;
+                    float acc = p ? cb[j][1] : cb[j][0];
+                    acc += (p ? cw[j][1] : cw[j][0]) * su[c0 - 1];
+                    acc += (p ? ce[j][1] : ce[j][0]) * su[c0 + 1];
+                    acc += (p ? cn[j][1] : cn[j][0]) * su[c0 - SU];
+                    acc += (p ? cso[j][1] : cso[j][0]) * su[c0 + SU];
+                    su[c0] = __fdividef(acc, p ? cd[j][1] : cd[j][0]);
                 }
                 const int pk = ring[ph];
                 if (pk >= 0) {
