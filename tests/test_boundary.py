@@ -87,6 +87,44 @@ def test_create_rejects_bad_problems_before_touching_the_device(lib, bad):
     assert not h.value
 
 
+def _matern_problem(nu=1.5, m=4, theta=(0.5, 0.2, 0.1, 0.05), with_psi=True, **kw):
+    p = _problem(**kw)
+    th = (C.c_double * len(theta))(*theta)
+    ps = (C.c_double * (m * m * 4))()
+    p.covariance, p.nystrom_m, p.matern_nu = 1, m, nu
+    p.nystrom_theta = C.cast(th, C.POINTER(C.c_double))
+    p.nystrom_psi = C.cast(ps, C.POINTER(C.c_double)) if with_psi else None
+    return p, (th, ps)
+
+
+@pytest.mark.parametrize("bad", [dict(nu=0.75), dict(nu=3.0), dict(m=1), dict(m=129), dict(with_psi=False),
+                                 dict(theta=(0.5, 0.0, 0.1, 0.05)), dict(theta=(0.5, -1.0, 0.1, 0.05)),
+                                 dict(m=1, n_modes=4)])
+def test_create_rejects_bad_matern_problems_before_touching_the_device(lib, bad):
+    p, keep = _matern_problem(**bad)
+    h = C.c_void_p()
+    assert lib.mlqmc_create(C.byref(p), 0, C.byref(h)) == 1
+    assert not h.value
+
+
+def test_create_rejects_unknown_covariance_and_more_modes_than_nodes(lib):
+    p = _problem()
+    p.covariance = 2
+    h = C.c_void_p()
+    assert lib.mlqmc_create(C.byref(p), 0, C.byref(h)) == 1
+    p, keep = _matern_problem(m=2, n_modes=5, theta=(0.5, 0.2, 0.1, 0.05, 0.01))  # 5 modes on 4 nodes
+    assert lib.mlqmc_create(C.byref(p), 0, C.byref(h)) == 1
+
+
+def test_nystrom_modes_rejects_bad_arguments(lib):
+    th = np.zeros(4)
+    ps = np.zeros(64)
+    dp = C.POINTER(C.c_double)
+    for args in [(0.75, 0.3, 1.0, 4, 4), (1.5, 0.0, 1.0, 4, 4), (1.5, 0.3, 0.0, 4, 4), (1.5, 0.3, 1.0, 1, 1),
+                 (1.5, 0.3, 1.0, 4, 0), (1.5, 0.3, 1.0, 2, 5)]:
+        assert lib.mlqmc_nystrom_modes(*args, th.ctypes.data_as(dp), ps.ctypes.data_as(dp)) == 1, args
+
+
 def test_create_rejects_even_generating_vector(lib):
     z = (C.c_uint32 * 4)(1, 3, 4, 7)
     p = _problem(sampler=1, genvec=C.cast(z, C.POINTER(C.c_uint32)))
