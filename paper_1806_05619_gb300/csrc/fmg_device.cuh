@@ -498,21 +498,6 @@ __device__ void vcycle(const TM& tm, const FmgArgs& A, int i, int t_top, const T
     }
 }
 
-// ||1 - A u||_2 on one level (b = 1), FP64 accumulation.
-template <typename T, typename TM>
-__device__ double resid_norm_ones(const TM& tm, const Lv<T>& L, double* red)
-{
-    const int n = L.n;
-    const double ih2 = static_cast<double>(n) * n;
-    double acc = 0.0;
-    for (int p = tm.rank(); p < n * n; p += tm.size()) {
-        const int i2 = p / n, i1 = p - i2 * n;
-        const double r = 1.0 - ih2 * static_cast<double>(apply_h2<T, T>(L.kx, L.ky, L.u, n, i1, i2));
-        acc += r * r;
-    }
-    return sqrt(team_sum(tm, acc, red));
-}
-
 // Exact widening of a positive normal float (a face coefficient) to double by
 // re-biasing its exponent on the integer pipe: the 8-bit exponent e becomes
 // e - 127 + 1023 and the 23-bit mantissa moves to the top of the 52-bit one.
@@ -583,29 +568,13 @@ __device__ __forceinline__ double apply_h2_64(const T* kx, const T* ky, const do
     return acc;
 }
 
-// Refinement path (mixed forms, and the converged FP64 form): r = 1 - A u64 in
-// FP64 with the working-precision faces widened; r stored to the working
-// precision right-hand side. Returns ||r||_2.
-// ih2 = n^2, hoisted by the caller.
+// Refinement path (mixed forms, and the converged FP64 form): r = 1 - A u64 of
+// one cell in FP64 with the working-precision faces widened; ih2 = n^2,
+// hoisted by the caller.
 template <typename T>
 __device__ __forceinline__ double resid64_cell(const Lv<T>& L, double ih2, int i1, int i2)
 {
     return fma(-ih2, apply_h2_64<T>(L.kx, L.ky, L.u64, L.n, i1, i2), 1.0);
-}
-
-template <typename TM, typename T>
-__device__ double resid64_to_rhs(const TM& tm, const Lv<T>& L, double* red)
-{
-    const int n = L.n;
-    const double ih2 = static_cast<double>(n) * n;
-    double acc = 0.0;
-    for (int p = tm.rank(); p < n * n; p += tm.size()) {
-        const int i2 = p / n;
-        const double r = resid64_cell(L, ih2, p - i2 * n, i2);
-        L.bc[p] = to_work<T>(r);
-        acc += r * r;
-    }
-    return sqrt(team_sum(tm, acc, red));
 }
 
 template <typename T, typename TM>

@@ -853,28 +853,45 @@ __global__ void kb_update64(FmgArgs A, int t, int B)
     }
 }
 
-// Per-sample residual norm (one CTA per sample, deterministic); the refinement
-// path also leaves r in bc for the next correction.
-template <typename T, bool REF>
-__global__ void __launch_bounds__(256) kb_resnorm(FmgArgs A, int t, int B)
+// Refinement residual r = 1 - A u64 of level t (left in bc for the next correction)
+// with the cells of each sample in P contiguous chunks, one CTA per (sample,
+// chunk), so that a few large samples still fill the GPU: part[i * P + q] =
+// the chunk's sum of r^2 (fixed order inside the CTA).
+template <typename T>
+__global__ void __launch_bounds__(256) kb_resnorm_part(FmgArgs A, int t, int B, int P, double* part)
 {
     __shared__ double red[48];
-    const BlockTeam tm;
-    for (int i = blockIdx.x; i < B; i += gridDim.x) {
+    const int n = A.lv[t].n;
+    const int nn = n * n;
+    const int csz = (nn + P - 1) / P;
+    const double ih2 = static_cast<double>(n) * n;
+    for (int w = blockIdx.x; w < B * P; w += gridDim.x) {  // uniform per CTA: every thread reaches block_sum
+        const int i = w / P, q = w - i * P;
         const Lv<T> L = view<T>(A, t, i);
-        double nr;
-        if constexpr (REF) nr = resid64_to_rhs(tm, L, red);
-        else nr = resid_norm_ones(tm, L, red);
-        if (threadIdx.x == 0) A.norms[i] = nr;
+        const int p1 = min(nn, (q + 1) * csz);
+        double acc = 0.0;
+        for (int p = q * csz + static_cast<int>(threadIdx.x); p < p1; p += blockDim.x) {
+            const int i2 = p / n;
+            const double r = resid64_cell(L, ih2, p - i2 * n, i2);
+            L.bc[p] = to_work<T>(r);
+            acc += r * r;
+        }
+        const double sum = block_sum(acc, red);
+        if (threadIdx.x == 0) part[w] = sum;
     }
 }
 
+// norms[i] = sqrt of the sum of sample i's P partial sums (in chunk order),
 // active[i] = (norm_i > thresh); *count = number of active samples.
-__global__ void kb_flags(const double* norms, int* active, int B, double thresh, int* count)
+__global__ void kb_norm_flags(const double* part, int P, double* norms, int* active, int B, double thresh, int* count)
 {
     GRID_STRIDE(i, B)
     {
-        const int a = norms[i] > thresh ? 1 : 0;
+        double sum = 0.0;
+        for (int q = 0; q < P; ++q) sum += part[static_cast<size_t>(i) * P + q];
+        const double nr = sqrt(sum);
+        norms[i] = nr;
+        const int a = nr > thresh ? 1 : 0;
         active[i] = a;
         if (a) atomicAdd(count, 1);
     }
@@ -1635,15 +1652,26 @@ mlqmc_status converge_batched(mlqmc_ctx* c, FmgArgs& A, int t, int B, cudaStream
 {
     const int64_t n = c->p.coarse_cells << t;
     const double es = sizeof(T), Mc = cells_of(c, t), Fc = faces_of(c, t);
+    // chunks of about 8192 cells per CTA (this path is never graph-captured: the buffer may grow here)
+    const int P = static_cast<int>(std::max<int64_t>(1, n * n / 8192));
+    if (static_cast<int64_t>(B) * P > c->part_cap) {
+        cudaFree(c->d_part);
+        c->d_part = nullptr;
+        c->part_cap = 0;
+        if (!ok(cudaMalloc(&c->d_part, sizeof(double) * static_cast<size_t>(B) * P))) return MLQMC_ERR_OOM;
+        c->part_cap = static_cast<int64_t>(B) * P;
+    }
     for (int it = 0;; ++it) {
         {
             Timed tm(c, kProfReduce, st, work_of<double>(B * (8.0 * Mc + es * (2.0 * Fc + Mc) + 8.0), B * 12.0 * Mc));
-            kb_resnorm<T, true><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
+            const int grid = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(B) * P, c->sm_count * 8));
+            kb_resnorm_part<T><<<grid, 256, 0, st>>>(A, t, B, P, c->d_part);
         }
         if (!ok(cudaMemsetAsync(c->d_count, 0, sizeof(int), st))) return MLQMC_ERR_CUDA;
         {
-            Timed tm(c, kProfReduce, st, work_of<double>(B * 12.0, 0.0));
-            kb_flags<<<grid_for(c, B), 256, 0, st>>>(c->d_norms, c->d_active, B, c->p.refine_rtol * n, c->d_count);
+            Timed tm(c, kProfReduce, st, work_of<double>(B * (8.0 * P + 12.0), B * 1.0 * P));
+            kb_norm_flags<<<grid_for(c, B), 256, 0, st>>>(c->d_part, P, c->d_norms, c->d_active, B,
+                                                          c->p.refine_rtol * n, c->d_count);
         }
         if (!ok(cudaMemcpyAsync(c->h_count, c->d_count, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
             !ok(cudaStreamSynchronize(st)))
@@ -1930,6 +1958,7 @@ void free_ctx(mlqmc_ctx* c)
     for (auto& P : c->pools) cudaFree(P.mem);
     if (c->staged) cudaEventDestroy(c->staged);
     cudaFree(c->d_psi_dense);
+    cudaFree(c->d_part);
     cudaFree(c->d_c32);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);

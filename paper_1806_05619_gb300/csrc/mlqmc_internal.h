@@ -118,6 +118,8 @@ struct mlqmc_ctx {
     double* d_chol = nullptr;         // banded level-0 factor per sample (interleaved by sample)
     float* d_chol32 = nullptr;        // its FP32 copy (mixed forms)
     double* d_norms = nullptr;
+    double* d_part = nullptr;  // partial residual sums of the converged forms (samples x chunks), grown on demand
+    int64_t part_cap = 0;
     int* d_active = nullptr;
     int* d_count = nullptr;
     SampleDesc* h_samples = nullptr;  // pinned staging
