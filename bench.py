@@ -106,7 +106,7 @@ KIND_KERNELS = {
     "level0": "kb_level0 (banded Cholesky and exact level-0 solve, one thread per sample)",
     "synth": "kb_synth_G/kb_synth_z (separable KL), kb_faces, kb_idiag",
     "smooth": "red-black sweeps (kb_rbgs_whole up to 64x64 with residual/correction fused, kb_rbgs_tma tiles "
-              "above; FP64 form: kb_rbgs_whole up to 32x32, kb_gs above)",
+              "above; FP64 form: kb_rbgs_whole up to 64x64, kb_gs above)",
     "transfer": "kb_resid_restrict, kb_prolong, kb_resid64, kb_update64",
     "coarse": "kb_coarse_fixed (V-cycle level-0 solves)",
     "reduce": "kb_qoi, kb_resnorm, k_sums, outputs",

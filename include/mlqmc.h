@@ -379,7 +379,7 @@ int64_t mlqmc_launch_count(const mlqmc_ctx* c);
  * has no sweeps and reports 0) and tuned_ms (host, n_levels x 5 doubles,
  * [level][kind] milliseconds of the tuning visit, 0 where not timed); either
  * may be NULL. The FP64 form takes a fixed rule, so that every context gives
- * the same bits: MLQMC_SMOOTHER_WHOLE for n <= 32, MLQMC_SMOOTHER_GS above
+ * the same bits: MLQMC_SMOOTHER_WHOLE for n <= 64, MLQMC_SMOOTHER_GS above
  * (both multiply by the stored FP64 1/D and agree to rounding); the others
  * are FP32 only.
  * mlqmc_set_smoother: force `kind` on `level` (1 <= level < n_levels) for

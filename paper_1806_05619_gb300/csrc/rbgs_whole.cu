@@ -1,5 +1,5 @@
 // Whole-sample red-black smoother for the small levels of the V-cycles
-// (Sec. 4), FP32 (n <= 64) and FP64 (n <= 32).
+// (Sec. 4), FP32 and FP64 (n <= 64).
 //
 // A sample's whole level (n <= 64) fits in shared memory: one warp (n <= 32,
 // several samples per CTA) or one CTA of 256 threads (n = 64) brings u, the
@@ -30,7 +30,7 @@ template <typename T, int N>
 struct WGeom {
     static constexpr bool F64 = sizeof(T) == 8;
     static constexpr int TS = N <= 32 ? 32 : 256;  // threads per sample
-    static constexpr int SPC = F64 ? (N <= 16 ? 8 : 2) : (N <= 16 ? 8 : (N == 32 ? 4 : 1));  // samples per CTA
+    static constexpr int SPC = N == 64 ? 1 : (N <= 16 ? 8 : (F64 ? 2 : 4));  // samples per CTA
     static constexpr int XP = N + 4;               // kx_pitch(N)
     static constexpr int NC = N / 2;
     static constexpr int oU = 0;
@@ -215,13 +215,13 @@ namespace mlqmc_whole {
 
 bool supported(int n, bool fp64)
 {
-    return n == 8 || n == 16 || n == 32 || (n == 64 && !fp64);
+    return n == 8 || n == 16 || n == 32 || n == 64;  // FP64 64 x 64: 171 KB, one sample per CTA
 }
 
 bool prepare()
 {
     return attrs<float, 8>() && attrs<float, 16>() && attrs<float, 32>() && attrs<float, 64>() &&
-           attrs<double, 8>() && attrs<double, 16>() && attrs<double, 32>();
+           attrs<double, 8>() && attrs<double, 16>() && attrs<double, 32>() && attrs<double, 64>();
 }
 
 bool launch(const FmgArgs& A, int t, int n, int B, int ns, int ones, int first, bool pre, bool post, bool fp64,
@@ -233,7 +233,8 @@ bool launch(const FmgArgs& A, int t, int n, int B, int ns, int ones, int first, 
         switch (n) {
         case 8: go<double, 8>(A, t, B, ns, ones, first, pre, post, st); break;
         case 16: go<double, 16>(A, t, B, ns, ones, first, pre, post, st); break;
-        default: go<double, 32>(A, t, B, ns, ones, first, pre, post, st); break;
+        case 32: go<double, 32>(A, t, B, ns, ones, first, pre, post, st); break;
+        default: go<double, 64>(A, t, B, ns, ones, first, pre, post, st); break;
         }
     } else {
         switch (n) {

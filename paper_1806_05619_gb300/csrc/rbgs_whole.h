@@ -7,7 +7,7 @@
 
 namespace mlqmc_whole {
 
-// Level sides whose whole grid one team stages in shared memory (FP32: n <= 64; FP64: n <= 32).
+// Level sides whose whole grid one team stages in shared memory (n <= 64).
 bool supported(int n, bool fp64);
 
 // Raise the dynamic shared-memory limit of every instance; once per process.

@@ -438,13 +438,13 @@ def test_autotuner_report():
         ctx.set_smoother(1, "tma")  # 16 x 16: no whole TMA tile with its halo inside the grid
     c64 = M.Context.from_config(W.scaled(W.CONFIG2, R=2), genvec=_genvec(cfg))
     for t, (k, _) in enumerate(c64.smoother_info()):
-        assert k == "gs" or (k == "whole" and (cfg["n0"] << t) <= 32)
+        assert k == "gs" or (k == "whole" and (cfg["n0"] << t) <= 64)
     with pytest.raises(M.MlqmcError):
         c64.set_smoother(3, "stream")  # FP64 form: kb_gs or the whole-sample smoother
 
 
 def test_fp64_whole_sample_smoother_matches_gs():
-    """FP64 form: the whole-sample smoother (levels up to 32 x 32) multiplies by
+    """FP64 form: the whole-sample smoother (levels up to 64 x 64) multiplies by
     the stored 1/D like kb_gs and fuses residual and correction with the same
     arithmetic: per-sample F agree with the kb_gs path to 1e-13."""
     cfg = W.scaled(W.CONFIG2, R=2)
@@ -453,7 +453,7 @@ def test_fp64_whole_sample_smoother_matches_gs():
     ns = sum((ne - nb) * (re_ - rb) for (_, nb, ne, rb, re_) in work)
     out = {}
     for name in ["gs", "whole"]:
-        for t in (1, 2):
+        for t in (1, 2, 3):
             ctx.set_smoother(t, name)
         sums = torch.zeros(cfg["n_levels"] * 2 * 2, dtype=torch.float64, device="cuda")
         F = torch.zeros(ns * cfg["n_levels"], dtype=torch.float64, device="cuda")
