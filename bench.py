@@ -67,7 +67,7 @@ def parse():
 
 
 def workload_config(rank: int, counts_div: int = 1):
-    cfg = dict(W.CONFIG2)
+    cfg = dict(W.LATTICE_6LEVEL)
     cfg["seed"] = cfg["seed"] + 1000 * rank
     cfg["counts"] = [max(1, c // counts_div) for c in cfg["counts"]]
     return cfg
@@ -606,7 +606,7 @@ def run_precision_form(dev, stream, flush, M):
     results' deviation from the FP64 ones (field, solution, F on every level)."""
     import torch
 
-    cfg = dict(W.CONFIG3)
+    cfg = dict(W.PRECISION_1024)
     cfg["log2_nmax"] = 10
     genvec, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
     top = cfg["n_levels"] - 1
@@ -663,7 +663,7 @@ def run_time_to_eps(M):
     and two smaller tolerances (3e-4, 1e-4) where the runs take longer."""
     from paper_1806_05619_gb300 import rates
 
-    cfg = dict(W.CONFIG4)
+    cfg = dict(W.ADAPTIVE_7LEVEL)
     cfg["log2_nmax"] = 12
     genvec, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
     out = {"workload": "Algorithm 1 on 7 levels 8x8..512x512, s=200, lambda=0.3, R=16, rtol 1e-10",

@@ -27,7 +27,7 @@ def main():
         f.write("# j z_j criterion_after_j\n")
         for j in range(100):
             f.write(f"{j} {int(z[j])} {float(e2[j]).hex()}\n")
-    cfg = W.CONFIG2
+    cfg = W.LATTICE_6LEVEL
     orc = O.Oracle(n_levels=cfg["n_levels"], n0=cfg["n0"], s=cfg["s"], sampler="lattice", seed=cfg["seed"],
                    R=cfg["R"], genvec=z, log2_nmax=cfg["log2_nmax"])
     with open(os.path.join(HERE, "lattice_bits_problem2.txt"), "w") as f:

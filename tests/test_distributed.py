@@ -14,7 +14,7 @@ torch = pytest.importorskip("torch")
 M = pytest.importorskip("paper_1806_05619_gb300")
 from paper_1806_05619_gb300 import distributed as D  # noqa: E402
 
-CFG = W.scaled(W.CONFIG2, n_levels=4, s=12, R=4, log2_nmax=6)
+CFG = W.scaled(W.LATTICE_6LEVEL, n_levels=4, s=12, R=4, log2_nmax=6)
 WORK = [(0, 0, 9, 0, 4), (1, 2, 6, 1, 4), (2, 0, 3, 0, 3), (3, 0, 2, 2, 4)]
 
 

@@ -33,7 +33,7 @@ def test_library_cbc_matches_the_stored_vector():
 
 def test_oracle_reproduces_the_stored_points_and_normals():
     z = [int(r[1]) for r in _rows("cbc_s100_m10.txt")]
-    cfg = W.CONFIG2
+    cfg = W.LATTICE_6LEVEL
     orc = O.Oracle(n_levels=cfg["n_levels"], n0=cfg["n0"], s=cfg["s"], sampler="lattice", seed=cfg["seed"],
                    R=cfg["R"], genvec=z, log2_nmax=cfg["log2_nmax"])
     for lv, r, n, j, bits, y in _rows("lattice_bits_problem2.txt"):
@@ -48,7 +48,7 @@ def test_device_points_and_normals_match_the_stored_values():
     import paper_1806_05619_gb300 as M
 
     z = [int(r[1]) for r in _rows("cbc_s100_m10.txt")]
-    ctx = M.Context.from_config(W.CONFIG2, genvec=z)
+    ctx = M.Context.from_config(W.LATTICE_6LEVEL, genvec=z)
     for lv, r, n, j, bits, y in _rows("lattice_bits_problem2.txt"):
         lv, r, n, j = int(lv), int(r), int(n), int(j)
         b = int(ctx.point_bits(lv, r, n, 1).cpu().numpy()[0, j]) & 0xFFFFFFFFFFFFFFFF

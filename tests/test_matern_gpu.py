@@ -53,7 +53,7 @@ def test_nystrom_modes_match_oracle(nu):
 
 
 def _ctx(precision, nu, m, s, theta, psi, **over):
-    cfg = W.scaled(W.CONFIG2, n_levels=4, s=s, R=2, precision=precision, log2_nmax=8, corr_len=0.3)
+    cfg = W.scaled(W.LATTICE_6LEVEL, n_levels=4, s=s, R=2, precision=precision, log2_nmax=8, corr_len=0.3)
     cfg.update(over)
     z, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
     ctx = M.Context.from_config(cfg, genvec=z, covariance="matern", matern_nu=nu, nystrom_m=m, nystrom_theta=theta,

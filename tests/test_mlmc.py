@@ -11,7 +11,7 @@ import workloads as W
 
 
 def _mc_oracle(**over):
-    cfg = W.scaled(W.CONFIG1, **over)
+    cfg = W.scaled(W.MC_4LEVEL, **over)
     return cfg, O.Oracle(n_levels=cfg["n_levels"], n0=cfg["n0"], s=cfg["s"], sigma=cfg["sigma"],
                          corr_len=cfg["corr_len"], qoi=cfg["qoi"], mu0=cfg["mu0"], nu1=cfg["nu1"],
                          nu2=cfg["nu2"], rtol=0.0, max_cycles=100, sampler="mc", seed=cfg["seed"], R=1,
@@ -68,7 +68,7 @@ def test_multilevel_run_invariants_and_bookkeeping():
 
 
 def test_rejects_lattice_or_recycling():
-    cfg = W.scaled(W.CONFIG2, n_levels=3, s=4, R=2, log2_nmax=6)
+    cfg = W.scaled(W.LATTICE_6LEVEL, n_levels=3, s=4, R=2, log2_nmax=6)
     z, _ = O.cbc(cfg["s"], cfg["log2_nmax"])
     orc = O.Oracle(n_levels=3, n0=8, s=4, sampler="lattice", seed=1, R=2, genvec=z, log2_nmax=6)
     assert orc.estimate_mlmc(1e-2)["status"] == O.ERR_ARG

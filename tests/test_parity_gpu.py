@@ -60,9 +60,9 @@ def _rel(a, b):
 # --------------------------------------------------------------------------- #
 
 
-@pytest.mark.parametrize("cid", [1, 2])
-def test_point_bits_bit_exact(cid):
-    cfg, ctx, orc = _pair(W.CONFIGS[cid])
+@pytest.mark.parametrize("pid", [1, 2])
+def test_point_bits_bit_exact(pid):
+    cfg, ctx, orc = _pair(W.PROBLEMS[pid])
     for level, r, nb, cnt in [(0, 0, 0, 64), (3, 5 % cfg["R"], 17, 45), (cfg["n_levels"] - 1, cfg["R"] - 1, 0, 7)]:
         bits = ctx.point_bits(level, r, nb, cnt).cpu().numpy().view(np.uint64)
         for i in range(cnt):
@@ -76,7 +76,7 @@ def test_point_bits_bit_exact(cid):
 
 
 def test_lattice_index_end_of_sequence():
-    cfg, ctx, orc = _pair(W.CONFIG2)
+    cfg, ctx, orc = _pair(W.LATTICE_6LEVEL)
     N = 2 ** cfg["log2_nmax"]
     bits = ctx.point_bits(2, 1, N - 3, 3).cpu().numpy().view(np.uint64)
     for i in range(3):
@@ -87,9 +87,9 @@ def test_lattice_index_end_of_sequence():
     assert e.value.code == 4
 
 
-@pytest.mark.parametrize("cid", [1, 2])
-def test_normals(cid):
-    cfg, ctx, orc = _pair(W.CONFIGS[cid])
+@pytest.mark.parametrize("pid", [1, 2])
+def test_normals(pid):
+    cfg, ctx, orc = _pair(W.PROBLEMS[pid])
     y = ctx.normals(2, 0, 5, 40).cpu().numpy()
     for i in range(40):
         want = orc.normals(2, 0, 5 + i)
@@ -102,17 +102,17 @@ def test_normals(cid):
 
 
 def test_modes_match():
-    cfg, ctx, orc = _pair(W.CONFIG2)
+    cfg, ctx, orc = _pair(W.LATTICE_6LEVEL)
     a, b, th = ctx.modes()
     ao, bo, tho, _ = orc.modes()
     assert np.array_equal(a, ao) and np.array_equal(b, bo)
     assert _rel(th, tho) < 1e-13
 
 
-@pytest.mark.parametrize("cid,levels", [(1, [0, 3]), (2, [0, 2, 4]), (3, [0, 3])])
-def test_fields_fp64(cid, levels):
-    cfg, ctx, orc = _pair(W.CONFIGS[cid], precision="fp64", rtol=0.0)
-    Y = W.random_normals(cfg["s"], 3, tag=20 + cid)
+@pytest.mark.parametrize("pid,levels", [(1, [0, 3]), (2, [0, 2, 4]), (3, [0, 3])])
+def test_fields_fp64(pid, levels):
+    cfg, ctx, orc = _pair(W.PROBLEMS[pid], precision="fp64", rtol=0.0)
+    Y = W.random_normals(cfg["s"], 3, tag=20 + pid)
     for t in levels:
         k = ctx.fields(t, torch.from_numpy(Y)).cpu().numpy()
         for i in range(3):
@@ -125,9 +125,9 @@ def test_fields_fp64(cid, levels):
 # --------------------------------------------------------------------------- #
 
 
-@pytest.mark.parametrize("cid,level,r,n", [(1, 3, 0, 5), (2, 0, 0, 0), (2, 3, 2, 7), (2, 5, 15, 3)])
-def test_single_sample_solutions_fp64(cid, level, r, n):
-    cfg, ctx, orc = _pair(W.CONFIGS[cid])
+@pytest.mark.parametrize("pid,level,r,n", [(1, 3, 0, 5), (2, 0, 0, 0), (2, 3, 2, 7), (2, 5, 15, 3)])
+def test_single_sample_solutions_fp64(pid, level, r, n):
+    cfg, ctx, orc = _pair(W.PROBLEMS[pid])
     sols, F = ctx.sample_solution(level, r, n)
     ref = orc.sample(level, r, n, want_u=True)
     assert ref["status"] == O.OK
@@ -170,21 +170,21 @@ def _check_sums(cfg, ctx, orc, work):
 
 
 def test_config1_full_sums():
-    cfg, ctx, orc = _pair(W.CONFIG1)
+    cfg, ctx, orc = _pair(W.MC_4LEVEL)
     work = W.fixed_count_work(cfg["counts"], cfg["R"])
     _check_sums(cfg, ctx, orc, work)
 
 
 @pytest.mark.parametrize("reuse", [True, False])
 def test_config2_ragged_work(reuse):
-    cfg, ctx, orc = _pair(W.CONFIG2, R=4, reuse=reuse)
+    cfg, ctx, orc = _pair(W.LATTICE_6LEVEL, R=4, reuse=reuse)
     work = [(0, 0, 13, 0, 3), (1, 5, 9, 1, 4), (2, 0, 3, 0, 4), (3, 2, 4, 2, 3), (4, 0, 1, 0, 2), (5, 0, 1, 3, 4),
             (2, 7, 7, 0, 4)]
     _check_sums(cfg, ctx, orc, work)
 
 
 def test_chunked_calls_equal_single_call():
-    cfg = W.scaled(W.CONFIG2, R=2)
+    cfg = W.scaled(W.LATTICE_6LEVEL, R=2)
     z = _genvec(cfg)
     work = [(0, 0, 40, 0, 2), (2, 0, 9, 0, 2), (3, 0, 3, 0, 2)]
     outs = []
@@ -200,7 +200,7 @@ def test_chunked_calls_equal_single_call():
 
 
 def test_empty_and_invalid_work():
-    cfg, ctx, orc = _pair(W.CONFIG2, R=2)
+    cfg, ctx, orc = _pair(W.LATTICE_6LEVEL, R=2)
     sums = torch.zeros(cfg["n_levels"] * 2 * 2, dtype=torch.float64, device="cuda")
     ctx.sample_levels([], sums)
     ctx.sample_levels([(1, 4, 4, 0, 2)], sums)
@@ -216,7 +216,7 @@ def test_full_config2_launch_sampled_against_oracle():
     """The bench's workload in its launch configuration: all 32256 samples of
     the fixed counts; sampled F rows against the oracle one by one, and the
     sums against a host recomputation from the per-sample F (any size)."""
-    cfg, ctx, orc = _pair(W.CONFIG2)
+    cfg, ctx, orc = _pair(W.LATTICE_6LEVEL)
     work = W.fixed_count_work(cfg["counts"], cfg["R"])
     nl, R = cfg["n_levels"], cfg["R"]
     nsamp = sum((ne - nb) * (re_ - rb) for (_, nb, ne, rb, re_) in work)
@@ -255,7 +255,7 @@ def test_full_config2_launch_sampled_against_oracle():
 
 
 def test_algorithm1_matches_oracle():
-    cfg, ctx, orc = _pair(W.CONFIG2, n_levels=5, n0=4, s=6, R=4, seed=11, log2_nmax=10)
+    cfg, ctx, orc = _pair(W.LATTICE_6LEVEL, n_levels=5, n0=4, s=6, R=4, seed=11, log2_nmax=10)
     eps = 4e-4
     g = ctx.estimate(eps)
     o = orc.estimate(eps)
@@ -268,7 +268,7 @@ def test_algorithm1_matches_oracle():
 
 
 def test_device_status_not_converged():
-    cfg, ctx, orc = _pair(W.CONFIG2, R=1, rtol=1e-30, max_cycles=0)
+    cfg, ctx, orc = _pair(W.LATTICE_6LEVEL, R=1, rtol=1e-30, max_cycles=0)
     sums = torch.zeros(cfg["n_levels"] * 2, dtype=torch.float64, device="cuda")
     ctx.sample_levels([(2, 0, 2, 0, 1)], sums)
     assert ctx.device_status() == 5
@@ -310,7 +310,7 @@ MIXED = [("mixed_tf32", _tf32_u), ("mixed_bf16x3", _bf16x3_u)]
 
 @pytest.mark.parametrize("precision,ufun", MIXED)
 def test_mixed_fields_within_bound(precision, ufun):
-    cfg, ctx, orc = _pair(W.CONFIG3, n_levels=4, precision=precision)
+    cfg, ctx, orc = _pair(W.PRECISION_1024, n_levels=4, precision=precision)
     Y = W.random_normals(cfg["s"], 2, tag=40)
     for t in [0, 3]:
         k = ctx.fields(t, torch.from_numpy(Y)).cpu().numpy()
@@ -325,7 +325,7 @@ def test_split_bf16_more_accurate_than_tf32():
     field's largest log-error is at least 8x below the TF32 one."""
     errs = {}
     for precision in ["mixed_tf32", "mixed_bf16x3"]:
-        cfg, ctx, orc = _pair(W.CONFIG3, n_levels=6, precision=precision)
+        cfg, ctx, orc = _pair(W.PRECISION_1024, n_levels=6, precision=precision)
         Y = W.random_normals(cfg["s"], 3, tag=42)
         k = ctx.fields(5, torch.from_numpy(Y)).cpu().numpy()
         errs[precision] = max(np.max(np.abs(np.log(k[i] / orc.field(5, Y[i])))) for i in range(3))
@@ -335,7 +335,7 @@ def test_split_bf16_more_accurate_than_tf32():
 @pytest.mark.parametrize("precision,ufun", MIXED)
 def test_tensor_core_fields_many_samples(precision, ufun):
     """More samples than one tensor-core tile (256) and several cell tiles."""
-    cfg, ctx, orc = _pair(W.CONFIG3, n_levels=4, precision=precision)
+    cfg, ctx, orc = _pair(W.PRECISION_1024, n_levels=4, precision=precision)
     Y = W.random_normals(cfg["s"], 300, tag=41)
     k = ctx.fields(2, torch.from_numpy(Y)).cpu().numpy()
     assert np.all(np.isfinite(k)) and np.all(k > 0)
@@ -349,7 +349,7 @@ def test_tensor_core_fields_many_samples(precision, ufun):
 
 @pytest.mark.parametrize("precision,ufun", MIXED)
 def test_mixed_qoi_within_bound(precision, ufun):
-    cfg, ctx, orc = _pair(W.CONFIG3, n_levels=5, R=2, precision=precision)
+    cfg, ctx, orc = _pair(W.PRECISION_1024, n_levels=5, R=2, precision=precision)
     for (lv, r, n) in [(4, 0, 3), (2, 1, 0)]:
         sols, F = ctx.sample_solution(lv, r, n)
         ref = orc.sample(lv, r, n, want_u=True)
@@ -397,7 +397,7 @@ def test_smoothers_agree_fixed_cycles():
     whole-sample smoothers (residual and correction fused), TMA-tile and
     plain-tile smoothers run the same red-black sweeps; per-sample F agree to
     FP32 rounding of the residual's summation order (1e-5 relative)."""
-    cfg = W.scaled(W.CONFIG2, R=2, precision="mixed_tf32")
+    cfg = W.scaled(W.LATTICE_6LEVEL, R=2, precision="mixed_tf32")
     z = _genvec(cfg)
     ctx = M.Context.from_config(cfg, genvec=z)
     work = [(5, 0, 3, 0, 2), (4, 1, 4, 0, 2), (3, 0, 5, 1, 2), (1, 2, 6, 0, 1)]
@@ -412,7 +412,7 @@ def test_smoothers_agree_converged():
     """Converged mixed form (rtol 1e-10, levels up to 128x128, samples leave
     the refinement loop at different steps): per-sample F of the wavefront and
     TMA-tile smoothers agree within 1e-8 relative."""
-    cfg = W.scaled(W.CONFIG3, n_levels=5, R=2)
+    cfg = W.scaled(W.PRECISION_1024, n_levels=5, R=2)
     z = _genvec(cfg)
     ctx = M.Context.from_config(cfg, genvec=z)
     work = [(4, 0, 6, 0, 2), (3, 0, 3, 0, 1)]
@@ -423,7 +423,7 @@ def test_smoothers_agree_converged():
 
 
 def test_autotuner_report():
-    cfg = W.scaled(W.CONFIG2, R=2, precision="mixed_tf32")
+    cfg = W.scaled(W.LATTICE_6LEVEL, R=2, precision="mixed_tf32")
     ctx = M.Context.from_config(cfg, genvec=_genvec(cfg), max_samples=2048)
     info = ctx.smoother_info()
     assert info[0][0] == "gs"
@@ -436,7 +436,7 @@ def test_autotuner_report():
             assert name == "tma"
     with pytest.raises(M.MlqmcError):
         ctx.set_smoother(1, "tma")  # 16 x 16: no whole TMA tile with its halo inside the grid
-    c64 = M.Context.from_config(W.scaled(W.CONFIG2, R=2), genvec=_genvec(cfg))
+    c64 = M.Context.from_config(W.scaled(W.LATTICE_6LEVEL, R=2), genvec=_genvec(cfg))
     for t, (k, _) in enumerate(c64.smoother_info()):
         assert k == "gs" or (k == "whole" and (cfg["n0"] << t) <= 64)
     with pytest.raises(M.MlqmcError):
@@ -447,7 +447,7 @@ def test_fp64_whole_sample_smoother_matches_gs():
     """FP64 form: the whole-sample smoother (levels up to 64 x 64) multiplies by
     the stored 1/D like kb_gs and fuses residual and correction with the same
     arithmetic: per-sample F agree with the kb_gs path to 1e-13."""
-    cfg = W.scaled(W.CONFIG2, R=2)
+    cfg = W.scaled(W.LATTICE_6LEVEL, R=2)
     ctx = M.Context.from_config(cfg, genvec=_genvec(cfg))
     work = [(5, 0, 2, 0, 2), (3, 0, 3, 0, 2), (2, 0, 4, 1, 2)]
     ns = sum((ne - nb) * (re_ - rb) for (_, nb, ne, rb, re_) in work)
@@ -476,7 +476,7 @@ def test_graph_replay_equals_direct_path(precision):
     later ones replay it: sums and per-sample F are bit-identical to the
     launch-by-launch call; a different call runs directly; turning graphs
     off gives the same results again."""
-    cfg = W.scaled(W.CONFIG2, R=2, precision=precision)
+    cfg = W.scaled(W.LATTICE_6LEVEL, R=2, precision=precision)
     ctx = M.Context.from_config(cfg, genvec=_genvec(cfg))
     nl = cfg["n_levels"]
     work = [(5, 0, 2, 0, 2), (3, 1, 5, 0, 1), (1, 0, 7, 1, 2)]
@@ -514,7 +514,7 @@ def test_graph_replay_with_profiling():
     """Profiling through a replayed graph: each replay's kernel brackets are
     read back; per-kind launch counts grow by the same amount per call and
     the results stay those of the direct path."""
-    cfg = W.scaled(W.CONFIG2, R=2, precision="mixed_tf32")
+    cfg = W.scaled(W.LATTICE_6LEVEL, R=2, precision="mixed_tf32")
     ctx = M.Context.from_config(cfg, genvec=_genvec(cfg))
     nl = cfg["n_levels"]
     work = [(4, 0, 3, 0, 2), (2, 0, 4, 0, 2)]

@@ -60,7 +60,7 @@ def test_measured_statistics_match_oracle_and_rates_are_plausible():
     import workloads as W
     import paper_1806_05619_gb300 as M
 
-    cfg = W.scaled(W.CONFIG2, n_levels=5, s=20, R=8, log2_nmax=10)
+    cfg = W.scaled(W.LATTICE_6LEVEL, n_levels=5, s=20, R=8, log2_nmax=10)
     z, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
     ctx = M.Context.from_config(cfg, genvec=z)
     r = rates.measure(ctx, n_points=64, lambda_level=2, gamma_levels=3)

@@ -17,7 +17,7 @@ torch = pytest.importorskip("torch")
 
 @pytest.mark.parametrize("n0,levels,qoi", [(6, 5, "mean"), (2, 6, "center"), (6, 4, "center")])
 def test_fp64_solutions_match_oracle(n0, levels, qoi):
-    cfg, ctx, orc = _pair(W.CONFIG2, n0=n0, n_levels=levels, s=20, R=2, qoi=qoi, log2_nmax=8)
+    cfg, ctx, orc = _pair(W.LATTICE_6LEVEL, n0=n0, n_levels=levels, s=20, R=2, qoi=qoi, log2_nmax=8)
     for (lv, r, n) in [(levels - 1, 1, 3), (levels - 2, 0, 0)]:
         sols, F = ctx.sample_solution(lv, r, n)
         ref = orc.sample(lv, r, n, want_u=True)
@@ -30,7 +30,7 @@ def test_fp64_solutions_match_oracle(n0, levels, qoi):
 
 @pytest.mark.parametrize("precision,ufun", MIXED)
 def test_mixed_qoi_on_non_power_of_two_levels(precision, ufun):
-    cfg, ctx, orc = _pair(W.CONFIG3, n0=6, n_levels=5, s=40, R=2, precision=precision, log2_nmax=8)
+    cfg, ctx, orc = _pair(W.PRECISION_1024, n0=6, n_levels=5, s=40, R=2, precision=precision, log2_nmax=8)
     names = [k for k, _ in ctx.smoother_info()]
     assert names[4] == "tma" or names[4] == "stream" or names[4] == "tile"
     for (lv, r, n) in [(4, 1, 2), (2, 0, 5)]:

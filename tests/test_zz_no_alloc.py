@@ -30,7 +30,7 @@ def ctx():
     if not os.path.exists(M.LIB_PATH):
         M.build()
     assert torch.cuda.is_available()
-    cfg = W.scaled(W.CONFIG2, n_levels=5, R=8)
+    cfg = W.scaled(W.LATTICE_6LEVEL, n_levels=5, R=8)
     z, _ = O.cbc(cfg["s"], cfg["log2_nmax"])
     return cfg, M.Context.from_config(cfg, genvec=z)
 

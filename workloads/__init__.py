@@ -17,9 +17,10 @@ import numpy as np
 SEED_BASE = 20180614
 
 
-def _cfg(cid, **kw):
+def _cfg(pid, **kw):
+    """A problem: id pid (its seed is SEED_BASE + pid) and its parameters."""
     base = dict(
-        cid=cid,
+        pid=pid,
         n0=8,
         sigma=1.0,
         corr_len=0.3,
@@ -31,7 +32,7 @@ def _cfg(cid, **kw):
         rtol=0.0,
         max_cycles=60,
         sampler="lattice",
-        seed=SEED_BASE + cid,
+        seed=SEED_BASE + pid,
         R=16,
         log2_nmax=10,
         reuse=True,
@@ -42,24 +43,24 @@ def _cfg(cid, **kw):
 
 # 1: plain FP64 MG-MLMC with reuse: 4 levels 4x4..32x32, s=10, MC normals,
 #    fixed N_l = [512,128,32,8], centre QoI.
-CONFIG1 = _cfg(1, n_levels=4, n0=4, s=10, qoi="center", sampler="mc", R=1,
-               counts=[512, 128, 32, 8], log2_nmax=32)
+MC_4LEVEL = _cfg(1, n_levels=4, n0=4, s=10, qoi="center", sampler="mc", R=1,
+                 counts=[512, 128, 32, 8], log2_nmax=32)
 # 2: MG-MLQMC in FP64: 6 levels 8x8..256x256, s=100, 2^10 points on level 0
 #    halving per level, R=16 shifts, mean-of-u QoI.
-CONFIG2 = _cfg(2, n_levels=6, s=100, counts=[1024, 512, 256, 128, 64, 32], log2_nmax=10)
+LATTICE_6LEVEL = _cfg(2, n_levels=6, s=100, counts=[1024, 512, 256, 128, 64, 32], log2_nmax=10)
 # 3: precision form on one finest level of 1024x1024: s=400, lambda=0.1,
 #    batches of 256 samples, FP64 refinement to 1e-10 around FP32 cycles.
-CONFIG3 = _cfg(3, n_levels=8, s=400, corr_len=0.1, precision="mixed_tf32", rtol=1e-10,
-               batch=256, finest=7, log2_nmax=10)
+PRECISION_1024 = _cfg(3, n_levels=8, s=400, corr_len=0.1, precision="mixed_tf32", rtol=1e-10,
+                      batch=256, finest=7, log2_nmax=10)
 # 4: adaptive MLQMC with reuse, 7 levels 8x8..512x512, s=200, R=16,
 #    eps in {1e-2, 3e-3, 1e-3}.
-CONFIG4 = _cfg(4, n_levels=7, s=200, precision="mixed_tf32", rtol=1e-10,
-               eps=[1e-2, 3e-3, 1e-3], log2_nmax=16)
+ADAPTIVE_7LEVEL = _cfg(4, n_levels=7, s=200, precision="mixed_tf32", rtol=1e-10,
+                       eps=[1e-2, 3e-3, 1e-3], log2_nmax=16)
 # 5: large adaptive MLQMC: 9 levels 8x8..2048x2048, s=1000, lambda=0.05.
-CONFIG5 = _cfg(5, n_levels=9, s=1000, corr_len=0.05, precision="mixed_tf32", rtol=1e-10,
-               eps=[1e-4], log2_nmax=16)
+ADAPTIVE_9LEVEL = _cfg(5, n_levels=9, s=1000, corr_len=0.05, precision="mixed_tf32", rtol=1e-10,
+                       eps=[1e-4], log2_nmax=16)
 
-CONFIGS = {1: CONFIG1, 2: CONFIG2, 3: CONFIG3, 4: CONFIG4, 5: CONFIG5}
+PROBLEMS = {1: MC_4LEVEL, 2: LATTICE_6LEVEL, 3: PRECISION_1024, 4: ADAPTIVE_7LEVEL, 5: ADAPTIVE_9LEVEL}
 
 
 def fixed_count_work(counts, R):
