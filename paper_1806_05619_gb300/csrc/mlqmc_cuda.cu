@@ -838,6 +838,38 @@ __global__ void kb_resid64(FmgArgs A, int t, int B)
     }
 }
 
+// Mixed forms, the refinement step that opens level t: the FMG interpolation
+// u64 = P u_(t-1) (of the FP32 copy of the coarse solution, in FP32: the
+// arithmetic of kb_prolong) and r = 1 - A u64 in FP64 (that of kb_resid64) in
+// one pass, each cell interpolating its own value and its four neighbours'.
+__global__ void kb_prolong_resid64(FmgArgs A, int t, int B)
+{
+    const int n = A.lv[t].n, nc = n >> 1;
+    const uint32_t per = static_cast<uint32_t>(n) * static_cast<uint32_t>(n);
+    const double ih2 = static_cast<double>(n) * n;
+    GRID_STRIDE(idx, B * per)
+    {
+        const int i = static_cast<int>(idx / per);
+        if (inactive(A, i)) continue;
+        const int p = static_cast<int>(idx - i * per);
+        const int i2 = p / n, i1 = p - i2 * n;
+        const float* e = at<float>(A.lv[t - 1].u, i);
+        const Lv<float> L = view<float>(A, t, i);
+        const double up = widen(prolong_cell<float, float>(e, nc, i1, i2));
+        const double uw = i1 > 0 ? widen(prolong_cell<float, float>(e, nc, i1 - 1, i2)) : 0.0;
+        const double ue = i1 < n - 1 ? widen(prolong_cell<float, float>(e, nc, i1 + 1, i2)) : 0.0;
+        const double un = i2 > 0 ? widen(prolong_cell<float, float>(e, nc, i1, i2 - 1)) : 0.0;
+        const double us = i2 < n - 1 ? widen(prolong_cell<float, float>(e, nc, i1, i2 + 1)) : 0.0;
+        L.u64[p] = up;
+        const float* kx = L.kx + i2 * kx_pitch(n);
+        double acc = widen_pos(kx[i1]) * (up - uw);
+        acc = fma(widen_pos(kx[i1 + 1]), up - ue, acc);
+        acc = fma(widen_pos(L.ky[i2 * n + i1]), up - un, acc);
+        acc = fma(widen_pos(L.ky[(i2 + 1) * n + i1]), up - us, acc);
+        L.bc[p] = narrow(fma(-ih2, acc, 1.0));
+    }
+}
+
 // Refinement path: u64 += e.
 template <typename T>
 __global__ void kb_update64(FmgArgs A, int t, int B)
@@ -1712,7 +1744,11 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
         if (B == 0) break;
         const int64_t n = c->p.coarse_cells << t;
         const double es = sizeof(T), Mc = cells_of(c, t), Fc = faces_of(c, t);
-        if (refine) {
+        if (refine && MX) {
+            Timed tm(c, kProfTransfer, st,
+                     work_of<double>(B * (es * 0.25 * Mc + 8.0 * Mc + es * (2.0 * Fc + Mc)), B * 10.0 * Mc));
+            kb_prolong_resid64<<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
+        } else if (refine) {
             {
                 Timed tm(c, kProfTransfer, st, work_of<T>(B * (es * 0.25 + 8.0) * Mc, B * 8.0 * Mc));
                 kb_prolong<T, false, true><<<grid_for(c, B * n * n / 4), 256, 0, st>>>(A, t, B);
@@ -1721,6 +1757,8 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
                 Timed tm(c, kProfTransfer, st, work_of<double>(B * (8.0 * Mc + es * (2.0 * Fc + Mc)), B * 10.0 * Mc));
                 kb_resid64<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
             }
+        }
+        if (refine) {
             if (zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
             for (int m = 0; m < c->p.mu0; ++m) {
                 mlqmc_status s = vcycle_batched<T>(c, A, t, B, false, st);
