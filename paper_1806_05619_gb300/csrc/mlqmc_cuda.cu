@@ -1585,19 +1585,22 @@ mlqmc_status smooth_stream(mlqmc_ctx* c, const FmgArgs& A, int t, int B, int nsw
 
 // nsweeps sweeps of level t by the TMA-fed tiled smoother, two per launch, u
 // -> u2 swapped after each launch; pro: the first launch adds P e first.
+// zin: u is zero on entry (first launch only reads no u).
 mlqmc_status smooth_tma(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int first, int ones, bool pro,
-                        cudaStream_t st)
+                        cudaStream_t st, bool zin = false)
 {
     const int n = c->p.coarse_cells << t;
     const double Mc = cells_of(c, t), Fc = faces_of(c, t);
     while (nsweeps > 0) {
         const int ns = nsweeps >= 2 ? 2 : 1;
-        const Work w = work_of<float>(4.0 * B * ((ones ? 3.0 : 4.0) * Mc + 2.0 * Fc + (pro ? 0.25 * Mc : 0.0)),
-                                      B * (10.0 * ns * Mc + (pro ? 8.0 * Mc : 0.0)));
+        const Work w = work_of<float>(
+            4.0 * B * ((ones ? 3.0 : 4.0) * Mc - (zin ? Mc : 0.0) + 2.0 * Fc + (pro ? 0.25 * Mc : 0.0)),
+            B * (10.0 * ns * Mc + (pro ? 8.0 * Mc : 0.0)));
         Timed tm(c, kProfSmooth, st, w);
-        if (!mlqmc_tma::launch(A, t, n, B, ns, ones, first, pro, c->sm_count, st)) return MLQMC_ERR_CUDA;
+        if (!mlqmc_tma::launch(A, t, n, B, ns, ones, first, pro, zin, c->sm_count, st)) return MLQMC_ERR_CUDA;
         swap_u(c, A, t);
         pro = false;
+        zin = false;
         nsweeps -= ns;
     }
     return MLQMC_OK;
@@ -1606,32 +1609,44 @@ mlqmc_status smooth_tma(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int
 // nsweeps sweeps of level t by the whole-sample smoother in one launch, u in
 // place; pre: also the restricted residual; post: P e added first.
 mlqmc_status smooth_whole(mlqmc_ctx* c, const FmgArgs& A, int t, int B, int nsweeps, int first, int ones, bool pre,
-                          bool post, cudaStream_t st)
+                          bool post, cudaStream_t st, bool zin = false)
 {
     const int n = c->p.coarse_cells << t;
     const bool f64 = !is_mixed(c->p);
     const double Mc = cells_of(c, t), Fc = faces_of(c, t), es = f64 ? 8.0 : 4.0;
     Work w;
-    w.bytes = es * B * ((ones ? 2.0 : 3.0) * Mc + (f64 ? Mc : 0.0) + 2.0 * Fc + (post ? 0.25 * Mc : 0.0) +
-                        (pre ? 0.25 * Mc : 0.0));
+    w.bytes = es * B * ((ones ? 2.0 : 3.0) * Mc - (zin ? Mc : 0.0) + (f64 ? Mc : 0.0) + 2.0 * Fc +
+                        (post ? 0.25 * Mc : 0.0) + (pre ? 0.25 * Mc : 0.0));
     const double fl = B * (10.0 * nsweeps * Mc + (post ? 8.0 * Mc : 0.0) + (pre ? 11.0 * Mc : 0.0));
     if (f64) w.f64 = fl;
     else w.f32 = fl;
     Timed tm(c, kProfSmooth, st, w);
-    return mlqmc_whole::launch(A, t, n, B, nsweeps, ones, first, pre, post, f64, st) ? MLQMC_OK : MLQMC_ERR_CUDA;
+    return mlqmc_whole::launch(A, t, n, B, nsweeps, ones, first, pre, post, zin, f64, st) ? MLQMC_OK : MLQMC_ERR_CUDA;
+}
+
+// Whether the pre-smoother of level t starts a correction from zero without
+// reading u (so the V-cycle need not clear u first).
+template <typename T>
+bool zero_in_smoother(const mlqmc_ctx* c, int t)
+{
+    const int sk = smoother_of<T>(c, t);
+    return c->p.nu1 > 0 && (sk == MLQMC_SMOOTHER_WHOLE || sk == MLQMC_SMOOTHER_TMA);
 }
 
 // Pre-smoothing of level t and the restricted residual into bc of level t-1.
+// zin: u is zero on entry (a correction level below the cycle's top) and the
+// smoother clears it itself (zero_in_smoother).
 template <typename T>
-mlqmc_status presmooth_restrict(mlqmc_ctx* c, FmgArgs& A, int t, int B, int top_ones, cudaStream_t st)
+mlqmc_status presmooth_restrict(mlqmc_ctx* c, FmgArgs& A, int t, int B, int top_ones, cudaStream_t st,
+                                bool zin = false)
 {
     const int sk = smoother_of<T>(c, t);
     if (sk == MLQMC_SMOOTHER_WHOLE && c->p.nu1 > 0)  // residual and restriction in the same pass
-        return smooth_whole(c, A, t, B, c->p.nu1, 0, top_ones, true, false, st);
+        return smooth_whole(c, A, t, B, c->p.nu1, 0, top_ones, true, false, st, zin);
     if (sk == MLQMC_SMOOTHER_STREAM && c->p.nu1 > 0)  // residual and restriction fused into the last pass
         return smooth_stream(c, A, t, B, c->p.nu1, 0, top_ones, true, false, st);
     if (sk == MLQMC_SMOOTHER_TMA && c->p.nu1 > 0) {
-        if (smooth_tma(c, A, t, B, c->p.nu1, 0, top_ones, false, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
+        if (smooth_tma(c, A, t, B, c->p.nu1, 0, top_ones, false, st, zin) != MLQMC_OK) return MLQMC_ERR_CUDA;
     } else {
         smooth<T>(c, A, t, B, c->p.nu1, 0, top_ones, false, st);
     }
@@ -1661,8 +1676,10 @@ mlqmc_status vcycle_batched(mlqmc_ctx* c, FmgArgs& A, int t_top, int B, bool one
 {
     for (int t = t_top; t >= 1; --t) {
         const int top_ones = (t == t_top && ones) ? 1 : 0;
-        if (t < t_top && zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
-        if (presmooth_restrict<T>(c, A, t, B, top_ones, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
+        // a correction level starts from zero: cleared here, or by its smoother
+        const bool zin = t < t_top && zero_in_smoother<T>(c, t);
+        if (t < t_top && !zin && zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
+        if (presmooth_restrict<T>(c, A, t, B, top_ones, st, zin) != MLQMC_OK) return MLQMC_ERR_CUDA;
     }
     {
         const double N0 = cells_of(c, 0), n0 = c->p.coarse_cells, es = sizeof(T);

@@ -54,7 +54,7 @@ struct TGeom {
 
 template <int TILE, int NS, bool POST>
 __global__ void __launch_bounds__(kThreads, TGeom<TILE, POST>::ctas_per_sm)
-    kb_rbgs_tma(const __grid_constant__ Maps maps, FmgArgs A, int t, int B, int ones, int first)
+    kb_rbgs_tma(const __grid_constant__ Maps maps, FmgArgs A, int t, int B, int ones, int first, int zin)
 {
     using Gm = TGeom<TILE, POST>;
     constexpr int SU = Gm::SU, XW = Gm::XW, EC = Gm::EC;
@@ -69,7 +69,10 @@ __global__ void __launch_bounds__(kThreads, TGeom<TILE, POST>::ctas_per_sm)
     const int per = tx_n * tx_n;
     const int total = B * per;
     const float h2 = 1.0f / (static_cast<float>(n) * static_cast<float>(n));
-    const uint32_t tx_bytes = 4u * (SU * SU + XW * SU + (SU + 1) * SU + (ones ? 0 : SU * SU) + (POST ? EC * EC : 0));
+    // zin (pre-smoothing of a correction, never with POST): u is zero on entry,
+    // so its tile is cleared in shared memory instead of copied
+    const uint32_t tx_bytes =
+        4u * ((zin ? 0 : SU * SU) + XW * SU + (SU + 1) * SU + (ones ? 0 : SU * SU) + (POST ? EC * EC : 0));
 
     if (threadIdx.x == 0) {
         mbar_init(&full[0], 1);
@@ -85,7 +88,7 @@ __global__ void __launch_bounds__(kThreads, TGeom<TILE, POST>::ctas_per_sm)
         float* S = bufs + slot * Gm::buf;
         uint64_t* bar = &full[slot];
         mbar_arrive_tx(bar, tx_bytes);
-        tensor_load_3d(S + Gm::oU, &maps.u, bar, x0 - kH, y0 - kH, i);
+        if (!zin) tensor_load_3d(S + Gm::oU, &maps.u, bar, x0 - kH, y0 - kH, i);
         tensor_load_3d(S + Gm::oKX, &maps.kx, bar, x0 - kH, y0 - kH, i);
         tensor_load_3d(S + Gm::oKY, &maps.ky, bar, x0 - kH, y0 - kH, i);
         if (!ones) tensor_load_3d(S + Gm::oB, &maps.b, bar, x0 - kH, y0 - kH, i);
@@ -143,6 +146,10 @@ __global__ void __launch_bounds__(kThreads, TGeom<TILE, POST>::ctas_per_sm)
         if (!(A.active && !A.active[i])) {
             float* S = bufs + slot * Gm::buf;
             float* su = S + Gm::oU;
+            if (zin) {
+                for (int q = threadIdx.x; q < SU * SU; q += kThreads) su[q] = 0.0f;
+                __syncthreads();
+            }
             const float* sb = S + Gm::oB;
             const float* skx = S + Gm::oKX;
             const float* sky = S + Gm::oKY;
@@ -316,15 +323,17 @@ bool attrs()
 }
 
 template <int TILE, int NS, bool POST>
-void run(const Maps& m, const FmgArgs& A, int t, int B, int tiles, int ones, int first, int sm_count, cudaStream_t st)
+void run(const Maps& m, const FmgArgs& A, int t, int B, int tiles, int ones, int first, int zin, int sm_count,
+         cudaStream_t st)
 {
     using Gm = TGeom<TILE, POST>;
     const int cap = Gm::ctas_per_sm * sm_count;
-    kb_rbgs_tma<TILE, NS, POST><<<tiles < cap ? tiles : cap, kThreads, Gm::bytes, st>>>(m, A, t, B, ones, first);
+    kb_rbgs_tma<TILE, NS, POST><<<tiles < cap ? tiles : cap, kThreads, Gm::bytes, st>>>(m, A, t, B, ones, first, zin);
 }
 
 template <int TILE>
-bool go(const FmgArgs& A, int t, int n, int B, int ns, int ones, int first, bool post, int sm_count, cudaStream_t st)
+bool go(const FmgArgs& A, int t, int n, int B, int ns, int ones, int first, bool post, int zin, int sm_count,
+        cudaStream_t st)
 {
     using Gm = TGeom<TILE, true>;
     const LevelDesc& L = A.lv[t];
@@ -339,11 +348,11 @@ bool go(const FmgArgs& A, int t, int n, int B, int ns, int ones, int first, bool
     if (!ok) return false;
     const int tiles = B * (n / TILE) * (n / TILE);
     if (ns == 2) {
-        if (post) run<TILE, 2, true>(m, A, t, B, tiles, ones, first, sm_count, st);
-        else run<TILE, 2, false>(m, A, t, B, tiles, ones, first, sm_count, st);
+        if (post) run<TILE, 2, true>(m, A, t, B, tiles, ones, first, 0, sm_count, st);
+        else run<TILE, 2, false>(m, A, t, B, tiles, ones, first, zin, sm_count, st);
     } else {
-        if (post) run<TILE, 1, true>(m, A, t, B, tiles, ones, first, sm_count, st);
-        else run<TILE, 1, false>(m, A, t, B, tiles, ones, first, sm_count, st);
+        if (post) run<TILE, 1, true>(m, A, t, B, tiles, ones, first, 0, sm_count, st);
+        else run<TILE, 1, false>(m, A, t, B, tiles, ones, first, zin, sm_count, st);
     }
     return cudaGetLastError() == cudaSuccess;
 }
@@ -362,12 +371,12 @@ bool prepare()
     return encode_fn() != nullptr && attrs<32>();
 }
 
-bool launch(const FmgArgs& A, int t, int n, int B, int ns, int ones, int first, bool post, int sm_count,
+bool launch(const FmgArgs& A, int t, int n, int B, int ns, int ones, int first, bool post, bool zin, int sm_count,
             cudaStream_t st)
 {
     if (B <= 0) return true;
-    if (!supported(n) || t < 1 || A.lv[t].n != n || (ns != 1 && ns != 2)) return false;
-    return go<32>(A, t, n, B, ns, ones, first, post, sm_count, st);
+    if (!supported(n) || t < 1 || A.lv[t].n != n || (ns != 1 && ns != 2) || (zin && post)) return false;
+    return go<32>(A, t, n, B, ns, ones, first, post, zin ? 1 : 0, sm_count, st);
 }
 
 }  // namespace mlqmc_tma

@@ -19,7 +19,9 @@ bool prepare();
 // right-hand side 1, else bc of level t. post: add the coarse-grid correction
 // P u_{t-1} to the staged u before the sweeps. Returns false when a tensor
 // map cannot be encoded or the launch fails.
-bool launch(const mlqmc_dev::FmgArgs& A, int t, int n, int B, int ns, int ones, int first, bool post, int sm_count,
-            cudaStream_t st);
+// zin: u is zero on entry (pre-smoothing of a correction; not with post): its
+// tiles are cleared in shared memory instead of copied.
+bool launch(const mlqmc_dev::FmgArgs& A, int t, int n, int B, int ns, int ones, int first, bool post, bool zin,
+            int sm_count, cudaStream_t st);
 
 }  // namespace mlqmc_tma

@@ -53,7 +53,7 @@ __device__ __forceinline__ void team_sync()
 
 template <typename T, int N, bool PRE, bool POST>
 __global__ void __launch_bounds__(WGeom<T, N>::TS * WGeom<T, N>::SPC)
-    kb_rbgs_whole(FmgArgs A, int t, int B, int ns, int ones, int first)
+    kb_rbgs_whole(FmgArgs A, int t, int B, int ns, int ones, int first, int zin)
 {
     using Gm = WGeom<T, N>;
     constexpr uint32_t es = sizeof(T);
@@ -74,12 +74,14 @@ __global__ void __launch_bounds__(WGeom<T, N>::TS * WGeom<T, N>::SPC)
     if (!act) return;
     const int ic = i;
     T* gu = at<T>(A.lv[t].u, ic);
+    // zin (pre-smoothing of a correction, never with POST): u is zero on entry,
+    // so it is not read but cleared in shared memory
     if (ts == 0) {
-        uint32_t bytes = es * (N * N + N * XP + (N + 1) * N + (ones ? 0 : N * N) + (Gm::F64 ? N * N : 0) +
+        uint32_t bytes = es * ((zin ? 0 : N * N) + N * XP + (N + 1) * N + (ones ? 0 : N * N) + (Gm::F64 ? N * N : 0) +
                                (POST ? NC * NC : 0));
         uint64_t* bar = &bars[g];
         mbar_arrive_tx(bar, bytes);
-        bulk_load(S + Gm::oU, gu, es * N * N, bar);
+        if (!zin) bulk_load(S + Gm::oU, gu, es * N * N, bar);
         bulk_load(S + Gm::oKX, at<T>(A.lv[t].kx, ic), es * N * XP, bar);
         bulk_load(S + Gm::oKY, at<T>(A.lv[t].ky, ic), es * (N + 1) * N, bar);
         if (!ones) bulk_load(S + Gm::oB, at<T>(A.lv[t].bc, ic), es * N * N, bar);
@@ -94,6 +96,10 @@ __global__ void __launch_bounds__(WGeom<T, N>::TS * WGeom<T, N>::SPC)
         return;
     }
     T* su = S + Gm::oU;
+    if (zin) {
+        for (int q = ts; q < N * N; q += TS) su[q] = T(0);
+        team_sync<T, N>();
+    }
     const T* skx = S + Gm::oKX;
     const T* sky = S + Gm::oKY;
     const T* sb = S + Gm::oB;
@@ -199,14 +205,14 @@ bool attrs()
 }
 
 template <typename T, int N>
-void go(const FmgArgs& A, int t, int B, int ns, int ones, int first, bool pre, bool post, cudaStream_t st)
+void go(const FmgArgs& A, int t, int B, int ns, int ones, int first, bool pre, bool post, int zin, cudaStream_t st)
 {
     using Gm = WGeom<T, N>;
     const int grid = (B + Gm::SPC - 1) / Gm::SPC;
     const int threads = Gm::TS * Gm::SPC;
-    if (pre) kb_rbgs_whole<T, N, true, false><<<grid, threads, Gm::bytes, st>>>(A, t, B, ns, ones, first);
-    else if (post) kb_rbgs_whole<T, N, false, true><<<grid, threads, Gm::bytes, st>>>(A, t, B, ns, ones, first);
-    else kb_rbgs_whole<T, N, false, false><<<grid, threads, Gm::bytes, st>>>(A, t, B, ns, ones, first);
+    if (pre) kb_rbgs_whole<T, N, true, false><<<grid, threads, Gm::bytes, st>>>(A, t, B, ns, ones, first, zin);
+    else if (post) kb_rbgs_whole<T, N, false, true><<<grid, threads, Gm::bytes, st>>>(A, t, B, ns, ones, first, 0);
+    else kb_rbgs_whole<T, N, false, false><<<grid, threads, Gm::bytes, st>>>(A, t, B, ns, ones, first, zin);
 }
 
 }  // namespace
@@ -224,24 +230,24 @@ bool prepare()
            attrs<double, 8>() && attrs<double, 16>() && attrs<double, 32>() && attrs<double, 64>();
 }
 
-bool launch(const FmgArgs& A, int t, int n, int B, int ns, int ones, int first, bool pre, bool post, bool fp64,
+bool launch(const FmgArgs& A, int t, int n, int B, int ns, int ones, int first, bool pre, bool post, bool zin, bool fp64,
             cudaStream_t st)
 {
     if (B <= 0) return true;
-    if (!supported(n, fp64) || t < 1 || A.lv[t].n != n || ns < 0 || (pre && post)) return false;
+    if (!supported(n, fp64) || t < 1 || A.lv[t].n != n || ns < 0 || (pre && post) || (zin && post)) return false;
     if (fp64) {
         switch (n) {
-        case 8: go<double, 8>(A, t, B, ns, ones, first, pre, post, st); break;
-        case 16: go<double, 16>(A, t, B, ns, ones, first, pre, post, st); break;
-        case 32: go<double, 32>(A, t, B, ns, ones, first, pre, post, st); break;
-        default: go<double, 64>(A, t, B, ns, ones, first, pre, post, st); break;
+        case 8: go<double, 8>(A, t, B, ns, ones, first, pre, post, zin ? 1 : 0, st); break;
+        case 16: go<double, 16>(A, t, B, ns, ones, first, pre, post, zin ? 1 : 0, st); break;
+        case 32: go<double, 32>(A, t, B, ns, ones, first, pre, post, zin ? 1 : 0, st); break;
+        default: go<double, 64>(A, t, B, ns, ones, first, pre, post, zin ? 1 : 0, st); break;
         }
     } else {
         switch (n) {
-        case 8: go<float, 8>(A, t, B, ns, ones, first, pre, post, st); break;
-        case 16: go<float, 16>(A, t, B, ns, ones, first, pre, post, st); break;
-        case 32: go<float, 32>(A, t, B, ns, ones, first, pre, post, st); break;
-        default: go<float, 64>(A, t, B, ns, ones, first, pre, post, st); break;
+        case 8: go<float, 8>(A, t, B, ns, ones, first, pre, post, zin ? 1 : 0, st); break;
+        case 16: go<float, 16>(A, t, B, ns, ones, first, pre, post, zin ? 1 : 0, st); break;
+        case 32: go<float, 32>(A, t, B, ns, ones, first, pre, post, zin ? 1 : 0, st); break;
+        default: go<float, 64>(A, t, B, ns, ones, first, pre, post, zin ? 1 : 0, st); break;
         }
     }
     return cudaGetLastError() == cudaSuccess;

@@ -18,7 +18,9 @@ bool prepare();
 // (i1 + i2) even). ones: right-hand side 1, else bc of level t. post: add
 // the coarse-grid correction P u_{t-1} to u before the sweeps. pre:
 // afterwards write bc of level t-1 = mean over the 4 children of b - A u.
+// zin: u is zero on entry (pre-smoothing of a correction; not with post): it is
+// cleared in shared memory instead of read.
 bool launch(const mlqmc_dev::FmgArgs& A, int t, int n, int B, int ns, int ones, int first, bool pre, bool post,
-            bool fp64, cudaStream_t st);
+            bool zin, bool fp64, cudaStream_t st);
 
 }  // namespace mlqmc_whole
