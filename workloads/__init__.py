@@ -60,7 +60,11 @@ ADAPTIVE_7LEVEL = _cfg(4, n_levels=7, s=200, precision="mixed_tf32", rtol=1e-10,
 ADAPTIVE_9LEVEL = _cfg(5, n_levels=9, s=1000, corr_len=0.05, precision="mixed_tf32", rtol=1e-10,
                        eps=[1e-4], log2_nmax=16)
 
-PROBLEMS = {1: MC_4LEVEL, 2: LATTICE_6LEVEL, 3: PRECISION_1024, 4: ADAPTIVE_7LEVEL, 5: ADAPTIVE_9LEVEL}
+# 6: multi-index variant, grid level x V-cycle count (one context per cycle
+#    count mu0 in {1, 2, 3}): 4 levels 4x4..32x32, s=10, lattice, R=4.
+MIMC_4LEVEL = _cfg(6, n_levels=4, n0=4, s=10, R=4, log2_nmax=12, mus=[1, 2, 3], eps=[1e-3])
+PROBLEMS = {1: MC_4LEVEL, 2: LATTICE_6LEVEL, 3: PRECISION_1024, 4: ADAPTIVE_7LEVEL, 5: ADAPTIVE_9LEVEL,
+            6: MIMC_4LEVEL}
 
 
 def fixed_count_work(counts, R):
