@@ -732,7 +732,41 @@ def run_time_to_eps(M):
                    "S1_work": wm / wq, "S2_work": wm / wg, "S3_work": wq / wg})
     keys = ("S1", "S2", "S3", "S1_work", "S2_work", "S3_work")
     out["speedups"] = {"per_eps": sp, "mean": {k: float(np.mean([x[k] for x in sp])) for k in keys}}
+    out["mimc"] = run_mimc(M, cfg, genvec, model)
     return out
+
+
+def run_mimc(M, cfg, genvec, model):
+    """Multi-index variant (grid level x V-cycle count, the outlook of Sec. 7)
+    on the same 7-level problem in the fixed-cycle mixed form: contexts with
+    mu0 = 1, 2, 3 (levels adaptive, every cycle count at each level), against
+    Algorithm 1 with mu0 = 3 (the mean both converge to), in device time and in
+    work (cells of the FMG hierarchy x V-cycles per level, times samples and
+    shifts)."""
+    mus = (1, 2, 3)
+    c = dict(cfg)
+    c.update(precision="mixed_tf32", rtol=0.0)
+    ctxs = [M.Context.from_config(c, genvec=genvec, mu0=mu, max_samples=1 << 17) for mu in mus]
+    rows = []
+    for eps in cfg["eps"] + [3e-4]:
+        r = M.estimate_mimc(ctxs, eps)
+        a = ctxs[-1].estimate(eps)
+        w_mimc = float(cfg["R"] * sum(r["N"][m][t] * float(model[t]) * (mus[m] + (mus[m - 1] if m else 0))
+                                      for m in range(len(mus)) for t in range(len(r["N"][m]))))
+        w_alg1 = cfg["R"] * mus[-1] * float(np.dot(a["N"][:a["L"] + 1], model[:a["L"] + 1]))
+        rows.append({"eps": eps, "mimc": {"seconds": r["wall_seconds"], "gpu_seconds": r["gpu_seconds"], "Q": r["Q"],
+                                          "varQ": r["varQ"], "bias": r["bias"], "bias_cycles": r["bias_cycles"],
+                                          "L": r["L"], "N": r["N"], "rounds": r["rounds"],
+                                          "run_status": r["run_status"], "work": w_mimc},
+                     "alg1_mu3": {"seconds": a["wall_seconds"], "gpu_seconds": a["gpu_seconds"], "Q": a["Q"],
+                                  "varQ": a["varQ"], "bias": a["bias"], "L": a["L"], "N": a["N"][:a["L"] + 1],
+                                  "rounds": a["rounds"], "run_status": a["run_status"], "work": w_alg1},
+                     "gpu_time_ratio": a["gpu_seconds"] / r["gpu_seconds"], "work_ratio": w_alg1 / w_mimc})
+    for x in ctxs:
+        x.close()
+    return {"workload": "7 levels 8x8..512x512, s=200, lambda=0.3, R=16, mixed_tf32 with fixed cycles, "
+                        "mu0 in {1,2,3}, levels adaptive; ratios are Algorithm 1 (mu0=3) over the multi-index run",
+            "rows": rows}
 
 
 def main():

@@ -253,6 +253,78 @@ mlqmc_status mlqmc_estimate(mlqmc_ctx* c, double eps, const mlqmc_run_opts* opts
 mlqmc_status mlqmc_estimate_mlmc(mlqmc_ctx* c, double eps, const mlqmc_run_opts* opts, mlqmc_result* out);
 
 /*
+ * Multi-index variant: the second refinement direction is the number of
+ * V-cycles of the FMG solve (the outlook of Sec. 7, multi-index Monte Carlo
+ * with levels x V-cycles). Index (t, m): grid level t and the cycle count of
+ * a context c_m. For one sample y the mixed difference is
+ *   D_{t,m}(y) = [F_t^{hi}(y) - F_{t-1}^{hi}(y)] - [F_t^{lo}(y) - F_{t-1}^{lo}(y)]
+ * with F^{hi}, F^{lo} the QoI of the FMG solves of that y by c_hi and c_lo
+ * (F_{-1} = 0); with c_lo = NULL (m = 0) the second bracket is zero and D is
+ * the level difference of mlqmc_sample_levels. An FMG that ends at level k
+ * yields D_{t,m} for every t <= k, and these are recycled exactly as in eq.
+ * Upsilon-reuse.
+ *
+ * Runs mlqmc_sample_levels for `work` on c_hi and on c_lo (the same y: both
+ * contexts draw the same points and shifts), then on `stream`
+ *   d_sums[(t*R + r)*2 + 0] += sum of D_{t,m},  [.. + 1] += sum of D_{t,m}^2
+ * over the samples of shift r whose FMG level k >= t (reuse) or k == t.
+ *  d_sums  device, n_levels * R * 2 doubles, caller-owned, not cleared.
+ *  d_D     device or NULL: per sample in work order n_levels doubles,
+ *          D_{0..level,m} then zeros.
+ * c_lo, when given, must equal c_hi in every problem field, the generating
+ * vector and the modes, except mu0, which must be smaller (else INVALID_ARG).
+ * Work is validated as in mlqmc_sample_levels. Scratch for the per-sample
+ * QoI of both contexts (n_levels doubles per sample each) is grown on demand
+ * inside the contexts. Asynchronous like mlqmc_sample_levels; deterministic.
+ * Errors: INVALID_ARG, POINTS_EXHAUSTED, OOM, CUDA.
+ */
+mlqmc_status mlqmc_sample_mixed(mlqmc_ctx* c_hi, mlqmc_ctx* c_lo, const mlqmc_work* work, int32_t n_work,
+                                double* d_sums, double* d_D, void* stream);
+
+#define MLQMC_MIMC_MAX_M 8
+/* Result of mlqmc_estimate_mimc; index (t, m) is stored at [m*32 + t]. */
+typedef struct {
+    double Q;             /* sum over {0..L} x {0..K-1} of the recycled mean mixed differences */
+    double varQ;          /* variance of Q from the R shift replicates of the whole estimator */
+    double bias;          /* eq. bias on the level direction: |Ybar_L| / (2^alpha + 1), Ybar_l = sum_m Ybar_{l,m} */
+    double alpha;         /* least-squares rate of |Ybar_l|, l = 1..L */
+    double bias_cycles;   /* indicator of the cycle direction: sum_t |Ybar_{t,K-1}| (not tested) */
+    int32_t L;            /* finest level used */
+    int32_t K;            /* number of cycle counts (contexts) */
+    int32_t rounds;       /* rounds of sample doubling */
+    int32_t run_status;   /* 0 done; 7 finest available level reached with the bias test failing; 8 round cap */
+    int32_t alpha_clamped;
+    int32_t pad;
+    double wall_seconds;  /* host wall time of the whole run */
+    double gpu_seconds;   /* device time of all sample launches (CUDA events) */
+    int64_t N[MLQMC_MIMC_MAX_M * 32];   /* samples whose FMG ended at level t, direction m */
+    double Ybar[MLQMC_MIMC_MAX_M * 32]; /* recycled mean of D_{t,m} over shifts (eq. Upsilon-reuse-bar) */
+    double Vell[MLQMC_MIMC_MAX_M * 32]; /* its variance from the replicates (eq. sample_variances) */
+    double C[MLQMC_MIMC_MAX_M * 32];    /* cost per sample used by the index choice */
+} mlqmc_mimc_result;
+
+/*
+ * Multi-index MLQMC, levels x cycle counts: ctx[0..K-1] are compatible
+ * contexts (as for mlqmc_sample_mixed) with strictly increasing mu0; direction
+ * m uses ctx[m] and ctx[m-1]. Algorithm 1 with the level direction adaptive
+ * and the cycle direction complete: levels are added one at a time from
+ * L = 0; for the index set {0..L} x {0..K-1}, each round doubles N_{t,m}
+ * (0 -> 1 point x R shifts) of the index with the largest V_{t,m} / C_{t,m}
+ * (unsampled first, ties -> smallest m, then smallest t; opts->batched: every
+ * index with at least half the largest ratio) until varQ <= eps^2/2; then,
+ * for L >= 2, the bias test of mlqmc_estimate on Ybar_l = sum_m Ybar_{l,m}
+ * (the level differences of the largest cycle count, by telescoping in m)
+ * decides between stopping and adding a level. Cost: opts->cost_model 0
+ * gives C_{t,m} = (sum_{t'<=t} n_t'^2) (mu0_m + mu0_{m-1}) (mu0_{-1} = 0), 1
+ * the measured GPU time per sample. K in 1..MLQMC_MIMC_MAX_M; with K = 1 this
+ * is mlqmc_estimate. opts->max_rounds caps the rounds (0 -> 1000).
+ * Blocking; uses its own stream. Errors: INVALID_ARG, OOM, CUDA, and the
+ * device status of the contexts.
+ */
+mlqmc_status mlqmc_estimate_mimc(mlqmc_ctx* const* ctx, int32_t K, double eps, const mlqmc_run_opts* opts,
+                                 mlqmc_mimc_result* out);
+
+/*
  * The estimator from reuse sums (host only, no context or device needed): for
  * levels t = 0..L and shifts r < R, sums[(t*R + r)*2 + 0] = sum of dF_t over
  * the samples that enter level t's difference ([.. + 1] the sum of squares,

@@ -67,6 +67,21 @@ class Result(C.Structure):
     ]
 
 
+MIMC_MAX_M = 8
+
+
+class MimcResult(C.Structure):
+    _fields_ = [
+        ("Q", C.c_double), ("varQ", C.c_double), ("bias", C.c_double), ("alpha", C.c_double),
+        ("bias_cycles", C.c_double),
+        ("L", C.c_int32), ("K", C.c_int32), ("rounds", C.c_int32), ("run_status", C.c_int32),
+        ("alpha_clamped", C.c_int32), ("pad", C.c_int32),
+        ("wall_seconds", C.c_double), ("gpu_seconds", C.c_double),
+        ("N", C.c_int64 * (MIMC_MAX_M * 32)), ("Ybar", C.c_double * (MIMC_MAX_M * 32)),
+        ("Vell", C.c_double * (MIMC_MAX_M * 32)), ("C", C.c_double * (MIMC_MAX_M * 32)),
+    ]
+
+
 def build(verbose: bool = False) -> str:
     """Compile ``libmlqmc.so`` for sm_103a in-tree (nvcc)."""
     from . import buildlib as _b
@@ -88,6 +103,9 @@ def lib():
             L.mlqmc_sample_levels.argtypes = [vp, C.POINTER(Work), i32, vp, vp, vp]
             L.mlqmc_estimate.argtypes = [vp, C.c_double, C.POINTER(RunOpts), C.POINTER(Result)]
             L.mlqmc_estimate_mlmc.argtypes = [vp, C.c_double, C.POINTER(RunOpts), C.POINTER(Result)]
+            L.mlqmc_sample_mixed.argtypes = [vp, vp, C.POINTER(Work), i32, vp, vp, vp]
+            L.mlqmc_estimate_mimc.argtypes = [C.POINTER(vp), i32, C.c_double, C.POINTER(RunOpts),
+                                              C.POINTER(MimcResult)]
             L.mlqmc_nystrom_modes.argtypes = [C.c_double, C.c_double, C.c_double, i32, i32, dp, dp]
             L.mlqmc_get_device_status.argtypes = [vp, vp]
             L.mlqmc_status_string.argtypes = [C.c_int]
@@ -112,6 +130,7 @@ def lib():
             L.mlqmc_launch_count.argtypes = [vp]
             L.mlqmc_launch_count.restype = i64
             for name in ["mlqmc_create", "mlqmc_sample_levels", "mlqmc_estimate", "mlqmc_estimate_mlmc",
+                         "mlqmc_sample_mixed", "mlqmc_estimate_mimc",
                          "mlqmc_nystrom_modes",
                          "mlqmc_get_device_status",
                          "mlqmc_cbc_genvec", "mlqmc_modes", "mlqmc_point_bits", "mlqmc_normals", "mlqmc_fields",
@@ -266,6 +285,17 @@ class Context:
         _check(lib().mlqmc_sample_levels(self.h, arr, len(work), _ptr(sums), _ptr(F), _stream(stream)),
                "mlqmc_sample_levels")
 
+    def sample_mixed(self, lo, work: Iterable, sums, D=None, stream=None):
+        """Accumulate the sums of the mixed differences D_{t,m} (this context's
+        cycle count against ``lo``'s; ``lo=None`` for the first direction) into
+        ``sums`` (device n_levels x R x 2, float64); per-sample D into ``D``."""
+        work = list(work)
+        arr = (Work * max(1, len(work)))()
+        for i, (lv, nb, ne, rb, re_) in enumerate(work):
+            arr[i] = Work(level=lv, pad=0, n_begin=nb, n_end=ne, r_begin=rb, r_end=re_)
+        _check(lib().mlqmc_sample_mixed(self.h, lo.h if lo is not None else None, arr, len(work), _ptr(sums),
+                                        _ptr(D), _stream(stream)), "mlqmc_sample_mixed")
+
     def device_status(self, stream=None):
         return lib().mlqmc_get_device_status(self.h, _stream(stream))
 
@@ -382,3 +412,24 @@ class Context:
 
     def launch_count(self) -> int:
         return int(lib().mlqmc_launch_count(self.h))
+
+
+def estimate_mimc(contexts, eps, max_rounds=0, cost_model=0, batched=False):
+    """Multi-index MLQMC (grid level x V-cycle count): Algorithm 1 over the
+    levels with every cycle count at each level; ``contexts`` differ only in
+    mu0, strictly increasing. Entries of N, Ybar, Vell and C are indexed
+    [m][t], t = 0..L."""
+    K = len(contexts)
+    hs = (C.c_void_p * max(1, K))(*[c.h for c in contexts])
+    o = RunOpts(max_rounds=max_rounds, cost_model=cost_model, batched=1 if batched else 0)
+    res = MimcResult()
+    _check(lib().mlqmc_estimate_mimc(hs, K, float(eps), C.byref(o), C.byref(res)), "mlqmc_estimate_mimc")
+    nl = res.L + 1
+
+    def grid(a):
+        return [[a[m * 32 + t] for t in range(nl)] for m in range(K)]
+
+    return dict(Q=res.Q, varQ=res.varQ, bias=res.bias, alpha=res.alpha, bias_cycles=res.bias_cycles, L=res.L,
+                K=res.K, rounds=res.rounds, run_status=res.run_status, alpha_clamped=res.alpha_clamped,
+                wall_seconds=res.wall_seconds, gpu_seconds=res.gpu_seconds,
+                N=grid(res.N), Ybar=grid(res.Ybar), Vell=grid(res.Vell), C=grid(res.C))

@@ -1990,6 +1990,9 @@ void free_ctx(mlqmc_ctx* c)
     if (!c) return;
     cudaFree(c->d_psi);
     cudaFree(c->d_psi32);
+    cudaFree(c->d_mix_F);
+    cudaFree(c->d_mix_S);
+    cudaFree(c->d_mix_W);
     cudaFree(c->d_grp_start);
     cudaFree(c->d_grp_b);
     cudaFree(c->d_grp_m);
@@ -2124,6 +2127,11 @@ mlqmc_status setup_matern(mlqmc_ctx* c, const mlqmc_problem* p)
     c->modes.b.assign(s, -1);
     c->modes.K1 = 0;
     c->Ka = 1;
+    // FNV-1a of the nodal eigenfunctions: contexts of one multi-index run must share them
+    uint64_t h = 1469598103934665603ull;
+    const unsigned char* bytes = reinterpret_cast<const unsigned char*>(p->nystrom_psi);
+    for (size_t i = 0; i < static_cast<size_t>(M) * s * sizeof(double); ++i) h = (h ^ bytes[i]) * 1099511628211ull;
+    c->psi_hash = h;
     std::vector<double> wpsi(static_cast<size_t>(M) * s), sq(s);
     for (int q = 0; q < M; ++q)
         for (int j = 0; j < s; ++j)

@@ -100,6 +100,7 @@ struct mlqmc_ctx {
     float* d_c32 = nullptr;  // mixed forms: FP32 KL coefficients of the chunk's samples (max_samples x s)
     bool c32_ready = false;  // d_c32 holds the current chunk's coefficients (set inside run_chunk)
     bool matern = false;
+    uint64_t psi_hash = 0;  // Matern: hash of the caller's nodal eigenfunctions
     double* d_psi_dense = nullptr;
     size_t dense_off[MLQMC_MAX_LEVELS] = {};
 
@@ -120,6 +121,14 @@ struct mlqmc_ctx {
     double* d_norms = nullptr;
     double* d_part = nullptr;  // partial residual sums of the converged forms (samples x chunks), grown on demand
     int64_t part_cap = 0;
+    // multi-index runs (mlqmc_sample_mixed): per-sample QoI in work order and
+    // a throw-away sums buffer for the inner mlqmc_sample_levels call, the
+    // work-item table on the device; grown on demand
+    double* d_mix_F = nullptr;
+    double* d_mix_S = nullptr;
+    int64_t mix_cap = 0;
+    void* d_mix_W = nullptr;
+    int mix_wcap = 0;
     int* d_active = nullptr;
     int* d_count = nullptr;
     SampleDesc* h_samples = nullptr;  // pinned staging

@@ -48,9 +48,10 @@ def test_struct_layouts_match_header():
 #include <stddef.h>
 #include "mlqmc.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(mlqmc_problem), offsetof(mlqmc_problem, genvec),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(mlqmc_problem), offsetof(mlqmc_problem, genvec),
          offsetof(mlqmc_problem, reuse), sizeof(mlqmc_work), sizeof(mlqmc_run_opts), sizeof(mlqmc_result),
-         offsetof(mlqmc_result, C));
+         offsetof(mlqmc_result, C), sizeof(mlqmc_mimc_result), offsetof(mlqmc_mimc_result, N),
+         offsetof(mlqmc_mimc_result, C));
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -60,8 +61,23 @@ int main(void) {
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), cfile, "-o", exe])
         vals = [int(v) for v in subprocess.check_output([exe]).split()]
     want = [C.sizeof(M.Problem), M.Problem.genvec.offset, M.Problem.reuse.offset, C.sizeof(M.Work),
-            C.sizeof(M.RunOpts), C.sizeof(M.Result), M.Result.C.offset]
+            C.sizeof(M.RunOpts), C.sizeof(M.Result), M.Result.C.offset, C.sizeof(M.MimcResult),
+            M.MimcResult.N.offset, M.MimcResult.C.offset]
     assert vals == want
+
+
+def test_multi_index_entries_reject_bad_arguments_before_touching_the_device(lib):
+    w = (M.Work * 1)(M.Work(level=0, pad=0, n_begin=0, n_end=1, r_begin=0, r_end=1))
+    sums = C.c_void_p(256)  # never dereferenced: the calls return first
+    assert lib.mlqmc_sample_mixed(None, None, w, 1, sums, None, None) == 1
+    res = M.MimcResult()
+    o = M.RunOpts()
+    hs = (C.c_void_p * 2)()
+    assert lib.mlqmc_estimate_mimc(None, 1, 1e-3, C.byref(o), C.byref(res)) == 1
+    assert lib.mlqmc_estimate_mimc(hs, 0, 1e-3, C.byref(o), C.byref(res)) == 1   # K < 1
+    assert lib.mlqmc_estimate_mimc(hs, 9, 1e-3, C.byref(o), C.byref(res)) == 1   # K > MLQMC_MIMC_MAX_M
+    assert lib.mlqmc_estimate_mimc(hs, 2, 1e-3, C.byref(o), C.byref(res)) == 1   # NULL contexts
+    assert lib.mlqmc_estimate_mimc(hs, 2, 0.0, C.byref(o), C.byref(res)) == 1    # eps <= 0
 
 
 def test_status_strings(lib):
