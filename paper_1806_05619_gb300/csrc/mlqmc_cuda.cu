@@ -840,13 +840,17 @@ __global__ void kb_resid64(FmgArgs A, int t, int B)
 
 // Mixed forms, the refinement step that opens level t: the FMG interpolation
 // u64 = P u_(t-1) (of the FP32 copy of the coarse solution, in FP32: the
-// arithmetic of kb_prolong) and r = 1 - A u64 in FP64 (that of kb_resid64) in
-// one pass, each cell interpolating its own value and its four neighbours'.
+// arithmetic of kb_prolong) and r = 1 - A u64 in one pass, each cell
+// interpolating its own value and its four neighbours'. Every input of this
+// residual is an FP32 number (u64 holds the widened FP32 interpolant), so it
+// is formed with FP32 error-free transformations (resid_f32x2) to within a
+// few units of 2^-48 of the terms, as accurate as the FP64 evaluation of
+// kb_resid64 before r is rounded to FP32, and without the FP64 pipe.
 __global__ void kb_prolong_resid64(FmgArgs A, int t, int B)
 {
     const int n = A.lv[t].n, nc = n >> 1;
     const uint32_t per = static_cast<uint32_t>(n) * static_cast<uint32_t>(n);
-    const double ih2 = static_cast<double>(n) * n;
+    const float ih2 = static_cast<float>(n) * static_cast<float>(n);  // exact: n = coarse_cells 2^t
     GRID_STRIDE(idx, B * per)
     {
         const int i = static_cast<int>(idx / per);
@@ -855,18 +859,17 @@ __global__ void kb_prolong_resid64(FmgArgs A, int t, int B)
         const int i2 = p / n, i1 = p - i2 * n;
         const float* e = at<float>(A.lv[t - 1].u, i);
         const Lv<float> L = view<float>(A, t, i);
-        const double up = widen(prolong_cell<float, float>(e, nc, i1, i2));
-        const double uw = i1 > 0 ? widen(prolong_cell<float, float>(e, nc, i1 - 1, i2)) : 0.0;
-        const double ue = i1 < n - 1 ? widen(prolong_cell<float, float>(e, nc, i1 + 1, i2)) : 0.0;
-        const double un = i2 > 0 ? widen(prolong_cell<float, float>(e, nc, i1, i2 - 1)) : 0.0;
-        const double us = i2 < n - 1 ? widen(prolong_cell<float, float>(e, nc, i1, i2 + 1)) : 0.0;
-        L.u64[p] = up;
+        // the interpolated u and the faces are FP32 numbers, so the residual
+        // of the FP64 u64 = widen(u) is evaluated exactly enough in FP32 pairs
+        const float up = prolong_cell<float, float>(e, nc, i1, i2);
+        const float uv[4] = {i1 > 0 ? prolong_cell<float, float>(e, nc, i1 - 1, i2) : 0.0f,
+                             i1 < n - 1 ? prolong_cell<float, float>(e, nc, i1 + 1, i2) : 0.0f,
+                             i2 > 0 ? prolong_cell<float, float>(e, nc, i1, i2 - 1) : 0.0f,
+                             i2 < n - 1 ? prolong_cell<float, float>(e, nc, i1, i2 + 1) : 0.0f};
+        L.u64[p] = widen(up);
         const float* kx = L.kx + i2 * kx_pitch(n);
-        double acc = widen_pos(kx[i1]) * (up - uw);
-        acc = fma(widen_pos(kx[i1 + 1]), up - ue, acc);
-        acc = fma(widen_pos(L.ky[i2 * n + i1]), up - un, acc);
-        acc = fma(widen_pos(L.ky[(i2 + 1) * n + i1]), up - us, acc);
-        L.bc[p] = narrow(fma(-ih2, acc, 1.0));
+        const float kv[4] = {kx[i1], kx[i1 + 1], L.ky[i2 * n + i1], L.ky[(i2 + 1) * n + i1]};
+        L.bc[p] = resid_f32x2(kv, up, uv, ih2);
     }
 }
 
