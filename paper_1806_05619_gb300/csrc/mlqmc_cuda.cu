@@ -848,28 +848,72 @@ __global__ void kb_resid64(FmgArgs A, int t, int B)
 // kb_resid64 before r is rounded to FP32, and without the FP64 pipe.
 __global__ void kb_prolong_resid64(FmgArgs A, int t, int B)
 {
+    // one thread per coarse cell (I1, I2), i.e. per 2 x 2 quad of fine cells:
+    // the quad and its ring of 8 fine neighbours all interpolate from the
+    // 3 x 3 coarse block around (I1, I2), odd-reflected across the boundary as
+    // in prolong_cell (a fine cell's out-of-range coarse neighbour is minus
+    // the value in its parent's own row or column)
     const int n = A.lv[t].n, nc = n >> 1;
-    const uint32_t per = static_cast<uint32_t>(n) * static_cast<uint32_t>(n);
+    const uint32_t per = static_cast<uint32_t>(nc) * static_cast<uint32_t>(nc);
     const float ih2 = static_cast<float>(n) * static_cast<float>(n);  // exact: n = coarse_cells 2^t
     GRID_STRIDE(idx, B * per)
     {
         const int i = static_cast<int>(idx / per);
         if (inactive(A, i)) continue;
-        const int p = static_cast<int>(idx - i * per);
-        const int i2 = p / n, i1 = p - i2 * n;
+        const int q = static_cast<int>(idx - i * per);
+        const int I2 = q / nc, I1 = q - I2 * nc;
         const float* e = at<float>(A.lv[t - 1].u, i);
         const Lv<float> L = view<float>(A, t, i);
-        // the interpolated u and the faces are FP32 numbers, so the residual
-        // of the FP64 u64 = widen(u) is evaluated exactly enough in FP32 pairs
-        const float up = prolong_cell<float, float>(e, nc, i1, i2);
-        const float uv[4] = {i1 > 0 ? prolong_cell<float, float>(e, nc, i1 - 1, i2) : 0.0f,
-                             i1 < n - 1 ? prolong_cell<float, float>(e, nc, i1 + 1, i2) : 0.0f,
-                             i2 > 0 ? prolong_cell<float, float>(e, nc, i1, i2 - 1) : 0.0f,
-                             i2 < n - 1 ? prolong_cell<float, float>(e, nc, i1, i2 + 1) : 0.0f};
-        L.u64[p] = widen(up);
-        const float* kx = L.kx + i2 * kx_pitch(n);
-        const float kv[4] = {kx[i1], kx[i1 + 1], L.ky[i2 * n + i1], L.ky[(i2 + 1) * n + i1]};
-        L.bc[p] = resid_f32x2(kv, up, uv, ih2);
+        float E[3][3];  // E[dy + 1][dx + 1]
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int x = I1 + dx, y = I2 + dy;
+                const bool ox = x < 0 || x >= nc, oy = y < 0 || y >= nc;
+                const float v = e[(oy ? I2 : y) * nc + (ox ? I1 : x)];
+                E[dy + 1][dx + 1] = (ox != oy) ? -v : v;
+            }
+        // fine cells 2I + f, f = -1..2 per axis (the four ring corners unused):
+        // parent offset (f - 1) / 2 rounded down, coarse neighbour towards the
+        // cell's side (+1 for odd f, -1 for even f); cells outside the grid are 0
+        float U[4][4];
+#pragma unroll
+        for (int fy = -1; fy <= 2; ++fy)
+#pragma unroll
+            for (int fx = -1; fx <= 2; ++fx) {
+                const bool ring_x = fx < 0 || fx > 1, ring_y = fy < 0 || fy > 1;
+                if (ring_x && ring_y) {
+                    U[fy + 1][fx + 1] = 0.0f;
+                    continue;
+                }
+                const int i1 = 2 * I1 + fx, i2 = 2 * I2 + fy;
+                if (i1 < 0 || i1 >= n || i2 < 0 || i2 >= n) {
+                    U[fy + 1][fx + 1] = 0.0f;
+                    continue;
+                }
+                const int px = fx < 0 ? -1 : (fx > 1 ? 1 : 0), py = fy < 0 ? -1 : (fy > 1 ? 1 : 0);
+                const int sx = (fx & 1) ? 1 : -1, sy = (fy & 1) ? 1 : -1;
+                const float a = E[py + 1][px + 1];
+                const float bx = E[py + 1][px + sx + 1];
+                const float cy = E[py + sy + 1][px + 1];
+                const float d = E[py + sy + 1][px + sx + 1];
+                U[fy + 1][fx + 1] = fmaf(0.5625f, a, fmaf(0.1875f, bx + cy, 0.0625f * d));
+            }
+        // residual of each quad cell: every input an FP32 number (pairs, as resid_f32x2 states)
+#pragma unroll
+        for (int qy = 0; qy < 2; ++qy)
+#pragma unroll
+            for (int qx = 0; qx < 2; ++qx) {
+                const int i1 = 2 * I1 + qx, i2 = 2 * I2 + qy;
+                const int p = i2 * n + i1;
+                const float up = U[qy + 1][qx + 1];
+                const float uv[4] = {U[qy + 1][qx], U[qy + 1][qx + 2], U[qy][qx + 1], U[qy + 2][qx + 1]};
+                const float* kx = L.kx + i2 * kx_pitch(n);
+                const float kv[4] = {kx[i1], kx[i1 + 1], L.ky[i2 * n + i1], L.ky[(i2 + 1) * n + i1]};
+                L.u64[p] = widen(up);
+                L.bc[p] = resid_f32x2(kv, up, uv, ih2);
+            }
     }
 }
 
@@ -1767,7 +1811,7 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
         if (refine && MX) {
             Timed tm(c, kProfTransfer, st,
                      work_of<double>(B * (es * 0.25 * Mc + 8.0 * Mc + es * (2.0 * Fc + Mc)), B * 10.0 * Mc));
-            kb_prolong_resid64<<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
+            kb_prolong_resid64<<<grid_for(c, B * (n / 2) * (n / 2)), 256, 0, st>>>(A, t, B);
         } else if (refine) {
             {
                 Timed tm(c, kProfTransfer, st, work_of<T>(B * (es * 0.25 + 8.0) * Mc, B * 8.0 * Mc));
