@@ -84,21 +84,27 @@ def n_samples(work):
 # --------------------------------------------------------------------------- #
 # Roofline denominators                                                         #
 # --------------------------------------------------------------------------- #
-HBM_GBS = 6755.5          # measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)
-BF16_TFLOPS = 1925.0      # measured cuBLAS bf16 burst (MEASURED_PEAKS.json bf16_tflops)
+# fallbacks when MEASURED_PEAKS.json is absent (one earlier GB300 measurement);
+# measured_peaks_override replaces them with this machine's figures
+HBM_GBS = 6800.0
+BF16_TFLOPS = 1900.0
+HBM_SRC = "fallback 6.8 TB/s (no measured copy bandwidth on this machine)"
+TC_SRC = "fallback bf16 1.9 PFLOP/s x nominal tf32/bf16 ratio"
 TF32_TFLOPS = BF16_TFLOPS * 1.1 / 2.25   # measured bf16 x nominal tf32/bf16 ratio (1.1 / 2.25 PFLOP/s dense)
 FP64_TFLOPS = 1.25        # nominal GB300 FP64 (an FMA probe measured 1.20)
 FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz = 80.5
 
 
 def measured_peaks_override():
-    global HBM_GBS, BF16_TFLOPS, TF32_TFLOPS
+    global HBM_GBS, BF16_TFLOPS, TF32_TFLOPS, HBM_SRC, TC_SRC
     pk = measured_peaks()
     if pk.get("hbm_gbs"):
         HBM_GBS = float(pk["hbm_gbs"])
+        HBM_SRC = "measured copy bandwidth (MEASURED_PEAKS.json)"
     if pk.get("bf16_tflops"):
         BF16_TFLOPS = float(pk["bf16_tflops"])
         TF32_TFLOPS = BF16_TFLOPS * 1.1 / 2.25
+        TC_SRC = "measured bf16 burst x nominal tf32/bf16 ratio"
 
 
 KIND_KERNELS = {
@@ -216,11 +222,9 @@ def kind_roofline(ms, work):
          "fp32_tflops": work["f32"] / t / 1e12, "tc_tflops": work["ftc"] / t / 1e12,
          "algorithmic_bytes": work["bytes"]}
     if best[0] == "hbm":
-        r.update(bound="hbm", achieved=r["gbs"], peak=HBM_GBS, unit="GB/s",
-                 peak_source="measured copy bandwidth (MEASURED_PEAKS.json)")
+        r.update(bound="hbm", achieved=r["gbs"], peak=HBM_GBS, unit="GB/s", peak_source=HBM_SRC)
     elif best[0] == "tensor":
-        r.update(bound="tensor", achieved=r["tc_tflops"], peak=TF32_TFLOPS, unit="TFLOP/s",
-                 peak_source="measured bf16 burst x nominal tf32/bf16 ratio")
+        r.update(bound="tensor", achieved=r["tc_tflops"], peak=TF32_TFLOPS, unit="TFLOP/s", peak_source=TC_SRC)
     elif best[0] == "alu64":
         r.update(bound="alu", achieved=r["fp64_tflops"], peak=FP64_TFLOPS, unit="TFLOP/s",
                  peak_source="FP64 1.25 TFLOP/s (nominal GB300 figure; FMA probe 1.20)")
