@@ -52,6 +52,8 @@ def parse():
                     help="form of the main measurement (the other form is reported under 'mixed')")
     ap.add_argument("--no-precision", action="store_true", help="skip the 1024x1024 precision-form comparison")
     ap.add_argument("--no-tte", action="store_true", help="skip the time-to-epsilon runs of Algorithm 1")
+    ap.add_argument("--no-matern", action="store_true",
+                    help="skip the Matern-covariance step (Nystrom eigenpairs) in both forms")
     ap.add_argument("--smoother", default="auto", choices=["auto", "stream", "tma", "tile"],
                     help="mixed form: force this smoother on every level it handles (default: the autotuner's pick)")
     ap.add_argument("--smoother-plan", default="",
@@ -522,6 +524,13 @@ def run_ours(args):
     if not args.no_tte and rank == 0 and args.counts_div == 1:
         tte = run_time_to_eps(M)
 
+    matern = None
+    if not args.no_matern and rank == 0 and args.counts_div == 1:
+        try:
+            matern = run_matern(cfg, work, genvec, dev, stream, flush, M)
+        except Exception as e:  # reported in the line; the main measurement stands
+            matern = {"error": f"{type(e).__name__}: {e}"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         counts = [max(1, c // 2) for c in cfg["counts"]]
@@ -561,9 +570,53 @@ def run_ours(args):
             line["precision_form"] = precision_form
         if tte:
             line["time_to_eps"] = tte
+        if matern:
+            line["matern"] = matern
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_matern(cfg, work, genvec, dev, stream, flush, M, steps=5, warmup=3):
+    """The same 6-level step with the Matern covariance (eq. matern, nu = 1,
+    the main step's lambda and sigma) whose KL modes are Nystrom eigenpairs on
+    16 x 16 nodes (Sec. 5): the eigensolve and create times (the per-level
+    Nystrom interpolation runs at create) and device-timed steps in the FP64
+    and mixed TF32 forms, L2 flushed between steps."""
+    import torch
+
+    nu, m = 1.0, 16
+    t0 = time.perf_counter()
+    th, ps = M.nystrom_modes(nu, cfg["corr_len"], cfg["sigma"], m, cfg["s"])
+    out = {"workload": f"6 levels 8x8..256x256, s={cfg['s']} Nystrom modes of the Matern covariance "
+                       f"(nu={nu}, lambda={cfg['corr_len']}, sigma={cfg['sigma']}) on {m}x{m} nodes; the main "
+                       "step's counts, shifts and FMG",
+           "eigensolve_seconds": time.perf_counter() - t0}
+    ns = n_samples(work)
+    sums = torch.zeros(cfg["n_levels"] * cfg["R"] * 2, dtype=torch.float64, device=dev)
+    for prec in ("fp64", "mixed_tf32"):
+        c = dict(cfg)
+        c["precision"] = prec
+        t0 = time.perf_counter()
+        ctx = M.Context.from_config(c, genvec=genvec, max_samples=ns, covariance="matern", matern_nu=nu,
+                                    nystrom_m=m, nystrom_theta=th, nystrom_psi=ps)
+        torch.cuda.synchronize(dev)  # the per-level interpolation it queued
+        create_s = time.perf_counter() - t0
+
+        def step():
+            sums.zero_()
+            ctx.sample_levels(work, sums, stream=stream)
+
+        for _ in range(warmup):
+            step()
+        ctx.check_device(stream)
+        torch.cuda.synchronize(dev)
+        ms = float(np.mean(timed_steps(step, steps, stream, flush)))
+        ctx.check_device(stream)
+        out[prec] = {"create_seconds": create_s, "ms_per_step": ms, "samples_per_s": ns / (ms * 1e-3)}
+        ctx.close()
+    out["mixed_speedup"] = out["fp64"]["ms_per_step"] / out["mixed_tf32"]["ms_per_step"]
+    return out
 
 
 def run_mixed_same_workload(args, cfg64, work, genvec, dev, stream, flush, M):
