@@ -110,6 +110,8 @@ def lib():
             L.or_field.argtypes = [C.c_void_p, C.c_int, dp, dp]
             L.or_field_z.argtypes = [C.c_void_p, C.c_int, dp, dp]
             L.or_apply_A.argtypes = [C.c_int, dp, dp, dp]
+            L.or_prolong_add.argtypes = [C.c_int, dp, dp]
+            L.or_prolong_add.restype = None
             L.or_sample.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_uint64, dp, dp, ip, C.c_int, ip, ip]
             L.or_fmg_fields.argtypes = [C.c_void_p, C.c_int, dp, dp, dp, dp, ip]
             L.or_vcycle_fields.argtypes = [C.c_void_p, C.c_int, dp, dp, dp]
@@ -200,6 +202,15 @@ def apply_A(n, k, u):
     u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
     out = np.zeros(n * n)
     lib().or_apply_A(int(n), _dp(k), _dp(u), _dp(out))
+    return out
+
+
+def prolong(nc, e):
+    """Cell-centred bilinear prolongation of a coarse nc x nc grid function to
+    2nc x 2nc with the odd reflection at the Dirichlet boundary (reading A4)."""
+    e = np.ascontiguousarray(e, dtype=np.float64).reshape(-1)
+    out = np.zeros(4 * nc * nc)
+    lib().or_prolong_add(int(nc), _dp(e), _dp(out))
     return out
 
 

@@ -501,6 +501,12 @@ static void prolong_add(int nc, const double* e, double* fine)
         }
 }
 
+/* The prolongation above on its own (tests): fine (2nc x 2nc) += P e. */
+void or_prolong_add(int nc, const double* e, double* fine)
+{
+    prolong_add(nc, e, fine);
+}
+
 /* Dense Cholesky of the level-0 matrix (reading A5: exact coarsest solve). */
 static int chol_factor(int n, const double* k, double* Lm)
 {

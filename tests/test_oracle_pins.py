@@ -6,6 +6,7 @@ dual-lattice sums, brute force) so that a dropped term, a wrong sign or index,
 or a transposed operand in the oracle fails at least one of them.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -44,6 +45,17 @@ def test_philox_uniform_and_avalanche():
     # distinct counters give distinct blocks (a permutation for a fixed key)
     seen = {tuple(O.philox4x32_10([i, 3, 0, 0], [9, 9])) for i in range(2000)}
     assert len(seen) == 2000
+
+
+def test_philox_known_answer_vectors():
+    # the generator's published known-answer vectors (tests/golden, cited there):
+    # a wrong multiplier, a swapped word or a missed key bump changes every block
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for row in rows:
+        w = [int(x, 16) for x in row]
+        assert list(O.philox4x32_10(w[0:4], w[4:6])) == w[6:10]
 
 
 def test_unit_map_open_interval():
@@ -326,6 +338,62 @@ def test_fmg_qoi_converges_to_poisson_series():
     for e in (errs_m, errs_c):
         r1, r2 = e[0] / e[1], e[1] / e[2]
         assert 3.5 < r1 < 4.5 and 3.5 < r2 < 4.5, e
+
+
+def _cell_grid(f, n):
+    c = (np.arange(n) + 0.5) / n
+    X1, X2 = np.meshgrid(c, c, indexing="xy")  # row = x2 (i2), column = x1 (i1)
+    return f(X1, X2)
+
+
+def test_prolongation_reproduces_bilinear_functions():
+    # reading A4: P is bilinear interpolation between coarse cell centres, with an
+    # odd reflection across the Dirichlet boundary for the missing neighbour
+    nc = 8
+    nf = 2 * nc
+
+    def prol(f):
+        return O.prolong(nc, _cell_grid(f, nc)).reshape(nf, nf)
+
+    # interior fine cells (their four coarse neighbours exist): exact for any bilinear function
+    g = lambda x1, x2: 0.3 - 1.7 * x1 + 2.9 * x2 + 4.1 * x1 * x2  # noqa: E731
+    assert np.max(np.abs(prol(g) - _cell_grid(g, nf))[1:-1, 1:-1]) < 1e-14
+    # boundary cells: the odd ghost equals the value of a function that is odd
+    # about that boundary, so such bilinear functions are reproduced there too
+    for f, sl in [(lambda x1, x2: x1 * x2, np.s_[:-1, :-1]),
+                  (lambda x1, x2: (1 - x1) * (1 - x2), np.s_[1:, 1:]),
+                  (lambda x1, x2: x1 * (1 - x2), np.s_[1:, :-1]),
+                  (lambda x1, x2: (1 - x1) * x2, np.s_[:-1, 1:])]:
+        assert np.max(np.abs(prol(f) - _cell_grid(f, nf))[sl]) < 1e-14
+    # one interior coarse cell (I2, I1) = (3, 4) with value 16: its four children
+    # take 9, the eight fine cells beside them 3, the four diagonal ones 1
+    e = np.zeros(nc * nc)
+    e[3 * nc + 4] = 16.0
+    v = O.prolong(nc, e).reshape(nf, nf)
+    w = np.outer([1, 3, 3, 1], [1, 3, 3, 1])
+    assert np.array_equal(v[5:9, 7:11], w) and np.sum(v) == 64.0
+
+
+@pytest.mark.parametrize("mu0,frac", [(1, 0.6), (2, 0.05)])
+def test_fixed_cycle_fmg_reaches_discretisation_accuracy(mu0, frac):
+    # FMG (Sec. 4, Fig. FMG) with a fixed number of V-cycles per level and no
+    # tolerance: on every level its F is within a fixed fraction of the
+    # discretisation error from the exact discrete solution's, so F converges to
+    # the continuous value (Poisson series, f = 1, k = 1) at O(h^2)
+    exact = {"mean": _poisson_mean(), "center": _poisson_series(0.5, 0.5)}
+    L = 5
+    ks = [np.ones((4 << t) ** 2) for t in range(L + 1)]
+    for qoi, ex in exact.items():
+        f = _oracle(n0=4, levels=L + 1, mu0=mu0, qoi=qoi).fmg_fields(L, ks)
+        d = _oracle(n0=4, levels=L + 1, mu0=mu0, qoi=qoi, rtol=1e-12, max_cycles=100).fmg_fields(L, ks)
+        assert f["status"] == O.OK and d["status"] == O.OK
+        assert list(f["cycles"][1:]) == [mu0] * L
+        F, Fh = f["F"], d["F"]
+        for t in range(1, L + 1):
+            assert abs(F[t] - Fh[t]) <= frac * abs(Fh[t] - ex), (qoi, t, F[t], Fh[t], ex)
+        err = np.abs(F - ex)
+        for t in range(2, L + 1):
+            assert 3.5 < err[t - 1] / err[t] < 4.5, (qoi, err)
 
 
 @pytest.mark.parametrize("variable_k", [False, True])
