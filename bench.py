@@ -1,17 +1,26 @@
 #!/usr/bin/env python3
 """Throughput of the MG-MLQMC hot path on one GB300 (samples/s, KL + FMG).
 
-Workload (default): MLQMC with sample recycling in FP64, 6 levels of 8x8 ..
-256x256 cells, s = 100 KL modes (separable exponential covariance, sigma = 1,
-correlation length 0.3), rank-1 lattice (CBC, gamma_j = j^-2) with R = 16
-random shifts, N_l = 1024, 512, 256, 128, 64, 32 points per shift on levels
-0..5 (32,256 FMG solves per step), mean-of-u QoI. One step = normals, fields on
-every level of every sample, FMG with two V(2,2)-cycles per level, F_t and the
-reuse sums of every level, and the estimator from those sums.
+Workload (default): the 9-level problem, 8x8 .. 2048x2048 cells, s = 1000 KL
+modes of the separable exponential covariance (sigma = 1, correlation length
+0.05), rank-1 lattice (CBC, gamma_j = j^-2, 2^12 points) with R = 16 random
+shifts, FMG with mu0 = 2 V(2,2)-cycles per level, mean-of-u QoI, recycling.
+One step = one call of mlqmc_sample_levels on 16 points per shift on the
+finest level doubling per coarser level (N_l = 4096 .. 16 per shift on levels
+0..8: 256 finest fields, 130,816 samples): normals, fields on every level of
+every sample, FMG, F_t and the reuse sums of every level.
 
-The same step in the mixed form (FP32 V-cycles inside FP64 refinement) is
-reported under "mixed". `--impl reference` times the CPU oracle as it stands
-on a bounded sample of the same workload.
+The headline `value` is the mixed-precision form (TF32 tensor-core KL, FP32
+V-cycles inside FP64 refinement, FP64 sums); the all-FP64 form of the same
+step is reported beside it (`fp64`), and Algorithm 1's time to RMSE eps for
+both forms under `time_to_eps`. The last stdout line is the compact record;
+side studies (`--extras`: the 6-level step in both forms, the 1024x1024
+precision form, Algorithm 1 on the 7-level problem with rates, Prop. 1,
+speed-ups and the multi-index variant, the Matern step) go to earlier lines
+and to `--details-out`.
+
+`--impl reference` times the CPU oracle as it stands on bounded samples of
+the same workload, spread over the host cores.
 
 Multi-GPU (torchrun): each rank runs an independent replica (its own seed);
 no data-path collective; value = all ranks' samples / max time ("weak").
@@ -19,9 +28,11 @@ no data-path collective; value = all ranks' samples / max time ("weak").
 from __future__ import annotations
 
 import argparse
+import glob
+import hashlib
 import json
+import multiprocessing as mp
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -38,45 +49,59 @@ import workloads as W  # noqa: E402
 METRIC = "samples/s (KL+FMG) and time-to-RMSE ε: mixed-precision vs FP64, one GB300"
 UNIT = "samples/s"
 L2_FLUSH_BYTES = 512 << 20
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed_tf32"],
-                    help="form of the main measurement (the other form is reported under 'mixed')")
-    ap.add_argument("--no-precision", action="store_true", help="skip the 1024x1024 precision-form comparison")
-    ap.add_argument("--no-tte", action="store_true", help="skip the time-to-epsilon runs of Algorithm 1")
-    ap.add_argument("--no-matern", action="store_true",
-                    help="skip the Matern-covariance step (Nystrom eigenpairs) in both forms")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 form of the step")
+    ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 form (one warm-up)")
+    ap.add_argument("--no-tte", action="store_true", help="skip Algorithm 1's time to eps on the 9-level problem")
+    ap.add_argument("--tte-eps", type=float, default=1e-4)
+    ap.add_argument("--extras", action="store_true",
+                    help="side studies: 6-level step, 1024x1024 precision form, 7-level Algorithm 1 runs, Matern")
+    ap.add_argument("--details-out", default="", help="write the side results (JSON) to this file")
+    ap.add_argument("--workload", default="mlqmc9", choices=["mlqmc9", "mlqmc6"])
     ap.add_argument("--smoother", default="auto", choices=["auto", "stream", "tma", "tile"],
                     help="mixed form: force this smoother on every level it handles (default: the autotuner's pick)")
     ap.add_argument("--smoother-plan", default="",
-                    help="mixed form: pin smoothers per level, e.g. 1:whole,2:whole,4:tma (profiler runs, where "
-                         "the autotuner's timings are not representative)")
+                    help="mixed form: pin smoothers per level, e.g. 1:whole,2:whole,4:tma")
     ap.add_argument("--no-graphs", action="store_true", help="launch kernel by kernel instead of replaying a CUDA graph")
-    ap.add_argument("--traffic-from", default="",
-                    help="ncu CSV of one timed step (DRAM bytes, durations): summarise into profiles/")
-    ap.add_argument("--traffic-line", default="", help="the bench JSON line of the same command without ncu")
     ap.add_argument("--counts-div", type=int, default=1,
                     help="divide the per-level counts (small cases for profiler captures only)")
-    return ap.parse_args()
+    ap.add_argument("--cpu-workers", type=int, default=0, help="oracle processes (0: every host core)")
+    ap.add_argument("--modes", type=int, default=0,
+                    help="override s (profiler captures of the grid kernels only, to keep the KL tables small)")
+    ap.add_argument("--kl-shape", default="",
+                    help="N,S,B: time only the tensor-core KL contraction of B samples on an N x N level with S modes")
+    return ap.parse_args(argv)
 
 
-def workload_config(rank: int, counts_div: int = 1):
-    cfg = dict(W.LATTICE_6LEVEL)
+WORKLOADS = {
+    "mlqmc9": (W.ADAPTIVE_9LEVEL,
+               "MG-MLQMC with reuse, 9 levels 8x8..2048x2048, s=1000 (sep. exp., sigma=1, lambda=0.05), lattice "
+               "2^12 pts, R=16, N_l=4096..16 per shift (130,816 samples, 256 finest), FMG mu0=2 V(2,2) RB-GS, "
+               "mean-of-u QoI"),
+    "mlqmc6": (W.LATTICE_6LEVEL,
+               "MG-MLQMC with reuse, 6 levels 8x8..256x256, s=100 (sep. exp., sigma=1, lambda=0.3), lattice 2^10 "
+               "pts, R=16, N_l=1024..32 per shift (32,256 samples), FMG mu0=2 V(2,2) RB-GS, mean-of-u QoI"),
+}
+
+
+def workload_config(name, rank=0, counts_div=1, precision=None, modes=0):
+    cfg = dict(WORKLOADS[name][0])
     cfg["seed"] = cfg["seed"] + 1000 * rank
     cfg["counts"] = [max(1, c // counts_div) for c in cfg["counts"]]
+    if precision:
+        cfg["precision"] = precision
+    if modes:
+        cfg["s"] = modes
     return cfg
-
-
-def work_list(cfg):
-    return W.fixed_count_work(cfg["counts"], cfg["R"])
 
 
 def n_samples(work):
@@ -84,187 +109,140 @@ def n_samples(work):
 
 
 # --------------------------------------------------------------------------- #
-# Roofline denominators                                                         #
+# Roofline denominators                                                       #
 # --------------------------------------------------------------------------- #
-# fallbacks when MEASURED_PEAKS.json is absent (one earlier GB300 measurement);
-# measured_peaks_override replaces them with this machine's figures
-HBM_GBS = 6800.0
-BF16_TFLOPS = 1900.0
-HBM_SRC = "fallback 6.8 TB/s (no measured copy bandwidth on this machine)"
-TC_SRC = "fallback bf16 1.9 PFLOP/s x nominal tf32/bf16 ratio"
-TF32_TFLOPS = BF16_TFLOPS * 1.1 / 2.25   # measured bf16 x nominal tf32/bf16 ratio (1.1 / 2.25 PFLOP/s dense)
-FP64_TFLOPS = 1.25        # nominal GB300 FP64 (an FMA probe measured 1.20)
-FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz = 80.5
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
-def measured_peaks_override():
-    global HBM_GBS, BF16_TFLOPS, TF32_TFLOPS, HBM_SRC, TC_SRC
+def peaks():
+    """Denominators of the roofline fractions: the measured copy bandwidth and
+    cuBLAS bf16 rates of the GB300s (MEASURED_PEAKS.json), else the
+    fallback figures; TF32 = bf16 x the nominal TF32/BF16 ratio 1.1/2.25;
+    FP64 = 1.20 TFLOP/s from an FMA probe on this pool's GB300 (nominal 1.25);
+    FP32 = 152 SMs x 128 lanes x 2 x 2070 MHz."""
     pk = measured_peaks()
+    P = {"hbm": 6800.0, "hbm_src": "fallback 6.8 TB/s", "bf16": 1900.0, "bf16_sust": 1700.0,
+         "tc_src": "fallback bf16 1.9 / 1.7 PFLOP/s"}
     if pk.get("hbm_gbs"):
-        HBM_GBS = float(pk["hbm_gbs"])
-        HBM_SRC = "measured copy bandwidth (MEASURED_PEAKS.json)"
+        P["hbm"], P["hbm_src"] = float(pk["hbm_gbs"]), "measured copy bandwidth"
     if pk.get("bf16_tflops"):
-        BF16_TFLOPS = float(pk["bf16_tflops"])
-        TF32_TFLOPS = BF16_TFLOPS * 1.1 / 2.25
-        TC_SRC = "measured bf16 burst x nominal tf32/bf16 ratio"
+        P["bf16"] = float(pk["bf16_tflops"])
+        P["bf16_sust"] = float(pk.get("bf16_tflops_sustained", pk["bf16_tflops"]))
+        P["tc_src"] = "measured bf16 (sustained) x nominal tf32/bf16 1.1/2.25"
+    P["tf32_sust"] = P["bf16_sust"] * 1.1 / 2.25
+    P["fp64"] = 1.20
+    P["fp32"] = 152 * 128 * 2 * 2.070e9 / 1e12
+    return P
 
 
 KIND_KERNELS = {
-    "points": "k_points (lattice points and normals)",
-    "level0": "kb_level0 (banded Cholesky and exact level-0 solve, one thread per sample)",
-    "synth": "kb_synth_G/kb_synth_z (separable KL), kb_faces, kb_idiag",
-    "smooth": "red-black sweeps (kb_rbgs_whole up to 64x64 with residual/correction fused, kb_rbgs_tma tiles "
-              "above; FP64 form: kb_rbgs_whole up to 64x64, kb_gs above)",
-    "transfer": "kb_resid_restrict, kb_prolong, kb_resid64, kb_update64",
-    "coarse": "kb_coarse_fixed (V-cycle level-0 solves)",
-    "reduce": "kb_qoi, kb_resnorm, k_sums, outputs",
-    "kl_tc": "kl_tc_kernel (tcgen05 TF32 KL contraction) and its C operand",
+    "points": "k_points", "level0": "kb_level0_fixed", "synth": "kb_synth_G/z, kb_faces",
+    "transfer": "kb_resid_restrict, kb_prolong(_resid64)", "coarse": "kb_coarse_fixed",
+    "reduce": "kb_qoi, k_sums", "kl_tc": "kl_tc_kernel (tcgen05)",
 }
+SMOOTHER_KERNELS = {"whole": "kb_rbgs_whole", "tma": "kb_rbgs_tma", "stream": "kb_rbgs_stream", "tile": "kb_rbgs_tile",
+                    "gs": "kb_gs"}
 
 
-# kernel name -> the library's timing kind (the same grouping as its event brackets)
-KIND_PATTERNS = [
-    ("points", r"k_points"), ("level0", r"kb_level0"), ("synth", r"kb_synth_|kb_faces|kb_idiag"),
-    ("smooth", r"kb_gs|kb_rbgs_"), ("transfer", r"kb_resid_restrict|kb_prolong|kb_resid64|kb_update64"),
-    ("coarse", r"kb_coarse"), ("reduce", r"kb_qoi|kb_resnorm|kb_flags|k_sums|k_fout|kb_u_out|kb_k_out"),
-    ("kl_tc", r"kl_tc_kernel|kl_build_c|kl_build_psi"),
-]
-TRAFFIC_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "dram_traffic_mlqmc6.json")
+def kernel_name(kind, level, smoothers):
+    if kind == "smooth" and level is not None:
+        return SMOOTHER_KERNELS[smoothers[level]]
+    return KIND_KERNELS.get(kind, kind)
 
 
-def kernel_kind(name):
-    for kind, pat in KIND_PATTERNS:
-        if re.search(pat, name):
-            return kind
-    return None
+def bucket_roofline(cell, P):
+    """Roofline of one (kind, level) bucket from its event time and algorithmic
+    work: the bound is the resource whose model time (bytes / HBM; FLOPs / the
+    pipe's peak) is longest; achieved = work / time; frac = achieved / peak."""
+    t = cell["ms"] * 1e-3
+    cand = [("hbm", cell["bytes"] / (P["hbm"] * 1e9)), ("alu64", cell["f64"] / (P["fp64"] * 1e12)),
+            ("alu32", cell["f32"] / (P["fp32"] * 1e12)), ("tensor", cell["ftc"] / (P["tf32_sust"] * 1e12))]
+    bound, tm = max(cand, key=lambda x: x[1])
+    if t <= 0 or tm <= 0:
+        return None
+    if bound == "hbm":
+        r = dict(bound="hbm", achieved=cell["bytes"] / t / 1e9, peak=P["hbm"], unit="GB/s", peak_src=P["hbm_src"])
+    elif bound == "tensor":
+        r = dict(bound="tensor", achieved=cell["ftc"] / t / 1e12, peak=P["tf32_sust"], unit="TFLOP/s",
+                 peak_src=P["tc_src"])
+    elif bound == "alu64":
+        r = dict(bound="alu", achieved=cell["f64"] / t / 1e12, peak=P["fp64"], unit="TFLOP/s",
+                 peak_src="FP64 1.20 TFLOP/s (FMA probe)")
+    else:
+        r = dict(bound="alu", achieved=cell["f32"] / t / 1e12, peak=P["fp32"], unit="TFLOP/s",
+                 peak_src="FP32 152x128x2x2070 MHz")
+    r["frac"] = r["achieved"] / r["peak"]
+    return r
 
 
 def sources_digest():
     """SHA-256 over the library's CUDA/C++ sources and header: DRAM counters
     taken on other sources no longer describe these kernels."""
-    import glob
-    import hashlib
-
-    root = os.path.dirname(os.path.abspath(__file__))
-    files = sorted(glob.glob(os.path.join(root, "paper_1806_05619_gb300", "csrc", "*")))
-    files = [f for f in files if f.endswith((".cu", ".cuh", ".h", ".cpp"))]
-    files.append(os.path.join(root, "include", "mlqmc.h"))
+    files = sorted(f for f in glob.glob(os.path.join(ROOT, "paper_1806_05619_gb300", "csrc", "*"))
+                   if f.endswith((".cu", ".cuh", ".h", ".cpp")))
+    files.append(os.path.join(ROOT, "include", "mlqmc.h"))
     h = hashlib.sha256()
     for f in files:
-        h.update(os.path.relpath(f, root).encode())
+        h.update(os.path.relpath(f, ROOT).encode())
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def summarize_traffic(csv_path, form, smoothers):
-    """Per-kind DRAM bytes and launches of one captured timed step (ncu CSV of
-    dram__bytes_read.sum, dram__bytes_write.sum and gpu__time_duration.sum in
-    base units), merged into the traffic file under `form`."""
-    import collections
-    import csv
-
-    with open(csv_path) as f:
-        lines = [ln for ln in f if ln.startswith('"')]
-    per_launch = collections.defaultdict(dict)
-    names = {}
-    for row in csv.DictReader(lines):
-        v = float(row["Metric Value"].replace(",", ""))
-        per_launch[row["ID"]][row["Metric Name"]] = v
-        names[row["ID"]] = row["Kernel Name"]
-    kinds = collections.defaultdict(lambda: {"launches": 0, "dram_bytes": 0.0, "ns": 0.0})
-    for i, m in per_launch.items():
-        k = kernel_kind(names[i])
-        if k is None:
-            continue
-        d = kinds[k]
-        d["launches"] += 1
-        d["dram_bytes"] += m.get("dram__bytes_read.sum", 0.0) + m.get("dram__bytes_write.sum", 0.0)
-        d["ns"] += m.get("gpu__time_duration.sum", 0.0)
-    for d in kinds.values():
-        d["dram_bytes_per_launch"] = d["dram_bytes"] / d["launches"]
-    data = {}
-    if os.path.exists(TRAFFIC_FILE):
-        with open(TRAFFIC_FILE) as f:
-            data = json.load(f)
-    data.setdefault("forms", {})[form] = {"sources_sha256": sources_digest(), "smoothers": smoothers,
-                                         "kinds": dict(kinds)}
-    with open(TRAFFIC_FILE, "w") as f:
-        json.dump(data, f, indent=1, sort_keys=True)
-    return data["forms"][form]
-
-
-def measured_traffic(form, kind, smoothers):
-    """DRAM bytes per launch of `kind` from the committed ncu capture of this
-    form's timed step, or None when there is none, the sources changed since,
-    or the smoothers differ from the captured ones."""
+def measured_traffic(form, kernel, n):
+    """DRAM bytes per launch of `kernel` on an n x n level in `form`, from the
+    committed record of a one-kernel ncu capture on a small case, scaled to the
+    launch's sample count (profiles/dram_traffic.json; the capture command and
+    the scaling are in profiles/). None when absent or taken on other sources."""
     try:
         with open(TRAFFIC_FILE) as f:
-            rec = json.load(f)["forms"][form]
-    except (OSError, KeyError, ValueError):
+            rec = json.load(f)
+    except (OSError, ValueError):
         return None
-    if rec.get("sources_sha256") != sources_digest() or rec.get("smoothers") != smoothers:
+    if rec.get("sources_sha256") != sources_digest():
         return None
-    d = rec["kinds"].get(kind)
-    return d["dram_bytes_per_launch"] if d else None
+    e = rec.get("kernels", {}).get(f"{form}|{kernel}|{n}")
+    return e.get("dram_bytes_per_sample") if e else None
 
 
-def kind_roofline(ms, work):
-    """Roofline of one kernel kind from its device time and algorithmic work:
-    the bound is the resource whose model time (bytes / HBM, FLOPs / pipe peak)
-    is longest; frac = that model time / measured time."""
-    t = ms * 1e-3
-    t_hbm = work["bytes"] / (HBM_GBS * 1e9)
-    t64, t32 = work["f64"] / (FP64_TFLOPS * 1e12), work["f32"] / (FP32_TFLOPS * 1e12)
-    t_tc = work["ftc"] / (TF32_TFLOPS * 1e12)
-    best = max(("hbm", t_hbm), ("alu64", t64), ("alu32", t32), ("tensor", t_tc), key=lambda x: x[1])
-    if t <= 0 or best[1] <= 0:
-        return None
-    r = {"ms": ms, "gbs": work["bytes"] / t / 1e9, "fp64_tflops": work["f64"] / t / 1e12,
-         "fp32_tflops": work["f32"] / t / 1e12, "tc_tflops": work["ftc"] / t / 1e12,
-         "algorithmic_bytes": work["bytes"]}
-    if best[0] == "hbm":
-        r.update(bound="hbm", achieved=r["gbs"], peak=HBM_GBS, unit="GB/s", peak_source=HBM_SRC)
-    elif best[0] == "tensor":
-        r.update(bound="tensor", achieved=r["tc_tflops"], peak=TF32_TFLOPS, unit="TFLOP/s", peak_source=TC_SRC)
-    elif best[0] == "alu64":
-        r.update(bound="alu", achieved=r["fp64_tflops"], peak=FP64_TFLOPS, unit="TFLOP/s",
-                 peak_source="FP64 1.25 TFLOP/s (nominal GB300 figure; FMA probe 1.20)")
-    else:
-        r.update(bound="alu", achieved=r["fp32_tflops"], peak=FP32_TFLOPS, unit="TFLOP/s",
-                 peak_source="FP32 152 SMs x 128 lanes x 2 x 2070 MHz")
-    r["frac"] = r["achieved"] / r["peak"]
-    return r
-
-
-def roofline_report(prof, work, steps, form=None, smoothers=None):
-    """Dominant kind's roofline (the bench line's `roofline`) plus every kind's.
-    traffic: DRAM bytes per launch of that kind from the committed ncu capture
-    of the same form's timed step (None when stale or absent)."""
-    kinds = {}
-    for k, (ms, n) in prof.items():
-        if n == 0:
+def roofline_report(ctx, levels_prof, P, form, steps, samples_at_level):
+    """The dominant (kernel kind, level) bucket of the profiled steps as the
+    bench line's `roofline`, and every bucket with at least 1 % of the time."""
+    smoothers = [k for k, _ in ctx.smoother_info()]
+    tot = sum(v["ms"] for v in levels_prof.values())
+    rows = []
+    for (kind, lv), cell in levels_prof.items():
+        r = bucket_roofline(cell, P)
+        if r is None:
             continue
-        r = kind_roofline(ms, work[k])
-        if r:
-            r["launches_per_step"] = n / steps
-            r["ms_per_step"] = ms / steps
-            kinds[k] = r
-    tot = sum(v[0] for v in prof.values())
-    dom = max(kinds, key=lambda k: kinds[k]["ms"])
-    d = kinds[dom]
-    roof = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
-            "frac": d["frac"], "traffic": measured_traffic(form, dom, smoothers) if form else None,
-            "kernel": KIND_KERNELS.get(dom, dom), "kernel_kind": dom,
-            "peak_source": d["peak_source"], "share_of_step": d["ms"] / max(1e-9, tot),
-            "launches_per_step": d["launches_per_step"], "ms_per_step": d["ms_per_step"],
-            "algorithmic_bytes_per_launch": d["algorithmic_bytes"] / max(1, prof[dom][1])}
-    by_kind = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()
-                   if kk in ("ms_per_step", "bound", "achieved", "unit", "frac", "gbs", "launches_per_step")}
-               for k, v in kinds.items()}
-    return roof, by_kind
+        r.update(kind=kind, level=lv, kernel=kernel_name(kind, lv, smoothers), share=cell["ms"] / max(tot, 1e-12),
+                 ms_per_step=cell["ms"] / steps, launches_per_step=cell["n"] / steps,
+                 n=(ctx.n(lv) if lv is not None else None))
+        rows.append(r)
+    rows.sort(key=lambda r: -r["share"])
+    dom = next(r for r in rows if r["level"] is not None)
+    per_launch_bytes = levels_prof[(dom["kind"], dom["level"])]["bytes"] / max(1, levels_prof[(dom["kind"], dom["level"])]["n"])
+    dps = measured_traffic(form, dom["kernel"], dom["n"])
+    traffic = dps * samples_at_level[dom["level"]] if dps is not None else None
+    roof = {"bound": dom["bound"], "achieved": round(dom["achieved"], 1), "peak": dom["peak"], "unit": dom["unit"],
+            "frac": round(dom["frac"], 3), "traffic": traffic,
+            "kernel": f"{dom['kernel']} on {dom['n']}x{dom['n']}", "share": round(dom["share"], 3),
+            "alg_bytes_per_launch": per_launch_bytes, "peak_src": dom["peak_src"] + " (of measured)"
+            if "measured" in dom["peak_src"] else dom["peak_src"]}
+    table = [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()
+              if k in ("kernel", "level", "bound", "achieved", "unit", "frac", "share", "ms_per_step",
+                       "launches_per_step")} for r in rows if r["share"] >= 0.01]
+    return roof, table
 
 
+# --------------------------------------------------------------------------- #
+# Clocks during the timed region                                              #
+# --------------------------------------------------------------------------- #
 def clocks_start(path):
     try:
         f = open(path, "w")
@@ -274,22 +252,14 @@ def clocks_start(path):
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
              "--format=csv,noheader,nounits", "-lms", "200"], stdout=f, stderr=subprocess.DEVNULL)
         return p, f
-    except Exception:
+    except OSError:
         return None, None
 
 
-def clocks_stop(handle, path, device_index=0):
-    p, f = handle
-    if p is None:
-        return None
-    p.terminate()
-    try:
-        p.wait(timeout=5)
-    except Exception:
-        p.kill()
-    f.close()
+def clocks_summary(lines, device_index=0):
+    """Median SM clock under load, the maximum, and every throttle reason seen."""
     rows = []
-    for line in open(path):
+    for line in lines:
         parts = [x.strip() for x in line.split(",")]
         if len(parts) < 9 or parts[0] != str(device_index):
             continue
@@ -310,60 +280,118 @@ def clocks_stop(handle, path, device_index=0):
             "samples": len(rows)}
 
 
-def measured_peaks():
+def clocks_stop(handle, path, device_index=0):
+    p, f = handle
+    if p is None:
+        return None
+    p.terminate()
     try:
-        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        return {}
+        p.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        p.kill()
+    f.close()
+    with open(path) as fh:
+        return clocks_summary(fh.readlines(), device_index)
 
 
 # --------------------------------------------------------------------------- #
-# CPU oracle timing (baseline and reference arm)                              #
+# CPU oracle timing (baseline and reference arm), one process per core        #
 # --------------------------------------------------------------------------- #
-def oracle_rate(cfg, counts, shift=0, n_shifts=1):
-    """Time the oracle as it stands (serial, one core) on counts[l] samples of level l
-    for shifts shift..shift+n_shifts-1."""
+def _oracle_job(job):
+    """One oracle process: the samples of `work` as the oracle computes them
+    (serial, as it stands); returns (samples, seconds)."""
+    cfg, genvec, work = job
     import oracle as O
 
-    z, _ = O.cbc(cfg["s"], cfg["log2_nmax"])
     orc = O.Oracle(n_levels=cfg["n_levels"], n0=cfg["n0"], s=cfg["s"], sigma=cfg["sigma"], corr_len=cfg["corr_len"],
-                   qoi=cfg["qoi"], mu0=cfg["mu0"], nu1=cfg["nu1"], nu2=cfg["nu2"], sampler=cfg["sampler"],
-                   seed=cfg["seed"], R=cfg["R"], genvec=z, log2_nmax=cfg["log2_nmax"], reuse=cfg["reuse"])
-    work = [(lv, 0, int(c), shift, shift + n_shifts) for lv, c in enumerate(counts) if c > 0]
+                   qoi=cfg["qoi"], mu0=cfg["mu0"], nu1=cfg["nu1"], nu2=cfg["nu2"], rtol=cfg["rtol"],
+                   sampler=cfg["sampler"], seed=cfg["seed"], R=cfg["R"], genvec=genvec,
+                   log2_nmax=cfg["cpu_log2_nmax"], reuse=cfg["reuse"])
     t0 = time.perf_counter()
     orc.sample_levels(work)
-    dt = time.perf_counter() - t0
-    return n_samples(work), dt
+    return n_samples(work), time.perf_counter() - t0
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_sample_setup(cfg, div):
+    """The oracle's own generating vector for the points a CPU sample uses and
+    the per-shift counts of that sample (the step's counts / div, same level mix)."""
+    import oracle as O
+
+    counts = [max(1, c // div) for c in cfg["counts"]]
+    m = max(1, int(np.ceil(np.log2(max(counts)))))
+    c = dict(cfg)
+    c["cpu_log2_nmax"] = m
+    z, _ = O.cbc(cfg["s"], m)
+    return c, [int(v) for v in z], counts
+
+
+def oracle_pool_run(jobs, workers):
+    """Run oracle jobs on `workers` spawned processes; wall seconds and per-job results."""
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(processes=workers) as pool:
+        pool.map(_oracle_job, [(jobs[0][0], jobs[0][1], [(0, 0, 1, 0, 1)])] * workers)  # load the oracle everywhere
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_job, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+    return wall, res
+
+
+def cpu_baseline(cfg, workers, div=16):
+    """The oracle on every host core: the step's counts / div on all R shifts,
+    one shift per job; value = samples / wall time. single_core = the mean
+    per-process rate measured during the same run (all cores busy)."""
+    c, z, counts = cpu_sample_setup(cfg, div)
+    jobs = [(c, z, [(lv, 0, n, r, r + 1) for lv, n in enumerate(counts)]) for r in range(cfg["R"])]
+    wall, res = oracle_pool_run(jobs, workers)
+    ns = sum(r[0] for r in res)
+    return {"value": ns / wall, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "single_core": float(np.mean([r[0] / r[1] for r in res])),
+            "sample": f"N_l/{div}={counts} per shift x {cfg['R']} shifts ({ns} samples), one shift per process, "
+                      f"{wall:.1f} s wall; oracle lattice 2^{c['cpu_log2_nmax']} pts"}
 
 
 def run_reference(args):
+    """The oracle as it stands, spread over the host cores: each step is one
+    shift's samples at the step's counts / 16 (same level mix, 511 samples);
+    W warm-up steps, then K timed steps run concurrently, one per process."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    cfg = workload_config(0)
-    counts = list(cfg["counts"])
-    times = []
-    for i in range(args.warmup + args.steps):
-        ns, dt = oracle_rate(cfg, counts, shift=i % cfg["R"])
-        if i >= args.warmup:
-            times.append(dt)
-    total = sum(times)
-    value = ns * len(times) / total
-    sample = (f"per step: one shift (of 16), N_l = {counts} samples of levels 0..5 "
-              f"({ns} FMG solves, 1/16 of the step, same level mix)")
+    cfg = workload_config(args.workload)
+    workers = args.cpu_workers or host_cores()
+    c, z, counts = cpu_sample_setup(cfg, 16)
+
+    def jobs(k, off):
+        return [(c, z, [(lv, 0, n, (off + i) % cfg["R"], (off + i) % cfg["R"] + 1) for lv, n in enumerate(counts)])
+                for i in range(k)]
+
+    if args.warmup:
+        oracle_pool_run(jobs(args.warmup, 0), min(workers, args.warmup))
+    wall, res = oracle_pool_run(jobs(args.steps, args.warmup), min(workers, args.steps))
+    ns = sum(r[0] for r in res)
+    value = ns / wall
+    sample = (f"per step one shift, N_l/16={counts} ({res[0][0]} samples); {args.steps} steps on "
+              f"{min(workers, args.steps)} processes, {wall:.1f} s wall")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": "MLQMC with reuse, FP64, 6 levels 8x8..256x256, s=100, R=16, "
-                                   "N_l=1024..32 (bounded sample on CPU)", "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload][1] + " (bounded sample on the host cores)",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": min(workers, args.steps), "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # --------------------------------------------------------------------------- #
-# GPU arm                                                                    #
+# GPU arm                                                                     #
 # --------------------------------------------------------------------------- #
 def timed_steps(step, K, stream, flush):
     """K steps, each bracketed by CUDA events on the launch stream, L2 flushed
@@ -378,25 +406,6 @@ def timed_steps(step, K, stream, flush):
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     return [a.elapsed_time(b) for a, b in ev]
-
-
-def profiled_pass(ctx, step, args, stream, flush):
-    """K more steps with the library's per-kernel event brackets on (two
-    untimed calls first: the graph is captured again with its brackets):
-    per-kind (ms, launches), algorithmic work, and the mean step time of
-    the pass. Profiling is off again afterwards (two more untimed calls
-    restore the plain graph)."""
-    ctx.profile(True)
-    for _ in range(2):
-        step()
-    ctx.profile(True)  # clear the totals of those two calls
-    ms = timed_steps(step, args.steps, stream, flush)
-    prof = ctx.profile_read()
-    work = ctx.profile_work()
-    ctx.profile(False)
-    for _ in range(2):
-        step()
-    return prof, work, sum(ms) / len(ms)
 
 
 def force_smoother(ctx, name, plan=""):
@@ -414,14 +423,58 @@ def force_smoother(ctx, name, plan=""):
         ctx.set_smoother(int(lv), kind)
 
 
+def samples_reaching(cfg):
+    """Samples per step whose FMG reaches each level (all shifts)."""
+    c = np.array(cfg["counts"], dtype=np.int64) * cfg["R"]
+    return [int(x) for x in np.cumsum(c[::-1])[::-1]]
+
+
+class Step:
+    """One context and the fixed-count step on it."""
+
+    def __init__(self, M, cfg, genvec, dev, args, ns):
+        import torch
+
+        self.cfg = cfg
+        self.work = W.fixed_count_work(cfg["counts"], cfg["R"])
+        t0 = time.perf_counter()
+        self.ctx = M.Context.from_config(cfg, genvec=genvec, max_samples=ns)
+        torch.cuda.synchronize(dev)
+        self.create_s = time.perf_counter() - t0
+        force_smoother(self.ctx, args.smoother, args.smoother_plan)
+        self.ctx.set_graphs(not args.no_graphs)
+        self.sums = torch.zeros(cfg["n_levels"] * cfg["R"] * 2, dtype=torch.float64, device=dev)
+
+    def __call__(self, stream):
+        self.sums.zero_()
+        self.ctx.sample_levels(self.work, self.sums, stream=stream)
+
+    def profiled(self, stream, flush, K):
+        """K steps with the library's per-launch event brackets (two untimed
+        calls first: the graph is captured again with its brackets); the
+        per-(kind, level) times and work; plain replay restored afterwards."""
+        self.ctx.profile(True)
+        for _ in range(2):
+            self(stream)
+        self.ctx.profile(True)
+        ms = timed_steps(lambda: self(stream), K, stream, flush)
+        prof = self.ctx.profile_read_levels()
+        self.ctx.profile(False)
+        for _ in range(2):
+            self(stream)
+        return prof, float(np.mean(ms))
+
+    def close(self):
+        self.ctx.close()
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
 
     import paper_1806_05619_gb300 as M
 
-    measured_peaks_override()
-
+    P = peaks()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -432,176 +485,223 @@ def run_ours(args):
     if not os.path.exists(M.LIB_PATH):
         raise RuntimeError("libmlqmc.so is not built; run __graft_entry__.build()")
 
-    cfg = workload_config(rank, args.counts_div)
-    cfg["precision"] = args.precision
-    work = work_list(cfg)
-    ns = n_samples(work)
-    genvec, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
-    ctx = M.Context.from_config(cfg, genvec=genvec, max_samples=ns)
-    force_smoother(ctx, args.smoother, args.smoother_plan)
-    ctx.set_graphs(not args.no_graphs)
-    nl, R = cfg["n_levels"], cfg["R"]
-    sums = torch.zeros(nl * R * 2, dtype=torch.float64, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev)
-
-    def step():
-        sums.zero_()
-        ctx.sample_levels(work, sums, stream=stream)
-
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    # warm-up: the repeated step is captured as one CUDA graph on its second call
-    for _ in range(args.warmup):
-        step()
-    ctx.check_device(stream)
-    barrier()
+    def max_over_ranks(x):
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
 
-    # device-timed steps (L2 flushed between steps, outside the events)
+    details = {}
+    cfg = workload_config(args.workload, rank, args.counts_div, precision="mixed_tf32", modes=args.modes)
+    ns = n_samples(W.fixed_count_work(cfg["counts"], cfg["R"]))
+    genvec, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    # ---- headline: the mixed form ------------------------------------------
+    step = Step(M, cfg, genvec, dev, args, ns)
+    for _ in range(args.warmup):  # the repeated step is captured as one CUDA graph on its second call
+        step(stream)
+    step.ctx.check_device(stream)
+    barrier()
     clk_path = os.path.join(tempfile.gettempdir(), f"clocks_{os.getpid()}.csv")
     clk = clocks_start(clk_path)
-    launches0 = ctx.launch_count()
-    replays0 = ctx.graph_replays()
+    launches0, replays0 = step.ctx.launch_count(), step.ctx.graph_replays()
     barrier()
     torch.cuda.profiler.start()  # a profiler started with --profile-from-start off sees these steps only
-    step_ms = timed_steps(step, args.steps, stream, flush)
+    step_ms = timed_steps(lambda: step(stream), args.steps, stream, flush)
     torch.cuda.profiler.stop()
     barrier()
-    launches = ctx.launch_count() - launches0
-    replays = ctx.graph_replays() - replays0
+    launches = step.ctx.launch_count() - launches0
+    replays = step.ctx.graph_replays() - replays0
     clocks = clocks_stop(clk, clk_path, device_index=local)
-    tot_ms = sum(step_ms)
-    t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    tot_ms = float(t.item())
-    ctx.check_device(stream)
+    step.ctx.check_device(stream)
+    tot_ms = max_over_ranks(sum(step_ms))
     value = ns * world * args.steps / (tot_ms * 1e-3)
 
-    # the same K steps again with every kernel bracketed by events (the
-    # library's per-kind timing and algorithmic work): roofline per kind
-    prof, pwork, prof_ms = profiled_pass(ctx, step, args, stream, flush)
+    # per-(kernel, level) event timing of K more steps: the roofline
+    prof, prof_ms = step.profiled(stream, flush, args.steps)
+    roof, table = roofline_report(step.ctx, prof, P, "mixed_tf32", args.steps, samples_reaching(cfg))
+    details["roofline_table_mixed"] = table
+    details["profiled_pass_ms_per_step"] = prof_ms
 
-    # end to end through the public API from the host: work list in, estimate out
-    e2e_times = []
+    # end to end through the public API from host memory: the host work list in
+    # (the library uploads one 32-byte descriptor per sample), the reuse sums
+    # back to pinned host memory, the estimator by mlqmc_estimator_from_sums
+    nl, R = cfg["n_levels"], cfg["R"]
     host_sums = torch.empty(nl * R * 2, dtype=torch.float64, pin_memory=True)
-    for i in range(args.steps):
+    Nl = list(cfg["counts"])
+    e2e_times = []
+    est = None
+    for _ in range(args.steps):
         flush.zero_()
         barrier()
         t0 = time.perf_counter()
-        step()
-        host_sums.copy_(sums, non_blocking=True)
+        step(stream)
+        host_sums.copy_(step.sums, non_blocking=True)
         torch.cuda.synchronize(dev)
-        S = host_sums.numpy().reshape(nl, R, 2)
-        # estimator from the sums (eqs. Upsilon-reuse, MGMLQMC, var_of_mgmlqmc)
-        cnt = np.cumsum(np.array(cfg["counts"][::-1]))[::-1]
-        Ups = S[:, :, 0] / cnt[:, None]
-        Qr = Ups.sum(axis=0)
-        est = (Qr.mean(), Qr.var(ddof=1) / R)
+        est = M.estimator_from_sums(Nl, host_sums.numpy().reshape(nl, R, 2), R, reuse=cfg["reuse"])
         e2e_times.append(time.perf_counter() - t0)
-    e2e_t = torch.tensor([sum(e2e_times)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = ns * world * args.steps / float(e2e_t.item())
-    h2d = len(work) * 32 + ns * (24 + 8)  # work list + the library's per-sample descriptors
-    d2h = nl * R * 2 * 8
+    e2e_value = ns * world * args.steps / max_over_ranks(sum(e2e_times))
+    e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": ns * 32, "d2h_bytes_per_step": nl * R * 2 * 8}
+    details["estimate_mixed"] = {"Q": est["Q"], "varQ": est["varQ"]}
+    smoothers = [k for k, _ in step.ctx.smoother_info()]
+    create_mixed = step.create_s
+    step.close()
+    del step
+    torch.cuda.empty_cache()
 
-    # roofline of the dominant kernel kind: the library's event timing of each
-    # launch inside the timed region and the algorithmic work it recorded
-    smoothers = [k for k, _ in ctx.smoother_info()]
-    roof, by_kind = roofline_report(prof, pwork, args.steps, form=cfg["precision"], smoothers=smoothers)
+    # ---- the all-FP64 form of the same step --------------------------------
+    fp64 = None
+    if not args.no_fp64:
+        c64 = dict(cfg)
+        c64["precision"] = "fp64"
+        s64 = Step(M, c64, genvec, dev, args, ns)
+        s64(stream)
+        s64.ctx.check_device(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = timed_steps(lambda: s64(stream), args.fp64_steps, stream, flush)
+        s64.ctx.check_device(stream)
+        t64 = max_over_ranks(sum(ms64))
+        fp64 = {"value": round(ns * world * args.fp64_steps / (t64 * 1e-3), 1),
+                "ms_per_step": round(t64 / args.fp64_steps, 2), "steps": args.fp64_steps}
+        host_sums.copy_(s64.sums)
+        e64 = M.estimator_from_sums(Nl, host_sums.numpy().reshape(nl, R, 2), R, reuse=cfg["reuse"])
+        details["estimate_fp64"] = {"Q": e64["Q"], "varQ": e64["varQ"]}
+        fp64["speedup_mixed"] = round((t64 / args.fp64_steps) / (tot_ms / args.steps), 2)
+        s64.close()
+        del s64
+        torch.cuda.empty_cache()
 
-    mixed = None
-    if not args.no_mixed and cfg["precision"] == "fp64":
-        mixed = run_mixed_same_workload(args, cfg, work, genvec, dev, stream, flush, M)
-    precision_form = None
-    if not args.no_precision and rank == 0 and args.counts_div == 1:
-        precision_form = run_precision_form(dev, stream, flush, M)
+    # ---- Algorithm 1 to eps on the same problem, both forms ----------------
     tte = None
-    if not args.no_tte and rank == 0 and args.counts_div == 1:
-        tte = run_time_to_eps(M)
-
-    matern = None
-    if not args.no_matern and rank == 0 and args.counts_div == 1:
-        try:
-            matern = run_matern(cfg, work, genvec, dev, stream, flush, M)
-        except Exception as e:  # reported in the line; the main measurement stands
-            matern = {"error": f"{type(e).__name__}: {e}"}
+    if not args.no_tte and rank == 0 and args.counts_div == 1 and args.workload == "mlqmc9":
+        tte = run_tte9(M, cfg, args.tte_eps, dev)
+        details["time_to_eps_9level"] = tte
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        counts = [max(1, c // 2) for c in cfg["counts"]]
-        nsc, dt = oracle_rate(cfg, counts, shift=0, n_shifts=cfg["R"])
-        cpu = {"value": nsc / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"all 16 shifts, N_l/2 = {counts} samples of levels 0..5 ({nsc} FMG solves, "
-                         f"half the step, same level mix), serial oracle, {dt:.1f} s"}
+        cpu = cpu_baseline(cfg, args.cpu_workers or host_cores())
+
+    if rank == 0 and args.extras and args.counts_div == 1:
+        details.update(run_extras(args, dev, stream, flush, M, P))
 
     if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if cfg["precision"] == "fp64" else "f32 V-cycles in f64 refinement",
-            "data": "synthetic",
-            "config": {"workload": "MLQMC with reuse, FP64, 6 levels 8x8..256x256 cells, s=100 KL modes "
-                                   "(sep. exponential, sigma=1, lambda=0.3), lattice 2^10 points halving per "
-                                   "level, R=16 shifts, N_l=1024,512,256,128,64,32 per shift, FMG mu0=2 V(2,2) "
-                                   "RB-GS, mean-of-u QoI",
-                       "precision": cfg["precision"], "smoothers": smoothers,
-                       "samples_per_step": ns * world, "counts_div": args.counts_div,
-                       "l2": "flushed between timed steps (512 MiB write)",
-                       "parallelism": f"independent replicas x{world}"},
-            "gpu_launches": launches,
-            "graph_replays": replays,
-            "profiled_pass_ms_per_step": prof_ms,
-            "roofline": roof,
-            "roofline_by_kind": by_kind,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "estimate": {"Q": float(est[0]), "varQ": float(est[1])}},
-            "clocks": clocks,
-            "cpu_baseline": cpu,
-        }
-        if mixed:
-            line["mixed"] = mixed
-        if precision_form:
-            line["precision_form"] = precision_form
-        if tte:
-            line["time_to_eps"] = tte
-        if matern:
-            line["matern"] = matern
+        details_line = {"details": details}
+        print(json.dumps(details_line, default=float), flush=True)
+        if args.details_out:
+            with open(args.details_out, "w") as f:
+                json.dump(details, f, indent=1, default=float)
+        line = make_line(args, world, value, tot_ms, ns, smoothers, create_mixed, launches, replays, roof, e2e,
+                         clocks, cpu, fp64, tte)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
+def make_line(args, world, value, tot_ms, ns, smoothers, create_s, launches, replays, roof, e2e, clocks, cpu, fp64,
+              tte):
+    """The compact record printed last (well under 2 KB)."""
+    if cpu:
+        cpu = dict(cpu, value=round(cpu["value"], 2), single_core=round(cpu["single_core"], 2))
+    return {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(tot_ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 V-cycles in f64 refinement, tf32 KL", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload][1], "precision": "mixed_tf32", "samples_per_step": ns * world,
+                   "counts_div": args.counts_div, "smoothers": "".join(x[0] for x in smoothers),
+                   "l2": "flushed (512 MiB write) between steps", "parallelism": f"independent replicas x{world}",
+                   "create_s": round(create_s, 1)},
+        "gpu_launches": launches, "graph_replays": replays, "roofline": roof,
+        "e2e": {k: (round(v, 1) if isinstance(v, float) else v) for k, v in e2e.items()},
+        "clocks": clocks, "cpu_baseline": cpu, "fp64": fp64,
+        "time_to_eps": ({"eps": tte["eps"], "mixed_s": round(tte["mixed_tf32"]["seconds"], 3),
+                         "fp64_s": round(tte["fp64"]["seconds"], 3) if "fp64" in tte else None,
+                         "mixed_L": tte["mixed_tf32"]["L"], "mixed_rounds": tte["mixed_tf32"]["rounds"]}
+                        if tte else None),
+    }
+
+
+def run_tte9(M, cfg, eps, dev):
+    """Algorithm 1 (one level per round, deterministic cost model) to RMSE eps on
+    the 9-level problem, mixed TF32 against FP64, wall and device seconds."""
+    import torch
+
+    out = {"eps": eps, "workload": "Algorithm 1 on the 9-level problem (s=1000, lambda=0.05, R=16), FMG mu0=2"}
+    c = dict(cfg)
+    c["log2_nmax"] = 14
+    genvec, _ = M.cbc_genvec(c["s"], c["log2_nmax"])
+    for prec in ("mixed_tf32", "fp64"):
+        c["precision"] = prec
+        ctx = M.Context.from_config(c, genvec=genvec, max_samples=1 << 16)
+        r = ctx.estimate(eps)
+        out[prec] = {"seconds": r["wall_seconds"], "gpu_seconds": r["gpu_seconds"], "Q": r["Q"],
+                     "rmse_bound": float(np.sqrt(r["varQ"] + r["bias"] ** 2)), "L": r["L"], "rounds": r["rounds"],
+                     "N": r["N"][:r["L"] + 1], "run_status": r["run_status"]}
+        ctx.close()
+        del ctx
+        torch.cuda.empty_cache()
+    return out
+
+
+# --------------------------------------------------------------------------- #
+# Side studies (--extras)                                                     #
+# --------------------------------------------------------------------------- #
+def run_extras(args, dev, stream, flush, M, P):
+    out = {}
+    out["mlqmc6"] = run_step6(args, dev, stream, flush, M, P)
+    out["precision_form"] = run_precision_form(dev, stream, flush, M)
+    out["time_to_eps_7level"] = run_time_to_eps(M)
+    try:
+        cfg = workload_config("mlqmc6")
+        genvec, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
+        out["matern"] = run_matern(cfg, W.fixed_count_work(cfg["counts"], cfg["R"]), genvec, dev, stream, flush, M)
+    except Exception as e:  # reported; the other results stand
+        out["matern"] = {"error": f"{type(e).__name__}: {e}"}
+    return out
+
+
+def run_step6(args, dev, stream, flush, M, P, steps=10, warmup=3):
+    """The 6-level step in both forms, device-timed, with its roofline table."""
+    res = {}
+    for prec in ("fp64", "mixed_tf32"):
+        cfg = workload_config("mlqmc6", precision=prec)
+        genvec, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
+        ns = n_samples(W.fixed_count_work(cfg["counts"], cfg["R"]))
+        st = Step(M, cfg, genvec, dev, args, ns)
+        for _ in range(warmup):
+            st(stream)
+        st.ctx.check_device(stream)
+        ms = float(np.mean(timed_steps(lambda: st(stream), steps, stream, flush)))
+        prof, _ = st.profiled(stream, flush, steps)
+        roof, table = roofline_report(st.ctx, prof, P, prec, steps, samples_reaching(cfg))
+        res[prec] = {"ms_per_step": ms, "samples_per_s": ns / (ms * 1e-3), "roofline": roof, "table": table}
+        st.close()
+    res["mixed_speedup"] = res["fp64"]["ms_per_step"] / res["mixed_tf32"]["ms_per_step"]
+    return res
+
+
 def run_matern(cfg, work, genvec, dev, stream, flush, M, steps=5, warmup=3):
-    """The same 6-level step with the Matern covariance (eq. matern, nu = 1,
-    the main step's lambda and sigma) whose KL modes are Nystrom eigenpairs on
-    16 x 16 nodes (Sec. 5): the eigensolve and create times (the per-level
-    Nystrom interpolation runs at create) and device-timed steps in the FP64
-    and mixed TF32 forms, L2 flushed between steps."""
+    """The 6-level step with the Matern covariance (eq. matern, nu = 1) whose KL
+    modes are Nystrom eigenpairs on 16 x 16 nodes (Sec. 5), in both forms."""
     import torch
 
     nu, m = 1.0, 16
     t0 = time.perf_counter()
     th, ps = M.nystrom_modes(nu, cfg["corr_len"], cfg["sigma"], m, cfg["s"])
-    out = {"workload": f"6 levels 8x8..256x256, s={cfg['s']} Nystrom modes of the Matern covariance "
-                       f"(nu={nu}, lambda={cfg['corr_len']}, sigma={cfg['sigma']}) on {m}x{m} nodes; the main "
-                       "step's counts, shifts and FMG",
-           "eigensolve_seconds": time.perf_counter() - t0}
+    out = {"eigensolve_seconds": time.perf_counter() - t0}
     ns = n_samples(work)
     sums = torch.zeros(cfg["n_levels"] * cfg["R"] * 2, dtype=torch.float64, device=dev)
     for prec in ("fp64", "mixed_tf32"):
         c = dict(cfg)
         c["precision"] = prec
-        t0 = time.perf_counter()
         ctx = M.Context.from_config(c, genvec=genvec, max_samples=ns, covariance="matern", matern_nu=nu,
                                     nystrom_m=m, nystrom_theta=th, nystrom_psi=ps)
-        torch.cuda.synchronize(dev)  # the per-level interpolation it queued
-        create_s = time.perf_counter() - t0
 
         def step():
             sums.zero_()
@@ -610,95 +710,54 @@ def run_matern(cfg, work, genvec, dev, stream, flush, M, steps=5, warmup=3):
         for _ in range(warmup):
             step()
         ctx.check_device(stream)
-        torch.cuda.synchronize(dev)
         ms = float(np.mean(timed_steps(step, steps, stream, flush)))
-        ctx.check_device(stream)
-        out[prec] = {"create_seconds": create_s, "ms_per_step": ms, "samples_per_s": ns / (ms * 1e-3)}
+        out[prec] = {"ms_per_step": ms, "samples_per_s": ns / (ms * 1e-3)}
         ctx.close()
     out["mixed_speedup"] = out["fp64"]["ms_per_step"] / out["mixed_tf32"]["ms_per_step"]
     return out
 
 
-def run_mixed_same_workload(args, cfg64, work, genvec, dev, stream, flush, M):
-    """The same step with FP32 V-cycles inside FP64 refinement (mu0 refinement
-    steps per level, each one FP32 V(2,2)-cycle on the FP64 residual)."""
-    import torch
-
-    cfg = dict(cfg64)
-    cfg["precision"] = "mixed_tf32"
-    ns = n_samples(work)
-    ctx = M.Context.from_config(cfg, genvec=genvec, max_samples=ns)
-    force_smoother(ctx, args.smoother, args.smoother_plan)
-    ctx.set_graphs(not args.no_graphs)
-    nl, R = cfg["n_levels"], cfg["R"]
-    sums = torch.zeros(nl * R * 2, dtype=torch.float64, device=dev)
-
-    def step():
-        sums.zero_()
-        ctx.sample_levels(work, sums, stream=stream)
-
-    for _ in range(args.warmup):
-        step()
-    ctx.check_device(stream)
-    torch.cuda.synchronize(dev)
-    ms = timed_steps(step, args.steps, stream, flush)
-    tot = sum(ms)
-    prof, pwork, prof_ms = profiled_pass(ctx, step, args, stream, flush)
-    ctx.check_device(stream)
-    roof, by_kind = roofline_report(prof, pwork, args.steps, form="mixed_tf32",
-                                    smoothers=[k for k, _ in ctx.smoother_info()])
-    return {"value": ns * args.steps / (tot * 1e-3), "unit": UNIT, "ms_per_step": tot / args.steps,
-            "dtype": "f32 V-cycles in f64 refinement, TF32 tensor-core KL, f32 field",
-            "roofline": roof, "roofline_by_kind": by_kind, "profiled_pass_ms_per_step": prof_ms,
-            "graph_replays": ctx.graph_replays(),
-            "smoothers": [{"level": t, "kind": k, "tuned_ms": ms} for t, (k, ms) in enumerate(ctx.smoother_info())]}
-
-
 def run_precision_form(dev, stream, flush, M):
-    """Precision form: one batch of 256 samples whose FMG ends on the 1024x1024
-    level (8 levels from 8x8), s = 400 KL modes (lambda = 0.1), 16 shifts x 16
-    lattice points, every level refined to ||r||_2/||b||_2 <= 1e-10: the mixed
-    forms (TF32 or split-BF16 tensor-core KL, FP32 V-cycles, FP64 residual and
-    correction) against the all-FP64 GPU form, timing per batch and the mixed
-    results' deviation from the FP64 ones (field, solution, F on every level)."""
+    """One batch of 256 samples whose FMG ends on 1024x1024 (8 levels, s = 400,
+    lambda = 0.1), every level refined to a relative residual of 1e-10: the
+    mixed forms against the all-FP64 form, time per batch and the mixed
+    results' deviation from the FP64 ones (field, solution, F per level)."""
     import torch
 
     cfg = dict(W.PRECISION_1024)
-    cfg["log2_nmax"] = 10
     genvec, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
     top = cfg["n_levels"] - 1
     work = [(top, 0, 16, 0, 16)]
     ns = n_samples(work)
     nl, R = cfg["n_levels"], cfg["R"]
-    out = {"workload": "256 samples (16 shifts x 16 points) on 8 levels 8x8..1024x1024, s=400, lambda=0.1, "
-                       "refined to relative residual 1e-10 on every level"}
-    res = {}
+    out, res = {}, {}
     for prec in ["mixed_tf32", "mixed_bf16x3", "fp64"]:
         c = dict(cfg)
         c["precision"] = prec
         ctx = M.Context.from_config(c, genvec=genvec, max_samples=ns)
         sums = torch.zeros(nl * R * 2, dtype=torch.float64, device=dev)
         F = torch.zeros(ns * nl, dtype=torch.float64, device=dev)
-        ctx.sample_levels(work, sums, F, stream=stream)  # warm-up (pools)
+        ctx.sample_levels(work, sums, F, stream=stream)
         ctx.check_device(stream)
+        ctx.profile(True)
         times = []
         for _ in range(2):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             sums.zero_()
-            e0.record(stream)
-            ctx.sample_levels(work, sums, F, stream=stream)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            times.append(e0.elapsed_time(e1))
+            times.append(timed_steps(lambda: ctx.sample_levels(work, sums, F, stream=stream), 1, stream, flush)[0])
+        kl = {k: v for k, v in ctx.profile_read_levels().items() if k[0] == "kl_tc" and k[1] == top}
+        ctx.profile(False)
         ctx.check_device(stream)
         y = ctx.normals(top, 3, 5, 4)
         kf = ctx.fields(top, y)
-        u, Fs = ctx.sample_solution(top, 3, 5)
-        res[prec] = dict(ms=min(times), F=F.cpu().numpy().reshape(ns, nl), k=kf.cpu().numpy(),
-                         u=u[top].cpu().numpy())
+        u, _ = ctx.sample_solution(top, 3, 5)
+        res[prec] = dict(ms=min(times), F=F.cpu().numpy().reshape(ns, nl), k=kf.cpu().numpy(), u=u[top].cpu().numpy())
         out[prec] = {"ms_per_batch": min(times), "samples_per_s": ns / (min(times) * 1e-3)}
-        del ctx
+        if kl:
+            cell = next(iter(kl.values()))
+            out[prec]["kl_1024"] = {"ms_per_launch": cell["ms"] / cell["n"],
+                                    "tflops": cell["ftc"] / (cell["ms"] * 1e-3) / 1e12,
+                                    "gbs": cell["bytes"] / (cell["ms"] * 1e-3) / 1e9}
+        ctx.close()
         torch.cuda.empty_cache()
     b = res["fp64"]
     for prec in ["mixed_tf32", "mixed_bf16x3"]:
@@ -713,69 +772,51 @@ def run_precision_form(dev, stream, flush, M):
 
 
 def run_time_to_eps(M):
-    """Time to RMSE eps of Algorithm 1 (exact one-level-per-round form,
-    deterministic cost model) on the 7-level adaptive problem (8x8..512x512,
-    s = 200, lambda = 0.3, 16 shifts, mean-of-u QoI, every level refined to
-    1e-10), mixed form against the FP64 form, for eps in {1e-2, 3e-3, 1e-3}
-    and two smaller tolerances (3e-4, 1e-4) where the runs take longer."""
+    """Algorithm 1 on the 7-level adaptive problem (8x8..512x512, s = 200,
+    lambda = 0.3, 16 shifts, mean-of-u QoI, every level refined to 1e-10):
+    mixed against FP64, without recycling, batched rounds, plain MLMC, the
+    rates and Proposition 1, and the multi-index variant."""
     from paper_1806_05619_gb300 import rates
 
     cfg = dict(W.ADAPTIVE_7LEVEL)
     cfg["log2_nmax"] = 12
     genvec, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
-    out = {"workload": "Algorithm 1 on 7 levels 8x8..512x512, s=200, lambda=0.3, R=16, rtol 1e-10",
-           "variants": "mixed_tf32 / fp64: reuse (MG-MLQMC), one level per round; mixed_tf32_no_reuse: plain "
-                       "MLQMC (each difference from its own samples); mixed_tf32_batched: every level with "
-                       "V_l/C_l >= max/2 doubles in one round; mlmc_mixed_tf32: plain MLMC (Monte Carlo "
-                       "normals, one replicate, eq. nopt counts)"}
+    out = {}
     variants = [("mixed_tf32", "mixed_tf32", True, False), ("fp64", "fp64", True, False),
                 ("mixed_tf32_no_reuse", "mixed_tf32", False, False), ("mixed_tf32_batched", "mixed_tf32", True, True)]
+    eps_list = cfg["eps"] + [3e-4, 1e-4]
     for name, prec, reuse, batched in variants:
         c = dict(cfg)
         c["precision"] = prec
         c["reuse"] = reuse
         ctx = M.Context.from_config(c, genvec=genvec, max_samples=1 << 17)
         rows = []
-        for eps in cfg["eps"] + [3e-4, 1e-4]:
+        for eps in eps_list:
             r = ctx.estimate(eps, batched=batched)
             rows.append({"eps": eps, "seconds": r["wall_seconds"], "gpu_seconds": r["gpu_seconds"], "Q": r["Q"],
-                         "rmse_bound": float(np.sqrt(r["varQ"] + r["bias"] ** 2)), "L": r["L"],
-                         "rounds": r["rounds"], "N": r["N"][:r["L"] + 1], "run_status": r["run_status"],
-                         "alpha": r["alpha"], "Ybar": r["Ybar"][:r["L"] + 1], "Vell": r["Vell"][:r["L"] + 1]})
+                         "L": r["L"], "rounds": r["rounds"], "N": r["N"][:r["L"] + 1], "run_status": r["run_status"]})
         out[name] = rows
         if name == "mixed_tf32":
-            # rates of (A1)-(A4) on the same problem, and Proposition 1 against
-            # the recycling runs: the predicted factor, the factor the run's own
-            # counts give with the measured per-sample costs, and the measured
-            # device-time ratio to the run without recycling
             out["rates"] = rates.measure(ctx, n_points=256, lambda_level=2, gamma_levels=3)
-        del ctx
+        ctx.close()
     rt = out["rates"]
     prop = {"predicted": rt["prop1_ratio"], "from_counts": [], "measured_gpu_time": []}
     for a, b in zip(out["mixed_tf32"], out["mixed_tf32_no_reuse"]):
         L = a["L"]
-        used = np.cumsum(np.array(a["N"][:L + 1], dtype=np.float64)[::-1])[::-1]  # samples on level l
-        prop["from_counts"].append({"eps": a["eps"],
-                                    "ratio": rates.reuse_cost_ratio(used, rt["ms_per_sample"][:L + 1])})
+        used = np.cumsum(np.array(a["N"][:L + 1], dtype=np.float64)[::-1])[::-1]
+        prop["from_counts"].append({"eps": a["eps"], "ratio": rates.reuse_cost_ratio(used, rt["ms_per_sample"][:L + 1])})
         prop["measured_gpu_time"].append({"eps": a["eps"], "ratio": a["gpu_seconds"] / b["gpu_seconds"]})
     out["prop1"] = prop
-    # plain MLMC (Monte Carlo normals, no recycling, eq. nopt counts) on the same
-    # problem, and the paper's speed-ups (Tab. speedup) in device time:
-    # S1 = MLMC / MLQMC, S2 = MLMC / MG-MLQMC, S3 = MLQMC / MG-MLQMC
     c = dict(cfg)
     c.update(precision="mixed_tf32", sampler="mc", R=1, reuse=False)
     ctx = M.Context.from_config(c, max_samples=1 << 17)
     rows = []
-    for eps in cfg["eps"] + [3e-4, 1e-4]:
+    for eps in eps_list:
         r = ctx.estimate_mlmc(eps)
         rows.append({"eps": eps, "seconds": r["wall_seconds"], "gpu_seconds": r["gpu_seconds"], "Q": r["Q"],
-                     "rmse_bound": float(np.sqrt(r["varQ"] + r["bias"] ** 2)), "L": r["L"],
-                     "rounds": r["rounds"], "N": r["N"][:r["L"] + 1], "run_status": r["run_status"]})
-    del ctx
+                     "L": r["L"], "rounds": r["rounds"], "N": r["N"][:r["L"] + 1], "run_status": r["run_status"]})
+    ctx.close()
     out["mlmc_mixed_tf32"] = rows
-    # also in work (cells of the FMG hierarchy per sample, sum_{t<=l} n_t^2, times samples
-    # and replicates): the paper's one-sample-per-core cost, which device time on a
-    # latency-bound GPU does not follow
     model = np.cumsum([(cfg["n0"] << t) ** 2 for t in range(cfg["n_levels"])])
 
     def work(row, R):
@@ -787,19 +828,15 @@ def run_time_to_eps(M):
         sp.append({"eps": m["eps"], "S1": m["gpu_seconds"] / q["gpu_seconds"],
                    "S2": m["gpu_seconds"] / g["gpu_seconds"], "S3": q["gpu_seconds"] / g["gpu_seconds"],
                    "S1_work": wm / wq, "S2_work": wm / wg, "S3_work": wq / wg})
-    keys = ("S1", "S2", "S3", "S1_work", "S2_work", "S3_work")
-    out["speedups"] = {"per_eps": sp, "mean": {k: float(np.mean([x[k] for x in sp])) for k in keys}}
+    out["speedups"] = sp
     out["mimc"] = run_mimc(M, cfg, genvec, model)
     return out
 
 
 def run_mimc(M, cfg, genvec, model):
     """Multi-index variant (grid level x V-cycle count, the outlook of Sec. 7)
-    on the same 7-level problem in the fixed-cycle mixed form: contexts with
-    mu0 = 1, 2, 3 (levels adaptive, every cycle count at each level), against
-    Algorithm 1 with mu0 = 3 (the mean both converge to), in device time and in
-    work (cells of the FMG hierarchy x V-cycles per level, times samples and
-    shifts)."""
+    on the 7-level problem in the fixed-cycle mixed form, mu0 in {1, 2, 3},
+    against Algorithm 1 with mu0 = 3, in device time and in work."""
     mus = (1, 2, 3)
     c = dict(cfg)
     c.update(precision="mixed_tf32", rtol=0.0)
@@ -811,30 +848,55 @@ def run_mimc(M, cfg, genvec, model):
         w_mimc = float(cfg["R"] * sum(r["N"][m][t] * float(model[t]) * (mus[m] + (mus[m - 1] if m else 0))
                                       for m in range(len(mus)) for t in range(len(r["N"][m]))))
         w_alg1 = cfg["R"] * mus[-1] * float(np.dot(a["N"][:a["L"] + 1], model[:a["L"] + 1]))
-        rows.append({"eps": eps, "mimc": {"seconds": r["wall_seconds"], "gpu_seconds": r["gpu_seconds"], "Q": r["Q"],
-                                          "varQ": r["varQ"], "bias": r["bias"], "bias_cycles": r["bias_cycles"],
-                                          "L": r["L"], "N": r["N"], "rounds": r["rounds"],
-                                          "run_status": r["run_status"], "work": w_mimc},
-                     "alg1_mu3": {"seconds": a["wall_seconds"], "gpu_seconds": a["gpu_seconds"], "Q": a["Q"],
-                                  "varQ": a["varQ"], "bias": a["bias"], "L": a["L"], "N": a["N"][:a["L"] + 1],
-                                  "rounds": a["rounds"], "run_status": a["run_status"], "work": w_alg1},
-                     "gpu_time_ratio": a["gpu_seconds"] / r["gpu_seconds"], "work_ratio": w_alg1 / w_mimc})
+        rows.append({"eps": eps, "mimc_gpu_s": r["gpu_seconds"], "alg1_gpu_s": a["gpu_seconds"],
+                     "gpu_time_ratio": a["gpu_seconds"] / r["gpu_seconds"], "work_ratio": w_alg1 / w_mimc,
+                     "mimc_L": r["L"], "alg1_L": a["L"]})
     for x in ctxs:
         x.close()
-    return {"workload": "7 levels 8x8..512x512, s=200, lambda=0.3, R=16, mixed_tf32 with fixed cycles, "
-                        "mu0 in {1,2,3}, levels adaptive; ratios are Algorithm 1 (mu0=3) over the multi-index run",
-            "rows": rows}
+    return rows
+
+
+def run_kl_shape(args):
+    """Only the tensor-core KL contraction (eq. truncatedKL): B samples on the
+    n x n level with s modes through mlqmc_fields (TF32, FP32 accumulation,
+    exp epilogue), device-timed per launch by the library's event brackets;
+    algorithmic work 2 n^2 s B FLOP and 4 (n^2 B + n^2 K + B K) bytes."""
+    import torch
+
+    import paper_1806_05619_gb300 as M
+
+    n, s, B = (int(x) for x in args.kl_shape.split(","))
+    L = int(round(np.log2(n // 8)))
+    cfg = W.scaled(W.PRECISION_1024, n_levels=L + 1, s=s, rtol=0.0)
+    genvec, _ = M.cbc_genvec(s, 10)
+    ctx = M.Context.from_config(cfg, genvec=genvec, max_samples=B)
+    y = torch.from_numpy(W.random_normals(s, B, tag=77)).cuda()
+    for _ in range(args.warmup):
+        ctx.fields(L, y)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    torch.cuda.profiler.start()
+    for _ in range(args.steps):
+        ctx.fields(L, y)
+    torch.cuda.profiler.stop()
+    cell = ctx.profile_read_levels()[("kl_tc", L)]
+    ctx.profile(False)
+    ctx.check_device()
+    P = peaks()
+    t = cell["ms"] * 1e-3 / cell["n"]
+    out = {"kl_shape": {"cells": n * n, "modes": s, "samples": B}, "ms_per_launch": t * 1e3,
+           "tflops": cell["ftc"] / cell["n"] / t / 1e12, "gbs": cell["bytes"] / cell["n"] / t / 1e9,
+           "tf32_peak_sustained": P["tf32_sust"], "hbm_peak": P["hbm"]}
+    out["tensor_frac"] = out["tflops"] / P["tf32_sust"]
+    out["hbm_frac"] = out["gbs"] / P["hbm"]
+    print(json.dumps(out), flush=True)
+    ctx.close()
 
 
 def main():
     args = parse()
-    if args.traffic_from:
-        # fold an ncu capture of one timed step (see profiles/) into the traffic file
-        with open(args.traffic_line) as f:
-            line = json.loads([ln for ln in f if ln.startswith("{")][-1])
-        form = line["config"]["precision"]
-        rec = summarize_traffic(args.traffic_from, form, line["config"]["smoothers"])
-        print(json.dumps({form: rec}, indent=1))
+    if args.kl_shape:
+        run_kl_shape(args)
         return
     if args.impl == "reference":
         run_reference(args)

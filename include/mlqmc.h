@@ -398,10 +398,10 @@ mlqmc_status mlqmc_sample_solution(mlqmc_ctx* c, int32_t level, int32_t r, int64
 /*
  * Allocation-free FMG solve from caller-supplied coefficient fields. The
  * paper has no counterpart: this entry point exists for callers that cannot
- * call cudaMalloc -- code that runs inside a CUDA stream capture or a graph
- * being built, plug-ins whose host application owns the device memory pool,
- * and real-time loops that must not touch the allocator. It needs no context
- * (mlqmc_create allocates) and allocates nothing: its scratch is one static
+ * call cudaMalloc -- plug-ins whose host application owns all device memory
+ * and hands them only their inputs and outputs, and real-time loops that must
+ * not wait on the allocator or risk an allocation failing mid-run. It needs
+ * no context (mlqmc_create allocates) and allocates nothing: its scratch is one static
  * device array of MLQMC_NOALLOC_SLOTS slots of MLQMC_NOALLOC_SLOT_BYTES
  * (16 x 1.25 MiB = 20 MiB) that every GPU loading this library holds until
  * the process exits.
@@ -510,6 +510,20 @@ mlqmc_status mlqmc_profile_read(mlqmc_ctx* c, double* out_ms, int64_t* out_n);
  * numerators of the roofline fractions. Recorded only while profiling is on.
  */
 mlqmc_status mlqmc_profile_work(mlqmc_ctx* c, double* out_bytes, double* out_f64, double* out_f32, double* out_ftc);
+
+/*
+ * The totals of mlqmc_profile_read and mlqmc_profile_work split by grid
+ * level, so that one kernel on one grid size can be put against its
+ * roofline: every output is a host array of 8 x MLQMC_PROFILE_LEVELS entries,
+ * entry [kind * MLQMC_PROFILE_LEVELS + t] for level t (0..MLQMC_PROFILE_LEVELS-2);
+ * the last column holds the launches that belong to no single level (normals,
+ * reuse sums, per-sample outputs). out_ms: device milliseconds; out_n:
+ * launches; out_bytes, out_f64, out_f32, out_ftc: algorithmic work as in
+ * mlqmc_profile_work. Any output may be NULL. Waits for the recorded events.
+ */
+#define MLQMC_PROFILE_LEVELS 13
+mlqmc_status mlqmc_profile_read_levels(mlqmc_ctx* c, double* out_ms, int64_t* out_n, double* out_bytes,
+                                       double* out_f64, double* out_f32, double* out_ftc);
 
 #ifdef __cplusplus
 }

@@ -121,6 +121,7 @@ def lib():
             L.mlqmc_profile.argtypes = [vp, i32]
             L.mlqmc_profile_read.argtypes = [vp, dp, C.POINTER(C.c_int64)]
             L.mlqmc_profile_work.argtypes = [vp, dp, dp, dp, dp]
+            L.mlqmc_profile_read_levels.argtypes = [vp, dp, C.POINTER(C.c_int64), dp, dp, dp, dp]
             L.mlqmc_smoother_info.argtypes = [vp, C.POINTER(C.c_int32), dp]
             L.mlqmc_set_smoother.argtypes = [vp, i32, i32]
             L.mlqmc_set_graphs.argtypes = [vp, i32]
@@ -134,7 +135,7 @@ def lib():
                          "mlqmc_nystrom_modes",
                          "mlqmc_get_device_status",
                          "mlqmc_cbc_genvec", "mlqmc_modes", "mlqmc_point_bits", "mlqmc_normals", "mlqmc_fields",
-                         "mlqmc_sample_solution", "mlqmc_profile", "mlqmc_profile_read", "mlqmc_profile_work", "mlqmc_smoother_info", "mlqmc_set_smoother", "mlqmc_set_graphs",
+                         "mlqmc_sample_solution", "mlqmc_profile", "mlqmc_profile_read", "mlqmc_profile_work", "mlqmc_profile_read_levels", "mlqmc_smoother_info", "mlqmc_set_smoother", "mlqmc_set_graphs",
                          "mlqmc_estimator_from_sums",
                          "mlqmc_fmg_fields_noalloc", "mlqmc_last_iterations"]:
                 getattr(L, name).restype = C.c_int
@@ -380,6 +381,30 @@ class Context:
                "mlqmc_profile_work")
         return {k: {"bytes": float(a[0][i]), "f64": float(a[1][i]), "f32": float(a[2][i]), "ftc": float(a[3][i])}
                 for i, k in enumerate(self.PROFILE_KINDS)}
+
+    PROFILE_LEVELS = 13  # MLQMC_PROFILE_LEVELS: levels 0..11, then launches of no single level
+
+    def profile_read_levels(self):
+        """{(kind, level): {"ms", "n", "bytes", "f64", "f32", "ftc"}} since profile(), for
+        the buckets with launches; level None holds the launches of no single level."""
+        nk, nl = len(self.PROFILE_KINDS), self.PROFILE_LEVELS
+        ms, by, f64, f32, ftc = (np.zeros(nk * nl) for _ in range(5))
+        n = np.zeros(nk * nl, dtype=np.int64)
+        dpp = C.POINTER(C.c_double)
+        _check(lib().mlqmc_profile_read_levels(self.h, ms.ctypes.data_as(dpp), n.ctypes.data_as(C.POINTER(C.c_int64)),
+                                               by.ctypes.data_as(dpp), f64.ctypes.data_as(dpp),
+                                               f32.ctypes.data_as(dpp), ftc.ctypes.data_as(dpp)),
+               "mlqmc_profile_read_levels")
+        out = {}
+        for k, name in enumerate(self.PROFILE_KINDS):
+            for t in range(nl):
+                i = k * nl + t
+                if n[i] == 0:
+                    continue
+                out[(name, t if t < nl - 1 else None)] = {"ms": float(ms[i]), "n": int(n[i]), "bytes": float(by[i]),
+                                                          "f64": float(f64[i]), "f32": float(f32[i]),
+                                                          "ftc": float(ftc[i])}
+        return out
 
     def last_iterations(self):
         """Per level, the most extra cycles / refinement steps any sample needed since the last query."""

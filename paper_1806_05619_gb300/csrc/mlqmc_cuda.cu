@@ -1281,19 +1281,21 @@ Work work_of(double bytes, double flops)
 struct Timed {
     mlqmc_ctx* c;
     int kind;
+    int level;
     cudaStream_t st;
     int nk;
     cudaEvent_t a = nullptr;
     Timed(mlqmc_ctx* c_, int kind_, cudaStream_t st_, const Work& w = Work(), int nk_ = 1)
-        : c(c_), kind(kind_), st(st_), nk(nk_)
+        : c(c_), kind(kind_), level(c_->prof_level), st(st_), nk(nk_)
     {
         if (c->profiling) {
             a = take_event(c);
             record(a);
-            c->prof_bytes[kind] += w.bytes;
-            c->prof_f64[kind] += w.f64;
-            c->prof_f32[kind] += w.f32;
-            c->prof_ftc[kind] += w.ftc;
+            ProfCell& pc = c->prof[kind][level];
+            pc.bytes += w.bytes;
+            pc.f64 += w.f64;
+            pc.f32 += w.f32;
+            pc.ftc += w.ftc;
         }
     }
     ~Timed()
@@ -1302,7 +1304,7 @@ struct Timed {
         if (!a) return;
         cudaEvent_t b = take_event(c);
         record(b);
-        c->marks.push_back({kind, nk, a, b});
+        c->marks.push_back({kind, level, nk, a, b});
     }
     // inside a stream capture the record must become an event-record node of
     // the graph (external), so that the host can time every replay
@@ -1311,6 +1313,14 @@ struct Timed {
         if (c->graph.capturing) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
         else cudaEventRecord(e, st);
     }
+};
+
+// The grid level that the brackets of the enclosing scope belong to.
+struct LevelTag {
+    mlqmc_ctx* c;
+    int prev;
+    LevelTag(mlqmc_ctx* c_, int t) : c(c_), prev(c_->prof_level) { c->prof_level = t; }
+    ~LevelTag() { c->prof_level = prev; }
 };
 
 // Cells and faces of one direction on level t.
@@ -1345,6 +1355,7 @@ mlqmc_status last_error()
 // Level-0 factor, exact solve and F_0 of samples 0..B-1 (one thread each).
 mlqmc_status launch_level0(mlqmc_ctx* c, const FmgArgs& A, int B, cudaStream_t st)
 {
+    LevelTag lt(c, 0);
     // per sample: faces in, band factor (n0 + 1 entries per row) and solutions out;
     // banded Cholesky N0 n0^2 and two triangular solves 4 N0 n0 FP64 FLOPs
     const double N0 = cells_of(c, 0), n0 = c->p.coarse_cells, es = is_mixed(c->p) ? 4.0 : 8.0;
@@ -1435,6 +1446,7 @@ bool uses_tc(const mlqmc_ctx* c, int t)
 template <typename T>
 mlqmc_status synth_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cudaStream_t st)
 {
+    LevelTag lt(c, t);
     const int64_t n = c->p.coarse_cells << t;
     if constexpr (sizeof(T) == 4) {
         if (uses_tc(c, t)) {
@@ -1504,6 +1516,7 @@ mlqmc_status build_c(mlqmc_ctx* c, int count, cudaStream_t st)
 
 mlqmc_status zero_u(mlqmc_ctx* c, int t, int B, cudaStream_t st)
 {
+    LevelTag lt(c, t);
     const LevelPool& P = c->pools[t];
     return ok(cudaMemsetAsync(P.mem + P.off[kU], 0, P.stride[kU] * static_cast<size_t>(B), st)) ? MLQMC_OK
                                                                                                 : MLQMC_ERR_CUDA;
@@ -1569,6 +1582,7 @@ int tile_side(const mlqmc_ctx* c, int t)
 template <typename T>
 void smooth(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int first, int ones, bool pro, cudaStream_t st)
 {
+    LevelTag lt(c, t);
     const int64_t n = c->p.coarse_cells << t;
     const int tile = tile_side<T>(c, t);
     const double es = sizeof(T), Mc = cells_of(c, t), Fc = faces_of(c, t);
@@ -1613,6 +1627,7 @@ void smooth(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int first, int 
 mlqmc_status smooth_stream(mlqmc_ctx* c, const FmgArgs& A, int t, int B, int nsweeps, int first, int ones, bool pre,
                            bool post, cudaStream_t st)
 {
+    LevelTag lt(c, t);
     const int n = c->p.coarse_cells << t;
     const double Mc = cells_of(c, t), Fc = faces_of(c, t);
     while (nsweeps > 0) {
@@ -1636,6 +1651,7 @@ mlqmc_status smooth_stream(mlqmc_ctx* c, const FmgArgs& A, int t, int B, int nsw
 mlqmc_status smooth_tma(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int first, int ones, bool pro,
                         cudaStream_t st, bool zin = false)
 {
+    LevelTag lt(c, t);
     const int n = c->p.coarse_cells << t;
     const double Mc = cells_of(c, t), Fc = faces_of(c, t);
     while (nsweeps > 0) {
@@ -1658,6 +1674,7 @@ mlqmc_status smooth_tma(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int
 mlqmc_status smooth_whole(mlqmc_ctx* c, const FmgArgs& A, int t, int B, int nsweeps, int first, int ones, bool pre,
                           bool post, cudaStream_t st, bool zin = false)
 {
+    LevelTag lt(c, t);
     const int n = c->p.coarse_cells << t;
     const bool f64 = !is_mixed(c->p);
     const double Mc = cells_of(c, t), Fc = faces_of(c, t), es = f64 ? 8.0 : 4.0;
@@ -1687,6 +1704,7 @@ template <typename T>
 mlqmc_status presmooth_restrict(mlqmc_ctx* c, FmgArgs& A, int t, int B, int top_ones, cudaStream_t st,
                                 bool zin = false)
 {
+    LevelTag lt(c, t);
     const int sk = smoother_of<T>(c, t);
     if (sk == MLQMC_SMOOTHER_WHOLE && c->p.nu1 > 0)  // residual and restriction in the same pass
         return smooth_whole(c, A, t, B, c->p.nu1, 0, top_ones, true, false, st, zin);
@@ -1708,6 +1726,7 @@ mlqmc_status presmooth_restrict(mlqmc_ctx* c, FmgArgs& A, int t, int B, int top_
 template <typename T>
 mlqmc_status correct_postsmooth(mlqmc_ctx* c, FmgArgs& A, int t, int B, int top_ones, cudaStream_t st)
 {
+    LevelTag lt(c, t);
     const int sk = smoother_of<T>(c, t);
     if (sk == MLQMC_SMOOTHER_WHOLE && c->p.nu2 > 0)  // the correction in the same pass
         return smooth_whole(c, A, t, B, c->p.nu2, 1, top_ones, false, true, st);
@@ -1731,6 +1750,7 @@ mlqmc_status vcycle_batched(mlqmc_ctx* c, FmgArgs& A, int t_top, int B, bool one
     {
         const double N0 = cells_of(c, 0), n0 = c->p.coarse_cells, es = sizeof(T);
         Timed tm(c, kProfSmallV, st, work_of<T>(B * es * (N0 * (n0 + 1.0) + 2.0 * N0), B * 4.0 * N0 * n0));
+        LevelTag lt(c, 0);
         launch_coarse<T>(c, A, B, st);
     }
     for (int t = 1; t <= t_top; ++t) {
@@ -1746,6 +1766,7 @@ mlqmc_status vcycle_batched(mlqmc_ctx* c, FmgArgs& A, int t_top, int B, bool one
 template <typename T>
 mlqmc_status converge_batched(mlqmc_ctx* c, FmgArgs& A, int t, int B, cudaStream_t st)
 {
+    LevelTag lt(c, t);
     const int64_t n = c->p.coarse_cells << t;
     const double es = sizeof(T), Mc = cells_of(c, t), Fc = faces_of(c, t);
     // chunks of about 8192 cells per CTA (this path is never graph-captured: the buffer may grow here)
@@ -1806,6 +1827,7 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
     for (int t = 1; t <= Lmax; ++t) {
         const int B = Bt[t];
         if (B == 0) break;
+        LevelTag lt(c, t);
         const int64_t n = c->p.coarse_cells << t;
         const double es = sizeof(T), Mc = cells_of(c, t), Fc = faces_of(c, t);
         if (refine && MX) {
@@ -2313,7 +2335,7 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
     }
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
-    c->pool_budget = std::min<size_t>(free_b / 2, static_cast<size_t>(96) << 30);
+    c->pool_budget = std::min<size_t>(free_b / 2, static_cast<size_t>(192) << 30);
     if (!mlqmc_tma::prepare() || !mlqmc_whole::prepare()) {
         free_ctx(c);
         return MLQMC_ERR_CUDA;
@@ -2385,15 +2407,18 @@ mlqmc_status graph_replay(mlqmc_ctx* c, cudaStream_t st)
         for (const auto& m : G.marks) {
             float ms = 0.0f;
             if (!ok(cudaEventElapsedTime(&ms, m.a, m.b))) return MLQMC_ERR_CUDA;
-            c->prof_ms[m.kind] += ms;
-            c->prof_n[m.kind] += m.nk;
+            c->prof[m.kind][m.level].ms += ms;
+            c->prof[m.kind][m.level].n += m.nk;
         }
-        for (int k = 0; k < kProfKinds; ++k) {
-            c->prof_bytes[k] += G.work[0][k];
-            c->prof_f64[k] += G.work[1][k];
-            c->prof_f32[k] += G.work[2][k];
-            c->prof_ftc[k] += G.work[3][k];
-        }
+        for (int k = 0; k < kProfKinds; ++k)
+            for (int l = 0; l < kProfLevels; ++l) {
+                ProfCell& pc = c->prof[k][l];
+                const ProfCell& gw = G.work[k][l];
+                pc.bytes += gw.bytes;
+                pc.f64 += gw.f64;
+                pc.f32 += gw.f32;
+                pc.ftc += gw.ftc;
+            }
     }
     return MLQMC_OK;
 }
@@ -2416,13 +2441,7 @@ mlqmc_status graph_capture(mlqmc_ctx* c, int count, const int* Bt, int Lmax, dou
     std::memcpy(G.h_samples, G.key.data(), static_cast<size_t>(count) * sizeof(SampleDesc));
     const size_t marks0 = c->marks.size();
     const int64_t launches0 = c->launches;
-    double w0[4][kProfKinds];
-    for (int k = 0; k < kProfKinds; ++k) {
-        w0[0][k] = c->prof_bytes[k];
-        w0[1][k] = c->prof_f64[k];
-        w0[2][k] = c->prof_f32[k];
-        w0[3][k] = c->prof_ftc[k];
-    }
+    std::vector<ProfCell> w0(&c->prof[0][0], &c->prof[0][0] + kProfKinds * kProfLevels);
     if (!ok(cudaStreamBeginCapture(G.stream, cudaStreamCaptureModeThreadLocal))) return MLQMC_ERR_CUDA;
     G.capturing = true;
     mlqmc_status s = ok(cudaMemcpyAsync(c->d_samples, G.h_samples, count * sizeof(SampleDesc), cudaMemcpyHostToDevice,
@@ -2437,16 +2456,17 @@ mlqmc_status graph_capture(mlqmc_ctx* c, int count, const int* Bt, int Lmax, dou
     c->marks.resize(marks0);
     G.launches = c->launches - launches0;
     c->launches = launches0;
-    for (int k = 0; k < kProfKinds; ++k) {
-        G.work[0][k] = c->prof_bytes[k] - w0[0][k];
-        G.work[1][k] = c->prof_f64[k] - w0[1][k];
-        G.work[2][k] = c->prof_f32[k] - w0[2][k];
-        G.work[3][k] = c->prof_ftc[k] - w0[3][k];
-        c->prof_bytes[k] = w0[0][k];
-        c->prof_f64[k] = w0[1][k];
-        c->prof_f32[k] = w0[2][k];
-        c->prof_ftc[k] = w0[3][k];
-    }
+    for (int k = 0; k < kProfKinds; ++k)
+        for (int l = 0; l < kProfLevels; ++l) {
+            ProfCell& pc = c->prof[k][l];
+            const ProfCell& before = w0[static_cast<size_t>(k) * kProfLevels + l];
+            ProfCell& gw = G.work[k][l];
+            gw.bytes = pc.bytes - before.bytes;
+            gw.f64 = pc.f64 - before.f64;
+            gw.f32 = pc.f32 - before.f32;
+            gw.ftc = pc.ftc - before.ftc;
+            pc = before;
+        }
     if (s == MLQMC_OK && (!ended || !graph)) s = MLQMC_ERR_CUDA;
     if (s == MLQMC_OK && !ok(cudaGraphInstantiate(&G.exec, graph, 0))) {
         G.exec = nullptr;
@@ -2683,11 +2703,8 @@ extern "C" mlqmc_status mlqmc_profile(mlqmc_ctx* c, int32_t enable)
     }
     c->marks.clear();
     c->profiling = enable != 0;
-    for (int i = 0; i < kProfKinds; ++i) {
-        c->prof_ms[i] = 0.0;
-        c->prof_n[i] = 0;
-        c->prof_bytes[i] = c->prof_f64[i] = c->prof_f32[i] = c->prof_ftc[i] = 0.0;
-    }
+    for (auto& row : c->prof)
+        for (auto& pc : row) pc = ProfCell();
     return MLQMC_OK;
 }
 
@@ -2696,31 +2713,68 @@ extern "C" mlqmc_status mlqmc_profile_work(mlqmc_ctx* c, double* out_bytes, doub
 {
     if (!c || !out_bytes || !out_f64 || !out_f32 || !out_ftc) return MLQMC_ERR_INVALID_ARG;
     for (int i = 0; i < kProfKinds; ++i) {
-        out_bytes[i] = c->prof_bytes[i];
-        out_f64[i] = c->prof_f64[i];
-        out_f32[i] = c->prof_f32[i];
-        out_ftc[i] = c->prof_ftc[i];
+        out_bytes[i] = out_f64[i] = out_f32[i] = out_ftc[i] = 0.0;
+        for (const ProfCell& pc : c->prof[i]) {
+            out_bytes[i] += pc.bytes;
+            out_f64[i] += pc.f64;
+            out_f32[i] += pc.f32;
+            out_ftc[i] += pc.ftc;
+        }
     }
     return MLQMC_OK;
 }
 
-extern "C" mlqmc_status mlqmc_profile_read(mlqmc_ctx* c, double* out_ms, int64_t* out_n)
+namespace {
+// Fold the recorded brackets into the per-kind, per-level times (waits for them).
+mlqmc_status drain_marks(mlqmc_ctx* c)
 {
-    if (!c || !out_ms || !out_n) return MLQMC_ERR_INVALID_ARG;
     for (auto& m : c->marks) {
         if (!ok(cudaEventSynchronize(m.b))) return MLQMC_ERR_CUDA;
         float ms = 0.0f;
         if (!ok(cudaEventElapsedTime(&ms, m.a, m.b))) return MLQMC_ERR_CUDA;
-        c->prof_ms[m.kind] += ms;
-        c->prof_n[m.kind] += m.nk;
+        c->prof[m.kind][m.level].ms += ms;
+        c->prof[m.kind][m.level].n += m.nk;
         c->pool.push_back(m.a);
         c->pool.push_back(m.b);
     }
     c->marks.clear();
+    return MLQMC_OK;
+}
+}  // namespace
+
+extern "C" mlqmc_status mlqmc_profile_read(mlqmc_ctx* c, double* out_ms, int64_t* out_n)
+{
+    if (!c || !out_ms || !out_n) return MLQMC_ERR_INVALID_ARG;
+    const mlqmc_status s = drain_marks(c);
+    if (s != MLQMC_OK) return s;
     for (int i = 0; i < kProfKinds; ++i) {
-        out_ms[i] = c->prof_ms[i];
-        out_n[i] = c->prof_n[i];
+        out_ms[i] = 0.0;
+        out_n[i] = 0;
+        for (const ProfCell& pc : c->prof[i]) {
+            out_ms[i] += pc.ms;
+            out_n[i] += pc.n;
+        }
     }
+    return MLQMC_OK;
+}
+
+extern "C" mlqmc_status mlqmc_profile_read_levels(mlqmc_ctx* c, double* out_ms, int64_t* out_n, double* out_bytes,
+                                                  double* out_f64, double* out_f32, double* out_ftc)
+{
+    if (!c) return MLQMC_ERR_INVALID_ARG;
+    const mlqmc_status s = drain_marks(c);
+    if (s != MLQMC_OK) return s;
+    for (int k = 0; k < kProfKinds; ++k)
+        for (int l = 0; l < kProfLevels; ++l) {
+            const ProfCell& pc = c->prof[k][l];
+            const size_t i = static_cast<size_t>(k) * kProfLevels + l;
+            if (out_ms) out_ms[i] = pc.ms;
+            if (out_n) out_n[i] = pc.n;
+            if (out_bytes) out_bytes[i] = pc.bytes;
+            if (out_f64) out_f64[i] = pc.f64;
+            if (out_f32) out_f32[i] = pc.f32;
+            if (out_ftc) out_ftc[i] = pc.ftc;
+        }
     return MLQMC_OK;
 }
 

@@ -63,6 +63,17 @@ enum ProfKind {
     kProfKinds = 8
 };
 
+// Profile buckets per grid level; the last holds launches of no single level
+// (normals, reuse sums, outputs).
+constexpr int kProfLevels = MLQMC_MAX_LEVELS + 1;
+constexpr int kProfNoLevel = MLQMC_MAX_LEVELS;
+static_assert(kProfLevels == MLQMC_PROFILE_LEVELS, "profile level buckets of the C ABI");
+
+struct ProfCell {
+    double ms = 0.0, bytes = 0.0, f64 = 0.0, f32 = 0.0, ftc = 0.0;
+    int64_t n = 0;
+};
+
 // Pool of per-sample arrays of one level: array a of sample i lives at
 // mem + off[a] + i * stride[a].
 enum PoolArr { kU = 0, kBc, kKx, kKy, kIdiag, kK, kG, kU64, kU2, kPoolArrs };
@@ -147,19 +158,17 @@ struct mlqmc_ctx {
     // optional per-kernel event timing
     bool profiling = false;
     struct Mark {
-        int kind, nk;  // kernel kind, kernels inside the bracket
+        int kind, level, nk;  // kernel kind, grid level (kProfNoLevel: none), kernels inside the bracket
         cudaEvent_t a, b;
     };
     std::vector<Mark> marks;        // recorded, not yet read
     std::vector<cudaEvent_t> pool;  // free events
-    double prof_ms[kProfKinds] = {};
-    int64_t prof_n[kProfKinds] = {};
-    // algorithmic work of the launches since mlqmc_profile(1): bytes each launch
-    // must move (every array it touches once) and FP64 / FP32 / tensor-core FLOPs
-    double prof_bytes[kProfKinds] = {};
-    double prof_f64[kProfKinds] = {};
-    double prof_f32[kProfKinds] = {};
-    double prof_ftc[kProfKinds] = {};
+    // per kernel kind and grid level: device time and launches of the read
+    // brackets, and the algorithmic work of the launches since mlqmc_profile(1)
+    // (bytes each launch must move with every array it touches once; FP64 /
+    // FP32 / tensor-core FLOPs)
+    ProfCell prof[kProfKinds][kProfLevels];
+    int prof_level = kProfNoLevel;  // level that the next brackets belong to
 
     // smoother of each level's V-cycle sweeps (MLQMC_SMOOTHER_*), picked by
     // the autotuner at creation (mixed forms) or fixed by mlqmc_set_smoother;
@@ -184,7 +193,7 @@ struct mlqmc_ctx {
         int seen = 0;  // 1: key seen once, 2: captured
         cudaGraphExec_t exec = nullptr;
         std::vector<Mark> marks;  // events recorded inside the graph (profiling)
-        double work[4][kProfKinds] = {};
+        ProfCell work[kProfKinds][kProfLevels];  // algorithmic work of one replay
         int64_t launches = 0;
         int64_t replays = 0;
         bool capturing = false;  // event brackets become graph event-record nodes

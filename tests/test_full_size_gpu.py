@@ -110,7 +110,7 @@ def test_problem3_batch_of_256_on_1024x1024(precision):
 
 @pytest.mark.parametrize("precision", ["mixed_tf32", "fp64"])
 def test_problem5_samples_on_2048x2048(precision):
-    cfg = W.scaled(W.ADAPTIVE_9LEVEL, precision=precision, log2_nmax=10)
+    cfg = W.scaled(W.ADAPTIVE_9LEVEL, precision=precision, log2_nmax=10, rtol=1e-10)
     top = cfg["n_levels"] - 1
     work = [(top, 0, 2, 0, 2), (0, 0, 40, 0, 3), (5, 3, 5, 1, 2)]
     ctx, orc = _setup(cfg, max_samples=256)

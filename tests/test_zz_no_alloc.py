@@ -1,14 +1,16 @@
-"""mlqmc_fmg_fields_noalloc against the regular path.
+"""mlqmc_fmg_fields_noalloc against the regular path and the oracle.
 
-Some callers cannot call cudaMalloc: code issued inside a CUDA stream capture,
-plug-ins whose host application owns the device memory pool, and real-time
-loops that must not touch the allocator. For them the library has one entry
-point that allocates nothing and keeps its scratch in a static device array.
-This test gives it the KL fields that a regular context synthesises for some
-samples and checks that the F_t it returns equal those of the regular
-mlqmc_sample_solution path (same tolerance as the other FP64 parity tests,
-1e-12 relative), on two calls in a row with different problem shapes, so the
-second call runs over whatever the first left in the shared scratch.
+Some callers cannot call cudaMalloc: plug-ins whose host application owns
+all device memory and hands them only their inputs and outputs, and
+real-time loops that must not wait on the allocator or risk an allocation
+failing mid-run. For them the library has one entry point that allocates
+nothing and keeps its scratch in a static device array. These tests give it
+KL fields and check the F_t it returns (1e-12 relative, the tolerance of the
+other FP64 parity tests), each on two calls in a row with different problem
+shapes, so the second call runs over whatever the first left in the shared
+scratch: against the regular mlqmc_sample_solution path on the fields a
+regular context synthesises, and against the oracle's FMG on the oracle's
+own fields.
 """
 import ctypes as C
 import os
@@ -68,6 +70,27 @@ def test_two_calls_match_regular_path(ctx):
     F2 = _noalloc(cfg, 3, k2, 7)
     ref2 = _regular(c, 2, 5, 0, 7)
     assert np.max(np.abs(F2 - ref2) / np.abs(ref2)) < 1e-12
+
+
+def test_two_calls_match_oracle_on_its_fields(ctx):
+    cfg, _ = ctx
+    z, _ = O.cbc(cfg["s"], cfg["log2_nmax"])
+    orc = O.Oracle(n_levels=cfg["n_levels"], n0=cfg["n0"], s=cfg["s"], sigma=cfg["sigma"], corr_len=cfg["corr_len"],
+                   qoi=cfg["qoi"], mu0=cfg["mu0"], nu1=cfg["nu1"], nu2=cfg["nu2"], sampler="lattice",
+                   seed=cfg["seed"], R=cfg["R"], genvec=z, log2_nmax=cfg["log2_nmax"], reuse=True)
+    for level, r, count in [(4, 1, 3), (2, 6, 4)]:
+        ks, refs = [], []
+        for i in range(count):
+            y = orc.normals(level, r, i)
+            kl = [orc.field(t, y) for t in range(level + 1)]
+            ks.append(np.concatenate(kl))
+            ref = orc.fmg_fields(level, kl)
+            assert ref["status"] == O.OK
+            refs.append(ref["F"])
+        k = torch.from_numpy(np.stack(ks)).cuda().contiguous()
+        F = _noalloc(cfg, level + 1, k, count)
+        ref = np.array(refs)
+        assert np.max(np.abs(F - ref) / np.abs(ref)) < 1e-12
 
 
 def test_rejects_problems_beyond_the_scratch(ctx):

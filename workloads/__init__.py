@@ -56,9 +56,13 @@ PRECISION_1024 = _cfg(3, n_levels=8, s=400, corr_len=0.1, precision="mixed_tf32"
 #    eps in {1e-2, 3e-3, 1e-3}.
 ADAPTIVE_7LEVEL = _cfg(4, n_levels=7, s=200, precision="mixed_tf32", rtol=1e-10,
                        eps=[1e-2, 3e-3, 1e-3], log2_nmax=16)
-# 5: large adaptive MLQMC: 9 levels 8x8..2048x2048, s=1000, lambda=0.05.
-ADAPTIVE_9LEVEL = _cfg(5, n_levels=9, s=1000, corr_len=0.05, precision="mixed_tf32", rtol=1e-10,
-                       eps=[1e-4], log2_nmax=16)
+# 5: large adaptive MLQMC: 9 levels 8x8..2048x2048, s=1000, lambda=0.05, R=16,
+#    FMG with fixed mu0 = 2 V(2,2)-cycles per level. One fixed-count step: 16
+#    points per shift on the finest level doubling per coarser level
+#    (N_l = 4096, 2048, ..., 16 on levels 0..8; 256 finest fields, 130,816
+#    samples); adaptive runs to eps = 1e-4.
+ADAPTIVE_9LEVEL = _cfg(5, n_levels=9, s=1000, corr_len=0.05, precision="mixed_tf32", rtol=0.0,
+                       eps=[1e-4], log2_nmax=12, counts=[16 << (8 - lv) for lv in range(9)])
 
 # 6: multi-index variant, grid level x V-cycle count (one context per cycle
 #    count mu0 in {1, 2, 3}): 4 levels 4x4..32x32, s=10, lattice, R=4.
