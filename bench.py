@@ -75,6 +75,8 @@ def parse(argv=None):
     ap.add_argument("--counts-div", type=int, default=1,
                     help="divide the per-level counts (small cases for profiler captures only)")
     ap.add_argument("--cpu-workers", type=int, default=0, help="oracle processes (0: every host core)")
+    ap.add_argument("--shifts", type=int, default=0,
+                    help="override R (profiler captures only, to keep the device footprint small)")
     ap.add_argument("--modes", type=int, default=0,
                     help="override s (profiler captures of the grid kernels only, to keep the KL tables small)")
     ap.add_argument("--kl-shape", default="",
@@ -93,8 +95,10 @@ WORKLOADS = {
 }
 
 
-def workload_config(name, rank=0, counts_div=1, precision=None, modes=0):
+def workload_config(name, rank=0, counts_div=1, precision=None, modes=0, shifts=0):
     cfg = dict(WORKLOADS[name][0])
+    if shifts:
+        cfg["R"] = shifts
     cfg["seed"] = cfg["seed"] + 1000 * rank
     cfg["counts"] = [max(1, c // counts_div) for c in cfg["counts"]]
     if precision:
@@ -497,7 +501,8 @@ def run_ours(args):
         return float(t.item())
 
     details = {}
-    cfg = workload_config(args.workload, rank, args.counts_div, precision="mixed_tf32", modes=args.modes)
+    cfg = workload_config(args.workload, rank, args.counts_div, precision="mixed_tf32", modes=args.modes,
+                          shifts=args.shifts)
     ns = n_samples(W.fixed_count_work(cfg["counts"], cfg["R"]))
     genvec, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
