@@ -480,6 +480,26 @@ mlqmc_status mlqmc_set_graphs(mlqmc_ctx* c, int32_t enable);
 int64_t mlqmc_graph_replays(const mlqmc_ctx* c);
 
 /*
+ * Round graphs (on with graph replay). A call of mlqmc_sample_levels that is
+ * not a repeat -- one adaptive round of Algorithm 1 (Sec. 3.3), whose sample
+ * counts differ from the previous round's -- runs as one graph launch when
+ * it fits one chunk and profiling is off: the descriptors are uploaded by one
+ * copy, then the call's kernels are captured into a graph, an instantiated
+ * graph of the same launch shape (the levels that run, their smoothers, the
+ * outputs asked for) is updated in place (cudaGraphExecUpdate) or a new one
+ * instantiated, and the graph is launched once. In the converged forms
+ * (refine_rtol > 0) each level's refinement loop becomes a conditional WHILE
+ * node: its body (the masked mu0 V-cycles, u64 += e, the residual norms and
+ * the loop decision) repeats on the device with no host round trip, taking
+ * the same decisions as the host loop (stop when no sample is above the
+ * tolerance; NOT_CONVERGED after refine_max_iter passes). Results equal those
+ * of the launch-by-launch path (same kernels, same order).
+ * mlqmc_graph_stats: out (host, 4 int64): repeat-graph replays, round-graph
+ * launches, in-place updates, instantiations since creation.
+ */
+mlqmc_status mlqmc_graph_stats(const mlqmc_ctx* c, int64_t* out);
+
+/*
  * Per-kernel device timing of mlqmc_sample_levels (off by default). With
  * enable = 1 every later launch is bracketed by CUDA events recorded on the
  * launch stream; enable = 0 stops recording. Either call clears the totals.

@@ -126,6 +126,7 @@ def lib():
             L.mlqmc_set_smoother.argtypes = [vp, i32, i32]
             L.mlqmc_set_graphs.argtypes = [vp, i32]
             L.mlqmc_estimator_from_sums.argtypes = [i32, i32, i32, C.POINTER(C.c_int64), dp, dp, dp, dp, dp]
+            L.mlqmc_graph_stats.argtypes = [vp, C.POINTER(C.c_int64)]
             L.mlqmc_graph_replays.argtypes = [vp]
             L.mlqmc_graph_replays.restype = i64
             L.mlqmc_launch_count.argtypes = [vp]
@@ -136,7 +137,7 @@ def lib():
                          "mlqmc_get_device_status",
                          "mlqmc_cbc_genvec", "mlqmc_modes", "mlqmc_point_bits", "mlqmc_normals", "mlqmc_fields",
                          "mlqmc_sample_solution", "mlqmc_profile", "mlqmc_profile_read", "mlqmc_profile_work", "mlqmc_profile_read_levels", "mlqmc_smoother_info", "mlqmc_set_smoother", "mlqmc_set_graphs",
-                         "mlqmc_estimator_from_sums",
+                         "mlqmc_estimator_from_sums", "mlqmc_graph_stats",
                          "mlqmc_fmg_fields_noalloc", "mlqmc_last_iterations"]:
                 getattr(L, name).restype = C.c_int
             _lib = L
@@ -434,6 +435,12 @@ class Context:
 
     def graph_replays(self) -> int:
         return int(lib().mlqmc_graph_replays(self.h))
+
+    def graph_stats(self):
+        """{"replays", "round_launches", "round_updates", "round_instantiations"} since creation."""
+        out = (C.c_int64 * 4)()
+        _check(lib().mlqmc_graph_stats(self.h, out), "mlqmc_graph_stats")
+        return dict(zip(["replays", "round_launches", "round_updates", "round_instantiations"], list(out)))
 
     def launch_count(self) -> int:
         return int(lib().mlqmc_launch_count(self.h))

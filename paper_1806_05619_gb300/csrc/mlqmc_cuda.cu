@@ -976,6 +976,39 @@ __global__ void kb_norm_flags(const double* part, int P, double* norms, int* act
     }
 }
 
+// Control of a device-side refinement loop (the body of a conditional WHILE
+// node of a round graph), the same decisions as the host loop of the
+// converged form: at iteration it (iter[0]) with cnt samples above the
+// threshold, stop when cnt = 0; when it has reached max_iter, stop and record
+// NOT_CONVERGED; else run the body once more. iter[MLQMC_MAX_LEVELS] keeps the
+// largest iteration reached. The count is cleared for the next pass.
+__global__ void k_loop_ctl(cudaGraphConditionalHandle h, int* count, int* iter, int max_iter, int* status)
+{
+    const int cnt = *count;
+    *count = 0;
+    const int it = iter[0];
+    if (it > iter[MLQMC_MAX_LEVELS]) iter[MLQMC_MAX_LEVELS] = it;
+    unsigned go = 0;
+    if (cnt > 0) {
+        if (it >= max_iter) {
+            atomicOr(status, kStatusNotConverged);
+        } else {
+            go = 1;
+            iter[0] = it + 1;
+        }
+    }
+    cudaGraphSetConditional(h, go);
+}
+
+// Zero n 16-byte words (the correction of a level inside a loop body, where a
+// graph takes kernel nodes).
+__global__ void k_zero16(uint4* p, size_t n)
+{
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x)
+        p[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+
 // Team index and count of a flat grid: one CTA or one warp per sample.
 template <typename TM>
 __device__ __forceinline__ int team_index()
@@ -1061,6 +1094,99 @@ __global__ void __launch_bounds__(256) kb_qoi(FmgArgs A, int t, int B)
                 u[p] = make_float2(narrow(w.x), narrow(w.y));
             }
         }
+    }
+}
+
+// F_t on large levels in chunks, so that a few large samples still fill the
+// GPU: CTA (i, q) of the B x P grid takes the cell pairs [q csz, (q+1) csz)
+// of sample i with the per-cell work of kb_qoi (UPD: u64 += e, the FP32 copy
+// of u64, the sum; U64 with FP32 work arrays: the FP32 copy and the sum;
+// else the sum) and writes its partial sum; kb_qoi_final adds each sample's
+// partials in order.
+template <typename T, bool U64, bool UPD>
+__global__ void __launch_bounds__(256) kb_qoi_part(FmgArgs A, int t, int B, int P, double* part)
+{
+    static_assert(!UPD || (U64 && sizeof(T) == 4), "the fused update is the mixed forms' refinement step");
+    __shared__ double red[48];
+    const int n = A.lv[t].n;
+    const int np = n * n / 2;  // cell pairs (n even)
+    const int csz = (np + P - 1) / P;
+    constexpr int kT = 256;
+    for (int w = blockIdx.x; w < B * P; w += gridDim.x) {  // uniform per CTA: every thread reaches block_sum
+        const int i = w / P, q = w - i * P;
+        const int p0 = q * csz, p1 = min(np, p0 + csz);
+        double acc = 0.0;
+        if constexpr (U64) {
+            double2* u64 = reinterpret_cast<double2*>(at<double>(A.lv[t].u64, i));
+            float2* u = reinterpret_cast<float2*>(at<float>(A.lv[t].u, i));
+            constexpr int U = 4;
+            int p = p0 + static_cast<int>(threadIdx.x);
+            for (; p + (U - 1) * kT < p1; p += U * kT) {
+                double2 r[U];
+                float2 d[U];
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+                    r[k] = u64[p + k * kT];
+                    if constexpr (UPD) d[k] = u[p + k * kT];
+                }
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+                    if constexpr (UPD) {
+                        r[k] = make_double2(r[k].x + widen(d[k].x), r[k].y + widen(d[k].y));
+                        u64[p + k * kT] = r[k];
+                    }
+                    if constexpr (sizeof(T) == 4) u[p + k * kT] = make_float2(narrow(r[k].x), narrow(r[k].y));
+                    acc += r[k].x;
+                    acc += r[k].y;
+                }
+            }
+            for (; p < p1; p += kT) {
+                double2 r = u64[p];
+                if constexpr (UPD) {
+                    const float2 d = u[p];
+                    r = make_double2(r.x + widen(d.x), r.y + widen(d.y));
+                    u64[p] = r;
+                }
+                if constexpr (sizeof(T) == 4) u[p] = make_float2(narrow(r.x), narrow(r.y));
+                acc += r.x;
+                acc += r.y;
+            }
+        } else {
+            const T* u = at<T>(A.lv[t].u, i);
+            for (int p = p0 + static_cast<int>(threadIdx.x); p < p1; p += kT) {
+                acc += static_cast<double>(u[2 * p]);
+                acc += static_cast<double>(u[2 * p + 1]);
+            }
+        }
+        const double sum = block_sum(acc, red);
+        if (threadIdx.x == 0) part[w] = sum;
+    }
+}
+
+// F_t of samples 0..B-1 from the chunk sums (mean of u, partials added in
+// order) or from the four centre cells (centre QoI).
+template <typename T, bool U64>
+__global__ void kb_qoi_final(FmgArgs A, int t, int B, int P, const double* __restrict__ part)
+{
+    const int n = A.lv[t].n;
+    GRID_STRIDE(i, B)
+    {
+        double v;
+        if (A.qoi == MLQMC_QOI_MEAN) {
+            double sum = 0.0;
+            for (int q = 0; q < P; ++q) sum += part[static_cast<size_t>(i) * P + q];
+            v = sum / (static_cast<double>(n) * n);
+        } else {
+            const int m = n / 2;
+            const int c[4] = {(m - 1) * n + (m - 1), (m - 1) * n + m, m * n + (m - 1), m * n + m};
+            double s4 = 0.0;
+            for (int k = 0; k < 4; ++k) {
+                if constexpr (U64) s4 += at<double>(A.lv[t].u64, i)[c[k]];
+                else s4 += static_cast<double>(at<T>(A.lv[t].u, i)[c[k]]);
+            }
+            v = 0.25 * s4;
+        }
+        A.F[static_cast<size_t>(i) * A.n_levels + t] = v;
     }
 }
 
@@ -1342,9 +1468,28 @@ int grid_for(mlqmc_ctx* c, int64_t work, int threads = 256)
     return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, static_cast<int64_t>(c->sm_count) * 32)));
 }
 
-int grid_samples(mlqmc_ctx* c, int B)
+// Chunks per sample of the large-level QoI pass (about 65536 cells each).
+int qoi_chunks(const mlqmc_ctx* c, int t)
 {
-    return std::max(1, std::min(B, c->sm_count * 8));
+    const int64_t n = c->p.coarse_cells << t;
+    return static_cast<int>(std::max<int64_t>(1, n * n / 65536));
+}
+
+// Room for the QoI partial sums of Bt[t] samples on every level t <= Lmax
+// (grown outside any capture; a new buffer invalidates captured graphs).
+mlqmc_status ensure_qpart(mlqmc_ctx* c, const int* Bt, int Lmax)
+{
+    int64_t need = 0;
+    for (int t = 0; t <= Lmax; ++t) need = std::max<int64_t>(need, static_cast<int64_t>(Bt[t]) * qoi_chunks(c, t));
+    if (need <= c->qpart_cap) return MLQMC_OK;
+    cudaDeviceSynchronize();
+    cudaFree(c->d_qpart);
+    c->d_qpart = nullptr;
+    c->qpart_cap = 0;
+    ++c->pool_epoch;
+    if (!ok(cudaMalloc(&c->d_qpart, sizeof(double) * static_cast<size_t>(need)))) return MLQMC_ERR_OOM;
+    c->qpart_cap = need;
+    return MLQMC_OK;
 }
 
 mlqmc_status last_error()
@@ -1518,8 +1663,14 @@ mlqmc_status zero_u(mlqmc_ctx* c, int t, int B, cudaStream_t st)
 {
     LevelTag lt(c, t);
     const LevelPool& P = c->pools[t];
-    return ok(cudaMemsetAsync(P.mem + P.off[kU], 0, P.stride[kU] * static_cast<size_t>(B), st)) ? MLQMC_OK
-                                                                                                : MLQMC_ERR_CUDA;
+    const size_t bytes = P.stride[kU] * static_cast<size_t>(B);  // strides are multiples of 256 bytes
+    if (c->graph.in_body) {
+        Timed tm(c, kProfTransfer, st, work_of<double>(static_cast<double>(bytes), 0.0));
+        k_zero16<<<grid_for(c, static_cast<int64_t>(bytes / 16)), 256, 0, st>>>(
+            reinterpret_cast<uint4*>(P.mem + P.off[kU]), bytes / 16);
+        return last_error();
+    }
+    return ok(cudaMemsetAsync(P.mem + P.off[kU], 0, bytes, st)) ? MLQMC_OK : MLQMC_ERR_CUDA;
 }
 
 // V-cycle on level t_top (>= 1) for samples 0..B-1: batched sweeps and
@@ -1760,6 +1911,84 @@ mlqmc_status vcycle_batched(mlqmc_ctx* c, FmgArgs& A, int t_top, int B, bool one
     return last_error();
 }
 
+// Residual norms, flags and the loop decision of one refinement pass on level t.
+template <typename T>
+mlqmc_status norms_and_ctl(mlqmc_ctx* c, const FmgArgs& A, int t, int B, int P, cudaGraphConditionalHandle h,
+                           cudaStream_t st)
+{
+    const double es = sizeof(T), Mc = cells_of(c, t), Fc = faces_of(c, t);
+    {
+        Timed tm(c, kProfReduce, st, work_of<double>(B * (8.0 * Mc + es * (2.0 * Fc + Mc) + 8.0), B * 12.0 * Mc));
+        const int grid = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(B) * P, c->sm_count * 8));
+        kb_resnorm_part<T><<<grid, 256, 0, st>>>(A, t, B, P, c->d_part);
+    }
+    {
+        const int64_t n = c->p.coarse_cells << t;
+        Timed tm(c, kProfReduce, st, work_of<double>(B * (8.0 * P + 12.0), B * 1.0 * P), 2);
+        kb_norm_flags<<<grid_for(c, B), 256, 0, st>>>(c->d_part, P, c->d_norms, c->d_active, B,
+                                                      c->p.refine_rtol * n, c->d_count);
+        k_loop_ctl<<<1, 1, 0, st>>>(h, c->d_count, c->d_iters + t, c->p.refine_max_iter, c->d_status);
+    }
+    return last_error();
+}
+
+// The converged form's loop on level t inside a round capture: the first
+// residual norms and the loop decision on the capture stream, then a
+// conditional WHILE node whose body (captured on the body stream) runs the
+// masked mu0 V-cycles, u64 += e, the next norms and the next decision. Same
+// kernels and order as the host loop, without a host round trip per pass.
+template <typename T>
+mlqmc_status converge_device(mlqmc_ctx* c, FmgArgs& A, int t, int B, int P, cudaStream_t st)
+{
+    mlqmc_ctx::GraphCache& G = c->graph;
+    const int64_t n = c->p.coarse_cells << t;
+    const double es = sizeof(T), Mc = cells_of(c, t);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t nd = 0;
+    if (!ok(cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, &edges, &nd)) ||
+        cs != cudaStreamCaptureStatusActive)
+        return MLQMC_ERR_CUDA;
+    cudaGraphConditionalHandle h{};
+    if (!ok(cudaGraphConditionalHandleCreate(&h, cg, 0, cudaGraphCondAssignDefault))) return MLQMC_ERR_CUDA;
+    if (!ok(cudaMemsetAsync(c->d_count, 0, sizeof(int), st)) ||
+        !ok(cudaMemsetAsync(c->d_iters + t, 0, sizeof(int), st)))
+        return MLQMC_ERR_CUDA;
+    mlqmc_status s = norms_and_ctl<T>(c, A, t, B, P, h, st);
+    if (s != MLQMC_OK) return s;
+    if (!ok(cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, &edges, &nd))) return MLQMC_ERR_CUDA;
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    if (!ok(cudaGraphAddNode(&node, cg, deps, edges, nd, &np))) return MLQMC_ERR_CUDA;
+    cudaStream_t bs = G.body;
+    if (!ok(cudaStreamBeginCaptureToGraph(bs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal)))
+        return MLQMC_ERR_CUDA;
+    G.in_body = true;
+    A.active = c->d_active;
+    s = zero_u(c, t, B, bs);
+    for (int m = 0; m < c->p.mu0 && s == MLQMC_OK; ++m) s = vcycle_batched<T>(c, A, t, B, false, bs);
+    if (s == MLQMC_OK) {
+        Timed tm(c, kProfTransfer, bs, work_of<double>(B * (16.0 + es) * Mc, B * Mc));
+        kb_update64<T><<<grid_for(c, B * n * n), 256, 0, bs>>>(A, t, B);
+    }
+    A.active = nullptr;
+    if (s == MLQMC_OK) s = norms_and_ctl<T>(c, A, t, B, P, h, bs);
+    G.in_body = false;
+    cudaGraph_t body_out = nullptr;
+    const bool ended = ok(cudaStreamEndCapture(bs, &body_out));
+    if (s != MLQMC_OK) return s;
+    if (!ended || !ok(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies)))
+        return MLQMC_ERR_CUDA;
+    return MLQMC_OK;
+}
+
 // Host loop of the converged form on level t (refinement path): per-sample
 // FP64 residual norms (r left in bc), active flags, then mu0 V-cycles on the
 // correction of the active samples and u64 += e, until none is active.
@@ -1778,6 +2007,7 @@ mlqmc_status converge_batched(mlqmc_ctx* c, FmgArgs& A, int t, int B, cudaStream
         if (!ok(cudaMalloc(&c->d_part, sizeof(double) * static_cast<size_t>(B) * P))) return MLQMC_ERR_OOM;
         c->part_cap = static_cast<int64_t>(B) * P;
     }
+    if (c->graph.round_capture) return converge_device<T>(c, A, t, B, P, st);
     for (int it = 0;; ++it) {
         {
             Timed tm(c, kProfReduce, st, work_of<double>(B * (8.0 * Mc + es * (2.0 * Fc + Mc) + 8.0), B * 12.0 * Mc));
@@ -1831,8 +2061,9 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
         const int64_t n = c->p.coarse_cells << t;
         const double es = sizeof(T), Mc = cells_of(c, t), Fc = faces_of(c, t);
         if (refine && MX) {
+            // the residual's 10 operations per cell run in FP32 error-free pairs: FP32 work
             Timed tm(c, kProfTransfer, st,
-                     work_of<double>(B * (es * 0.25 * Mc + 8.0 * Mc + es * (2.0 * Fc + Mc)), B * 10.0 * Mc));
+                     work_of<float>(B * (es * 0.25 * Mc + 8.0 * Mc + es * (2.0 * Fc + Mc)), B * 10.0 * Mc));
             kb_prolong_resid64<<<grid_for(c, B * (n / 2) * (n / 2)), 256, 0, st>>>(A, t, B);
         } else if (refine) {
             {
@@ -1878,10 +2109,21 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
                 if (fuse_update) kb_qoi<T, true, WarpTeam, MX><<<grid, 256, 0, st>>>(A, t, B);
                 else if (refine) kb_qoi<T, true, WarpTeam><<<grid, 256, 0, st>>>(A, t, B);
                 else kb_qoi<T, false, WarpTeam><<<grid, 256, 0, st>>>(A, t, B);
-            } else {
-                if (fuse_update) kb_qoi<T, true, BlockTeam, MX><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
-                else if (refine) kb_qoi<T, true, BlockTeam><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
-                else kb_qoi<T, false, BlockTeam><<<grid_samples(c, B), 256, 0, st>>>(A, t, B);
+            } else {  // chunks of a sample over several CTAs, partial sums added in order
+                const int P = qoi_chunks(c, t);
+                const bool pass = fuse_update || (refine && sizeof(T) == 4) || c->p.qoi == MLQMC_QOI_MEAN;
+                const int grid = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(B) * P, c->sm_count * 8));
+                if (pass) {
+                    if constexpr (MX) {
+                        if (fuse_update) kb_qoi_part<T, true, true><<<grid, 256, 0, st>>>(A, t, B, P, c->d_qpart);
+                        else kb_qoi_part<T, true, false><<<grid, 256, 0, st>>>(A, t, B, P, c->d_qpart);
+                    } else {
+                        if (refine) kb_qoi_part<T, true, false><<<grid, 256, 0, st>>>(A, t, B, P, c->d_qpart);
+                        else kb_qoi_part<T, false, false><<<grid, 256, 0, st>>>(A, t, B, P, c->d_qpart);
+                    }
+                }
+                if (refine) kb_qoi_final<T, true><<<grid_for(c, B), 256, 0, st>>>(A, t, B, P, c->d_qpart);
+                else kb_qoi_final<T, false><<<grid_for(c, B), 256, 0, st>>>(A, t, B, P, c->d_qpart);
             }
         }
         if (d_usol) {
@@ -2082,10 +2324,12 @@ void free_ctx(mlqmc_ctx* c)
     cudaFree(c->d_count);
     cudaFree(c->d_status);
     cudaFree(c->d_queue);
+    cudaFree(c->d_iters);
     for (auto& P : c->pools) cudaFree(P.mem);
     if (c->staged) cudaEventDestroy(c->staged);
     cudaFree(c->d_psi_dense);
     cudaFree(c->d_part);
+    cudaFree(c->d_qpart);
     cudaFree(c->d_c32);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
@@ -2293,6 +2537,8 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
            ok(cudaMallocHost(&c->h_samples, ms * sizeof(SampleDesc))) &&
            ok(cudaMallocHost(&c->h_count, sizeof(int))) && ok(cudaMalloc(&c->d_status, sizeof(int))) &&
            ok(cudaMalloc(&c->d_queue, sizeof(int))) && ok(cudaMemset(c->d_status, 0, sizeof(int))) &&
+           ok(cudaMalloc(&c->d_iters, 2 * MLQMC_MAX_LEVELS * sizeof(int))) &&
+           ok(cudaMemset(c->d_iters, 0, 2 * MLQMC_MAX_LEVELS * sizeof(int))) &&
            ok(cudaEventCreateWithFlags(&c->staged, cudaEventDisableTiming)) &&
            ok(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) &&
            ok(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) &&
@@ -2350,6 +2596,7 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
 }
 
 void graph_free(mlqmc_ctx* c);
+void round_graphs_free(mlqmc_ctx* c);
 
 extern "C" void mlqmc_destroy(mlqmc_ctx* c)
 {
@@ -2379,10 +2626,21 @@ void graph_reset(mlqmc_ctx* c)
     G.key.clear();
 }
 
+void round_graphs_free(mlqmc_ctx* c)
+{
+    mlqmc_ctx::GraphCache& G = c->graph;
+    if (G.stream) cudaStreamSynchronize(G.stream);
+    for (auto& e : G.round_execs) cudaGraphExecDestroy(e.exec);
+    G.round_execs.clear();
+}
+
 void graph_free(mlqmc_ctx* c)
 {
     graph_reset(c);
+    round_graphs_free(c);
     mlqmc_ctx::GraphCache& G = c->graph;
+    if (G.body) cudaStreamDestroy(G.body);
+    G.body = nullptr;
     if (G.stream) cudaStreamDestroy(G.stream);
     if (G.in) cudaEventDestroy(G.in);
     if (G.out) cudaEventDestroy(G.out);
@@ -2482,6 +2740,103 @@ mlqmc_status graph_capture(mlqmc_ctx* c, int count, const int* Bt, int Lmax, dou
     return graph_replay(c, st);
 }
 
+// Everything a round graph needs allocated before its capture (nothing may be
+// allocated while capturing): the level pools and the converged forms'
+// partial-norm buffer.
+mlqmc_status prepare_round(mlqmc_ctx* c, const int* Bt, int Lmax)
+{
+    for (int t = 0; t <= Lmax; ++t) {
+        mlqmc_status s = ensure_pool(c, t, Bt[t]);
+        if (s != MLQMC_OK) return s;
+    }
+    if (c->p.refine_rtol > 0.0) {
+        int64_t need = 0;
+        for (int t = 1; t <= Lmax; ++t) {
+            const int64_t n = c->p.coarse_cells << t;
+            need = std::max<int64_t>(need, static_cast<int64_t>(Bt[t]) * std::max<int64_t>(1, n * n / 8192));
+        }
+        if (need > c->part_cap) {
+            cudaDeviceSynchronize();
+            cudaFree(c->d_part);
+            c->d_part = nullptr;
+            c->part_cap = 0;
+            if (!ok(cudaMalloc(&c->d_part, sizeof(double) * static_cast<size_t>(need)))) return MLQMC_ERR_OOM;
+            c->part_cap = need;
+        }
+    }
+    return MLQMC_OK;
+}
+
+// One call (one chunk, descriptors already staged) as one graph launch:
+// capture run_chunk on the graph stream (converged forms: device-side
+// refinement loops), update the instantiated graph of the same launch shape
+// in place, or instantiate one, and launch it between events of `st`.
+mlqmc_status round_graph(mlqmc_ctx* c, int count, const int* Bt, int Lmax, double* d_sums, double* d_F,
+                         cudaStream_t st)
+{
+    mlqmc_ctx::GraphCache& G = c->graph;
+    if (!G.stream && !ok(cudaStreamCreateWithFlags(&G.stream, cudaStreamNonBlocking))) return MLQMC_ERR_CUDA;
+    if (!G.body && !ok(cudaStreamCreateWithFlags(&G.body, cudaStreamNonBlocking))) return MLQMC_ERR_CUDA;
+    if (!G.in && !ok(cudaEventCreateWithFlags(&G.in, cudaEventDisableTiming))) return MLQMC_ERR_CUDA;
+    if (!G.out && !ok(cudaEventCreateWithFlags(&G.out, cudaEventDisableTiming))) return MLQMC_ERR_CUDA;
+    // launch shape: the levels that run and their smoothers, the outputs asked for
+    std::vector<int32_t> key;
+    key.push_back(Lmax);
+    for (int t = 0; t <= Lmax; ++t) key.push_back(Bt[t] > 0 ? c->smoother[t] : -1);
+    key.push_back(d_F ? 1 : 0);
+    key.push_back(d_sums ? 1 : 0);
+    // an instantiated graph may still be running the previous call
+    if (!ok(cudaStreamSynchronize(G.stream))) return MLQMC_ERR_CUDA;
+    if (!ok(cudaStreamBeginCapture(G.stream, cudaStreamCaptureModeThreadLocal))) return MLQMC_ERR_CUDA;
+    G.capturing = true;
+    G.round_capture = true;
+    mlqmc_status s = run_chunk(c, count, Bt, Lmax, d_sums, d_F, nullptr, G.stream);
+    G.capturing = false;
+    G.round_capture = false;
+    G.in_body = false;
+    cudaGraph_t graph = nullptr;
+    const bool ended = ok(cudaStreamEndCapture(G.stream, &graph));
+    if (s == MLQMC_OK && (!ended || !graph)) s = MLQMC_ERR_CUDA;
+    cudaGraphExec_t exec = nullptr;
+    if (s == MLQMC_OK) {
+        auto it = std::find_if(G.round_execs.begin(), G.round_execs.end(),
+                               [&](const mlqmc_ctx::GraphCache::RoundExec& e) { return e.key == key; });
+        if (it != G.round_execs.end()) {
+            cudaGraphExecUpdateResultInfo info{};
+            if (ok(cudaGraphExecUpdate(it->exec, graph, &info))) {
+                exec = it->exec;
+                ++G.round_updates;
+            } else {
+                cudaGetLastError();
+                cudaGraphExecDestroy(it->exec);
+                G.round_execs.erase(it);
+            }
+        }
+        if (!exec) {
+            if (ok(cudaGraphInstantiate(&exec, graph, 0))) {
+                ++G.round_instantiations;
+                if (G.round_execs.size() >= 16) {
+                    cudaGraphExecDestroy(G.round_execs.front().exec);
+                    G.round_execs.erase(G.round_execs.begin());
+                }
+                G.round_execs.push_back({key, exec});
+            } else {
+                exec = nullptr;
+                s = MLQMC_ERR_CUDA;
+            }
+        }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (s != MLQMC_OK) return s;
+    if (!ok(cudaEventRecord(G.in, st)) || !ok(cudaStreamWaitEvent(G.stream, G.in, 0)) ||
+        !ok(cudaGraphLaunch(exec, G.stream)) || !ok(cudaEventRecord(G.out, G.stream)) ||
+        !ok(cudaStreamWaitEvent(st, G.out, 0)))
+        return MLQMC_ERR_CUDA;
+    ++G.round_launches;
+    return MLQMC_OK;
+}
+
 extern "C" mlqmc_status mlqmc_sample_levels(mlqmc_ctx* c, const mlqmc_work* work, int32_t n_work, double* d_sums,
                                             double* d_F, void* stream)
 {
@@ -2548,6 +2903,10 @@ extern "C" mlqmc_status mlqmc_sample_levels(mlqmc_ctx* c, const mlqmc_work* work
         for (int q = 0; q < count; ++q) all[a + q].canon = q;
         int Bt[MLQMC_MAX_LEVELS], Lmax = -1;
         count_levels(all.data() + a, count, p.n_levels, Bt, &Lmax);
+        {
+            const mlqmc_status qs = ensure_qpart(c, Bt, Lmax);
+            if (qs != MLQMC_OK) return qs;
+        }
         const bool single = a == 0 && b == all.size();
         mlqmc_ctx::GraphCache& G = c->graph;
         if (graphable && single) {
@@ -2560,9 +2919,13 @@ extern "C" mlqmc_status mlqmc_sample_levels(mlqmc_ctx* c, const mlqmc_work* work
             if (same && G.seen == 1 && fits) return graph_capture(c, count, Bt, Lmax, d_sums, d_F, st);
         }
         if (graphable && single) graph_reset(c);
-        mlqmc_status s = stage_samples(c, all.data() + a, count, st);
+        // a call that is not a repeat (an adaptive round): one graph launch
+        const bool round = G.enabled && G.rounds && single && !c->profiling;
+        mlqmc_status s = round ? prepare_round(c, Bt, Lmax) : MLQMC_OK;
+        if (s == MLQMC_OK) s = stage_samples(c, all.data() + a, count, st);
         if (s != MLQMC_OK) return s;
-        s = run_chunk(c, count, Bt, Lmax, d_sums, d_F, nullptr, st);
+        s = round ? round_graph(c, count, Bt, Lmax, d_sums, d_F, st)
+                  : run_chunk(c, count, Bt, Lmax, d_sums, d_F, nullptr, st);
         if (s != MLQMC_OK) return s;
         if (graphable && single) {  // remember the call: the next identical one is captured
             G.key = all;
@@ -2686,6 +3049,8 @@ extern "C" mlqmc_status mlqmc_sample_solution(mlqmc_ctx* c, int32_t level, int32
     if (s != MLQMC_OK) return s;
     int Bt[MLQMC_MAX_LEVELS];
     for (int t = 0; t < c->p.n_levels; ++t) Bt[t] = t <= level ? 1 : 0;
+    s = ensure_qpart(c, Bt, level);
+    if (s != MLQMC_OK) return s;
     s = run_chunk(c, 1, Bt, level, nullptr, nullptr, d_u, st);
     if (s != MLQMC_OK) return s;
     if (!ok(cudaMemcpyAsync(d_F, c->d_F, (level + 1) * sizeof(double), cudaMemcpyDeviceToDevice, st)))
@@ -2924,8 +3289,14 @@ extern "C" mlqmc_status mlqmc_fmg_fields_noalloc(int32_t coarse_cells, int32_t n
 extern "C" mlqmc_status mlqmc_last_iterations(mlqmc_ctx* c, int32_t* out)
 {
     if (!c || !out) return MLQMC_ERR_INVALID_ARG;
+    // device-side loops (round graphs) keep their maxima on the device
+    int dev[MLQMC_MAX_LEVELS] = {};
+    if (!ok(cudaDeviceSynchronize()) ||
+        !ok(cudaMemcpy(dev, c->d_iters + MLQMC_MAX_LEVELS, sizeof(dev), cudaMemcpyDeviceToHost)) ||
+        !ok(cudaMemset(c->d_iters + MLQMC_MAX_LEVELS, 0, sizeof(dev))))
+        return MLQMC_ERR_CUDA;
     for (int t = 0; t < c->p.n_levels; ++t) {
-        out[t] = c->last_iters[t];
+        out[t] = std::max(c->last_iters[t], dev[t]);
         c->last_iters[t] = 0;
     }
     return MLQMC_OK;
@@ -2959,8 +3330,21 @@ extern "C" mlqmc_status mlqmc_set_smoother(mlqmc_ctx* c, int32_t level, int32_t 
 extern "C" mlqmc_status mlqmc_set_graphs(mlqmc_ctx* c, int32_t enable)
 {
     if (!c) return MLQMC_ERR_INVALID_ARG;
-    if (!enable) graph_reset(c);
+    if (!enable) {
+        graph_reset(c);
+        round_graphs_free(c);
+    }
     c->graph.enabled = enable != 0;
+    return MLQMC_OK;
+}
+
+extern "C" mlqmc_status mlqmc_graph_stats(const mlqmc_ctx* c, int64_t* out)
+{
+    if (!c || !out) return MLQMC_ERR_INVALID_ARG;
+    out[0] = c->graph.replays;
+    out[1] = c->graph.round_launches;
+    out[2] = c->graph.round_updates;
+    out[3] = c->graph.round_instantiations;
     return MLQMC_OK;
 }
 

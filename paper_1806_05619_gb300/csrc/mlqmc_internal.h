@@ -132,6 +132,8 @@ struct mlqmc_ctx {
     double* d_norms = nullptr;
     double* d_part = nullptr;  // partial residual sums of the converged forms (samples x chunks), grown on demand
     int64_t part_cap = 0;
+    double* d_qpart = nullptr;  // QoI partial sums of the large levels (samples x chunks), grown on demand
+    int64_t qpart_cap = 0;
     // multi-index runs (mlqmc_sample_mixed): per-sample QoI in work order and
     // a throw-away sums buffer for the inner mlqmc_sample_levels call, the
     // work-item table on the device; grown on demand
@@ -197,6 +199,21 @@ struct mlqmc_ctx {
         int64_t launches = 0;
         int64_t replays = 0;
         bool capturing = false;  // event brackets become graph event-record nodes
+        // Round graphs: a call that is not a repeat (an adaptive round of
+        // Algorithm 1) is captured as one graph, the converged forms'
+        // refinement loops as conditional WHILE nodes driven by the device,
+        // and launched once; an instantiated graph of the same launch shape
+        // is updated in place (cudaGraphExecUpdate) instead of rebuilt.
+        bool rounds = true;
+        bool round_capture = false;   // capturing a round: loops run on the device
+        bool in_body = false;         // capturing a conditional body (no memset nodes)
+        cudaStream_t body = nullptr;  // captures the loop bodies
+        struct RoundExec {
+            std::vector<int32_t> key;
+            cudaGraphExec_t exec;
+        };
+        std::vector<RoundExec> round_execs;
+        int64_t round_launches = 0, round_updates = 0, round_instantiations = 0;
     } graph;
     uint64_t pool_epoch = 0;  // bumped whenever a pool or device buffer is reallocated
 
@@ -204,5 +221,9 @@ struct mlqmc_ctx {
     int host_status = 0;      // deferred status found on the host (converged-form loops)
     int last_iters[MLQMC_MAX_LEVELS] = {};  // extra cycles / refinement steps per level, last converged-form call
     int* d_queue = nullptr;   // work-queue counter
+    // device-side refinement loops (round graphs): per level the current
+    // iteration [t] and the largest iteration reached since the last
+    // mlqmc_last_iterations [MLQMC_MAX_LEVELS + t]
+    int* d_iters = nullptr;
     int64_t launches = 0;
 };
