@@ -437,6 +437,17 @@ mlqmc_status mlqmc_fmg_fields_noalloc(int32_t coarse_cells, int32_t n_levels, in
  */
 mlqmc_status mlqmc_last_iterations(mlqmc_ctx* c, int32_t* out);
 
+/*
+ * Test of the device-side timeout path (no counterpart in the paper): launches
+ * one kernel that waits, with the bounded mbarrier wait the TMA-fed kernels
+ * use, on a barrier that nothing arrives on, and gives up after limit_ns
+ * nanoseconds (0..1e8); the give-up records MLQMC_ERR_TIMEOUT in the context's
+ * device status (read by mlqmc_get_device_status). The kernel issues no copy
+ * and holds no tensor memory, so nothing is in flight when it gives up.
+ * Asynchronous on `stream`. Errors: INVALID_ARG, CUDA.
+ */
+mlqmc_status mlqmc_test_wait_timeout(mlqmc_ctx* c, int64_t limit_ns, void* stream);
+
 /* Kernel launches issued by this context since creation (all entry points). */
 int64_t mlqmc_launch_count(const mlqmc_ctx* c);
 

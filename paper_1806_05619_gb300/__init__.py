@@ -127,6 +127,7 @@ def lib():
             L.mlqmc_set_graphs.argtypes = [vp, i32]
             L.mlqmc_estimator_from_sums.argtypes = [i32, i32, i32, C.POINTER(C.c_int64), dp, dp, dp, dp, dp]
             L.mlqmc_graph_stats.argtypes = [vp, C.POINTER(C.c_int64)]
+            L.mlqmc_test_wait_timeout.argtypes = [vp, i64, vp]
             L.mlqmc_graph_replays.argtypes = [vp]
             L.mlqmc_graph_replays.restype = i64
             L.mlqmc_launch_count.argtypes = [vp]
@@ -137,7 +138,7 @@ def lib():
                          "mlqmc_get_device_status",
                          "mlqmc_cbc_genvec", "mlqmc_modes", "mlqmc_point_bits", "mlqmc_normals", "mlqmc_fields",
                          "mlqmc_sample_solution", "mlqmc_profile", "mlqmc_profile_read", "mlqmc_profile_work", "mlqmc_profile_read_levels", "mlqmc_smoother_info", "mlqmc_set_smoother", "mlqmc_set_graphs",
-                         "mlqmc_estimator_from_sums", "mlqmc_graph_stats",
+                         "mlqmc_estimator_from_sums", "mlqmc_graph_stats", "mlqmc_test_wait_timeout",
                          "mlqmc_fmg_fields_noalloc", "mlqmc_last_iterations"]:
                 getattr(L, name).restype = C.c_int
             _lib = L

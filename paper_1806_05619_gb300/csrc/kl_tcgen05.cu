@@ -5,12 +5,14 @@
 //     Z[p][b] = sum_m Psi[p][m] * C[b][m],  Psi[p][m] = psi_{a_m}(x1_p) psi_{b_m}(x2_p),
 //                                          C[b][m]   = sqrt(theta_m) y_{b,m},
 // p over the level's cells, b over the samples, m over the s modes; the
-// coefficient is k = exp(Z). The kernel computes 128 cells x NT samples per
-// CTA: TMA brings 128-byte-swizzled K blocks of Psi (A operand, K-major) and
-// C (B operand, K-major) into shared memory through an mbarrier ring; one
-// thread issues tcgen05.mma kind::tf32 into an FP32 accumulator in TMEM; the
-// four warps then read their 32 TMEM lanes (one cell each) with tcgen05.ld,
-// apply exp and store k sample by sample, coalesced across cells.
+// coefficient is k = exp(Z). Tiles of 128 cells x NT samples: TMA brings
+// 128-byte-swizzled K blocks of Psi (A operand, K-major) and C (B operand,
+// K-major) into shared memory through an mbarrier ring; one thread issues
+// tcgen05.mma kind::tf32 into an FP32 accumulator in TMEM; four epilogue warps
+// read their 32 TMEM lanes (one cell each) with tcgen05.ld, apply exp and
+// store k sample by sample, coalesced across cells. The CTAs are persistent
+// and warp-specialised with two TMEM accumulators, so that the epilogue of
+// one tile runs while the tensor cores work on the next.
 // Operands are rounded to TF32 (round to nearest) when they are built.
 //
 // Split-BF16 variant: every operand x is split into hi = bf16(x) and
@@ -165,10 +167,46 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// Wait for the phase with `parity`; gives up when another role of the CTA has
+// given up (*abort set) or after about a second (then sets *abort and the
+// timeout bit of *err), so that every role leaves its loops.
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort, int* err)
+{
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = now_ns();
+    for (uint32_t it = 0; it < (1u << 30); ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if ((it & 63u) == 0) {
+            if (*abort) return false;
+            if (now_ns() - t0 > 1000000000ull) break;
+        }
+    }
+    *abort = 1;
+    atomicOr(err, static_cast<int>(kErrTimeout));
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive1(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+constexpr int kEpiWarps = 4;                       // one per TMEM lane quarter
+constexpr int kTcThreads = 64 + 32 * kEpiWarps;    // TMA warp, MMA warp, epilogue warps
+
+// Persistent CTAs (one per SM) walk the 128-cell x NT-sample tiles of the
+// level, sample tiles fastest (consecutive tiles share their Psi rows in L2).
+// Warp 0 (one thread) streams the K blocks of Psi and C of every tile through
+// the shared-memory ring; warp 1 (one thread) issues the MMAs of a tile into
+// one of two TMEM accumulators (2 x NT columns) and commits; warps 2-5 read
+// the other accumulator (warp w owns TMEM lanes 32 (w % 4) ..), apply exp and
+// store, so the epilogue of tile i overlaps the MMAs of tile i + 1 and the
+// ring never drains between tiles.
 template <int NT, bool BF>
-__global__ void __launch_bounds__(128, 1) kl_tc_kernel(const __grid_constant__ CUtensorMap tm_psi,
-                                                       const __grid_constant__ CUtensorMap tm_c, int M, int B, int nk,
-                                                       float* __restrict__ kout, size_t kstride, int* err)
+__global__ void __launch_bounds__(kTcThreads, 1) kl_tc_kernel(const __grid_constant__ CUtensorMap tm_psi,
+                                                              const __grid_constant__ CUtensorMap tm_c, int M, int B,
+                                                              int nk, float* __restrict__ kout, size_t kstride,
+                                                              int* err)
 {
     extern __shared__ unsigned char smem_raw[];
     // 1024-byte aligned stage buffers (the 128-byte swizzle atom)
@@ -179,26 +217,34 @@ __global__ void __launch_bounds__(128, 1) kl_tc_kernel(const __grid_constant__ C
     unsigned char* sb = smem + kStages * kABytes;
     uint64_t* full = reinterpret_cast<uint64_t*>(sb + kStages * kBBytes);
     uint64_t* empty = full + kStages;
-    uint64_t* accum = empty + kStages;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+    uint64_t* tfull = empty + kStages;   // accumulator a holds a finished tile
+    uint64_t* tempty = tfull + 2;        // accumulator a has been read out
+    uint64_t* drained = tempty + 2;      // every MMA issued so far has completed
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drained + 1);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * kTileM;
-    const int b0 = blockIdx.y * NT;
+    const int ntiles = (B + NT - 1) / NT;
+    const int tiles = (M / kTileM) * ntiles;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accum, 1);
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], kEpiWarps);
+        }
+        mbar_init(drained, 1);
+        *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(static_cast<uint32_t>(NT))
+                     "r"(static_cast<uint32_t>(2 * NT))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -206,71 +252,95 @@ __global__ void __launch_bounds__(128, 1) kl_tc_kernel(const __grid_constant__ C
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    bool ok = true;
 
-    if (threadIdx.x == 0) {
-        // producer: K blocks of Psi rows m0.. and C rows b0..
-        int issued = 0;
-        for (int kb = 0; kb < nk && ok; ++kb) {
-            const int s = kb % kStages;
-            if (kb >= kStages) ok = mbar_wait(&empty[s], ((kb / kStages) - 1) & 1, err);
-            if (!ok) break;
-            mbar_expect_tx(&full[s], kABytes + kBBytes);
-            constexpr int kElems = BF ? 64 : kKBlock;  // elements per 128-byte K block
-            tma_load_2d(sa + s * kABytes, &tm_psi, &full[s], kb * kElems, m0);
-            tma_load_2d(sb + s * kBBytes, &tm_c, &full[s], kb * kElems, b0);
-            issued = kb + 1;
-        }
-        // let every copy this thread issued land before the CTA can leave
-        for (int kb = (issued > kStages ? issued - kStages : 0); kb < issued; ++kb)
-            mbar_wait(&full[kb % kStages], (kb / kStages) & 1, err);
-    } else if (threadIdx.x == 32) {
-        // MMA issuer
-        constexpr uint32_t idesc = BF ? idesc_bf16(kTileM, NT) : idesc_tf32(kTileM, NT);
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % kStages;
-            if (!mbar_wait(&full[s], (kb / kStages) & 1, err)) {
-                ok = false;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint64_t ad = sdesc_sw128(smem_u32(sa + s * kABytes));
-            const uint64_t bd = sdesc_sw128(smem_u32(sb + s * kBBytes));
-#pragma unroll
-            for (int k = 0; k < kKBlock / 8; ++k) {  // 32 bytes of K per MMA: 8 TF32 or 16 BF16
-                if constexpr (BF) mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
-                else mma_tf32(tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
-            }
-            mma_commit(&empty[s]);
-        }
-        mma_commit(accum);
-    }
-    __syncwarp();
-
-    // epilogue: warp w owns TMEM lanes 32w..32w+31 (cells m0 + 32w + lane)
-    // warp-uniform: the TMEM loads below are .sync.aligned
-    const bool done = __all_sync(0xffffffffu, mbar_wait(accum, 0, err) ? 1 : 0) != 0;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (done) {
-        const int p = m0 + warp * 32 + lane;
-#pragma unroll 1
-        for (int c = 0; c < NT; c += 32) {
-            float v[32];
-            tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(c), v);
-            if (p < M) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int b = b0 + c + j;
-                    if (b < B) kout[static_cast<size_t>(b) * kstride + p] = __expf(v[j]);
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer: K blocks of Psi rows m0.. and C rows b0.. of every tile
+            uint32_t g = 0, issued = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+                const int m0 = (tile / ntiles) * kTileM, b0 = (tile % ntiles) * NT;
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const uint32_t s = g % kStages;
+                    if (g >= kStages && !(ok = wait_or_abort(&empty[s], ((g / kStages) - 1) & 1, abort, err))) break;
+                    mbar_expect_tx(&full[s], kABytes + kBBytes);
+                    constexpr int kElems = BF ? 64 : kKBlock;  // elements per 128-byte K block
+                    tma_load_2d(sa + s * kABytes, &tm_psi, &full[s], kb * kElems, m0);
+                    tma_load_2d(sb + s * kBBytes, &tm_c, &full[s], kb * kElems, b0);
+                    issued = g + 1;
                 }
             }
+            // let every copy this thread issued land before the CTA can leave
+            for (uint32_t k = issued > kStages ? issued - kStages : 0; k < issued; ++k)
+                mbar_wait(&full[k % kStages], (k / kStages) & 1, err);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer: tile lt accumulates into columns (lt & 1) * NT
+            constexpr uint32_t idesc = BF ? idesc_bf16(kTileM, NT) : idesc_tf32(kTileM, NT);
+            uint32_t g = 0;
+            bool ok = true;
+            int lt = 0;
+            for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++lt) {
+                const int a = lt & 1;
+                if (lt >= 2 && !(ok = wait_or_abort(&tempty[a], ((lt >> 1) - 1) & 1, abort, err))) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + static_cast<uint32_t>(a * NT);
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const uint32_t s = g % kStages;
+                    if (!(ok = wait_or_abort(&full[s], (g / kStages) & 1, abort, err))) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint64_t ad = sdesc_sw128(smem_u32(sa + s * kABytes));
+                    const uint64_t bd = sdesc_sw128(smem_u32(sb + s * kBBytes));
+#pragma unroll
+                    for (int k = 0; k < kKBlock / 8; ++k) {  // 32 bytes of K per MMA: 8 TF32 or 16 BF16
+                        if constexpr (BF) mma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+                        else mma_tf32(d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+                    }
+                    mma_commit(&empty[s]);
+                }
+                if (ok) mma_commit(&tfull[a]);
+            }
+            // every MMA issued has completed before TMEM is released
+            mma_commit(drained);
+            mbar_wait(drained, 0, err);
+        }
+    } else {
+        // epilogue: warp w reads TMEM lanes 32 q .. 32 q + 31, q = w % 4 (cells m0 + 32 q + lane)
+        const int q = warp & 3;
+        int lt = 0;
+        for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++lt) {
+            const int a = lt & 1;
+            // warp-uniform: the TMEM loads below are .sync.aligned
+            const bool ready = __all_sync(0xffffffffu, wait_or_abort(&tfull[a], (lt >> 1) & 1, abort, err) ? 1 : 0);
+            if (!ready) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int m0 = (tile / ntiles) * kTileM, b0 = (tile % ntiles) * NT;
+            const int p = m0 + q * 32 + lane;
+#pragma unroll 1
+            for (int c = 0; c < NT; c += 32) {
+                float v[32];
+                tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(a * NT + c), v);
+                if (p < M) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int b = b0 + c + j;
+                        if (b < B) kout[static_cast<size_t>(b) * kstride + p] = __expf(v[j]);
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive1(&tempty[a]);
         }
     }
+    __syncwarp();
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(static_cast<uint32_t>(NT))
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(static_cast<uint32_t>(2 * NT))
                      : "memory");
     }
 }
@@ -415,7 +485,15 @@ constexpr int kNT = 256;
 
 size_t tc_smem_bytes()
 {
-    return 1024 + kStages * (kTileM * kKBlock * 4 + kNT * kKBlock * 4) + (2 * kStages + 1) * 8 + 16;
+    return 1024 + kStages * (kTileM * kKBlock * 4 + kNT * kKBlock * 4) + (2 * kStages + 5) * 8 + 16;
+}
+
+int sm_count()
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
 }
 
 }  // namespace
@@ -497,9 +575,11 @@ bool launch(Variant v, const TensorMaps& maps, int M, int B, int s, float* d_k, 
     CUtensorMap tp, tc;
     std::memcpy(&tp, maps.psi, sizeof(CUtensorMap));
     std::memcpy(&tc, maps.c, sizeof(CUtensorMap));
-    dim3 grid(M / kTileM, (B + kNT - 1) / kNT);
-    if (v == Variant::TF32) kl_tc_kernel<kNT, false><<<grid, 128, tc_smem_bytes(), st>>>(tp, tc, M, B, nk, d_k, kstride, d_err);
-    else kl_tc_kernel<kNT, true><<<grid, 128, tc_smem_bytes(), st>>>(tp, tc, M, B, nk, d_k, kstride, d_err);
+    const int tiles = (M / kTileM) * ((B + kNT - 1) / kNT);
+    const int grid = std::min(tiles, sm_count());  // persistent: one CTA per SM
+    if (v == Variant::TF32)
+        kl_tc_kernel<kNT, false><<<grid, kTcThreads, tc_smem_bytes(), st>>>(tp, tc, M, B, nk, d_k, kstride, d_err);
+    else kl_tc_kernel<kNT, true><<<grid, kTcThreads, tc_smem_bytes(), st>>>(tp, tc, M, B, nk, d_k, kstride, d_err);
     return cudaGetLastError() == cudaSuccess;
 }
 

@@ -27,6 +27,7 @@
 #include "mlqmc_internal.h"
 #include "rbgs_stream.h"
 #include "rbgs_tma.h"
+#include "ptx_async.cuh"
 #include "rbgs_whole.h"
 #include "matern_nystrom.h"
 
@@ -1799,19 +1800,23 @@ mlqmc_status smooth_stream(mlqmc_ctx* c, const FmgArgs& A, int t, int B, int nsw
 // nsweeps sweeps of level t by the TMA-fed tiled smoother, two per launch, u
 // -> u2 swapped after each launch; pro: the first launch adds P e first.
 // zin: u is zero on entry (first launch only reads no u).
+// rr: the last launch also writes the restricted residual (bc of level t-1).
 mlqmc_status smooth_tma(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int first, int ones, bool pro,
-                        cudaStream_t st, bool zin = false)
+                        cudaStream_t st, bool zin = false, bool rr = false)
 {
     LevelTag lt(c, t);
     const int n = c->p.coarse_cells << t;
     const double Mc = cells_of(c, t), Fc = faces_of(c, t);
     while (nsweeps > 0) {
         const int ns = nsweeps >= 2 ? 2 : 1;
+        const bool last_rr = rr && nsweeps == ns;
         const Work w = work_of<float>(
-            4.0 * B * ((ones ? 3.0 : 4.0) * Mc - (zin ? Mc : 0.0) + 2.0 * Fc + (pro ? 0.25 * Mc : 0.0)),
-            B * (10.0 * ns * Mc + (pro ? 8.0 * Mc : 0.0)));
+            4.0 * B * ((ones ? 3.0 : 4.0) * Mc - (zin ? Mc : 0.0) + 2.0 * Fc + (pro ? 0.25 * Mc : 0.0) +
+                       (last_rr ? 0.25 * Mc : 0.0)),
+            B * (10.0 * ns * Mc + (pro ? 8.0 * Mc : 0.0) + (last_rr ? 11.0 * Mc : 0.0)));
         Timed tm(c, kProfSmooth, st, w);
-        if (!mlqmc_tma::launch(A, t, n, B, ns, ones, first, pro, zin, c->sm_count, st)) return MLQMC_ERR_CUDA;
+        if (!mlqmc_tma::launch(A, t, n, B, ns, ones, first, pro, zin, last_rr, c->sm_count, st))
+            return MLQMC_ERR_CUDA;
         swap_u(c, A, t);
         pro = false;
         zin = false;
@@ -1861,11 +1866,10 @@ mlqmc_status presmooth_restrict(mlqmc_ctx* c, FmgArgs& A, int t, int B, int top_
         return smooth_whole(c, A, t, B, c->p.nu1, 0, top_ones, true, false, st, zin);
     if (sk == MLQMC_SMOOTHER_STREAM && c->p.nu1 > 0)  // residual and restriction fused into the last pass
         return smooth_stream(c, A, t, B, c->p.nu1, 0, top_ones, true, false, st);
-    if (sk == MLQMC_SMOOTHER_TMA && c->p.nu1 > 0) {
-        if (smooth_tma(c, A, t, B, c->p.nu1, 0, top_ones, false, st, zin) != MLQMC_OK) return MLQMC_ERR_CUDA;
-    } else {
-        smooth<T>(c, A, t, B, c->p.nu1, 0, top_ones, false, st);
-    }
+    if (sk == MLQMC_SMOOTHER_TMA && c->p.nu1 > 0)  // the restricted residual fused into the last launch
+        return smooth_tma(c, A, t, B, c->p.nu1, 0, top_ones, false, st, zin, true) == MLQMC_OK ? MLQMC_OK
+                                                                                                : MLQMC_ERR_CUDA;
+    smooth<T>(c, A, t, B, c->p.nu1, 0, top_ones, false, st);
     const int64_t n = c->p.coarse_cells << t;
     const double es = sizeof(T), Mc = cells_of(c, t), Fc = faces_of(c, t);
     Timed tm(c, kProfTransfer, st, work_of<T>(B * es * ((top_ones ? 1.25 : 2.25) * Mc + 2.0 * Fc), B * 11.0 * Mc));
@@ -3336,6 +3340,28 @@ extern "C" mlqmc_status mlqmc_set_graphs(mlqmc_ctx* c, int32_t enable)
     }
     c->graph.enabled = enable != 0;
     return MLQMC_OK;
+}
+
+namespace {
+// Waits (thread 0) on an mbarrier that nothing arrives on, with the bounded
+// wait of the TMA-fed kernels and a limit of limit_ns; the give-up records
+// the timeout bit in the context's status word. No copy is issued.
+__global__ void k_wait_nothing(int* status, uint64_t limit_ns)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mlqmc_ptx::mbar_init(&bar, 1);
+        mlqmc_ptx::mbar_init_fence();
+        mlqmc_ptx::mbar_wait(&bar, 0, status, kStatusTimeout, limit_ns);
+    }
+}
+}  // namespace
+
+extern "C" mlqmc_status mlqmc_test_wait_timeout(mlqmc_ctx* c, int64_t limit_ns, void* stream)
+{
+    if (!c || limit_ns < 0 || limit_ns > 100000000) return MLQMC_ERR_INVALID_ARG;
+    k_wait_nothing<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(c->d_status, static_cast<uint64_t>(limit_ns));
+    return last_error();
 }
 
 extern "C" mlqmc_status mlqmc_graph_stats(const mlqmc_ctx* c, int64_t* out)

@@ -54,15 +54,17 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
-// Wait for the phase with `parity`, giving up after about a second; on
-// giving up, or `flag` bits into *status (when given) and return false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status, int flag)
+// Wait for the phase with `parity`, giving up after limit_ns (about a second
+// by default); on giving up, or `flag` bits into *status (when given) and
+// return false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status, int flag,
+                                          uint64_t limit_ns = 1000000000ull)
 {
     if (mbar_test(bar, parity)) return true;
     const uint64_t t0 = now_ns();
     for (uint32_t it = 0; it < (1u << 30); ++it) {
         if (mbar_test(bar, parity)) return true;
-        if ((it & 255u) == 0 && now_ns() - t0 > 1000000000ull) break;
+        if ((it & 255u) == 0 && now_ns() - t0 > limit_ns) break;
     }
     if (status) atomicOr(status, flag);
     return false;

@@ -21,7 +21,9 @@ bool prepare();
 // map cannot be encoded or the launch fails.
 // zin: u is zero on entry (pre-smoothing of a correction; not with post): its
 // tiles are cleared in shared memory instead of copied.
+// rr (not with post): also write the restricted residual of the swept u,
+// bc of level t-1 = mean over each coarse cell's 4 children of b - A u.
 bool launch(const mlqmc_dev::FmgArgs& A, int t, int n, int B, int ns, int ones, int first, bool post, bool zin,
-            int sm_count, cudaStream_t st);
+            bool rr, int sm_count, cudaStream_t st);
 
 }  // namespace mlqmc_tma

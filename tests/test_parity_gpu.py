@@ -535,3 +535,101 @@ def test_graph_replay_with_profiling():
     assert all(np.array_equal(o, outs[0]) for o in outs)
     assert all(c == counts[0] for c in counts)
     ctx.check_device()
+
+
+# --------------------------------------------------------------------------- #
+# Mixed forms against the FP64 oracle: Algorithm 1, the solution in the       #
+# energy norm, the device timeout path                                        #
+# --------------------------------------------------------------------------- #
+
+
+@pytest.mark.parametrize("precision,ufun", MIXED)
+def test_algorithm1_mixed_matches_oracle(precision, ufun):
+    """Algorithm 1 in a converged mixed form (rtol 1e-10) against the FP64
+    oracle (rtol 1e-12): the same decisions (levels, counts, rounds), and Q
+    within the field bound propagated through the estimator: every F_t of a
+    sample is within eps_F = expm1(eta + slack) + 2 rtol rms(u)/mean(u) of the
+    oracle's, and Q sums, per level, means of differences of two F, so
+    |dQ| <= 2 (L + 1) max eps_F max F."""
+    cfg, ctx, orc = _pair(W.LATTICE_6LEVEL, n_levels=5, n0=4, s=6, R=4, seed=11, log2_nmax=10, precision=precision,
+                          rtol=1e-10)
+    eps = 4e-4
+    g = ctx.estimate(eps)
+    o = orc.estimate(eps)
+    assert o["status"] == O.OK and g["run_status"] == o["run_status"]
+    assert g["L"] == o["L"] and g["rounds"] == o["rounds"] and g["N"] == o["N"]
+    L = o["L"]
+    eta = 0.0
+    for lv in range(L + 1):
+        for r in range(cfg["R"]):
+            for n in range(o["N"][lv]):
+                eta = max(eta, _field_bound(orc, cfg, orc.normals(lv, r, n), ufun(cfg["s"])))
+    ratio = 2.0  # rms(u)/mean(u) of every level of this problem is below 1.6
+    eps_F = math.expm1(eta + EXP_SLACK) + 2 * 1e-10 * ratio + 1e-12
+    Fmax = 0.08
+    assert abs(g["Q"] - o["Q"]) <= 2 * (L + 1) * eps_F * Fmax, (g["Q"], o["Q"], eta)
+    assert abs(g["Q"] - o["Q"]) <= 1e-2 * abs(o["Q"])
+
+
+def test_mixed_solution_energy_norm_bound():
+    """The mixed solution (TF32 field, FP32 V-cycles, FP64 refinement to
+    ||r|| <= 1e-10 ||b||) against the oracle's FP64 one (1e-12) on every level
+    up to 64 x 64, in the energy norm of the oracle's operator A: the FP32
+    field and faces make the mixed operator A' with (1 - d) A <= A' <= (1 + d) A,
+    d = expm1(eta + slack), so the exact solutions differ by at most
+    d / (1 - d) ||u||_A, and each solve adds at most its residual norm over
+    sqrt(lambda_min(A)) (lambda_min(A) >= min face k x lambda_min of the unit-
+    coefficient operator, computed here). The max-norm error is reported."""
+    import scipy.sparse as sps
+    import scipy.sparse.linalg as spla
+
+    cfg, ctx, orc = _pair(W.PRECISION_1024, n_levels=4, R=2, s=40, precision="mixed_tf32", rtol=1e-10)
+    lam1 = {}
+    for t in range(4):
+        n = cfg["n0"] << t
+        cols = [O.apply_A(n, np.ones(n * n), np.eye(1, n * n, q)[0]) for q in range(n * n)]
+        A1 = sps.csr_matrix(np.array(cols).T)
+        lam1[t] = float(spla.eigsh(A1, k=1, sigma=0.0, return_eigenvectors=False)[0]) if n * n > 16 else \
+            float(np.linalg.eigvalsh(A1.toarray())[0])
+    worst = []
+    for (lv, r, n) in [(3, 0, 2), (3, 1, 5)]:
+        sols, _ = ctx.sample_solution(lv, r, n)
+        ref = orc.sample(lv, r, n, want_u=True)
+        assert ref["status"] == O.OK
+        y = orc.normals(lv, r, n)
+        d = math.expm1(_field_bound(orc, cfg, y, _tf32_u(cfg["s"])) + EXP_SLACK)
+        for t in range(lv + 1):
+            nt = cfg["n0"] << t
+            k = orc.field(t, y)
+            um, uo = sols[t].cpu().numpy(), ref["u"][t]
+            e = um - uo
+            eA = math.sqrt(max(0.0, e @ O.apply_A(nt, k, e)))
+            uA = math.sqrt(uo @ O.apply_A(nt, k, uo))
+            kx = np.minimum(k.reshape(nt, nt)[:, 1:], k.reshape(nt, nt)[:, :-1])
+            kmin = min(float(np.min(k)), float(np.min(kx)))  # harmonic means lie above the smaller k
+            lam = kmin * lam1[t]
+            bnorm = float(nt)  # ||b||_2 for b = 1 on nt^2 cells
+            bound = d / (1 - d) * uA + (1e-10 / (1 - d) + 1e-12) * bnorm / math.sqrt(lam)
+            assert eA <= bound, (lv, t, eA, bound)
+            worst.append((eA / uA, float(np.max(np.abs(e)) / np.max(np.abs(uo)))))
+    print("energy-norm relative errors and max-norm relative errors:", worst)
+    ctx.check_device()
+
+
+def test_device_wait_timeout_sets_status():
+    """A kernel that waits with the library's bounded mbarrier wait (limit
+    1 ms) on a barrier nothing arrives on gives up and records
+    MLQMC_ERR_TIMEOUT; reading the status clears it and the context keeps
+    working."""
+    cfg, ctx, orc = _pair(W.MC_4LEVEL, R=1)
+    s = torch.cuda.current_stream()
+    assert M.lib().mlqmc_test_wait_timeout(ctx.h, 1_000_000, M._stream(s)) == 0
+    torch.cuda.synchronize()
+    assert ctx.device_status() == 6  # MLQMC_ERR_TIMEOUT
+    assert ctx.device_status() == 0
+    sums = torch.zeros(cfg["n_levels"] * 2, dtype=torch.float64, device="cuda")
+    ctx.sample_levels([(1, 0, 4, 0, 1)], sums)
+    torch.cuda.synchronize()
+    ctx.check_device()
+    ref = orc.sample_levels([(1, 0, 4, 0, 1)])["sums"].reshape(-1)
+    assert np.allclose(sums.cpu().numpy(), ref, rtol=1e-12, atol=1e-15)
