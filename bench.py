@@ -184,34 +184,37 @@ def bucket_roofline(cell, P):
     return r
 
 
-def sources_digest():
-    """SHA-256 over the library's CUDA/C++ sources and header: DRAM counters
-    taken on other sources no longer describe these kernels."""
-    files = sorted(f for f in glob.glob(os.path.join(ROOT, "paper_1806_05619_gb300", "csrc", "*"))
-                   if f.endswith((".cu", ".cuh", ".h", ".cpp")))
-    files.append(os.path.join(ROOT, "include", "mlqmc.h"))
+def sources_digest(files=None):
+    """SHA-256 over source files (paths relative to the repository; default:
+    the library's CUDA/C++ sources and header): DRAM counters taken on other
+    sources no longer describe these kernels."""
+    if files is None:
+        files = sorted(os.path.relpath(f, ROOT) for f in glob.glob(os.path.join(ROOT, "paper_1806_05619_gb300", "csrc", "*"))
+                       if f.endswith((".cu", ".cuh", ".h", ".cpp")))
+        files.append("include/mlqmc.h")
     h = hashlib.sha256()
     for f in files:
-        h.update(os.path.relpath(f, ROOT).encode())
-        with open(f, "rb") as fh:
+        h.update(f.encode())
+        with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
 def measured_traffic(form, kernel, n):
-    """DRAM bytes per launch of `kernel` on an n x n level in `form`, from the
-    committed record of a one-kernel ncu capture on a small case, scaled to the
-    launch's sample count (profiles/dram_traffic.json; the capture command and
-    the scaling are in profiles/). None when absent or taken on other sources."""
+    """DRAM bytes per sample of a launch of `kernel` on an n x n level in
+    `form`, from the committed record of one-kernel ncu captures on a small
+    case (profiles/dram_traffic.json; the capture commands and the scaling are
+    in profiles/). None when absent or when the kernel's source files differ
+    from those the record was taken on."""
     try:
         with open(TRAFFIC_FILE) as f:
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    if rec.get("sources_sha256") != sources_digest():
-        return None
     e = rec.get("kernels", {}).get(f"{form}|{kernel}|{n}")
-    return e.get("dram_bytes_per_sample") if e else None
+    if not e or sources_digest(e.get("sources")) != e.get("sources_sha256"):
+        return None
+    return e.get("dram_bytes_per_sample")
 
 
 def roofline_report(ctx, levels_prof, P, form, steps, samples_at_level):
@@ -453,18 +456,19 @@ class Step:
         self.sums.zero_()
         self.ctx.sample_levels(self.work, self.sums, stream=stream)
 
-    def profiled(self, stream, flush, K):
-        """K steps with the library's per-launch event brackets (two untimed
-        calls first: the graph is captured again with its brackets); the
-        per-(kind, level) times and work; plain replay restored afterwards."""
+    def profiled(self, stream, flush, K, warm=2, restore=True):
+        """K steps with the library's per-launch event brackets (`warm`
+        untimed calls first: the graph is captured again with its brackets);
+        the per-(kind, level) times and work; plain replay restored afterwards
+        when `restore`."""
         self.ctx.profile(True)
-        for _ in range(2):
+        for _ in range(warm):
             self(stream)
         self.ctx.profile(True)
         ms = timed_steps(lambda: self(stream), K, stream, flush)
         prof = self.ctx.profile_read_levels()
         self.ctx.profile(False)
-        for _ in range(2):
+        for _ in range(2 if restore else 0):
             self(stream)
         return prof, float(np.mean(ms))
 
@@ -556,6 +560,7 @@ def run_ours(args):
     e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": ns * 32, "d2h_bytes_per_step": nl * R * 2 * 8}
     details["estimate_mixed"] = {"Q": est["Q"], "varQ": est["varQ"]}
     smoothers = [k for k, _ in step.ctx.smoother_info()]
+    details["autotuner"] = {"smoothers": step.ctx.smoother_info(), "schedule": step.ctx.schedule_info()}
     create_mixed = step.create_s
     step.close()
     del step
@@ -578,6 +583,8 @@ def run_ours(args):
         host_sums.copy_(s64.sums)
         e64 = M.estimator_from_sums(Nl, host_sums.numpy().reshape(nl, R, 2), R, reuse=cfg["reuse"])
         details["estimate_fp64"] = {"Q": e64["Q"], "varQ": e64["varQ"]}
+        prof64, _ = s64.profiled(stream, flush, 1, warm=0, restore=False)
+        _, details["roofline_table_fp64"] = roofline_report(s64.ctx, prof64, P, "fp64", 1, samples_reaching(c64))
         fp64["speedup_mixed"] = round((t64 / args.fp64_steps) / (tot_ms / args.steps), 2)
         s64.close()
         del s64
@@ -627,6 +634,8 @@ def make_line(args, world, value, tot_ms, ns, smoothers, create_s, launches, rep
         "clocks": clocks, "cpu_baseline": cpu, "fp64": fp64,
         "time_to_eps": ({"eps": tte["eps"], "mixed_s": round(tte["mixed_tf32"]["seconds"], 3),
                          "fp64_s": round(tte["fp64"]["seconds"], 3) if "fp64" in tte else None,
+                         "mixed_round_graphs_s": (round(tte["mixed_tf32_round_graphs"]["seconds"], 3)
+                                                  if "mixed_tf32_round_graphs" in tte else None),
                          "mixed_L": tte["mixed_tf32"]["L"], "mixed_rounds": tte["mixed_tf32"]["rounds"]}
                         if tte else None),
     }
@@ -641,13 +650,17 @@ def run_tte9(M, cfg, eps, dev):
     c = dict(cfg)
     c["log2_nmax"] = 14
     genvec, _ = M.cbc_genvec(c["s"], c["log2_nmax"])
-    for prec in ("mixed_tf32", "fp64"):
+    # the default policy launches a fixed-cycle round kernel by kernel; the
+    # third run forces one graph launch per round for comparison
+    for name, prec, rounds in (("mixed_tf32", "mixed_tf32", "converged"), ("fp64", "fp64", "converged"),
+                               ("mixed_tf32_round_graphs", "mixed_tf32", "on")):
         c["precision"] = prec
         ctx = M.Context.from_config(c, genvec=genvec, max_samples=1 << 16)
+        ctx.set_round_graphs(rounds)
         r = ctx.estimate(eps)
-        out[prec] = {"seconds": r["wall_seconds"], "gpu_seconds": r["gpu_seconds"], "Q": r["Q"],
+        out[name] = {"seconds": r["wall_seconds"], "gpu_seconds": r["gpu_seconds"], "Q": r["Q"],
                      "rmse_bound": float(np.sqrt(r["varQ"] + r["bias"] ** 2)), "L": r["L"], "rounds": r["rounds"],
-                     "N": r["N"][:r["L"] + 1], "run_status": r["run_status"]}
+                     "N": r["N"][:r["L"] + 1], "run_status": r["run_status"], "graphs": ctx.graph_stats()}
         ctx.close()
         del ctx
         torch.cuda.empty_cache()
@@ -787,14 +800,17 @@ def run_time_to_eps(M):
     cfg["log2_nmax"] = 12
     genvec, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
     out = {}
-    variants = [("mixed_tf32", "mixed_tf32", True, False), ("fp64", "fp64", True, False),
-                ("mixed_tf32_no_reuse", "mixed_tf32", False, False), ("mixed_tf32_batched", "mixed_tf32", True, True)]
+    variants = [("mixed_tf32", "mixed_tf32", True, False, True), ("fp64", "fp64", True, False, True),
+                ("mixed_tf32_no_reuse", "mixed_tf32", False, False, True),
+                ("mixed_tf32_batched", "mixed_tf32", True, True, True),
+                ("mixed_tf32_launch_by_launch", "mixed_tf32", True, False, False)]
     eps_list = cfg["eps"] + [3e-4, 1e-4]
-    for name, prec, reuse, batched in variants:
+    for name, prec, reuse, batched, graphs in variants:
         c = dict(cfg)
         c["precision"] = prec
         c["reuse"] = reuse
         ctx = M.Context.from_config(c, genvec=genvec, max_samples=1 << 17)
+        ctx.set_graphs(graphs)
         rows = []
         for eps in eps_list:
             r = ctx.estimate(eps, batched=batched)

@@ -474,6 +474,25 @@ mlqmc_status mlqmc_smoother_info(const mlqmc_ctx* c, int32_t* kind, double* tune
 mlqmc_status mlqmc_set_smoother(mlqmc_ctx* c, int32_t level, int32_t kind);
 
 /*
+ * Batch-size schedule of the autotuner (mixed forms). The sample count of a
+ * level varies from call to call (Algorithm 1's rounds start at one point
+ * per shift and double), and the best kernel shape changes with it. A call
+ * with fewer than 256 samples on a level uses that level's small-batch
+ * choices, tuned on 64 samples; larger calls use the choices of
+ * mlqmc_smoother_info (tuned on 1024). For the tensor-core KL contraction the
+ * autotuner also times tiles of 128 and of 256 samples per CTA on up to
+ * 262,144 of the level's cells, for 64 and for 256 samples, and keeps the
+ * faster width per class. mlqmc_set_smoother forces a smoother for every
+ * batch size. Outputs (host, any may be NULL): smoother_small (n_levels
+ * int32, MLQMC_SMOOTHER_*; 0 for level 0); tuned_small_ms (n_levels x 5, as
+ * tuned_ms); kl_nt (n_levels x 2: [level][small, large] samples per tile; 0
+ * where the level has no tensor-core contraction); tuned_kl_ms (n_levels x 2
+ * x 2: [level][class][128, 256] milliseconds).
+ */
+mlqmc_status mlqmc_schedule_info(const mlqmc_ctx* c, int32_t* smoother_small, double* tuned_small_ms, int32_t* kl_nt,
+                                 double* tuned_kl_ms);
+
+/*
  * Graph replay (on by default). In the fixed-cycle forms (refine_rtol = 0) a
  * call of mlqmc_sample_levels that fits one chunk and repeats the previous
  * call exactly (same ranked samples, same d_sums and d_F, no pool
@@ -491,10 +510,11 @@ mlqmc_status mlqmc_set_graphs(mlqmc_ctx* c, int32_t enable);
 int64_t mlqmc_graph_replays(const mlqmc_ctx* c);
 
 /*
- * Round graphs (on with graph replay). A call of mlqmc_sample_levels that is
+ * Round graphs (with graph replay on). A call of mlqmc_sample_levels that is
  * not a repeat -- one adaptive round of Algorithm 1 (Sec. 3.3), whose sample
  * counts differ from the previous round's -- runs as one graph launch when
- * it fits one chunk and profiling is off: the descriptors are uploaded by one
+ * round graphs apply to it (mlqmc_set_round_graphs), it fits one chunk and
+ * profiling is off: the descriptors are uploaded by one
  * copy, then the call's kernels are captured into a graph, an instantiated
  * graph of the same launch shape (the levels that run, their smoothers, the
  * outputs asked for) is updated in place (cudaGraphExecUpdate) or a new one
@@ -509,6 +529,16 @@ int64_t mlqmc_graph_replays(const mlqmc_ctx* c);
  * launches, in-place updates, instantiations since creation.
  */
 mlqmc_status mlqmc_graph_stats(const mlqmc_ctx* c, int64_t* out);
+
+/*
+ * Which calls run as round graphs: mode 0 none, 1 every call that is not a
+ * repeat, 2 (the default) such calls of the converged forms (refine_rtol > 0),
+ * where the refinement loops then run on the device without a host round
+ * trip per pass. A one-off call of a fixed-cycle form has no such loop: there
+ * the capture and update of its graph (host work while the GPU waits) cost
+ * more than launching its kernels one by one. Errors: INVALID_ARG.
+ */
+mlqmc_status mlqmc_set_round_graphs(mlqmc_ctx* c, int32_t mode);
 
 /*
  * Per-kernel device timing of mlqmc_sample_levels (off by default). With

@@ -124,9 +124,11 @@ def lib():
             L.mlqmc_profile_read_levels.argtypes = [vp, dp, C.POINTER(C.c_int64), dp, dp, dp, dp]
             L.mlqmc_smoother_info.argtypes = [vp, C.POINTER(C.c_int32), dp]
             L.mlqmc_set_smoother.argtypes = [vp, i32, i32]
+            L.mlqmc_schedule_info.argtypes = [vp, C.POINTER(C.c_int32), dp, C.POINTER(C.c_int32), dp]
             L.mlqmc_set_graphs.argtypes = [vp, i32]
             L.mlqmc_estimator_from_sums.argtypes = [i32, i32, i32, C.POINTER(C.c_int64), dp, dp, dp, dp, dp]
             L.mlqmc_graph_stats.argtypes = [vp, C.POINTER(C.c_int64)]
+            L.mlqmc_set_round_graphs.argtypes = [vp, i32]
             L.mlqmc_test_wait_timeout.argtypes = [vp, i64, vp]
             L.mlqmc_graph_replays.argtypes = [vp]
             L.mlqmc_graph_replays.restype = i64
@@ -137,8 +139,8 @@ def lib():
                          "mlqmc_nystrom_modes",
                          "mlqmc_get_device_status",
                          "mlqmc_cbc_genvec", "mlqmc_modes", "mlqmc_point_bits", "mlqmc_normals", "mlqmc_fields",
-                         "mlqmc_sample_solution", "mlqmc_profile", "mlqmc_profile_read", "mlqmc_profile_work", "mlqmc_profile_read_levels", "mlqmc_smoother_info", "mlqmc_set_smoother", "mlqmc_set_graphs",
-                         "mlqmc_estimator_from_sums", "mlqmc_graph_stats", "mlqmc_test_wait_timeout",
+                         "mlqmc_sample_solution", "mlqmc_profile", "mlqmc_profile_read", "mlqmc_profile_work", "mlqmc_profile_read_levels", "mlqmc_smoother_info", "mlqmc_set_smoother", "mlqmc_schedule_info", "mlqmc_set_graphs",
+                         "mlqmc_estimator_from_sums", "mlqmc_graph_stats", "mlqmc_set_round_graphs", "mlqmc_test_wait_timeout",
                          "mlqmc_fmg_fields_noalloc", "mlqmc_last_iterations"]:
                 getattr(L, name).restype = C.c_int
             _lib = L
@@ -426,6 +428,24 @@ class Context:
         return [(self.SMOOTHERS[kind[t]], {self.SMOOTHERS[k]: float(ms[t, k]) for k in range(nk) if ms[t, k] > 0})
                 for t in range(self.n_levels)]
 
+    def schedule_info(self):
+        """The autotuner's batch-size schedule: per level the small-batch smoother
+        (with its tuning times) and the KL tile width (samples per tile) for
+        small and large batches (with the timings of widths 128 and 256)."""
+        nl, nk = self.n_levels, len(self.SMOOTHERS)
+        ss = (C.c_int32 * nl)()
+        sms = np.zeros(nl * nk)
+        nt = (C.c_int32 * (2 * nl))()
+        kms = np.zeros(nl * 4)
+        dpp = C.POINTER(C.c_double)
+        _check(lib().mlqmc_schedule_info(self.h, ss, sms.ctypes.data_as(dpp), nt, kms.ctypes.data_as(dpp)),
+               "mlqmc_schedule_info")
+        sms, kms = sms.reshape(nl, nk), kms.reshape(nl, 2, 2)
+        return [{"smoother_small": self.SMOOTHERS[ss[t]],
+                 "small_ms": {self.SMOOTHERS[k]: float(sms[t, k]) for k in range(nk) if sms[t, k] > 0},
+                 "kl_nt": [nt[2 * t], nt[2 * t + 1]],
+                 "kl_ms": [[float(kms[t, c_, k]) for k in range(2)] for c_ in range(2)]} for t in range(nl)]
+
     def set_smoother(self, level: int, name: str):
         """Force smoother `name` ("tile", "stream", "tma" or "whole") on `level` for later calls."""
         _check(lib().mlqmc_set_smoother(self.h, int(level), self.SMOOTHERS.index(name)), "mlqmc_set_smoother")
@@ -436,6 +456,13 @@ class Context:
 
     def graph_replays(self) -> int:
         return int(lib().mlqmc_graph_replays(self.h))
+
+    ROUND_GRAPHS = {"off": 0, "on": 1, "converged": 2}
+
+    def set_round_graphs(self, mode: str):
+        """Which one-off calls run as one graph launch: "off", "on", or "converged"
+        (the default: calls of the converged forms only)."""
+        _check(lib().mlqmc_set_round_graphs(self.h, self.ROUND_GRAPHS[mode]), "mlqmc_set_round_graphs")
 
     def graph_stats(self):
         """{"replays", "round_launches", "round_updates", "round_instantiations"} since creation."""

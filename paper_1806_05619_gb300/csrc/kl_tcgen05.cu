@@ -483,9 +483,10 @@ bool encode_2d(CUtensorMap* map, const void* base, uint64_t rows, uint64_t kdim,
 
 constexpr int kNT = 256;
 
-size_t tc_smem_bytes()
+size_t tc_smem_bytes(int nt = kNT)
 {
-    return 1024 + kStages * (kTileM * kKBlock * 4 + kNT * kKBlock * 4) + (2 * kStages + 5) * 8 + 16;
+    return 1024 + kStages * (kTileM * kKBlock * 4 + static_cast<size_t>(nt) * kKBlock * 4) + (2 * kStages + 5) * 8 +
+           16;
 }
 
 int sm_count()
@@ -556,30 +557,41 @@ bool make_maps(Variant v, const void* d_psi, int M, const void* d_c, int rows_c,
     const bool bf = v == Variant::BF16X3;
     static_assert(sizeof(TensorMaps::psi) >= sizeof(CUtensorMap), "map storage");
     return encode_2d(reinterpret_cast<CUtensorMap*>(maps->psi), d_psi, static_cast<uint64_t>(M), kd, kTileM, bf) &&
-           encode_2d(reinterpret_cast<CUtensorMap*>(maps->c), d_c, static_cast<uint64_t>(rows_c), kd, kNT, bf);
+           encode_2d(reinterpret_cast<CUtensorMap*>(maps->c), d_c, static_cast<uint64_t>(rows_c), kd, kNT, bf) &&
+           encode_2d(reinterpret_cast<CUtensorMap*>(maps->c128), d_c, static_cast<uint64_t>(rows_c), kd, 128, bf);
 }
 
 bool prepare_kernel()
 {
-    const int b = static_cast<int>(tc_smem_bytes());
+    const int b = static_cast<int>(tc_smem_bytes(kNT)), b128 = static_cast<int>(tc_smem_bytes(128));
     return cudaFuncSetAttribute(kl_tc_kernel<kNT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) ==
                cudaSuccess &&
-           cudaFuncSetAttribute(kl_tc_kernel<kNT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) == cudaSuccess;
+           cudaFuncSetAttribute(kl_tc_kernel<kNT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(kl_tc_kernel<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b128) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(kl_tc_kernel<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b128) ==
+               cudaSuccess;
 }
 
 bool launch(Variant v, const TensorMaps& maps, int M, int B, int s, float* d_k, size_t kstride, int* d_err,
-            cudaStream_t st)
+            cudaStream_t st, int nt)
 {
-    if (M % kTileM != 0 || B <= 0) return false;
+    if (M % kTileM != 0 || B <= 0 || (nt != 128 && nt != kNT)) return false;
     const int nk = static_cast<int>(row_bytes(v, s) / 128);  // 128-byte K blocks
     CUtensorMap tp, tc;
     std::memcpy(&tp, maps.psi, sizeof(CUtensorMap));
-    std::memcpy(&tc, maps.c, sizeof(CUtensorMap));
-    const int tiles = (M / kTileM) * ((B + kNT - 1) / kNT);
+    std::memcpy(&tc, nt == 128 ? maps.c128 : maps.c, sizeof(CUtensorMap));
+    const int tiles = (M / kTileM) * ((B + nt - 1) / nt);
     const int grid = std::min(tiles, sm_count());  // persistent: one CTA per SM
-    if (v == Variant::TF32)
-        kl_tc_kernel<kNT, false><<<grid, kTcThreads, tc_smem_bytes(), st>>>(tp, tc, M, B, nk, d_k, kstride, d_err);
-    else kl_tc_kernel<kNT, true><<<grid, kTcThreads, tc_smem_bytes(), st>>>(tp, tc, M, B, nk, d_k, kstride, d_err);
+    const size_t smem = tc_smem_bytes(nt);
+    if (nt == 128) {
+        if (v == Variant::TF32) kl_tc_kernel<128, false><<<grid, kTcThreads, smem, st>>>(tp, tc, M, B, nk, d_k, kstride, d_err);
+        else kl_tc_kernel<128, true><<<grid, kTcThreads, smem, st>>>(tp, tc, M, B, nk, d_k, kstride, d_err);
+    } else {
+        if (v == Variant::TF32) kl_tc_kernel<kNT, false><<<grid, kTcThreads, smem, st>>>(tp, tc, M, B, nk, d_k, kstride, d_err);
+        else kl_tc_kernel<kNT, true><<<grid, kTcThreads, smem, st>>>(tp, tc, M, B, nk, d_k, kstride, d_err);
+    }
     return cudaGetLastError() == cudaSuccess;
 }
 

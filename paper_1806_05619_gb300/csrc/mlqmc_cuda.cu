@@ -901,20 +901,30 @@ __global__ void kb_prolong_resid64(FmgArgs A, int t, int B)
                 const float d = E[py + sy + 1][px + sx + 1];
                 U[fy + 1][fx + 1] = fmaf(0.5625f, a, fmaf(0.1875f, bx + cy, 0.0625f * d));
             }
-        // residual of each quad cell: every input an FP32 number (pairs, as resid_f32x2 states)
+        // residual of each quad cell: every input an FP32 number (pairs, as resid_f32x2 states);
+        // a quad row's two cells are adjacent: their faces are loaded and their
+        // u64 and b written as pairs (16- and 8-byte accesses; i1 even, pitches even)
 #pragma unroll
-        for (int qy = 0; qy < 2; ++qy)
+        for (int qy = 0; qy < 2; ++qy) {
+            const int i1 = 2 * I1, i2 = 2 * I2 + qy;
+            const int p = i2 * n + i1;
+            const float* kxr = L.kx + i2 * kx_pitch(n) + i1;
+            const float2 kx01 = *reinterpret_cast<const float2*>(kxr);
+            const float kx2 = kxr[2];
+            const float2 kyn = *reinterpret_cast<const float2*>(L.ky + i2 * n + i1);
+            const float2 kys = *reinterpret_cast<const float2*>(L.ky + (i2 + 1) * n + i1);
+            float r[2];
 #pragma unroll
             for (int qx = 0; qx < 2; ++qx) {
-                const int i1 = 2 * I1 + qx, i2 = 2 * I2 + qy;
-                const int p = i2 * n + i1;
                 const float up = U[qy + 1][qx + 1];
                 const float uv[4] = {U[qy + 1][qx], U[qy + 1][qx + 2], U[qy][qx + 1], U[qy + 2][qx + 1]};
-                const float* kx = L.kx + i2 * kx_pitch(n);
-                const float kv[4] = {kx[i1], kx[i1 + 1], L.ky[i2 * n + i1], L.ky[(i2 + 1) * n + i1]};
-                L.u64[p] = widen(up);
-                L.bc[p] = resid_f32x2(kv, up, uv, ih2);
+                const float kv[4] = {qx ? kx01.y : kx01.x, qx ? kx2 : kx01.y, qx ? kyn.y : kyn.x,
+                                     qx ? kys.y : kys.x};
+                r[qx] = resid_f32x2(kv, up, uv, ih2);
             }
+            *reinterpret_cast<double2*>(L.u64 + p) = make_double2(widen(U[qy + 1][1]), widen(U[qy + 1][2]));
+            *reinterpret_cast<float2*>(L.bc + p) = make_float2(r[0], r[1]);
+        }
     }
 }
 
@@ -1551,18 +1561,17 @@ mlqmc_status launch_points(mlqmc_ctx* c, const SampleDesc* d_s, int count, doubl
     return last_error();
 }
 
-// Smoother of level t's sweeps in working precision T (FP64: kb_gs).
-template <typename T>
-int smoother_of(const mlqmc_ctx* c, int t)
+// Smoother of level t's sweeps for a call with B samples on the level (the
+// autotuner's batch-size schedule).
+int smoother_for(const mlqmc_ctx* c, int t, int B)
 {
-    return c->smoother[t];
+    return B < kSmallBatch ? c->smoother_small[t] : c->smoother[t];
 }
 
-// True when level t's FP32 sweeps run on the wavefront smoother (rbgs_stream.cu).
-template <typename T>
-bool streams(const mlqmc_ctx* c, int t)
+// Samples per tile of the tensor-core KL of level t for B samples.
+int kl_nt_for(const mlqmc_ctx* c, int t, int B)
 {
-    return smoother_of<T>(c, t) == MLQMC_SMOOTHER_STREAM;
+    return c->kl_nt[t][B < kSmallBatch ? 0 : 1];
 }
 
 // Whether smoother kind k can run level t in the context's form (FP64: kb_gs
@@ -1605,8 +1614,7 @@ mlqmc_status synth_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cudaStr
             w.ftc = 2.0 * M * c->p.n_modes * B;
             Timed tm(c, kProfKlTc, st, w);
             if (!mlqmc_kl::launch(c->kl_variant, c->kl_maps[t], static_cast<int>(n * n), B, c->p.n_modes, k,
-                                  P.stride[kK] / sizeof(float),
-                                  c->d_status, st))
+                                  P.stride[kK] / sizeof(float), c->d_status, st, kl_nt_for(c, t, B)))
                 return MLQMC_ERR_CUDA;
         }
     }
@@ -1642,7 +1650,7 @@ mlqmc_status synth_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cudaStr
         if (sizeof(T) == 4 && n % 4 == 0) kb_faces4<<<grid_for(c, B * n * n / 4), 256, 0, st>>>(A, t, B);
         else kb_faces<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
     }
-    if (t > 0 && (sizeof(T) == 8 || smoother_of<T>(c, t) <= MLQMC_SMOOTHER_TILE)) {  // 1/D: FP64 sweeps, tiles
+    if (t > 0 && (sizeof(T) == 8 || smoother_for(c, t, B) <= MLQMC_SMOOTHER_TILE)) {  // 1/D: FP64 sweeps, tiles
         Timed tm(c, kProfSynth, st, work_of<T>(B * es * (2.0 * Fc + Mc), B * 5.0 * Mc));
         kb_idiag<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
     }
@@ -1723,10 +1731,10 @@ bool tile_attrs()
 // launches per sweep (FP64 is arithmetic-bound on GB300 and the tiles' halo
 // updates would add work).
 template <typename T>
-int tile_side(const mlqmc_ctx* c, int t)
+int tile_side(const mlqmc_ctx* c, int t, int B)
 {
     const int64_t n = c->p.coarse_cells << t;
-    if (sizeof(T) == 8 || c->smoother[t] != MLQMC_SMOOTHER_TILE) return 0;
+    if (sizeof(T) == 8 || smoother_for(c, t, B) != MLQMC_SMOOTHER_TILE) return 0;
     return n >= 32 && n % 32 == 0 ? 32 : (n == 16 ? 16 : (n == 8 ? 8 : 0));
 }
 
@@ -1736,7 +1744,7 @@ void smooth(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int first, int 
 {
     LevelTag lt(c, t);
     const int64_t n = c->p.coarse_cells << t;
-    const int tile = tile_side<T>(c, t);
+    const int tile = tile_side<T>(c, t, B);
     const double es = sizeof(T), Mc = cells_of(c, t), Fc = faces_of(c, t);
     const Work pro_work = work_of<T>(B * es * (0.25 * Mc + 2.0 * Mc), B * 8.0 * Mc);
     if (pro && tile == 0) {
@@ -1801,6 +1809,8 @@ mlqmc_status smooth_stream(mlqmc_ctx* c, const FmgArgs& A, int t, int B, int nsw
 // -> u2 swapped after each launch; pro: the first launch adds P e first.
 // zin: u is zero on entry (first launch only reads no u).
 // rr: the last launch also writes the restricted residual (bc of level t-1).
+// Bytes per cell: u in, u2 out, b in (unless ones), kx and ky in, e in (pro, a
+// quarter-size array) and the restricted residual out (rr, a quarter).
 mlqmc_status smooth_tma(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int first, int ones, bool pro,
                         cudaStream_t st, bool zin = false, bool rr = false)
 {
@@ -1811,7 +1821,7 @@ mlqmc_status smooth_tma(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int
         const int ns = nsweeps >= 2 ? 2 : 1;
         const bool last_rr = rr && nsweeps == ns;
         const Work w = work_of<float>(
-            4.0 * B * ((ones ? 3.0 : 4.0) * Mc - (zin ? Mc : 0.0) + 2.0 * Fc + (pro ? 0.25 * Mc : 0.0) +
+            4.0 * B * ((ones ? 2.0 : 3.0) * Mc - (zin ? Mc : 0.0) + 2.0 * Fc + (pro ? 0.25 * Mc : 0.0) +
                        (last_rr ? 0.25 * Mc : 0.0)),
             B * (10.0 * ns * Mc + (pro ? 8.0 * Mc : 0.0) + (last_rr ? 11.0 * Mc : 0.0)));
         Timed tm(c, kProfSmooth, st, w);
@@ -1847,9 +1857,9 @@ mlqmc_status smooth_whole(mlqmc_ctx* c, const FmgArgs& A, int t, int B, int nswe
 // Whether the pre-smoother of level t starts a correction from zero without
 // reading u (so the V-cycle need not clear u first).
 template <typename T>
-bool zero_in_smoother(const mlqmc_ctx* c, int t)
+bool zero_in_smoother(const mlqmc_ctx* c, int t, int B)
 {
-    const int sk = smoother_of<T>(c, t);
+    const int sk = smoother_for(c, t, B);
     return c->p.nu1 > 0 && (sk == MLQMC_SMOOTHER_WHOLE || sk == MLQMC_SMOOTHER_TMA);
 }
 
@@ -1861,7 +1871,7 @@ mlqmc_status presmooth_restrict(mlqmc_ctx* c, FmgArgs& A, int t, int B, int top_
                                 bool zin = false)
 {
     LevelTag lt(c, t);
-    const int sk = smoother_of<T>(c, t);
+    const int sk = smoother_for(c, t, B);
     if (sk == MLQMC_SMOOTHER_WHOLE && c->p.nu1 > 0)  // residual and restriction in the same pass
         return smooth_whole(c, A, t, B, c->p.nu1, 0, top_ones, true, false, st, zin);
     if (sk == MLQMC_SMOOTHER_STREAM && c->p.nu1 > 0)  // residual and restriction fused into the last pass
@@ -1882,7 +1892,7 @@ template <typename T>
 mlqmc_status correct_postsmooth(mlqmc_ctx* c, FmgArgs& A, int t, int B, int top_ones, cudaStream_t st)
 {
     LevelTag lt(c, t);
-    const int sk = smoother_of<T>(c, t);
+    const int sk = smoother_for(c, t, B);
     if (sk == MLQMC_SMOOTHER_WHOLE && c->p.nu2 > 0)  // the correction in the same pass
         return smooth_whole(c, A, t, B, c->p.nu2, 1, top_ones, false, true, st);
     if (sk == MLQMC_SMOOTHER_STREAM && c->p.nu2 > 0)  // the correction fused into the first pass
@@ -1898,7 +1908,7 @@ mlqmc_status vcycle_batched(mlqmc_ctx* c, FmgArgs& A, int t_top, int B, bool one
     for (int t = t_top; t >= 1; --t) {
         const int top_ones = (t == t_top && ones) ? 1 : 0;
         // a correction level starts from zero: cleared here, or by its smoother
-        const bool zin = t < t_top && zero_in_smoother<T>(c, t);
+        const bool zin = t < t_top && zero_in_smoother<T>(c, t, B);
         if (t < t_top && !zin && zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
         if (presmooth_restrict<T>(c, A, t, B, top_ones, st, zin) != MLQMC_OK) return MLQMC_ERR_CUDA;
     }
@@ -2152,6 +2162,8 @@ void default_smoothers(mlqmc_ctx* c)
         else if (smoother_fits(c, MLQMC_SMOOTHER_STREAM, t)) c->smoother[t] = MLQMC_SMOOTHER_STREAM;
         else if (smoother_fits(c, MLQMC_SMOOTHER_TMA, t)) c->smoother[t] = MLQMC_SMOOTHER_TMA;
         else c->smoother[t] = MLQMC_SMOOTHER_TILE;
+        c->smoother_small[t] = c->smoother[t];
+        c->kl_nt[t][0] = c->kl_nt[t][1] = mlqmc_kl::tile_samples();
     }
 }
 
@@ -2174,12 +2186,14 @@ mlqmc_status tune_smoothers(mlqmc_ctx* c)
         return MLQMC_ERR_CUDA;
     mlqmc_status res = MLQMC_OK;
     const int all[4] = {MLQMC_SMOOTHER_GS, MLQMC_SMOOTHER_WHOLE, MLQMC_SMOOTHER_STREAM, MLQMC_SMOOTHER_TMA};
-    for (int t = 1; t < c->p.n_levels && res == MLQMC_OK; ++t) {
+    int large_best[MLQMC_MAX_LEVELS] = {};
+    for (int t = 1; t < c->p.n_levels && res == MLQMC_OK; ++t)
+    for (int cls = 1; cls >= 0 && res == MLQMC_OK; --cls) {  // large batches, then small ones
         int cands[4], nc = 0;
         for (int k : all)
             if ((f64 || k != MLQMC_SMOOTHER_GS) && smoother_fits(c, k, t)) cands[nc++] = k;
         if (nc < 2) continue;
-        int64_t B = 1024;  // the same for every context, whatever its max_samples
+        int64_t B = cls ? 1024 : 64;  // the same for every context, whatever its max_samples
         const size_t per = level_bytes_per_sample(c->p, c->Ka, t) + level_bytes_per_sample(c->p, c->Ka, t - 1);
         while (B > 64 && per * static_cast<size_t>(B) > c->pool_budget / 4) B /= 2;
         if (ensure_pool(c, t - 1, B) != MLQMC_OK || ensure_pool(c, t, B) != MLQMC_OK) {
@@ -2191,9 +2205,10 @@ mlqmc_status tune_smoothers(mlqmc_ctx* c)
             const size_t bytes = level_bytes_per_sample(c->p, c->Ka, u) * static_cast<size_t>(P.cap);
             if (!ok(cudaMemsetAsync(P.mem, 0, bytes, st))) res = MLQMC_ERR_CUDA;
         }
+        double* tms = cls ? c->tune_ms[t] : c->tune_small_ms[t];
         int best = cands[0];
         for (int k = 0; k < nc && res == MLQMC_OK; ++k) {
-            c->smoother[t] = cands[k];
+            c->smoother[t] = c->smoother_small[t] = cands[k];
             FmgArgs A = base_args(c);
             float ms = 0.0f, tot = 0.0f;
             for (int rep = 0; rep < 4 && res == MLQMC_OK; ++rep) {  // one untimed visit, then three timed
@@ -2209,10 +2224,15 @@ mlqmc_status tune_smoothers(mlqmc_ctx* c)
                     res = MLQMC_ERR_CUDA;
                 if (rep > 0) tot += ms;
             }
-            c->tune_ms[t][cands[k]] = tot / 3.0;
-            if (c->tune_ms[t][cands[k]] < c->tune_ms[t][best]) best = cands[k];
+            tms[cands[k]] = tot / 3.0;
+            if (tms[cands[k]] < tms[best]) best = cands[k];
         }
-        c->smoother[t] = best;
+        if (cls) {
+            large_best[t] = best;
+        } else {
+            c->smoother[t] = large_best[t];
+            c->smoother_small[t] = best;
+        }
     }
     if (res == MLQMC_OK && !ok(cudaStreamSynchronize(st))) res = MLQMC_ERR_CUDA;
     if (res == MLQMC_OK && c->host_status == 0) {
@@ -2225,6 +2245,71 @@ mlqmc_status tune_smoothers(mlqmc_ctx* c)
     cudaStreamDestroy(st);
     c->launches = launches0;
     if (res != MLQMC_OK) default_smoothers(c);
+    return res;
+}
+
+// Autotuner of the tensor-core KL tile width (mixed forms): for every level
+// with the contraction, time one launch with 128 and with 256 samples per
+// tile on up to 262,144 of the level's cells (the per-tile work is the
+// level's own) for 64 and for 256 samples (the small- and large-batch
+// classes), zeroed C operand, scratch output; keep the faster width per class.
+mlqmc_status tune_kl(mlqmc_ctx* c)
+{
+    if (!c->kl_tc) return MLQMC_OK;
+    const int Bs[2] = {64, 256}, NTs[2] = {128, 256};
+    int64_t maxM = 0;
+    for (int t = 0; t < c->p.n_levels; ++t)
+        if (c->d_psi_tc[t]) {
+            const int64_t n = c->p.coarse_cells << t;
+            maxM = std::max<int64_t>(maxM, std::min<int64_t>(n * n, 262144));
+        }
+    if (maxM == 0) return MLQMC_OK;
+    float* out = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    mlqmc_status res = MLQMC_OK;
+    if (!ok(cudaMalloc(&out, sizeof(float) * static_cast<size_t>(maxM) * Bs[1]))) {
+        cudaGetLastError();
+        return MLQMC_ERR_OOM;
+    }
+    if (!ok(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) || !ok(cudaEventCreate(&e0)) ||
+        !ok(cudaEventCreate(&e1)) ||
+        !ok(cudaMemsetAsync(c->d_C, 0, static_cast<size_t>(c->max_samples) *
+                                           mlqmc_kl::row_bytes(c->kl_variant, c->p.n_modes), st)))
+        res = MLQMC_ERR_CUDA;
+    for (int t = 0; t < c->p.n_levels && res == MLQMC_OK; ++t) {
+        if (!c->d_psi_tc[t]) continue;
+        const int64_t n = c->p.coarse_cells << t;
+        const int M = static_cast<int>(std::min<int64_t>(n * n, 262144));
+        for (int cls = 0; cls < 2 && res == MLQMC_OK; ++cls) {
+            for (int k = 0; k < 2 && res == MLQMC_OK; ++k) {
+                float ms = 0.0f, tot = 0.0f;
+                for (int rep = 0; rep < 4 && res == MLQMC_OK; ++rep) {  // one untimed launch, then three timed
+                    if (!ok(cudaEventRecord(e0, st)) ||
+                        !mlqmc_kl::launch(c->kl_variant, c->kl_maps[t], M, Bs[cls], c->p.n_modes, out,
+                                          static_cast<size_t>(M), c->d_status, st, NTs[k]) ||
+                        !ok(cudaEventRecord(e1, st)) || !ok(cudaEventSynchronize(e1)) ||
+                        !ok(cudaEventElapsedTime(&ms, e0, e1)))
+                        res = MLQMC_ERR_CUDA;
+                    if (rep > 0) tot += ms;
+                }
+                c->tune_kl_ms[t][cls][k] = tot / 3.0;
+            }
+            c->kl_nt[t][cls] = c->tune_kl_ms[t][cls][0] < c->tune_kl_ms[t][cls][1] ? NTs[0] : NTs[1];
+        }
+    }
+    if (res == MLQMC_OK && !ok(cudaStreamSynchronize(st))) res = MLQMC_ERR_CUDA;
+    if (res == MLQMC_OK) {
+        int dev = 0;
+        if (!ok(cudaMemcpy(&dev, c->d_status, sizeof(int), cudaMemcpyDeviceToHost))) res = MLQMC_ERR_CUDA;
+        else if (dev != 0) res = MLQMC_ERR_DEVICE_STATUS;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    cudaFree(out);
+    if (res != MLQMC_OK)
+        for (int t = 0; t < c->p.n_levels; ++t) c->kl_nt[t][0] = c->kl_nt[t][1] = mlqmc_kl::tile_samples();
     return res;
 }
 
@@ -2591,6 +2676,7 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
         return MLQMC_ERR_CUDA;
     }
     st = tune_smoothers(c);
+    if (st == MLQMC_OK) st = tune_kl(c);
     if (st != MLQMC_OK) {
         free_ctx(c);
         return st;
@@ -2786,7 +2872,10 @@ mlqmc_status round_graph(mlqmc_ctx* c, int count, const int* Bt, int Lmax, doubl
     // launch shape: the levels that run and their smoothers, the outputs asked for
     std::vector<int32_t> key;
     key.push_back(Lmax);
-    for (int t = 0; t <= Lmax; ++t) key.push_back(Bt[t] > 0 ? c->smoother[t] : -1);
+    for (int t = 0; t <= Lmax; ++t) {
+        key.push_back(Bt[t] > 0 ? smoother_for(c, t, Bt[t]) : -1);
+        key.push_back(Bt[t] > 0 ? kl_nt_for(c, t, Bt[t]) : 0);
+    }
     key.push_back(d_F ? 1 : 0);
     key.push_back(d_sums ? 1 : 0);
     // an instantiated graph may still be running the previous call
@@ -2924,7 +3013,8 @@ extern "C" mlqmc_status mlqmc_sample_levels(mlqmc_ctx* c, const mlqmc_work* work
         }
         if (graphable && single) graph_reset(c);
         // a call that is not a repeat (an adaptive round): one graph launch
-        const bool round = G.enabled && G.rounds && single && !c->profiling;
+        const bool round = G.enabled && single && !c->profiling &&
+                           (G.rounds == 1 || (G.rounds == 2 && p.refine_rtol > 0.0));
         mlqmc_status s = round ? prepare_round(c, Bt, Lmax) : MLQMC_OK;
         if (s == MLQMC_OK) s = stage_samples(c, all.data() + a, count, st);
         if (s != MLQMC_OK) return s;
@@ -3321,12 +3411,27 @@ extern "C" mlqmc_status mlqmc_smoother_info(const mlqmc_ctx* c, int32_t* kind, d
     return MLQMC_OK;
 }
 
+extern "C" mlqmc_status mlqmc_schedule_info(const mlqmc_ctx* c, int32_t* smoother_small, double* tuned_small_ms,
+                                            int32_t* kl_nt, double* tuned_kl_ms)
+{
+    if (!c) return MLQMC_ERR_INVALID_ARG;
+    for (int t = 0; t < c->p.n_levels; ++t) {
+        if (smoother_small) smoother_small[t] = t == 0 ? 0 : c->smoother_small[t];
+        for (int k = 0; k < 5 && tuned_small_ms; ++k) tuned_small_ms[t * 5 + k] = c->tune_small_ms[t][k];
+        for (int cls = 0; cls < 2; ++cls) {
+            if (kl_nt) kl_nt[t * 2 + cls] = c->d_psi_tc[t] ? c->kl_nt[t][cls] : 0;
+            for (int k = 0; k < 2 && tuned_kl_ms; ++k) tuned_kl_ms[(t * 2 + cls) * 2 + k] = c->tune_kl_ms[t][cls][k];
+        }
+    }
+    return MLQMC_OK;
+}
+
 extern "C" mlqmc_status mlqmc_set_smoother(mlqmc_ctx* c, int32_t level, int32_t kind)
 {
     if (!c || level < 1 || level >= c->p.n_levels || kind < MLQMC_SMOOTHER_GS || kind > MLQMC_SMOOTHER_WHOLE ||
         (kind == MLQMC_SMOOTHER_GS && is_mixed(c->p)) || !smoother_fits(c, kind, level))
         return MLQMC_ERR_INVALID_ARG;
-    c->smoother[level] = kind;
+    c->smoother[level] = c->smoother_small[level] = kind;  // every batch size
     ++c->pool_epoch;  // a captured graph runs the old smoother
     return MLQMC_OK;
 }
@@ -3362,6 +3467,13 @@ extern "C" mlqmc_status mlqmc_test_wait_timeout(mlqmc_ctx* c, int64_t limit_ns, 
     if (!c || limit_ns < 0 || limit_ns > 100000000) return MLQMC_ERR_INVALID_ARG;
     k_wait_nothing<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(c->d_status, static_cast<uint64_t>(limit_ns));
     return last_error();
+}
+
+extern "C" mlqmc_status mlqmc_set_round_graphs(mlqmc_ctx* c, int32_t mode)
+{
+    if (!c || mode < 0 || mode > 2) return MLQMC_ERR_INVALID_ARG;
+    c->graph.rounds = mode;
+    return MLQMC_OK;
 }
 
 extern "C" mlqmc_status mlqmc_graph_stats(const mlqmc_ctx* c, int64_t* out)

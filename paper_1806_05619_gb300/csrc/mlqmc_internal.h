@@ -63,6 +63,9 @@ enum ProfKind {
     kProfKinds = 8
 };
 
+// Below this many samples in a call a level follows its small-batch schedule.
+constexpr int kSmallBatch = 256;
+
 // Profile buckets per grid level; the last holds launches of no single level
 // (normals, reuse sums, outputs).
 constexpr int kProfLevels = MLQMC_MAX_LEVELS + 1;
@@ -177,6 +180,15 @@ struct mlqmc_ctx {
     // tune_ms: the tuner's time per candidate (ms, 0 when not timed)
     int smoother[MLQMC_MAX_LEVELS] = {};
     double tune_ms[MLQMC_MAX_LEVELS][5] = {};
+    // batch-size schedule of the autotuner: a level with fewer than
+    // kSmallBatch samples in a call uses smoother_small (tuned on 64 samples)
+    // instead of smoother (tuned on 1024); the tensor-core KL takes kl_nt[t][0]
+    // or kl_nt[t][1] samples per tile (128 or 256), tuned on 64 and 256
+    // samples (tune_kl_ms[t][class][0: 128, 1: 256])
+    int smoother_small[MLQMC_MAX_LEVELS] = {};
+    double tune_small_ms[MLQMC_MAX_LEVELS][5] = {};
+    int kl_nt[MLQMC_MAX_LEVELS][2] = {};
+    double tune_kl_ms[MLQMC_MAX_LEVELS][2][2] = {};
 
     // Replay of repeated identical calls of the fixed-cycle forms as one CUDA
     // graph: the second call with the same ranked samples, outputs and pools
@@ -204,7 +216,7 @@ struct mlqmc_ctx {
         // refinement loops as conditional WHILE nodes driven by the device,
         // and launched once; an instantiated graph of the same launch shape
         // is updated in place (cudaGraphExecUpdate) instead of rebuilt.
-        bool rounds = true;
+        int rounds = 2;               // 0 off, 1 on, 2 on in the converged forms only (the default)
         bool round_capture = false;   // capturing a round: loops run on the device
         bool in_body = false;         // capturing a conditional body (no memset nodes)
         cudaStream_t body = nullptr;  // captures the loop bodies

@@ -78,15 +78,17 @@ def test_traffic_record_and_its_invalidation(bench, tmp_path, monkeypatch):
     traffic = tmp_path / "dram_traffic.json"
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(traffic))
     assert bench.measured_traffic("mixed_tf32", "kb_rbgs_tma", 2048) is None  # no record
-    rec = {"sources_sha256": bench.sources_digest(),
-           "kernels": {"mixed_tf32|kb_rbgs_tma|2048": {"dram_bytes_per_sample": 123.0}}}
+    files = ["paper_1806_05619_gb300/csrc/rbgs_tma.cu", "paper_1806_05619_gb300/csrc/fmg_device.cuh"]
+    entry = {"dram_bytes_per_sample": 123.0, "sources": files, "sources_sha256": bench.sources_digest(files)}
+    rec = {"kernels": {"mixed_tf32|kb_rbgs_tma|2048": entry}}
     traffic.write_text(json.dumps(rec))
     assert bench.measured_traffic("mixed_tf32", "kb_rbgs_tma", 2048) == 123.0
     assert bench.measured_traffic("mixed_tf32", "kb_rbgs_tma", 1024) is None   # another level
     assert bench.measured_traffic("fp64", "kb_rbgs_tma", 2048) is None         # another form
-    rec["sources_sha256"] = "0" * 64                                            # other library sources
+    entry["sources_sha256"] = "0" * 64                                          # other kernel sources
     traffic.write_text(json.dumps(rec))
     assert bench.measured_traffic("mixed_tf32", "kb_rbgs_tma", 2048) is None
+    assert bench.sources_digest(files) != bench.sources_digest(files[:1])
 
 
 def test_clock_summary(bench):

@@ -121,3 +121,44 @@ def test_problem5_samples_on_2048x2048(precision):
         _check_F(cfg, orc, Fg[q], lv, r, n, precision)
     _check_sums_from_F(cfg, Fg, sums, index)
     _check_field(cfg, ctx, orc, 6, orc.normals(top, 0, 1), precision)
+
+
+_ORACLE_F = {}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_tf32"])
+def test_problem5_bench_step_sampled_against_oracle(precision):
+    """The step bench.py times, in its launch configuration: the 9-level
+    problem with N_l = 4096..16 per shift on 16 shifts (130,816 samples, 256
+    on 2048 x 2048) in one mlqmc_sample_levels call, FMG with fixed mu0 = 2
+    V(2,2)-cycles. Sampled samples' F on every level against the oracle's
+    fixed-cycle FMG of the same point: FP64 form within 1e-12; mixed form
+    within expm1(eta + slack) (the TF32 field and FP32 faces, the bound of the
+    other mixed tests) plus 2^-16 (the FP32 arithmetic of the V-cycles acts on
+    the correction, a few percent of u, with relative rounding well below
+    2^-12). The reuse sums equal those recomputed from the per-sample F."""
+    cfg = W.scaled(W.ADAPTIVE_9LEVEL, precision=precision)
+    work = W.fixed_count_work(cfg["counts"], cfg["R"])
+    ns = sum((ne - nb) * (re_ - rb) for (_, nb, ne, rb, re_) in work)
+    assert ns == 130816
+    ctx, orc = _setup(cfg, max_samples=ns)
+    Fg, sums, index = _run(ctx, cfg, work)
+    ctx.close()
+    assert np.all(np.isfinite(Fg))
+    picks = [len(index) - 1, len(index) - 256, index.index((5, 7, 3)), 17]  # two finest, one mid, one coarse
+    eta_u = UFUN[precision](cfg["s"])
+    for q in picks:
+        lv, r, n = index[q]
+        key = (lv, r, n)
+        if key not in _ORACLE_F:
+            ref = orc.sample(lv, r, n)
+            assert ref["status"] == O.OK
+            _ORACLE_F[key] = ref["F"]
+        want = _ORACLE_F[key]
+        if precision == "fp64":
+            tol = 1e-12
+        else:
+            tol = math.expm1(_field_bound(orc, cfg, orc.normals(lv, r, n), eta_u) + EXP_SLACK) + 2.0 ** -16
+        rel = np.max(np.abs(Fg[q, :lv + 1] / want - 1.0))
+        assert rel <= tol, (precision, lv, r, n, rel, tol)
+    _check_sums_from_F(cfg, Fg, sums, index)

@@ -443,6 +443,45 @@ def test_autotuner_report():
         c64.set_smoother(3, "stream")  # FP64 form: kb_gs or the whole-sample smoother
 
 
+def test_batch_schedule_report_and_results():
+    """The autotuner's batch-size schedule: a small-batch smoother per level
+    (the fastest of its timings on 64 samples) and a KL tile width (128 or 256
+    samples) per tensor-core level and batch class (the faster of the two
+    timings); calls of either class still match the oracle within the TF32
+    field bound."""
+    cfg, ctx, orc = _pair(W.PRECISION_1024, n_levels=6, R=2, precision="mixed_tf32", rtol=1e-10)
+    info = ctx.schedule_info()
+    for t, row in enumerate(info):
+        n = cfg["n0"] << t
+        if t > 0:
+            assert row["smoother_small"] in ("stream", "tma", "tile", "whole")
+            if len(row["small_ms"]) >= 2:
+                assert row["smoother_small"] == min(row["small_ms"], key=row["small_ms"].get), (t, row)
+        if n * n >= 128 and (n * n) % 128 == 0:
+            for cls in range(2):
+                assert row["kl_nt"][cls] in (128, 256)
+                ms = row["kl_ms"][cls]
+                assert min(ms) > 0 and row["kl_nt"][cls] == (128 if ms[0] < ms[1] else 256)
+        else:
+            assert row["kl_nt"] == [0, 0]
+    for (lv, r, n) in [(5, 0, 1), (5, 1, 2)]:
+        _, F = ctx.sample_solution(lv, r, n)
+        ref = orc.sample(lv, r, n)
+        eta = _field_bound(orc, cfg, orc.normals(lv, r, n), _tf32_u(cfg["s"])) + EXP_SLACK
+        assert np.max(np.abs(F.cpu().numpy() / ref["F"] - 1)) <= math.expm1(eta) + 1e-9
+    work = [(5, 0, 20, 0, 2), (2, 0, 200, 0, 2)]  # 440 samples reach levels 0..2: the large class there
+    sums = torch.zeros(cfg["n_levels"] * cfg["R"] * 2, dtype=torch.float64, device="cuda")
+    F = torch.zeros(440 * cfg["n_levels"], dtype=torch.float64, device="cuda")
+    ctx.sample_levels(work, sums, F)
+    torch.cuda.synchronize()
+    ctx.check_device()
+    Fg = F.cpu().numpy().reshape(440, cfg["n_levels"])
+    for q, (lv, r, n) in [(0, (5, 0, 0)), (439, (2, 1, 199))]:
+        ref = orc.sample(lv, r, n)
+        eta = _field_bound(orc, cfg, orc.normals(lv, r, n), _tf32_u(cfg["s"])) + EXP_SLACK
+        assert np.max(np.abs(Fg[q, :lv + 1] / ref["F"] - 1)) <= math.expm1(eta) + 1e-9
+
+
 def test_fp64_whole_sample_smoother_matches_gs():
     """FP64 form: the whole-sample smoother (levels up to 64 x 64) multiplies by
     the stored 1/D like kb_gs and fuses residual and correction with the same

@@ -29,13 +29,14 @@ ROUNDS = [
 ]
 
 
-def _contexts(precision, rtol):
+def _context(precision, rtol):
+    # one context for both paths: two contexts could tune different smoothers
+    # (the choice changes FP32 rounding)
     cfg = W.scaled(W.LATTICE_6LEVEL, R=2, s=24, precision=precision, rtol=rtol, max_cycles=30)
     z, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
-    on = M.Context.from_config(cfg, genvec=z)
-    off = M.Context.from_config(cfg, genvec=z)
-    off.set_graphs(False)
-    return cfg, on, off
+    ctx = M.Context.from_config(cfg, genvec=z)
+    ctx.set_round_graphs("on")  # the fixed-cycle forms too (their default is launch by launch)
+    return cfg, ctx
 
 
 def _call(ctx, cfg, work):
@@ -52,31 +53,33 @@ def _call(ctx, cfg, work):
 @pytest.mark.parametrize("precision,rtol", [("fp64", 0.0), ("mixed_tf32", 0.0), ("fp64", 1e-10),
                                             ("mixed_tf32", 1e-10)])
 def test_rounds_equal_direct_path(precision, rtol):
-    cfg, on, off = _contexts(precision, rtol)
-    for work in ROUNDS:
-        a = _call(on, cfg, work)
-        b = _call(off, cfg, work)
-        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), work
-    if rtol > 0:
-        assert on.last_iterations() == off.last_iterations()
-    st = on.graph_stats()
+    cfg, ctx = _context(precision, rtol)
+    on = [_call(ctx, cfg, work) for work in ROUNDS]
+    it_on = ctx.last_iterations()
+    st = ctx.graph_stats()
     assert st["round_launches"] >= len(ROUNDS) - 1
     assert st["round_updates"] >= 2 and st["round_instantiations"] >= 1
-    assert off.graph_stats()["round_launches"] == 0
+    ctx.set_graphs(False)
+    off = [_call(ctx, cfg, work) for work in ROUNDS]
+    assert ctx.graph_stats()["round_launches"] == st["round_launches"]
+    for work, a, b in zip(ROUNDS, on, off):
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), work
+    if rtol > 0:
+        assert it_on == ctx.last_iterations()
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed_tf32"])
 def test_algorithm1_same_with_and_without_round_graphs(precision):
     cfg = W.scaled(W.ADAPTIVE_7LEVEL, n_levels=5, s=24, precision=precision, log2_nmax=12)
     z, _ = M.cbc_genvec(cfg["s"], cfg["log2_nmax"])
-    res = []
-    for graphs in (True, False):
-        ctx = M.Context.from_config(cfg, genvec=z)
-        ctx.set_graphs(graphs)
-        r = ctx.estimate(3e-3)
-        res.append((r, ctx.graph_stats()))
-        ctx.close()
-    (a, sa), (b, sb) = res
+    ctx = M.Context.from_config(cfg, genvec=z)
+    ctx.set_round_graphs("on")
+    a = ctx.estimate(3e-3)
+    sa = ctx.graph_stats()
+    ctx.set_graphs(False)
+    b = ctx.estimate(3e-3)
+    sb = ctx.graph_stats()
+    ctx.close()
     assert a["L"] == b["L"] and a["rounds"] == b["rounds"] and a["N"] == b["N"]
     assert a["Q"] == b["Q"] and a["varQ"] == b["varQ"]
-    assert sa["round_launches"] == a["rounds"] and sb["round_launches"] == 0
+    assert sa["round_launches"] == a["rounds"] and sb["round_launches"] == sa["round_launches"]
