@@ -2,19 +2,31 @@
 // by the TMA.
 //
 // Persistent CTAs walk the tiles of one level (TX x TY cells of one sample
-// each, TX * TY / 4 threads; tiles of a sample consecutive so that their
-// halos meet in L2). For each tile the TMA brings, as 3D tiled copies out of
-// the sample pools, the tile plus a 4-cell halo of u, b, the x faces and the
-// y faces (zeros outside the domain, which is the Dirichlet ghost value), and
-// for the fused coarse-grid correction the coarse solution around it. Two
-// buffers: while one tile is smoothed in shared memory the next one is in
-// flight. On the staged tile, half sweep p (p = 0 .. 2 NS - 1) updates its
-// colour on the tile grown by 2 NS - 1 - p cells, so after the last one the
-// tile itself holds exactly NS sweeps (temporal blocking); the result goes to
-// u2 (ping-pong: the halos of neighbouring tiles must see the old values).
-// The last pre-smoothing launch of a level can also form the residual of its
-// tile and its 2 x 2 restriction (the right-hand side of the next coarser
-// level), so that no separate pass re-reads u, b and the faces.
+// each; tiles of a sample consecutive so that their halos meet in L2). For
+// each tile the TMA brings, as 3D tiled copies out of the sample pools, the
+// "frame" -- the tile plus kH = 4 cells on every side -- of b, the x faces and
+// the y faces, u on the frame plus one more cell around it (zeros outside the
+// domain, which is the Dirichlet ghost value), and for the fused coarse-grid
+// correction the coarse solution around it. Two buffers: while one tile is
+// smoothed the next one is in flight.
+//
+// Every thread owns a 4 x 2 block of the frame and keeps its u, faces, h^2 b
+// and reciprocal diagonal in registers. Half sweep p (p = 0 .. 2 NS - 1)
+// updates the colour's cells of the whole frame: a cell's update reads its
+// two in-block neighbours from registers, the rows above and below the block
+// with one 16-byte shared load each and its left or right neighbour from the
+// next lane (a warp shuffle; shared memory where that lane holds another
+// row). Frame cells at distance d from the tile are exact after half sweep p
+// while d <= kH - p (their neighbours one cell further out were exact one half
+// sweep earlier, and the extra ring of u is exact before the first one), so
+// after the last half sweep the tile and one ring around it hold exactly NS
+// sweeps (temporal blocking); values further out are discarded. Cells
+// outside the domain have a zero reciprocal diagonal and right-hand side, so
+// they stay at zero. The result goes to u2 (ping-pong: the halos of
+// neighbouring tiles must see the old values). The last pre-smoothing launch
+// of a level can also form the residual of its tile and its 2 x 2 restriction
+// (the right-hand side of the next coarser level), so that no separate pass
+// re-reads u, b and the faces.
 #include "rbgs_tma.h"
 
 #include <cuda.h>
@@ -30,8 +42,9 @@ using namespace mlqmc_ptx;
 
 namespace {
 
-constexpr int kH = 4;  // staged halo (keeps x - kH a multiple of 4 floats: 16-byte TMA coordinates)
+constexpr int kH = 4;  // staged frame around the tile (keeps x - kH a multiple of 4 floats: 16-byte TMA coordinates)
 constexpr int kSmemPerSM = 233472;  // 228 KB of shared memory per SM, 1 KB of it reserved per CTA
+constexpr unsigned kFull = 0xffffffffu;
 
 struct Maps {
     CUtensorMap u, kx, ky, b, e;
@@ -39,21 +52,58 @@ struct Maps {
 
 constexpr int round32(int v) { return (v + 31) / 32 * 32; }  // 128-byte aligned sub-buffers
 
-// RR (pre-smoothing with the restricted residual): u is staged with one more
-// cell of halo (UOY = 1 more row above and below; UOX = 4 more columns on
-// each side, so that the copy's x origin stays on a 16-byte boundary), the
-// half sweeps grow one cell further, and the tile plus a one-cell ring end
-// with exactly NS sweeps: the residual of every tile cell follows.
-template <int TX, int TY, bool POST, bool RR = false>
+template <int V>
+struct Colour {
+    static constexpr int value = V;
+};
+
+template <bool V>
+struct Flag {
+    static constexpr bool value = V;
+};
+
+// Coordinates (sample i, tile row ty, tile column tx) of a CTA's tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...: split once, then advanced by
+// gridDim.x with carries instead of two divisions per tile.
+struct TileWalk {
+    int txn, tyn, gi, gty, gtx;
+    __device__ TileWalk(int txn_, int tyn_) : txn(txn_), tyn(tyn_) { split(gridDim.x, gi, gty, gtx); }
+    __device__ void split(int tile, int& i, int& ty, int& tx) const
+    {
+        const int per = txn * tyn;
+        i = tile / per;
+        const int tr = tile - i * per;
+        ty = tr / txn;
+        tx = tr - ty * txn;
+    }
+    __device__ void advance(int& i, int& ty, int& tx) const
+    {
+        tx += gtx;
+        if (tx >= txn) {
+            tx -= txn;
+            ++ty;
+        }
+        ty += gty;
+        if (ty >= tyn) {
+            ty -= tyn;
+            ++i;
+        }
+        i += gi;
+    }
+};
+
+template <int TX, int TY, bool POST>
 struct TGeom {
-    static constexpr int SX = TX + 2 * kH;         // staged cells per row (b, faces; u without RR)
-    static constexpr int SY = TY + 2 * kH;         // staged rows
+    static constexpr int SX = TX + 2 * kH;         // frame cells per row (b, faces)
+    static constexpr int SY = TY + 2 * kH;         // frame rows
     static constexpr int XW = SX + 4;              // staged x faces per row (box width, 16-byte multiple)
     static constexpr int ECX = TX / 2 + 2 * kH;    // staged coarse cells per row
     static constexpr int ECY = TY / 2 + 2 * kH;    // staged coarse rows
-    static constexpr int UOX = RR ? 4 : 0, UOY = RR ? 1 : 0;
-    static constexpr int UP = SX + 2 * UOX;        // staged u: row pitch
-    static constexpr int UR = SY + 2 * UOY;        // staged u: rows
+    static constexpr int UP = SX + 8;              // staged u: row pitch (4 more columns on each side)
+    static constexpr int UR = SY + 2;              // staged u: rows (one more above and below)
+    static constexpr int BX = SX / 4, BY = SY / 2;  // 4 x 2 blocks of the frame, one per thread
+    static constexpr int NB = BX * BY;
+    static constexpr int threads = round32(NB);
     static constexpr int oU = 0;
     static constexpr int oB = oU + round32(UP * UR);
     static constexpr int oKX = oB + round32(SX * SY);
@@ -61,33 +111,26 @@ struct TGeom {
     static constexpr int oE = oKY + round32((SY + 1) * SX);
     static constexpr int buf = oE + (POST ? round32(ECX * ECY) : 0);  // floats per buffer
     static constexpr size_t bytes = 128 + 2 * sizeof(float) * static_cast<size_t>(buf);
-    static constexpr int threads = TX * TY / 4;    // four tile cells per thread
     static constexpr int by_smem = static_cast<int>(kSmemPerSM / (bytes + 1024));
     static constexpr int ctas_per_sm = by_smem < 2048 / threads ? by_smem : 2048 / threads;
-    static_assert(!(POST && RR), "the correction is fused into post-smoothing, the residual into pre-smoothing");
     static_assert((SX * 4) % 16 == 0 && (XW * 4) % 16 == 0 && (ECX * 4) % 16 == 0 && (UP * 4) % 16 == 0,
                   "TMA boxes: 16-byte rows");
-    static_assert(TX % 32 == 0 && (TY / 2) % (threads / 32 / (TX / 32)) == 0 && TY == 4 * (threads / 32 / (TX / 32)),
-                  "each warp: a 32-column half-tile row pair, two row pairs per thread");
+    static_assert(TX % 32 == 0 && TY % 2 == 0 && kH % 4 == 0, "whole blocks on the tile and the frame");
+    static_assert(ctas_per_sm >= 1, "shared memory");
 };
 
-template <int TX, int TY, int NS, bool POST, bool RR = false>
-__global__ void __launch_bounds__(TGeom<TX, TY, POST, RR>::threads, TGeom<TX, TY, POST, RR>::ctas_per_sm)
+template <int TX, int TY, int NS, bool POST, bool RR>
+__global__ void __launch_bounds__(TGeom<TX, TY, POST>::threads, TGeom<TX, TY, POST>::ctas_per_sm)
     kb_rbgs_tma(const __grid_constant__ Maps maps, FmgArgs A, int t, int B, int ones, int first, int zin)
 {
-    using Gm = TGeom<TX, TY, POST, RR>;
-    constexpr int SX = Gm::SX, XW = Gm::XW, ECX = Gm::ECX;
-    constexpr int UP = Gm::UP, UOX = Gm::UOX, UOY = Gm::UOY;
+    using Gm = TGeom<TX, TY, POST>;
+    constexpr int SX = Gm::SX, SY = Gm::SY, XW = Gm::XW, ECX = Gm::ECX, UP = Gm::UP, BX = Gm::BX;
     constexpr int kThreads = Gm::threads;
-    constexpr int HN = 2 * NS;          // half sweeps
-    constexpr int GR = RR ? 1 : 0;      // extra growth: the ring around the tile ends fully swept
-    constexpr int GMAX = HN - 1 + GR;   // largest growth
-    constexpr int NRING = (2 * GMAX * (TX / 2 + GMAX) + TY * GMAX + kThreads - 1) / kThreads;  // ring cells per thread
-    constexpr int CH = TX / 32;                  // 32-column halves of the tile
-    constexpr int WR = kThreads / 32 / CH;       // warps per half: row pairs rp, rp + WR
-    static_assert(HN <= kH && HN + GR <= kH + UOY, "halo");
-    // staged u index of the cell at (sy, sx) of the b/face frame (origin x0 - kH, y0 - kH)
-    auto uix = [](int sy, int sx) { return (sy + UOY) * UP + sx + UOX; };
+    constexpr int HN = 2 * NS;  // half sweeps
+    static_assert(HN <= kH, "the tile and one ring around it end exact");
+    static_assert(!(POST && RR), "the correction is fused into post-smoothing, the residual into pre-smoothing");
+    // staged u index of the frame cell (sy, sx) (frame origin x0 - kH, y0 - kH)
+    auto uix = [](int sy, int sx) { return (sy + 1) * UP + sx + 4; };
     extern __shared__ __align__(128) unsigned char smraw[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smraw);
     float* bufs = reinterpret_cast<float*>(smraw + 128);
@@ -100,8 +143,7 @@ __global__ void __launch_bounds__(TGeom<TX, TY, POST, RR>::threads, TGeom<TX, TY
     // zin (pre-smoothing of a correction, never with POST): u is zero on entry,
     // so its tile is cleared in shared memory instead of copied
     const uint32_t tx_bytes =
-        4u * ((zin ? 0 : UP * Gm::UR) + XW * Gm::SY + (Gm::SY + 1) * SX + (ones ? 0 : SX * Gm::SY) +
-              (POST ? ECX * Gm::ECY : 0));
+        4u * ((zin ? 0 : UP * Gm::UR) + XW * SY + (SY + 1) * SX + (ones ? 0 : SX * SY) + (POST ? ECX * Gm::ECY : 0));
 
     if (threadIdx.x == 0) {
         mbar_init(&full[0], 1);
@@ -110,247 +152,296 @@ __global__ void __launch_bounds__(TGeom<TX, TY, POST, RR>::threads, TGeom<TX, TY
     }
     __syncthreads();
 
-    auto issue = [&](int tile, int slot) {
-        const int i = tile / per;
-        const int tr = tile - i * per;
-        const int y0 = (tr / txn) * TY, x0 = (tr % txn) * TX;
+    auto issue = [&](int i, int ty, int tx, int slot) {
+        const int y0 = ty * TY, x0 = tx * TX;
         float* S = bufs + slot * Gm::buf;
         uint64_t* bar = &full[slot];
         mbar_arrive_tx(bar, tx_bytes);
-        if (!zin) tensor_load_3d(S + Gm::oU, &maps.u, bar, x0 - kH - UOX, y0 - kH - UOY, i);
+        if (!zin) tensor_load_3d(S + Gm::oU, &maps.u, bar, x0 - kH - 4, y0 - kH - 1, i);
         tensor_load_3d(S + Gm::oKX, &maps.kx, bar, x0 - kH, y0 - kH, i);
         tensor_load_3d(S + Gm::oKY, &maps.ky, bar, x0 - kH, y0 - kH, i);
         if (!ones) tensor_load_3d(S + Gm::oB, &maps.b, bar, x0 - kH, y0 - kH, i);
         if (POST) tensor_load_3d(S + Gm::oE, &maps.e, bar, x0 / 2 - kH, y0 / 2 - kH, i);
     };
 
-    // Work of half sweep ph (growth g = HN - 1 - ph) on the staged tile:
-    // - the tile's own TY rows x TX / 2 cells of the colour, two per thread:
-    //   warp w takes the 32-column half ch = w / WR of the tile and the row
-    //   pairs rp and rp + WR (rp = w % WR), lanes 0-15 the upper row of a
-    //   pair and 16-31 the lower one, so every shared access of a warp hits
-    //   32 distinct banks;
-    // - the ring of the grown region around the tile (2 g (TX / 2 + g) + TY g
-    //   cells, NRING per thread): the 2g full rows above and below (TX / 2 + g
-    //   cells each, by cell index m) and g cells at the ends of each tile row
-    //   (by index k: the left strip's cells first). Packed per thread: bit 15
-    //   = end-of-row cell, bits 8-14 staged row, bits 0-7 m or k; -1: none.
-    int ring[HN][NRING];
-#pragma unroll
-    for (int ph = 0; ph < HN; ++ph) {
-        const int g = HN - 1 - ph + GR;
-        const int full = 2 * g * (TX / 2 + g);
-#pragma unroll
-        for (int q = 0; q < NRING; ++q) {
-            const int r = threadIdx.x + q * kThreads;
-            int pk = -1;
-            if (r < full) {
-                const int rr = r / (TX / 2 + g), m = r - rr * (TX / 2 + g);
-                const int sy = rr < g ? kH - g + rr : kH + TY + rr - g;
-                pk = (sy << 8) | m;
-            } else if (r < full + TY * g) {
-                const int rr = (r - full) / g, k = r - full - rr * g;
-                pk = 0x8000 | ((kH + rr) << 8) | k;
-            }
-            ring[ph][q] = g > 0 ? pk : -1;
-        }
-    }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ch = warp / WR, rp = warp - (warp / WR) * WR;
+    // the thread's block: frame rows sy0, sy0 + 1, columns sx0 .. sx0 + 3
+    const int lane = threadIdx.x & 31;
+    const bool owner = static_cast<int>(threadIdx.x) < Gm::NB;
+    const int br = threadIdx.x / BX, bc = threadIdx.x - (threadIdx.x / BX) * BX;
+    const int sy0 = 2 * br, sx0 = 4 * bc;
+    const bool core = owner && br >= kH / 2 && br < kH / 2 + TY / 2 && bc >= kH / 4 && bc < kH / 4 + TX / 4;
+    // side neighbours come from the next lane unless that lane holds another
+    // frame row (or is in another warp): then from shared memory
+    const bool lsm = owner && (lane == 0 || bc == 0);
+    const bool rsm = owner && (lane == 31 || bc == BX - 1);
 
+    const TileWalk walk(txn, tyn);
+    int ci, cty, ctx;  // this tile
+    walk.split(blockIdx.x, ci, cty, ctx);
+    int ni = ci, nty = cty, ntx = ctx;  // the next one
     bool live = true;
     int issued = 0;  // tiles issued by this CTA (thread 0's count)
     if (threadIdx.x == 0 && static_cast<int>(blockIdx.x) < total) {
-        issue(blockIdx.x, 0);
+        issue(ci, cty, ctx, 0);
         issued = 1;
     }
     int it = 0;
     for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++it) {
         const int slot = it & 1;
         const int next = tile + gridDim.x;
+        walk.advance(ni, nty, ntx);
         if (threadIdx.x == 0 && next < total) {
-            issue(next, slot ^ 1);  // the other buffer was released by the barrier ending the last iteration
+            issue(ni, nty, ntx, slot ^ 1);  // the other buffer was released by the barrier ending the last iteration
             ++issued;
         }
         if (live) live = mbar_wait(&full[slot], (it >> 1) & 1, A.status, kStatusTimeout);
-        const int i = tile / per;
-        const int tr = tile - i * per;
-        const int y0 = (tr / txn) * TY, x0 = (tr % txn) * TX;
+        const int i = ci;
+        const int y0 = cty * TY, x0 = ctx * TX;
+        ci = ni, cty = nty, ctx = ntx;
         // uniform per CTA: a skipped tile skips every barrier below together
         if (!(A.active && !A.active[i])) {
             float* S = bufs + slot * Gm::buf;
             float* su = S + Gm::oU;
             if (zin) {
-                for (int q = threadIdx.x; q < UP * Gm::UR; q += kThreads) su[q] = 0.0f;
+                float4* s4 = reinterpret_cast<float4*>(su);
+                for (int q = threadIdx.x; q < UP * Gm::UR / 4; q += kThreads) s4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
                 __syncthreads();
             }
             const float* sb = S + Gm::oB;
             const float* skx = S + Gm::oKX;
             const float* sky = S + Gm::oKY;
+
+            // the block in registers: u, x faces (w of cell k = fx[r][k], e =
+            // fx[r][k + 1]), y faces (north fy[r][k], south fy[r + 1][k]), h^2 b
+            // and the reciprocal diagonal; both zero outside the domain
+            float uu[2][4], fx[2][5], fy[3][4], cb[2][4], id[2][4];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) uu[r][k] = fx[r][k] = fy[r][k] = cb[r][k] = id[r][k] = 0.0f;
+                fx[r][4] = 0.0f;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) fy[2][k] = 0.0f;
+            if (owner) {
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const float4 v = *reinterpret_cast<const float4*>(su + uix(sy0 + r, sx0));
+                    uu[r][0] = v.x, uu[r][1] = v.y, uu[r][2] = v.z, uu[r][3] = v.w;
+                    const float4 kv = *reinterpret_cast<const float4*>(skx + (sy0 + r) * XW + sx0);
+                    fx[r][0] = kv.x, fx[r][1] = kv.y, fx[r][2] = kv.z, fx[r][3] = kv.w;
+                    fx[r][4] = skx[(sy0 + r) * XW + sx0 + 4];
+                }
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const float4 yv = *reinterpret_cast<const float4*>(sky + (sy0 + j) * SX + sx0);
+                    fy[j][0] = yv.x, fy[j][1] = yv.y, fy[j][2] = yv.z, fy[j][3] = yv.w;
+                }
+                float bv[2][4];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    bv[r][0] = bv[r][1] = bv[r][2] = bv[r][3] = 1.0f;
+                    if (!ones) {
+                        const float4 v = *reinterpret_cast<const float4*>(sb + (sy0 + r) * SX + sx0);
+                        bv[r][0] = v.x, bv[r][1] = v.y, bv[r][2] = v.z, bv[r][3] = v.w;
+                    }
+                }
+                auto diag = [&](auto all_in) {
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        const int gy = y0 - kH + sy0 + r;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int gx = x0 - kH + sx0 + k;
+                            const bool in = decltype(all_in)::value || (gy >= 0 && gy < n && gx >= 0 && gx < n);
+                            const float d = fx[r][k] + fx[r][k + 1] + fy[r][k] + fy[r + 1][k];
+                            id[r][k] = in ? __fdividef(1.0f, d) : 0.0f;
+                            cb[r][k] = in ? h2 * bv[r][k] : 0.0f;
+                        }
+                    }
+                };
+                if (x0 >= kH && x0 + TX + kH <= n && y0 >= kH && y0 + TY + kH <= n) diag(Flag<true>());
+                else diag(Flag<false>());
+            }
             if constexpr (POST) {
-                // coarse-grid correction on every staged cell of the domain, one
-                // 2 x 2 block of fine cells (one coarse parent) per thread: the
-                // parent's 3 x 3 coarse neighbourhood, a neighbour outside the
-                // coarse grid replaced by minus the parent's row or column
-                // (odd reflection; the corner then by the product of the two
-                // signs), gives each fine cell the arithmetic of prolong_cell
+                // coarse-grid correction of the block's cells in the domain: each
+                // coarse parent's 3 x 3 neighbourhood, a neighbour outside the
+                // coarse grid replaced by minus the parent's row or column (odd
+                // reflection; the corner then by the product of the two signs)
                 const float* se = S + Gm::oE;
                 const int nc = n >> 1;
-                constexpr int SBX = SX / 2, SBY = Gm::SY / 2;  // staged blocks (x0 - kH, y0 - kH even)
-                for (int q = threadIdx.x; q < SBX * SBY; q += kThreads) {
-                    const int by = q / SBX, bx = q - (q / SBX) * SBX;
-                    const int I2 = (y0 - kH) / 2 + by, I1 = (x0 - kH) / 2 + bx;
-                    if (I2 < 0 || I2 >= nc || I1 < 0 || I1 >= nc) continue;
-                    const int ey = I2 - (y0 / 2 - kH), ex = I1 - (x0 / 2 - kH);  // in the staged coarse box
-                    const bool lo1 = I1 == 0, hi1 = I1 == nc - 1, lo2 = I2 == 0, hi2 = I2 == nc - 1;
-                    float E[3][3];
+                const int I2 = (y0 - kH) / 2 + br, I1b = (x0 - kH) / 2 + 2 * bc;
+                if (owner && I2 >= 0 && I2 < nc) {
+                    // coarse rows I2 - 1 .. I2 + 1, columns I1b - 1 .. I1b + 2 of the staged box
+                    const float* sc = se + (br + 1) * ECX + 2 * bc + 1;
+                    float C[3][4];
 #pragma unroll
-                    for (int dy = -1; dy <= 1; ++dy) {
+                    for (int a = 0; a < 3; ++a)
 #pragma unroll
-                        for (int dx = -1; dx <= 1; ++dx) {
-                            const bool ry = (dy < 0 && lo2) || (dy > 0 && hi2);
-                            const bool rx = (dx < 0 && lo1) || (dx > 0 && hi1);
-                            const float v = se[(ey + (ry ? 0 : dy)) * ECX + ex + (rx ? 0 : dx)];
-                            E[dy + 1][dx + 1] = (ry != rx) ? -v : v;
+                        for (int b = 0; b < 4; ++b) C[a][b] = sc[a * ECX + b];
+                    const bool lo2 = I2 == 0, hi2 = I2 == nc - 1;
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const int I1 = I1b + kk;
+                        if (I1 < 0 || I1 >= nc) continue;
+                        const bool lo1 = I1 == 0, hi1 = I1 == nc - 1;
+                        float E[3][3];
+#pragma unroll
+                        for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                const bool ry = (dy < 0 && lo2) || (dy > 0 && hi2);
+                                const bool rx = (dx < 0 && lo1) || (dx > 0 && hi1);
+                                const float a = rx ? C[1 + dy][kk + 1] : C[1 + dy][kk + 1 + dx];
+                                const float b = rx ? C[1][kk + 1] : C[1][kk + 1 + dx];
+                                const float v = ry ? b : a;
+                                E[dy + 1][dx + 1] = (ry != rx) ? -v : v;
+                            }
+                        }
+#pragma unroll
+                        for (int fy2 = 0; fy2 < 2; ++fy2) {
+#pragma unroll
+                            for (int fx2 = 0; fx2 < 2; ++fx2) {
+                                const int dy = 2 * fy2, dx = 2 * fx2;  // -1 -> 0, +1 -> 2 in E
+                                uu[fy2][2 * kk + fx2] +=
+                                    fmaf(0.5625f, E[1][1], fmaf(0.1875f, E[1][dx] + E[dy][1], 0.0625f * E[dy][dx]));
+                            }
                         }
                     }
-                    float* f = su + uix(2 * by, 2 * bx);
+                }
+                if (owner) {
 #pragma unroll
-                    for (int fy = 0; fy < 2; ++fy) {
-#pragma unroll
-                        for (int fx = 0; fx < 2; ++fx) {
-                            const int dy = 2 * fy, dx = 2 * fx;  // -1 -> 0, +1 -> 2 in E
-                            f[fy * UP + fx] +=
-                                fmaf(0.5625f, E[1][1], fmaf(0.1875f, E[1][dx] + E[dy][1], 0.0625f * E[dy][dx]));
-                        }
-                    }
+                    for (int r = 0; r < 2; ++r)
+                        *reinterpret_cast<float4*>(su + uix(sy0 + r, sx0)) =
+                            make_float4(uu[r][0], uu[r][1], uu[r][2], uu[r][3]);
                 }
                 __syncthreads();
             }
-            // tiles whose grown regions stay inside the domain skip the per-cell test
-            const bool interior =
-                x0 >= HN + GR && y0 >= HN + GR && x0 + TX + HN + GR <= n && y0 + TY + HN + GR <= n;
-            // one red-black update of staged cell (sy, sx)
-            auto update = [&](int sy, int sx) {
-                const int c0 = sy * SX + sx;
-                const int cu = uix(sy, sx);
-                const float* kr = skx + sy * XW;
-                const float w = kr[sx], e = kr[sx + 1];
-                const float nn = sky[c0], so = sky[c0 + SX];
-                float acc = h2 * (ones ? 1.0f : sb[c0]);
-                acc += w * su[cu - 1];
-                acc += e * su[cu + 1];
-                acc += nn * su[cu - UP];
-                acc += so * su[cu + UP];
-                su[cu] = __fdividef(acc, w + e + nn + so);  // hardware reciprocal: within 2 ulp
+
+            // one update: neighbours west, east, north, south (operand order of
+            // the other smoothers' update)
+            auto upd = [&](int r, int k, float uw, float ue, float un, float us) {
+                float acc = cb[r][k];
+                acc += fx[r][k] * uw;
+                acc += fx[r][k + 1] * ue;
+                acc += fy[r][k] * un;
+                acc += fy[r + 1][k] * us;
+                uu[r][k] = acc * id[r][k];
             };
-            // the thread's own tile cells (two rows, both colours): their faces,
-            // h^2 b and diagonal stay in registers across the half sweeps, so an
-            // update reads only the four neighbouring u from shared memory (same
-            // operands, same order as `update`)
-            float cw[2][2], ce[2][2], cn[2][2], cso[2][2], cb[2][2], cd[2][2];
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int sy = kH + 2 * (rp + WR * j) + (lane >> 4);
-                // lanes 16-31 hold the next row (every row pitch is even): they load
-                // their other column first, so each load of the warp hits 32 banks
-                const bool swap = (lane >> 4) != 0;
-                float vw[2], ve[2], vn[2], vs[2], vb[2];
-#pragma unroll
-                for (int pp = 0; pp < 2; ++pp) {
-                    const int sx = kH + 32 * ch + 2 * (lane & 15) + (pp ^ (lane >> 4));
-                    const int c0 = sy * SX + sx;
-                    const float* kr = skx + sy * XW;
-                    vw[pp] = kr[sx];
-                    ve[pp] = kr[sx + 1];
-                    vn[pp] = sky[c0];
-                    vs[pp] = sky[c0 + SX];
-                    vb[pp] = ones ? 1.0f : sb[c0];
+            // half sweep of colour C: cells (sx + sy) % 2 == C, i.e. k = C, C + 2
+            // in row 0 of the block and k = 1 - C, 3 - C in row 1
+            auto half = [&](auto colour) {
+                constexpr int C = decltype(colour)::value;
+                float ab[4] = {0.f, 0.f, 0.f, 0.f}, bl[4] = {0.f, 0.f, 0.f, 0.f};
+                if (owner) {
+                    const float4 a = *reinterpret_cast<const float4*>(su + uix(sy0 - 1, sx0));
+                    const float4 b = *reinterpret_cast<const float4*>(su + uix(sy0 + 2, sx0));
+                    ab[0] = a.x, ab[1] = a.y, ab[2] = a.z, ab[3] = a.w;
+                    bl[0] = b.x, bl[1] = b.y, bl[2] = b.z, bl[3] = b.w;
                 }
-#pragma unroll
-                for (int p = 0; p < 2; ++p) {
-                    const int q = p ^ 1;
-                    cw[j][p] = swap ? vw[q] : vw[p];
-                    ce[j][p] = swap ? ve[q] : ve[p];
-                    cn[j][p] = swap ? vn[q] : vn[p];
-                    cso[j][p] = swap ? vs[q] : vs[p];
-                    cb[j][p] = h2 * (swap ? vb[q] : vb[p]);
-                    cd[j][p] = cw[j][p] + ce[j][p] + cn[j][p] + cso[j][p];
+                if constexpr (C == 0) {
+                    // row 0 needs the west neighbour of k = 0, row 1 the east one of k = 3
+                    float l0 = __shfl_up_sync(kFull, uu[0][3], 1);
+                    float r1 = __shfl_down_sync(kFull, uu[1][0], 1);
+                    if (lsm) l0 = su[uix(sy0, sx0 - 1)];
+                    if (rsm) r1 = su[uix(sy0 + 1, sx0 + 4)];
+                    upd(0, 0, l0, uu[0][1], ab[0], uu[1][0]);
+                    upd(0, 2, uu[0][1], uu[0][3], ab[2], uu[1][2]);
+                    upd(1, 1, uu[1][0], uu[1][2], uu[0][1], bl[1]);
+                    upd(1, 3, uu[1][2], r1, uu[0][3], bl[3]);
+                } else {
+                    float r0 = __shfl_down_sync(kFull, uu[0][0], 1);
+                    float l1 = __shfl_up_sync(kFull, uu[1][3], 1);
+                    if (rsm) r0 = su[uix(sy0, sx0 + 4)];
+                    if (lsm) l1 = su[uix(sy0 + 1, sx0 - 1)];
+                    upd(0, 1, uu[0][0], uu[0][2], ab[1], uu[1][1]);
+                    upd(0, 3, uu[0][2], r0, ab[3], uu[1][3]);
+                    upd(1, 0, l1, uu[1][1], uu[0][0], bl[0]);
+                    upd(1, 2, uu[1][1], uu[1][3], uu[0][2], bl[2]);
                 }
-            }
+                // the other colour's values in these rows are rewritten unchanged,
+                // so readers of them in this half sweep see the same value
+                if (owner) {
+#pragma unroll
+                    for (int r = 0; r < 2; ++r)
+                        *reinterpret_cast<float4*>(su + uix(sy0 + r, sx0)) =
+                            make_float4(uu[r][0], uu[r][1], uu[r][2], uu[r][3]);
+                }
+                __syncthreads();
+            };
 #pragma unroll
             for (int ph = 0; ph < HN; ++ph) {
-                const int colour = (first + ph) & 1;
-                const int g = HN - 1 - ph + GR;  // growth of the updated region beyond the tile
-                // colour cells: (gx + gy) & 1 == colour, with x0 - kH and y0 - kH even
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int sy = kH + 2 * (rp + WR * j) + (lane >> 4);
-                    const int p = (colour + sy) & 1;
-                    const int cu = uix(sy, kH + 32 * ch + 2 * (lane & 15) + p);
-                    float acc = p ? cb[j][1] : cb[j][0];
-                    acc += (p ? cw[j][1] : cw[j][0]) * su[cu - 1];
-                    acc += (p ? ce[j][1] : ce[j][0]) * su[cu + 1];
-                    acc += (p ? cn[j][1] : cn[j][0]) * su[cu - UP];
-                    acc += (p ? cso[j][1] : cso[j][0]) * su[cu + UP];
-                    su[cu] = __fdividef(acc, p ? cd[j][1] : cd[j][0]);
-                }
-#pragma unroll
-                for (int q = 0; q < NRING; ++q) {
-                    const int pk = ring[ph][q];
-                    if (pk >= 0) {
-                        const int sy = (pk >> 8) & 127;
-                        const int p = (colour + g + sy) & 1;
-                        int m = pk & 255;
-                        if (pk & 0x8000) m = m < ((g - p + 1) >> 1) ? m : m + TX / 2;  // left strip, then right
-                        const int sx = kH - g + 2 * m + p;
-                        const int gy = y0 - kH + sy, gx = x0 - kH + sx;
-                        if (interior || (gy >= 0 && gy < n && gx >= 0 && gx < n)) update(sy, sx);
-                    }
-                }
-                __syncthreads();
+                if ((first + ph) & 1) half(Colour<1>());
+                else half(Colour<0>());
             }
             if constexpr (RR) {
                 // residual b - A u (flux form, u = 0 across the boundary, where the
-                // face holds 2 k) of the thread's four tile cells, from their faces
-                // in registers; the 2 x 2 mean of each coarse cell's children (its
-                // two rows are lanes l and l + 16) is the right-hand side of level
-                // t - 1. Lanes 16-31 take their other column first (32 banks).
-                const float ih2 = static_cast<float>(n) * static_cast<float>(n);
-                const bool swap = (lane >> 4) != 0;
-                float* bco = at<float>(A.lv[t - 1].bc, i);
-                const int nc = n >> 1;
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int sy = kH + 2 * (rp + WR * j) + (lane >> 4);
-                    float rs = 0.0f;
-#pragma unroll
-                    for (int pp = 0; pp < 2; ++pp) {
-                        const int p = pp ^ (lane >> 4);
-                        const int cu = uix(sy, kH + 32 * ch + 2 * (lane & 15) + p);
-                        const int q = pp ^ 1;
-                        const float w = swap ? cw[j][q] : cw[j][pp], e = swap ? ce[j][q] : ce[j][pp];
-                        const float nn = swap ? cn[j][q] : cn[j][pp], so = swap ? cso[j][q] : cso[j][pp];
-                        const float bb = swap ? cb[j][q] : cb[j][pp];
-                        const float up = su[cu];
-                        float acc = w * (up - su[cu - 1]);
-                        acc += e * (up - su[cu + 1]);
-                        acc += nn * (up - su[cu - UP]);
-                        acc += so * (up - su[cu + UP]);
-                        rs += (bb - acc) * ih2;
+                // face holds 2 k) and its 2 x 2 restriction (the right-hand side of
+                // level t - 1). The colour of the last half sweep has a zero
+                // residual (its update solved each of its equations with the other
+                // colour fixed), so only the other colour's cells are formed: in
+                // row r of the block the cells k with (k + r) % 2 != L, L the last
+                // colour; each coarse cell has one of them in each of its rows.
+                auto restrict_rr = [&](auto last) {
+                    constexpr int L = decltype(last)::value;
+                    float ab[4] = {0.f, 0.f, 0.f, 0.f}, bl[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (owner) {
+                        const float4 a = *reinterpret_cast<const float4*>(su + uix(sy0 - 1, sx0));
+                        const float4 b = *reinterpret_cast<const float4*>(su + uix(sy0 + 2, sx0));
+                        ab[0] = a.x, ab[1] = a.y, ab[2] = a.z, ab[3] = a.w;
+                        bl[0] = b.x, bl[1] = b.y, bl[2] = b.z, bl[3] = b.w;
                     }
-                    const float tot = rs + __shfl_xor_sync(0xffffffffu, rs, 16);
-                    if (lane < 16)
-                        bco[static_cast<size_t>(y0 / 2 + rp + WR * j) * nc + x0 / 2 + 16 * ch + lane] = 0.25f * tot;
-                }
+                    // row 0 forms k = 1 - L, 3 - L (the west neighbour of k = 0 when
+                    // L = 1), row 1 forms k = L, L + 2 (the east one of k = 3 when L = 1)
+                    float s0, s1;
+                    if constexpr (L == 1) {
+                        s0 = __shfl_up_sync(kFull, uu[0][3], 1);
+                        s1 = __shfl_down_sync(kFull, uu[1][0], 1);
+                        if (lsm) s0 = su[uix(sy0, sx0 - 1)];
+                        if (rsm) s1 = su[uix(sy0 + 1, sx0 + 4)];
+                    } else {
+                        s0 = __shfl_down_sync(kFull, uu[0][0], 1);
+                        s1 = __shfl_up_sync(kFull, uu[1][3], 1);
+                        if (rsm) s0 = su[uix(sy0, sx0 + 4)];
+                        if (lsm) s1 = su[uix(sy0 + 1, sx0 - 1)];
+                    }
+                    if (core) {
+                        const float ih2 = static_cast<float>(n) * static_cast<float>(n);
+                        float res[2][2];  // [row][coarse cell]
+#pragma unroll
+                        for (int r = 0; r < 2; ++r) {
+#pragma unroll
+                            for (int kk = 0; kk < 2; ++kk) {
+                                const int k = 2 * kk + ((r + L + 1) & 1);
+                                const float sd = r == 0 ? s0 : s1;
+                                const float up = uu[r][k];
+                                const float uw = k == 0 ? sd : uu[r][k > 0 ? k - 1 : 0];
+                                const float ue = k == 3 ? sd : uu[r][k < 3 ? k + 1 : 3];
+                                const float un = r == 0 ? ab[k] : uu[0][k];
+                                const float us = r == 1 ? bl[k] : uu[1][k];
+                                float acc = fx[r][k] * (up - uw);
+                                acc += fx[r][k + 1] * (up - ue);
+                                acc += fy[r][k] * (up - un);
+                                acc += fy[r + 1][k] * (up - us);
+                                res[r][kk] = (cb[r][k] - acc) * ih2;
+                            }
+                        }
+                        const int nc = n >> 1;
+                        float* bco = at<float>(A.lv[t - 1].bc, i);
+                        const float2 o = make_float2(0.25f * (res[0][0] + res[1][0]), 0.25f * (res[0][1] + res[1][1]));
+                        *reinterpret_cast<float2*>(bco + static_cast<size_t>((y0 - kH) / 2 + br) * nc + (x0 - kH) / 2 +
+                                                   2 * bc) = o;
+                    }
+                };
+                if ((first + HN - 1) & 1) restrict_rr(Colour<1>());
+                else restrict_rr(Colour<0>());
             }
-            float* uo = at<float>(A.lv[t].u2, i);
-            constexpr int TV = TX / 4;
-            static_assert((UP * 4) % 16 == 0 && ((kH + UOX) * 4) % 16 == 0, "16-byte aligned staged rows");
-            for (int q = threadIdx.x; q < TY * TV; q += kThreads) {
-                const int ry = q / TV, v = q - (q / TV) * TV;
-                *reinterpret_cast<float4*>(uo + static_cast<size_t>(y0 + ry) * n + x0 + 4 * v) =
-                    *reinterpret_cast<const float4*>(su + uix(ry + kH, kH + 4 * v));
+            if (core) {
+                float* uo = at<float>(A.lv[t].u2, i);
+#pragma unroll
+                for (int r = 0; r < 2; ++r)
+                    *reinterpret_cast<float4*>(uo + static_cast<size_t>(y0 - kH + sy0 + r) * n + x0 - kH + sx0) =
+                        make_float4(uu[r][0], uu[r][1], uu[r][2], uu[r][3]);
             }
         }
         // this buffer is refilled by the TMA next iteration: order the generic accesses first
@@ -359,6 +450,331 @@ __global__ void __launch_bounds__(TGeom<TX, TY, POST, RR>::threads, TGeom<TX, TY
     }
     if (threadIdx.x == 0 && !live) {
         // a wait gave up: let the tiles still in flight land before the CTA leaves
+        const uint64_t t0 = now_ns();
+        for (int k = issued - 2 < 0 ? 0 : issued - 2; k < issued; ++k)
+            while (!mbar_test(&full[k & 1], (k >> 1) & 1) && now_ns() - t0 < 1000000000ull) {
+            }
+    }
+}
+
+// Band form for sides of 128 and more: tiles of 56 x TY cells (the last tile
+// of a row shifted left to end at the domain's edge, so that it overlaps its
+// neighbour; both compute the shared cells from the same inputs in the same
+// order and write identical values), whose 64-column frame is one warp wide.
+// Warp w owns frame rows 4 w .. 4 w + 3, lane l columns 2 l, 2 l + 1: a cell's
+// left and right neighbours come from the same thread or a warp shuffle, its
+// vertical ones from the same thread except in a band's first and last row,
+// which are exchanged through shared memory. The frame edge's outer
+// neighbours (the extra ring of u) are read from shared memory in the first
+// half sweep only: later half sweeps only need them for cells that are no
+// longer exact.
+template <int TY, bool POST>
+struct BGeom {
+    static constexpr int TX = 56;
+    static constexpr int SX = TX + 2 * kH;         // 64 frame columns: 32 lanes x 2
+    static constexpr int SY = TY + 2 * kH;
+    static constexpr int XW = SX + 4;
+    static constexpr int ECX = TX / 2 + 2 * kH;
+    static constexpr int ECY = TY / 2 + 2 * kH;
+    static constexpr int UP = SX + 8;
+    static constexpr int UR = SY + 2;
+    static constexpr int bands = SY / 4;
+    static constexpr int threads = 32 * bands;
+    static constexpr int oU = 0;
+    static constexpr int oB = oU + round32(UP * UR);
+    static constexpr int oKX = oB + round32(SX * SY);
+    static constexpr int oKY = oKX + round32(XW * SY);
+    static constexpr int oE = oKY + round32((SY + 1) * SX);
+    static constexpr int buf = oE + (POST ? round32(ECX * ECY) : 0);
+    static constexpr size_t bytes = 128 + 2 * sizeof(float) * static_cast<size_t>(buf);
+    static constexpr int by_smem = static_cast<int>(kSmemPerSM / (bytes + 1024));
+    static constexpr int ctas_per_sm = by_smem < 2048 / threads ? by_smem : 2048 / threads;
+    static_assert(SX == 64 && SY % 4 == 0 && TY % 4 == 0, "one warp per 4-row band of a 64-column frame");
+    static_assert((SX * 4) % 16 == 0 && (XW * 4) % 16 == 0 && (ECX * 4) % 16 == 0 && (UP * 4) % 16 == 0,
+                  "TMA boxes: 16-byte rows");
+    static_assert(ctas_per_sm >= 1, "shared memory");
+};
+
+template <int TY, int NS, bool POST, bool RR>
+__global__ void __launch_bounds__(BGeom<TY, POST>::threads, BGeom<TY, POST>::ctas_per_sm)
+    kb_rbgs_tma_band(const __grid_constant__ Maps maps, FmgArgs A, int t, int B, int ones, int first, int zin)
+{
+    using Gm = BGeom<TY, POST>;
+    constexpr int TX = Gm::TX, SX = Gm::SX, SY = Gm::SY, XW = Gm::XW, ECX = Gm::ECX, UP = Gm::UP;
+    constexpr int kThreads = Gm::threads;
+    constexpr int HN = 2 * NS;
+    static_assert(HN <= kH, "the tile and one ring around it end exact");
+    static_assert(!(POST && RR), "the correction is fused into post-smoothing, the residual into pre-smoothing");
+    auto uix = [](int sy, int sx) { return (sy + 1) * UP + sx + 4; };
+    extern __shared__ __align__(128) unsigned char smraw[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smraw);
+    float* bufs = reinterpret_cast<float*>(smraw + 128);
+
+    const int n = A.lv[t].n;
+    const int txn = (n + TX - 1) / TX, tyn = n / TY;
+    const int per = txn * tyn;
+    const int total = B * per;
+    const float h2 = 1.0f / (static_cast<float>(n) * static_cast<float>(n));
+    const uint32_t tx_bytes =
+        4u * ((zin ? 0 : UP * Gm::UR) + XW * SY + (SY + 1) * SX + (ones ? 0 : SX * SY) + (POST ? ECX * Gm::ECY : 0));
+
+    if (threadIdx.x == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+
+    // the last tile of a row ends at the domain's edge
+    auto x_of = [&](int tx) { return tx * TX < n - TX ? tx * TX : n - TX; };
+    auto issue = [&](int i, int ty, int tx, int slot) {
+        const int x0 = x_of(tx), y0 = ty * TY;
+        float* S = bufs + slot * Gm::buf;
+        uint64_t* bar = &full[slot];
+        mbar_arrive_tx(bar, tx_bytes);
+        if (!zin) tensor_load_3d(S + Gm::oU, &maps.u, bar, x0 - kH - 4, y0 - kH - 1, i);
+        tensor_load_3d(S + Gm::oKX, &maps.kx, bar, x0 - kH, y0 - kH, i);
+        tensor_load_3d(S + Gm::oKY, &maps.ky, bar, x0 - kH, y0 - kH, i);
+        if (!ones) tensor_load_3d(S + Gm::oB, &maps.b, bar, x0 - kH, y0 - kH, i);
+        if (POST) tensor_load_3d(S + Gm::oE, &maps.e, bar, x0 / 2 - kH, y0 / 2 - kH, i);
+    };
+
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int sy0 = 4 * w, sx0 = 2 * lane;
+    const bool core = w >= kH / 4 && w < kH / 4 + TY / 4 && lane >= kH / 2 && lane < kH / 2 + TX / 2;
+
+    const TileWalk walk(txn, tyn);
+    int ci, cty, ctx;
+    walk.split(blockIdx.x, ci, cty, ctx);
+    int ni = ci, nty = cty, ntx = ctx;
+    bool live = true;
+    int issued = 0;
+    if (threadIdx.x == 0 && static_cast<int>(blockIdx.x) < total) {
+        issue(ci, cty, ctx, 0);
+        issued = 1;
+    }
+    int it = 0;
+    for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++it) {
+        const int slot = it & 1;
+        const int next = tile + gridDim.x;
+        walk.advance(ni, nty, ntx);
+        if (threadIdx.x == 0 && next < total) {
+            issue(ni, nty, ntx, slot ^ 1);
+            ++issued;
+        }
+        if (live) live = mbar_wait(&full[slot], (it >> 1) & 1, A.status, kStatusTimeout);
+        const int i = ci, x0 = x_of(ctx), y0 = cty * TY;
+        ci = ni, cty = nty, ctx = ntx;
+        if (!(A.active && !A.active[i])) {
+            float* S = bufs + slot * Gm::buf;
+            float* su = S + Gm::oU;
+            if (zin) {
+                float4* s4 = reinterpret_cast<float4*>(su);
+                for (int q = threadIdx.x; q < UP * Gm::UR / 4; q += kThreads) s4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                __syncthreads();
+            }
+            const float* sb = S + Gm::oB;
+            const float* skx = S + Gm::oKX;
+            const float* sky = S + Gm::oKY;
+
+            // the thread's 2 x 4 cells: u, x faces (w of column j = fx[r][j], e =
+            // fx[r][j + 1]), y faces (north fy[r][j], south fy[r + 1][j]), h^2 b
+            // and the reciprocal diagonal, both zero outside the domain
+            float uu[4][2], fx[4][3], fy[5][2], cb[4][2], id[4][2];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float2 v = *reinterpret_cast<const float2*>(su + uix(sy0 + r, sx0));
+                uu[r][0] = v.x, uu[r][1] = v.y;
+                const float2 kv = *reinterpret_cast<const float2*>(skx + (sy0 + r) * XW + sx0);
+                fx[r][0] = kv.x, fx[r][1] = kv.y;
+                fx[r][2] = __shfl_down_sync(kFull, kv.x, 1);
+                if (lane == 31) fx[r][2] = skx[(sy0 + r) * XW + SX];
+            }
+#pragma unroll
+            for (int j = 0; j < 5; ++j) {
+                const float2 v = *reinterpret_cast<const float2*>(sky + (sy0 + j) * SX + sx0);
+                fy[j][0] = v.x, fy[j][1] = v.y;
+            }
+            float bv[4][2];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                bv[r][0] = bv[r][1] = 1.0f;
+                if (!ones) {
+                    const float2 v = *reinterpret_cast<const float2*>(sb + (sy0 + r) * SX + sx0);
+                    bv[r][0] = v.x, bv[r][1] = v.y;
+                }
+            }
+            auto diag = [&](auto all_in) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int gy = y0 - kH + sy0 + r;
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const int gx = x0 - kH + sx0 + j;
+                        const bool in = decltype(all_in)::value || (gy >= 0 && gy < n && gx >= 0 && gx < n);
+                        const float d = fx[r][j] + fx[r][j + 1] + fy[r][j] + fy[r + 1][j];
+                        id[r][j] = in ? __fdividef(1.0f, d) : 0.0f;
+                        cb[r][j] = in ? h2 * bv[r][j] : 0.0f;
+                    }
+                }
+            };
+            if (x0 >= kH && x0 + TX + kH <= n && y0 >= kH && y0 + TY + kH <= n) diag(Flag<true>());
+            else diag(Flag<false>());
+            if constexpr (POST) {
+                // coarse-grid correction (odd reflection at the coarse boundary, as
+                // in the square-block form): the thread's two columns share the
+                // coarse column I1, its rows 0-1 and 2-3 the coarse rows I2a, I2a + 1
+                const float* se = S + Gm::oE;
+                const int nc = n >> 1;
+                const int I1 = (x0 - kH) / 2 + lane, I2a = (y0 - kH) / 2 + 2 * w;
+                // away from the coarse boundary (every parent and its neighbours
+                // inside the coarse grid) no reflection is needed
+                const bool inner = x0 >= 6 && x0 + TX + 6 <= n && y0 >= 6 && y0 + TY + 6 <= n;
+                auto correct = [&](auto reflect) {
+                    constexpr bool R = decltype(reflect)::value;
+                    if (R && (I1 < 0 || I1 >= nc)) return;
+                    const float* sc = se + (2 * w + 1) * ECX + lane + 1;  // coarse (I2a - 1, I1 - 1)
+                    float C[4][3];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 3; ++b) C[a][b] = sc[a * ECX + b];
+                    const bool lo1 = R && I1 == 0, hi1 = R && I1 == nc - 1;
+#pragma unroll
+                    for (int pr = 0; pr < 2; ++pr) {
+                        const int I2 = I2a + pr;
+                        if (R && (I2 < 0 || I2 >= nc)) continue;
+                        const bool lo2 = R && I2 == 0, hi2 = R && I2 == nc - 1;
+                        float E[3][3];
+#pragma unroll
+                        for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                const bool ry = (dy < 0 && lo2) || (dy > 0 && hi2);
+                                const bool rx = (dx < 0 && lo1) || (dx > 0 && hi1);
+                                const float a = rx ? C[pr + 1 + dy][1] : C[pr + 1 + dy][1 + dx];
+                                const float b = rx ? C[pr + 1][1] : C[pr + 1][1 + dx];
+                                const float v = ry ? b : a;
+                                E[dy + 1][dx + 1] = (ry != rx) ? -v : v;
+                            }
+                        }
+#pragma unroll
+                        for (int fy2 = 0; fy2 < 2; ++fy2) {
+#pragma unroll
+                            for (int fx2 = 0; fx2 < 2; ++fx2) {
+                                const int dy = 2 * fy2, dx = 2 * fx2;
+                                uu[2 * pr + fy2][fx2] +=
+                                    fmaf(0.5625f, E[1][1], fmaf(0.1875f, E[1][dx] + E[dy][1], 0.0625f * E[dy][dx]));
+                            }
+                        }
+                    }
+                };
+                if (inner) correct(Flag<false>());
+                else correct(Flag<true>());
+                *reinterpret_cast<float2*>(su + uix(sy0, sx0)) = make_float2(uu[0][0], uu[0][1]);
+                *reinterpret_cast<float2*>(su + uix(sy0 + 3, sx0)) = make_float2(uu[3][0], uu[3][1]);
+                __syncthreads();
+            }
+
+            auto upd = [&](int r, int j, float uw, float ue, float un, float us) {
+                float acc = cb[r][j];
+                acc += fx[r][j] * uw;
+                acc += fx[r][j + 1] * ue;
+                acc += fy[r][j] * un;
+                acc += fy[r + 1][j] * us;
+                uu[r][j] = acc * id[r][j];
+            };
+            // half sweep of colour C: in row r of the band the cell of column
+            // j = (C + r) % 2; edge: read the frame's outer ring (first half sweep)
+            auto half = [&](auto colour, bool edge) {
+                constexpr int C = decltype(colour)::value;
+                float side[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    if (((C + r) & 1) == 0) {
+                        side[r] = __shfl_up_sync(kFull, uu[r][1], 1);  // west neighbour of column 0
+                        if (edge && lane == 0) side[r] = su[uix(sy0 + r, -1)];
+                    } else {
+                        side[r] = __shfl_down_sync(kFull, uu[r][0], 1);  // east neighbour of column 1
+                        if (edge && lane == 31) side[r] = su[uix(sy0 + r, SX)];
+                    }
+                }
+                const float above = su[uix(sy0 - 1, sx0 + C)];
+                const float below = su[uix(sy0 + 4, sx0 + 1 - C)];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int j = (C + r) & 1;
+                    const float uw = j == 0 ? side[r] : uu[r][0];
+                    const float ue = j == 0 ? uu[r][1] : side[r];
+                    const float un = r == 0 ? above : uu[r > 0 ? r - 1 : 0][j];
+                    const float us = r == 3 ? below : uu[r < 3 ? r + 1 : 3][j];
+                    upd(r, j, uw, ue, un, us);
+                }
+                *reinterpret_cast<float2*>(su + uix(sy0, sx0)) = make_float2(uu[0][0], uu[0][1]);
+                *reinterpret_cast<float2*>(su + uix(sy0 + 3, sx0)) = make_float2(uu[3][0], uu[3][1]);
+                __syncthreads();
+            };
+#pragma unroll
+            for (int ph = 0; ph < HN; ++ph) {
+                if ((first + ph) & 1) half(Colour<1>(), ph == 0);
+                else half(Colour<0>(), ph == 0);
+            }
+            if constexpr (RR) {
+                // residual b - A u (flux form, u = 0 across the boundary, where the
+                // face holds 2 k) and its 2 x 2 restriction (the right-hand side of
+                // level t - 1). The colour of the last half sweep has a zero
+                // residual (its update solved each of its equations with the other
+                // colour fixed), so only the other colour's cells are formed: in
+                // row r the cell of column (L + 1 + r) % 2, L the last colour.
+                auto restrict_rr = [&](auto last) {
+                    constexpr int L = decltype(last)::value;
+                    float side[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        side[r] = ((L + 1 + r) & 1) == 0 ? __shfl_up_sync(kFull, uu[r][1], 1)
+                                                         : __shfl_down_sync(kFull, uu[r][0], 1);
+                    const float above = su[uix(sy0 - 1, sx0 + ((L + 1) & 1))];
+                    const float below = su[uix(sy0 + 4, sx0 + (L & 1))];
+                    if (core) {
+                        const float ih2 = static_cast<float>(n) * static_cast<float>(n);
+                        float res[4];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            const int j = (L + 1 + r) & 1;
+                            const float up = uu[r][j];
+                            const float uw = j == 0 ? side[r] : uu[r][0];
+                            const float ue = j == 0 ? uu[r][1] : side[r];
+                            const float un = r == 0 ? above : uu[r > 0 ? r - 1 : 0][j];
+                            const float us = r == 3 ? below : uu[r < 3 ? r + 1 : 3][j];
+                            float acc = fx[r][j] * (up - uw);
+                            acc += fx[r][j + 1] * (up - ue);
+                            acc += fy[r][j] * (up - un);
+                            acc += fy[r + 1][j] * (up - us);
+                            res[r] = (cb[r][j] - acc) * ih2;
+                        }
+                        const int nc = n >> 1;
+                        float* bco = at<float>(A.lv[t - 1].bc, i);
+#pragma unroll
+                        for (int pr = 0; pr < 2; ++pr)
+                            bco[static_cast<size_t>((y0 - kH) / 2 + 2 * w + pr) * nc + (x0 - kH) / 2 + lane] =
+                                0.25f * (res[2 * pr] + res[2 * pr + 1]);
+                    }
+                };
+                if ((first + HN - 1) & 1) restrict_rr(Colour<1>());
+                else restrict_rr(Colour<0>());
+            }
+            if (core) {
+                float* uo = at<float>(A.lv[t].u2, i);
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    *reinterpret_cast<float2*>(uo + static_cast<size_t>(y0 - kH + sy0 + r) * n + x0 - kH + sx0) =
+                        make_float2(uu[r][0], uu[r][1]);
+            }
+        }
+        fence_proxy_async();
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && !live) {
         const uint64_t t0 = now_ns();
         for (int k = issued - 2 < 0 ? 0 : issued - 2; k < issued; ++k)
             while (!mbar_test(&full[k & 1], (k >> 1) & 1) && now_ns() - t0 < 1000000000ull) {
@@ -399,25 +815,30 @@ template <int TX, int TY, int NS, bool POST, bool RR = false>
 bool attr()
 {
     return cudaFuncSetAttribute(kb_rbgs_tma<TX, TY, NS, POST, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(TGeom<TX, TY, POST, RR>::bytes)) == cudaSuccess;
+                                static_cast<int>(TGeom<TX, TY, POST>::bytes)) == cudaSuccess;
 }
 
-// Tile shapes: pre-smoothing (with or without the restricted residual) in
-// 64 x 32 tiles of 512 threads where the side allows (less halo and ring per
-// cell, half the barriers per cell), else 32 x 32; post-smoothing with the
-// fused correction in 32 x 32 tiles of 256 threads (its extra registers).
+template <int TY, int NS, bool POST, bool RR = false>
+bool battr()
+{
+    return cudaFuncSetAttribute(kb_rbgs_tma_band<TY, NS, POST, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(BGeom<TY, POST>::bytes)) == cudaSuccess;
+}
+
+// Square-block form (32 x 32 tiles, 224 threads) for sides below 128; band
+// form (56 x 32 tiles, 320 threads) from 128 on.
 bool attrs()
 {
     return attr<32, 32, 1, false>() && attr<32, 32, 1, true>() && attr<32, 32, 2, false>() &&
            attr<32, 32, 2, true>() && attr<32, 32, 1, false, true>() && attr<32, 32, 2, false, true>() &&
-           attr<64, 32, 1, false>() && attr<64, 32, 2, false>() && attr<64, 32, 1, false, true>() &&
-           attr<64, 32, 2, false, true>();
+           battr<32, 1, false>() && battr<32, 1, true>() && battr<32, 2, false>() && battr<32, 2, true>() &&
+           battr<32, 1, false, true>() && battr<32, 2, false, true>();
 }
 
 template <int TX, int TY, int NS, bool POST, bool RR>
 bool run(const FmgArgs& A, int t, int n, int B, int ones, int first, int zin, int sm_count, cudaStream_t st)
 {
-    using Gm = TGeom<TX, TY, POST, RR>;
+    using Gm = TGeom<TX, TY, POST>;
     const LevelDesc& L = A.lv[t];
     Maps m;
     std::memset(&m, 0, sizeof(m));
@@ -435,15 +856,37 @@ bool run(const FmgArgs& A, int t, int n, int B, int ones, int first, int zin, in
     return cudaGetLastError() == cudaSuccess;
 }
 
+template <int TY, int NS, bool POST, bool RR>
+bool run_band(const FmgArgs& A, int t, int n, int B, int ones, int first, int zin, int sm_count, cudaStream_t st)
+{
+    using Gm = BGeom<TY, POST>;
+    const LevelDesc& L = A.lv[t];
+    Maps m;
+    std::memset(&m, 0, sizeof(m));
+    const uint64_t un = static_cast<uint64_t>(n), ub = static_cast<uint64_t>(B);
+    const bool ok = encode_3d(&m.u, L.u, un, un, un, ub, Gm::UP, Gm::UR) &&
+                    encode_3d(&m.kx, L.kx, un + 4, static_cast<uint64_t>(kx_pitch(n)), un, ub, Gm::XW, Gm::SY) &&
+                    encode_3d(&m.ky, L.ky, un, un, un + 1, ub, Gm::SX, Gm::SY + 1) &&
+                    (ones || encode_3d(&m.b, L.bc, un, un, un, ub, Gm::SX, Gm::SY)) &&
+                    (!POST || encode_3d(&m.e, A.lv[t - 1].u, un / 2, un / 2, un / 2, ub, Gm::ECX, Gm::ECY));
+    if (!ok) return false;
+    const int tiles = B * ((n + Gm::TX - 1) / Gm::TX) * (n / TY);
+    const int cap = Gm::ctas_per_sm * sm_count;
+    kb_rbgs_tma_band<TY, NS, POST, RR>
+        <<<tiles < cap ? tiles : cap, Gm::threads, Gm::bytes, st>>>(m, A, t, B, ones, first, zin);
+    return cudaGetLastError() == cudaSuccess;
+}
+
 template <int NS>
 bool go(const FmgArgs& A, int t, int n, int B, int ones, int first, bool post, int zin, bool rr, int sm_count,
         cudaStream_t st)
 {
-    if (post) return run<32, 32, NS, true, false>(A, t, n, B, ones, first, 0, sm_count, st);
-    if (n % 64 == 0 && n >= 128) {  // every box (up to 80 columns) within the level's extent
-        if (rr) return run<64, 32, NS, false, true>(A, t, n, B, ones, first, zin, sm_count, st);
-        return run<64, 32, NS, false, false>(A, t, n, B, ones, first, zin, sm_count, st);
+    if (n >= 128) {  // every box (up to 72 columns) within the level's extent
+        if (post) return run_band<32, NS, true, false>(A, t, n, B, ones, first, 0, sm_count, st);
+        if (rr) return run_band<32, NS, false, true>(A, t, n, B, ones, first, zin, sm_count, st);
+        return run_band<32, NS, false, false>(A, t, n, B, ones, first, zin, sm_count, st);
     }
+    if (post) return run<32, 32, NS, true, false>(A, t, n, B, ones, first, 0, sm_count, st);
     if (rr) return run<32, 32, NS, false, true>(A, t, n, B, ones, first, zin, sm_count, st);
     return run<32, 32, NS, false, false>(A, t, n, B, ones, first, zin, sm_count, st);
 }
