@@ -9,6 +9,7 @@
 
 #include <cstdint>
 
+#include "fastdiv.h"
 #include "mlqmc_internal.h"
 
 namespace mlqmc_dev {
@@ -30,7 +31,23 @@ struct ArrDesc {
 struct LevelDesc {
     int n;
     ArrDesc u, bc, kx, ky, idiag, k, G, u64, u2;  // u2: ping-pong partner of u for the tiled smoother
+    // dividers of a flat cell index (nc = n / 2, nq = n / 4, Ka the KL groups)
+    FastDiv by_n, by_nc, by_nq, by_nn, by_ncnc, by_nnc, by_nnq, by_kan;
 };
+
+// Fill the dividers of level descriptor d (d.n set), on the host.
+inline void set_divisors(LevelDesc& d, int Ka)
+{
+    const uint32_t n = static_cast<uint32_t>(d.n), nc = n / 2 > 0 ? n / 2 : 1, nq = n / 4 > 0 ? n / 4 : 1;
+    d.by_n = FastDiv(n);
+    d.by_nc = FastDiv(nc);
+    d.by_nq = FastDiv(nq);
+    d.by_nn = FastDiv(n * n);
+    d.by_ncnc = FastDiv(nc * nc);
+    d.by_nnc = FastDiv(n * nc);
+    d.by_nnq = FastDiv(n * nq);
+    d.by_kan = FastDiv(static_cast<uint32_t>(Ka > 0 ? Ka : 1) * n);
+}
 
 template <typename T>
 struct Lv {
@@ -546,6 +563,45 @@ __device__ __forceinline__ float narrow(double x)
     const uint32_t mag = static_cast<uint32_t>((r >> 29) - (896ull << 23));
     return __uint_as_float(mag | sgn);
 }
+
+static __device__ __noinline__ float narrow_rest_rare(double x, float hi)
+{
+    return __double2float_rn(x - static_cast<double>(hi));
+}
+
+// x - narrow(x) rounded to FP32, from the bits of x: the 29 significand bits
+// that narrow() drops, less 2^29 when it rounded up, times 2^(e - 1075) (e the
+// biased exponent of x); exact before that last rounding, which errs by at
+// most 2^-48 |x|. Exponents below 949 (|x| < 2^-74) or outside narrow()'s
+// integer path take an FP64 subtraction (out of line).
+__device__ __forceinline__ float narrow_rest(double x, float hi)
+{
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned long long a = b & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned e = static_cast<unsigned>(a >> 52);
+    if (e < 949u || e > 1150u) return narrow_rest_rare(x, hi);
+    const uint32_t low = static_cast<uint32_t>(a & 0x1FFFFFFFull);
+    const uint32_t up = (low + 0x0FFFFFFFu + (static_cast<uint32_t>(a >> 29) & 1u)) >> 29;
+    const int d = static_cast<int>(low) - static_cast<int>(up << 29);
+    const float mag = static_cast<float>(d) * __uint_as_float((e - 948u) << 23);
+    return (b >> 63) ? -mag : mag;
+}
+
+// Running sum of FP64 values given as FP32 pairs (hi, lo), x = hi + lo: hi
+// added by TwoSum (the rounding error kept), the errors and the lo parts
+// added in FP32. For k values the error is within about k 2^-48 of their
+// magnitudes' sum, without the FP64 pipe.
+struct PairSum {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float h, float l)
+    {
+        const float s = hi + h;
+        const float bb = s - hi;
+        lo += ((hi - (s - bb)) + (h - bb)) + l;
+        hi = s;
+    }
+    __device__ __forceinline__ double value() const { return widen(hi) + widen(lo); }
+};
 
 // Error-free transformations in FP32: Knuth's TwoSum (a + b = s + e exactly)
 // and the product error by one FMA (a b = p + e exactly), the building blocks

@@ -427,9 +427,9 @@ __global__ void kb_synth_G(FmgArgs A, int t, int B)
     const uint32_t per = static_cast<uint32_t>(A.Ka) * static_cast<uint32_t>(n);
     GRID_STRIDE(idx, B * per)
     {
-        const int i = static_cast<int>(idx / per);
+        const int i = static_cast<int>(A.lv[t].by_kan.div(idx));
         const int rem = static_cast<int>(idx - i * per);
-        const int a = rem / n;
+        const int a = static_cast<int>(A.lv[t].by_n.div(rem));
         const int i2 = rem - a * n;
         T acc = T(0);
         const int g1 = A.grp_start[a + 1];
@@ -468,9 +468,9 @@ __global__ void kb_synth_z(FmgArgs A, int t, int B)
     const uint32_t per = static_cast<uint32_t>(n) * static_cast<uint32_t>(n);
     GRID_STRIDE(idx, B * per)
     {
-        const int i = static_cast<int>(idx / per);
+        const int i = static_cast<int>(A.lv[t].by_nn.div(idx));
         const int p = static_cast<int>(idx - i * per);
-        const int i2 = p / n;
+        const int i2 = static_cast<int>(A.lv[t].by_n.div(p));
         const int i1 = p - i2 * n;
         const T* G = at<T>(A.lv[t].G, i);
         T z = T(0);
@@ -529,14 +529,12 @@ __global__ void kb_faces(FmgArgs A, int t, int B)
     // one cell per thread: its west x face and north y face, plus the east
     // boundary face in the last column and the south one in the last row
     const int n = A.lv[t].n;
-    const bool pow2 = (n & (n - 1)) == 0;
-    const int lg = __ffs(n) - 1;
     const uint32_t per = static_cast<uint32_t>(n) * static_cast<uint32_t>(n);
     GRID_STRIDE(idx, B * per)
     {
-        const int i = pow2 ? static_cast<int>(idx >> (2 * lg)) : static_cast<int>(idx / per);
+        const int i = static_cast<int>(A.lv[t].by_nn.div(idx));
         const int p = static_cast<int>(idx - i * per);
-        const int i2 = pow2 ? p >> lg : p / n;
+        const int i2 = static_cast<int>(A.lv[t].by_n.div(p));
         const int i1 = p - i2 * n;
         const T* k = at<T>(A.lv[t].k, i);
         T* kx = at<T>(A.lv[t].kx, i) + i2 * kx_pitch(n);
@@ -560,9 +558,9 @@ __global__ void kb_faces4(FmgArgs A, int t, int B)
     const uint32_t per = static_cast<uint32_t>(n) * static_cast<uint32_t>(q);
     GRID_STRIDE(idx, B * per)
     {
-        const int i = static_cast<int>(idx / per);
+        const int i = static_cast<int>(A.lv[t].by_nnq.div(idx));
         const int p4 = static_cast<int>(idx - i * per);
-        const int i2 = p4 / q;
+        const int i2 = static_cast<int>(A.lv[t].by_nq.div(p4));
         const int i1 = (p4 - i2 * q) * 4;
         const float* k = at<float>(A.lv[t].k, i);
         float* kx = at<float>(A.lv[t].kx, i) + i2 * kx_pitch(n);
@@ -592,9 +590,9 @@ __global__ void kb_idiag(FmgArgs A, int t, int B)
     const uint32_t per = static_cast<uint32_t>(n) * static_cast<uint32_t>(n);
     GRID_STRIDE(idx, B * per)
     {
-        const int i = static_cast<int>(idx / per);
+        const int i = static_cast<int>(A.lv[t].by_nn.div(idx));
         const int p = static_cast<int>(idx - i * per);
-        const int i2 = p / n;
+        const int i2 = static_cast<int>(A.lv[t].by_n.div(p));
         at<T>(A.lv[t].idiag, i)[p] = inv_diag(at<T>(A.lv[t].kx, i), at<T>(A.lv[t].ky, i), n, p - i2 * n, i2);
     }
 }
@@ -609,10 +607,10 @@ __global__ void kb_gs(FmgArgs A, int t, int B, int colour, int ones)
     const T h2 = T(1) / (T(n) * T(n));
     GRID_STRIDE(idx, B * per)
     {
-        const int i = static_cast<int>(idx / per);
+        const int i = static_cast<int>(A.lv[t].by_nnc.div(idx));
         if (inactive(A, i)) continue;
         const int q = static_cast<int>(idx - i * per);
-        const int i2 = q / half;
+        const int i2 = static_cast<int>(A.lv[t].by_nc.div(q));
         const Lv<T> L = view<T>(A, t, i);
         gs_cell(L, ones ? nullptr : L.bc, h2, 2 * (q - i2 * half) + ((i2 + colour) & 1), i2);
     }
@@ -737,10 +735,10 @@ __global__ void kb_resid_restrict(FmgArgs A, int t, int B, int ones)
     const uint32_t per = static_cast<uint32_t>(nc) * static_cast<uint32_t>(nc);
     GRID_STRIDE(idx, B * per)
     {
-        const int i = static_cast<int>(idx / per);
+        const int i = static_cast<int>(A.lv[t].by_ncnc.div(idx));
         if (inactive(A, i)) continue;
         const int q = static_cast<int>(idx - i * per);
-        const int I2 = q / nc;
+        const int I2 = static_cast<int>(A.lv[t].by_nc.div(q));
         const Lv<T> F = view<T>(A, t, i);
         at<T>(A.lv[t - 1].bc, i)[q] = resid_restrict_cell(F, ones ? nullptr : F.bc, q - I2 * nc, I2);
     }
@@ -785,10 +783,10 @@ __global__ void kb_prolong(FmgArgs A, int t, int B)
     const uint32_t per = static_cast<uint32_t>(nc) * static_cast<uint32_t>(nc);
     GRID_STRIDE(idx, B * per)
     {
-        const int i = static_cast<int>(idx / per);
+        const int i = static_cast<int>(A.lv[t].by_ncnc.div(idx));
         if (inactive(A, i)) continue;
         const int q = static_cast<int>(idx - i * per);
-        const int I2 = q / nc;
+        const int I2 = static_cast<int>(A.lv[t].by_nc.div(q));
         const int I1 = q - I2 * nc;
         const size_t o = static_cast<size_t>(2 * I2) * n + 2 * I1;
         if constexpr (U64) {
@@ -830,10 +828,10 @@ __global__ void kb_resid64(FmgArgs A, int t, int B)
     const double ih2 = static_cast<double>(n) * n;
     GRID_STRIDE(idx, B * per)
     {
-        const int i = static_cast<int>(idx / per);
+        const int i = static_cast<int>(A.lv[t].by_nn.div(idx));
         if (inactive(A, i)) continue;
         const int p = static_cast<int>(idx - i * per);
-        const int i2 = p / n;
+        const int i2 = static_cast<int>(A.lv[t].by_n.div(p));
         const Lv<T> L = view<T>(A, t, i);
         L.bc[p] = to_work<T>(resid64_cell(L, ih2, p - i2 * n, i2));
     }
@@ -847,7 +845,7 @@ __global__ void kb_resid64(FmgArgs A, int t, int B)
 // is formed with FP32 error-free transformations (resid_f32x2) to within a
 // few units of 2^-48 of the terms, as accurate as the FP64 evaluation of
 // kb_resid64 before r is rounded to FP32, and without the FP64 pipe.
-__global__ void kb_prolong_resid64(FmgArgs A, int t, int B)
+__global__ void __launch_bounds__(256, 5) kb_prolong_resid64(FmgArgs A, int t, int B)
 {
     // one thread per coarse cell (I1, I2), i.e. per 2 x 2 quad of fine cells:
     // the quad and its ring of 8 fine neighbours all interpolate from the
@@ -859,10 +857,10 @@ __global__ void kb_prolong_resid64(FmgArgs A, int t, int B)
     const float ih2 = static_cast<float>(n) * static_cast<float>(n);  // exact: n = coarse_cells 2^t
     GRID_STRIDE(idx, B * per)
     {
-        const int i = static_cast<int>(idx / per);
+        const int i = static_cast<int>(A.lv[t].by_ncnc.div(idx));
         if (inactive(A, i)) continue;
         const int q = static_cast<int>(idx - i * per);
-        const int I2 = q / nc, I1 = q - I2 * nc;
+        const int I2 = static_cast<int>(A.lv[t].by_nc.div(q)), I1 = q - I2 * nc;
         const float* e = at<float>(A.lv[t - 1].u, i);
         const Lv<float> L = view<float>(A, t, i);
         float E[3][3];  // E[dy + 1][dx + 1]
@@ -936,7 +934,7 @@ __global__ void kb_update64(FmgArgs A, int t, int B)
     const uint32_t per = static_cast<uint32_t>(n) * static_cast<uint32_t>(n);
     GRID_STRIDE(idx, B * per)
     {
-        const int i = static_cast<int>(idx / per);
+        const int i = static_cast<int>(A.lv[t].by_nn.div(idx));
         if (inactive(A, i)) continue;
         const int p = static_cast<int>(idx - i * per);
         at<double>(A.lv[t].u64, i)[p] += widen(at<T>(A.lv[t].u, i)[p]);
@@ -961,7 +959,7 @@ __global__ void __launch_bounds__(256) kb_resnorm_part(FmgArgs A, int t, int B, 
         const int p1 = min(nn, (q + 1) * csz);
         double acc = 0.0;
         for (int p = q * csz + static_cast<int>(threadIdx.x); p < p1; p += blockDim.x) {
-            const int i2 = p / n;
+            const int i2 = static_cast<int>(A.lv[t].by_n.div(p));
             const double r = resid64_cell(L, ih2, p - i2 * n, i2);
             L.bc[p] = to_work<T>(r);
             acc += r * r;
@@ -1128,6 +1126,8 @@ __global__ void __launch_bounds__(256) kb_qoi_part(FmgArgs A, int t, int B, int 
         const int p0 = q * csz, p1 = min(np, p0 + csz);
         double acc = 0.0;
         if constexpr (U64) {
+            // mixed forms: the sum from the FP32 copy and its remainder (PairSum)
+            PairSum ps;
             double2* u64 = reinterpret_cast<double2*>(at<double>(A.lv[t].u64, i));
             float2* u = reinterpret_cast<float2*>(at<float>(A.lv[t].u, i));
             constexpr int U = 4;
@@ -1146,9 +1146,15 @@ __global__ void __launch_bounds__(256) kb_qoi_part(FmgArgs A, int t, int B, int 
                         r[k] = make_double2(r[k].x + widen(d[k].x), r[k].y + widen(d[k].y));
                         u64[p + k * kT] = r[k];
                     }
-                    if constexpr (sizeof(T) == 4) u[p + k * kT] = make_float2(narrow(r[k].x), narrow(r[k].y));
-                    acc += r[k].x;
-                    acc += r[k].y;
+                    if constexpr (sizeof(T) == 4) {
+                        const float2 h = make_float2(narrow(r[k].x), narrow(r[k].y));
+                        u[p + k * kT] = h;
+                        ps.add(h.x, narrow_rest(r[k].x, h.x));
+                        ps.add(h.y, narrow_rest(r[k].y, h.y));
+                    } else {
+                        acc += r[k].x;
+                        acc += r[k].y;
+                    }
                 }
             }
             for (; p < p1; p += kT) {
@@ -1158,10 +1164,17 @@ __global__ void __launch_bounds__(256) kb_qoi_part(FmgArgs A, int t, int B, int 
                     r = make_double2(r.x + widen(d.x), r.y + widen(d.y));
                     u64[p] = r;
                 }
-                if constexpr (sizeof(T) == 4) u[p] = make_float2(narrow(r.x), narrow(r.y));
-                acc += r.x;
-                acc += r.y;
+                if constexpr (sizeof(T) == 4) {
+                    const float2 h = make_float2(narrow(r.x), narrow(r.y));
+                    u[p] = h;
+                    ps.add(h.x, narrow_rest(r.x, h.x));
+                    ps.add(h.y, narrow_rest(r.y, h.y));
+                } else {
+                    acc += r.x;
+                    acc += r.y;
+                }
             }
+            if constexpr (sizeof(T) == 4) acc = ps.value();
         } else {
             const T* u = at<T>(A.lv[t].u, i);
             for (int p = p0 + static_cast<int>(threadIdx.x); p < p1; p += kT) {
@@ -1209,7 +1222,7 @@ __global__ void kb_k_out(FmgArgs A, int t, int B, double* out)
     const uint32_t per = static_cast<uint32_t>(n) * static_cast<uint32_t>(n);
     GRID_STRIDE(idx, B * per)
     {
-        const int i = static_cast<int>(idx / per);
+        const int i = static_cast<int>(A.lv[t].by_nn.div(idx));
         const int p = static_cast<int>(idx - i * per);
         out[static_cast<size_t>(A.samples[i].canon) * per + p] = static_cast<double>(at<T>(A.lv[t].k, i)[p]);
     }
@@ -1368,6 +1381,7 @@ FmgArgs base_args(mlqmc_ctx* c)
         const LevelPool& P = c->pools[t];
         LevelDesc& d = A.lv[t];
         d.n = c->p.coarse_cells << t;
+        set_divisors(d, c->Ka);
         ArrDesc* arr[kPoolArrs] = {&d.u, &d.bc, &d.kx, &d.ky, &d.idiag, &d.k, &d.G, &d.u64, &d.u2};
         for (int a = 0; a < kPoolArrs; ++a) {
             arr[a]->base = P.mem ? P.mem + P.off[a] : nullptr;
@@ -1903,13 +1917,16 @@ mlqmc_status correct_postsmooth(mlqmc_ctx* c, FmgArgs& A, int t, int B, int top_
 }
 
 template <typename T>
-mlqmc_status vcycle_batched(mlqmc_ctx* c, FmgArgs& A, int t_top, int B, bool ones, cudaStream_t st)
+mlqmc_status vcycle_batched(mlqmc_ctx* c, FmgArgs& A, int t_top, int B, bool ones, cudaStream_t st,
+                            bool top_zero = false)
 {
     for (int t = t_top; t >= 1; --t) {
         const int top_ones = (t == t_top && ones) ? 1 : 0;
-        // a correction level starts from zero: cleared here, or by its smoother
-        const bool zin = t < t_top && zero_in_smoother<T>(c, t, B);
-        if (t < t_top && !zin && zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
+        // a correction level (and, top_zero, the top level: the first cycle of a
+        // refinement step) starts from zero: cleared here, or by its smoother
+        const bool zero_entry = t < t_top || top_zero;
+        const bool zin = zero_entry && zero_in_smoother<T>(c, t, B);
+        if (zero_entry && !zin && zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
         if (presmooth_restrict<T>(c, A, t, B, top_ones, st, zin) != MLQMC_OK) return MLQMC_ERR_CUDA;
     }
     {
@@ -1986,8 +2003,7 @@ mlqmc_status converge_device(mlqmc_ctx* c, FmgArgs& A, int t, int B, int P, cuda
         return MLQMC_ERR_CUDA;
     G.in_body = true;
     A.active = c->d_active;
-    s = zero_u(c, t, B, bs);
-    for (int m = 0; m < c->p.mu0 && s == MLQMC_OK; ++m) s = vcycle_batched<T>(c, A, t, B, false, bs);
+    for (int m = 0; m < c->p.mu0 && s == MLQMC_OK; ++m) s = vcycle_batched<T>(c, A, t, B, false, bs, m == 0);
     if (s == MLQMC_OK) {
         Timed tm(c, kProfTransfer, bs, work_of<double>(B * (16.0 + es) * Mc, B * Mc));
         kb_update64<T><<<grid_for(c, B * n * n), 256, 0, bs>>>(A, t, B);
@@ -2044,8 +2060,8 @@ mlqmc_status converge_batched(mlqmc_ctx* c, FmgArgs& A, int t, int B, cudaStream
             break;
         }
         A.active = c->d_active;
-        mlqmc_status s = zero_u(c, t, B, st);
-        for (int m = 0; m < c->p.mu0 && s == MLQMC_OK; ++m) s = vcycle_batched<T>(c, A, t, B, false, st);
+        mlqmc_status s = MLQMC_OK;
+        for (int m = 0; m < c->p.mu0 && s == MLQMC_OK; ++m) s = vcycle_batched<T>(c, A, t, B, false, st, m == 0);
         if (s == MLQMC_OK) {
             Timed tm(c, kProfTransfer, st, work_of<double>(B * (16.0 + es) * Mc, B * Mc));
             kb_update64<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
@@ -2090,9 +2106,8 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
             }
         }
         if (refine) {
-            if (zero_u(c, t, B, st) != MLQMC_OK) return MLQMC_ERR_CUDA;
             for (int m = 0; m < c->p.mu0; ++m) {
-                mlqmc_status s = vcycle_batched<T>(c, A, t, B, false, st);
+                mlqmc_status s = vcycle_batched<T>(c, A, t, B, false, st, m == 0);
                 if (s != MLQMC_OK) return s;
             }
             if (!fuse_update) {
@@ -3365,6 +3380,7 @@ extern "C" mlqmc_status mlqmc_fmg_fields_noalloc(int32_t coarse_cells, int32_t n
     for (int t = 0; t < n_levels; ++t) {
         LevelDesc& d = A.lv[t];
         d.n = coarse_cells << t;
+        set_divisors(d, A.Ka);
         ArrDesc* arr[kPoolArrs] = {&d.u, &d.bc, &d.kx, &d.ky, &d.idiag, &d.k, &d.G, &d.u64, &d.u2};
         for (int a = 0; a < kPoolArrs; ++a) {
             arr[a]->base = scratch + offs[t][a];
