@@ -835,6 +835,30 @@ bool attrs()
            battr<32, 1, false, true>() && battr<32, 2, false, true>();
 }
 
+// Persistent grid for `per` tiles per sample. A CTA takes every grid-th tile,
+// so it visits per / gcd(grid, per) tile positions in turn; when that cycle
+// is short (the capacity a multiple of a large part of `per`, e.g. 304 CTAs
+// for the 608 tiles of a 1024 x 1024 level) the CTAs holding edge tiles
+// (domain tests, reflections, the shifted last tile) hold them in every
+// sample and set the launch's length. Then the largest count up to the
+// capacity that shares no factor with `per` is taken instead.
+int grid_of(int tiles, int per, int cap)
+{
+    if (tiles <= cap) return tiles;
+    auto gcd = [](int a, int b) {
+        while (b) {
+            const int r = a % b;
+            a = b;
+            b = r;
+        }
+        return a;
+    };
+    if (per / gcd(cap, per) >= 8) return cap;
+    for (int g = cap; g > cap - 32 && g > 0; --g)
+        if (gcd(g, per) == 1) return g;
+    return cap;
+}
+
 template <int TX, int TY, int NS, bool POST, bool RR>
 bool run(const FmgArgs& A, int t, int n, int B, int ones, int first, int zin, int sm_count, cudaStream_t st)
 {
@@ -849,10 +873,9 @@ bool run(const FmgArgs& A, int t, int n, int B, int ones, int first, int zin, in
                     (ones || encode_3d(&m.b, L.bc, un, un, un, ub, Gm::SX, Gm::SY)) &&
                     (!POST || encode_3d(&m.e, A.lv[t - 1].u, un / 2, un / 2, un / 2, ub, Gm::ECX, Gm::ECY));
     if (!ok) return false;
-    const int tiles = B * (n / TX) * (n / TY);
-    const int cap = Gm::ctas_per_sm * sm_count;
-    kb_rbgs_tma<TX, TY, NS, POST, RR>
-        <<<tiles < cap ? tiles : cap, Gm::threads, Gm::bytes, st>>>(m, A, t, B, ones, first, zin);
+    const int per = (n / TX) * (n / TY);
+    kb_rbgs_tma<TX, TY, NS, POST, RR><<<grid_of(B * per, per, Gm::ctas_per_sm * sm_count), Gm::threads, Gm::bytes,
+                                        st>>>(m, A, t, B, ones, first, zin);
     return cudaGetLastError() == cudaSuccess;
 }
 
@@ -870,10 +893,9 @@ bool run_band(const FmgArgs& A, int t, int n, int B, int ones, int first, int zi
                     (ones || encode_3d(&m.b, L.bc, un, un, un, ub, Gm::SX, Gm::SY)) &&
                     (!POST || encode_3d(&m.e, A.lv[t - 1].u, un / 2, un / 2, un / 2, ub, Gm::ECX, Gm::ECY));
     if (!ok) return false;
-    const int tiles = B * ((n + Gm::TX - 1) / Gm::TX) * (n / TY);
-    const int cap = Gm::ctas_per_sm * sm_count;
-    kb_rbgs_tma_band<TY, NS, POST, RR>
-        <<<tiles < cap ? tiles : cap, Gm::threads, Gm::bytes, st>>>(m, A, t, B, ones, first, zin);
+    const int per = ((n + Gm::TX - 1) / Gm::TX) * (n / TY);
+    kb_rbgs_tma_band<TY, NS, POST, RR><<<grid_of(B * per, per, Gm::ctas_per_sm * sm_count), Gm::threads, Gm::bytes,
+                                         st>>>(m, A, t, B, ones, first, zin);
     return cudaGetLastError() == cudaSuccess;
 }
 
