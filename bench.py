@@ -201,11 +201,13 @@ def sources_digest(files=None):
 
 
 def measured_traffic(form, kernel, n):
-    """DRAM bytes per sample of a launch of `kernel` on an n x n level in
-    `form`, from the committed record of one-kernel ncu captures on a small
-    case (profiles/dram_traffic.json; the capture commands and the scaling are
-    in profiles/). None when absent or when the kernel's source files differ
-    from those the record was taken on."""
+    """DRAM bytes per algorithmic byte of `kernel` on an n x n level in `form`:
+    the ratio over one-kernel ncu captures on a small case (the capture
+    commands and the algorithmic bytes of each captured launch are in the
+    record, profiles/dram_traffic.json); the traffic of a launch in the timed
+    step is that ratio times its algorithmic bytes, i.e. the captured traffic
+    scaled by the cells processed. None when absent or when the kernel's
+    source files differ from those the record was taken on."""
     try:
         with open(TRAFFIC_FILE) as f:
             rec = json.load(f)
@@ -214,10 +216,10 @@ def measured_traffic(form, kernel, n):
     e = rec.get("kernels", {}).get(f"{form}|{kernel}|{n}")
     if not e or sources_digest(e.get("sources")) != e.get("sources_sha256"):
         return None
-    return e.get("dram_bytes_per_sample")
+    return e.get("dram_per_alg_byte")
 
 
-def roofline_report(ctx, levels_prof, P, form, steps, samples_at_level):
+def roofline_report(ctx, levels_prof, P, form, steps):
     """The dominant (kernel kind, level) bucket of the profiled steps as the
     bench line's `roofline`, and every bucket with at least 1 % of the time."""
     smoothers = [k for k, _ in ctx.smoother_info()]
@@ -234,8 +236,8 @@ def roofline_report(ctx, levels_prof, P, form, steps, samples_at_level):
     rows.sort(key=lambda r: -r["share"])
     dom = next(r for r in rows if r["level"] is not None)
     per_launch_bytes = levels_prof[(dom["kind"], dom["level"])]["bytes"] / max(1, levels_prof[(dom["kind"], dom["level"])]["n"])
-    dps = measured_traffic(form, dom["kernel"], dom["n"])
-    traffic = dps * samples_at_level[dom["level"]] if dps is not None else None
+    ratio = measured_traffic(form, dom["kernel"], dom["n"])
+    traffic = round(ratio * per_launch_bytes) if ratio is not None else None
     roof = {"bound": dom["bound"], "achieved": round(dom["achieved"], 1), "peak": dom["peak"], "unit": dom["unit"],
             "frac": round(dom["frac"], 3), "traffic": traffic,
             "kernel": f"{dom['kernel']} on {dom['n']}x{dom['n']}", "share": round(dom["share"], 3),
@@ -430,12 +432,6 @@ def force_smoother(ctx, name, plan=""):
         ctx.set_smoother(int(lv), kind)
 
 
-def samples_reaching(cfg):
-    """Samples per step whose FMG reaches each level (all shifts)."""
-    c = np.array(cfg["counts"], dtype=np.int64) * cfg["R"]
-    return [int(x) for x in np.cumsum(c[::-1])[::-1]]
-
-
 class Step:
     """One context and the fixed-count step on it."""
 
@@ -535,7 +531,7 @@ def run_ours(args):
 
     # per-(kernel, level) event timing of K more steps: the roofline
     prof, prof_ms = step.profiled(stream, flush, args.steps)
-    roof, table = roofline_report(step.ctx, prof, P, "mixed_tf32", args.steps, samples_reaching(cfg))
+    roof, table = roofline_report(step.ctx, prof, P, "mixed_tf32", args.steps)
     details["roofline_table_mixed"] = table
     details["profiled_pass_ms_per_step"] = prof_ms
 
@@ -584,7 +580,7 @@ def run_ours(args):
         e64 = M.estimator_from_sums(Nl, host_sums.numpy().reshape(nl, R, 2), R, reuse=cfg["reuse"])
         details["estimate_fp64"] = {"Q": e64["Q"], "varQ": e64["varQ"]}
         prof64, _ = s64.profiled(stream, flush, 1, warm=0, restore=False)
-        _, details["roofline_table_fp64"] = roofline_report(s64.ctx, prof64, P, "fp64", 1, samples_reaching(c64))
+        _, details["roofline_table_fp64"] = roofline_report(s64.ctx, prof64, P, "fp64", 1)
         fp64["speedup_mixed"] = round((t64 / args.fp64_steps) / (tot_ms / args.steps), 2)
         s64.close()
         del s64
@@ -697,7 +693,7 @@ def run_step6(args, dev, stream, flush, M, P, steps=10, warmup=3):
         st.ctx.check_device(stream)
         ms = float(np.mean(timed_steps(lambda: st(stream), steps, stream, flush)))
         prof, _ = st.profiled(stream, flush, steps)
-        roof, table = roofline_report(st.ctx, prof, P, prec, steps, samples_reaching(cfg))
+        roof, table = roofline_report(st.ctx, prof, P, prec, steps)
         res[prec] = {"ms_per_step": ms, "samples_per_s": ns / (ms * 1e-3), "roofline": roof, "table": table}
         st.close()
     res["mixed_speedup"] = res["fp64"]["ms_per_step"] / res["mixed_tf32"]["ms_per_step"]

@@ -845,7 +845,7 @@ __global__ void kb_resid64(FmgArgs A, int t, int B)
 // is formed with FP32 error-free transformations (resid_f32x2) to within a
 // few units of 2^-48 of the terms, as accurate as the FP64 evaluation of
 // kb_resid64 before r is rounded to FP32, and without the FP64 pipe.
-__global__ void __launch_bounds__(256, 5) kb_prolong_resid64(FmgArgs A, int t, int B)
+__global__ void __launch_bounds__(256, 4) kb_prolong_resid64(FmgArgs A, int t, int B)
 {
     // one thread per coarse cell (I1, I2), i.e. per 2 x 2 quad of fine cells:
     // the quad and its ring of 8 fine neighbours all interpolate from the
@@ -863,6 +863,18 @@ __global__ void __launch_bounds__(256, 5) kb_prolong_resid64(FmgArgs A, int t, i
         const int I2 = static_cast<int>(A.lv[t].by_nc.div(q)), I1 = q - I2 * nc;
         const float* e = at<float>(A.lv[t - 1].u, i);
         const Lv<float> L = view<float>(A, t, i);
+        // the quad's faces, loaded before any store of this iteration
+        float2 kx01[2], kyn[2], kys[2];
+        float kx2[2];
+#pragma unroll
+        for (int qy = 0; qy < 2; ++qy) {
+            const int i1 = 2 * I1, i2 = 2 * I2 + qy;
+            const float* kxr = L.kx + i2 * kx_pitch(n) + i1;
+            kx01[qy] = *reinterpret_cast<const float2*>(kxr);
+            kx2[qy] = kxr[2];
+            kyn[qy] = *reinterpret_cast<const float2*>(L.ky + i2 * n + i1);
+            kys[qy] = *reinterpret_cast<const float2*>(L.ky + (i2 + 1) * n + i1);
+        }
         float E[3][3];  // E[dy + 1][dx + 1]
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy)
@@ -906,18 +918,13 @@ __global__ void __launch_bounds__(256, 5) kb_prolong_resid64(FmgArgs A, int t, i
         for (int qy = 0; qy < 2; ++qy) {
             const int i1 = 2 * I1, i2 = 2 * I2 + qy;
             const int p = i2 * n + i1;
-            const float* kxr = L.kx + i2 * kx_pitch(n) + i1;
-            const float2 kx01 = *reinterpret_cast<const float2*>(kxr);
-            const float kx2 = kxr[2];
-            const float2 kyn = *reinterpret_cast<const float2*>(L.ky + i2 * n + i1);
-            const float2 kys = *reinterpret_cast<const float2*>(L.ky + (i2 + 1) * n + i1);
             float r[2];
 #pragma unroll
             for (int qx = 0; qx < 2; ++qx) {
                 const float up = U[qy + 1][qx + 1];
                 const float uv[4] = {U[qy + 1][qx], U[qy + 1][qx + 2], U[qy][qx + 1], U[qy + 2][qx + 1]};
-                const float kv[4] = {qx ? kx01.y : kx01.x, qx ? kx2 : kx01.y, qx ? kyn.y : kyn.x,
-                                     qx ? kys.y : kys.x};
+                const float kv[4] = {qx ? kx01[qy].y : kx01[qy].x, qx ? kx2[qy] : kx01[qy].y,
+                                     qx ? kyn[qy].y : kyn[qy].x, qx ? kys[qy].y : kys[qy].x};
                 r[qx] = resid_f32x2(kv, up, uv, ih2);
             }
             *reinterpret_cast<double2*>(L.u64 + p) = make_double2(widen(U[qy + 1][1]), widen(U[qy + 1][2]));

@@ -63,14 +63,14 @@ def test_roofline_report_takes_the_longest_level_bucket(bench, monkeypatch):
             ("smooth", 2): _cell(1.0, 12, bytes_=hbm * 0.1e-3),
             ("transfer", 8): _cell(2.0, 4, bytes_=hbm * 1e-3),
             ("reduce", None): _cell(7.0, 2, bytes_=1e6)}  # no single level: never the dominant kernel
-    monkeypatch.setattr(bench, "measured_traffic", lambda form, kernel, n: 1000.0 if n == 2048 else None)
+    monkeypatch.setattr(bench, "measured_traffic", lambda form, kernel, n: 0.95 if n == 2048 else None)
     ctx = _Ctx(["gs", "whole", "whole", "whole", "tma", "tma", "tma", "tma", "tma"])
-    roof, table = bench.roofline_report(ctx, prof, P, "mixed_tf32", steps=2, samples_at_level=[0] * 8 + [256])
+    roof, table = bench.roofline_report(ctx, prof, P, "mixed_tf32", steps=2)
     assert roof["kernel"] == "kb_rbgs_tma on 2048x2048"
     assert roof["frac"] == pytest.approx(0.5, abs=1e-3)
     assert roof["alg_bytes_per_launch"] == pytest.approx(hbm * 3e-3 / 12, rel=1e-12)
     assert roof["share"] == pytest.approx(6.0 / 16.0, abs=1e-3)
-    assert roof["traffic"] == 1000.0 * 256  # per sample x samples of the launch
+    assert roof["traffic"] == round(0.95 * hbm * 3e-3 / 12)  # DRAM per algorithmic byte x the launch's bytes
     assert {r["kernel"] for r in table} >= {"kb_rbgs_tma", "kb_rbgs_whole", "kb_qoi, k_sums"}
 
 
@@ -79,10 +79,10 @@ def test_traffic_record_and_its_invalidation(bench, tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(traffic))
     assert bench.measured_traffic("mixed_tf32", "kb_rbgs_tma", 2048) is None  # no record
     files = ["paper_1806_05619_gb300/csrc/rbgs_tma.cu", "paper_1806_05619_gb300/csrc/fmg_device.cuh"]
-    entry = {"dram_bytes_per_sample": 123.0, "sources": files, "sources_sha256": bench.sources_digest(files)}
+    entry = {"dram_per_alg_byte": 0.93, "sources": files, "sources_sha256": bench.sources_digest(files)}
     rec = {"kernels": {"mixed_tf32|kb_rbgs_tma|2048": entry}}
     traffic.write_text(json.dumps(rec))
-    assert bench.measured_traffic("mixed_tf32", "kb_rbgs_tma", 2048) == 123.0
+    assert bench.measured_traffic("mixed_tf32", "kb_rbgs_tma", 2048) == 0.93
     assert bench.measured_traffic("mixed_tf32", "kb_rbgs_tma", 1024) is None   # another level
     assert bench.measured_traffic("fp64", "kb_rbgs_tma", 2048) is None         # another form
     entry["sources_sha256"] = "0" * 64                                          # other kernel sources
@@ -136,4 +136,3 @@ def test_cpu_sample_keeps_the_level_mix(bench):
     cfg = bench.workload_config("mlqmc9")
     assert cfg["counts"] == [4096, 2048, 1024, 512, 256, 128, 64, 32, 16]
     assert bench.n_samples(W.fixed_count_work(cfg["counts"], cfg["R"])) == 130816
-    assert bench.samples_reaching(cfg)[-1] == 256 and bench.samples_reaching(cfg)[0] == 130816
