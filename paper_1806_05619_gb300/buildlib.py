@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmlqmc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["mlqmc_cuda.cu", "kl_tcgen05.cu", "rbgs_stream.cu", "rbgs_tma.cu", "rbgs_whole.cu", "matern_nystrom.cu",
+SOURCES = ["mlqmc_cuda.cu", "kl_tcgen05.cu", "rbgs_stream.cu", "rbgs_tma.cu", "resid_tma.cu", "rbgs_whole.cu", "matern_nystrom.cu",
            "mimc.cu", "mlqmc_host.cpp"]
 
 

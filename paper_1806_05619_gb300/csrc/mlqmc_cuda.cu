@@ -27,6 +27,7 @@
 #include "mlqmc_internal.h"
 #include "rbgs_stream.h"
 #include "rbgs_tma.h"
+#include "resid_tma.h"
 #include "ptx_async.cuh"
 #include "rbgs_whole.h"
 #include "matern_nystrom.h"
@@ -2101,7 +2102,11 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
             // the residual's 10 operations per cell run in FP32 error-free pairs: FP32 work
             Timed tm(c, kProfTransfer, st,
                      work_of<float>(B * (es * 0.25 * Mc + 8.0 * Mc + es * (2.0 * Fc + Mc)), B * 10.0 * Mc));
-            kb_prolong_resid64<<<grid_for(c, B * (n / 2) * (n / 2)), 256, 0, st>>>(A, t, B);
+            if (mlqmc_resid::supported(n)) {
+                if (!mlqmc_resid::launch(A, t, n, B, c->sm_count, st)) return MLQMC_ERR_CUDA;
+            } else {
+                kb_prolong_resid64<<<grid_for(c, B * (n / 2) * (n / 2)), 256, 0, st>>>(A, t, B);
+            }
         } else if (refine) {
             {
                 Timed tm(c, kProfTransfer, st, work_of<T>(B * (es * 0.25 + 8.0) * Mc, B * 8.0 * Mc));
@@ -2693,7 +2698,7 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     c->pool_budget = std::min<size_t>(free_b / 2, static_cast<size_t>(192) << 30);
-    if (!mlqmc_tma::prepare() || !mlqmc_whole::prepare()) {
+    if (!mlqmc_tma::prepare() || !mlqmc_whole::prepare() || !mlqmc_resid::prepare()) {
         free_ctx(c);
         return MLQMC_ERR_CUDA;
     }

@@ -29,13 +29,11 @@
 // re-reads u, b and the faces.
 #include "rbgs_tma.h"
 
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
 #include <cstdint>
 #include <cstring>
 
 #include "ptx_async.cuh"
+#include "tma_encode.h"
 
 using namespace mlqmc_dev;
 using namespace mlqmc_ptx;
@@ -782,34 +780,8 @@ __global__ void __launch_bounds__(BGeom<TY, POST>::threads, BGeom<TY, POST>::cta
     }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
-    return fn;
-}
-
-// FP32 array of per-sample blocks: x extent w (row pitch `pitch` floats), h rows, B samples.
-bool encode_3d(CUtensorMap* map, const ArrDesc& a, uint64_t w, uint64_t pitch, uint64_t h, uint64_t B, uint32_t bw,
-               uint32_t bh)
-{
-    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
-    if (!fn || !a.base) return false;
-    const cuuint64_t dims[3] = {w, h, B};
-    const cuuint64_t strides[2] = {pitch * sizeof(float), static_cast<cuuint64_t>(a.stride)};
-    const cuuint32_t box[3] = {bw, bh, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, a.base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
+using mlqmc_tmap::encode_3d;
+using mlqmc_tmap::encode_fn;
 
 template <int TX, int TY, int NS, bool POST, bool RR = false>
 bool attr()
