@@ -52,6 +52,11 @@ struct Maps {
     CUtensorMap e, kx, ky;
 };
 
+template <bool V>
+struct Edge {
+    static constexpr bool value = V;
+};
+
 __global__ void __launch_bounds__(kThreads, kCtasPerSM)
     kb_prolong_resid_tma(const __grid_constant__ Maps maps, FmgArgs A, int t, int B)
 {
@@ -133,75 +138,83 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSM)
             const float* skx = S + oKX;
             const float* sky = S + oKY;
             const Lv<float> L = view<float>(A, t, i);
+            // a tile whose parents and their neighbours all lie inside the coarse
+            // grid needs neither the reflection nor the range tests (uniform per CTA)
+            const bool inner = I1_0 >= 1 && I1_0 + kCX + 1 <= nc && I2_0 >= 1 && I2_0 + kCY + 1 <= nc;
+            auto quads = [&](auto edge) {
+                constexpr bool EDGE = decltype(edge)::value;
 #pragma unroll 1
-            for (int k = 0; k < 2; ++k) {
-                const int q = static_cast<int>(threadIdx.x) + k * kThreads;
-                const int cx = q & (kCX - 1), cy = q / kCX;
-                const int I1 = I1_0 + cx, I2 = I2_0 + cy;
-                // the quad's faces (staged fine row 2 cy + qy, column 2 cx)
-                float2 kx01[2], kyn[2], kys[2];
-                float kx2[2];
+                for (int k = 0; k < 2; ++k) {
+                    const int q = static_cast<int>(threadIdx.x) + k * kThreads;
+                    const int cx = q & (kCX - 1), cy = q / kCX;
+                    const int I1 = I1_0 + cx, I2 = I2_0 + cy;
+                    // the quad's faces (staged fine row 2 cy + qy, column 2 cx)
+                    float2 kx01[2], kyn[2], kys[2];
+                    float kx2[2];
 #pragma unroll
-                for (int qy = 0; qy < 2; ++qy) {
-                    const int r = 2 * cy + qy, c = 2 * cx;
-                    kx01[qy] = *reinterpret_cast<const float2*>(skx + r * kXW + c);
-                    kx2[qy] = skx[r * kXW + c + 2];
-                    kyn[qy] = *reinterpret_cast<const float2*>(sky + r * kFX + c);
-                    kys[qy] = *reinterpret_cast<const float2*>(sky + (r + 1) * kFX + c);
-                }
-                float E[3][3];  // E[dy + 1][dx + 1]; parent at staged (cy + 1, cx + 4)
-#pragma unroll
-                for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        const int x = I1 + dx, y = I2 + dy;
-                        const bool ox = x < 0 || x >= nc, oy = y < 0 || y >= nc;
-                        const float v = se[(cy + 1 + (oy ? 0 : dy)) * kEW + cx + 4 + (ox ? 0 : dx)];
-                        E[dy + 1][dx + 1] = (ox != oy) ? -v : v;
+                    for (int qy = 0; qy < 2; ++qy) {
+                        const int r = 2 * cy + qy, c = 2 * cx;
+                        kx01[qy] = *reinterpret_cast<const float2*>(skx + r * kXW + c);
+                        kx2[qy] = skx[r * kXW + c + 2];
+                        kyn[qy] = *reinterpret_cast<const float2*>(sky + r * kFX + c);
+                        kys[qy] = *reinterpret_cast<const float2*>(sky + (r + 1) * kFX + c);
                     }
-                // fine cells 2I + f, f = -1..2 per axis (the four ring corners unused):
-                // parent offset (f - 1) / 2 rounded down, coarse neighbour towards the
-                // cell's side (+1 for odd f, -1 for even f); cells outside the grid are 0
-                float U[4][4];
+                    float E[3][3];  // E[dy + 1][dx + 1]; parent at staged (cy + 1, cx + 4)
 #pragma unroll
-                for (int fy = -1; fy <= 2; ++fy)
+                    for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
-                    for (int fx = -1; fx <= 2; ++fx) {
-                        const bool ring_x = fx < 0 || fx > 1, ring_y = fy < 0 || fy > 1;
-                        if (ring_x && ring_y) {
-                            U[fy + 1][fx + 1] = 0.0f;
-                            continue;
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            const int x = I1 + dx, y = I2 + dy;
+                            const bool ox = EDGE && (x < 0 || x >= nc), oy = EDGE && (y < 0 || y >= nc);
+                            const float v = se[(cy + 1 + (oy ? 0 : dy)) * kEW + cx + 4 + (ox ? 0 : dx)];
+                            E[dy + 1][dx + 1] = (ox != oy) ? -v : v;
                         }
-                        const int i1 = 2 * I1 + fx, i2 = 2 * I2 + fy;
-                        if (i1 < 0 || i1 >= n || i2 < 0 || i2 >= n) {
-                            U[fy + 1][fx + 1] = 0.0f;
-                            continue;
+                    // fine cells 2I + f, f = -1..2 per axis (the four ring corners unused):
+                    // parent offset (f - 1) / 2 rounded down, coarse neighbour towards the
+                    // cell's side (+1 for odd f, -1 for even f); cells outside the grid are 0
+                    float U[4][4];
+#pragma unroll
+                    for (int fy = -1; fy <= 2; ++fy)
+#pragma unroll
+                        for (int fx = -1; fx <= 2; ++fx) {
+                            const bool ring_x = fx < 0 || fx > 1, ring_y = fy < 0 || fy > 1;
+                            if (ring_x && ring_y) {
+                                U[fy + 1][fx + 1] = 0.0f;
+                                continue;
+                            }
+                            const int i1 = 2 * I1 + fx, i2 = 2 * I2 + fy;
+                            if (EDGE && (i1 < 0 || i1 >= n || i2 < 0 || i2 >= n)) {
+                                U[fy + 1][fx + 1] = 0.0f;
+                                continue;
+                            }
+                            const int px = fx < 0 ? -1 : (fx > 1 ? 1 : 0), py = fy < 0 ? -1 : (fy > 1 ? 1 : 0);
+                            const int sx = (fx & 1) ? 1 : -1, sy = (fy & 1) ? 1 : -1;
+                            const float a = E[py + 1][px + 1];
+                            const float bx = E[py + 1][px + sx + 1];
+                            const float cyv = E[py + sy + 1][px + 1];
+                            const float d = E[py + sy + 1][px + sx + 1];
+                            U[fy + 1][fx + 1] = fmaf(0.5625f, a, fmaf(0.1875f, bx + cyv, 0.0625f * d));
                         }
-                        const int px = fx < 0 ? -1 : (fx > 1 ? 1 : 0), py = fy < 0 ? -1 : (fy > 1 ? 1 : 0);
-                        const int sx = (fx & 1) ? 1 : -1, sy = (fy & 1) ? 1 : -1;
-                        const float a = E[py + 1][px + 1];
-                        const float bx = E[py + 1][px + sx + 1];
-                        const float cyv = E[py + sy + 1][px + 1];
-                        const float d = E[py + sy + 1][px + sx + 1];
-                        U[fy + 1][fx + 1] = fmaf(0.5625f, a, fmaf(0.1875f, bx + cyv, 0.0625f * d));
-                    }
 #pragma unroll
-                for (int qy = 0; qy < 2; ++qy) {
-                    const int i1 = 2 * I1, i2 = 2 * I2 + qy;
-                    const int p = i2 * n + i1;
-                    float r[2];
+                    for (int qy = 0; qy < 2; ++qy) {
+                        const int i1 = 2 * I1, i2 = 2 * I2 + qy;
+                        const int p = i2 * n + i1;
+                        float r[2];
 #pragma unroll
-                    for (int qx = 0; qx < 2; ++qx) {
-                        const float up = U[qy + 1][qx + 1];
-                        const float uv[4] = {U[qy + 1][qx], U[qy + 1][qx + 2], U[qy][qx + 1], U[qy + 2][qx + 1]};
-                        const float kv[4] = {qx ? kx01[qy].y : kx01[qy].x, qx ? kx2[qy] : kx01[qy].y,
-                                             qx ? kyn[qy].y : kyn[qy].x, qx ? kys[qy].y : kys[qy].x};
-                        r[qx] = resid_f32x2(kv, up, uv, ih2);
+                        for (int qx = 0; qx < 2; ++qx) {
+                            const float up = U[qy + 1][qx + 1];
+                            const float uv[4] = {U[qy + 1][qx], U[qy + 1][qx + 2], U[qy][qx + 1], U[qy + 2][qx + 1]};
+                            const float kv[4] = {qx ? kx01[qy].y : kx01[qy].x, qx ? kx2[qy] : kx01[qy].y,
+                                                 qx ? kyn[qy].y : kyn[qy].x, qx ? kys[qy].y : kys[qy].x};
+                            r[qx] = resid_f32x2(kv, up, uv, ih2);
+                        }
+                        *reinterpret_cast<double2*>(L.u64 + p) = make_double2(widen(U[qy + 1][1]), widen(U[qy + 1][2]));
+                        *reinterpret_cast<float2*>(L.bc + p) = make_float2(r[0], r[1]);
                     }
-                    *reinterpret_cast<double2*>(L.u64 + p) = make_double2(widen(U[qy + 1][1]), widen(U[qy + 1][2]));
-                    *reinterpret_cast<float2*>(L.bc + p) = make_float2(r[0], r[1]);
                 }
-            }
+            };
+            if (inner) quads(Edge<false>());
+            else quads(Edge<true>());
         }
         // this buffer is refilled by the TMA next iteration: order the generic accesses first
         fence_proxy_async();
