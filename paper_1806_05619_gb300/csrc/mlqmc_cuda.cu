@@ -104,6 +104,42 @@ __global__ void k_points(const SampleDesc* __restrict__ smp, int count, int s, i
     }
 }
 
+// Mixed TF32 form with separable modes: the chunk's normals (the FP32
+// inverse CDF of k_points, stored widened in Y) and, from the same FP64
+// product sqrt(theta_m) y_m, its FP32 rounding (the coefficients of the SIMT
+// synthesis, as k_coef32) and its TF32 rounding (the tensor-core C operand,
+// zero-padded to kpad columns, as kl_build_c), in one pass over (sample,
+// column): the three kernels' values without re-reading Y. Samples in rank
+// order with canon = rank (the batched calls).
+__global__ void k_points_mixed(const SampleDesc* __restrict__ smp, int count, int s, int kpad, FastDiv by_kpad,
+                               int sampler, uint64_t seed, const uint32_t* __restrict__ z,
+                               const double* __restrict__ sq, double* __restrict__ Y, float* __restrict__ c32,
+                               float* __restrict__ C)
+{
+    const uint32_t total = static_cast<uint32_t>(count) * static_cast<uint32_t>(kpad);
+    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int i = static_cast<int>(by_kpad.div(idx));
+        const int m = static_cast<int>(idx - static_cast<uint32_t>(i) * static_cast<uint32_t>(kpad));
+        if (m >= s) {
+            C[idx] = 0.0f;
+            continue;
+        }
+        const SampleDesc d = smp[i];
+        const uint64_t x = point_bits(sampler, seed, z, d.level, d.r, d.n, m);
+        const uint64_t k = x >> 11;  // u = (k + 1/2) 2^-53
+        const bool lo = k < (1ull << 52);
+        const uint64_t kk = lo ? k : ((1ull << 53) - 1ull) - k;
+        const float y = normcdfinvf(fmaf(__ull2float_rn(kk), 0x1p-53f, 0x1p-54f));
+        const double yw = widen(lo ? y : -y);
+        Y[static_cast<size_t>(d.canon) * s + m] = yw;
+        const float pf = narrow(sq[m] * yw);
+        c32[static_cast<size_t>(i) * s + m] = pf;
+        uint32_t r;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(pf));
+        C[idx] = __uint_as_float(r);
+    }
+}
+
 // Flat loops in 32-bit indices: chunks are cut so that every level's
 // samples x elements stays below 2^31 (see mlqmc_sample_levels).
 #define GRID_STRIDE(idx, total)                                                                       \
@@ -2350,13 +2386,29 @@ mlqmc_status run_chunk(mlqmc_ctx* c, int count, const int* Bt, int Lmax, double*
         if (s != MLQMC_OK) return s;
     }
     FmgArgs A = base_args(c);
-    mlqmc_status s = launch_points(c, c->d_samples, count, c->d_Y, nullptr, st);
-    if (s != MLQMC_OK) return s;
-    s = build_c(c, count, st);
-    if (s != MLQMC_OK) return s;
+    mlqmc_status s = MLQMC_OK;
+    const int kpad = c->kl_tc ? static_cast<int>(mlqmc_kl::row_bytes(c->kl_variant, p.n_modes) / 4) : 0;
+    if (is_mixed(p) && !c->matern && c->kl_tc && c->kl_variant == mlqmc_kl::Variant::TF32 &&
+        static_cast<int64_t>(count) * kpad < (int64_t{1} << 31)) {
+        // normals, FP32 coefficients and the C operand in one pass
+        const int64_t total = static_cast<int64_t>(count) * kpad;
+        Timed tm(c, kProfPoints, st,
+                 work_of<float>(static_cast<double>(count) * (p.n_modes * 12.0 + kpad * 4.0 + sizeof(SampleDesc)), 0.0));
+        k_points_mixed<<<grid_for(c, total), 256, 0, st>>>(c->d_samples, count, p.n_modes, kpad,
+                                                           FastDiv(static_cast<uint32_t>(kpad)), p.sampler, p.seed,
+                                                           c->d_z, c->d_sqrt_theta, c->d_Y, c->d_c32,
+                                                           static_cast<float*>(c->d_C));
+        if (last_error() != MLQMC_OK) return MLQMC_ERR_CUDA;
+        c->c32_ready = true;
+    } else {
+        s = launch_points(c, c->d_samples, count, c->d_Y, nullptr, st);
+        if (s != MLQMC_OK) return s;
+        s = build_c(c, count, st);
+        if (s != MLQMC_OK) return s;
+    }
     // mixed forms, separable modes: FP32 coefficients of all the chunk's
     // samples once, before both streams' SIMT syntheses read them
-    if (is_mixed(p) && !c->matern) {
+    if (is_mixed(p) && !c->matern && !c->c32_ready) {
         Timed tm(c, kProfSynth, st, work_of<double>(count * 12.0 * p.n_modes, count * 1.0 * p.n_modes));
         k_coef32<<<grid_for(c, static_cast<int64_t>(count) * p.n_modes), 256, 0, st>>>(A, count, c->d_sqrt_theta,
                                                                                         c->d_c32);
