@@ -243,8 +243,10 @@ __device__ __forceinline__ double rsqrt64(double d)
 __device__ __forceinline__ float expT(float x) { return expf(x); }
 __device__ __forceinline__ double expT(double x) { return exp64(x); }
 
-// Harmonic mean 2ab/(a+b) of two cell coefficients (FP64 through rcp64).
-__device__ __forceinline__ float hmean(float a, float b) { return 2.0f * a * b / (a + b); }
+// Harmonic mean 2ab/(a+b) of two cell coefficients: FP32 with the hardware
+// reciprocal (__fdividef, within 2 ulp; the coefficients are positive and
+// far from the range where it flushes), FP64 through rcp64.
+__device__ __forceinline__ float hmean(float a, float b) { return __fdividef(2.0f * a * b, a + b); }
 __device__ __forceinline__ double hmean(double a, double b) { return 2.0 * a * b * rcp64(a + b); }
 __device__ __forceinline__ float recip(float d) { return 1.0f / d; }
 __device__ __forceinline__ double recip(double d) { return rcp64(d); }

@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) kl_tc_kernel(const __grid_const
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int ntiles = (B + NT - 1) / NT;
-    const int tiles = (M / kTileM) * ntiles;
+    const int tiles = ((M + kTileM - 1) / kTileM) * ntiles;  // the Psi map holds whole 128-row tiles (zero rows past M)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -577,12 +577,12 @@ bool prepare_kernel()
 bool launch(Variant v, const TensorMaps& maps, int M, int B, int s, float* d_k, size_t kstride, int* d_err,
             cudaStream_t st, int nt)
 {
-    if (M % kTileM != 0 || B <= 0 || (nt != 128 && nt != kNT)) return false;
+    if (M <= 0 || B <= 0 || (nt != 128 && nt != kNT)) return false;
     const int nk = static_cast<int>(row_bytes(v, s) / 128);  // 128-byte K blocks
     CUtensorMap tp, tc;
     std::memcpy(&tp, maps.psi, sizeof(CUtensorMap));
     std::memcpy(&tc, nt == 128 ? maps.c128 : maps.c, sizeof(CUtensorMap));
-    const int tiles = (M / kTileM) * ((B + nt - 1) / nt);
+    const int tiles = ((M + kTileM - 1) / kTileM) * ((B + nt - 1) / nt);
     const int grid = std::min(tiles, sm_count());  // persistent: one CTA per SM
     const size_t smem = tc_smem_bytes(nt);
     if (nt == 128) {

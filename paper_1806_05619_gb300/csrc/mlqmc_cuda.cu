@@ -75,12 +75,40 @@ __device__ __forceinline__ uint64_t point_bits(int sampler, uint64_t seed, const
                         0x4D43524Eu, seed, j);
 }
 
+// The lattice shifts depend only on (level, r, j): a table of them, filled
+// once per context by philox_coord itself, replaces the ten Philox rounds
+// per point of the batched point kernels (same bits).
+__global__ void k_shift_table(int R, int L, int s, uint64_t seed, uint64_t* __restrict__ tab)
+{
+    const int64_t total = static_cast<int64_t>(R) * L * s;
+    for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int j = static_cast<int>(idx % s);
+        const int64_t rest = idx / s;
+        const int r = static_cast<int>(rest % R), level = static_cast<int>(rest / R);
+        tab[idx] = philox_coord(static_cast<uint32_t>(r), static_cast<uint32_t>(level), 0x53484654u, seed, j);
+    }
+}
+
+// point_bits, with the lattice shift from the table when there is one
+__device__ __forceinline__ uint64_t point_bits_tab(int sampler, uint64_t seed, const uint32_t* z,
+                                                   const uint64_t* tab, int R, int s, int level, int r, int64_t n,
+                                                   int j)
+{
+    if (tab && sampler == MLQMC_SAMPLER_LATTICE) {
+        const uint32_t t = __brev(static_cast<uint32_t>(n)) * z[j];
+        return (static_cast<uint64_t>(t) << 32) + tab[(static_cast<size_t>(level) * R + r) * s + j];
+    }
+    return point_bits(sampler, seed, z, level, r, n, j);
+}
+
 // Points and normals y = Phi^-1(u) (Sec. 3.2). fp32 (mixed forms, whose
 // normals only enter FP32 and tensor-core arithmetic): Phi^-1 in FP32, each
 // half of (0, 1) taken from its own end (1 - u formed exactly in integers),
 // so both tails keep float resolution; the FP64 form uses FP64.
 __global__ void k_points(const SampleDesc* __restrict__ smp, int count, int s, int sampler, uint64_t seed,
-                         const uint32_t* __restrict__ z, double* __restrict__ Y, uint64_t* __restrict__ bits, int fp32)
+                         const uint32_t* __restrict__ z, const uint64_t* __restrict__ tab, int R,
+                         double* __restrict__ Y, uint64_t* __restrict__ bits, int fp32)
 {
     const int64_t total = static_cast<int64_t>(count) * s;
     for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
@@ -88,7 +116,7 @@ __global__ void k_points(const SampleDesc* __restrict__ smp, int count, int s, i
         const int q = static_cast<int>(idx / s);
         const int j = static_cast<int>(idx - static_cast<int64_t>(q) * s);
         const SampleDesc d = smp[q];
-        const uint64_t x = point_bits(sampler, seed, z, d.level, d.r, d.n, j);
+        const uint64_t x = point_bits_tab(sampler, seed, z, tab, R, s, d.level, d.r, d.n, j);
         const size_t o = static_cast<size_t>(d.canon) * s + j;
         if (bits) bits[o] = x;
         if (Y && fp32) {
@@ -113,8 +141,8 @@ __global__ void k_points(const SampleDesc* __restrict__ smp, int count, int s, i
 // order with canon = rank (the batched calls).
 __global__ void k_points_mixed(const SampleDesc* __restrict__ smp, int count, int s, int kpad, FastDiv by_kpad,
                                int sampler, uint64_t seed, const uint32_t* __restrict__ z,
-                               const double* __restrict__ sq, double* __restrict__ Y, float* __restrict__ c32,
-                               float* __restrict__ C)
+                               const uint64_t* __restrict__ tab, int R, const double* __restrict__ sq,
+                               double* __restrict__ Y, float* __restrict__ c32, float* __restrict__ C)
 {
     const uint32_t total = static_cast<uint32_t>(count) * static_cast<uint32_t>(kpad);
     for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
@@ -125,7 +153,7 @@ __global__ void k_points_mixed(const SampleDesc* __restrict__ smp, int count, in
             continue;
         }
         const SampleDesc d = smp[i];
-        const uint64_t x = point_bits(sampler, seed, z, d.level, d.r, d.n, m);
+        const uint64_t x = point_bits_tab(sampler, seed, z, tab, R, s, d.level, d.r, d.n, m);
         const uint64_t k = x >> 11;  // u = (k + 1/2) 2^-53
         const bool lo = k < (1ull << 52);
         const uint64_t kk = lo ? k : ((1ull << 53) - 1ull) - k;
@@ -1614,8 +1642,8 @@ mlqmc_status launch_points(mlqmc_ctx* c, const SampleDesc* d_s, int count, doubl
 {
     const int64_t total = static_cast<int64_t>(count) * c->p.n_modes;
     Timed tm(c, kProfPoints, st, work_of<double>(8.0 * total + sizeof(SampleDesc) * count, 0.0));
-    k_points<<<grid_for(c, total), 256, 0, st>>>(d_s, count, c->p.n_modes, c->p.sampler, c->p.seed, c->d_z, Y, bits,
-                                                 is_mixed(c->p) ? 1 : 0);
+    k_points<<<grid_for(c, total), 256, 0, st>>>(d_s, count, c->p.n_modes, c->p.sampler, c->p.seed, c->d_z,
+                                                 c->d_shift, c->p.n_shifts, Y, bits, is_mixed(c->p) ? 1 : 0);
     return last_error();
 }
 
@@ -1654,7 +1682,7 @@ bool uses_tc(const mlqmc_ctx* c, int t)
 }
 
 // Batched KL field and faces of level t for samples 0..B-1. The field comes
-// from the tensor-core contraction (mixed TF32 form, levels of >= 128 cells)
+// from the tensor-core contraction (mixed forms, every level)
 // or from the separable SIMT sum; the C operand must already be built.
 template <typename T>
 mlqmc_status synth_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cudaStream_t st)
@@ -2396,8 +2424,8 @@ mlqmc_status run_chunk(mlqmc_ctx* c, int count, const int* Bt, int Lmax, double*
                  work_of<float>(static_cast<double>(count) * (p.n_modes * 12.0 + kpad * 4.0 + sizeof(SampleDesc)), 0.0));
         k_points_mixed<<<grid_for(c, total), 256, 0, st>>>(c->d_samples, count, p.n_modes, kpad,
                                                            FastDiv(static_cast<uint32_t>(kpad)), p.sampler, p.seed,
-                                                           c->d_z, c->d_sqrt_theta, c->d_Y, c->d_c32,
-                                                           static_cast<float*>(c->d_C));
+                                                           c->d_z, c->d_shift, p.n_shifts, c->d_sqrt_theta, c->d_Y,
+                                                           c->d_c32, static_cast<float*>(c->d_C));
         if (last_error() != MLQMC_OK) return MLQMC_ERR_CUDA;
         c->c32_ready = true;
     } else {
@@ -2477,6 +2505,7 @@ void free_ctx(mlqmc_ctx* c)
     cudaFree(c->d_grp_m);
     cudaFree(c->d_grp_sqrt);
     cudaFree(c->d_z);
+    cudaFree(c->d_shift);
     cudaFree(c->d_ma);
     cudaFree(c->d_mb);
     cudaFree(c->d_sqrt_theta);
@@ -2689,6 +2718,21 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
         free_ctx(c);
         return kst;
     }
+    // lattice shift table, while it stays small (up to 2^22 entries, 32 MB)
+    if (p->sampler == MLQMC_SAMPLER_LATTICE &&
+        static_cast<int64_t>(p->n_shifts) * p->n_levels * p->n_modes <= (int64_t{1} << 22)) {
+        const int64_t total = static_cast<int64_t>(p->n_shifts) * p->n_levels * p->n_modes;
+        if (!ok(cudaMalloc(&c->d_shift, static_cast<size_t>(total) * sizeof(uint64_t)))) {
+            free_ctx(c);
+            return MLQMC_ERR_OOM;
+        }
+        k_shift_table<<<static_cast<int>(std::min<int64_t>((total + 255) / 256, 4096)), 256>>>(
+            p->n_shifts, p->n_levels, p->n_modes, p->seed, c->d_shift);
+        if (!ok(cudaGetLastError()) || !ok(cudaDeviceSynchronize())) {
+            free_ctx(c);
+            return MLQMC_ERR_CUDA;
+        }
+    }
 
     // per-chunk buffers
     c->max_samples = max_samples_per_call > 0 ? max_samples_per_call : 65536;
@@ -2725,20 +2769,23 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
         free_ctx(c);
         return MLQMC_ERR_CUDA;
     }
-    // tensor-core KL tables (mixed TF32 form): Psi of every level with a whole number of 128-cell tiles
+    // tensor-core KL tables (mixed forms): Psi of every level, its rows padded
+    // with zeros to whole 128-cell tiles (the contraction stores only the
+    // level's cells)
     if (p->precision == MLQMC_MIXED_TF32 || p->precision == MLQMC_MIXED_BF16X3) {
         c->kl_variant = p->precision == MLQMC_MIXED_TF32 ? mlqmc_kl::Variant::TF32 : mlqmc_kl::Variant::BF16X3;
         const size_t rb = mlqmc_kl::row_bytes(c->kl_variant, p->n_modes);
         good = mlqmc_kl::prepare_kernel() && ok(cudaMalloc(&c->d_C, ms * rb));
         for (int t = 0; good && t < p->n_levels; ++t) {
             const int n = p->coarse_cells << t;
-            if ((n * n) % 128 != 0) continue;
-            good = ok(cudaMalloc(&c->d_psi_tc[t], static_cast<size_t>(n) * n * rb)) &&
+            const int mpad = (n * n + 127) / 128 * 128;
+            good = ok(cudaMalloc(&c->d_psi_tc[t], static_cast<size_t>(mpad) * rb)) &&
+                   ok(cudaMemset(c->d_psi_tc[t], 0, static_cast<size_t>(mpad) * rb)) &&
                    (c->matern ? mlqmc_kl::build_psi_dense(c->kl_variant, c->d_psi_dense + c->dense_off[t],
                                                           static_cast<int64_t>(n) * n, p->n_modes, c->d_psi_tc[t], 0)
                               : mlqmc_kl::build_psi(c->kl_variant, c->d_psi + c->psi_off[t], n, p->n_modes, c->d_ma,
                                                     c->d_mb, c->d_psi_tc[t], 0)) &&
-                   mlqmc_kl::make_maps(c->kl_variant, c->d_psi_tc[t], n * n, c->d_C, static_cast<int>(ms), p->n_modes,
+                   mlqmc_kl::make_maps(c->kl_variant, c->d_psi_tc[t], mpad, c->d_C, static_cast<int>(ms), p->n_modes,
                                        &c->kl_maps[t]);
         }
         if (!good || !ok(cudaDeviceSynchronize())) {

@@ -106,6 +106,7 @@ struct mlqmc_ctx {
     int* d_grp_m = nullptr;
     double* d_grp_sqrt = nullptr;
     uint32_t* d_z = nullptr;
+    uint64_t* d_shift = nullptr;  // lattice shifts [(level * R + r) * s + j] (null: Philox per point)
     int* d_ma = nullptr;               // modes in order: first index a
     int* d_mb = nullptr;               // second index b
     double* d_sqrt_theta = nullptr;    // sqrt(theta_m)
@@ -118,7 +119,7 @@ struct mlqmc_ctx {
     double* d_psi_dense = nullptr;
     size_t dense_off[MLQMC_MAX_LEVELS] = {};
 
-    // tensor-core KL (mixed TF32 form): Psi per level with >= 128 cells, C per chunk
+    // tensor-core KL (mixed forms): Psi per level (rows padded to 128-cell tiles), C per chunk
     bool kl_tc = false;
     void* d_psi_tc[MLQMC_MAX_LEVELS] = {};  // Psi operand per level (FP32 or split BF16 rows)
     void* d_C = nullptr;   // C operand of the contraction (FP32 or split BF16 rows)
