@@ -649,6 +649,26 @@ __device__ __forceinline__ float resid_f32x2(const float (&k)[4], float up, cons
     return __fadd_rn(rh, __fsub_rn(re, al));
 }
 
+// The mixed forms' one refinement update of a cell, u64 + e: in the fixed-
+// cycle forms u64 still holds the widened FP32 interpolant U, so U + e is a
+// sum of two floats that TwoSum gives exactly as the pair (h, lo): h =
+// fl32(U + e) is the FP32 copy and (h, lo) goes into a PairSum; the FP64
+// value h + lo (the correctly rounded U + e, as the FP64 add gives it) is
+// formed only when it is stored (keep). A u64 that is not a widened float
+// takes the FP64 add.
+__device__ __forceinline__ void update_pair(double w, float e, bool keep, float& h, float& lo, double& r)
+{
+    const float U = narrow(w);
+    if (__double_as_longlong(widen(U)) == __double_as_longlong(w)) {
+        two_sum32(U, e, h, lo);
+        if (keep) r = widen(h) + widen(lo);
+    } else {
+        r = w + widen(e);
+        h = narrow(r);
+        lo = narrow_rest(r, h);
+    }
+}
+
 // A double result stored in working precision T.
 template <typename T>
 __device__ __forceinline__ T to_work(double x)

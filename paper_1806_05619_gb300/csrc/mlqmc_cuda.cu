@@ -1109,9 +1109,11 @@ __device__ __forceinline__ int team_count()
 // sample on small ones (TM), the sum in a fixed order either way.
 // UPD (mixed forms, one refinement step per level): the step's last update
 // u64 += e (e the FP32 correction in u), the FP32 copy of u64 and the sum run
-// in one pass over each thread's cell pairs, so u64 is read once.
+// in one pass over each thread's cell pairs, so u64 is read once; the new
+// u64 is stored only when something reads it later (keep64: the centre QoI,
+// the solution output), else only its FP32 copy and the sum leave the pass.
 template <typename T, bool U64, typename TM, bool UPD = false>
-__global__ void __launch_bounds__(256) kb_qoi(FmgArgs A, int t, int B)
+__global__ void __launch_bounds__(256) kb_qoi(FmgArgs A, int t, int B, int keep64)
 {
     static_assert(!UPD || (U64 && sizeof(T) == 4), "the fused update is the mixed forms' refinement step");
     __shared__ double red[48];
@@ -1139,7 +1141,7 @@ __global__ void __launch_bounds__(256) kb_qoi(FmgArgs A, int t, int B)
 #pragma unroll
                 for (int k = 0; k < U; ++k) {
                     const double2 r = make_double2(w[k].x + widen(d[k].x), w[k].y + widen(d[k].y));
-                    u64[p + k * sz] = r;
+                    if (keep64) u64[p + k * sz] = r;
                     u[p + k * sz] = make_float2(narrow(r.x), narrow(r.y));
                     acc += r.x;
                     acc += r.y;
@@ -1149,7 +1151,7 @@ __global__ void __launch_bounds__(256) kb_qoi(FmgArgs A, int t, int B)
                 const double2 w = u64[p];
                 const float2 d = u[p];
                 const double2 r = make_double2(w.x + widen(d.x), w.y + widen(d.y));
-                u64[p] = r;
+                if (keep64) u64[p] = r;
                 u[p] = make_float2(narrow(r.x), narrow(r.y));
                 acc += r.x;
                 acc += r.y;
@@ -1185,7 +1187,7 @@ __global__ void __launch_bounds__(256) kb_qoi(FmgArgs A, int t, int B)
 // else the sum) and writes its partial sum; kb_qoi_final adds each sample's
 // partials in order.
 template <typename T, bool U64, bool UPD>
-__global__ void __launch_bounds__(256) kb_qoi_part(FmgArgs A, int t, int B, int P, double* part)
+__global__ void __launch_bounds__(256) kb_qoi_part(FmgArgs A, int t, int B, int P, double* part, int keep64)
 {
     static_assert(!UPD || (U64 && sizeof(T) == 4), "the fused update is the mixed forms' refinement step");
     __shared__ double red[48];
@@ -1215,10 +1217,15 @@ __global__ void __launch_bounds__(256) kb_qoi_part(FmgArgs A, int t, int B, int 
 #pragma unroll
                 for (int k = 0; k < U; ++k) {
                     if constexpr (UPD) {
-                        r[k] = make_double2(r[k].x + widen(d[k].x), r[k].y + widen(d[k].y));
-                        u64[p + k * kT] = r[k];
-                    }
-                    if constexpr (sizeof(T) == 4) {
+                        float2 h, lo;
+                        double2 rr = make_double2(0.0, 0.0);
+                        update_pair(r[k].x, d[k].x, keep64, h.x, lo.x, rr.x);
+                        update_pair(r[k].y, d[k].y, keep64, h.y, lo.y, rr.y);
+                        if (keep64) u64[p + k * kT] = rr;
+                        u[p + k * kT] = h;
+                        ps.add(h.x, lo.x);
+                        ps.add(h.y, lo.y);
+                    } else if constexpr (sizeof(T) == 4) {
                         const float2 h = make_float2(narrow(r[k].x), narrow(r[k].y));
                         u[p + k * kT] = h;
                         ps.add(h.x, narrow_rest(r[k].x, h.x));
@@ -1230,13 +1237,18 @@ __global__ void __launch_bounds__(256) kb_qoi_part(FmgArgs A, int t, int B, int 
                 }
             }
             for (; p < p1; p += kT) {
-                double2 r = u64[p];
+                const double2 r = u64[p];
                 if constexpr (UPD) {
                     const float2 d = u[p];
-                    r = make_double2(r.x + widen(d.x), r.y + widen(d.y));
-                    u64[p] = r;
-                }
-                if constexpr (sizeof(T) == 4) {
+                    float2 h, lo;
+                    double2 rr = make_double2(0.0, 0.0);
+                    update_pair(r.x, d.x, keep64, h.x, lo.x, rr.x);
+                    update_pair(r.y, d.y, keep64, h.y, lo.y, rr.y);
+                    if (keep64) u64[p] = rr;
+                    u[p] = h;
+                    ps.add(h.x, lo.x);
+                    ps.add(h.y, lo.y);
+                } else if constexpr (sizeof(T) == 4) {
                     const float2 h = make_float2(narrow(r.x), narrow(r.y));
                     u[p] = h;
                     ps.add(h.x, narrow_rest(r.x, h.x));
@@ -2207,24 +2219,26 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
         {
             // bytes: u (or u64) read, the FP32 copy written; fused update: u64 also
             // written and the correction read (FP64: update and sum)
-            const double qb = fuse_update ? 24.0 : (refine ? 8.0 : es) + (refine && sizeof(T) == 4 ? 4.0 : 0.0);
+            // u64 written back only when read later (centre QoI, solution output)
+            const int keep64 = (d_usol != nullptr || c->p.qoi != MLQMC_QOI_MEAN) ? 1 : 0;
+            const double qb = fuse_update ? (keep64 ? 24.0 : 16.0) : (refine ? 8.0 : es) + (refine && sizeof(T) == 4 ? 4.0 : 0.0);
             Timed tm(c, kProfReduce, st, work_of<double>(B * qb * Mc, B * (fuse_update ? 2.0 : 1.0) * Mc));
             if (n * n <= 4096) {  // one warp per sample
                 const int grid = std::max(1, std::min((B + 7) / 8, c->sm_count * 16));
-                if (fuse_update) kb_qoi<T, true, WarpTeam, MX><<<grid, 256, 0, st>>>(A, t, B);
-                else if (refine) kb_qoi<T, true, WarpTeam><<<grid, 256, 0, st>>>(A, t, B);
-                else kb_qoi<T, false, WarpTeam><<<grid, 256, 0, st>>>(A, t, B);
+                if (fuse_update) kb_qoi<T, true, WarpTeam, MX><<<grid, 256, 0, st>>>(A, t, B, keep64);
+                else if (refine) kb_qoi<T, true, WarpTeam><<<grid, 256, 0, st>>>(A, t, B, 1);
+                else kb_qoi<T, false, WarpTeam><<<grid, 256, 0, st>>>(A, t, B, 1);
             } else {  // chunks of a sample over several CTAs, partial sums added in order
                 const int P = qoi_chunks(c, t);
                 const bool pass = fuse_update || (refine && sizeof(T) == 4) || c->p.qoi == MLQMC_QOI_MEAN;
                 const int grid = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(B) * P, c->sm_count * 8));
                 if (pass) {
                     if constexpr (MX) {
-                        if (fuse_update) kb_qoi_part<T, true, true><<<grid, 256, 0, st>>>(A, t, B, P, c->d_qpart);
-                        else kb_qoi_part<T, true, false><<<grid, 256, 0, st>>>(A, t, B, P, c->d_qpart);
+                        if (fuse_update) kb_qoi_part<T, true, true><<<grid, 256, 0, st>>>(A, t, B, P, c->d_qpart, keep64);
+                        else kb_qoi_part<T, true, false><<<grid, 256, 0, st>>>(A, t, B, P, c->d_qpart, 1);
                     } else {
-                        if (refine) kb_qoi_part<T, true, false><<<grid, 256, 0, st>>>(A, t, B, P, c->d_qpart);
-                        else kb_qoi_part<T, false, false><<<grid, 256, 0, st>>>(A, t, B, P, c->d_qpart);
+                        if (refine) kb_qoi_part<T, true, false><<<grid, 256, 0, st>>>(A, t, B, P, c->d_qpart, 1);
+                        else kb_qoi_part<T, false, false><<<grid, 256, 0, st>>>(A, t, B, P, c->d_qpart, 1);
                     }
                 }
                 if (refine) kb_qoi_final<T, true><<<grid_for(c, B), 256, 0, st>>>(A, t, B, P, c->d_qpart);
