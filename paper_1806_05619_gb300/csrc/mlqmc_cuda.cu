@@ -1187,7 +1187,8 @@ __global__ void __launch_bounds__(256) kb_qoi(FmgArgs A, int t, int B, int keep6
 // else the sum) and writes its partial sum; kb_qoi_final adds each sample's
 // partials in order.
 template <typename T, bool U64, bool UPD>
-__global__ void __launch_bounds__(256) kb_qoi_part(FmgArgs A, int t, int B, int P, double* part, int keep64)
+__global__ void __launch_bounds__(256) kb_qoi_part(FmgArgs A, int t, int B, int P, double* part, int keep64,
+                                                   int interp32)
 {
     static_assert(!UPD || (U64 && sizeof(T) == 4), "the fused update is the mixed forms' refinement step");
     __shared__ double red[48];
@@ -1199,7 +1200,42 @@ __global__ void __launch_bounds__(256) kb_qoi_part(FmgArgs A, int t, int B, int 
         const int i = w / P, q = w - i * P;
         const int p0 = q * csz, p1 = min(np, p0 + csz);
         double acc = 0.0;
-        if constexpr (U64) {
+        if (UPD && interp32) {
+            // the interpolant U in FP32 (the level's field array): U + e exactly
+            // as the TwoSum pair, its high part the FP32 copy
+            PairSum ps;
+            const float2* kf = reinterpret_cast<const float2*>(at<float>(A.lv[t].k, i));
+            float2* u = reinterpret_cast<float2*>(at<float>(A.lv[t].u, i));
+            constexpr int U = 4;
+            int p = p0 + static_cast<int>(threadIdx.x);
+            for (; p + (U - 1) * kT < p1; p += U * kT) {
+                float2 w[U], d[U];
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+                    w[k] = kf[p + k * kT];
+                    d[k] = u[p + k * kT];
+                }
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+                    float2 h, lo;
+                    two_sum32(w[k].x, d[k].x, h.x, lo.x);
+                    two_sum32(w[k].y, d[k].y, h.y, lo.y);
+                    u[p + k * kT] = h;
+                    ps.add(h.x, lo.x);
+                    ps.add(h.y, lo.y);
+                }
+            }
+            for (; p < p1; p += kT) {
+                const float2 w = kf[p], d = u[p];
+                float2 h, lo;
+                two_sum32(w.x, d.x, h.x, lo.x);
+                two_sum32(w.y, d.y, h.y, lo.y);
+                u[p] = h;
+                ps.add(h.x, lo.x);
+                ps.add(h.y, lo.y);
+            }
+            acc = ps.value();
+        } else if constexpr (U64) {
             // mixed forms: the sum from the FP32 copy and its remainder (PairSum)
             PairSum ps;
             double2* u64 = reinterpret_cast<double2*>(at<double>(A.lv[t].u64, i));
@@ -2168,18 +2204,24 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
     // inside the QoI kernel, which reads u64 anyway
     const bool fuse_update = MX && refine && !(c->p.refine_rtol > 0.0);
     size_t uoff = static_cast<size_t>(A.lv[0].n) * A.lv[0].n;
+    // u64 written back by the fused update only when read later (centre QoI,
+    // solution output); otherwise, on the TMA interpolation levels, the
+    // interpolant itself travels in FP32 (interp32: in the level's field array)
+    const int keep64 = (d_usol != nullptr || c->p.qoi != MLQMC_QOI_MEAN) ? 1 : 0;
     for (int t = 1; t <= Lmax; ++t) {
         const int B = Bt[t];
         if (B == 0) break;
         LevelTag lt(c, t);
         const int64_t n = c->p.coarse_cells << t;
         const double es = sizeof(T), Mc = cells_of(c, t), Fc = faces_of(c, t);
+        const int interp32 = (fuse_update && !keep64 && mlqmc_resid::supported(static_cast<int>(n))) ? 1 : 0;
         if (refine && MX) {
             // the residual's 10 operations per cell run in FP32 error-free pairs: FP32 work
             Timed tm(c, kProfTransfer, st,
-                     work_of<float>(B * (es * 0.25 * Mc + 8.0 * Mc + es * (2.0 * Fc + Mc)), B * 10.0 * Mc));
+                     work_of<float>(B * (es * 0.25 * Mc + (interp32 ? 4.0 : 8.0) * Mc + es * (2.0 * Fc + Mc)),
+                                    B * 10.0 * Mc));
             if (mlqmc_resid::supported(n)) {
-                if (!mlqmc_resid::launch(A, t, n, B, c->sm_count, st)) return MLQMC_ERR_CUDA;
+                if (!mlqmc_resid::launch(A, t, n, B, interp32 != 0, c->sm_count, st)) return MLQMC_ERR_CUDA;
             } else {
                 kb_prolong_resid64<<<grid_for(c, B * (n / 2) * (n / 2)), 256, 0, st>>>(A, t, B);
             }
@@ -2219,9 +2261,8 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
         {
             // bytes: u (or u64) read, the FP32 copy written; fused update: u64 also
             // written and the correction read (FP64: update and sum)
-            // u64 written back only when read later (centre QoI, solution output)
-            const int keep64 = (d_usol != nullptr || c->p.qoi != MLQMC_QOI_MEAN) ? 1 : 0;
-            const double qb = fuse_update ? (keep64 ? 24.0 : 16.0) : (refine ? 8.0 : es) + (refine && sizeof(T) == 4 ? 4.0 : 0.0);
+            const double qb = fuse_update ? (keep64 ? 24.0 : interp32 ? 12.0 : 16.0)
+                                          : (refine ? 8.0 : es) + (refine && sizeof(T) == 4 ? 4.0 : 0.0);
             Timed tm(c, kProfReduce, st, work_of<double>(B * qb * Mc, B * (fuse_update ? 2.0 : 1.0) * Mc));
             if (n * n <= 4096) {  // one warp per sample
                 const int grid = std::max(1, std::min((B + 7) / 8, c->sm_count * 16));
@@ -2234,11 +2275,11 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
                 const int grid = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(B) * P, c->sm_count * 8));
                 if (pass) {
                     if constexpr (MX) {
-                        if (fuse_update) kb_qoi_part<T, true, true><<<grid, 256, 0, st>>>(A, t, B, P, c->d_qpart, keep64);
-                        else kb_qoi_part<T, true, false><<<grid, 256, 0, st>>>(A, t, B, P, c->d_qpart, 1);
+                        if (fuse_update) kb_qoi_part<T, true, true><<<grid, 256, 0, st>>>(A, t, B, P, c->d_qpart, keep64, interp32);
+                        else kb_qoi_part<T, true, false><<<grid, 256, 0, st>>>(A, t, B, P, c->d_qpart, 1, 0);
                     } else {
-                        if (refine) kb_qoi_part<T, true, false><<<grid, 256, 0, st>>>(A, t, B, P, c->d_qpart, 1);
-                        else kb_qoi_part<T, false, false><<<grid, 256, 0, st>>>(A, t, B, P, c->d_qpart, 1);
+                        if (refine) kb_qoi_part<T, true, false><<<grid, 256, 0, st>>>(A, t, B, P, c->d_qpart, 1, 0);
+                        else kb_qoi_part<T, false, false><<<grid, 256, 0, st>>>(A, t, B, P, c->d_qpart, 1, 0);
                     }
                 }
                 if (refine) kb_qoi_final<T, true><<<grid_for(c, B), 256, 0, st>>>(A, t, B, P, c->d_qpart);

@@ -13,7 +13,9 @@
 // (odd reflection across the coarse boundary: a fine cell's out-of-range
 // coarse neighbour is minus the value in its parent's own row or column), and
 // each quad cell's residual 1 - A u64 is formed from FP32 error-free pairs
-// (resid_f32x2) and rounded once to FP32; u64 gets the widened interpolant.
+// (resid_f32x2) and rounded once to FP32; u64 gets the widened interpolant
+// (interp32: the FP32 interpolant goes to the level's field array instead,
+// for the fixed-cycle forms whose refinement update reads it only as FP32).
 // The operations are those of the grid-stride form, value for value, so the
 // two give the same bits; this one reads every input once per tile from
 // shared memory instead of global memory.
@@ -58,7 +60,7 @@ struct Edge {
 };
 
 __global__ void __launch_bounds__(kThreads, kCtasPerSM)
-    kb_prolong_resid_tma(const __grid_constant__ Maps maps, FmgArgs A, int t, int B)
+    kb_prolong_resid_tma(const __grid_constant__ Maps maps, FmgArgs A, int t, int B, int interp32)
 {
     extern __shared__ __align__(128) unsigned char smraw[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smraw);
@@ -208,7 +210,11 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSM)
                                                  qx ? kyn[qy].y : kyn[qy].x, qx ? kys[qy].y : kys[qy].x};
                             r[qx] = resid_f32x2(kv, up, uv, ih2);
                         }
-                        *reinterpret_cast<double2*>(L.u64 + p) = make_double2(widen(U[qy + 1][1]), widen(U[qy + 1][2]));
+                        if (interp32)  // the interpolant in FP32, in the level's field array (no longer read)
+                            *reinterpret_cast<float2*>(L.k + p) = make_float2(U[qy + 1][1], U[qy + 1][2]);
+                        else
+                            *reinterpret_cast<double2*>(L.u64 + p) =
+                                make_double2(widen(U[qy + 1][1]), widen(U[qy + 1][2]));
                         *reinterpret_cast<float2*>(L.bc + p) = make_float2(r[0], r[1]);
                     }
                 }
@@ -245,7 +251,7 @@ bool prepare()
                                 static_cast<int>(kBytes)) == cudaSuccess;
 }
 
-bool launch(const FmgArgs& A, int t, int n, int B, int sm_count, cudaStream_t st)
+bool launch(const FmgArgs& A, int t, int n, int B, bool interp32, int sm_count, cudaStream_t st)
 {
     if (B <= 0) return true;
     if (!supported(n) || t < 1 || A.lv[t].n != n) return false;
@@ -259,7 +265,7 @@ bool launch(const FmgArgs& A, int t, int n, int B, int sm_count, cudaStream_t st
     if (!ok) return false;
     const int tiles = B * (n / kFX) * (n / kFY);
     const int cap = kCtasPerSM * sm_count;
-    kb_prolong_resid_tma<<<tiles < cap ? tiles : cap, kThreads, kBytes, st>>>(m, A, t, B);
+    kb_prolong_resid_tma<<<tiles < cap ? tiles : cap, kThreads, kBytes, st>>>(m, A, t, B, interp32 ? 1 : 0);
     return cudaGetLastError() == cudaSuccess;
 }
 

@@ -19,8 +19,10 @@ bool prepare();
 // samples 0..B-1 of A: u64 = P u_(t-1) (the FP32 copy of the coarse solution
 // interpolated in FP32, widened) and bc = 1 - A u64 rounded to FP32 from FP32
 // error-free pairs; inactive samples skipped. The same arithmetic, operand
-// for operand, as the grid-stride form in mlqmc_cuda.cu. Returns false when a
-// tensor map cannot be encoded or the launch fails.
-bool launch(const mlqmc_dev::FmgArgs& A, int t, int n, int B, int sm_count, cudaStream_t st);
+// for operand, as the grid-stride form in mlqmc_cuda.cu. interp32: the
+// interpolant is stored as FP32 in the level's field array k (whose field is
+// no longer read once the faces are formed) instead of widened into u64.
+// Returns false when a tensor map cannot be encoded or the launch fails.
+bool launch(const mlqmc_dev::FmgArgs& A, int t, int n, int B, bool interp32, int sm_count, cudaStream_t st);
 
 }  // namespace mlqmc_resid
