@@ -146,8 +146,8 @@ def peaks():
 
 KIND_KERNELS = {
     "points": "k_points", "level0": "kb_level0_fixed", "synth": "kb_synth_G/z, kb_faces",
-    "transfer": "kb_resid_restrict, kb_prolong(_resid64)", "coarse": "kb_coarse_fixed",
-    "reduce": "kb_qoi, k_sums", "kl_tc": "kl_tc_kernel (tcgen05)",
+    "transfer": "kb_prolong_resid_tma, kb_resid_restrict, kb_prolong(_resid64)", "coarse": "kb_coarse_fixed",
+    "reduce": "kb_qoi(_part), k_sums", "kl_tc": "kl_tc_kernel (tcgen05)",
 }
 SMOOTHER_KERNELS = {"whole": "kb_rbgs_whole", "tma": "kb_rbgs_tma", "stream": "kb_rbgs_stream", "tile": "kb_rbgs_tile",
                     "gs": "kb_gs"}

@@ -392,6 +392,31 @@ def _mixed_F(ctx, cfg, work, names):
     return out
 
 
+def test_fp32_interpolant_path_matches_fp64_store():
+    """Fixed-cycle mixed form with the mean QoI: a plain sampling call carries
+    the FMG interpolant of the TMA levels (128x128, 256x256) in FP32 and forms
+    each level's one refinement update as an exact FP32 pair; a call that asks
+    for the solution keeps the FP64 store (u64 += e in FP64). Both are the
+    same update of the same numbers, so per-level F agree to the FP32 pair
+    sum's accuracy (1e-12 relative), and both match the oracle within the
+    TF32 field bound."""
+    cfg, ctx, orc = _pair(W.LATTICE_6LEVEL, R=2, precision="mixed_tf32")
+    nl = cfg["n_levels"]
+    for (lv, r, n) in [(5, 0, 0), (5, 1, 3), (4, 0, 1)]:
+        sums = torch.zeros(nl * cfg["R"] * 2, dtype=torch.float64, device="cuda")
+        F = torch.zeros(nl, dtype=torch.float64, device="cuda")
+        ctx.sample_levels([(lv, n, n + 1, r, r + 1)], sums, F)
+        torch.cuda.synchronize()
+        ctx.check_device()
+        _, Fs = ctx.sample_solution(lv, r, n)
+        a = F.cpu().numpy()[:lv + 1]
+        b = Fs.cpu().numpy()
+        assert _rel(a, b) <= 1e-12, (lv, r, n, a, b)
+        ref = orc.sample(lv, r, n)
+        eta = _field_bound(orc, cfg, orc.normals(lv, r, n), _tf32_u(cfg["s"])) + EXP_SLACK
+        assert np.max(np.abs(a / ref["F"] - 1)) <= math.expm1(eta) + 1e-9
+
+
 def test_smoothers_agree_fixed_cycles():
     """Mixed form, fixed cycles (6 levels up to 256x256): the wavefront and
     whole-sample smoothers (residual and correction fused), TMA-tile and
