@@ -138,7 +138,8 @@ __global__ void k_points(const SampleDesc* __restrict__ smp, int count, int s, i
 // synthesis, as k_coef32) and its TF32 rounding (the tensor-core C operand,
 // zero-padded to kpad columns, as kl_build_c), in one pass over (sample,
 // column): the three kernels' values without re-reading Y. Samples in rank
-// order with canon = rank (the batched calls).
+// order with canon = rank (the batched calls). Y and c32 may be null (every
+// level's field from the tensor cores: only C is read).
 __global__ void k_points_mixed(const SampleDesc* __restrict__ smp, int count, int s, int kpad, FastDiv by_kpad,
                                int sampler, uint64_t seed, const uint32_t* __restrict__ z,
                                const uint64_t* __restrict__ tab, int R, const double* __restrict__ sq,
@@ -159,9 +160,9 @@ __global__ void k_points_mixed(const SampleDesc* __restrict__ smp, int count, in
         const uint64_t kk = lo ? k : ((1ull << 53) - 1ull) - k;
         const float y = normcdfinvf(fmaf(__ull2float_rn(kk), 0x1p-53f, 0x1p-54f));
         const double yw = widen(lo ? y : -y);
-        Y[static_cast<size_t>(d.canon) * s + m] = yw;
+        if (Y) Y[static_cast<size_t>(d.canon) * s + m] = yw;
         const float pf = narrow(sq[m] * yw);
-        c32[static_cast<size_t>(i) * s + m] = pf;
+        if (c32) c32[static_cast<size_t>(i) * s + m] = pf;
         uint32_t r;
         asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(pf));
         C[idx] = __uint_as_float(r);
@@ -1654,7 +1655,20 @@ mlqmc_status launch_level0(mlqmc_ctx* c, const FmgArgs& A, int B, cudaStream_t s
                    (8.0 + es) * N0 + 8.0);
     w.f64 = B * (N0 * n0 * n0 + 4.0 * N0 * n0);
     Timed tm(c, kProfSmall, st, w);
-    const int g64 = std::max(1, std::min((B + 63) / 64, c->sm_count * 8));
+    // n0 = 8: one wave of resident CTAs (shared memory allows five per SM),
+    // each looping over its samples, so that all of them are placed at once
+    // and the other stream's kernels are not queued behind a second wave
+    int per_sm = 8;
+    if (c->p.coarse_cells == 8) {
+        const bool mx = is_mixed(c->p);
+        if (!ok(mx ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_level0_fixed<float, true, 8>, 64,
+                                                                  level0_smem<8>())
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_level0_fixed<double, false, 8>, 64,
+                                                                  level0_smem<8>())))
+            return MLQMC_ERR_CUDA;
+        per_sm = std::max(1, per_sm);
+    }
+    const int g64 = std::max(1, std::min((B + 63) / 64, c->sm_count * per_sm));
     if (c->p.coarse_cells == 8) {
         if (is_mixed(c->p)) kb_level0_fixed<float, true, 8><<<g64, 64, level0_smem<8>(), st>>>(A, B);
         else kb_level0_fixed<double, false, 8><<<g64, 64, level0_smem<8>(), st>>>(A, B);
@@ -1729,16 +1743,20 @@ bool uses_tc(const mlqmc_ctx* c, int t)
     return c->kl_tc && c->d_psi_tc[t] != nullptr;
 }
 
+enum class SynthPart { all, field, faces };
+
 // Batched KL field and faces of level t for samples 0..B-1. The field comes
 // from the tensor-core contraction (mixed forms, every level)
 // or from the separable SIMT sum; the C operand must already be built.
+// part: the tensor-core field alone, or the faces alone (after it).
 template <typename T>
-mlqmc_status synth_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cudaStream_t st)
+mlqmc_status synth_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cudaStream_t st,
+                           SynthPart part = SynthPart::all)
 {
     LevelTag lt(c, t);
     const int64_t n = c->p.coarse_cells << t;
     if constexpr (sizeof(T) == 4) {
-        if (uses_tc(c, t)) {
+        if (uses_tc(c, t) && part != SynthPart::faces) {
             const LevelPool& P = c->pools[t];
             float* k = reinterpret_cast<float*>(P.mem + P.off[kK]);
             const double M = static_cast<double>(n * n);
@@ -1752,7 +1770,8 @@ mlqmc_status synth_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cudaStr
                 return MLQMC_ERR_CUDA;
         }
     }
-    if (c->matern && (!uses_tc(c, t) || sizeof(T) != 4)) {
+    if (part == SynthPart::faces) {
+    } else if (c->matern && (!uses_tc(c, t) || sizeof(T) != 4)) {
         const double M = static_cast<double>(n * n), sm = c->p.n_modes;
         Timed tm(c, kProfSynth, st,
                  work_of<T>(8.0 * M * sm * std::ceil(B / static_cast<double>(kDenseG)) + sizeof(T) * M * B,
@@ -1778,6 +1797,7 @@ mlqmc_status synth_batched(mlqmc_ctx* c, const FmgArgs& A, int t, int B, cudaStr
             kb_synth_z<T><<<grid_for(c, B * n * n), 256, 0, st>>>(A, t, B);
         }
     }
+    if (part == SynthPart::field) return last_error();
     const double es = sizeof(T), Mc = cells_of(c, t), Fc = faces_of(c, t);
     {
         Timed tm(c, kProfSynth, st, work_of<T>(B * es * (Mc + 2.0 * Fc), B * 6.0 * Fc));
@@ -2471,18 +2491,24 @@ mlqmc_status run_chunk(mlqmc_ctx* c, int count, const int* Bt, int Lmax, double*
     FmgArgs A = base_args(c);
     mlqmc_status s = MLQMC_OK;
     const int kpad = c->kl_tc ? static_cast<int>(mlqmc_kl::row_bytes(c->kl_variant, p.n_modes) / 4) : 0;
+    // every level's field from the tensor cores: the normals and the FP32
+    // coefficients of the SIMT synthesis are not read
+    bool all_tc = true;
+    for (int t = 0; t <= Lmax; ++t) all_tc = all_tc && uses_tc(c, t);
     if (is_mixed(p) && !c->matern && c->kl_tc && c->kl_variant == mlqmc_kl::Variant::TF32 &&
         static_cast<int64_t>(count) * kpad < (int64_t{1} << 31)) {
         // normals, FP32 coefficients and the C operand in one pass
         const int64_t total = static_cast<int64_t>(count) * kpad;
         Timed tm(c, kProfPoints, st,
-                 work_of<float>(static_cast<double>(count) * (p.n_modes * 12.0 + kpad * 4.0 + sizeof(SampleDesc)), 0.0));
-        k_points_mixed<<<grid_for(c, total), 256, 0, st>>>(c->d_samples, count, p.n_modes, kpad,
-                                                           FastDiv(static_cast<uint32_t>(kpad)), p.sampler, p.seed,
-                                                           c->d_z, c->d_shift, p.n_shifts, c->d_sqrt_theta, c->d_Y,
-                                                           c->d_c32, static_cast<float*>(c->d_C));
+                 work_of<float>(static_cast<double>(count) * (p.n_modes * (all_tc ? 0.0 : 12.0) + kpad * 4.0 +
+                                                              sizeof(SampleDesc)),
+                                0.0));
+        k_points_mixed<<<grid_for(c, total), 256, 0, st>>>(
+            c->d_samples, count, p.n_modes, kpad, FastDiv(static_cast<uint32_t>(kpad)), p.sampler, p.seed, c->d_z,
+            c->d_shift, p.n_shifts, c->d_sqrt_theta, all_tc ? nullptr : c->d_Y, all_tc ? nullptr : c->d_c32,
+            static_cast<float*>(c->d_C));
         if (last_error() != MLQMC_OK) return MLQMC_ERR_CUDA;
-        c->c32_ready = true;
+        c->c32_ready = !all_tc;
     } else {
         s = launch_points(c, c->d_samples, count, c->d_Y, nullptr, st);
         if (s != MLQMC_OK) return s;
@@ -2491,7 +2517,7 @@ mlqmc_status run_chunk(mlqmc_ctx* c, int count, const int* Bt, int Lmax, double*
     }
     // mixed forms, separable modes: FP32 coefficients of all the chunk's
     // samples once, before both streams' SIMT syntheses read them
-    if (is_mixed(p) && !c->matern && !c->c32_ready) {
+    if (is_mixed(p) && !c->matern && !c->c32_ready && !all_tc) {
         Timed tm(c, kProfSynth, st, work_of<double>(count * 12.0 * p.n_modes, count * 1.0 * p.n_modes));
         k_coef32<<<grid_for(c, static_cast<int64_t>(count) * p.n_modes), 256, 0, st>>>(A, count, c->d_sqrt_theta,
                                                                                         c->d_c32);
@@ -2505,10 +2531,25 @@ mlqmc_status run_chunk(mlqmc_ctx* c, int count, const int* Bt, int Lmax, double*
         return MLQMC_ERR_CUDA;
     }
     s = is_mixed(p) ? synth_batched<float>(c, A, 0, Bt[0], c->side) : synth_batched<double>(c, A, 0, Bt[0], c->side);
-    if (s == MLQMC_OK) s = launch_level0(c, A, Bt[0], c->side);
-    if (!ok(cudaEventRecord(c->ev_join, c->side))) s = MLQMC_ERR_CUDA;
-    for (int t = 1; s == MLQMC_OK && t <= Lmax && Bt[t] > 0; ++t)
-        s = is_mixed(p) ? synth_batched<float>(c, A, t, Bt[t], st) : synth_batched<double>(c, A, t, Bt[t], st);
+    if (is_mixed(p) && all_tc) {
+        // the persistent contractions cannot start beside the factorisation's
+        // CTAs (both need most of an SM's shared memory): the main stream
+        // issues the other levels' contractions first, the factorisation
+        // follows them and runs beside those levels' faces
+        for (int t = 1; s == MLQMC_OK && t <= Lmax && Bt[t] > 0; ++t)
+            s = synth_batched<float>(c, A, t, Bt[t], st, SynthPart::field);
+        if (!ok(cudaEventRecord(c->ev_fields, st)) || !ok(cudaStreamWaitEvent(c->side, c->ev_fields, 0)))
+            s = MLQMC_ERR_CUDA;
+        if (s == MLQMC_OK) s = launch_level0(c, A, Bt[0], c->side);
+        if (!ok(cudaEventRecord(c->ev_join, c->side))) s = MLQMC_ERR_CUDA;
+        for (int t = 1; s == MLQMC_OK && t <= Lmax && Bt[t] > 0; ++t)
+            s = synth_batched<float>(c, A, t, Bt[t], st, SynthPart::faces);
+    } else {
+        if (s == MLQMC_OK) s = launch_level0(c, A, Bt[0], c->side);
+        if (!ok(cudaEventRecord(c->ev_join, c->side))) s = MLQMC_ERR_CUDA;
+        for (int t = 1; s == MLQMC_OK && t <= Lmax && Bt[t] > 0; ++t)
+            s = is_mixed(p) ? synth_batched<float>(c, A, t, Bt[t], st) : synth_batched<double>(c, A, t, Bt[t], st);
+    }
     if (!ok(cudaStreamWaitEvent(st, c->ev_join, 0)) && s == MLQMC_OK) s = MLQMC_ERR_CUDA;
     c->c32_ready = false;
     if (s != MLQMC_OK) return s;
@@ -2585,6 +2626,7 @@ void free_ctx(mlqmc_ctx* c)
     cudaFree(c->d_c32);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_fields) cudaEventDestroy(c->ev_fields);
     if (c->side) cudaStreamDestroy(c->side);
     for (auto& m : c->marks) {
         cudaEventDestroy(m.a);
@@ -2809,7 +2851,8 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
            ok(cudaEventCreateWithFlags(&c->staged, cudaEventDisableTiming)) &&
            ok(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) &&
            ok(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) &&
-           ok(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+           ok(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)) &&
+           ok(cudaEventCreateWithFlags(&c->ev_fields, cudaEventDisableTiming));
     if (!good) {
         free_ctx(c);
         return MLQMC_ERR_OOM;

@@ -152,9 +152,11 @@ struct mlqmc_ctx {
     int* h_count = nullptr;           // pinned
     cudaEvent_t staged = nullptr;     // recorded after the last copy out of the staging buffer
     // level 0 (its field, faces and banded factorisation) runs on a second
-    // stream beside the other levels' fields: fork and join by events
+    // stream beside the other levels' fields: fork and join by events; with
+    // every field from the tensor cores the factorisation waits for ev_fields
+    // (the other levels' contractions issued) and runs beside their faces
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fields = nullptr;
     size_t chol_stride = 0;
 
     // level pools, grown on demand; chunks are cut to fit pool_budget bytes
