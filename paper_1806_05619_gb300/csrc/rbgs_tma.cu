@@ -602,22 +602,36 @@ __global__ void __launch_bounds__(BGeom<TY, POST>::threads, BGeom<TY, POST>::cta
                     bv[r][0] = v.x, bv[r][1] = v.y;
                 }
             }
-            auto diag = [&](auto all_in) {
+            // cells outside the domain get a zero reciprocal diagonal, so that
+            // they stay 0 (their h^2 b is finite: the TMA's zero fill, or 1);
+            // the column and row tests only where the tile's frame leaves the
+            // domain on that axis (tile-uniform)
+            auto diag = [&](auto cols_in, auto rows_in) {
+                constexpr bool CA = decltype(cols_in)::value, RA = decltype(rows_in)::value;
+                const int gy0 = y0 - kH + sy0, gx0 = x0 - kH + sx0;
+                bool ci[2], ri[4];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) ci[j] = CA || static_cast<unsigned>(gx0 + j) < static_cast<unsigned>(n);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) ri[r] = RA || static_cast<unsigned>(gy0 + r) < static_cast<unsigned>(n);
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
-                    const int gy = y0 - kH + sy0 + r;
 #pragma unroll
                     for (int j = 0; j < 2; ++j) {
-                        const int gx = x0 - kH + sx0 + j;
-                        const bool in = decltype(all_in)::value || (gy >= 0 && gy < n && gx >= 0 && gx < n);
                         const float d = fx[r][j] + fx[r][j + 1] + fy[r][j] + fy[r + 1][j];
-                        id[r][j] = in ? __fdividef(1.0f, d) : 0.0f;
-                        cb[r][j] = in ? h2 * bv[r][j] : 0.0f;
+                        const float q = __fdividef(1.0f, d);
+                        id[r][j] = (CA || ci[j]) && (RA || ri[r]) ? q : 0.0f;
+                        cb[r][j] = h2 * bv[r][j];
                     }
                 }
             };
-            if (x0 >= kH && x0 + TX + kH <= n && y0 >= kH && y0 + TY + kH <= n) diag(Flag<true>());
-            else diag(Flag<false>());
+            {
+                const bool ax = x0 >= kH && x0 + TX + kH <= n, ay = y0 >= kH && y0 + TY + kH <= n;
+                if (ax && ay) diag(Flag<true>(), Flag<true>());
+                else if (ay) diag(Flag<false>(), Flag<true>());
+                else if (ax) diag(Flag<true>(), Flag<false>());
+                else diag(Flag<false>(), Flag<false>());
+            }
             if constexpr (POST) {
                 // coarse-grid correction (odd reflection at the coarse boundary, as
                 // in the square-block form): the thread's two columns share the
@@ -627,48 +641,64 @@ __global__ void __launch_bounds__(BGeom<TY, POST>::threads, BGeom<TY, POST>::cta
                 const int I1 = (x0 - kH) / 2 + lane, I2a = (y0 - kH) / 2 + 2 * w;
                 // away from the coarse boundary (every parent and its neighbours
                 // inside the coarse grid) no reflection is needed
-                const bool inner = x0 >= 6 && x0 + TX + 6 <= n && y0 >= 6 && y0 + TY + 6 <= n;
-                auto correct = [&](auto reflect) {
-                    constexpr bool R = decltype(reflect)::value;
-                    if (R && (I1 < 0 || I1 >= nc)) return;
+                const bool inx = x0 >= 6 && x0 + TX + 6 <= n, iny = y0 >= 6 && y0 + TY + 6 <= n;
+                auto correct = [&](auto reflect_x, auto reflect_y) {
+                    constexpr bool RX = decltype(reflect_x)::value, RY = decltype(reflect_y)::value;
+                    if (RX && (I1 < 0 || I1 >= nc)) return;
                     const float* sc = se + (2 * w + 1) * ECX + lane + 1;  // coarse (I2a - 1, I1 - 1)
                     float C[4][3];
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
 #pragma unroll
                         for (int b = 0; b < 3; ++b) C[a][b] = sc[a * ECX + b];
-                    const bool lo1 = R && I1 == 0, hi1 = R && I1 == nc - 1;
+                    // the odd reflection written into the coarse block: a ghost
+                    // column is minus the boundary column beside it, then a ghost
+                    // row minus the row beside it (so a ghost corner is plus the
+                    // boundary cell); row a holds coarse row I2a - 1 + a
+                    if constexpr (RX) {
+                        if (I1 == 0) {
+#pragma unroll
+                            for (int a = 0; a < 4; ++a) C[a][0] = -C[a][1];
+                        }
+                        if (I1 == nc - 1) {
+#pragma unroll
+                            for (int a = 0; a < 4; ++a) C[a][2] = -C[a][1];
+                        }
+                    }
+                    if constexpr (RY) {
+#pragma unroll
+                        for (int a = 2; a >= 0; --a)
+                            if (I2a - 1 + a < 0) {
+#pragma unroll
+                                for (int b = 0; b < 3; ++b) C[a][b] = -C[a + 1][b];
+                            }
+#pragma unroll
+                        for (int a = 1; a < 4; ++a)
+                            if (I2a - 1 + a >= nc) {
+#pragma unroll
+                                for (int b = 0; b < 3; ++b) C[a][b] = -C[a - 1][b];
+                            }
+                    }
 #pragma unroll
                     for (int pr = 0; pr < 2; ++pr) {
                         const int I2 = I2a + pr;
-                        if (R && (I2 < 0 || I2 >= nc)) continue;
-                        const bool lo2 = R && I2 == 0, hi2 = R && I2 == nc - 1;
-                        float E[3][3];
-#pragma unroll
-                        for (int dy = -1; dy <= 1; ++dy) {
-#pragma unroll
-                            for (int dx = -1; dx <= 1; ++dx) {
-                                const bool ry = (dy < 0 && lo2) || (dy > 0 && hi2);
-                                const bool rx = (dx < 0 && lo1) || (dx > 0 && hi1);
-                                const float a = rx ? C[pr + 1 + dy][1] : C[pr + 1 + dy][1 + dx];
-                                const float b = rx ? C[pr + 1][1] : C[pr + 1][1 + dx];
-                                const float v = ry ? b : a;
-                                E[dy + 1][dx + 1] = (ry != rx) ? -v : v;
-                            }
-                        }
+                        if (RY && (I2 < 0 || I2 >= nc)) continue;
 #pragma unroll
                         for (int fy2 = 0; fy2 < 2; ++fy2) {
 #pragma unroll
                             for (int fx2 = 0; fx2 < 2; ++fx2) {
-                                const int dy = 2 * fy2, dx = 2 * fx2;
+                                const int dy = 2 * fy2, dx = 2 * fx2;  // E[i][j] = C[pr + i][j]
                                 uu[2 * pr + fy2][fx2] +=
-                                    fmaf(0.5625f, E[1][1], fmaf(0.1875f, E[1][dx] + E[dy][1], 0.0625f * E[dy][dx]));
+                                    fmaf(0.5625f, C[pr + 1][1],
+                                         fmaf(0.1875f, C[pr + 1][dx] + C[pr + dy][1], 0.0625f * C[pr + dy][dx]));
                             }
                         }
                     }
                 };
-                if (inner) correct(Flag<false>());
-                else correct(Flag<true>());
+                if (inx && iny) correct(Flag<false>(), Flag<false>());
+                else if (iny) correct(Flag<true>(), Flag<false>());
+                else if (inx) correct(Flag<false>(), Flag<true>());
+                else correct(Flag<true>(), Flag<true>());
                 *reinterpret_cast<float2*>(su + uix(sy0, sx0)) = make_float2(uu[0][0], uu[0][1]);
                 *reinterpret_cast<float2*>(su + uix(sy0 + 3, sx0)) = make_float2(uu[3][0], uu[3][1]);
                 __syncthreads();
