@@ -140,11 +140,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSM)
             const float* skx = S + oKX;
             const float* sky = S + oKY;
             const Lv<float> L = view<float>(A, t, i);
-            // a tile whose parents and their neighbours all lie inside the coarse
-            // grid needs neither the reflection nor the range tests (uniform per CTA)
-            const bool inner = I1_0 >= 1 && I1_0 + kCX + 1 <= nc && I2_0 >= 1 && I2_0 + kCY + 1 <= nc;
-            auto quads = [&](auto edge) {
-                constexpr bool EDGE = decltype(edge)::value;
+            // the tile's parents all lie inside the coarse grid; the reflection
+            // and the zero cells outside the fine grid only on an axis where
+            // the tile reaches the coarse boundary (uniform per CTA)
+            const bool ex = I1_0 == 0 || I1_0 + kCX >= nc, ey = I2_0 == 0 || I2_0 + kCY >= nc;
+            auto quads = [&](auto edge_x, auto edge_y) {
+                constexpr bool EX = decltype(edge_x)::value, EY = decltype(edge_y)::value;
 #pragma unroll 1
                 for (int k = 0; k < 2; ++k) {
                     const int q = static_cast<int>(threadIdx.x) + k * kThreads;
@@ -165,12 +166,30 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSM)
 #pragma unroll
                     for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
-                        for (int dx = -1; dx <= 1; ++dx) {
-                            const int x = I1 + dx, y = I2 + dy;
-                            const bool ox = EDGE && (x < 0 || x >= nc), oy = EDGE && (y < 0 || y >= nc);
-                            const float v = se[(cy + 1 + (oy ? 0 : dy)) * kEW + cx + 4 + (ox ? 0 : dx)];
-                            E[dy + 1][dx + 1] = (ox != oy) ? -v : v;
+                        for (int dx = -1; dx <= 1; ++dx) E[dy + 1][dx + 1] = se[(cy + 1 + dy) * kEW + cx + 4 + dx];
+                    // odd reflection across the coarse boundary, written into the
+                    // block: a ghost column is minus the parent's column, then a
+                    // ghost row minus the parent's row (a ghost corner: plus the parent)
+                    if constexpr (EX) {
+                        if (I1 == 0) {
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) E[a][0] = -E[a][1];
                         }
+                        if (I1 == nc - 1) {
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) E[a][2] = -E[a][1];
+                        }
+                    }
+                    if constexpr (EY) {
+                        if (I2 == 0) {
+#pragma unroll
+                            for (int b = 0; b < 3; ++b) E[0][b] = -E[1][b];
+                        }
+                        if (I2 == nc - 1) {
+#pragma unroll
+                            for (int b = 0; b < 3; ++b) E[2][b] = -E[1][b];
+                        }
+                    }
                     // fine cells 2I + f, f = -1..2 per axis (the four ring corners unused):
                     // parent offset (f - 1) / 2 rounded down, coarse neighbour towards the
                     // cell's side (+1 for odd f, -1 for even f); cells outside the grid are 0
@@ -184,11 +203,6 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSM)
                                 U[fy + 1][fx + 1] = 0.0f;
                                 continue;
                             }
-                            const int i1 = 2 * I1 + fx, i2 = 2 * I2 + fy;
-                            if (EDGE && (i1 < 0 || i1 >= n || i2 < 0 || i2 >= n)) {
-                                U[fy + 1][fx + 1] = 0.0f;
-                                continue;
-                            }
                             const int px = fx < 0 ? -1 : (fx > 1 ? 1 : 0), py = fy < 0 ? -1 : (fy > 1 ? 1 : 0);
                             const int sx = (fx & 1) ? 1 : -1, sy = (fy & 1) ? 1 : -1;
                             const float a = E[py + 1][px + 1];
@@ -197,6 +211,15 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSM)
                             const float d = E[py + sy + 1][px + sx + 1];
                             U[fy + 1][fx + 1] = fmaf(0.5625f, a, fmaf(0.1875f, bx + cyv, 0.0625f * d));
                         }
+                    // ring cells outside the fine grid are 0 (fine cell 2 I + f, f = -1 or 2)
+                    if constexpr (EX) {
+                        if (I1 == 0) U[1][0] = U[2][0] = 0.0f;
+                        if (I1 == nc - 1) U[1][3] = U[2][3] = 0.0f;
+                    }
+                    if constexpr (EY) {
+                        if (I2 == 0) U[0][1] = U[0][2] = 0.0f;
+                        if (I2 == nc - 1) U[3][1] = U[3][2] = 0.0f;
+                    }
 #pragma unroll
                     for (int qy = 0; qy < 2; ++qy) {
                         const int i1 = 2 * I1, i2 = 2 * I2 + qy;
@@ -219,8 +242,10 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSM)
                     }
                 }
             };
-            if (inner) quads(Edge<false>());
-            else quads(Edge<true>());
+            if (!ex && !ey) quads(Edge<false>(), Edge<false>());
+            else if (!ey) quads(Edge<true>(), Edge<false>());
+            else if (!ex) quads(Edge<false>(), Edge<true>());
+            else quads(Edge<true>(), Edge<true>());
         }
         // this buffer is refilled by the TMA next iteration: order the generic accesses first
         fence_proxy_async();
