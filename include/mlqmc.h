@@ -57,7 +57,7 @@ typedef enum { MLQMC_QOI_CENTER = 0, MLQMC_QOI_MEAN = 1 } mlqmc_qoi;
 /* Smoother of a level's red-black sweeps (all compute the same sweeps). */
 typedef enum {
     MLQMC_SMOOTHER_GS = 0,     /* one launch per colour (FP64 form) */
-    MLQMC_SMOOTHER_TILE = 1,   /* shared-memory tiles staged by plain loads, two sweeps per launch */
+    MLQMC_SMOOTHER_TILE = 1,   /* shared-memory tiles staged by plain loads (FP32: two sweeps per launch, FP64: one) */
     MLQMC_SMOOTHER_STREAM = 2, /* row wavefront with bulk-copy rings, residual/correction fused (n <= 256) */
     MLQMC_SMOOTHER_TMA = 3,    /* 32 x 32 tiles staged by TMA tensor copies, double-buffered (n >= 64) */
     MLQMC_SMOOTHER_WHOLE = 4   /* the whole grid of a sample in shared memory, residual/correction fused (n <= 64) */
@@ -463,8 +463,11 @@ int64_t mlqmc_launch_count(const mlqmc_ctx* c);
  * [level][kind] milliseconds of the tuning visit, 0 where not timed); either
  * may be NULL. The FP64 form takes a fixed rule, so that every context gives
  * the same bits: MLQMC_SMOOTHER_WHOLE for n <= 64, MLQMC_SMOOTHER_GS above
- * (both multiply by the stored FP64 1/D and agree to rounding); the others
- * are FP32 only.
+ * (both multiply by the stored FP64 1/D and agree to rounding).
+ * MLQMC_SMOOTHER_TILE also runs the FP64 form (one sweep per launch on
+ * 32 x 32 tiles, sides 8, 16 or a multiple of 32; kb_gs's operations in
+ * kb_gs's order) but is slower there, FP64 issue being the limit on GB300;
+ * the wavefront and TMA smoothers are FP32 only.
  * mlqmc_set_smoother: force `kind` on `level` (1 <= level < n_levels) for
  * later calls; MLQMC_ERR_INVALID_ARG if that smoother cannot run the level
  * in the context's form (GS in a mixed form, an FP32-only smoother in the

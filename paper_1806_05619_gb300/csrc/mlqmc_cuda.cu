@@ -683,83 +683,101 @@ __global__ void kb_gs(FmgArgs A, int t, int B, int colour, int ones)
 }
 
 // NS full red-black sweeps of one TILE x TILE tile per CTA iteration (temporal
-// blocking, FP32): u, 1/D and b are staged in shared memory with a halo of 4
-// cells on each side (128-bit loads from 16-byte aligned rows, zeros outside
-// the domain, which is the Dirichlet ghost value), the x and y faces of the
-// same region too; the NS sweeps consume 2*NS of that halo.
+// blocking): u, 1/D and b are staged in shared memory with a halo of H cells
+// on each side (16-byte loads from 16-byte aligned rows, zeros outside the
+// domain, which is the Dirichlet ghost value), the x and y faces of the same
+// region too; the NS sweeps consume 2*NS of that halo. FP32 (mixed forms) and
+// FP64 (FP64 form, one sweep per launch: FP64 arithmetic is the scarce
+// resource on GB300, so the halo is kept at the 2 cells one sweep consumes).
 // u is read from u and written to u2 (ping-pong, so no tile reads a
 // neighbour's half-updated cells). Phase p updates its colour on the tile
-// grown by H-1-p; the result equals NS passes of kb_gs over both colours.
+// grown by 2*NS-1-p with the operations of gs_cell in its order (an outside
+// neighbour is a staged zero, whose product adds exactly nothing); the result
+// equals NS passes of kb_gs over both colours, bit for bit.
 // first: colour of the first half sweep (0 red for pre-smoothing, 1 black).
 // PROLONG: the staged u first receives the coarse-grid correction P e from
 // level t-1 (post-smoothing of the V-cycle), as kb_prolong would add it.
-template <int TILE, int NS, bool PROLONG>
+template <typename T, int NS>
+struct TileHalo {
+    static constexpr int H = (sizeof(T) == 8 && NS == 1) ? 2 : 4;  // x0 - H stays 16-byte aligned
+};
+
+template <typename T, int TILE, int NS, bool PROLONG>
 __global__ void __launch_bounds__(256) kb_rbgs_tile(FmgArgs A, int t, int B, int ones, int first)
 {
     static_assert(NS == 1 || NS == 2, "one or two sweeps per launch");
-    constexpr int H = 4;              // staged halo: keeps x0 - H a multiple of 4 (16-byte loads)
-    constexpr int HN = 2 * NS;        // halo the NS sweeps consume
-    constexpr int SU = TILE + 2 * H;  // staged side (multiple of 4)
-    constexpr int V = SU / 4;         // float4 per staged row
-    static_assert(SU % 4 == 0, "staged rows are whole float4");
+    using V16 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    constexpr int VW = 16 / static_cast<int>(sizeof(T));  // elements per 16-byte vector
+    constexpr int H = TileHalo<T, NS>::H;                  // staged halo
+    constexpr int HN = 2 * NS;                             // halo the NS sweeps consume
+    constexpr int SU = TILE + 2 * H;                       // staged side
+    constexpr int V = SU / VW;                             // vectors per staged row
+    static_assert(SU % VW == 0 && H % VW == 0 && H >= HN, "staged rows are whole 16-byte vectors");
     extern __shared__ float4 smraw4[];
-    float* su = reinterpret_cast<float*>(smraw4);  // SU x SU
-    float* sid = su + SU * SU;                       // SU x SU
-    float* sb = sid + SU * SU;                       // SU x SU
-    float* sky = sb + SU * SU;                       // (SU + 1) face rows x SU
-    float* skx = sky + (SU + 1) * SU;                // SU rows x (SU + 1) faces
+    T* su = reinterpret_cast<T*>(smraw4);  // SU x SU
+    T* sid = su + SU * SU;                 // SU x SU
+    T* sb = sid + SU * SU;                 // SU x SU
+    T* sky = sb + SU * SU;                 // (SU + 1) face rows x SU
+    T* skx = sky + (SU + 1) * SU;          // SU rows x (SU + 1) faces
     const int n = A.lv[t].n;
     const int tx_n = n / TILE;
     const uint32_t per = static_cast<uint32_t>(tx_n) * static_cast<uint32_t>(tx_n);
-    const float h2 = 1.0f / (static_cast<float>(n) * static_cast<float>(n));
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const T h2 = T(1) / (static_cast<T>(n) * static_cast<T>(n));
+    V16 z4, o4;
+    {
+        T* zp = reinterpret_cast<T*>(&z4);
+        T* op = reinterpret_cast<T*>(&o4);
+#pragma unroll
+        for (int j = 0; j < VW; ++j) zp[j] = T(0), op[j] = T(1);
+    }
     for (int64_t tile = blockIdx.x; tile < B * per; tile += gridDim.x) {
         const int i = static_cast<int>(tile / per);
         if (inactive(A, i)) continue;
         const int tr = static_cast<int>(tile - i * per);
         const int y0 = (tr / tx_n) * TILE, x0 = (tr % tx_n) * TILE;
-        const Lv<float> L = view<float>(A, t, i);
-        float* uo = at<float>(A.lv[t].u2, i);
-        // cell arrays: rows y0-H.., columns x0-H.. in float4 (x0-H is a multiple of 4)
+        const Lv<T> L = view<T>(A, t, i);
+        T* uo = at<T>(A.lv[t].u2, i);
+        // cell arrays: rows y0-H.., columns x0-H.. in 16-byte vectors (x0-H is a multiple of VW)
 #pragma unroll 4
         for (int q = threadIdx.x; q < SU * V; q += blockDim.x) {
             const int r = q / V, v = q - (q / V) * V;
-            const int gy = y0 - H + r, gx = x0 - H + 4 * v;
+            const int gy = y0 - H + r, gx = x0 - H + VW * v;
             const bool in = gy >= 0 && gy < n && gx >= 0 && gx < n;
             const size_t o = static_cast<size_t>(gy) * n + gx;
-            reinterpret_cast<float4*>(su)[q] = in ? *reinterpret_cast<const float4*>(L.u + o) : z4;
-            reinterpret_cast<float4*>(sid)[q] = in ? *reinterpret_cast<const float4*>(L.idiag + o) : z4;
-            reinterpret_cast<float4*>(sb)[q] =
-                in ? (ones ? make_float4(1.f, 1.f, 1.f, 1.f) : *reinterpret_cast<const float4*>(L.bc + o)) : z4;
+            reinterpret_cast<V16*>(su)[q] = in ? *reinterpret_cast<const V16*>(L.u + o) : z4;
+            reinterpret_cast<V16*>(sid)[q] = in ? *reinterpret_cast<const V16*>(L.idiag + o) : z4;
+            reinterpret_cast<V16*>(sb)[q] = in ? (ones ? o4 : *reinterpret_cast<const V16*>(L.bc + o)) : z4;
         }
         if constexpr (PROLONG) {
             // coarse-grid correction first: u += P e on every staged cell of the domain
             __syncthreads();
-            const float* e = at<float>(A.lv[t - 1].u, i);
+            const T* e = at<T>(A.lv[t - 1].u, i);
             const int nc = n >> 1;
             for (int q = threadIdx.x; q < SU * SU; q += blockDim.x) {
                 const int gy = y0 - H + q / SU, gx = x0 - H + q % SU;
-                if (gy >= 0 && gy < n && gx >= 0 && gx < n) su[q] += prolong_cell<float, float>(e, nc, gx, gy);
+                if (gy >= 0 && gy < n && gx >= 0 && gx < n) su[q] += prolong_cell<T, T>(e, nc, gx, gy);
             }
         }
         // y faces: face rows y0-H .. y0-H+SU, columns as above
 #pragma unroll 4
         for (int q = threadIdx.x; q < (SU + 1) * V; q += blockDim.x) {
             const int r = q / V, v = q - (q / V) * V;
-            const int gy = y0 - H + r, gx = x0 - H + 4 * v;
+            const int gy = y0 - H + r, gx = x0 - H + VW * v;
             const bool in = gy >= 0 && gy <= n && gx >= 0 && gx < n;
-            reinterpret_cast<float4*>(sky)[q] = in ? *reinterpret_cast<const float4*>(L.ky + static_cast<size_t>(gy) * n + gx) : z4;
+            reinterpret_cast<V16*>(sky)[q] =
+                in ? *reinterpret_cast<const V16*>(L.ky + static_cast<size_t>(gy) * n + gx) : z4;
         }
         // x faces: rows y0-H.., faces x0-H .. x0-H+SU (row pitch kx_pitch(n): scalar loads)
 #pragma unroll 4
         for (int q = threadIdx.x; q < SU * (SU + 1); q += blockDim.x) {
             const int r = q / (SU + 1), f = q - (q / (SU + 1)) * (SU + 1);
             const int gy = y0 - H + r, gx = x0 - H + f;
-            skx[q] = (gy >= 0 && gy < n && gx >= 0 && gx <= n) ? L.kx[static_cast<size_t>(gy) * kx_pitch(n) + gx] : 0.f;
+            skx[q] = (gy >= 0 && gy < n && gx >= 0 && gx <= n) ? L.kx[static_cast<size_t>(gy) * kx_pitch(n) + gx]
+                                                                : T(0);
         }
         __syncthreads();
 #pragma unroll
-        for (int ph = 0; ph < 2 * NS; ++ph) {
+        for (int ph = 0; ph < HN; ++ph) {
             const int colour = (first + ph) & 1;
             const int g = HN - 1 - ph;  // growth of the updated region beyond the tile
             const int side = TILE + 2 * g;
@@ -772,8 +790,8 @@ __global__ void __launch_bounds__(256) kb_rbgs_tile(FmgArgs A, int t, int B, int
                 if (gy < 0 || gy >= n || gx < 0 || gx >= n) continue;
                 const int sy = gy - y0 + H, sx = gx - x0 + H;
                 const int c0 = sy * SU + sx;
-                const float* kr = skx + sy * (SU + 1);
-                float acc = h2 * sb[c0];
+                const T* kr = skx + sy * (SU + 1);
+                T acc = h2 * sb[c0];
                 acc += kr[sx] * su[c0 - 1];
                 acc += kr[sx + 1] * su[c0 + 1];
                 acc += sky[sy * SU + sx] * su[c0 - SU];
@@ -782,12 +800,15 @@ __global__ void __launch_bounds__(256) kb_rbgs_tile(FmgArgs A, int t, int B, int
             }
             __syncthreads();
         }
-        constexpr int TV = TILE / 4;
+        constexpr int TV = TILE / VW;
         for (int q = threadIdx.x; q < TILE * TV; q += blockDim.x) {
             const int ry = q / TV, v = q - (q / TV) * TV;
-            const float* src = su + (ry + H) * SU + H + 4 * v;
-            *reinterpret_cast<float4*>(uo + static_cast<size_t>(y0 + ry) * n + x0 + 4 * v) =
-                make_float4(src[0], src[1], src[2], src[3]);
+            const T* src = su + (ry + H) * SU + H + VW * v;
+            V16 w;
+            T* wp = reinterpret_cast<T*>(&w);
+#pragma unroll
+            for (int j = 0; j < VW; ++j) wp[j] = src[j];
+            *reinterpret_cast<V16*>(uo + static_cast<size_t>(y0 + ry) * n + x0 + VW * v) = w;
         }
         __syncthreads();
     }
@@ -1722,12 +1743,14 @@ int kl_nt_for(const mlqmc_ctx* c, int t, int B)
     return c->kl_nt[t][B < kSmallBatch ? 0 : 1];
 }
 
-// Whether smoother kind k can run level t in the context's form (FP64: kb_gs
-// and the whole-sample smoother; the tiled and wavefront ones are FP32 only).
+// Whether smoother kind k can run level t in the context's form (FP64: kb_gs,
+// the whole-sample smoother and the plain tiles; the TMA-tiled and wavefront
+// ones are FP32 only).
 bool smoother_fits(const mlqmc_ctx* c, int k, int t)
 {
     const int n = c->p.coarse_cells << t;
-    if (!is_mixed(c->p) && k != MLQMC_SMOOTHER_GS && k != MLQMC_SMOOTHER_WHOLE) return false;
+    if (!is_mixed(c->p) && k != MLQMC_SMOOTHER_GS && k != MLQMC_SMOOTHER_WHOLE && k != MLQMC_SMOOTHER_TILE)
+        return false;
     switch (k) {
     case MLQMC_SMOOTHER_STREAM: return mlqmc_stream::supported(n);
     case MLQMC_SMOOTHER_TMA: return mlqmc_tma::supported(n);
@@ -1846,49 +1869,58 @@ void swap_u(mlqmc_ctx* c, FmgArgs& A, int t)
     std::swap(A.lv[t].u, A.lv[t].u2);
 }
 
-template <int TILE, int NS>
+template <typename T, int TILE, int NS>
 constexpr size_t tile_smem()
 {
-    constexpr int SU = TILE + 8;
-    return sizeof(float) * (3 * SU * SU + 2 * (SU + 1) * SU);
+    constexpr int SU = TILE + 2 * TileHalo<T, NS>::H;
+    return sizeof(T) * (3 * SU * SU + 2 * (SU + 1) * SU);
 }
 
-template <int TILE, int NS>
+template <typename T, int TILE, int NS>
 void launch_tile(mlqmc_ctx* c, const FmgArgs& A, int t, int B, int ones, int first, bool pro, cudaStream_t st)
 {
     const int64_t n = c->p.coarse_cells << t;
     const int64_t tiles = B * (n / TILE) * (n / TILE);
     const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(tiles, c->sm_count * 16)));
-    if (pro) kb_rbgs_tile<TILE, NS, true><<<grid, 256, tile_smem<TILE, NS>(), st>>>(A, t, B, ones, first);
-    else kb_rbgs_tile<TILE, NS, false><<<grid, 256, tile_smem<TILE, NS>(), st>>>(A, t, B, ones, first);
+    constexpr size_t smem = tile_smem<T, TILE, NS>();
+    if (pro) kb_rbgs_tile<T, TILE, NS, true><<<grid, 256, smem, st>>>(A, t, B, ones, first);
+    else kb_rbgs_tile<T, TILE, NS, false><<<grid, 256, smem, st>>>(A, t, B, ones, first);
 }
 
-template <int TILE, int NS>
+template <typename T, int TILE, int NS>
 bool tile_attr()
 {
-    const int b = static_cast<int>(tile_smem<TILE, NS>());
-    return cudaFuncSetAttribute(kb_rbgs_tile<TILE, NS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) ==
+    const int b = static_cast<int>(tile_smem<T, TILE, NS>());
+    return cudaFuncSetAttribute(kb_rbgs_tile<T, TILE, NS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) ==
                cudaSuccess &&
-           cudaFuncSetAttribute(kb_rbgs_tile<TILE, NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) ==
+           cudaFuncSetAttribute(kb_rbgs_tile<T, TILE, NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) ==
                cudaSuccess;
+}
+
+// FP32 tiles take two sweeps per launch (memory-bound, the halo work is
+// cheap); FP64 tiles one (FP64 arithmetic is the scarce resource on GB300:
+// a second sweep would add 21 % halo updates to save 24 of 48 bytes per cell).
+template <typename T>
+constexpr int tile_sweeps()
+{
+    return sizeof(T) == 8 ? 1 : 2;
 }
 
 template <int TILE>
 bool tile_attrs()
 {
-    return tile_attr<TILE, 2>() && tile_attr<TILE, 1>();
+    return tile_attr<float, TILE, 2>() && tile_attr<float, TILE, 1>() && tile_attr<double, TILE, 1>();
 }
 
 // nsweeps full red-black sweeps of level t (first: colour of the first half
-// sweep). FP32: two sweeps per tiled launch (memory-bound, the halo work is
-// cheap). FP64 and sides other than 8, 16 or a multiple of 32: two kb_gs
-// launches per sweep (FP64 is arithmetic-bound on GB300 and the tiles' halo
-// updates would add work).
+// sweep), on tiles of 8, 16 or 32 cells where the level's smoother is the
+// plain-tile one, else (FP64 form, sides that are not such a multiple) two
+// kb_gs launches per sweep.
 template <typename T>
 int tile_side(const mlqmc_ctx* c, int t, int B)
 {
     const int64_t n = c->p.coarse_cells << t;
-    if (sizeof(T) == 8 || smoother_for(c, t, B) != MLQMC_SMOOTHER_TILE) return 0;
+    if (smoother_for(c, t, B) != MLQMC_SMOOTHER_TILE) return 0;
     return n >= 32 && n % 32 == 0 ? 32 : (n == 16 ? 16 : (n == 8 ? 8 : 0));
 }
 
@@ -1907,7 +1939,7 @@ void smooth(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int first, int 
         pro = false;
     }
     while (nsweeps > 0) {
-        const int ns = nsweeps >= 2 ? 2 : 1;
+        const int ns = nsweeps >= 2 && (tile == 0 || tile_sweeps<T>() == 2) ? 2 : 1;
         // one colour (kb_gs): all of u and the faces, 1/D and b of that colour, its u written;
         // tiled: u, faces, 1/D and b once, u2 written once for ns sweeps (+ e of level t-1)
         const double b_in = ones ? 0.0 : 1.0;
@@ -1922,9 +1954,16 @@ void smooth(mlqmc_ctx* c, FmgArgs& A, int t, int B, int nsweeps, int first, int 
             nsweeps -= ns;
             continue;
         }
-        if (tile == 32) (ns == 2 ? launch_tile<32, 2> : launch_tile<32, 1>)(c, A, t, B, ones, first, pro, st);
-        else if (tile == 16) (ns == 2 ? launch_tile<16, 2> : launch_tile<16, 1>)(c, A, t, B, ones, first, pro, st);
-        else (ns == 2 ? launch_tile<8, 2> : launch_tile<8, 1>)(c, A, t, B, ones, first, pro, st);
+        if constexpr (tile_sweeps<T>() == 2) {
+            if (tile == 32) (ns == 2 ? launch_tile<T, 32, 2> : launch_tile<T, 32, 1>)(c, A, t, B, ones, first, pro, st);
+            else if (tile == 16)
+                (ns == 2 ? launch_tile<T, 16, 2> : launch_tile<T, 16, 1>)(c, A, t, B, ones, first, pro, st);
+            else (ns == 2 ? launch_tile<T, 8, 2> : launch_tile<T, 8, 1>)(c, A, t, B, ones, first, pro, st);
+        } else {
+            if (tile == 32) launch_tile<T, 32, 1>(c, A, t, B, ones, first, pro, st);
+            else if (tile == 16) launch_tile<T, 16, 1>(c, A, t, B, ones, first, pro, st);
+            else launch_tile<T, 8, 1>(c, A, t, B, ones, first, pro, st);
+        }
         swap_u(c, A, t);
         pro = false;
         nsweeps -= ns;
@@ -2317,7 +2356,9 @@ mlqmc_status fmg_stages(mlqmc_ctx* c, FmgArgs& A, const int* Bt, int Lmax, doubl
 }
 
 // Default smoother per level: the FP32 wavefront where it fits, else the TMA
-// tiles, else the plain tiles; FP64 form: kb_gs.
+// tiles, else the plain tiles; FP64 form: the whole-sample smoother up to
+// 64 x 64, kb_gs above (the FP64 plain tiles move less data but take longer:
+// FP64 issue, not HBM, bounds these sweeps on GB300).
 void default_smoothers(mlqmc_ctx* c)
 {
     for (int t = 0; t < c->p.n_levels; ++t) {

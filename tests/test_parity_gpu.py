@@ -465,7 +465,7 @@ def test_autotuner_report():
     for t, (k, _) in enumerate(c64.smoother_info()):
         assert k == "gs" or (k == "whole" and (cfg["n0"] << t) <= 64)
     with pytest.raises(M.MlqmcError):
-        c64.set_smoother(3, "stream")  # FP64 form: kb_gs or the whole-sample smoother
+        c64.set_smoother(3, "stream")  # FP64 form: kb_gs, the whole-sample smoother or the plain tiles
 
 
 def test_batch_schedule_report_and_results():
@@ -525,6 +525,36 @@ def test_fp64_whole_sample_smoother_matches_gs():
     mask = out["gs"] != 0
     assert _rel(out["whole"][mask], out["gs"][mask]) <= 1e-13
     ctx.check_device()
+
+
+def test_fp64_tile_smoother_matches_gs():
+    """FP64 form: the plain-tile smoother (one full red-black sweep per launch
+    on 32 x 32 tiles, the coarse-grid correction added to the staged tile)
+    performs kb_gs's operations in kb_gs's order, an outside neighbour being a
+    staged zero; with it on the 128 x 128 and 256 x 256 levels, per-sample F
+    and the reuse sums agree with two kb_gs launches per sweep (the default
+    there) to 1e-13, and stay within 1e-12 of the oracle."""
+    cfg, ctx, orc = _pair(W.LATTICE_6LEVEL, R=2)
+    assert [k for k, _ in ctx.smoother_info()][4:6] == ["gs", "gs"]
+    work = [(5, 0, 3, 0, 2), (4, 1, 4, 0, 2), (2, 0, 4, 1, 2)]
+    ns = sum((ne - nb) * (re_ - rb) for (_, nb, ne, rb, re_) in work)
+    out, sums = {}, {}
+    for name in ["tile", "gs"]:
+        for t in (4, 5):
+            ctx.set_smoother(t, name)
+        S = torch.zeros(cfg["n_levels"] * 2 * 2, dtype=torch.float64, device="cuda")
+        F = torch.zeros(ns * cfg["n_levels"], dtype=torch.float64, device="cuda")
+        ctx.sample_levels(work, S, F)
+        torch.cuda.synchronize()
+        ctx.check_device()
+        out[name] = F.cpu().numpy().reshape(ns, cfg["n_levels"])
+        sums[name] = S.cpu().numpy()
+    mask = out["gs"] != 0
+    assert _rel(out["tile"][mask], out["gs"][mask]) <= 1e-13
+    assert _rel(sums["tile"], sums["gs"]) <= 1e-13
+    for q, (lv, r, n) in [(0, (5, 0, 0)), (5, (5, 1, 2)), (6, (4, 0, 1))]:
+        ref = orc.sample(lv, r, n)
+        assert np.max(np.abs(out["tile"][q, :lv + 1] / ref["F"] - 1)) <= 1e-12, (lv, r, n)
 
 
 # --------------------------------------------------------------------------- #
