@@ -632,6 +632,10 @@ def make_line(args, world, value, tot_ms, ns, smoothers, create_s, launches, rep
                          "fp64_s": round(tte["fp64"]["seconds"], 3) if "fp64" in tte else None,
                          "mixed_round_graphs_s": (round(tte["mixed_tf32_round_graphs"]["seconds"], 3)
                                                   if "mixed_tf32_round_graphs" in tte else None),
+                         "mixed_batched_s": (round(tte["mixed_tf32_batched"]["seconds"], 3)
+                                             if "mixed_tf32_batched" in tte else None),
+                         "mixed_batched_rounds": (tte["mixed_tf32_batched"]["rounds"]
+                                                  if "mixed_tf32_batched" in tte else None),
                          "mixed_L": tte["mixed_tf32"]["L"], "mixed_rounds": tte["mixed_tf32"]["rounds"]}
                         if tte else None),
     }
@@ -647,13 +651,18 @@ def run_tte9(M, cfg, eps, dev):
     c["log2_nmax"] = 14
     genvec, _ = M.cbc_genvec(c["s"], c["log2_nmax"])
     # the default policy launches a fixed-cycle round kernel by kernel; the
-    # third run forces one graph launch per round for comparison
-    for name, prec, rounds in (("mixed_tf32", "mixed_tf32", "converged"), ("fp64", "fp64", "converged"),
-                               ("mixed_tf32_round_graphs", "mixed_tf32", "on")):
+    # third run forces one graph launch per round for comparison; the batched
+    # runs double every level whose V/C is within half of the largest in the
+    # same round (all those levels' samples in one call, one graph launch)
+    for name, prec, rounds, batched in (("mixed_tf32", "mixed_tf32", "converged", False),
+                                        ("fp64", "fp64", "converged", False),
+                                        ("mixed_tf32_round_graphs", "mixed_tf32", "on", False),
+                                        ("mixed_tf32_batched", "mixed_tf32", "converged", True),
+                                        ("mixed_tf32_batched_round_graphs", "mixed_tf32", "on", True)):
         c["precision"] = prec
         ctx = M.Context.from_config(c, genvec=genvec, max_samples=1 << 16)
         ctx.set_round_graphs(rounds)
-        r = ctx.estimate(eps)
+        r = ctx.estimate(eps, batched=batched)
         out[name] = {"seconds": r["wall_seconds"], "gpu_seconds": r["gpu_seconds"], "Q": r["Q"],
                      "rmse_bound": float(np.sqrt(r["varQ"] + r["bias"] ** 2)), "L": r["L"], "rounds": r["rounds"],
                      "N": r["N"][:r["L"] + 1], "run_status": r["run_status"], "graphs": ctx.graph_stats()}
