@@ -8,8 +8,9 @@
 // coefficient is k = exp(Z). Tiles of 128 cells x NT samples: TMA brings
 // 128-byte-swizzled K blocks of Psi (A operand, K-major) and C (B operand,
 // K-major) into shared memory through an mbarrier ring; one thread issues
-// tcgen05.mma kind::tf32 into an FP32 accumulator in TMEM; four epilogue warps
-// read their 32 TMEM lanes (one cell each) with tcgen05.ld, apply exp and
+// tcgen05.mma kind::tf32 into an FP32 accumulator in TMEM; eight epilogue
+// warps (two per 32-lane quarter of TMEM, half of the tile's samples each)
+// read their TMEM lanes (one cell each) with tcgen05.ld, apply exp and
 // store k sample by sample, coalesced across cells. The CTAs are persistent
 // and warp-specialised with two TMEM accumulators, so that the epilogue of
 // one tile runs while the tensor cores work on the next.
@@ -37,7 +38,12 @@ namespace {
 
 constexpr int kTileM = 128;      // cells per CTA (TMEM lanes)
 constexpr int kKBlock = 32;      // K elements per stage (128 bytes of FP32)
-constexpr int kStages = 4;
+// shared-memory ring stages: 192 KB of A (128 cells) and B (NT samples) K blocks
+template <int NT>
+constexpr int stages_for()
+{
+    return NT == 128 ? 6 : 4;
+}
 constexpr uint32_t kErrTimeout = 4;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -191,23 +197,26 @@ __device__ __forceinline__ void mbar_arrive1(uint64_t* bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-constexpr int kEpiWarps = 4;                       // one per TMEM lane quarter
+constexpr int kEpiWarps = 8;                       // two per TMEM lane quarter, half the columns each
 constexpr int kTcThreads = 64 + 32 * kEpiWarps;    // TMA warp, MMA warp, epilogue warps
 
 // Persistent CTAs (one per SM) walk the 128-cell x NT-sample tiles of the
 // level, sample tiles fastest (consecutive tiles share their Psi rows in L2).
 // Warp 0 (one thread) streams the K blocks of Psi and C of every tile through
 // the shared-memory ring; warp 1 (one thread) issues the MMAs of a tile into
-// one of two TMEM accumulators (2 x NT columns) and commits; warps 2-5 read
-// the other accumulator (warp w owns TMEM lanes 32 (w % 4) ..), apply exp and
-// store, so the epilogue of tile i overlaps the MMAs of tile i + 1 and the
-// ring never drains between tiles.
+// one of two TMEM accumulators (2 x NT columns) and commits; warps 2-9 read
+// the other accumulator (warp w owns TMEM lanes 32 (w % 4) .. and half of the
+// columns), apply exp and store, so the epilogue of tile i overlaps the MMAs
+// of tile i + 1 and the ring never drains between tiles. The ring holds 192 KB
+// of K blocks: four stages of 128 + 256 rows, six of 128 + 128 (one and a half
+// tiles at s = 100).
 template <int NT, bool BF>
 __global__ void __launch_bounds__(kTcThreads, 1) kl_tc_kernel(const __grid_constant__ CUtensorMap tm_psi,
                                                               const __grid_constant__ CUtensorMap tm_c, int M, int B,
                                                               int nk, float* __restrict__ kout, size_t kstride,
                                                               int* err)
 {
+    constexpr int kStages = stages_for<NT>();
     extern __shared__ unsigned char smem_raw[];
     // 1024-byte aligned stage buffers (the 128-byte swizzle atom)
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -306,8 +315,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) kl_tc_kernel(const __grid_const
             mbar_wait(drained, 0, err);
         }
     } else {
-        // epilogue: warp w reads TMEM lanes 32 q .. 32 q + 31, q = w % 4 (cells m0 + 32 q + lane)
+        // epilogue: warp w reads TMEM lanes 32 q .. 32 q + 31, q = w % 4 (cells m0 + 32 q + lane),
+        // accumulator columns [h NT / 2, (h + 1) NT / 2), h = (w - 2) / 4
         const int q = warp & 3;
+        const int c_lo = ((warp - 2) >> 2) * (NT / 2);
         int lt = 0;
         for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++lt) {
             const int a = lt & 1;
@@ -318,7 +329,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) kl_tc_kernel(const __grid_const
             const int m0 = (tile / ntiles) * kTileM, b0 = (tile % ntiles) * NT;
             const int p = m0 + q * 32 + lane;
 #pragma unroll 1
-            for (int c = 0; c < NT; c += 32) {
+            for (int c = c_lo; c < c_lo + NT / 2; c += 32) {
                 float v[32];
                 tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(a * NT + c), v);
                 if (p < M) {
@@ -485,8 +496,8 @@ constexpr int kNT = 256;
 
 size_t tc_smem_bytes(int nt = kNT)
 {
-    return 1024 + kStages * (kTileM * kKBlock * 4 + static_cast<size_t>(nt) * kKBlock * 4) + (2 * kStages + 5) * 8 +
-           16;
+    const int st = nt == 128 ? stages_for<128>() : stages_for<kNT>();
+    return 1024 + st * (kTileM * kKBlock * 4 + static_cast<size_t>(nt) * kKBlock * 4) + (2 * st + 5) * 8 + 16;
 }
 
 int sm_count()
