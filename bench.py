@@ -636,6 +636,8 @@ def make_line(args, world, value, tot_ms, ns, smoothers, create_s, launches, rep
                                              if "mixed_tf32_batched" in tte else None),
                          "mixed_batched_rounds": (tte["mixed_tf32_batched"]["rounds"]
                                                   if "mixed_tf32_batched" in tte else None),
+                         "fp64_batched_s": (round(tte["fp64_batched"]["seconds"], 3)
+                                            if "fp64_batched" in tte else None),
                          "mixed_L": tte["mixed_tf32"]["L"], "mixed_rounds": tte["mixed_tf32"]["rounds"]}
                         if tte else None),
     }
@@ -658,7 +660,8 @@ def run_tte9(M, cfg, eps, dev):
                                         ("fp64", "fp64", "converged", False),
                                         ("mixed_tf32_round_graphs", "mixed_tf32", "on", False),
                                         ("mixed_tf32_batched", "mixed_tf32", "converged", True),
-                                        ("mixed_tf32_batched_round_graphs", "mixed_tf32", "on", True)):
+                                        ("mixed_tf32_batched_round_graphs", "mixed_tf32", "on", True),
+                                        ("fp64_batched", "fp64", "converged", True)):
         c["precision"] = prec
         ctx = M.Context.from_config(c, genvec=genvec, max_samples=1 << 16)
         ctx.set_round_graphs(rounds)
