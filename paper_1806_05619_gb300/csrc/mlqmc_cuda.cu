@@ -401,6 +401,137 @@ __global__ void __launch_bounds__(64) kb_level0_fixed(FmgArgs A, int B)
     }
 }
 
+// Level 0 for n0 = NC for calls of few samples: the same factorisation,
+// substitutions and F_0 as kb_level0_fixed, every operation in its order, but
+// each step of the factorisation split over the NC + 2 warps of a CTA that
+// holds 32 samples (lane = sample). On GB300 an FP64 warp instruction holds
+// its SM sub-partition for about 70 cycles whatever its active lanes, so one
+// thread's ~4,700 FP64 operations take about 0.15 ms however few samples a
+// call has; split this way a step costs its diagonal's chain only. Step j:
+// warp 0 forms d_j and 1/L(j,j), warp l (1..NC) the dot product of row j+l,
+// warp NC+1 the forward value; after a barrier warp l scales its entry of
+// column j, warp NC+1 finishes y_j and warp 0 writes the finished row j to
+// the global factor; a second barrier ends the step. Warp NC+1 then runs the
+// backward substitution (the factor rows from global memory, written by warp
+// 0 before the barriers) and forms F_0. The ring of NC+1 rows and the
+// forward values of the group's samples sit in shared memory. Lanes past B
+// compute on sample B-1 and store nothing.
+template <typename T, bool MX, int NC>
+__global__ void __launch_bounds__(32 * (NC + 2)) kb_level0_split(FmgArgs A, int B)
+{
+    constexpr int N = NC * NC, W = NC + 1;
+    __shared__ double ring[W * W * 32];  // [(slot * W + e) * 32 + lane]
+    __shared__ double ys[N * 32];        // forward values, then the solution
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t cs = A.chol.stride;
+    double* fac = reinterpret_cast<double*>(A.chol.base);
+    float* f32 = reinterpret_cast<float*>(A.chol32);
+    const double h2 = 1.0 / (static_cast<double>(NC) * NC);
+    auto Rs = [&](int slot, int e) -> double& { return ring[(slot * W + e) * 32 + lane]; };
+    for (int base = blockIdx.x * 32; base < B; base += gridDim.x * 32) {
+        const int i = base + lane;
+        const bool live = i < B;
+        const int si = live ? i : B - 1;
+        const Lv<T> L0 = view<T>(A, 0, si);
+        double win[NC];  // forward substitution: win[q - 1] = y_(j - q)
+#pragma unroll
+        for (int q = 0; q < NC; ++q) win[q] = 0.0;
+        auto step = [&](int j, auto full) {
+            constexpr bool FULL = decltype(full)::value;
+            const int s0 = j % W;
+            double a = 0.0, v = 0.0;
+            int sr = 0;
+            const int l = warp;  // row j + l for warps 1..NC
+            if (warp == 0) {
+                const int j1 = j % NC, j2 = j / NC;
+                double d = widen(L0.kx[j2 * kx_pitch(NC) + j1]) + widen(L0.kx[j2 * kx_pitch(NC) + j1 + 1]) +
+                           widen(L0.ky[j2 * NC + j1]) + widen(L0.ky[(j2 + 1) * NC + j1]);
+#pragma unroll
+                for (int q = 1; q <= NC; ++q) {
+                    if (!FULL && q > j) break;
+                    const double lq = Rs(s0, q);
+                    d -= lq * lq;
+                }
+                Rs(s0, 0) = rsqrt64(d);
+            } else if (warp <= NC) {
+                const int r = j + l;
+                if (r < N) {
+                    sr = s0 + l >= W ? s0 + l - W : s0 + l;
+                    a = widen(band_a(L0.kx, L0.ky, NC, r, l));
+                    if constexpr (FULL) {
+                        for (int u = 0; u < NC - l; ++u) a -= Rs(sr, NC - u) * Rs(s0, NC - l - u);
+                    } else {
+                        for (int tt = (r - NC > 0 ? r - NC : 0); tt < j; ++tt) a -= Rs(sr, r - tt) * Rs(s0, j - tt);
+                    }
+                }
+            } else {
+                v = h2;  // forward substitution, f = 1
+#pragma unroll
+                for (int q = 1; q <= NC; ++q) {
+                    if (!FULL && q > j) break;
+                    v -= Rs(s0, q) * win[q - 1];
+                }
+            }
+            __syncthreads();
+            const double rl = Rs(s0, 0);
+            if (warp == 0) {
+                if (live) {
+#pragma unroll
+                    for (int e = 0; e <= NC; ++e) {
+                        if (!FULL && e > j) break;
+                        fac[static_cast<size_t>(j * W + e) * cs + i] = Rs(s0, e);
+                        if constexpr (MX) f32[static_cast<size_t>(j * W + e) * cs + i] = narrow(Rs(s0, e));
+                    }
+                }
+            } else if (warp <= NC) {
+                if (j + l < N) Rs(sr, l) = a * rl;
+            } else {
+                const double yj = v * rl;
+                ys[j * 32 + lane] = yj;
+#pragma unroll
+                for (int q = NC - 1; q > 0; --q) win[q] = win[q - 1];
+                win[0] = yj;
+            }
+            __syncthreads();
+        };
+        for (int j = 0; j < NC; ++j) step(j, std::false_type());
+        for (int j = NC; j < N; ++j) step(j, std::true_type());
+        if (warp == NC + 1) {
+            // backward: x_r = (y_r - sum_q L(r+q, r) x_(r+q)) / L(r, r), win[q - 1] = x_(r+q)
+            double* x = (MX || A.refine) ? L0.u64 : reinterpret_cast<double*>(L0.u);
+#pragma unroll
+            for (int q = 0; q < NC; ++q) win[q] = 0.0;
+            for (int r = N - 1; r >= 0; --r) {
+                double v = ys[r * 32 + lane];
+#pragma unroll
+                for (int q = 1; q <= NC; ++q)
+                    if (r + q < N) v -= fac[static_cast<size_t>((r + q) * W + q) * cs + si] * win[q - 1];
+                const double xr = v * fac[static_cast<size_t>(r * W) * cs + si];
+                ys[r * 32 + lane] = xr;
+                if (live) {
+                    x[r] = xr;
+                    if constexpr (MX) reinterpret_cast<float*>(L0.u)[r] = narrow(xr);  // FP32 copy for the first FMG interpolation
+                }
+#pragma unroll
+                for (int q = NC - 1; q > 0; --q) win[q] = win[q - 1];
+                win[0] = xr;
+            }
+            double F0;
+            if (A.qoi == MLQMC_QOI_MEAN) {
+                double acc = 0.0;
+                for (int r = 0; r < N; ++r) acc += ys[r * 32 + lane];
+                F0 = acc / static_cast<double>(N);
+            } else {
+                constexpr int m = NC / 2;
+                F0 = 0.25 * (ys[((m - 1) * NC + (m - 1)) * 32 + lane] + ys[((m - 1) * NC + m) * 32 + lane] +
+                             ys[(m * NC + (m - 1)) * 32 + lane] + ys[(m * NC + m) * 32 + lane]);
+            }
+            if (live) A.F[static_cast<size_t>(i) * A.n_levels] = F0;
+        }
+        __syncthreads();
+    }
+}
+
 template <int NC>
 constexpr size_t level0_smem()
 {
@@ -1664,7 +1795,10 @@ mlqmc_status last_error()
     return ok(cudaGetLastError()) ? MLQMC_OK : MLQMC_ERR_CUDA;
 }
 
-// Level-0 factor, exact solve and F_0 of samples 0..B-1 (one thread each).
+// Calls with fewer level-0 samples than this take kb_level0_split.
+constexpr int kLevel0SplitBelow = 16384;
+
+// Level-0 factor, exact solve and F_0 of samples 0..B-1.
 mlqmc_status launch_level0(mlqmc_ctx* c, const FmgArgs& A, int B, cudaStream_t st)
 {
     LevelTag lt(c, 0);
@@ -1690,7 +1824,19 @@ mlqmc_status launch_level0(mlqmc_ctx* c, const FmgArgs& A, int B, cudaStream_t s
         per_sm = std::max(1, per_sm);
     }
     const int g64 = std::max(1, std::min((B + 63) / 64, c->sm_count * per_sm));
-    if (c->p.coarse_cells == 8) {
+    // few samples: one thread per sample would leave most SM sub-partitions
+    // idle, each warp's FP64 chain alone setting the time; split every step
+    // of a group of 32 samples over the warps of a CTA instead (same results)
+    const int g32 = (B + 31) / 32;
+    if (B < kLevel0SplitBelow && (c->p.coarse_cells == 8 || c->p.coarse_cells == 4)) {
+        if (c->p.coarse_cells == 8) {
+            if (is_mixed(c->p)) kb_level0_split<float, true, 8><<<g32, 32 * 10, 0, st>>>(A, B);
+            else kb_level0_split<double, false, 8><<<g32, 32 * 10, 0, st>>>(A, B);
+        } else {
+            if (is_mixed(c->p)) kb_level0_split<float, true, 4><<<g32, 32 * 6, 0, st>>>(A, B);
+            else kb_level0_split<double, false, 4><<<g32, 32 * 6, 0, st>>>(A, B);
+        }
+    } else if (c->p.coarse_cells == 8) {
         if (is_mixed(c->p)) kb_level0_fixed<float, true, 8><<<g64, 64, level0_smem<8>(), st>>>(A, B);
         else kb_level0_fixed<double, false, 8><<<g64, 64, level0_smem<8>(), st>>>(A, B);
     } else if (c->p.coarse_cells == 4) {

@@ -527,6 +527,37 @@ def test_fp64_whole_sample_smoother_matches_gs():
     ctx.check_device()
 
 
+@pytest.mark.parametrize("pid,precision", [(2, "fp64"), (6, "fp64"), (2, "mixed_tf32"), (6, "mixed_tf32")])
+def test_level0_split_kernel_matches_thread_per_sample(pid, precision):
+    """The level-0 exact solve of calls with fewer than 16,384 samples splits
+    every factorisation step over the warps of a CTA (kb_level0_split); larger
+    calls take one thread per sample (kb_level0_fixed). Both perform the same
+    operations in the same order: F_0 of the same samples is bit-identical in
+    the FP64 form (n0 = 8 and n0 = 4) and, in the mixed form, agrees to 1e-13
+    (the tensor-core fields of the two calls may use other tile widths), and
+    the small call stays within 1e-12 of the oracle (FP64 form)."""
+    cfg, ctx, orc = _pair(W.PROBLEMS[pid], precision=precision)
+    R, npts = cfg["R"], 16384 // cfg["R"]
+    nl = cfg["n_levels"]
+    out = {}
+    for name, work in (("big", [(0, 0, npts, 0, R)]), ("small", [(0, 0, 64, 0, 2)])):
+        ns = sum((ne - nb) * (re_ - rb) for (_, nb, ne, rb, re_) in work)
+        S = torch.zeros(nl * R * 2, dtype=torch.float64, device="cuda")
+        F = torch.zeros(ns * nl, dtype=torch.float64, device="cuda")
+        ctx.sample_levels(work, S, F)
+        torch.cuda.synchronize()
+        ctx.check_device()
+        out[name] = F.cpu().numpy().reshape(ns, nl)[:, 0]
+    big = np.concatenate([out["big"][r * npts: r * npts + 64] for r in range(2)])
+    if precision == "fp64":
+        assert np.array_equal(out["small"], big)
+        for q, (r, n) in [(0, (0, 0)), (70, (1, 6)), (127, (1, 63))]:
+            ref = orc.sample(0, r, n)
+            assert abs(out["small"][q] / ref["F"][0] - 1) <= 1e-12, (r, n)
+    else:
+        assert _rel(out["small"], big) <= 1e-13
+
+
 def test_fp64_tile_smoother_matches_gs():
     """FP64 form: the plain-tile smoother (one full red-black sweep per launch
     on 32 x 32 tiles, the coarse-grid correction added to the staged tile)
