@@ -62,6 +62,7 @@ def parse(argv=None):
     ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 form of the step")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 form (one warm-up)")
     ap.add_argument("--no-tte", action="store_true", help="skip Algorithm 1's time to eps on the 9-level problem")
+    ap.add_argument("--no-per-level", action="store_true", help="skip the samples/s per finest level")
     ap.add_argument("--tte-eps", type=float, default=1e-4)
     ap.add_argument("--extras", action="store_true",
                     help="side studies: 6-level step, 1024x1024 precision form, 7-level Algorithm 1 runs, Matern")
@@ -417,6 +418,32 @@ def timed_steps(step, K, stream, flush):
     return [a.elapsed_time(b) for a, b in ev]
 
 
+def per_level_rates(step, stream, flush, K, warm=2):
+    """Samples/s per finest level: for each level l, a call with only the
+    step's level-l samples (N_l points x R shifts; FMG on levels 0..l of each),
+    `warm` untimed calls (the repeat is replayed as a graph, as in the step),
+    then K calls device-timed with the L2 flushed before each."""
+    cfg = step.cfg
+    out = []
+    for lv, n in enumerate(cfg["counts"]):
+        if n <= 0:
+            continue
+        work = [(lv, 0, n, 0, cfg["R"])]
+
+        def call():
+            step.sums.zero_()
+            step.ctx.sample_levels(work, step.sums, stream=stream)
+
+        for _ in range(warm):
+            call()
+        ms = float(np.mean(timed_steps(call, K, stream, flush)))
+        ns = n * cfg["R"]
+        out.append({"level": lv, "n": step.ctx.n(lv), "samples": ns, "ms": round(ms, 4),
+                    "samples_per_s": round(ns / (ms * 1e-3), 1)})
+    step.ctx.check_device(stream)
+    return out
+
+
 def force_smoother(ctx, name, plan=""):
     if ctx.precision == "fp64":
         return
@@ -557,6 +584,8 @@ def run_ours(args):
     details["estimate_mixed"] = {"Q": est["Q"], "varQ": est["varQ"]}
     smoothers = [k for k, _ in step.ctx.smoother_info()]
     details["autotuner"] = {"smoothers": step.ctx.smoother_info(), "schedule": step.ctx.schedule_info()}
+    if not args.no_per_level:
+        details["per_finest_level"] = {"mixed_tf32": per_level_rates(step, stream, flush, args.steps)}
     create_mixed = step.create_s
     step.close()
     del step
@@ -582,6 +611,8 @@ def run_ours(args):
         prof64, _ = s64.profiled(stream, flush, 1, warm=0, restore=False)
         _, details["roofline_table_fp64"] = roofline_report(s64.ctx, prof64, P, "fp64", 1)
         fp64["speedup_mixed"] = round((t64 / args.fp64_steps) / (tot_ms / args.steps), 2)
+        if not args.no_per_level:
+            details.setdefault("per_finest_level", {})["fp64"] = per_level_rates(s64, stream, flush, 1, warm=1)
         s64.close()
         del s64
         torch.cuda.empty_cache()
