@@ -408,8 +408,9 @@ __global__ void __launch_bounds__(64) kb_level0_fixed(FmgArgs A, int B)
 // its SM sub-partition for about 70 cycles whatever its active lanes, so one
 // thread's ~4,700 FP64 operations take about 0.15 ms however few samples a
 // call has; split this way a step costs its diagonal's chain only. Step j:
-// warp 0 forms d_j and 1/L(j,j), warp l (1..NC) the dot product of row j+l,
-// warp NC+1 the forward value; after a barrier warp l scales its entry of
+// warp 0 forms d_j and 1/L(j,j) (the face sum of d_j formed one step ahead by
+// warp NC, whose band row is the shortest), warp l (1..NC) the dot product of
+// row j+l, warp NC+1 the forward value; after a barrier warp l scales its entry of
 // column j, warp NC+1 finishes y_j and warp 0 writes the finished row j to
 // the global factor; a second barrier ends the step. Warp NC+1 then runs the
 // backward substitution (the factor rows from global memory, written by warp
@@ -422,6 +423,7 @@ __global__ void __launch_bounds__(32 * (NC + 2)) kb_level0_split(FmgArgs A, int 
     constexpr int N = NC * NC, W = NC + 1;
     __shared__ double ring[W * W * 32];  // [(slot * W + e) * 32 + lane]
     __shared__ double ys[N * 32];        // forward values, then the solution
+    __shared__ double dg[2 * 32];        // the diagonal sum of the next step, formed one step ahead
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const size_t cs = A.chol.stride;
     double* fac = reinterpret_cast<double*>(A.chol.base);
@@ -442,10 +444,14 @@ __global__ void __launch_bounds__(32 * (NC + 2)) kb_level0_split(FmgArgs A, int 
             double a = 0.0, v = 0.0;
             int sr = 0;
             const int l = warp;  // row j + l for warps 1..NC
+            // the face sum of row jj's diagonal, in kb_level0_fixed's order
+            auto diag_sum = [&](int jj) {
+                const int j1 = jj % NC, j2 = jj / NC;
+                return widen(L0.kx[j2 * kx_pitch(NC) + j1]) + widen(L0.kx[j2 * kx_pitch(NC) + j1 + 1]) +
+                       widen(L0.ky[j2 * NC + j1]) + widen(L0.ky[(j2 + 1) * NC + j1]);
+            };
             if (warp == 0) {
-                const int j1 = j % NC, j2 = j / NC;
-                double d = widen(L0.kx[j2 * kx_pitch(NC) + j1]) + widen(L0.kx[j2 * kx_pitch(NC) + j1 + 1]) +
-                           widen(L0.ky[j2 * NC + j1]) + widen(L0.ky[(j2 + 1) * NC + j1]);
+                double d = j == 0 ? diag_sum(0) : dg[(j & 1) * 32 + lane];  // step j > 0: formed by warp NC
 #pragma unroll
                 for (int q = 1; q <= NC; ++q) {
                     if (!FULL && q > j) break;
@@ -454,6 +460,7 @@ __global__ void __launch_bounds__(32 * (NC + 2)) kb_level0_split(FmgArgs A, int 
                 }
                 Rs(s0, 0) = rsqrt64(d);
             } else if (warp <= NC) {
+                if (warp == NC && j + 1 < N) dg[((j + 1) & 1) * 32 + lane] = diag_sum(j + 1);  // the lightest row's warp
                 const int r = j + l;
                 if (r < N) {
                     sr = s0 + l >= W ? s0 + l - W : s0 + l;
@@ -1599,9 +1606,14 @@ mlqmc_status ensure_pool(mlqmc_ctx* c, int t, int64_t need)
 {
     LevelPool& P = c->pools[t];
     if (need <= P.cap) return MLQMC_OK;
-    const int64_t cap = std::max<int64_t>(need, P.cap + P.cap / 2);
     size_t st[kPoolArrs];
     level_strides(c->p, c->Ka, t, st);
+    // Algorithm 1 doubles a level's count round by round, and each growth
+    // waits for the device and reallocates: small pools grow fourfold, so
+    // that two doublings fit, large ones by half
+    const size_t per = level_bytes_per_sample(c->p, c->Ka, t);
+    const bool small = per * static_cast<size_t>(4 * std::max<int64_t>(P.cap, need)) <= (size_t(256) << 20);
+    const int64_t cap = std::max<int64_t>(need, small ? 4 * P.cap : P.cap + P.cap / 2);
     size_t off = 0, offs[kPoolArrs];
     for (int a = 0; a < kPoolArrs; ++a) {
         offs[a] = off;
@@ -2822,6 +2834,7 @@ void free_ctx(mlqmc_ctx* c)
     for (auto e : c->pool) cudaEventDestroy(e);
     if (c->h_samples) cudaFreeHost(c->h_samples);
     if (c->h_count) cudaFreeHost(c->h_count);
+    if (c->h_status) cudaFreeHost(c->h_status);
     delete c;
 }
 
@@ -3031,7 +3044,8 @@ extern "C" mlqmc_status mlqmc_create(const mlqmc_problem* p, int64_t max_samples
            ok(cudaMalloc(&c->d_norms, ms * sizeof(double))) &&
            ok(cudaMalloc(&c->d_active, ms * sizeof(int))) && ok(cudaMalloc(&c->d_count, sizeof(int))) &&
            ok(cudaMallocHost(&c->h_samples, ms * sizeof(SampleDesc))) &&
-           ok(cudaMallocHost(&c->h_count, sizeof(int))) && ok(cudaMalloc(&c->d_status, sizeof(int))) &&
+           ok(cudaMallocHost(&c->h_count, sizeof(int))) && ok(cudaMallocHost(&c->h_status, sizeof(int))) &&
+           ok(cudaMalloc(&c->d_status, sizeof(int))) &&
            ok(cudaMalloc(&c->d_queue, sizeof(int))) && ok(cudaMemset(c->d_status, 0, sizeof(int))) &&
            ok(cudaMalloc(&c->d_iters, 2 * MLQMC_MAX_LEVELS * sizeof(int))) &&
            ok(cudaMemset(c->d_iters, 0, 2 * MLQMC_MAX_LEVELS * sizeof(int))) &&
@@ -3445,6 +3459,15 @@ extern "C" mlqmc_status mlqmc_sample_levels(mlqmc_ctx* c, const mlqmc_work* work
     return MLQMC_OK;
 }
 
+// Deferred status bits -> the status a call reports (the most severe first).
+static mlqmc_status status_of_bits(int h)
+{
+    if (h & kStatusTimeout) return MLQMC_ERR_TIMEOUT;
+    if (h & kStatusNotConverged) return MLQMC_ERR_NOT_CONVERGED;
+    if (h & kStatusCheck) return MLQMC_ERR_DEVICE_STATUS;
+    return MLQMC_OK;
+}
+
 extern "C" mlqmc_status mlqmc_get_device_status(mlqmc_ctx* c, void* stream)
 {
     if (!c) return MLQMC_ERR_INVALID_ARG;
@@ -3456,11 +3479,22 @@ extern "C" mlqmc_status mlqmc_get_device_status(mlqmc_ctx* c, void* stream)
         return MLQMC_ERR_CUDA;
     h |= c->host_status;
     c->host_status = 0;
-    if (h & kStatusTimeout) return MLQMC_ERR_TIMEOUT;
-    if (h & kStatusNotConverged) return MLQMC_ERR_NOT_CONVERGED;
-    if (h & kStatusCheck) return MLQMC_ERR_DEVICE_STATUS;
-    return MLQMC_OK;
+    return status_of_bits(h);
 }
+
+namespace mlqmc {
+mlqmc_status fetch_round(mlqmc_ctx* c, const double* d_sums, double* h_sums, size_t n, cudaStream_t st)
+{
+    if (!c || (n > 0 && (!d_sums || !h_sums))) return MLQMC_ERR_INVALID_ARG;
+    if ((n > 0 && !ok(cudaMemcpyAsync(h_sums, d_sums, n * sizeof(double), cudaMemcpyDeviceToHost, st))) ||
+        !ok(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
+        !ok(cudaMemsetAsync(c->d_status, 0, sizeof(int), st)) || !ok(cudaStreamSynchronize(st)))
+        return MLQMC_ERR_CUDA;
+    const int h = *c->h_status | c->host_status;
+    c->host_status = 0;
+    return status_of_bits(h);
+}
+}  // namespace mlqmc
 
 extern "C" mlqmc_status mlqmc_modes(const mlqmc_ctx* c, int32_t* a, int32_t* b, double* theta)
 {

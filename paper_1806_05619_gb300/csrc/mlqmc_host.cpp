@@ -290,13 +290,7 @@ mlqmc_status run_estimate(mlqmc_ctx* c, double eps, const mlqmc_run_opts* o, mlq
             st = mlqmc_sample_levels(c, work.data(), static_cast<int32_t>(work.size()), d_sums, nullptr, stream);
             cudaEventRecord(e1, stream);
             if (st != MLQMC_OK) goto done;
-            if (cudaMemcpyAsync(sums.data(), d_sums, sums.size() * sizeof(double), cudaMemcpyDeviceToHost,
-                                stream) != cudaSuccess ||
-                cudaStreamSynchronize(stream) != cudaSuccess) {
-                st = MLQMC_ERR_CUDA;
-                goto done;
-            }
-            st = mlqmc_get_device_status(c, stream);
+            st = fetch_round(c, d_sums, sums.data(), sums.size(), stream);  // sums and device status, one sync
             if (st != MLQMC_OK) goto done;
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, e0, e1);
@@ -420,13 +414,7 @@ mlqmc_status run_estimate_mlmc(mlqmc_ctx* c, double eps, const mlqmc_run_opts* o
             st = mlqmc_sample_levels(c, work.data(), static_cast<int32_t>(work.size()), d_sums, nullptr, stream);
             cudaEventRecord(e1, stream);
             if (st != MLQMC_OK) break;
-            if (cudaMemcpyAsync(sums.data(), d_sums, sums.size() * sizeof(double), cudaMemcpyDeviceToHost,
-                                stream) != cudaSuccess ||
-                cudaStreamSynchronize(stream) != cudaSuccess) {
-                st = MLQMC_ERR_CUDA;
-                break;
-            }
-            st = mlqmc_get_device_status(c, stream);
+            st = fetch_round(c, d_sums, sums.data(), sums.size(), stream);  // sums and device status, one sync
             if (st != MLQMC_OK) break;
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, e0, e1);

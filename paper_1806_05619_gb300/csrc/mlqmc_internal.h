@@ -38,6 +38,11 @@ void psi_table(const Eig1D& e, double corr_len, int K1, int n, std::vector<doubl
 mlqmc_status run_estimate(mlqmc_ctx* c, double eps, const mlqmc_run_opts* o, mlqmc_result* out);
 mlqmc_status run_estimate_mlmc(mlqmc_ctx* c, double eps, const mlqmc_run_opts* o, mlqmc_result* out);
 
+// A round's reuse sums (n doubles, device -> host) and the deferred device
+// status in one synchronisation of `st`; the status word is cleared on `st`
+// after it is read. Returns what mlqmc_get_device_status would.
+mlqmc_status fetch_round(mlqmc_ctx* c, const double* d_sums, double* h_sums, size_t n, cudaStream_t st);
+
 }  // namespace mlqmc
 
 // ---- device-side sample descriptor ---------------------------------------
@@ -150,6 +155,7 @@ struct mlqmc_ctx {
     int* d_count = nullptr;
     SampleDesc* h_samples = nullptr;  // pinned staging
     int* h_count = nullptr;           // pinned
+    int* h_status = nullptr;          // pinned: the status word read with a round's sums
     cudaEvent_t staged = nullptr;     // recorded after the last copy out of the staging buffer
     // level 0 (its field, faces and banded factorisation) runs on a second
     // stream beside the other levels' fields: fork and join by events; with
