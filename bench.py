@@ -63,6 +63,9 @@ def parse(argv=None):
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 form (one warm-up)")
     ap.add_argument("--no-tte", action="store_true", help="skip Algorithm 1's time to eps on the 9-level problem")
     ap.add_argument("--no-per-level", action="store_true", help="skip the samples/s per finest level")
+    ap.add_argument("--tte-profile", action="store_true",
+                    help="only Algorithm 1 (mixed, one level per round) to --tte-eps on the 9-level problem, "
+                         "inside a profiler range, for a launch list")
     ap.add_argument("--tte-eps", type=float, default=1e-4)
     ap.add_argument("--extras", action="store_true",
                     help="side studies: 6-level step, 1024x1024 precision form, 7-level Algorithm 1 runs, Matern")
@@ -953,8 +956,34 @@ def run_kl_shape(args):
     ctx.close()
 
 
+def run_tte_profile(args):
+    """Algorithm 1 on the 9-level problem in the mixed form, one level per
+    round, with a profiler range around the estimate only (context creation
+    and the autotuner stay outside): one summary line."""
+    import torch
+
+    import paper_1806_05619_gb300 as M
+
+    c = dict(workload_config("mlqmc9", precision="mixed_tf32"))
+    c["log2_nmax"] = 14
+    genvec, _ = M.cbc_genvec(c["s"], c["log2_nmax"])
+    ctx = M.Context.from_config(c, genvec=genvec, max_samples=1 << 16)
+    ctx.set_round_graphs("converged")
+    torch.cuda.synchronize()
+    n0 = ctx.launch_count()
+    torch.cuda.profiler.start()
+    r = ctx.estimate(args.tte_eps)
+    torch.cuda.profiler.stop()
+    print(json.dumps({"tte_profile": {"eps": args.tte_eps, "seconds": r["wall_seconds"], "rounds": r["rounds"],
+                                      "L": r["L"], "N": r["N"][:r["L"] + 1], "launches": ctx.launch_count() - n0}}))
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.tte_profile:
+        run_tte_profile(args)
+        return
     if args.kl_shape:
         run_kl_shape(args)
         return
