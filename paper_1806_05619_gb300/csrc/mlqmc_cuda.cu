@@ -406,8 +406,10 @@ __global__ void __launch_bounds__(64) kb_level0_fixed(FmgArgs A, int B)
 // each step of the factorisation split over the NC + 2 warps of a CTA that
 // holds 32 samples (lane = sample). On GB300 an FP64 warp instruction holds
 // its SM sub-partition for about 70 cycles whatever its active lanes, so one
-// thread's ~4,700 FP64 operations take about 0.15 ms however few samples a
-// call has; split this way a step costs its diagonal's chain only. Step j:
+// thread's ~4,700 FP64 operations take 0.15 ms or more however few samples a
+// call has. Split this way a step's FP64 work runs on several sub-partitions
+// at once; what remains per step is the dependent chain of the reciprocal
+// square root and the shared FP64 pipes (about 0.18 ms per call). Step j:
 // warp 0 forms d_j and 1/L(j,j) (the face sum of d_j formed one step ahead by
 // warp NC, whose band row is the shortest), warp l (1..NC) the dot product of
 // row j+l, warp NC+1 the forward value; after a barrier warp l scales its entry of
