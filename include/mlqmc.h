@@ -225,7 +225,10 @@ mlqmc_status mlqmc_sample_levels(mlqmc_ctx* c, const mlqmc_work* work, int32_t n
 /*
  * Algorithm 1 (MG-MLQMC(eps)): adaptive levels and sample doubling until the
  * variance estimate is <= eps^2/2 and the bias estimate is <= eps/sqrt(2).
- * Blocking; the result is in host memory. Uses its own stream.
+ * Blocking; the result is in host memory. Uses its own stream. After each
+ * round the reuse sums and the context's deferred device status come back in
+ * one synchronisation (the status word is then cleared, as by
+ * mlqmc_get_device_status); a device error ends the run with its status.
  */
 mlqmc_status mlqmc_estimate(mlqmc_ctx* c, double eps, const mlqmc_run_opts* opts, mlqmc_result* out);
 
