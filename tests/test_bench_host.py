@@ -116,7 +116,9 @@ def test_final_line_is_compact(bench):
            "sample": "N_l/16=[256, 128, 64, 32, 16, 8, 4, 2, 1] per shift x 16 shifts (8176 samples), one shift per "
                      "process, 30.1 s wall; oracle lattice 2^8 pts"}
     fp64 = {"value": 90000.0, "ms_per_step": 1453.2, "steps": 3, "speedup_mixed": 6.1}
-    tte = {"eps": 1e-4, "mixed_tf32": {"seconds": 1.234, "L": 5, "rounds": 40}, "fp64": {"seconds": 7.89}}
+    tte = {"eps": 1e-4, "mixed_tf32": {"seconds": 1.234, "L": 5, "rounds": 40}, "fp64": {"seconds": 7.89},
+           "mixed_tf32_round_graphs": {"seconds": 1.345}, "mixed_tf32_batched": {"seconds": 1.111, "rounds": 33},
+           "fp64_batched": {"seconds": 6.543}}
     line = bench.make_line(args, 1, 654321.5, 2000.0, 130816, ["gs", "whole", "whole", "whole", "tma", "tma", "tma",
                                                                 "tma", "tma"], 12.3, 123, 10, roof, e2e, clocks, cpu,
                            fp64, tte)
@@ -128,6 +130,8 @@ def test_final_line_is_compact(bench):
     assert line["config"]["workload"].startswith("MG-MLQMC with reuse, 9 levels")
     for key in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
         assert key in line["roofline"]
+    for key in ("mixed_s", "fp64_s", "mixed_round_graphs_s", "mixed_batched_s", "mixed_batched_rounds", "fp64_batched_s"):
+        assert line["time_to_eps"][key] is not None, key
 
 
 def test_cpu_sample_keeps_the_level_mix(bench):
